@@ -1,0 +1,397 @@
+/*
+ * Plain, slow CPU oracle for schema-driven layout conversion.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline / reference legs may load this library.  It
+ * shares no code, header or table with the CUDA library.
+ *
+ * What it computes is the plain definition of the paper's default transfer
+ * between layouts: "copy the arrays corresponding to each property one by
+ * one" (Sec. VI-B, Defining Layouts), i.e. for every object and every
+ * property, copy the property's bytes from its source address to its
+ * destination address.  Layout rules:
+ *
+ *  - Schema lowering.  Sub-group members are stored as if declared at the
+ *    top level (Sec. V, sub-group property); an array property of extent E
+ *    is E separate per-index columns (Sec. V, array property); a jagged
+ *    vector property keeps a prefix sum of the sizes as a global property
+ *    and all values as one contiguous vector (Sec. V, jagged vector
+ *    property).
+ *  - AoS record: natural C alignment, a sub-group laid out as a nested
+ *    struct (aligned to its widest member, size rounded up to it).  The
+ *    jagged member is the pair {uint32 length, uint64 begin} at the member's
+ *    position, `begin` an element index into a separate child-record pool.
+ *  - SoA, single block ("DynamicStruct", Sec. VI-B): columns in flattened
+ *    order, each starting at a multiple of 128 bytes; for a jagged schema
+ *    the offsets column (N+1 entries) and the child columns (M entries
+ *    each) follow.
+ *  - AoSoA(B) ("allocating memory in blocks of a given size", Sec. IV):
+ *    each block is the C struct { T_0 c0[B]; T_1 c1[B]; ... } of the
+ *    flattened columns.
+ *  - Every destination byte that no property writes is 0.
+ *
+ * Parity unpinned: the 128-byte SoA column alignment, the AoSoA in-block
+ * arrangement and the AoS jagged descriptor are readings (the paper fixes no
+ * bytes for them); they are checked by round trips and special cases only.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL 1
+#define ORC_ESIZE 2
+#define ORC_EOVERFLOW 4
+
+#define ORC_AOS 0
+#define ORC_SOA 1
+#define ORC_AOSOA 2
+
+#define TK_FIELD 1
+#define TK_GROUP 2
+#define TK_END 3
+#define TK_JAGGED 4
+
+#define ORC_MAXCOLS 1024
+
+typedef struct orc_schema {
+  int ncols;
+  uint32_t col_size[ORC_MAXCOLS];
+  uint64_t col_aos_off[ORC_MAXCOLS];
+  uint64_t stride;
+  uint64_t align;
+  int has_jagged;
+  uint64_t len_off;   /* AoS offset of the uint32 length */
+  uint64_t begin_off; /* AoS offset of the uint64 begin */
+  uint32_t off_size;  /* 4 or 8 */
+  struct orc_schema* child;
+} orc_schema;
+
+typedef struct orc_side {
+  int32_t kind;
+  uint32_t block;
+  uint8_t* base;        /* AoS records / AoSoA blocks / SoA single block */
+  uint8_t** cols;       /* SoA per-column pointers, or NULL */
+  uint8_t* offsets;     /* SoA offsets column, or NULL (inside base) */
+  uint8_t** child_cols; /* SoA child columns, or NULL (inside base) */
+  uint8_t* pool;        /* AoS child-record pool */
+  uint64_t n;           /* records */
+  uint64_t m;           /* children (capacity when destination) */
+} orc_side;
+
+static uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+static void free_schema(orc_schema* s) {
+  if (!s) return;
+  free_schema(s->child);
+  free(s);
+}
+
+/* Lays out members until TK_END (nested) or the end of the tokens.
+ * Column offsets are written relative to the start of this (sub)struct. */
+static int layout_members(orc_schema* s, const int32_t* tk, int ntk, int* pos,
+                          int nested, int in_child, uint64_t* size_out,
+                          uint64_t* align_out) {
+  uint64_t cur = 0, al = 1;
+  int closed = 0;
+  while (*pos < ntk) {
+    int op = tk[*pos];
+    if (op == TK_END) {
+      if (nested <= 0) return ORC_EINVAL;
+      (*pos)++;
+      closed = 1;
+      break;
+    } else if (op == TK_FIELD) {
+      if (*pos + 2 >= ntk) return ORC_EINVAL;
+      uint32_t size = (uint32_t)tk[*pos + 1];
+      int32_t extent = tk[*pos + 2];
+      *pos += 3;
+      if (!(size == 1 || size == 2 || size == 4 || size == 8) || extent < 1)
+        return ORC_EINVAL;
+      uint64_t off = align_up(cur, size);
+      for (int k = 0; k < extent; k++) {
+        if (s->ncols >= ORC_MAXCOLS) return ORC_EINVAL;
+        s->col_size[s->ncols] = size;
+        s->col_aos_off[s->ncols] = off + (uint64_t)k * size;
+        s->ncols++;
+      }
+      cur = off + (uint64_t)extent * size;
+      if (size > al) al = size;
+    } else if (op == TK_GROUP) {
+      (*pos)++;
+      int first = s->ncols;
+      int had_jag = s->has_jagged;
+      uint64_t gsize, galign;
+      int rc = layout_members(s, tk, ntk, pos, 1, in_child, &gsize, &galign);
+      if (rc) return rc;
+      uint64_t goff = align_up(cur, galign);
+      for (int c = first; c < s->ncols; c++) s->col_aos_off[c] += goff;
+      if (s->has_jagged && !had_jag) {
+        s->len_off += goff;
+        s->begin_off += goff;
+      }
+      cur = goff + gsize;
+      if (galign > al) al = galign;
+    } else if (op == TK_JAGGED) {
+      if (*pos + 2 >= ntk || s->has_jagged || in_child) return ORC_EINVAL;
+      uint32_t osz = (uint32_t)tk[*pos + 1];
+      int nchild = tk[*pos + 2];
+      *pos += 3;
+      if (!(osz == 4 || osz == 8) || nchild < 1 || *pos + nchild > ntk)
+        return ORC_EINVAL;
+      orc_schema* ch = (orc_schema*)calloc(1, sizeof(orc_schema));
+      if (!ch) return ORC_EINVAL;
+      int cpos = 0;
+      uint64_t csize, calign;
+      int rc = layout_members(ch, tk + *pos, nchild, &cpos, 0, 1, &csize, &calign);
+      if (rc || ch->ncols == 0) {
+        free_schema(ch);
+        return ORC_EINVAL;
+      }
+      ch->stride = csize;
+      ch->align = calign;
+      *pos += nchild;
+      s->has_jagged = 1;
+      s->off_size = osz;
+      s->child = ch;
+      s->len_off = align_up(cur, 4);
+      cur = s->len_off + 4;
+      s->begin_off = align_up(cur, 8);
+      cur = s->begin_off + 8;
+      if (al < 8) al = 8;
+    } else {
+      return ORC_EINVAL;
+    }
+  }
+  if (nested > 0 && !closed) return ORC_EINVAL;
+  *size_out = align_up(cur, al);
+  *align_out = al;
+  return ORC_OK;
+}
+
+orc_schema* orc_schema_new(const int32_t* tokens, int ntokens, int* status) {
+  orc_schema* s = (orc_schema*)calloc(1, sizeof(orc_schema));
+  int pos = 0;
+  uint64_t size, al;
+  int rc = s ? layout_members(s, tokens, ntokens, &pos, 0, 0, &size, &al) : ORC_EINVAL;
+  if (rc == ORC_OK && s->ncols == 0 && !s->has_jagged) rc = ORC_EINVAL;
+  if (rc) {
+    free_schema(s);
+    if (status) *status = rc;
+    return NULL;
+  }
+  s->stride = size;
+  s->align = al;
+  if (status) *status = ORC_OK;
+  return s;
+}
+
+void orc_schema_free(orc_schema* s) { free_schema(s); }
+int orc_ncols(const orc_schema* s) { return s->ncols; }
+uint32_t orc_col_size(const orc_schema* s, int c) { return s->col_size[c]; }
+uint64_t orc_col_aos_off(const orc_schema* s, int c) { return s->col_aos_off[c]; }
+uint64_t orc_stride(const orc_schema* s) { return s->stride; }
+int orc_has_jagged(const orc_schema* s) { return s->has_jagged; }
+uint64_t orc_len_off(const orc_schema* s) { return s->len_off; }
+uint64_t orc_begin_off(const orc_schema* s) { return s->begin_off; }
+uint32_t orc_off_size(const orc_schema* s) { return s->off_size; }
+const orc_schema* orc_child(const orc_schema* s) { return s->child; }
+
+/* ---- layout address rules ---- */
+
+/* AoSoA(B): start of column c inside a block (C struct of B-element arrays). */
+uint64_t orc_aosoa_col_start(const orc_schema* s, uint32_t B, int c) {
+  uint64_t end = 0, start = 0;
+  for (int k = 0; k <= c; k++) {
+    start = align_up(end, s->col_size[k]);
+    end = start + (uint64_t)B * s->col_size[k];
+  }
+  return start;
+}
+
+uint64_t orc_aosoa_block_bytes(const orc_schema* s, uint32_t B) {
+  uint64_t end = 0, al = 1;
+  for (int k = 0; k < s->ncols; k++) {
+    end = align_up(end, s->col_size[k]) + (uint64_t)B * s->col_size[k];
+    if (s->col_size[k] > al) al = s->col_size[k];
+  }
+  return align_up(end, al);
+}
+
+/* SoA single block: region r of the block, in order: the data columns
+ * 0..ncols-1, then (jagged) the offsets column, then the child columns.
+ * Each region starts at a multiple of 128 bytes. */
+static uint64_t soa_region_bytes(const orc_schema* s, uint64_t n, uint64_t m, int r) {
+  if (r < s->ncols) return n * s->col_size[r];
+  if (r == s->ncols) return (n + 1) * s->off_size;
+  return m * s->child->col_size[r - s->ncols - 1];
+}
+
+static int soa_nregions(const orc_schema* s) {
+  return s->ncols + (s->has_jagged ? 1 + s->child->ncols : 0);
+}
+
+uint64_t orc_soa_region_start(const orc_schema* s, uint64_t n, uint64_t m, int r) {
+  uint64_t start = 0, end = 0;
+  for (int k = 0; k <= r; k++) {
+    start = align_up(end, 128);
+    end = start + soa_region_bytes(s, n, m, k);
+  }
+  return start;
+}
+
+uint64_t orc_soa_bytes(const orc_schema* s, uint64_t n, uint64_t m) {
+  int nr = soa_nregions(s);
+  uint64_t end = orc_soa_region_start(s, n, m, nr - 1) + soa_region_bytes(s, n, m, nr - 1);
+  return align_up(end, 128);
+}
+
+/* Bytes of the `base` buffer of a side. */
+uint64_t orc_base_bytes(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m) {
+  if (kind == ORC_AOS) return n * s->stride;
+  if (kind == ORC_SOA) return orc_soa_bytes(s, n, m);
+  if (kind == ORC_AOSOA) return (B ? (n + B - 1) / B : 0) * orc_aosoa_block_bytes(s, B);
+  return 0;
+}
+
+static uint8_t* col_addr(const orc_schema* s, const orc_side* v, int c, uint64_t i) {
+  uint64_t sz = s->col_size[c];
+  switch (v->kind) {
+    case ORC_AOS:
+      return v->base + i * s->stride + s->col_aos_off[c];
+    case ORC_SOA:
+      if (v->cols) return v->cols[c] + i * sz;
+      return v->base + orc_soa_region_start(s, v->n, v->m, c) + i * sz;
+    default:
+      return v->base + (i / v->block) * orc_aosoa_block_bytes(s, v->block) +
+             orc_aosoa_col_start(s, v->block, c) + (i % v->block) * sz;
+  }
+}
+
+static uint8_t* offsets_ptr(const orc_schema* s, const orc_side* v) {
+  if (v->offsets) return v->offsets;
+  return v->base + orc_soa_region_start(s, v->n, v->m, s->ncols);
+}
+
+static uint8_t* child_col_ptr(const orc_schema* s, const orc_side* v, int cc) {
+  if (v->child_cols) return v->child_cols[cc];
+  return v->base + orc_soa_region_start(s, v->n, v->m, s->ncols + 1 + cc);
+}
+
+static uint64_t rd(const uint8_t* p, uint32_t size) {
+  uint64_t x = 0;
+  memcpy(&x, p, size); /* little-endian host */
+  return x;
+}
+
+static void wr(uint8_t* p, uint64_t x, uint32_t size) { memcpy(p, &x, size); }
+
+static int valid_side(const orc_side* v) {
+  if (v->kind == ORC_AOSOA) return v->block >= 1;
+  return v->kind == ORC_AOS || v->kind == ORC_SOA;
+}
+
+/* Sets every byte of the destination to zero (step "zero the non-data
+ * bytes"; data bytes are overwritten afterwards). */
+static void zero_side(const orc_schema* s, const orc_side* d) {
+  if (d->kind == ORC_SOA && d->cols) {
+    for (int c = 0; c < s->ncols; c++) memset(d->cols[c], 0, d->n * s->col_size[c]);
+    if (s->has_jagged) {
+      memset(offsets_ptr(s, d), 0, (d->n + 1) * s->off_size);
+      for (int cc = 0; cc < s->child->ncols; cc++)
+        memset(child_col_ptr(s, d, cc), 0, d->m * s->child->col_size[cc]);
+    }
+    return;
+  }
+  memset(d->base, 0, orc_base_bytes(s, d->kind, d->block, d->n, d->m));
+  if (d->kind == ORC_SOA && s->has_jagged) {
+    if (d->offsets) memset(d->offsets, 0, (d->n + 1) * s->off_size);
+    if (d->child_cols)
+      for (int cc = 0; cc < s->child->ncols; cc++)
+        memset(d->child_cols[cc], 0, d->m * s->child->col_size[cc]);
+  }
+  if (d->kind == ORC_AOS && s->has_jagged && d->pool)
+    memset(d->pool, 0, d->m * s->child->stride);
+}
+
+/* Converts one collection from `src` to `dst` (same schema, same N).
+ * For a jagged schema only AoS <-> SoA is defined; *m_out receives the
+ * number of child values written. */
+int orc_convert(const orc_schema* s, const orc_side* src, orc_side* dst, uint64_t* m_out) {
+  if (!valid_side(src) || !valid_side(dst) || src->n != dst->n) return ORC_EINVAL;
+  uint64_t n = src->n;
+  if (m_out) *m_out = 0;
+  if (s->has_jagged) {
+    int a2s = src->kind == ORC_AOS && dst->kind == ORC_SOA;
+    int s2a = src->kind == ORC_SOA && dst->kind == ORC_AOS;
+    if (!a2s && !s2a) return ORC_EINVAL;
+    if (a2s) {
+      /* Prefix sum of the sizes, checked against the offset type (Sec. V,
+       * jagged vector property: the prefix type may be narrower than the
+       * collection's size type). */
+      uint64_t total = 0;
+      uint64_t lim = s->off_size == 4 ? 0xffffffffull : ~0ull;
+      for (uint64_t i = 0; i < n; i++) {
+        const uint8_t* rec = src->base + i * s->stride;
+        uint64_t len = rd(rec + s->len_off, 4);
+        uint64_t beg = rd(rec + s->begin_off, 8);
+        if (beg > src->m || len > src->m - beg) return ORC_EINVAL;
+        if (len > lim - total) return ORC_EOVERFLOW;
+        total += len;
+      }
+      if (total > dst->m) return ORC_ESIZE;
+    } else {
+      const uint8_t* off = offsets_ptr(s, src);
+      for (uint64_t i = 0; i < n; i++) {
+        uint64_t a = rd(off + i * s->off_size, s->off_size);
+        uint64_t b = rd(off + (i + 1) * s->off_size, s->off_size);
+        if (b < a || b - a > 0xffffffffull) return ORC_EINVAL;
+      }
+      if (n > 0 && rd(off + n * s->off_size, s->off_size) > src->m) return ORC_EINVAL;
+      if (dst->m < src->m) return ORC_ESIZE;
+    }
+  }
+
+  zero_side(s, dst);
+
+  /* The default transfer: every property of every object, one by one. */
+  for (uint64_t i = 0; i < n; i++)
+    for (int c = 0; c < s->ncols; c++)
+      memcpy(col_addr(s, dst, c, i), col_addr(s, src, c, i), s->col_size[c]);
+
+  if (!s->has_jagged) return ORC_OK;
+  const orc_schema* ch = s->child;
+  if (src->kind == ORC_AOS) {
+    uint8_t* off = offsets_ptr(s, dst);
+    uint64_t run = 0;
+    wr(off, 0, s->off_size);
+    for (uint64_t i = 0; i < n; i++) {
+      const uint8_t* rec = src->base + i * s->stride;
+      uint64_t len = rd(rec + s->len_off, 4);
+      uint64_t beg = rd(rec + s->begin_off, 8);
+      for (uint64_t k = 0; k < len; k++)
+        for (int cc = 0; cc < ch->ncols; cc++)
+          memcpy(child_col_ptr(s, dst, cc) + (run + k) * ch->col_size[cc],
+                 src->pool + (beg + k) * ch->stride + ch->col_aos_off[cc], ch->col_size[cc]);
+      run += len;
+      wr(off + (i + 1) * s->off_size, run, s->off_size);
+    }
+    if (m_out) *m_out = run;
+  } else {
+    const uint8_t* off = offsets_ptr(s, src);
+    for (uint64_t i = 0; i < n; i++) {
+      uint8_t* rec = dst->base + i * s->stride;
+      uint64_t a = rd(off + i * s->off_size, s->off_size);
+      uint64_t b = rd(off + (i + 1) * s->off_size, s->off_size);
+      wr(rec + s->len_off, b - a, 4);
+      wr(rec + s->begin_off, a, 8);
+    }
+    /* Child values are written contiguously, slot j <- value j. */
+    for (uint64_t j = 0; j < src->m; j++)
+      for (int cc = 0; cc < ch->ncols; cc++)
+        memcpy(dst->pool + j * ch->stride + ch->col_aos_off[cc],
+               child_col_ptr(s, src, cc) + j * ch->col_size[cc], ch->col_size[cc]);
+    if (m_out) *m_out = src->m;
+  }
+  return ORC_OK;
+}

@@ -1,0 +1,46 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake in a private copy of the oracle's C source (a
+dropped alignment, an off-by-one index, a wrong operand), builds it, and
+runs the pin tests against it in a subprocess: they must fail.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "mrn_oracle.c")
+
+MUTANTS = {
+    "aosoa_no_align": ("start = align_up(end, s->col_size[k]);", "start = end;"),
+    "begin_align_4": ("s->begin_off = align_up(cur, 8);", "s->begin_off = align_up(cur, 4);"),
+    "group_not_aligned": ("uint64_t goff = align_up(cur, galign);", "uint64_t goff = cur;"),
+    "no_tail_padding": ("*size_out = align_up(cur, al);", "*size_out = cur;"),
+    "offsets_off_by_one": ("wr(off + (i + 1) * s->off_size, run, s->off_size);",
+                           "wr(off + i * s->off_size, run, s->off_size);"),
+    "wrong_record": ("memcpy(col_addr(s, dst, c, i), col_addr(s, src, c, i), s->col_size[c]);",
+                     "memcpy(col_addr(s, dst, c, i), col_addr(s, src, c, (i + 1) % n), s->col_size[c]);"),
+    "soa_align_64": ("start = align_up(end, 128);", "start = align_up(end, 64);"),
+    "child_wrong_column": ("src->pool + (beg + k) * ch->stride + ch->col_aos_off[cc]",
+                           "src->pool + (beg + k) * ch->stride + ch->col_aos_off[0]"),
+    "aosoa_slot_swapped": ("(i % v->block) * sz;", "((v->block - 1 - i % v->block)) * sz;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, name
+    mut = tmp_path / "mutant.c"
+    mut.write_text(src.replace(old, new))
+    lib = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O1", "-shared", "-fPIC", str(mut), "-o", str(lib)], check=True)
+    env = dict(os.environ, MRN_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, "pins did not catch mutant %s" % name
+    assert "failed" in r.stdout

@@ -1,0 +1,326 @@
+"""Pins the CPU oracle to things other than itself.
+
+* numpy's aligned structured dtypes (the C compiler's layout rules) for the
+  AoS record and the AoSoA block, and numpy field access for the columns;
+* round-trip identities between layouts;
+* closed forms: all-equal field sizes make AoS->SoA a matrix transpose, a
+  single-field schema makes every layout a plain copy;
+* the jagged offsets invariants and numpy's cumsum / concatenation for the
+  flattened child values (Sec. V, jagged vector property);
+* brute force over every small schema, with unique byte values, so that a
+  lost, duplicated or misplaced byte fails.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+from np_layout import (struct_dtype, aos_from_values, aos_columns,
+                       block_dtype, aosoa_columns, fill_block_column)
+
+# a sub-group that needs alignment and tail padding of its own
+NESTED = [("a", "u8", 1),
+          ("g", "group", [("x", "f64", 1), ("y", "u8", 1),
+                          ("h", "group", [("p", "u16", 3)])]),
+          ("b", "u8", 1), ("c", "u32", 2)]
+
+SCHEMAS = {"points": datagen.POINTS, "cells": datagen.CELLS,
+           "sensor": datagen.SENSOR, "nested": NESTED}
+
+
+def values_for(desc, n, seed):
+    return datagen.random_columns(desc, n, seed)
+
+
+# ---------------------------------------------------------------- AoS rules
+
+@pytest.mark.parametrize("name", ["points", "cells", "sensor", "nested", "tracks", "particle"])
+def test_aos_offsets_match_numpy_aligned_struct(name):
+    desc = {"points": datagen.POINTS, "cells": datagen.CELLS,
+            "sensor": datagen.SENSOR, "nested": NESTED, "tracks": datagen.TRACKS,
+            "particle": datagen.PARTICLE}[name]
+    s = oracle.Schema(desc)
+    dt = struct_dtype(desc)
+    assert s.stride == dt.itemsize
+    # numpy offsets of the flattened leaves
+    offs = []
+
+    def walk(d, base):
+        for fname in d.names:
+            sub, off = d.fields[fname][0], d.fields[fname][1]
+            if sub.names is not None:
+                walk(sub, base + off)
+            elif fname.endswith("_length") or fname.endswith("_begin"):
+                continue
+            elif sub.shape:
+                offs.extend(base + off + k * sub.base.itemsize for k in range(sub.shape[0]))
+            else:
+                offs.append(base + off)
+    walk(dt, 0)
+    assert s.col_aos_off == offs
+    if s.has_jagged:
+        jn = datagen.jagged_member(desc)[0]
+        assert s.len_off == dt.fields[jn + "_length"][1]
+        assert s.begin_off == dt.fields[jn + "_begin"][1]
+
+
+def test_workload_strides():
+    # the three workload records: 32-byte points with 7 bytes of padding,
+    # 24-byte cells, 24-byte tracks with the {length, begin} descriptor
+    assert oracle.Schema(datagen.POINTS).stride == 32
+    assert oracle.Schema(datagen.POINTS).col_aos_off == [0, 4, 8, 12, 16, 24]
+    assert oracle.Schema(datagen.CELLS).stride == 24
+    t = oracle.Schema(datagen.TRACKS)
+    assert (t.stride, t.len_off, t.begin_off, t.child.stride) == (24, 12, 16, 8)
+
+
+@pytest.mark.parametrize("name", list(SCHEMAS))
+@pytest.mark.parametrize("n", [0, 1, 5, 33, 1000])
+def test_soa_to_aos_equals_numpy_fill(name, n):
+    desc = SCHEMAS[name]
+    s = oracle.Schema(desc)
+    d = values_for(desc, n, 11)
+    aos = oracle.pack(s, d, "aos")
+    ref = aos_from_values(desc, d["columns"], n)
+    assert aos.base[: n * s.stride].tobytes() == ref.tobytes()
+
+
+@pytest.mark.parametrize("name", list(SCHEMAS))
+@pytest.mark.parametrize("n", [0, 1, 7, 129, 1000])
+def test_aos_to_soa_equals_numpy_fields(name, n):
+    desc = SCHEMAS[name]
+    s = oracle.Schema(desc)
+    ref = aos_from_values(desc, values_for(desc, n, 3)["columns"], n)
+    raw = np.frombuffer(ref.tobytes(), np.uint8).copy() if n else np.zeros(1, np.uint8)
+    soa = oracle.convert(s, oracle.Side("aos", n, base=raw), "soa")
+    cols = aos_columns(desc, raw, n)
+    for c in range(s.ncols):
+        assert oracle.region(s, soa, c).tobytes() == cols[c].tobytes()
+    # every byte of the block outside the columns is zero
+    mask = np.ones(soa.base.size, bool)
+    for c in range(s.ncols):
+        st = s.soa_region_start(n, 0, c)
+        mask[st:st + n * s.col_size[c]] = False
+        assert st % 128 == 0
+    assert not soa.base[mask].any()
+
+
+# ------------------------------------------------------------- AoSoA rules
+
+@pytest.mark.parametrize("name", list(SCHEMAS))
+@pytest.mark.parametrize("B", [1, 3, 8, 32, 128])
+@pytest.mark.parametrize("n", [0, 1, 31, 32, 33, 300])
+def test_aosoa_matches_numpy_block_struct(name, B, n):
+    desc = SCHEMAS[name]
+    s = oracle.Schema(desc)
+    d = values_for(desc, n, 5)
+    assert s.aosoa_block_bytes(B) == block_dtype(desc, B).itemsize
+    out = oracle.pack(s, d, "aosoa", B)
+    cols, blocks = aosoa_columns(desc, out.base, n, B)
+    want = oracle.flat_columns(d["columns"])
+    for c in range(s.ncols):
+        assert cols[c].view(np.uint8).tobytes() == want[c].tobytes()
+    # tail slots of the last block and every alignment hole are zero:
+    # rebuild the blocks from the columns with numpy and compare all bytes
+    ref = np.zeros(len(blocks), block_dtype(desc, B))
+    for c in range(s.ncols):
+        fill_block_column(ref, c, cols[c], n)
+    assert out.base[: ref.nbytes].tobytes() == ref.tobytes()
+
+
+# ------------------------------------------------------------ round trips
+
+@pytest.mark.parametrize("name", list(SCHEMAS))
+@pytest.mark.parametrize("n", [0, 1, 100, 4097])
+def test_round_trips_identity(name, n):
+    desc = SCHEMAS[name]
+    s = oracle.Schema(desc)
+    d = values_for(desc, n, 21)
+    aos = oracle.pack(s, d, "aos")
+    a = oracle.convert(s, oracle.convert(s, aos, "soa"), "aos")
+    assert a.base.tobytes() == aos.base.tobytes()
+    b = oracle.convert(s, oracle.convert(s, oracle.convert(s, aos, "aosoa", 32), "soa"), "aos")
+    assert b.base.tobytes() == aos.base.tobytes()
+    soa = oracle.convert(s, aos, "soa")
+    c = oracle.convert(s, oracle.convert(s, oracle.convert(s, soa, "aosoa", 32), "aosoa", 128), "soa")
+    assert c.base.tobytes() == soa.base.tobytes()
+    via = oracle.convert(s, oracle.convert(s, aos, "aosoa", 8), "soa")
+    assert via.base.tobytes() == soa.base.tobytes()
+
+
+# ------------------------------------------------------------ closed forms
+
+@pytest.mark.parametrize("size,dt", [(1, "u8"), (2, "u16"), (4, "f32"), (8, "u64")])
+@pytest.mark.parametrize("F", [1, 3, 5])
+def test_equal_sizes_is_a_transpose(size, dt, F):
+    desc = [("f%d" % k, dt, 1) for k in range(F)]
+    s = oracle.Schema(desc)
+    n = 77
+    d = values_for(desc, n, 9)
+    aos = oracle.pack(s, d, "aos")
+    mat = aos.base.view(np.dtype("<u%d" % size)).reshape(n, F)
+    soa = oracle.convert(s, aos, "soa")
+    for c in range(F):
+        assert oracle.region(s, soa, c).view(mat.dtype).tolist() == mat.T[c].tolist()
+
+
+@pytest.mark.parametrize("dt", ["u8", "u16", "f32", "f64"])
+def test_single_field_every_layout_is_a_copy(dt):
+    desc = [("v", dt, 1)]
+    s = oracle.Schema(desc)
+    n = 64
+    d = values_for(desc, n, 4)
+    raw = d["columns"][0].view(np.uint8).tobytes()
+    for kind, B in [("aos", 0), ("soa", 0), ("aosoa", 16), ("aosoa", 64)]:
+        out = oracle.pack(s, d, kind, B)
+        assert out.base.tobytes()[: len(raw)] == raw
+
+
+def test_array_property_is_extent_columns():
+    # an array property of extent E is E per-index columns (Sec. V)
+    desc = [("a", "u16", 3), ("b", "u8", 1)]
+    s = oracle.Schema(desc)
+    assert s.ncols == 4 and s.col_size == [2, 2, 2, 1]
+    n = 10
+    d = values_for(desc, n, 8)
+    soa = oracle.convert(s, oracle.pack(s, d, "aos"), "soa")
+    for k in range(3):
+        assert oracle.region(s, soa, k).view("<u2").tolist() == d["columns"][0][:, k].tolist()
+
+
+# ------------------------------------------------------------------ jagged
+
+def _tracks(n, seed, **kw):
+    s = oracle.Schema(datagen.TRACKS)
+    return s, datagen.workload("tracks", n, seed, **kw)
+
+
+@pytest.mark.parametrize("n", [0, 1, 5, 1000])
+def test_offsets_invariants_and_children(n):
+    s, d = _tracks(n, 2)
+    order = np.random.default_rng(7).permutation(n)
+    aos = oracle.shuffle_pool(s, oracle.pack(s, d, "aos"), order, gap=1)
+    soa = oracle.convert(s, aos, "soa", m=d["m"])
+    off = oracle.region(s, soa, s.ncols).view(np.uint32).astype(np.int64)
+    lens = d["lengths"].astype(np.int64)
+    assert off[0] == 0 and (np.diff(off) >= 0).all()
+    assert off[-1] == lens.sum() == d["m"] == soa.written
+    assert off.tolist() == np.concatenate([[0], np.cumsum(lens)]).tolist()
+    # children: concatenation of every parent's slice of the shuffled pool
+    pool = np.frombuffer(aos.pool[: aos.m * 8].tobytes(), struct_dtype([("index", "u32", 1), ("weight", "f32", 1)]))
+    recs = np.frombuffer(aos.base[: n * 24].tobytes(), struct_dtype(datagen.TRACKS), count=n)
+    parts = [pool[int(b):int(b) + int(L)] for b, L in zip(recs["hits_begin"], recs["hits_length"])]
+    kids = np.concatenate(parts) if parts else pool[:0]
+    assert oracle.region(s, soa, s.ncols + 1).tobytes() == np.ascontiguousarray(kids["index"]).tobytes()
+    assert oracle.region(s, soa, s.ncols + 2).tobytes() == np.ascontiguousarray(kids["weight"]).tobytes()
+    # parent columns through numpy field access
+    for c, name in enumerate(["pt", "eta", "label"]):
+        assert oracle.region(s, soa, c).tobytes() == np.ascontiguousarray(recs[name]).tobytes()
+
+
+@pytest.mark.parametrize("n", [0, 3, 500])
+def test_jagged_round_trip_canonical(n):
+    s, d = _tracks(n, 4)
+    aos = oracle.pack(s, d, "aos")
+    soa = oracle.convert(s, aos, "soa", m=d["m"])
+    back = oracle.convert(s, soa, "aos", m=d["m"])
+    assert back.base.tobytes() == aos.base.tobytes()
+    assert back.pool[: d["m"] * 8].tobytes() == aos.pool[: d["m"] * 8].tobytes()
+    # canonical pool: begin == offset, length == difference
+    recs = np.frombuffer(back.base[: n * 24].tobytes(), struct_dtype(datagen.TRACKS), count=n)
+    off = np.concatenate([[0], np.cumsum(d["lengths"].astype(np.int64))])
+    assert recs["hits_begin"].tolist() == off[:-1].tolist()
+    assert recs["hits_length"].tolist() == d["lengths"].tolist()
+
+
+def test_jagged_empty_children_and_u64_offsets():
+    desc = [("a", "u8", 1), ("v", "jagged", "u64", [("x", "f64", 1)])]
+    s = oracle.Schema(desc)
+    d = datagen.jagged_random(desc, 50, 3, mean_len=0.0)
+    assert d["m"] == 0
+    aos = oracle.pack(s, d, "aos")
+    soa = oracle.convert(s, aos, "soa", m=0)
+    assert oracle.region(s, soa, s.ncols).view(np.uint64).tolist() == [0] * 51
+
+
+def test_u32_offset_overflow_is_reported():
+    s = oracle.Schema(datagen.TRACKS)
+    n = 3
+    recs = np.zeros(n, struct_dtype(datagen.TRACKS))
+    recs["hits_length"] = 2**31
+    recs["hits_begin"] = 0
+    raw = np.frombuffer(recs.tobytes(), np.uint8).copy()
+    pool = np.zeros(8, np.uint8)  # never read: the prefix sum fails first
+    src = oracle.Side("aos", n, 2**32, base=raw, pool=pool)
+    dst = oracle.alloc(s, "soa", n, 0)
+    st, _ = oracle.convert_into(s, src, dst)
+    assert st == oracle.EOVERFLOW
+
+
+def test_bad_begin_and_small_capacity_rejected():
+    s, d = _tracks(20, 6)
+    aos = oracle.pack(s, d, "aos")
+    bad = oracle.Side("aos", 20, d["m"] - 1, base=aos.base, pool=aos.pool)
+    assert oracle.convert_into(s, bad, oracle.alloc(s, "soa", 20, d["m"]))[0] == oracle.EINVAL
+    small = oracle.alloc(s, "soa", 20, d["m"] - 1)
+    assert oracle.convert_into(s, aos, small)[0] == oracle.ESIZE
+
+
+# -------------------------------------------------------------- brute force
+
+DTS = ["u8", "u16", "u32", "u64", "f32", "f64"]
+FIELD_TYPES = [(dt, e) for dt in DTS for e in (1, 3)]
+
+
+def _small_schemas():
+    out = []
+    for k in (1, 2):
+        for combo in itertools.product(FIELD_TYPES, repeat=k):
+            out.append([("f%d" % i, dt, e) for i, (dt, e) in enumerate(combo)])
+    rng = np.random.default_rng(0)
+    for _ in range(60):
+        idx = rng.integers(0, len(FIELD_TYPES), 3)
+        out.append([("f%d" % i, *FIELD_TYPES[j]) for i, j in enumerate(idx)])
+    return out
+
+
+def _unique_bytes(s, n):
+    """AoS bytes where field byte k holds (k mod 251) + 1 and padding is 0."""
+    raw = np.zeros(max(1, n * s.stride), np.uint8)
+    k = 0
+    for i in range(n):
+        for c in range(s.ncols):
+            o = i * s.stride + s.col_aos_off[c]
+            for b in range(s.col_size[c]):
+                raw[o + b] = (k % 251) + 1
+                k += 1
+    return raw
+
+
+@pytest.mark.parametrize("desc", _small_schemas(), ids=lambda d: "-".join("%s%d" % (m[1], m[2]) for m in d))
+def test_brute_force_small_schemas(desc):
+    s = oracle.Schema(desc)
+    dt = struct_dtype(desc)
+    assert s.stride == dt.itemsize
+    for n in (0, 1, 2, 3, 7, 8, 9):
+        raw = _unique_bytes(s, n)
+        src = oracle.Side("aos", n, base=raw)
+        want = aos_columns(desc, raw, n)
+        soa = oracle.convert(s, src, "soa")
+        for c in range(s.ncols):
+            assert oracle.region(s, soa, c).tobytes() == want[c].tobytes()
+        for B in (1, 2, 4, 8):
+            blk = oracle.convert(s, src, "aosoa", B)
+            cols, blocks = aosoa_columns(desc, blk.base, n, B)
+            ref = np.zeros(len(blocks), block_dtype(desc, B))
+            for c in range(s.ncols):
+                assert cols[c].tobytes() == want[c].tobytes()
+                fill_block_column(ref, c, want[c], n)
+            assert blk.base[: ref.nbytes].tobytes() == ref.tobytes()
+            back = oracle.convert(s, blk, "aos")
+            assert back.base[: n * s.stride].tobytes() == raw[: n * s.stride].tobytes()
+        # no byte lost or duplicated: the multiset of data bytes is preserved
+        got = np.concatenate([oracle.region(s, soa, c) for c in range(s.ncols)]) if n else np.zeros(0, np.uint8)
+        assert sorted(got.tolist()) == sorted(raw[raw != 0].tolist())
