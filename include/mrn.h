@@ -1,0 +1,337 @@
+/*
+ * mrn.h — C ABI of the B300 (sm_103a) layout-conversion library.
+ *
+ * The library converts collections of records between memory layouts, as
+ * described by "Marionette: Data Structure Description and Management for
+ * Heterogeneous Computing" (arXiv 2511.04853):
+ *
+ *   - a record schema is a list of properties (Sec. V): per-item properties,
+ *     fixed-extent array properties, sub-groups and one jagged vector
+ *     property;
+ *   - a collection is stored in a layout (Sec. IV, Sec. VI-B): array of
+ *     structures (AoS), structure of arrays (SoA) or blocks of B records
+ *     (AoSoA(B)), in a memory context (Sec. VI-A: host, pinned host, device);
+ *   - a transfer between two layouts copies every property of every object
+ *     (Sec. VI-B "Transferring data between layouts"); between memory
+ *     contexts it is fused with the copy (Sec. VI-A, memcopy_with_context).
+ *
+ * Conventions for every call:
+ *   - Every function returns an int status (MRN_OK = 0, else an MRN_E* code)
+ *     unless documented otherwise.  No C++ exception crosses this boundary.
+ *   - Pointers are plain host or device addresses.  The caller owns every
+ *     data buffer; the library owns schemas, its scratch and staging memory,
+ *     batches and servers.
+ *   - Device work is ordered on the caller's stream (`mrn_stream` is a
+ *     cudaStream_t; NULL is the legacy default stream) and is asynchronous
+ *     unless documented otherwise.  Errors found on the host are returned at
+ *     once; errors found by a kernel (offset overflow, bad child indices, a
+ *     destination that is too small, a wait that timed out) are recorded in
+ *     a per-device status word, returned and cleared by mrn_sync().
+ *   - Only the current CUDA device is used; device views must name it.
+ *   - Source and destination buffers must not overlap.
+ */
+#ifndef MRN_H
+#define MRN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define MRN_OK 0
+#define MRN_EINVAL 1       /* bad schema, view or argument                    */
+#define MRN_ESIZE 2        /* a destination (or child capacity) is too small  */
+#define MRN_EALIGN 3       /* a column is not aligned to its element size     */
+#define MRN_EOVERFLOW 4    /* a prefix sum does not fit the offset type       */
+#define MRN_ENOMEM 5       /* allocation failed / request exceeds a budget    */
+#define MRN_ETIMEOUT 6     /* a bounded device or host wait expired           */
+#define MRN_ECUDA 7        /* a CUDA runtime call failed                      */
+#define MRN_EBUSY 8        /* not finished yet (server poll)                  */
+#define MRN_ENOTFOUND 9    /* unknown ticket                                  */
+#define MRN_EUNSUPPORTED 10 /* valid request this build does not implement    */
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* mrn_status_str(int status);
+/* Library version, major*10000 + minor*100 + patch. */
+int mrn_version(void);
+
+/* ------------------------------------------------------------------ schema */
+/* Element types of a property.  MRN_BOOL is one byte, copied verbatim. */
+typedef enum mrn_dtype {
+  MRN_U8 = 0, MRN_I8 = 1, MRN_U16 = 2, MRN_I16 = 3, MRN_U32 = 4, MRN_I32 = 5,
+  MRN_U64 = 6, MRN_I64 = 7, MRN_F32 = 8, MRN_F64 = 9, MRN_BOOL = 10
+} mrn_dtype;
+
+typedef struct mrn_schema mrn_schema; /* opaque, library-owned */
+
+/* Creates an empty, unfinalized schema.  *out receives the handle. */
+int mrn_schema_create(mrn_schema** out);
+
+/* Appends a per-item property (extent 1) or an array property of `extent`
+ * elements (Sec. V, "per-item property", "array property").  An array of
+ * extent E is stored as E separate columns in SoA/AoSoA layouts and as a C
+ * array inside the AoS record.  `name` is copied (max 63 bytes). */
+int mrn_schema_add_field(mrn_schema* s, const char* name, int dtype, uint32_t extent);
+
+/* Opens / closes a sub-group property (Sec. V, "sub-group property"): its
+ * members are stored as separate columns, as if declared at the top level;
+ * in the AoS record the group is a nested struct (aligned to its widest
+ * member, size rounded up to that alignment).  Groups may nest. */
+int mrn_schema_begin_group(mrn_schema* s, const char* name);
+int mrn_schema_end_group(mrn_schema* s);
+
+/* Appends a jagged vector property (Sec. V, "jagged vector property"): a
+ * per-object vector of child records described by the finalized schema
+ * `child` (copied; the caller keeps ownership of `child`).  `offset_dtype`
+ * is MRN_U32 or MRN_U64, the type of the prefix sum of the sizes.
+ *   AoS side: the member is stored as {uint32 length; uint64 begin} at its
+ *     position in the record; `begin` indexes a separate pool of child
+ *     records (view.child_pool, child AoS layout).
+ *   SoA side: an offsets column of N+1 entries (offsets[0] = 0 unless an
+ *     offset base is given, offsets[N] = number of children) and one column
+ *     per flattened child property, holding all children contiguously.
+ * At most one jagged property per schema; the child may not be jagged.
+ * Returns MRN_EINVAL otherwise. */
+int mrn_schema_add_jagged(mrn_schema* s, const char* name, int offset_dtype,
+                          const mrn_schema* child);
+
+/* Compiles the schema (flattening, AoS offsets, column tables).  After this
+ * the schema is immutable and may be shared between threads. */
+int mrn_schema_finalize(mrn_schema* s);
+
+/* Frees a schema.  Views that point to it must not be used afterwards. */
+void mrn_schema_destroy(mrn_schema* s);
+
+typedef struct mrn_schema_info {
+  uint32_t n_columns;      /* flattened data columns (jagged member excluded) */
+  uint32_t aos_stride;     /* bytes per AoS record                           */
+  uint32_t aos_align;      /* alignment of the AoS record                    */
+  int32_t has_jagged;      /* 1 if the schema has a jagged property          */
+  uint32_t jag_length_offset; /* AoS offset of the jagged uint32 length      */
+  uint32_t jag_begin_offset;  /* AoS offset of the jagged uint64 begin       */
+  uint32_t offset_size;    /* 4 or 8 (jagged), else 0                        */
+  uint32_t child_columns;  /* flattened child columns (jagged), else 0       */
+  uint32_t child_stride;   /* bytes per child AoS record (jagged), else 0    */
+  uint32_t reserved;
+  uint64_t hash;           /* structural hash (sizes, offsets, nesting)      */
+} mrn_schema_info;
+
+typedef struct mrn_column_info {
+  uint32_t size;        /* element bytes: 1, 2, 4 or 8                       */
+  uint32_t aos_offset;  /* byte offset inside the AoS record                 */
+  int32_t dtype;        /* mrn_dtype                                         */
+  uint32_t reserved;
+  char name[128];       /* dotted path, "[k]" suffix for array elements      */
+} mrn_column_info;
+
+/* Information about a finalized schema. */
+int mrn_schema_info_get(const mrn_schema* s, mrn_schema_info* out);
+/* Column c (0 <= c < n_columns) of a finalized schema; `child` = 1 selects
+ * the jagged child's columns. */
+int mrn_schema_column(const mrn_schema* s, int child, uint32_t c, mrn_column_info* out);
+/* AoS stride and the AoS offsets of the n_columns data columns (up to cap). */
+int mrn_schema_aos_layout(const mrn_schema* s, size_t* stride, size_t* offsets, size_t cap);
+
+/* ------------------------------------------------------------------ layout */
+typedef enum mrn_layout_kind { MRN_AOS = 0, MRN_SOA = 1, MRN_AOSOA = 2 } mrn_layout_kind;
+typedef enum mrn_memctx {
+  MRN_MEM_HOST = 0,        /* pageable host memory                           */
+  MRN_MEM_HOST_PINNED = 1, /* page-locked host memory (cudaHostAlloc)        */
+  MRN_MEM_DEVICE = 2       /* device global memory of `device`               */
+} mrn_memctx;
+
+/* kind + block size B (AoSoA only; B >= 1, ignored otherwise).
+ *   AoS:      record i at base + i*aos_stride.
+ *   SoA:      column c is a contiguous array; either view.columns[c], or, if
+ *             view.columns is NULL, the single-block ("DynamicStruct",
+ *             Sec. VI-B) arrangement inside view.base: regions in order
+ *             [data columns][offsets][child columns], each region starting at
+ *             a multiple of 128 bytes from base, sized for N records / N+1
+ *             offsets / M children.
+ *   AoSoA(B): block b at base + b*block_bytes is the C struct
+ *             { T_0 c0[B]; T_1 c1[B]; ... } of the flattened columns; record
+ *             i is slot i%B of block i/B.  Jagged schemas are not supported
+ *             in AoSoA (MRN_EUNSUPPORTED).
+ * In every destination, bytes no property writes (AoS padding, alignment
+ * holes, unused AoSoA slots of the last block) are written as zero. */
+typedef struct mrn_layout {
+  int32_t kind;
+  uint32_t block;
+} mrn_layout;
+
+typedef struct mrn_view {
+  const mrn_schema* schema;
+  mrn_layout layout;
+  int32_t mem;            /* mrn_memctx                                       */
+  int32_t device;         /* CUDA ordinal for MRN_MEM_DEVICE                  */
+  uint64_t n_records;     /* N, size tag of the objects                       */
+  uint64_t n_children;    /* M, size tag of the jagged values: the number of
+                             child records (source) or the child capacity
+                             (destination)                                    */
+  void* base;             /* AoS records / AoSoA blocks / single-block SoA    */
+  void* const* columns;   /* SoA: optional n_columns column pointers          */
+  void* offsets;          /* SoA jagged: optional offsets column (N+1)        */
+  void* const* child_columns; /* SoA jagged: optional child column pointers   */
+  void* child_pool;       /* AoS jagged: child records (child AoS layout)     */
+  uint64_t offset_base;   /* SoA jagged destination: added to every offset
+                             (shards of one collection); 0 otherwise          */
+} mrn_view;
+
+/* Bytes needed for view.base of a collection of n records / m children in
+ * `layout` (AoS: records only; the child pool is mrn_child_pool_bytes). */
+int mrn_required_bytes(const mrn_schema* s, mrn_layout layout, uint64_t n, uint64_t m, size_t* out);
+/* Bytes of an AoS child pool of m child records. */
+int mrn_child_pool_bytes(const mrn_schema* s, uint64_t m, size_t* out);
+/* Start of region r inside a single-block SoA of n records / m children:
+ * r < n_columns: data column r; r == n_columns: offsets; then child columns. */
+int mrn_soa_region_offset(const mrn_schema* s, uint64_t n, uint64_t m, uint32_t r, size_t* out);
+/* AoSoA(B): bytes per block, and the start of column c inside a block. */
+int mrn_aosoa_block_bytes(const mrn_schema* s, uint32_t B, size_t* out);
+int mrn_aosoa_column_offset(const mrn_schema* s, uint32_t B, uint32_t c, size_t* out);
+
+/* --------------------------------------------------------------- convert */
+/* Converts src into dst, both MRN_MEM_DEVICE on the current device, same
+ * schema and n_records.  Any pair of AoS / SoA / AoSoA(B) layouts for a
+ * schema without a jagged property; AoS <-> SoA for a jagged schema:
+ *   AoS -> SoA: offsets = offset_base + exclusive prefix sum of the lengths
+ *     (N+1 entries), child values gathered from child_pool[begin + k] in
+ *     object order.  dst.n_children is the child capacity; children beyond it
+ *     are not written and MRN_ESIZE is recorded.  Sum of lengths larger than
+ *     the offset type records MRN_EOVERFLOW; begin + length beyond
+ *     src.n_children records MRN_EINVAL (the bad children are not read).
+ *   SoA -> AoS: length = offsets[i+1] - offsets[i], begin = offsets[i]; the
+ *     src.n_children child values are written to pool slots 0..M-1
+ *     (dst.n_children must be >= src.n_children, else MRN_ESIZE).
+ * Asynchronous on `stream`.  The CUDA path is the only path: without a
+ * device the call returns MRN_ECUDA. */
+int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream);
+
+/* Waits for `stream` and returns the first error a kernel recorded since the
+ * previous mrn_sync on this device (then clears it), else MRN_OK.  When
+ * several were recorded the order is ETIMEOUT, EOVERFLOW, EINVAL, ESIZE. */
+int mrn_sync(void* stream);
+/* As mrn_sync, but returns every recorded code: bit k of *bits = code k. */
+int mrn_sync_bits(void* stream, uint32_t* bits);
+
+/* Sum of the jagged lengths of an AoS device view (the number of child
+ * values an AoS -> SoA conversion writes).  Synchronous; *m receives it. */
+int mrn_jagged_count(const mrn_view* src, uint64_t* m, void* stream);
+
+/* Test and fault-injection settings of the jagged AoS -> SoA scan (host
+ * side; they take effect for conversions planned afterwards):
+ *   key 1: index of a tile that never publishes its sum (-1: none), so that
+ *          its successors' bounded waits expire and record MRN_ETIMEOUT;
+ *   key 2: bound of each look-back wait in nanoseconds (default 2e9). */
+int mrn_debug_set(int key, long long value);
+
+/* ------------------------------------------------------- transfer+convert */
+typedef struct mrn_transfer_opts {
+  size_t chunk_bytes; /* source bytes per chunk (0: 4 MiB); rounded to records
+                         (and to whole blocks for AoSoA)                      */
+  int32_t n_slots;    /* staging slots in flight (0: 4, max 16)               */
+  int32_t reserved;
+} mrn_transfer_opts;
+
+/* Converts between a host view (MRN_MEM_HOST or MRN_MEM_HOST_PINNED) and a
+ * device view, in either direction (the analogue of a copy between
+ * collections in different memory contexts, Sec. VI-A/VI-B).  The source is
+ * split into chunks of whole records; host->device chunks are copied into
+ * device staging slots with cudaMemcpyAsync on a copy stream and converted
+ * from staging into their final place on a compute stream, so copies and
+ * conversions of different chunks overlap; device->host is the mirror
+ * (convert into staging, then copy out).  Equal layouts skip staging.
+ * Jagged schemas: the whole source is staged, then converted.
+ * Ordered after prior work on `stream`; later work on `stream` waits for
+ * it.  Pageable host memory works but serialises the copies. */
+int mrn_transfer_convert(const mrn_view* src, const mrn_view* dst,
+                         const mrn_transfer_opts* opts, void* stream);
+
+/* ---------------------------------------------------------------- batching */
+typedef struct mrn_job {
+  const mrn_view* src; /* device view */
+  const mrn_view* dst; /* device view */
+} mrn_job;
+
+typedef struct mrn_batch mrn_batch; /* opaque */
+
+/* Prepares many independent conversions (any schemas, any supported layout
+ * pairs, jagged AoS<->SoA included) to run in ONE persistent kernel launch:
+ * a device job table, a prefix over the jobs' tiles, per-job tile sizes from
+ * the autotuner cache.  With use_graph = 1 the launch sequence (scratch
+ * reset + persistent kernel) is captured once into a CUDA graph and each
+ * mrn_batch_launch replays it.  The views' buffers must stay valid while the
+ * batch is used.  Copies the job descriptions; `jobs` may be freed. */
+int mrn_batch_create(const mrn_job* jobs, size_t n_jobs, int use_graph, mrn_batch** out);
+/* Runs every job of the batch on `stream` (one persistent launch). */
+int mrn_batch_launch(mrn_batch* b, void* stream);
+/* Baseline: runs the same jobs with one mrn_convert launch per job. */
+int mrn_batch_launch_per_job(mrn_batch* b, void* stream);
+/* Points job j at new buffers of the same schemas, layouts and sizes (the
+ * job table is rewritten; the graph is reused). */
+int mrn_batch_update(mrn_batch* b, size_t j, const mrn_view* src, const mrn_view* dst);
+void mrn_batch_destroy(mrn_batch* b);
+
+typedef struct mrn_tune_result {
+  uint32_t threads;       /* threads per CTA                                  */
+  uint32_t ctas_per_sm;   /* resident CTAs per SM of the grid                 */
+  uint32_t tile_records;  /* records per tile                                 */
+  uint32_t reserved;
+  double gbps;            /* algorithmic GB/s of the winner                   */
+  double default_gbps;    /* algorithmic GB/s of the default configuration    */
+} mrn_tune_result;
+
+/* Times candidate launch shapes (threads per CTA, CTAs per SM, records per
+ * tile) for converting n_hint records of `s` from `src` to `dst` layouts on
+ * scratch device buffers, and caches the fastest for this (schema hash,
+ * layout pair).  Later conversions and batches use the cached shape.
+ * Synchronous.  `out` may be NULL. */
+int mrn_autotune(const mrn_schema* s, mrn_layout src, mrn_layout dst, uint64_t n_hint,
+                 mrn_tune_result* out);
+/* Forgets every cached tuning result. */
+int mrn_autotune_clear(void);
+
+/* ------------------------------------------------------------------ server */
+typedef struct mrn_server mrn_server; /* opaque, internally synchronised */
+
+typedef struct mrn_server_opts {
+  size_t hbm_budget_bytes; /* device memory the server may hold at once       */
+  int32_t max_slots;       /* requests on the device at once (0: 8)           */
+  int32_t reserved;
+  size_t chunk_bytes;      /* transfer chunk (0: 4 MiB)                       */
+} mrn_server_opts;
+
+typedef struct mrn_server_stats {
+  uint64_t submitted, admitted, completed, rejected, failed;
+  uint64_t bytes_in, bytes_out;  /* source / destination bytes of completed   */
+  double p50_ms, p99_ms, max_ms, mean_ms; /* latency, arrival -> completion   */
+  double busy_s;                 /* wall time from first arrival to last done */
+  uint64_t peak_device_bytes;    /* high-water mark of admitted footprints    */
+} mrn_server_stats;
+
+/* Starts a conversion server on the current device: a host thread admits
+ * requests in arrival order as slots and budget allow (continuous batching:
+ * new requests join while others are on the device), runs each on its own
+ * stream pair, and records latency from submission to completion. */
+int mrn_server_create(const mrn_server_opts* opts, mrn_server** out);
+/* Queues one conversion.  At least one side must be a host view; device
+ * sides must be on the current device.  A request whose device footprint
+ * (staging plus device intermediates) exceeds the whole budget is rejected
+ * at once with MRN_ENOMEM.  *ticket identifies the request.  The views'
+ * buffers must stay valid until the request completes. */
+int mrn_server_submit(mrn_server* sv, const mrn_view* src, const mrn_view* dst, uint64_t* ticket);
+/* Non-blocking: *done = 1 and *status = the request's status when finished. */
+int mrn_server_poll(mrn_server* sv, uint64_t ticket, int* done, int* status);
+/* Blocks until the request finished or timeout_ns passed (MRN_ETIMEOUT). */
+int mrn_server_wait(mrn_server* sv, uint64_t ticket, uint64_t timeout_ns, int* status);
+int mrn_server_stats_get(mrn_server* sv, mrn_server_stats* out);
+/* Drains outstanding requests, stops the thread, frees device memory. */
+void mrn_server_destroy(mrn_server* sv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRN_H */

@@ -1,0 +1,382 @@
+// C ABI entry points for device conversions: view validation, plan
+// building, kernel dispatch, device status.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+
+#include "mrn_internal.h"
+
+namespace mrn {
+
+// Fault-injection and bounded-wait settings of the jagged look-back, set
+// through mrn_debug_set.
+std::atomic<long long> g_skip_publish_tile{-1};
+std::atomic<unsigned long long> g_timeout_ns{2000000000ull};
+
+namespace {
+
+bool is_pow2(uint64_t x) { return x && !(x & (x - 1)); }
+
+uint32_t log2u(uint64_t x) {
+  uint32_t k = 0;
+  while ((1ull << k) < x) ++k;
+  return k;
+}
+
+uint32_t lowbit(uint64_t x) { return x ? (uint32_t)(x & (~x + 1)) : 1u << 30; }
+
+int current_device() {
+  int d = -1;
+  if (cudaGetDevice(&d) != cudaSuccess) return -1;
+  return d;
+}
+
+bool on_device(const mrn_view& v) { return v.mem == MRN_MEM_DEVICE; }
+
+// Fills the field-major column pointers of a SoA / AoSoA side.
+int fm_side(const mrn_schema* s, const mrn_view& v, bool child, SidePlan* sp) {
+  const mrn_schema* t = child ? s->child.get() : s;
+  const uint32_t nc = (uint32_t)t->cols.size();
+  std::memset(sp, 0, sizeof(*sp));
+  sp->kind = v.layout.kind;
+  sp->block_shift = MRN_NO_SHIFT;
+  if (v.layout.kind == MRN_SOA) {
+    void* const* cols = child ? v.child_columns : v.columns;
+    for (uint32_t c = 0; c < nc; ++c) {
+      char* p;
+      if (cols) {
+        p = static_cast<char*>(cols[c]);
+      } else {
+        if (!v.base) return MRN_EINVAL;
+        const uint32_t region = child ? (uint32_t)s->cols.size() + 1 + c : c;
+        p = static_cast<char*>(v.base) + soa_region_start(s, v.n_records, v.n_children, region);
+      }
+      if (!p && (child ? v.n_children : v.n_records) > 0) return MRN_EINVAL;
+      if (reinterpret_cast<uintptr_t>(p) % t->cols[c].size) return MRN_EALIGN;
+      sp->col[c] = p;
+    }
+    return MRN_OK;
+  }
+  // AoSoA
+  const uint32_t B = v.layout.block;
+  sp->block = B;
+  sp->block_bytes = aosoa_block_bytes(t, B);
+  if (is_pow2(B)) sp->block_shift = log2u(B);
+  sp->base = static_cast<char*>(v.base);
+  if (!sp->base && v.n_records > 0) return MRN_EINVAL;
+  if (reinterpret_cast<uintptr_t>(sp->base) % 8) return MRN_EALIGN;
+  for (uint32_t c = 0; c < nc; ++c) sp->col[c] = sp->base + aosoa_col_start(t, B, c);
+  return MRN_OK;
+}
+
+// AoS entries of a schema level, sorted by offset; the jagged descriptor is
+// included for the parent level.
+void aos_entries(const mrn_schema* t, bool with_jag, ConvPlan* p) {
+  uint32_t k = 0;
+  for (uint32_t c = 0; c < t->cols.size(); ++c)
+    p->aos_cols[k++] = ColPlan{(uint16_t)t->cols[c].size, (int16_t)c, t->cols[c].aos_off};
+  if (with_jag && t->has_jagged) {
+    p->aos_cols[k++] = ColPlan{4, (int16_t)FM_JLEN, t->len_off};
+    p->aos_cols[k++] = ColPlan{8, (int16_t)FM_JBEGIN, t->begin_off};
+  }
+  std::stable_sort(p->aos_cols, p->aos_cols + k,
+                   [](const ColPlan& a, const ColPlan& b) { return a.aos_off < b.aos_off; });
+  p->naos = k;
+  p->ncols = (uint32_t)t->cols.size();
+  for (uint32_t c = 0; c < t->cols.size(); ++c) p->fm_size[c] = (uint8_t)t->cols[c].size;
+  p->stride = t->stride;
+  p->aos_words = (t->stride + 3) / 4;
+}
+
+uint32_t aos_vec(uint32_t stride, const void* base) {
+  return std::min<uint32_t>(16, std::min(lowbit(stride), lowbit(reinterpret_cast<uintptr_t>(base))));
+}
+
+// Plan of one schema level between two views (child = the jagged children).
+int level_plan(const mrn_schema* s, const mrn_view& src, const mrn_view& dst, bool child, uint64_t n,
+               ConvPlan* p) {
+  std::memset(p, 0, sizeof(*p));
+  const mrn_schema* t = child ? s->child.get() : s;
+  if (t->cols.size() > MRN_MAX_COLS) return MRN_EUNSUPPORTED;
+  aos_entries(t, !child, p);
+  p->n = n;
+  p->n_fm_pad = n;
+  const bool sa = src.layout.kind == MRN_AOS, da = dst.layout.kind == MRN_AOS;
+  int rc;
+  if (sa && !da) {
+    p->dir = DIR_AOS_FM;
+    p->src.kind = K_AOS;
+    p->src.base = static_cast<char*>(child ? src.child_pool : src.base);
+    if ((rc = fm_side(s, dst, child, &p->dst))) return rc;
+    p->vec = aos_vec(p->stride, p->src.base);
+  } else if (!sa && da) {
+    p->dir = DIR_FM_AOS;
+    p->dst.kind = K_AOS;
+    p->dst.base = static_cast<char*>(child ? dst.child_pool : dst.base);
+    if ((rc = fm_side(s, src, child, &p->src))) return rc;
+    p->vec = aos_vec(p->stride, p->dst.base);
+  } else if (!sa && !da) {
+    p->dir = DIR_FM_FM;
+    if ((rc = fm_side(s, src, child, &p->src))) return rc;
+    if ((rc = fm_side(s, dst, child, &p->dst))) return rc;
+    p->vec = 1;
+  } else {
+    return MRN_EINVAL;  // AoS -> AoS is a plain copy, handled by the caller
+  }
+  if (!child && dst.layout.kind == MRN_AOSOA) {
+    const uint64_t B = dst.layout.block;
+    p->n_fm_pad = (n + B - 1) / B * B;
+  }
+  if ((p->dir == DIR_AOS_FM && !p->src.base && n) || (p->dir == DIR_FM_AOS && !p->dst.base && n))
+    return MRN_EINVAL;
+  return MRN_OK;
+}
+
+// Alignment holes of a single-block SoA or AoSoA destination.
+void gap_plan(const mrn_schema* s, const mrn_view& dst, GapPlan* g) {
+  std::memset(g, 0, sizeof(*g));
+  auto add = [&](uint64_t a, uint64_t b) {
+    if (b > a && g->ngaps < MRN_MAX_GAPS) {
+      g->off[g->ngaps] = a;
+      g->len[g->ngaps] = (uint32_t)(b - a);
+      g->ngaps++;
+    }
+  };
+  g->base = static_cast<char*>(dst.base);
+  if (dst.layout.kind == MRN_SOA) {
+    if (dst.columns || !dst.base) return;
+    const uint64_t n = dst.n_records, m = dst.n_children;
+    const uint32_t nc = (uint32_t)s->cols.size();
+    const uint32_t nr = nc + (s->has_jagged ? 1 + (uint32_t)s->child->cols.size() : 0);
+    if (s->has_jagged && (dst.offsets || dst.child_columns)) return;
+    uint64_t prev_end = 0;
+    for (uint32_t r = 0; r < nr; ++r) {
+      const uint64_t st = soa_region_start(s, n, m, r);
+      add(prev_end, st);
+      uint64_t bytes = r < nc ? n * s->cols[r].size
+                              : (r == nc ? (n + 1) * s->off_size : m * s->child->cols[r - nc - 1].size);
+      prev_end = st + bytes;
+    }
+    add(prev_end, soa_total_bytes(s, n, m));
+    g->nblocks = 1;
+    g->block_bytes = 0;
+  } else if (dst.layout.kind == MRN_AOSOA) {
+    const uint32_t B = dst.layout.block;
+    uint64_t prev_end = 0;
+    for (uint32_t c = 0; c < s->cols.size(); ++c) {
+      const uint64_t st = aosoa_col_start(s, B, c);
+      add(prev_end, st);
+      prev_end = st + (uint64_t)B * s->cols[c].size;
+    }
+    add(prev_end, aosoa_block_bytes(s, B));
+    g->block_bytes = aosoa_block_bytes(s, B);
+    g->nblocks = (dst.n_records + B - 1) / B;
+  }
+}
+
+}  // namespace
+
+int zero_dst_gaps(const mrn_view& dst, void* stream) {
+  GapPlan g;
+  gap_plan(dst.schema, dst, &g);
+  return g.ngaps ? launch_zero_gaps(g, stream) : MRN_OK;
+}
+
+int validate_pair(const mrn_view* src, const mrn_view* dst, bool need_device, bool* is_jagged) {
+  if (!src || !dst || !src->schema || !dst->schema) return MRN_EINVAL;
+  const mrn_schema* s = src->schema;
+  if (!s->finalized || !dst->schema->finalized || s->hash != dst->schema->hash) return MRN_EINVAL;
+  if (src->n_records != dst->n_records) return MRN_EINVAL;
+  for (const mrn_view* v : {src, dst}) {
+    if (v->layout.kind < MRN_AOS || v->layout.kind > MRN_AOSOA) return MRN_EINVAL;
+    if (v->layout.kind == MRN_AOSOA && v->layout.block < 1) return MRN_EINVAL;
+    if (v->mem < MRN_MEM_HOST || v->mem > MRN_MEM_DEVICE) return MRN_EINVAL;
+  }
+  if (need_device) {
+    const int dev = current_device();
+    if (dev < 0) return MRN_ECUDA;
+    if (!on_device(*src) || !on_device(*dst) || src->device != dev || dst->device != dev)
+      return MRN_EINVAL;
+  }
+  *is_jagged = s->has_jagged;
+  if (s->cols.size() > MRN_MAX_COLS) return MRN_EUNSUPPORTED;
+  if (s->has_jagged) {
+    if (s->child->cols.size() > MRN_MAX_COLS) return MRN_EUNSUPPORTED;
+    if (src->layout.kind == MRN_AOSOA || dst->layout.kind == MRN_AOSOA) return MRN_EUNSUPPORTED;
+    if (src->layout.kind == dst->layout.kind) return MRN_EUNSUPPORTED;
+  }
+  return MRN_OK;
+}
+
+uint64_t tune_key(uint64_t hash, const mrn_layout& a, const mrn_layout& b) {
+  uint64_t h = hash ^ 0x9e3779b97f4a7c15ull;
+  for (uint64_t v : {(uint64_t)a.kind, (uint64_t)a.block, (uint64_t)b.kind, (uint64_t)b.block}) {
+    h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+  }
+  return h;
+}
+
+int build_plan(const mrn_view& src, const mrn_view& dst, ConvPlan* p) {
+  int rc = level_plan(src.schema, src, dst, false, src.n_records, p);
+  mrn_layout a = src.layout, b = dst.layout;
+  if (a.kind != MRN_AOSOA) a.block = 0;
+  if (b.kind != MRN_AOSOA) b.block = 0;
+  p->tune_key = tune_key(src.schema->hash, a, b);
+  return rc;
+}
+
+int build_jagged_plan(const mrn_view& src, const mrn_view& dst, JagPlan* jp) {
+  const mrn_schema* s = src.schema;
+  std::memset(jp, 0, sizeof(*jp));
+  const bool a2s = src.layout.kind == MRN_AOS;
+  const mrn_view& soa = a2s ? dst : src;
+  const uint64_t m = a2s ? dst.n_children : src.n_children;
+  int rc = level_plan(s, src, dst, false, src.n_records, &jp->parent);
+  if (rc) return rc;
+  rc = level_plan(s, src, dst, true, m, &jp->child);
+  if (rc) return rc;
+  jp->off_size = s->off_size;
+  char* offs = static_cast<char*>(soa.offsets);
+  if (!offs) {
+    if (!soa.base) return MRN_EINVAL;
+    offs = static_cast<char*>(soa.base) + soa_region_start(s, soa.n_records, soa.n_children,
+                                                           (uint32_t)s->cols.size());
+  }
+  if (reinterpret_cast<uintptr_t>(offs) % s->off_size) return MRN_EALIGN;
+  jp->offsets = offs;
+  jp->skip_publish_tile = g_skip_publish_tile.load();
+  jp->timeout_ns = g_timeout_ns.load();
+  if (a2s) {
+    jp->pool_n = src.n_children;
+    jp->capacity = dst.n_children;
+    jp->offset_base = dst.offset_base;
+    if (src.n_children > 0 && !src.child_pool) return MRN_EINVAL;
+  } else {
+    jp->m_src = src.n_children;
+    if (dst.n_children < src.n_children) return MRN_ESIZE;
+    if (src.n_children > 0 && !dst.child_pool) return MRN_EINVAL;
+  }
+  return MRN_OK;
+}
+
+}  // namespace mrn
+
+using namespace mrn;
+
+extern "C" {
+
+const char* mrn_status_str(int st) {
+  switch (st) {
+    case MRN_OK: return "MRN_OK";
+    case MRN_EINVAL: return "MRN_EINVAL";
+    case MRN_ESIZE: return "MRN_ESIZE";
+    case MRN_EALIGN: return "MRN_EALIGN";
+    case MRN_EOVERFLOW: return "MRN_EOVERFLOW";
+    case MRN_ENOMEM: return "MRN_ENOMEM";
+    case MRN_ETIMEOUT: return "MRN_ETIMEOUT";
+    case MRN_ECUDA: return "MRN_ECUDA";
+    case MRN_EBUSY: return "MRN_EBUSY";
+    case MRN_ENOTFOUND: return "MRN_ENOTFOUND";
+    case MRN_EUNSUPPORTED: return "MRN_EUNSUPPORTED";
+    default: return "MRN_UNKNOWN";
+  }
+}
+
+int mrn_version(void) { return 10000; }
+
+int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
+  bool jag = false;
+  int rc = validate_pair(src, dst, true, &jag);
+  if (rc) return rc;
+  const mrn_schema* s = src->schema;
+  if (jag) {
+    JagPlan jp;
+    if ((rc = build_jagged_plan(*src, *dst, &jp))) return rc;
+    if (src->layout.kind == MRN_AOS) {
+      cudaStream_t st = static_cast<cudaStream_t>(stream);
+      void* scratch = nullptr;
+      if (src->n_records > 0) {
+        if (cudaMallocAsync(&scratch, jagged_scratch_bytes(src->n_records), st) != cudaSuccess)
+          return MRN_ENOMEM;
+      }
+      rc = launch_jagged_a2s(jp, scratch, stream);
+      if (scratch) cudaFreeAsync(scratch, st);
+      if (rc) return rc;
+    } else {
+      if ((rc = launch_jagged_s2a(jp, stream))) return rc;
+    }
+    GapPlan g;
+    gap_plan(s, *dst, &g);
+    return g.ngaps ? launch_zero_gaps(g, stream) : MRN_OK;
+  }
+  if (src->layout.kind == MRN_AOS && dst->layout.kind == MRN_AOS) {
+    const size_t bytes = (size_t)src->n_records * s->stride;
+    if (bytes && (!src->base || !dst->base)) return MRN_EINVAL;
+    if (!bytes) return MRN_OK;
+    return cudaMemcpyAsync(dst->base, src->base, bytes, cudaMemcpyDeviceToDevice,
+                           static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? MRN_OK
+               : MRN_ECUDA;
+  }
+  ConvPlan p;
+  if ((rc = build_plan(*src, *dst, &p))) return rc;
+  const LaunchShape sh = tuned_shape(p);
+  if ((rc = launch_convert(p, stream, &sh))) return rc;
+  GapPlan g;
+  gap_plan(s, *dst, &g);
+  return g.ngaps ? launch_zero_gaps(g, stream) : MRN_OK;
+}
+
+int mrn_sync(void* stream) {
+  uint32_t bits = 0;
+  int rc = read_and_clear_status(stream, &bits);
+  if (rc) return rc;
+  return status_from_bits(bits);
+}
+
+int mrn_sync_bits(void* stream, uint32_t* bits) {
+  if (!bits) return MRN_EINVAL;
+  return read_and_clear_status(stream, bits);
+}
+
+int mrn_jagged_count(const mrn_view* src, uint64_t* m, void* stream) {
+  if (!src || !m || !src->schema || !src->schema->finalized || !src->schema->has_jagged ||
+      src->layout.kind != MRN_AOS || src->mem != MRN_MEM_DEVICE)
+    return MRN_EINVAL;
+  if (src->device != current_device()) return MRN_EINVAL;
+  *m = 0;
+  if (src->n_records == 0) return MRN_OK;
+  if (!src->base) return MRN_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ConvPlan p;
+  std::memset(&p, 0, sizeof(p));
+  aos_entries(src->schema, true, &p);
+  p.n = src->n_records;
+  p.src.base = static_cast<char*>(src->base);
+  uint64_t* d = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&d), sizeof(uint64_t), st) != cudaSuccess) return MRN_ENOMEM;
+  int rc = MRN_OK;
+  if (cudaMemsetAsync(d, 0, sizeof(uint64_t), st) != cudaSuccess) rc = MRN_ECUDA;
+  if (!rc) rc = launch_jagged_count(p, d, stream);
+  uint64_t h = 0;
+  if (!rc && cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = MRN_ECUDA;
+  cudaFreeAsync(d, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) rc = MRN_ECUDA;
+  if (!rc) *m = h;
+  return rc;
+}
+
+int mrn_debug_set(int key, long long value) {
+  switch (key) {
+    case 1: g_skip_publish_tile.store(value); return MRN_OK;
+    case 2:
+      if (value <= 0) return MRN_EINVAL;
+      g_timeout_ns.store((unsigned long long)value);
+      return MRN_OK;
+    default: return MRN_EINVAL;
+  }
+}
+
+}  // extern "C"

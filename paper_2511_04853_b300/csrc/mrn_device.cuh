@@ -1,0 +1,249 @@
+// Device routines of the conversion kernels (sm_103a).
+//
+// Mapping: one warp handles 32 consecutive records, one record per lane.
+//  - Record-major side (AoS): each lane moves its own record with the widest
+//    vector access the stride and base alignment allow (16 B for a 32-byte
+//    record, 8 B for a 24-byte one); the 32 lanes together touch one
+//    contiguous span of 32*stride bytes, whose sectors L1 reuses across the
+//    lane's successive vector loads.
+//  - Field-major side (SoA / AoSoA): for every column the 32 lanes access 32
+//    consecutive elements, i.e. one contiguous 32*size byte segment per warp
+//    instruction (a full 128-byte line for 4-byte fields).
+//  - Between the two, each lane keeps its record as 32-bit words in a
+//    lane-private shared-memory column (word k of lane l at k*33 + l, so a
+//    warp's accesses to word k hit 32 distinct banks); fields are extracted
+//    from / merged into those words by their byte offset, which the schema
+//    only knows at run time.  Records longer than 64 bytes are processed in
+//    64-byte windows (a naturally aligned field never straddles one).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mrn_plan.h"
+
+#define MRN_WIN_WORDS 16
+#define MRN_TW_PITCH 33
+#define MRN_TW_WORDS_PER_WARP (MRN_WIN_WORDS * MRN_TW_PITCH)
+
+__device__ __forceinline__ uint32_t lowbits_mask(uint32_t size) {
+  return size >= 4 ? 0xffffffffu : ((1u << (8 * size)) - 1u);
+}
+
+// Address of element i of field-major column c.
+__device__ __forceinline__ char* fm_addr(const SidePlan& sp, int c, uint32_t size, uint64_t i) {
+  char* col = sp.col[c];
+  if (sp.kind == K_SOA) return col + i * size;
+  uint64_t blk, slot;
+  if (sp.block_shift != MRN_NO_SHIFT) {
+    blk = i >> sp.block_shift;
+    slot = i & (uint64_t)(sp.block - 1);
+  } else {
+    blk = i / sp.block;
+    slot = i - blk * sp.block;
+  }
+  return col + blk * sp.block_bytes + slot * size;
+}
+
+__device__ __forceinline__ uint64_t ld_elem(const char* a, uint32_t size) {
+  switch (size) {
+    case 1: return __ldg(reinterpret_cast<const unsigned char*>(a));
+    case 2: return __ldg(reinterpret_cast<const unsigned short*>(a));
+    case 4: return __ldg(reinterpret_cast<const unsigned int*>(a));
+    default: return __ldg(reinterpret_cast<const unsigned long long*>(a));
+  }
+}
+
+__device__ __forceinline__ void st_elem(char* a, uint32_t size, uint64_t v) {
+  switch (size) {
+    case 1: *reinterpret_cast<unsigned char*>(a) = (unsigned char)v; break;
+    case 2: *reinterpret_cast<unsigned short*>(a) = (unsigned short)v; break;
+    case 4: *reinterpret_cast<unsigned int*>(a) = (unsigned int)v; break;
+    default: *reinterpret_cast<unsigned long long*>(a) = v; break;
+  }
+}
+
+// Loads nbytes (<= 64, a multiple of V) of a record window into w[0..15]
+// with V-byte accesses; w must be zero on entry for V < 4.
+template <int V>
+__device__ __forceinline__ void load_words(const char* p, uint32_t nbytes, uint32_t (&w)[16]) {
+  if constexpr (V == 16) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k * 16 < (int)nbytes) {
+        uint4 v = __ldg(reinterpret_cast<const uint4*>(p) + k);
+        w[4 * k] = v.x; w[4 * k + 1] = v.y; w[4 * k + 2] = v.z; w[4 * k + 3] = v.w;
+      }
+  } else if constexpr (V == 8) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k * 8 < (int)nbytes) {
+        uint2 v = __ldg(reinterpret_cast<const uint2*>(p) + k);
+        w[2 * k] = v.x; w[2 * k + 1] = v.y;
+      }
+  } else if constexpr (V == 4) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (k * 4 < (int)nbytes) w[k] = __ldg(reinterpret_cast<const unsigned int*>(p) + k);
+  } else if constexpr (V == 2) {
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+      if (k * 2 < (int)nbytes)
+        w[k >> 1] |= (uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p) + k) << ((k & 1) * 16);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 64; ++k)
+      if (k < (int)nbytes)
+        w[k >> 2] |= (uint32_t)__ldg(reinterpret_cast<const unsigned char*>(p) + k) << ((k & 3) * 8);
+  }
+}
+
+template <int V>
+__device__ __forceinline__ void store_words(char* p, uint32_t nbytes, const uint32_t (&w)[16]) {
+  if constexpr (V == 16) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k * 16 < (int)nbytes)
+        reinterpret_cast<uint4*>(p)[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+  } else if constexpr (V == 8) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k * 8 < (int)nbytes) reinterpret_cast<uint2*>(p)[k] = make_uint2(w[2 * k], w[2 * k + 1]);
+  } else if constexpr (V == 4) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (k * 4 < (int)nbytes) reinterpret_cast<unsigned int*>(p)[k] = w[k];
+  } else if constexpr (V == 2) {
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+      if (k * 2 < (int)nbytes)
+        reinterpret_cast<unsigned short*>(p)[k] = (unsigned short)(w[k >> 1] >> ((k & 1) * 16));
+  } else {
+#pragma unroll
+    for (int k = 0; k < 64; ++k)
+      if (k < (int)nbytes)
+        reinterpret_cast<unsigned char*>(p)[k] = (unsigned char)(w[k >> 2] >> ((k & 3) * 8));
+  }
+}
+
+// AoS record -> field-major columns, one record per lane.
+//   r      destination record index (field-major side)
+//   ld_ok  the lane has a source record at `rec`
+//   st_ok  the lane writes destination record r (zeros when !ld_ok)
+// The jagged descriptor, if the plan has one, is returned in *jlen / *jbeg.
+template <int V>
+__device__ __forceinline__ void aos_to_fm_lane(const ConvPlan& p, uint64_t r, bool ld_ok, bool st_ok,
+                                               const char* rec, uint32_t* tw, int lane,
+                                               uint32_t* jlen, uint64_t* jbeg) {
+  uint32_t ci = 0;
+  const uint32_t naos = p.naos, stride = p.stride, aw = p.aos_words;
+  for (uint32_t win = 0; win < aw; win += MRN_WIN_WORDS) {
+    uint32_t w[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) w[k] = 0;
+    const uint32_t nb = min(64u, stride - win * 4);
+    if (ld_ok) load_words<V>(rec + win * 4, nb, w);
+    const uint32_t nw = min((uint32_t)MRN_WIN_WORDS, aw - win);
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (k < (int)nw) tw[k * MRN_TW_PITCH + lane] = w[k];
+    const uint32_t wend = (win + MRN_WIN_WORDS) * 4;
+    for (; ci < naos; ++ci) {
+      const ColPlan cp = p.aos_cols[ci];
+      if (cp.aos_off >= wend) break;
+      const uint32_t wi = cp.aos_off / 4 - win;
+      const uint32_t lo = tw[wi * MRN_TW_PITCH + lane];
+      if (cp.fm >= 0) {
+        if (st_ok) {
+          char* d = fm_addr(p.dst, cp.fm, cp.size, r);
+          const uint32_t sh = (cp.aos_off & 3) * 8;
+          switch (cp.size) {
+            case 1: *reinterpret_cast<unsigned char*>(d) = (unsigned char)(lo >> sh); break;
+            case 2: *reinterpret_cast<unsigned short*>(d) = (unsigned short)(lo >> sh); break;
+            case 4: *reinterpret_cast<unsigned int*>(d) = lo; break;
+            default:
+              *reinterpret_cast<uint2*>(d) = make_uint2(lo, tw[(wi + 1) * MRN_TW_PITCH + lane]);
+              break;
+          }
+        }
+      } else if (cp.fm == FM_JLEN) {
+        *jlen = lo;
+      } else {
+        *jbeg = (uint64_t)lo | ((uint64_t)tw[(wi + 1) * MRN_TW_PITCH + lane] << 32);
+      }
+    }
+  }
+}
+
+// Field-major columns -> AoS record, one record per lane; padding bytes are
+// written as zero.  The jagged descriptor (if any) is taken from jlen/jbeg.
+template <int V>
+__device__ __forceinline__ void fm_to_aos_lane(const ConvPlan& p, uint64_t r, bool ok, char* rec,
+                                               uint32_t* tw, int lane, uint32_t jlen, uint64_t jbeg) {
+  uint32_t ci = 0;
+  const uint32_t naos = p.naos, stride = p.stride, aw = p.aos_words;
+  for (uint32_t win = 0; win < aw; win += MRN_WIN_WORDS) {
+    const uint32_t nw = min((uint32_t)MRN_WIN_WORDS, aw - win);
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (k < (int)nw) tw[k * MRN_TW_PITCH + lane] = 0;
+    const uint32_t wend = (win + MRN_WIN_WORDS) * 4;
+    for (; ci < naos; ++ci) {
+      const ColPlan cp = p.aos_cols[ci];
+      if (cp.aos_off >= wend) break;
+      const uint32_t wi = cp.aos_off / 4 - win;
+      uint64_t v;
+      if (cp.fm >= 0)
+        v = ok ? ld_elem(fm_addr(p.src, cp.fm, cp.size, r), cp.size) : 0;
+      else
+        v = cp.fm == FM_JLEN ? (uint64_t)jlen : jbeg;
+      uint32_t* t = tw + wi * MRN_TW_PITCH + lane;
+      if (cp.size == 8) {
+        t[0] = (uint32_t)v;
+        t[MRN_TW_PITCH] = (uint32_t)(v >> 32);
+      } else if (cp.size == 4) {
+        t[0] = (uint32_t)v;
+      } else {
+        t[0] |= ((uint32_t)v & lowbits_mask(cp.size)) << ((cp.aos_off & 3) * 8);
+      }
+    }
+    if (ok) {
+      uint32_t w[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) w[k] = k < (int)nw ? tw[k * MRN_TW_PITCH + lane] : 0u;
+      store_words<V>(rec + win * 4, min(64u, stride - win * 4), w);
+    }
+  }
+}
+
+// Field-major -> field-major (SoA <-> AoSoA(B), AoSoA(B) -> AoSoA(B')),
+// one record per lane, column by column.
+__device__ __forceinline__ void fm_to_fm_lane(const ConvPlan& p, uint64_t r, bool ld_ok, bool st_ok) {
+  if (!st_ok) return;
+  for (uint32_t c = 0; c < p.ncols; ++c) {
+    const uint32_t sz = p.fm_size[c];
+    const uint64_t v = ld_ok ? ld_elem(fm_addr(p.src, c, sz, r), sz) : 0;
+    st_elem(fm_addr(p.dst, c, sz, r), sz, v);
+  }
+}
+
+// ---- ordered global memory access for the decoupled look-back
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+#define MRN_TS_AGG (1ull << 62)
+#define MRN_TS_PREFIX (2ull << 62)
+#define MRN_TS_VALUE ((1ull << 62) - 1)

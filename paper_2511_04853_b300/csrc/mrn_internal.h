@@ -1,0 +1,91 @@
+// Internal declarations shared by the library's host and device sources.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <memory>
+#include <tuple>
+#include <string>
+#include <vector>
+
+#include "../../include/mrn.h"
+#include "mrn_plan.h"
+
+struct mrn_schema_node;
+
+// One flattened column of a compiled schema.
+struct MrnColumn {
+  uint32_t size;
+  uint32_t aos_off;
+  int32_t dtype;
+  std::string name;
+};
+
+struct mrn_schema {
+  // ---- builder state
+  bool finalized = false;
+  std::vector<std::unique_ptr<mrn_schema_node>> roots;
+  std::vector<mrn_schema_node*> open_groups;
+  // ---- compiled state (valid once finalized)
+  std::vector<MrnColumn> cols;
+  uint32_t stride = 0;
+  uint32_t align = 1;
+  bool has_jagged = false;
+  uint32_t len_off = 0, begin_off = 0, off_size = 0;
+  std::unique_ptr<mrn_schema> child;
+  uint64_t hash = 0;
+};
+
+namespace mrn {
+
+inline uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+uint32_t dtype_size(int dtype);
+
+// ---- layout rules (the library's own implementation)
+uint64_t aosoa_block_bytes(const mrn_schema* s, uint32_t B);
+uint64_t aosoa_col_start(const mrn_schema* s, uint32_t B, uint32_t c);
+uint64_t soa_region_start(const mrn_schema* s, uint64_t n, uint64_t m, uint32_t r);
+uint64_t soa_total_bytes(const mrn_schema* s, uint64_t n, uint64_t m);
+uint64_t base_bytes(const mrn_schema* s, const mrn_layout& l, uint64_t n, uint64_t m);
+
+// ---- device status word and scratch helpers (mrn_kernels.cu)
+int device_sm_count();
+int read_and_clear_status(void* stream, uint32_t* bits);
+int status_from_bits(uint32_t bits);
+
+// ---- plan building (mrn_api.cpp)
+uint64_t tune_key(uint64_t hash, const mrn_layout& a, const mrn_layout& b);
+// Builds the conversion plan of a validated non-jagged view pair.
+int build_plan(const mrn_view& src, const mrn_view& dst, ConvPlan* p);
+// Builds the plan of a validated jagged view pair.
+int build_jagged_plan(const mrn_view& src, const mrn_view& dst, JagPlan* jp);
+// Zeroes the alignment holes of a single-block SoA or AoSoA device view.
+int zero_dst_gaps(const mrn_view& dst, void* stream);
+// Host-side validation of a device view pair; fills *is_jagged.
+int validate_pair(const mrn_view* src, const mrn_view* dst, bool need_device, bool* is_jagged);
+
+// ---- kernel launchers (mrn_kernels.cu); all asynchronous on `stream`
+struct LaunchShape {
+  uint32_t threads = 256;
+  uint32_t ctas_per_sm = 0;  // 0: fill the SM (occupancy)
+  uint32_t tile_records = 0; // 0: default
+};
+int launch_convert(const ConvPlan& p, void* stream, const LaunchShape* shape);
+int launch_zero_gaps(const GapPlan& g, void* stream);
+// Jagged conversions.  `scratch` (AoS->SoA only) must hold
+// jagged_scratch_bytes(n) bytes; it is cleared on `stream` first.
+uint64_t jagged_scratch_bytes(uint64_t n);
+int launch_jagged_a2s(JagPlan& jp, void* scratch, void* stream);
+int launch_jagged_s2a(const JagPlan& jp, void* stream);
+int launch_jagged_count(const ConvPlan& parent, uint64_t* dev_total, void* stream);
+
+// Cached launch shape for a plan (autotuner), or the default.
+LaunchShape tuned_shape(const ConvPlan& p);
+
+}  // namespace mrn
+
+namespace mrn {
+void store_tuned_shape(uint64_t key, const LaunchShape& s);
+void clear_tuned_shapes();
+}  // namespace mrn

@@ -1,0 +1,461 @@
+// Conversion kernels for sm_103a and their launchers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <mutex>
+
+#include "mrn_device.cuh"
+#include "mrn_internal.h"
+
+// Per-device status word: bit k set = a kernel found error code k.
+__device__ unsigned int g_mrn_status_bits;
+
+__device__ __forceinline__ void flag_error(int code) { atomicOr(&g_mrn_status_bits, 1u << code); }
+
+// ------------------------------------------------------------- conversion
+
+// One warp per 32 records, grid-stride over warps.
+template <int V, int DIR>
+__global__ void __launch_bounds__(256) k_convert(const __grid_constant__ ConvPlan p) {
+  extern __shared__ uint32_t smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  uint32_t* tw = smem + warp * MRN_TW_WORDS_PER_WARP;
+  const uint64_t wpb = blockDim.x >> 5;
+  const uint64_t total_warps = (uint64_t)gridDim.x * wpb;
+  const uint64_t nrec = DIR == DIR_FM_AOS ? p.n : p.n_fm_pad;
+  for (uint64_t w = (uint64_t)blockIdx.x * wpb + warp; w * 32 < nrec; w += total_warps) {
+    const uint64_t r = w * 32 + lane;
+    const bool ld_ok = r < p.n;
+    const bool st_ok = r < nrec;
+    if constexpr (DIR == DIR_AOS_FM) {
+      uint32_t jl = 0;
+      uint64_t jb = 0;
+      aos_to_fm_lane<V>(p, r, ld_ok, st_ok, p.src.base + r * p.stride, tw, lane, &jl, &jb);
+    } else if constexpr (DIR == DIR_FM_AOS) {
+      fm_to_aos_lane<V>(p, r, ld_ok, p.dst.base + r * p.stride, tw, lane, 0u, 0ull);
+    } else {
+      fm_to_fm_lane(p, r, ld_ok, st_ok);
+    }
+  }
+}
+
+__global__ void k_zero_gaps(const __grid_constant__ GapPlan g) {
+  const uint64_t total = g.nblocks * g.ngaps;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t b = t / g.ngaps;
+    const uint32_t k = (uint32_t)(t - b * g.ngaps);
+    char* p = g.base + b * g.block_bytes + g.off[k];
+    for (uint32_t i = 0; i < g.len[k]; ++i) p[i] = 0;
+  }
+}
+
+// ------------------------------------------------------------------ jagged
+
+__device__ __forceinline__ void write_offset(char* offs, uint32_t osz, uint64_t i, uint64_t v) {
+  if (osz == 4)
+    reinterpret_cast<unsigned int*>(offs)[i] = (unsigned int)v;
+  else
+    reinterpret_cast<unsigned long long*>(offs)[i] = v;
+}
+
+__device__ __forceinline__ uint64_t read_offset(const char* offs, uint32_t osz, uint64_t i) {
+  if (osz == 4) return __ldg(reinterpret_cast<const unsigned int*>(offs) + i);
+  return __ldg(reinterpret_cast<const unsigned long long*>(offs) + i);
+}
+
+// AoS parents (+ child pool) -> SoA parents, offsets, child columns, in one
+// pass: each CTA takes the next tile of 256 parents (dynamic tile id, so all
+// of a tile's predecessors are already running), converts the parents,
+// scans their lengths, obtains the tile's child base by a decoupled
+// look-back over the predecessors' published sums (every wait bounded by
+// timeout_ns), writes the offsets and gathers its children, load-balanced
+// over the tile's threads.
+template <int VP, int VC>
+__global__ void __launch_bounds__(256) k_jagged_a2s(const __grid_constant__ JagPlan jp) {
+  __shared__ uint32_t tw_all[8 * MRN_TW_WORDS_PER_WARP];
+  __shared__ unsigned long long s_excl[MRN_JAG_TILE + 1];
+  __shared__ unsigned long long s_beg[MRN_JAG_TILE];
+  __shared__ unsigned long long s_warp[8];
+  __shared__ unsigned long long s_base;
+  __shared__ unsigned int s_tile;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t* tw = tw_all + warp * MRN_TW_WORDS_PER_WARP;
+  const ConvPlan& P = jp.parent;
+
+  if (tid == 0) s_tile = atomicAdd(jp.tile_counter, 1u);
+  __syncthreads();
+  const uint64_t tile = s_tile;
+  const uint64_t r = tile * MRN_JAG_TILE + tid;
+  const bool ok = r < P.n;
+
+  uint32_t len = 0;
+  uint64_t beg = 0;
+  aos_to_fm_lane<VP>(P, r, ok, ok, P.src.base + r * P.stride, tw, lane, &len, &beg);
+  if (!ok) len = 0;
+  bool bad = false;
+  if (ok && (beg > jp.pool_n || (uint64_t)len > jp.pool_n - beg)) {
+    flag_error(MRN_EINVAL);
+    bad = true;
+  }
+
+  // CTA-wide exclusive scan of the lengths (64-bit sums).
+  unsigned long long x = len;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long t = lane < 8 ? s_warp[lane] : 0ull;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < 8) s_warp[lane] = t;
+  }
+  __syncthreads();
+  const unsigned long long excl = x - len + (warp > 0 ? s_warp[warp - 1] : 0ull);
+  const unsigned long long agg = s_warp[7];
+  s_excl[tid] = excl;
+  if (tid == MRN_JAG_TILE - 1) s_excl[MRN_JAG_TILE] = agg;
+  s_beg[tid] = bad ? ~0ull : beg;
+
+  // Decoupled look-back for the tile's base (number of children of all
+  // earlier tiles).
+  if (tid == 0) {
+    unsigned long long prefix = 0;
+    unsigned long long* st = jp.tile_state;
+    const bool publish = (long long)tile != jp.skip_publish_tile;
+    if (tile == 0) {
+      if (publish) st_release_u64(&st[0], MRN_TS_PREFIX | (agg & MRN_TS_VALUE));
+    } else {
+      if (publish) st_release_u64(&st[tile], MRN_TS_AGG | (agg & MRN_TS_VALUE));
+      long long j = (long long)tile - 1;
+      const unsigned long long deadline = global_ns() + jp.timeout_ns;
+      unsigned int spins = 0;
+      while (j >= 0) {
+        const unsigned long long v = ld_acquire_u64(&st[j]);
+        const unsigned long long fl = v & ~MRN_TS_VALUE;
+        if (fl == 0) {
+          // bounded wait: by wall clock and by iteration count
+          if (global_ns() > deadline || ++spins > (1u << 26)) {
+            flag_error(MRN_ETIMEOUT);
+            break;
+          }
+          __nanosleep(64);
+          continue;
+        }
+        prefix += v & MRN_TS_VALUE;
+        if (fl == MRN_TS_PREFIX) break;
+        --j;
+      }
+      if (publish) st_release_u64(&st[tile], MRN_TS_PREFIX | ((prefix + agg) & MRN_TS_VALUE));
+    }
+    s_base = prefix;
+  }
+  __syncthreads();
+  const unsigned long long base = s_base;
+
+  // Offsets: offset_base + children before this parent.
+  if (ok) {
+    const unsigned long long o = jp.offset_base + base + excl;
+    write_offset(jp.offsets, jp.off_size, r, o);
+    if (r == P.n - 1) {
+      const unsigned long long end = o + len;
+      write_offset(jp.offsets, jp.off_size, P.n, end);
+      if (jp.total_out) *jp.total_out = base + excl + len;
+      if (jp.off_size == 4 && (end > 0xffffffffull || end < o)) flag_error(MRN_EOVERFLOW);
+    } else if (jp.off_size == 4 && o + len > 0xffffffffull) {
+      flag_error(MRN_EOVERFLOW);
+    }
+  }
+
+  // Children: slot j of the tile belongs to the last parent p with
+  // s_excl[p] <= j; each warp moves 32 consecutive slots.
+  for (unsigned long long j0 = (unsigned long long)warp * 32; j0 < agg; j0 += MRN_JAG_TILE) {
+    const unsigned long long j = j0 + lane;
+    const bool cok = j < agg;
+    int lo = 0, hi = MRN_JAG_TILE;
+    if (cok) {
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_excl[mid] <= j) lo = mid; else hi = mid;
+      }
+    }
+    const unsigned long long pb = s_beg[lo];
+    const unsigned long long src_idx = pb + (j - s_excl[lo]);
+    const unsigned long long dst_idx = base + j;
+    const bool st_ok = cok && dst_idx < jp.capacity;
+    if (cok && !st_ok) flag_error(MRN_ESIZE);
+    const bool ld_ok = st_ok && pb != ~0ull;
+    uint32_t dl;
+    uint64_t db;
+    aos_to_fm_lane<VC>(jp.child, dst_idx, ld_ok, st_ok,
+                       jp.child.src.base + src_idx * jp.child.stride, tw, lane, &dl, &db);
+  }
+}
+
+// SoA parents, offsets, child columns -> AoS parents and a canonical child
+// pool.  Warps [0, parent_warps) build parent records (length and begin from
+// the offsets), the remaining warps convert the m_src children.
+template <int VP, int VC>
+__global__ void __launch_bounds__(256) k_jagged_s2a(const __grid_constant__ JagPlan jp,
+                                                    unsigned long long parent_warps) {
+  extern __shared__ uint32_t smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* tw = smem + warp * MRN_TW_WORDS_PER_WARP;
+  const uint64_t wpb = blockDim.x >> 5;
+  const uint64_t child_warps = (jp.m_src + 31) / 32;
+  const uint64_t all = parent_warps + child_warps;
+  const uint64_t total_warps = (uint64_t)gridDim.x * wpb;
+  for (uint64_t w = (uint64_t)blockIdx.x * wpb + warp; w < all; w += total_warps) {
+    if (w < parent_warps) {
+      const ConvPlan& P = jp.parent;
+      const uint64_t r = w * 32 + lane;
+      const bool ok = r < P.n;
+      uint64_t a = 0, b = 0;
+      if (ok) {
+        a = read_offset(jp.offsets, jp.off_size, r);
+        b = read_offset(jp.offsets, jp.off_size, r + 1);
+        if (b < a || b - a > 0xffffffffull) flag_error(MRN_EINVAL);
+      }
+      fm_to_aos_lane<VP>(P, r, ok, P.dst.base + r * P.stride, tw, lane, (uint32_t)(b - a), a);
+    } else {
+      const ConvPlan& C = jp.child;
+      const uint64_t j = (w - parent_warps) * 32 + lane;
+      const bool ok = j < jp.m_src;
+      fm_to_aos_lane<VC>(C, j, ok, C.dst.base + j * C.stride, tw, lane, 0u, 0ull);
+    }
+  }
+}
+
+// Sum of the jagged lengths of AoS parents.
+__global__ void k_jagged_count(const char* base, uint64_t n, uint32_t stride, uint32_t len_off,
+                               unsigned long long* total) {
+  unsigned long long s = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    s += __ldg(reinterpret_cast<const unsigned int*>(base + i * stride + len_off));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(total, s);
+}
+
+__global__ void k_write_offset0(char* offs, uint32_t osz, unsigned long long v) {
+  write_offset(offs, osz, 0, v);
+}
+
+// ================================================================== host
+
+namespace mrn {
+
+namespace {
+
+std::mutex g_mu;
+int g_sm_count = 0;
+
+constexpr size_t kConvSmem = 8 * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t);
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return MRN_OK;
+  if (e == cudaErrorMemoryAllocation) return MRN_ENOMEM;
+  return MRN_ECUDA;
+}
+
+template <int V, int DIR>
+void* conv_kernel_ptr() {
+  return reinterpret_cast<void*>(&k_convert<V, DIR>);
+}
+
+template <int DIR>
+void* conv_kernel_for(uint32_t vec) {
+  switch (vec) {
+    case 16: return conv_kernel_ptr<16, DIR>();
+    case 8: return conv_kernel_ptr<8, DIR>();
+    case 4: return conv_kernel_ptr<4, DIR>();
+    case 2: return conv_kernel_ptr<2, DIR>();
+    default: return conv_kernel_ptr<1, DIR>();
+  }
+}
+
+void* conv_kernel(uint32_t dir, uint32_t vec) {
+  if (dir == DIR_AOS_FM) return conv_kernel_for<DIR_AOS_FM>(vec);
+  if (dir == DIR_FM_AOS) return conv_kernel_for<DIR_FM_AOS>(vec);
+  return conv_kernel_ptr<1, DIR_FM_FM>();
+}
+
+// Resident CTAs per SM of a kernel (cached per kernel and shape).
+int occupancy(const void* fn, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::vector<std::tuple<const void*, int, size_t, int>> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto& e : cache)
+    if (std::get<0>(e) == fn && std::get<1>(e) == threads && std::get<2>(e) == smem) return std::get<3>(e);
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess || n < 1) n = 1;
+  cache.emplace_back(fn, threads, smem, n);
+  return n;
+}
+
+}  // namespace
+
+int device_sm_count() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_sm_count == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      g_sm_count = 1;
+  }
+  return g_sm_count;
+}
+
+int status_from_bits(uint32_t bits) {
+  static const int order[] = {MRN_ETIMEOUT, MRN_EOVERFLOW, MRN_EINVAL, MRN_ESIZE, MRN_EALIGN, MRN_ECUDA};
+  for (int c : order)
+    if (bits & (1u << c)) return c;
+  return MRN_OK;
+}
+
+int read_and_clear_status(void* stream, uint32_t* bits) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return MRN_ECUDA;
+  unsigned int v = 0, zero = 0;
+  e = cudaMemcpyFromSymbolAsync(&v, g_mrn_status_bits, sizeof(v), 0, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyToSymbolAsync(g_mrn_status_bits, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return MRN_ECUDA;
+  *bits = v;
+  return MRN_OK;
+}
+
+int launch_convert(const ConvPlan& p, void* stream, const LaunchShape* shape) {
+  const uint64_t nrec = p.dir == DIR_FM_AOS ? p.n : p.n_fm_pad;
+  if (nrec == 0) return MRN_OK;
+  LaunchShape sh = shape ? *shape : LaunchShape{};
+  if (sh.threads != 128 && sh.threads != 256) sh.threads = 256;
+  void* fn = conv_kernel(p.dir, p.vec);
+  const size_t smem = (sh.threads / 32) * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t);
+  const int per_sm = sh.ctas_per_sm ? (int)sh.ctas_per_sm : occupancy(fn, (int)sh.threads, smem);
+  const uint64_t warps = (nrec + 31) / 32;
+  const uint64_t need = (warps + sh.threads / 32 - 1) / (sh.threads / 32);
+  const uint64_t cap = (uint64_t)device_sm_count() * (uint64_t)per_sm;
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(need, cap));
+  void* args[] = {const_cast<ConvPlan*>(&p)};
+  cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(sh.threads), args, smem,
+                                   static_cast<cudaStream_t>(stream));
+  return cuda_status(e);
+}
+
+int launch_zero_gaps(const GapPlan& g, void* stream) {
+  const uint64_t total = g.nblocks * g.ngaps;
+  if (total == 0) return MRN_OK;
+  const unsigned grid = (unsigned)std::min<uint64_t>((total + 255) / 256, 4096);
+  k_zero_gaps<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(g);
+  return cuda_status(cudaGetLastError());
+}
+
+uint64_t jagged_scratch_bytes(uint64_t n) {
+  const uint64_t ntiles = (n + MRN_JAG_TILE - 1) / MRN_JAG_TILE;
+  return 256 + ntiles * sizeof(unsigned long long);
+}
+
+namespace {
+template <int VP, int VC>
+void* jag_a2s_ptr() { return reinterpret_cast<void*>(&k_jagged_a2s<VP, VC>); }
+template <int VP>
+void* jag_a2s_for(uint32_t vc) {
+  switch (vc) {
+    case 16: return jag_a2s_ptr<VP, 16>();
+    case 8: return jag_a2s_ptr<VP, 8>();
+    case 4: return jag_a2s_ptr<VP, 4>();
+    case 2: return jag_a2s_ptr<VP, 2>();
+    default: return jag_a2s_ptr<VP, 1>();
+  }
+}
+void* jag_a2s(uint32_t vp, uint32_t vc) {
+  switch (vp) {
+    case 16: return jag_a2s_for<16>(vc);
+    case 8: return jag_a2s_for<8>(vc);
+    case 4: return jag_a2s_for<4>(vc);
+    case 2: return jag_a2s_for<2>(vc);
+    default: return jag_a2s_for<1>(vc);
+  }
+}
+template <int VP, int VC>
+void* jag_s2a_ptr() { return reinterpret_cast<void*>(&k_jagged_s2a<VP, VC>); }
+template <int VP>
+void* jag_s2a_for(uint32_t vc) {
+  switch (vc) {
+    case 16: return jag_s2a_ptr<VP, 16>();
+    case 8: return jag_s2a_ptr<VP, 8>();
+    case 4: return jag_s2a_ptr<VP, 4>();
+    case 2: return jag_s2a_ptr<VP, 2>();
+    default: return jag_s2a_ptr<VP, 1>();
+  }
+}
+void* jag_s2a(uint32_t vp, uint32_t vc) {
+  switch (vp) {
+    case 16: return jag_s2a_for<16>(vc);
+    case 8: return jag_s2a_for<8>(vc);
+    case 4: return jag_s2a_for<4>(vc);
+    case 2: return jag_s2a_for<2>(vc);
+    default: return jag_s2a_for<1>(vc);
+  }
+}
+}  // namespace
+
+int launch_jagged_a2s(JagPlan& jp, void* scratch, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint64_t n = jp.parent.n;
+  if (n == 0) {
+    k_write_offset0<<<1, 1, 0, s>>>(jp.offsets, jp.off_size, jp.offset_base);
+    return cuda_status(cudaGetLastError());
+  }
+  jp.ntiles = (n + MRN_JAG_TILE - 1) / MRN_JAG_TILE;
+  if (jp.ntiles > 0x7fffffffull) return MRN_EUNSUPPORTED;
+  char* sc = static_cast<char*>(scratch);
+  jp.tile_counter = reinterpret_cast<unsigned int*>(sc);
+  jp.tile_state = reinterpret_cast<unsigned long long*>(sc + 256);
+  cudaError_t e = cudaMemsetAsync(sc, 0, jagged_scratch_bytes(n), s);
+  if (e != cudaSuccess) return cuda_status(e);
+  void* fn = jag_a2s(jp.parent.vec, jp.child.vec);
+  void* args[] = {&jp};
+  e = cudaLaunchKernel(fn, dim3((unsigned)jp.ntiles), dim3(MRN_JAG_TILE), args, 0, s);
+  return cuda_status(e);
+}
+
+int launch_jagged_s2a(const JagPlan& jp, void* stream) {
+  const uint64_t pw = (jp.parent.n + 31) / 32;
+  const uint64_t cw = (jp.m_src + 31) / 32;
+  if (pw + cw == 0) return MRN_OK;
+  void* fn = jag_s2a(jp.parent.vec, jp.child.vec);
+  const int per_sm = occupancy(fn, 256, kConvSmem);
+  const uint64_t need = (pw + cw + 7) / 8;
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)device_sm_count() * per_sm));
+  unsigned long long pwu = pw;
+  void* args[] = {const_cast<JagPlan*>(&jp), &pwu};
+  return cuda_status(cudaLaunchKernel(fn, dim3(grid), dim3(256), args, kConvSmem,
+                                      static_cast<cudaStream_t>(stream)));
+}
+
+int launch_jagged_count(const ConvPlan& parent, uint64_t* dev_total, void* stream) {
+  uint32_t len_off = 0;
+  for (uint32_t i = 0; i < parent.naos; ++i)
+    if (parent.aos_cols[i].fm == FM_JLEN) len_off = parent.aos_cols[i].aos_off;
+  const unsigned grid = (unsigned)std::max<uint64_t>(
+      1, std::min<uint64_t>((parent.n + 255) / 256, (uint64_t)device_sm_count() * 8));
+  k_jagged_count<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      parent.src.base, parent.n, parent.stride, len_off, reinterpret_cast<unsigned long long*>(dev_total));
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace mrn

@@ -1,0 +1,84 @@
+// Plain-old-data conversion plans: built on the host from a schema and two
+// views, passed to kernels by value (kernel parameters live in the constant
+// bank) or stored in a device job table for the batched launch.
+#pragma once
+
+#include <cstdint>
+
+#define MRN_MAX_COLS 64   // flattened data columns per schema (and per child)
+#define MRN_MAX_GAPS 160  // zero-fill ranges of one destination
+#define MRN_NO_SHIFT 0xffffffffu
+
+enum MrnKind : int32_t { K_AOS = 0, K_SOA = 1, K_AOSOA = 2 };
+enum MrnDir : uint32_t { DIR_AOS_FM = 0, DIR_FM_AOS = 1, DIR_FM_FM = 2 };
+
+// Field-major side (SoA or AoSoA) or record-major side (AoS) of a plan.
+struct SidePlan {
+  int32_t kind;
+  uint32_t block;        // AoSoA B
+  uint32_t block_shift;  // log2(B) when B is a power of two, else MRN_NO_SHIFT
+  uint32_t reserved;
+  uint64_t block_bytes;  // AoSoA bytes per block
+  char* base;            // AoS records / AoSoA blocks
+  // SoA: start of column c.  AoSoA: base + start of column c inside a block.
+  char* col[MRN_MAX_COLS];
+};
+
+// One entry of the AoS record, in increasing offset order.
+struct ColPlan {
+  uint16_t size;     // 1, 2, 4 or 8
+  int16_t fm;        // field-major column index, or FM_JLEN / FM_JBEGIN
+  uint32_t aos_off;  // byte offset in the AoS record
+};
+#define FM_JLEN (-1)    // the jagged member's uint32 length
+#define FM_JBEGIN (-2)  // the jagged member's uint64 begin
+
+struct ConvPlan {
+  uint64_t n;          // records
+  uint64_t n_fm_pad;   // records written on the destination (AoSoA: N rounded up to B)
+  uint32_t dir;        // MrnDir
+  uint32_t naos;       // entries of aos_cols
+  uint32_t ncols;      // field-major (data) columns
+  uint32_t stride;     // AoS stride
+  uint32_t aos_words;  // ceil(stride / 4)
+  uint32_t vec;        // AoS access width in bytes (1, 2, 4, 8, 16)
+  uint64_t tune_key;   // (schema, layout pair) key of the launch-shape cache
+  ColPlan aos_cols[MRN_MAX_COLS + 2];
+  uint8_t fm_size[MRN_MAX_COLS];
+  SidePlan src, dst;
+};
+
+// Jagged AoS <-> SoA conversion: the parents' plan (data columns plus the
+// {length, begin} descriptor) and the children's plan (pool <-> child
+// columns), with the offsets column and the look-back scratch.
+struct JagPlan {
+  ConvPlan parent;
+  ConvPlan child;
+  char* offsets;             // SoA offsets column (N+1 entries)
+  uint32_t off_size;         // 4 or 8
+  uint32_t reserved;
+  uint64_t offset_base;      // added to every offset written (AoS -> SoA)
+  uint64_t pool_n;           // AoS -> SoA: child records in the source pool
+  uint64_t capacity;         // AoS -> SoA: child capacity of the destination
+  uint64_t m_src;            // SoA -> AoS: child values in the source
+  uint64_t ntiles;           // AoS -> SoA: tiles of 256 parents
+  unsigned long long* tile_state;  // ntiles words: flag (2 bits) | value
+  unsigned int* tile_counter;      // dynamic tile id
+  unsigned long long timeout_ns;   // bound of each look-back wait
+  long long skip_publish_tile;     // fault injection: tile that never publishes (-1: none)
+  unsigned long long* total_out;   // optional: receives the number of children
+};
+
+// Zero-fill of the alignment holes of a destination: for each of `nblocks`
+// blocks of `block_bytes`, the byte ranges [off[k], off[k] + len[k]).
+struct GapPlan {
+  char* base;
+  uint64_t nblocks;
+  uint64_t block_bytes;
+  uint32_t ngaps;
+  uint32_t reserved;
+  uint64_t off[MRN_MAX_GAPS];
+  uint32_t len[MRN_MAX_GAPS];
+};
+
+#define MRN_JAG_TILE 256  // parents per tile of the jagged scan

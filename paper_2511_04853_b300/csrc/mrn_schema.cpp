@@ -1,0 +1,339 @@
+// Schema builder and compiler: lowers a property description (Sec. V) to
+// flattened columns with AoS offsets, and implements the layout rules.
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "mrn_internal.h"
+
+struct mrn_schema_node {
+  enum Kind { FIELD, GROUP, JAGGED } kind;
+  std::string name;
+  int dtype = 0;
+  uint32_t extent = 1;
+  int offset_dtype = 0;
+  std::vector<std::unique_ptr<mrn_schema_node>> members;  // GROUP
+  std::unique_ptr<mrn_schema> child;                      // JAGGED (finalized copy)
+};
+
+namespace mrn {
+
+uint32_t dtype_size(int dtype) {
+  switch (dtype) {
+    case MRN_U8: case MRN_I8: case MRN_BOOL: return 1;
+    case MRN_U16: case MRN_I16: return 2;
+    case MRN_U32: case MRN_I32: case MRN_F32: return 4;
+    case MRN_U64: case MRN_I64: case MRN_F64: return 8;
+    default: return 0;
+  }
+}
+
+namespace {
+
+uint64_t fnv(uint64_t h, uint64_t v) {
+  for (int i = 0; i < 8; ++i) {
+    h ^= (v >> (8 * i)) & 0xff;
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+// Lays out the members of one struct level (C rules: each member at the
+// next multiple of its alignment; a group is a nested struct).  Column
+// offsets are relative to the struct start.  Returns false on error.
+bool lay_out(const std::vector<std::unique_ptr<mrn_schema_node>>& members, const std::string& prefix,
+             mrn_schema* s, uint64_t* size, uint64_t* align) {
+  uint64_t cur = 0, al = 1;
+  for (const auto& m : members) {
+    if (m->kind == mrn_schema_node::FIELD) {
+      const uint32_t sz = dtype_size(m->dtype);
+      const uint64_t off = align_up(cur, sz);
+      for (uint32_t k = 0; k < m->extent; ++k) {
+        MrnColumn c;
+        c.size = sz;
+        c.aos_off = (uint32_t)(off + (uint64_t)k * sz);
+        c.dtype = m->dtype;
+        c.name = prefix + m->name;
+        if (m->extent > 1) c.name += "[" + std::to_string(k) + "]";
+        s->cols.push_back(c);
+      }
+      cur = off + (uint64_t)m->extent * sz;
+      al = std::max<uint64_t>(al, sz);
+    } else if (m->kind == mrn_schema_node::GROUP) {
+      const size_t first = s->cols.size();
+      const bool had = s->has_jagged;
+      uint64_t gs = 0, ga = 1;
+      if (!lay_out(m->members, prefix + m->name + ".", s, &gs, &ga)) return false;
+      const uint64_t goff = align_up(cur, ga);
+      for (size_t c = first; c < s->cols.size(); ++c) s->cols[c].aos_off += (uint32_t)goff;
+      if (s->has_jagged && !had) {
+        s->len_off += (uint32_t)goff;
+        s->begin_off += (uint32_t)goff;
+      }
+      cur = goff + gs;
+      al = std::max(al, ga);
+    } else {
+      if (s->has_jagged) return false;
+      s->has_jagged = true;
+      s->off_size = dtype_size(m->offset_dtype);
+      s->len_off = (uint32_t)align_up(cur, 4);
+      cur = s->len_off + 4;
+      s->begin_off = (uint32_t)align_up(cur, 8);
+      cur = s->begin_off + 8;
+      al = std::max<uint64_t>(al, 8);
+    }
+    if (cur > 0xffffffffull) return false;
+  }
+  *size = align_up(cur, al);
+  *align = al;
+  return true;
+}
+
+mrn_schema_node* find_jagged(const std::vector<std::unique_ptr<mrn_schema_node>>& members) {
+  for (const auto& m : members) {
+    if (m->kind == mrn_schema_node::JAGGED) return m.get();
+    if (m->kind == mrn_schema_node::GROUP)
+      if (auto* j = find_jagged(m->members)) return j;
+  }
+  return nullptr;
+}
+
+std::unique_ptr<mrn_schema_node> clone_node(const mrn_schema_node& n);
+
+std::unique_ptr<mrn_schema> clone_schema(const mrn_schema& s) {
+  auto c = std::make_unique<mrn_schema>();
+  for (const auto& r : s.roots) c->roots.push_back(clone_node(*r));
+  c->finalized = s.finalized;
+  c->cols = s.cols;
+  c->stride = s.stride;
+  c->align = s.align;
+  c->has_jagged = s.has_jagged;
+  c->len_off = s.len_off;
+  c->begin_off = s.begin_off;
+  c->off_size = s.off_size;
+  if (s.child) c->child = clone_schema(*s.child);
+  c->hash = s.hash;
+  return c;
+}
+
+std::unique_ptr<mrn_schema_node> clone_node(const mrn_schema_node& n) {
+  auto c = std::make_unique<mrn_schema_node>();
+  c->kind = n.kind;
+  c->name = n.name;
+  c->dtype = n.dtype;
+  c->extent = n.extent;
+  c->offset_dtype = n.offset_dtype;
+  for (const auto& m : n.members) c->members.push_back(clone_node(*m));
+  if (n.child) c->child = clone_schema(*n.child);
+  return c;
+}
+
+std::vector<std::unique_ptr<mrn_schema_node>>* current_list(mrn_schema* s) {
+  return s->open_groups.empty() ? &s->roots : &s->open_groups.back()->members;
+}
+
+bool valid_name(const char* name) { return name && std::strlen(name) < 64; }
+
+}  // namespace
+
+uint64_t aosoa_col_start(const mrn_schema* s, uint32_t B, uint32_t c) {
+  uint64_t end = 0, start = 0;
+  for (uint32_t k = 0; k <= c; ++k) {
+    start = align_up(end, s->cols[k].size);
+    end = start + (uint64_t)B * s->cols[k].size;
+  }
+  return start;
+}
+
+uint64_t aosoa_block_bytes(const mrn_schema* s, uint32_t B) {
+  uint64_t end = 0, al = 1;
+  for (const auto& c : s->cols) {
+    end = align_up(end, c.size) + (uint64_t)B * c.size;
+    al = std::max<uint64_t>(al, c.size);
+  }
+  return align_up(end, al);
+}
+
+namespace {
+uint64_t region_bytes(const mrn_schema* s, uint64_t n, uint64_t m, uint32_t r) {
+  const uint32_t nc = (uint32_t)s->cols.size();
+  if (r < nc) return n * s->cols[r].size;
+  if (r == nc) return (n + 1) * s->off_size;
+  return m * s->child->cols[r - nc - 1].size;
+}
+uint32_t region_count(const mrn_schema* s) {
+  return (uint32_t)s->cols.size() + (s->has_jagged ? 1 + (uint32_t)s->child->cols.size() : 0);
+}
+}  // namespace
+
+uint64_t soa_region_start(const mrn_schema* s, uint64_t n, uint64_t m, uint32_t r) {
+  uint64_t pos = 0;
+  for (uint32_t k = 0; k < r; ++k) pos = align_up(pos + region_bytes(s, n, m, k), 128);
+  return pos;
+}
+
+uint64_t soa_total_bytes(const mrn_schema* s, uint64_t n, uint64_t m) {
+  const uint32_t nr = region_count(s);
+  return align_up(soa_region_start(s, n, m, nr - 1) + region_bytes(s, n, m, nr - 1), 128);
+}
+
+uint64_t base_bytes(const mrn_schema* s, const mrn_layout& l, uint64_t n, uint64_t m) {
+  switch (l.kind) {
+    case MRN_AOS: return n * s->stride;
+    case MRN_SOA: return soa_total_bytes(s, n, m);
+    default: return (n + l.block - 1) / l.block * aosoa_block_bytes(s, l.block);
+  }
+}
+
+}  // namespace mrn
+
+using namespace mrn;
+
+extern "C" {
+
+int mrn_schema_create(mrn_schema** out) {
+  if (!out) return MRN_EINVAL;
+  *out = new (std::nothrow) mrn_schema();
+  return *out ? MRN_OK : MRN_ENOMEM;
+}
+
+void mrn_schema_destroy(mrn_schema* s) { delete s; }
+
+int mrn_schema_add_field(mrn_schema* s, const char* name, int dtype, uint32_t extent) {
+  if (!s || s->finalized || !valid_name(name) || dtype_size(dtype) == 0 || extent < 1 ||
+      extent > 4096)
+    return MRN_EINVAL;
+  auto n = std::make_unique<mrn_schema_node>();
+  n->kind = mrn_schema_node::FIELD;
+  n->name = name;
+  n->dtype = dtype;
+  n->extent = extent;
+  current_list(s)->push_back(std::move(n));
+  return MRN_OK;
+}
+
+int mrn_schema_begin_group(mrn_schema* s, const char* name) {
+  if (!s || s->finalized || !valid_name(name) || s->open_groups.size() >= 32) return MRN_EINVAL;
+  auto n = std::make_unique<mrn_schema_node>();
+  n->kind = mrn_schema_node::GROUP;
+  n->name = name;
+  mrn_schema_node* raw = n.get();
+  current_list(s)->push_back(std::move(n));
+  s->open_groups.push_back(raw);
+  return MRN_OK;
+}
+
+int mrn_schema_end_group(mrn_schema* s) {
+  if (!s || s->finalized || s->open_groups.empty()) return MRN_EINVAL;
+  s->open_groups.pop_back();
+  return MRN_OK;
+}
+
+int mrn_schema_add_jagged(mrn_schema* s, const char* name, int offset_dtype, const mrn_schema* child) {
+  if (!s || s->finalized || !valid_name(name) || !child || !child->finalized || child->has_jagged ||
+      child->cols.empty() || (offset_dtype != MRN_U32 && offset_dtype != MRN_U64) ||
+      find_jagged(s->roots))
+    return MRN_EINVAL;
+  auto n = std::make_unique<mrn_schema_node>();
+  n->kind = mrn_schema_node::JAGGED;
+  n->name = name;
+  n->offset_dtype = offset_dtype;
+  n->child = clone_schema(*child);
+  current_list(s)->push_back(std::move(n));
+  return MRN_OK;
+}
+
+int mrn_schema_finalize(mrn_schema* s) {
+  if (!s || s->finalized || !s->open_groups.empty()) return MRN_EINVAL;
+  s->cols.clear();
+  s->has_jagged = false;
+  uint64_t size = 0, al = 1;
+  if (!lay_out(s->roots, "", s, &size, &al)) return MRN_EINVAL;
+  if (s->cols.empty() && !s->has_jagged) return MRN_EINVAL;
+  s->stride = (uint32_t)size;
+  s->align = (uint32_t)al;
+  if (s->has_jagged) s->child = clone_schema(*find_jagged(s->roots)->child);
+  uint64_t h = 1469598103934665603ull;
+  h = fnv(h, s->stride);
+  h = fnv(h, s->cols.size());
+  for (const auto& c : s->cols) h = fnv(fnv(h, c.size), c.aos_off);
+  if (s->has_jagged) {
+    h = fnv(fnv(fnv(h, s->len_off), s->begin_off), s->off_size);
+    h = fnv(h, s->child->hash);
+  }
+  s->hash = h;
+  s->finalized = true;
+  return MRN_OK;
+}
+
+int mrn_schema_info_get(const mrn_schema* s, mrn_schema_info* out) {
+  if (!s || !s->finalized || !out) return MRN_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  out->n_columns = (uint32_t)s->cols.size();
+  out->aos_stride = s->stride;
+  out->aos_align = s->align;
+  out->has_jagged = s->has_jagged ? 1 : 0;
+  if (s->has_jagged) {
+    out->jag_length_offset = s->len_off;
+    out->jag_begin_offset = s->begin_off;
+    out->offset_size = s->off_size;
+    out->child_columns = (uint32_t)s->child->cols.size();
+    out->child_stride = s->child->stride;
+  }
+  out->hash = s->hash;
+  return MRN_OK;
+}
+
+int mrn_schema_column(const mrn_schema* s, int child, uint32_t c, mrn_column_info* out) {
+  if (!s || !s->finalized || !out) return MRN_EINVAL;
+  const mrn_schema* t = child ? s->child.get() : s;
+  if (!t || c >= t->cols.size()) return MRN_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  out->size = t->cols[c].size;
+  out->aos_offset = t->cols[c].aos_off;
+  out->dtype = t->cols[c].dtype;
+  std::strncpy(out->name, t->cols[c].name.c_str(), sizeof(out->name) - 1);
+  return MRN_OK;
+}
+
+int mrn_schema_aos_layout(const mrn_schema* s, size_t* stride, size_t* offsets, size_t cap) {
+  if (!s || !s->finalized) return MRN_EINVAL;
+  if (stride) *stride = s->stride;
+  if (offsets)
+    for (size_t c = 0; c < s->cols.size() && c < cap; ++c) offsets[c] = s->cols[c].aos_off;
+  return MRN_OK;
+}
+
+int mrn_required_bytes(const mrn_schema* s, mrn_layout l, uint64_t n, uint64_t m, size_t* out) {
+  if (!s || !s->finalized || !out || l.kind < MRN_AOS || l.kind > MRN_AOSOA ||
+      (l.kind == MRN_AOSOA && l.block < 1))
+    return MRN_EINVAL;
+  *out = (size_t)base_bytes(s, l, n, m);
+  return MRN_OK;
+}
+
+int mrn_child_pool_bytes(const mrn_schema* s, uint64_t m, size_t* out) {
+  if (!s || !s->finalized || !s->has_jagged || !out) return MRN_EINVAL;
+  *out = (size_t)(m * s->child->stride);
+  return MRN_OK;
+}
+
+int mrn_soa_region_offset(const mrn_schema* s, uint64_t n, uint64_t m, uint32_t r, size_t* out) {
+  if (!s || !s->finalized || !out || r >= region_count(s)) return MRN_EINVAL;
+  *out = (size_t)soa_region_start(s, n, m, r);
+  return MRN_OK;
+}
+
+int mrn_aosoa_block_bytes(const mrn_schema* s, uint32_t B, size_t* out) {
+  if (!s || !s->finalized || !out || B < 1) return MRN_EINVAL;
+  *out = (size_t)aosoa_block_bytes(s, B);
+  return MRN_OK;
+}
+
+int mrn_aosoa_column_offset(const mrn_schema* s, uint32_t B, uint32_t c, size_t* out) {
+  if (!s || !s->finalized || !out || B < 1 || c >= s->cols.size()) return MRN_EINVAL;
+  *out = (size_t)aosoa_col_start(s, B, c);
+  return MRN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,367 @@
+// Transfer-and-convert between host and device views (the analogue of a
+// copy between collections in different memory contexts, Sec. VI-A/VI-B):
+// the source is cut into chunks of whole records; chunk k is copied with
+// cudaMemcpyAsync on a copy stream into staging slot k % S and converted on
+// a compute stream, so copies and conversions of different chunks overlap.
+#include "mrn_transfer.h"
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+namespace mrn {
+
+namespace {
+
+constexpr uint64_t kPartAlign = 256;
+
+bool is_host(const mrn_view& v) { return v.mem == MRN_MEM_HOST || v.mem == MRN_MEM_HOST_PINNED; }
+
+bool same_layout(const mrn_view& a, const mrn_view& b) {
+  return a.layout.kind == b.layout.kind &&
+         (a.layout.kind != MRN_AOSOA || a.layout.block == b.layout.block);
+}
+
+char* soa_part(const mrn_view& v, uint32_t region, void* const* cols, uint32_t idx) {
+  if (cols) return static_cast<char*>(cols[idx]);
+  return static_cast<char*>(v.base) + soa_region_start(v.schema, v.n_records, v.n_children, region);
+}
+
+uint64_t gcd64(uint64_t a, uint64_t b) {
+  while (b) {
+    const uint64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+uint64_t lcm64(uint64_t a, uint64_t b) { return a / gcd64(a, b) * b; }
+
+// A device view with the same structure as `like`, its parts packed into
+// `stage` (each part 256-byte aligned).  Returns the bytes used.
+uint64_t staged_view(const mrn_view& like, char* stage, mrn_view* out, std::vector<void*>& cols,
+                     std::vector<void*>& ccols) {
+  const mrn_schema* s = like.schema;
+  *out = like;
+  out->mem = MRN_MEM_DEVICE;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  out->device = dev;
+  out->offset_base = like.offset_base;
+  uint64_t pos = 0;
+  auto take = [&](uint64_t bytes) {
+    char* p = stage ? stage + pos : nullptr;
+    pos += align_up(std::max<uint64_t>(bytes, 1), kPartAlign);
+    return p;
+  };
+  const uint64_t n = like.n_records, m = like.n_children;
+  out->columns = nullptr;
+  out->child_columns = nullptr;
+  out->offsets = nullptr;
+  out->child_pool = nullptr;
+  if (like.layout.kind == MRN_AOS) {
+    out->base = take(n * s->stride);
+    if (s->has_jagged) out->child_pool = take(m * s->child->stride);
+  } else if (like.layout.kind == MRN_AOSOA) {
+    out->base = take((n + like.layout.block - 1) / like.layout.block * aosoa_block_bytes(s, like.layout.block));
+  } else {
+    cols.assign(s->cols.size(), nullptr);
+    for (size_t c = 0; c < s->cols.size(); ++c) cols[c] = take(n * s->cols[c].size);
+    out->columns = cols.data();
+    out->base = cols.empty() ? nullptr : cols[0];
+    if (s->has_jagged) {
+      out->offsets = take((n + 1) * s->off_size);
+      ccols.assign(s->child->cols.size(), nullptr);
+      for (size_t c = 0; c < s->child->cols.size(); ++c) ccols[c] = take(m * s->child->cols[c].size);
+      out->child_columns = ccols.data();
+    }
+  }
+  return pos;
+}
+
+int copy_parts(const std::vector<ViewPart>& from, const std::vector<ViewPart>& to, cudaMemcpyKind kind,
+               cudaStream_t s) {
+  if (from.size() != to.size()) return MRN_EINVAL;
+  for (size_t i = 0; i < from.size(); ++i) {
+    const uint64_t b = std::min(from[i].bytes, to[i].bytes);
+    if (!b) continue;
+    if (!from[i].ptr || !to[i].ptr) return MRN_EINVAL;
+    if (cudaMemcpyAsync(to[i].ptr, from[i].ptr, b, kind, s) != cudaSuccess) return MRN_ECUDA;
+  }
+  return MRN_OK;
+}
+
+}  // namespace
+
+std::vector<ViewPart> view_parts(const mrn_view& v) {
+  const mrn_schema* s = v.schema;
+  const uint64_t n = v.n_records, m = v.n_children;
+  std::vector<ViewPart> out;
+  if (v.layout.kind == MRN_AOS) {
+    out.push_back({static_cast<char*>(v.base), n * s->stride});
+    if (s->has_jagged) out.push_back({static_cast<char*>(v.child_pool), m * s->child->stride});
+  } else if (v.layout.kind == MRN_AOSOA) {
+    const uint64_t B = v.layout.block;
+    out.push_back({static_cast<char*>(v.base), (n + B - 1) / B * aosoa_block_bytes(s, (uint32_t)B)});
+  } else {
+    const uint32_t nc = (uint32_t)s->cols.size();
+    for (uint32_t c = 0; c < nc; ++c) out.push_back({soa_part(v, c, v.columns, c), n * s->cols[c].size});
+    if (s->has_jagged) {
+      char* offs = v.offsets ? static_cast<char*>(v.offsets) : soa_part(v, nc, nullptr, 0);
+      out.push_back({offs, (n + 1) * s->off_size});
+      for (uint32_t c = 0; c < s->child->cols.size(); ++c)
+        out.push_back({soa_part(v, nc + 1 + c, v.child_columns, c), m * s->child->cols[c].size});
+    }
+  }
+  return out;
+}
+
+mrn_view sub_view(const mrn_view& v, uint64_t r0, uint64_t cnt, std::vector<void*>& cols) {
+  const mrn_schema* s = v.schema;
+  mrn_view o = v;
+  o.n_records = cnt;
+  if (v.layout.kind == MRN_AOS) {
+    o.base = static_cast<char*>(v.base) + r0 * s->stride;
+  } else if (v.layout.kind == MRN_AOSOA) {
+    o.base = static_cast<char*>(v.base) + r0 / v.layout.block * aosoa_block_bytes(s, v.layout.block);
+  } else {
+    cols.assign(s->cols.size(), nullptr);
+    for (uint32_t c = 0; c < s->cols.size(); ++c)
+      cols[c] = soa_part(v, c, v.columns, c) + r0 * s->cols[c].size;
+    o.columns = cols.data();
+    o.base = cols.empty() ? nullptr : cols[0];
+  }
+  return o;
+}
+
+uint64_t record_bytes(const mrn_schema* s, const mrn_layout& l) {
+  if (l.kind == MRN_AOS) return s->stride;
+  if (l.kind == MRN_AOSOA) return (aosoa_block_bytes(s, l.block) + l.block - 1) / l.block;
+  uint64_t b = 0;
+  for (const auto& c : s->cols) b += c.size;
+  return b;
+}
+
+TransferEngine::~TransferEngine() {
+  if (!ready_) return;
+  cudaStreamSynchronize(s_copy_);
+  cudaStreamSynchronize(s_conv_);
+  for (auto e : ev_copied_) cudaEventDestroy(e);
+  for (auto e : ev_free_) cudaEventDestroy(e);
+  cudaEventDestroy(ev_start_);
+  cudaEventDestroy(ev_copy_done_);
+  cudaEventDestroy(ev_done_);
+  cudaStreamDestroy(s_copy_);
+  cudaStreamDestroy(s_conv_);
+  if (staging_) cudaFree(staging_);
+}
+
+int TransferEngine::init() {
+  if (ready_) return MRN_OK;
+  if (cudaStreamCreateWithFlags(&s_copy_, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s_conv_, cudaStreamNonBlocking) != cudaSuccess)
+    return MRN_ECUDA;
+  const unsigned fl = cudaEventDisableTiming;
+  ev_copied_.resize(16);
+  ev_free_.resize(16);
+  for (int i = 0; i < 16; ++i)
+    if (cudaEventCreateWithFlags(&ev_copied_[i], fl) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_free_[i], fl) != cudaSuccess)
+      return MRN_ECUDA;
+  if (cudaEventCreateWithFlags(&ev_start_, fl) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ev_copy_done_, fl) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ev_done_, fl) != cudaSuccess)
+    return MRN_ECUDA;
+  ready_ = true;
+  return MRN_OK;
+}
+
+int TransferEngine::ensure_staging(uint64_t bytes) {
+  if (bytes <= staging_bytes_) return MRN_OK;
+  cudaStreamSynchronize(s_copy_);
+  cudaStreamSynchronize(s_conv_);
+  if (staging_) cudaFree(staging_);
+  staging_ = nullptr;
+  staging_bytes_ = 0;
+  if (cudaMalloc(&staging_, bytes) != cudaSuccess) {
+    staging_ = nullptr;
+    cudaGetLastError();
+    return MRN_ENOMEM;
+  }
+  staging_bytes_ = bytes;
+  return MRN_OK;
+}
+
+namespace {
+// Records per chunk and staging bytes per slot.
+void chunk_geometry(const mrn_view& src, const mrn_view& dst, uint64_t chunk_bytes, uint64_t* R,
+                    uint64_t* slot_bytes) {
+  const bool h2d = src.mem != MRN_MEM_DEVICE;
+  const mrn_view& hv = h2d ? src : dst;  // host-side layout is the staged one
+  uint64_t q = 32;
+  if (src.layout.kind == MRN_AOSOA) q = lcm64(q, src.layout.block);
+  if (dst.layout.kind == MRN_AOSOA) q = lcm64(q, dst.layout.block);
+  const uint64_t rb = std::max<uint64_t>(1, record_bytes(hv.schema, hv.layout));
+  uint64_t r = std::max<uint64_t>(1, chunk_bytes / rb);
+  r = std::max<uint64_t>(q, r / q * q);
+  r = std::min<uint64_t>(r, std::max<uint64_t>(q, (src.n_records + q - 1) / q * q));
+  *R = r;
+  mrn_view like = hv;
+  like.n_records = r;
+  mrn_view tmp;
+  std::vector<void*> a, b;
+  *slot_bytes = staged_view(like, nullptr, &tmp, a, b);
+}
+}  // namespace
+
+uint64_t TransferEngine::staging_bytes(const mrn_view& src, const mrn_view& dst, uint64_t chunk_bytes,
+                                       int n_slots) {
+  const bool whole = src.schema->has_jagged;
+  if (same_layout(src, dst)) return 0;
+  if (whole) {
+    const mrn_view& hv = src.mem != MRN_MEM_DEVICE ? src : dst;
+    mrn_view like = hv, tmp;
+    if (src.mem == MRN_MEM_DEVICE) like.n_children = src.n_children;
+    std::vector<void*> a, b;
+    return staged_view(like, nullptr, &tmp, a, b);
+  }
+  uint64_t R, slot;
+  chunk_geometry(src, dst, chunk_bytes ? chunk_bytes : (4ull << 20), &R, &slot);
+  return slot * (uint64_t)std::max(1, std::min(16, n_slots ? n_slots : 4));
+}
+
+int TransferEngine::run(const mrn_view& src, const mrn_view& dst, uint64_t chunk_bytes, int n_slots,
+                        cudaStream_t user, char* arena, uint64_t arena_bytes) {
+  int rc = init();
+  if (rc) return rc;
+  if (!chunk_bytes) chunk_bytes = 4ull << 20;
+  n_slots = std::max(1, std::min(16, n_slots ? n_slots : 4));
+  if (cudaEventRecord(ev_start_, user) != cudaSuccess) return MRN_ECUDA;
+  cudaStreamWaitEvent(s_copy_, ev_start_, 0);
+  cudaStreamWaitEvent(s_conv_, ev_start_, 0);
+  const bool h2d = is_host(src);
+  const cudaMemcpyKind kind = h2d ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+  if (same_layout(src, dst)) {
+    // Equal layouts: the storage is copied verbatim, part by part.
+    rc = copy_parts(view_parts(src), view_parts(dst), kind, s_copy_);
+  } else {
+    const uint64_t need = staging_bytes(src, dst, chunk_bytes, n_slots);
+    char* stage = arena;
+    if (!stage) {
+      if ((rc = ensure_staging(need))) return rc;
+      stage = staging_;
+    } else if (arena_bytes < need) {
+      return MRN_ENOMEM;
+    }
+    rc = src.schema->has_jagged ? run_whole(src, dst, user, stage, need)
+                                : run_chunked(src, dst, chunk_bytes, n_slots, user, stage, need);
+  }
+  if (cudaEventRecord(ev_copy_done_, s_copy_) != cudaSuccess) return MRN_ECUDA;
+  cudaStreamWaitEvent(s_conv_, ev_copy_done_, 0);
+  if (cudaEventRecord(ev_done_, s_conv_) != cudaSuccess) return MRN_ECUDA;
+  if (cudaStreamWaitEvent(user, ev_done_, 0) != cudaSuccess) return MRN_ECUDA;
+  return rc;
+}
+
+int TransferEngine::run_whole(const mrn_view& src, const mrn_view& dst, cudaStream_t, char* stage,
+                              uint64_t) {
+  const bool h2d = is_host(src);
+  std::vector<void*> a, b;
+  mrn_view staged;
+  int rc;
+  if (h2d) {
+    staged_view(src, stage, &staged, a, b);
+    if ((rc = copy_parts(view_parts(src), view_parts(staged), cudaMemcpyHostToDevice, s_copy_))) return rc;
+    cudaEventRecord(ev_copied_[0], s_copy_);
+    cudaStreamWaitEvent(s_conv_, ev_copied_[0], 0);
+    return mrn_convert(&staged, &dst, s_conv_);
+  }
+  mrn_view like = dst;
+  like.n_children = dst.layout.kind == MRN_AOS ? src.n_children : dst.n_children;
+  staged_view(like, stage, &staged, a, b);
+  if ((rc = mrn_convert(&src, &staged, s_conv_))) return rc;
+  cudaEventRecord(ev_copied_[0], s_conv_);
+  cudaStreamWaitEvent(s_copy_, ev_copied_[0], 0);
+  auto from = view_parts(staged), to = view_parts(dst);
+  return copy_parts(from, to, cudaMemcpyDeviceToHost, s_copy_);
+}
+
+int TransferEngine::run_chunked(const mrn_view& src, const mrn_view& dst, uint64_t chunk_bytes,
+                                int n_slots, cudaStream_t, char* stage, uint64_t) {
+  const bool h2d = is_host(src);
+  const mrn_view& hv = h2d ? src : dst;
+  const mrn_view& dv = h2d ? dst : src;
+  uint64_t R, slot_bytes;
+  chunk_geometry(src, dst, chunk_bytes, &R, &slot_bytes);
+  const uint64_t n = src.n_records;
+  int rc;
+  // Host single-block SoA destination: its alignment holes are zeroed here.
+  if (!h2d && dst.layout.kind == MRN_SOA && !dst.columns && dst.base) {
+    auto parts = view_parts(dst);
+    uint64_t prev = 0;
+    char* base = static_cast<char*>(dst.base);
+    for (const auto& p : parts) {
+      const uint64_t st = p.ptr - base;
+      if (st > prev) std::memset(base + prev, 0, st - prev);
+      prev = st + p.bytes;
+    }
+    const uint64_t total = soa_total_bytes(dst.schema, dst.n_records, dst.n_children);
+    if (total > prev) std::memset(base + prev, 0, total - prev);
+  }
+  std::vector<void*> hc, dc, sc, sc2;
+  for (uint64_t k = 0, r0 = 0; r0 < n; ++k, r0 += R) {
+    const uint64_t cnt = std::min(R, n - r0);
+    const int slot = (int)(k % (uint64_t)n_slots);
+    mrn_view hsub = sub_view(hv, r0, cnt, hc);
+    mrn_view dsub = sub_view(dv, r0, cnt, dc);
+    mrn_view like = hv;
+    like.n_records = cnt;
+    mrn_view staged;
+    staged_view(like, stage + (uint64_t)slot * slot_bytes, &staged, sc, sc2);
+    if (h2d) {
+      cudaStreamWaitEvent(s_copy_, ev_free_[slot], 0);
+      if ((rc = copy_parts(view_parts(hsub), view_parts(staged), cudaMemcpyHostToDevice, s_copy_))) return rc;
+      cudaEventRecord(ev_copied_[slot], s_copy_);
+      cudaStreamWaitEvent(s_conv_, ev_copied_[slot], 0);
+      if ((rc = mrn_convert(&staged, &dsub, s_conv_))) return rc;
+      cudaEventRecord(ev_free_[slot], s_conv_);
+    } else {
+      cudaStreamWaitEvent(s_conv_, ev_free_[slot], 0);
+      if ((rc = mrn_convert(&dsub, &staged, s_conv_))) return rc;
+      cudaEventRecord(ev_copied_[slot], s_conv_);
+      cudaStreamWaitEvent(s_copy_, ev_copied_[slot], 0);
+      if ((rc = copy_parts(view_parts(staged), view_parts(hsub), cudaMemcpyDeviceToHost, s_copy_))) return rc;
+      cudaEventRecord(ev_free_[slot], s_copy_);
+    }
+  }
+  // Device single-block SoA destination: zero its alignment holes once.
+  if (h2d) return zero_dst_gaps(dst, s_conv_);
+  return MRN_OK;
+}
+
+namespace {
+std::mutex g_engine_mu;
+TransferEngine* g_engine = nullptr;
+}  // namespace
+
+}  // namespace mrn
+
+using namespace mrn;
+
+extern "C" int mrn_transfer_convert(const mrn_view* src, const mrn_view* dst, const mrn_transfer_opts* opts,
+                                    void* stream) {
+  bool jag = false;
+  int rc = validate_pair(src, dst, false, &jag);
+  if (rc) return rc;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MRN_ECUDA;
+  const bool h2d = is_host(*src) && dst->mem == MRN_MEM_DEVICE && dst->device == dev;
+  const bool d2h = src->mem == MRN_MEM_DEVICE && src->device == dev && is_host(*dst);
+  if (!h2d && !d2h) return MRN_EINVAL;
+  if (jag && dst->layout.kind == MRN_AOS && dst->n_children < src->n_children) return MRN_ESIZE;
+  std::lock_guard<std::mutex> lk(g_engine_mu);
+  if (!g_engine) g_engine = new TransferEngine();
+  return g_engine->run(*src, *dst, opts ? opts->chunk_bytes : 0, opts ? opts->n_slots : 0,
+                       static_cast<cudaStream_t>(stream));
+}

@@ -1,0 +1,229 @@
+"""GPU parity of the jagged path (Sec. V, jagged vector property): the prefix
+sum of the sizes and the flattened children must equal the oracle's exactly,
+in both directions, for canonical and shuffled child pools; the device-side
+checks (offset overflow, child capacity, child indices, bounded look-back
+waits) must report their status codes without faulting."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+import paper_2511_04853_b300 as mrn
+from gpu_util import dev, dev_dest, dev_view, garbage, host, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def tracks(n, seed=2, **kw):
+    return mrn.Schema(datagen.TRACKS), oracle.Schema(datagen.TRACKS), datagen.workload("tracks", n, seed, **kw)
+
+
+def a2s_check(s, o, o_aos, m_cap=None):
+    n = o_aos.n
+    m = o_aos.m if m_cap is None else m_cap
+    o_soa = oracle.convert(o, o_aos, "soa", m=m)
+    src = dev_view(s, o_aos, o)
+    dst = dev_dest(s, "soa", n, m)
+    mrn.convert(src, dst)
+    assert mrn.sync() == mrn.OK
+    nb = o.base_bytes("soa", 0, n, m)
+    got, want = host(dst.tensors[0], nb), o_soa.base[:nb]
+    if not np.array_equal(got, want):
+        bad = np.nonzero(got != want)[0]
+        raise AssertionError("%d bytes differ, first at %d" % (bad.size, bad[0]))
+    return o_soa, dst
+
+
+def test_tracks_100000_both_directions():
+    n = 100000
+    s, o, d = tracks(n)
+    o_aos = oracle.pack(o, d, "aos")
+    o_soa, dst = a2s_check(s, o, o_aos)
+    off = host(dst.tensors[0])[o.soa_region_start(n, d["m"], 3):][: (n + 1) * 4].view(np.uint32)
+    assert off[0] == 0 and off[-1] == d["m"] and (np.diff(off.astype(np.int64)) >= 0).all()
+    back = dev_dest(s, "aos", n, d["m"])
+    mrn.convert(dst, back)
+    assert mrn.sync() == mrn.OK
+    assert np.array_equal(host(back.tensors[0], n * 24), o_aos.base[: n * 24])
+    assert np.array_equal(host(back.tensors[1], d["m"] * 8), o_aos.pool[: d["m"] * 8])
+    assert mrn.jagged_count(dev_view(s, o_aos, o)) == d["m"]
+
+
+def test_tracks_raw_bits_and_shuffled_pool_with_gaps():
+    n = 20000
+    s, o, d = tracks(n, seed=5, raw=True)
+    o_aos = oracle.pack(o, d, "aos")
+    order = np.random.default_rng(9).permutation(n)
+    shuffled = oracle.shuffle_pool(o, o_aos, order, gap=2)
+    a2s_check(s, o, shuffled, m_cap=d["m"])
+
+
+@pytest.mark.parametrize("n", [0, 1, 255, 256, 257, 1000, 5003])
+@pytest.mark.parametrize("osz", ["u32", "u64"])
+def test_sizes_and_offset_types(n, osz):
+    desc = [("a", "u8", 1), ("b", "f64", 1),
+            ("v", "jagged", osz, [("x", "u16", 1), ("y", "u8", 3), ("z", "f64", 1)]),
+            ("c", "u32", 2)]
+    s, o = mrn.Schema(desc), oracle.Schema(desc)
+    d = datagen.jagged_random(desc, n, 11 + n, mean_len=3.0, max_len=40)
+    o_aos = oracle.pack(o, d, "aos")
+    o_soa, dst = a2s_check(s, o, o_aos)
+    back = dev_dest(s, "aos", n, d["m"])
+    mrn.convert(dst, back)
+    assert mrn.sync() == mrn.OK
+    assert np.array_equal(host(back.tensors[0], n * o.stride), o_aos.base[: n * o.stride])
+    cs = o.child.stride
+    assert np.array_equal(host(back.tensors[1], d["m"] * cs), o_aos.pool[: d["m"] * cs])
+
+
+def test_particle_schema():
+    s, o = mrn.Schema(datagen.PARTICLE), oracle.Schema(datagen.PARTICLE)
+    n = 3000
+    d = datagen.jagged_random(datagen.PARTICLE, n, 4, mean_len=6.0, max_len=25)
+    o_aos = oracle.pack(o, d, "aos")
+    a2s_check(s, o, o_aos)
+
+
+def test_long_rows_and_empty_rows():
+    """Lengths up to 256 mixed with many zero-length objects."""
+    desc = datagen.TRACKS
+    s, o = mrn.Schema(desc), oracle.Schema(desc)
+    n = 3000
+    rng = np.random.default_rng(1)
+    lengths = np.where(rng.random(n) < 0.7, 0, rng.integers(200, 257, n)).astype(np.uint32)
+    m = int(lengths.sum())
+    d = {"columns": [rng.random(n).astype(np.float32), rng.random(n).astype(np.float32),
+                     rng.integers(0, 9, n).astype(np.int32)], "n": n, "lengths": lengths,
+         "children": [rng.integers(0, 2**32, m, dtype=np.uint64).astype(np.uint32),
+                      rng.random(m).astype(np.float32)], "m": m}
+    a2s_check(s, o, oracle.pack(o, d, "aos"))
+
+
+def test_separate_offsets_and_child_columns():
+    n = 4000
+    s, o, d = tracks(n, seed=3)
+    o_aos = oracle.pack(o, d, "aos")
+    o_soa = oracle.convert(o, o_aos, "soa", m=d["m"])
+    cols = [garbage(n * 4) for _ in range(3)]
+    offs = garbage((n + 1) * 4)
+    kids = [garbage(d["m"] * 4) for _ in range(2)]
+    dst = mrn.View(s, "soa", n, columns=cols, offsets=offs, child_columns=kids, m=d["m"])
+    mrn.convert(dev_view(s, o_aos, o), dst)
+    assert mrn.sync() == mrn.OK
+    for c in range(3):
+        assert np.array_equal(host(cols[c]), oracle.region(o, o_soa, c))
+    assert np.array_equal(host(offs), oracle.region(o, o_soa, 3))
+    for c in range(2):
+        assert np.array_equal(host(kids[c]), oracle.region(o, o_soa, 4 + c))
+
+
+def test_offset_base_shards_concatenate():
+    """Two shards converted with offset_base equal the whole collection."""
+    n = 6000
+    s, o, d = tracks(n, seed=8)
+    o_aos = oracle.pack(o, d, "aos")
+    o_soa = oracle.convert(o, o_aos, "soa", m=d["m"])
+    whole_off = oracle.region(o, o_soa, 3).view(np.uint32)
+    half = 2500  # not a multiple of the tile
+    lens = d["lengths"]
+    m0 = int(lens[:half].sum())
+    parts = []
+    for lo, hi, base in [(0, half, 0), (half, n, m0)]:
+        sub = oracle.Side("aos", hi - lo, o_aos.m, base=o_aos.base[lo * 24: hi * 24].copy(), pool=o_aos.pool)
+        mm = int(lens[lo:hi].sum())
+        src = mrn.View(s, "aos", hi - lo, base=dev(sub.base), child_pool=dev(o_aos.pool), m=o_aos.m)
+        offs = garbage((hi - lo + 1) * 4)
+        kids = [garbage(mm * 4) for _ in range(2)]
+        cols = [garbage((hi - lo) * 4) for _ in range(3)]
+        dst = mrn.View(s, "soa", hi - lo, columns=cols, offsets=offs, child_columns=kids, m=mm,
+                       offset_base=base)
+        mrn.convert(src, dst)
+        assert mrn.sync() == mrn.OK
+        parts.append((host(offs).view(np.uint32), [host(k) for k in kids]))
+    offs_all = np.concatenate([parts[0][0][:-1], parts[1][0]])
+    assert np.array_equal(offs_all, whole_off)
+    for c in range(2):
+        assert np.array_equal(np.concatenate([parts[0][1][c], parts[1][1][c]]),
+                              oracle.region(o, o_soa, 4 + c))
+
+
+def test_u32_offset_overflow_reported():
+    """offset_base close to 2^32: the u32 prefix sum overflows; the kernel
+    records MRN_EOVERFLOW (all buffers are real and in bounds)."""
+    n = 600
+    s, o, d = tracks(n, seed=4)
+    o_aos = oracle.pack(o, d, "aos")
+    dst = dev_dest(s, "soa", n, d["m"])
+    dst.s.offset_base = 2**32 - 100
+    mrn.convert(dev_view(s, o_aos, o), dst)
+    bits = mrn.sync_bits()
+    assert bits & (1 << mrn.EOVERFLOW)
+
+
+def test_child_capacity_too_small():
+    n = 2000
+    s, o, d = tracks(n, seed=6)
+    o_aos = oracle.pack(o, d, "aos")
+    cap = d["m"] // 2
+    o_soa = oracle.convert(o, o_aos, "soa", m=d["m"])
+    kids = [garbage(cap * 4) for _ in range(2)]
+    cols = [garbage(n * 4) for _ in range(3)]
+    offs = garbage((n + 1) * 4)
+    dst = mrn.View(s, "soa", n, columns=cols, offsets=offs, child_columns=kids, m=cap)
+    mrn.convert(dev_view(s, o_aos, o), dst)
+    assert mrn.sync() == mrn.ESIZE
+    # what fits is still right, and the offsets are complete
+    assert np.array_equal(host(offs), oracle.region(o, o_soa, 3))
+    for c in range(2):
+        assert np.array_equal(host(kids[c]), oracle.region(o, o_soa, 4 + c)[: cap * 4])
+
+
+def test_child_index_beyond_pool_reported():
+    n = 1000
+    s, o, d = tracks(n, seed=7)
+    o_aos = oracle.pack(o, d, "aos")
+    src = mrn.View(s, "aos", n, base=dev(o_aos.base), child_pool=dev(o_aos.pool), m=d["m"] - 5)
+    dst = dev_dest(s, "soa", n, d["m"])
+    mrn.convert(src, dst)
+    assert mrn.sync() == mrn.EINVAL
+
+
+def test_decreasing_offsets_reported():
+    n = 100
+    s, o, d = tracks(n, seed=1)
+    o_soa = oracle.convert(o, oracle.pack(o, d, "aos"), "soa", m=d["m"])
+    base = o_soa.base.copy()
+    st = o.soa_region_start(n, d["m"], 3)
+    offs = base[st: st + (n + 1) * 4].view(np.uint32)
+    offs[50], offs[51] = offs[51], offs[50] + 1000
+    src = mrn.View(s, "soa", n, base=dev(base), m=d["m"])
+    dst = dev_dest(s, "aos", n, d["m"])
+    mrn.convert(src, dst)
+    assert mrn.sync() == mrn.EINVAL
+
+
+def test_lookback_wait_is_bounded():
+    """Fault injection on the host side: tile 1 never publishes its sum, so
+    tile 2's look-back wait must expire (1 ms bound) and report
+    MRN_ETIMEOUT; the context stays usable afterwards."""
+    n = 4 * 256
+    s, o, d = tracks(n, seed=3)
+    o_aos = oracle.pack(o, d, "aos")
+    try:
+        mrn.debug_set(2, 1_000_000)
+        mrn.debug_set(1, 1)
+        dst = dev_dest(s, "soa", n, d["m"])
+        mrn.convert(dev_view(s, o_aos, o), dst)
+        assert mrn.sync() == mrn.ETIMEOUT
+    finally:
+        mrn.debug_set(1, -1)
+        mrn.debug_set(2, 2_000_000_000)
+    a2s_check(s, o, o_aos)  # normal operation afterwards
+
+
+def test_aosoa_with_jagged_is_unsupported():
+    s = mrn.Schema(datagen.TRACKS)
+    buf = garbage(1 << 12)
+    src = mrn.View(s, "aos", 10, base=buf, child_pool=buf, m=1)
+    dst = mrn.View(s, "aosoa", 10, block=32, base=buf)
+    assert mrn.convert_status(src, dst) == mrn.EUNSUPPORTED
