@@ -178,6 +178,8 @@ void gap_plan(const mrn_schema* s, const mrn_view& dst, GapPlan* g) {
 
 }  // namespace
 
+void gap_plan_of(const mrn_view& dst, GapPlan* g) { gap_plan(dst.schema, dst, g); }
+
 int zero_dst_gaps(const mrn_view& dst, void* stream) {
   GapPlan g;
   gap_plan(dst.schema, dst, &g);

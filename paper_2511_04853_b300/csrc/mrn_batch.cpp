@@ -1,0 +1,259 @@
+// Batched conversions: many collections (any schemas and layout pairs) in
+// one persistent kernel launch, optionally replayed from a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mrn_internal.h"
+
+struct mrn_batch {
+  int device = -1;
+  bool use_graph = false;
+  // Owned copies of the job views and of the column-pointer arrays they
+  // reference (the caller's arrays may be freed after create).
+  std::vector<mrn_view> src, dst;
+  std::vector<std::vector<void*>> cols;  // 4 per job
+  std::vector<size_t> first_entry;       // job -> index of its first table entry
+  std::vector<BatchJob> jobs;
+  std::vector<unsigned long long> first_tile;
+  unsigned long long total_tiles = 0;
+  BatchJob* d_jobs = nullptr;
+  unsigned long long* d_first = nullptr;
+  char* d_scratch = nullptr;  // counter (256 B) + one look-back word per tile
+  size_t scratch_bytes = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint32_t ctas_per_sm = 0;
+
+  ~mrn_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+    cudaFree(d_jobs);
+    cudaFree(d_first);
+    cudaFree(d_scratch);
+  }
+};
+
+namespace mrn {
+namespace {
+
+// Copies a view and the pointer arrays it references.
+void own_view(const mrn_view& v, std::vector<void*>* c0, std::vector<void*>* c1, mrn_view* out) {
+  *out = v;
+  const mrn_schema* s = v.schema;
+  if (v.columns) {
+    c0->assign(v.columns, v.columns + s->cols.size());
+    out->columns = c0->data();
+  }
+  if (v.child_columns && s->has_jagged) {
+    c1->assign(v.child_columns, v.child_columns + s->child->cols.size());
+    out->child_columns = c1->data();
+  }
+}
+
+// Plans one job (everything but tile_begin), followed by a zero-fill job
+// when the destination has alignment holes.
+int plan_job(const mrn_view& src, const mrn_view& dst, std::vector<BatchJob>* out) {
+  bool jag = false;
+  int rc = validate_pair(&src, &dst, true, &jag);
+  if (rc) return rc;
+  BatchJob j;
+  std::memset(&j, 0, sizeof(j));
+  if (jag) {
+    if ((rc = build_jagged_plan(src, dst, &j.jp))) return rc;
+    if (src.layout.kind == MRN_AOS) {
+      j.kind = JOB_JAG_A2S;
+      j.ntiles = (src.n_records + MRN_JAG_TILE - 1) / MRN_JAG_TILE;
+    } else {
+      j.kind = JOB_JAG_S2A;
+      j.parent_groups = (src.n_records + 31) / 32;
+      const uint64_t groups = j.parent_groups + (j.jp.m_src + 31) / 32;
+      j.ntiles = (groups + 7) / 8;
+    }
+  } else {
+    if (src.layout.kind == MRN_AOS && dst.layout.kind == MRN_AOS) return MRN_EUNSUPPORTED;
+    if ((rc = build_plan(src, dst, &j.jp.parent))) return rc;
+    j.kind = JOB_CONVERT;
+    const LaunchShape sh = tuned_shape(j.jp.parent);
+    uint32_t tr = sh.tile_records ? sh.tile_records : 1024;
+    tr = std::max<uint32_t>(256, tr / 256 * 256);
+    j.tile_records = tr;
+    const ConvPlan& p = j.jp.parent;
+    const uint64_t nrec = p.dir == DIR_FM_AOS ? p.n : p.n_fm_pad;
+    j.ntiles = (nrec + tr - 1) / tr;
+  }
+  out->push_back(j);
+  GapPlan g;
+  gap_plan_of(dst, &g);
+  if (g.ngaps && g.nblocks) {
+    BatchJob z;
+    std::memset(&z, 0, sizeof(z));
+    z.kind = JOB_ZERO;
+    z.gp = g;
+    z.ntiles = (g.nblocks * g.ngaps + 255) / 256;
+    out->push_back(z);
+  }
+  return MRN_OK;
+}
+
+int rebuild_tables(mrn_batch* b) {
+  b->jobs.clear();
+  b->first_entry.clear();
+  for (size_t i = 0; i < b->src.size(); ++i) {
+    b->first_entry.push_back(b->jobs.size());
+    int rc = plan_job(b->src[i], b->dst[i], &b->jobs);
+    if (rc) return rc;
+  }
+  b->first_tile.assign(b->jobs.size(), 0);
+  unsigned long long t = 0;
+  for (size_t i = 0; i < b->jobs.size(); ++i) {
+    b->jobs[i].tile_begin = t;
+    b->first_tile[i] = t;
+    t += b->jobs[i].ntiles;
+  }
+  b->total_tiles = t;
+  return MRN_OK;
+}
+
+int upload(mrn_batch* b) {
+  const size_t jb = std::max<size_t>(1, b->jobs.size()) * sizeof(BatchJob);
+  const size_t fb = std::max<size_t>(1, b->first_tile.size()) * sizeof(unsigned long long);
+  b->scratch_bytes = 256 + (size_t)b->total_tiles * sizeof(unsigned long long);
+  if (cudaMalloc(&b->d_jobs, jb) != cudaSuccess || cudaMalloc(&b->d_first, fb) != cudaSuccess ||
+      cudaMalloc(&b->d_scratch, b->scratch_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return MRN_ENOMEM;
+  }
+  if (b->jobs.empty()) return MRN_OK;
+  if (cudaMemcpy(b->d_jobs, b->jobs.data(), b->jobs.size() * sizeof(BatchJob), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(b->d_first, b->first_tile.data(), b->first_tile.size() * sizeof(unsigned long long),
+                 cudaMemcpyHostToDevice) != cudaSuccess)
+    return MRN_ECUDA;
+  return MRN_OK;
+}
+
+int enqueue(mrn_batch* b, cudaStream_t s) {
+  if (b->total_tiles == 0) return MRN_OK;
+  if (cudaMemsetAsync(b->d_scratch, 0, b->scratch_bytes, s) != cudaSuccess) return MRN_ECUDA;
+  return launch_batch(b->d_jobs, b->d_first, (unsigned)b->jobs.size(), b->total_tiles,
+                      reinterpret_cast<unsigned int*>(b->d_scratch),
+                      reinterpret_cast<unsigned long long*>(b->d_scratch + 256), b->ctas_per_sm, s);
+}
+
+int capture(mrn_batch* b) {
+  if (!b->cap && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return MRN_ECUDA;
+  if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MRN_ECUDA;
+  const int rc = enqueue(b, b->cap);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+  if (rc || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc ? rc : MRN_ECUDA;
+  }
+  b->graph = g;
+  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) return MRN_ECUDA;
+  return MRN_OK;
+}
+
+}  // namespace
+}  // namespace mrn
+
+using namespace mrn;
+
+extern "C" {
+
+int mrn_batch_create(const mrn_job* jobs, size_t n_jobs, int use_graph, mrn_batch** out) {
+  if (!out || (n_jobs && !jobs) || n_jobs > 0x7fffffff) return MRN_EINVAL;
+  *out = nullptr;
+  mrn_batch* b = new (std::nothrow) mrn_batch();
+  if (!b) return MRN_ENOMEM;
+  cudaGetDevice(&b->device);
+  b->use_graph = use_graph != 0;
+  b->src.resize(n_jobs);
+  b->dst.resize(n_jobs);
+  b->cols.resize(4 * n_jobs);
+  for (size_t i = 0; i < n_jobs; ++i) {
+    if (!jobs[i].src || !jobs[i].dst) {
+      delete b;
+      return MRN_EINVAL;
+    }
+    own_view(*jobs[i].src, &b->cols[4 * i], &b->cols[4 * i + 1], &b->src[i]);
+    own_view(*jobs[i].dst, &b->cols[4 * i + 2], &b->cols[4 * i + 3], &b->dst[i]);
+  }
+  int rc = rebuild_tables(b);
+  if (!rc && b->total_tiles > 0x7fffffffull) rc = MRN_EUNSUPPORTED;
+  if (!rc) rc = upload(b);
+  if (!rc && b->use_graph) rc = capture(b);
+  if (rc) {
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return MRN_OK;
+}
+
+int mrn_batch_launch(mrn_batch* b, void* stream) {
+  if (!b) return MRN_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (b->exec) return cudaGraphLaunch(b->exec, s) == cudaSuccess ? MRN_OK : MRN_ECUDA;
+  return enqueue(b, s);
+}
+
+int mrn_batch_launch_per_job(mrn_batch* b, void* stream) {
+  if (!b) return MRN_EINVAL;
+  for (size_t i = 0; i < b->src.size(); ++i) {
+    const int rc = mrn_convert(&b->src[i], &b->dst[i], stream);
+    if (rc) return rc;
+  }
+  return MRN_OK;
+}
+
+int mrn_batch_update(mrn_batch* b, size_t j, const mrn_view* src, const mrn_view* dst) {
+  if (!b || !src || !dst || !src->schema || j >= b->src.size()) return MRN_EINVAL;
+  const mrn_view& os = b->src[j];
+  const mrn_view& od = b->dst[j];
+  // The job table keeps its shape: same schema, layouts and sizes.
+  if (src->schema->hash != os.schema->hash || src->layout.kind != os.layout.kind ||
+      src->layout.block != os.layout.block || dst->layout.kind != od.layout.kind ||
+      dst->layout.block != od.layout.block || src->n_records != os.n_records ||
+      src->n_children != os.n_children || dst->n_children != od.n_children)
+    return MRN_EINVAL;
+  std::vector<void*> c[4];
+  mrn_view ns, nd;
+  own_view(*src, &c[0], &c[1], &ns);
+  own_view(*dst, &c[2], &c[3], &nd);
+  std::vector<BatchJob> fresh;
+  int rc = plan_job(ns, nd, &fresh);
+  if (rc) return rc;
+  const size_t k = b->first_entry[j];
+  const size_t next = j + 1 < b->first_entry.size() ? b->first_entry[j + 1] : b->jobs.size();
+  if (fresh.size() != next - k) return MRN_EINVAL;
+  for (size_t i = 0; i < fresh.size(); ++i) {
+    if (fresh[i].ntiles != b->jobs[k + i].ntiles) return MRN_EINVAL;
+    fresh[i].tile_begin = b->jobs[k + i].tile_begin;
+  }
+  for (int q = 0; q < 4; ++q) b->cols[4 * j + q] = std::move(c[q]);
+  own_view(*src, &b->cols[4 * j], &b->cols[4 * j + 1], &b->src[j]);
+  own_view(*dst, &b->cols[4 * j + 2], &b->cols[4 * j + 3], &b->dst[j]);
+  for (size_t i = 0; i < fresh.size(); ++i) {
+    b->jobs[k + i] = fresh[i];
+    if (cudaMemcpy(b->d_jobs + k + i, &fresh[i], sizeof(BatchJob), cudaMemcpyHostToDevice) != cudaSuccess)
+      return MRN_ECUDA;
+  }
+  return MRN_OK;
+}
+
+void mrn_batch_destroy(mrn_batch* b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  delete b;
+}
+
+}  // extern "C"

@@ -98,6 +98,23 @@ __device__ __forceinline__ void load_words(const char* p, uint32_t nbytes, uint3
   }
 }
 
+// V == 0: the access width is chosen at run time from `vec` (a uniform
+// branch per 64-byte window), for kernels that serve many plans at once.
+template <int V>
+__device__ __forceinline__ void load_any(const char* p, uint32_t nbytes, uint32_t (&w)[16], uint32_t vec) {
+  if constexpr (V != 0) {
+    load_words<V>(p, nbytes, w);
+  } else {
+    switch (vec) {
+      case 16: load_words<16>(p, nbytes, w); break;
+      case 8: load_words<8>(p, nbytes, w); break;
+      case 4: load_words<4>(p, nbytes, w); break;
+      case 2: load_words<2>(p, nbytes, w); break;
+      default: load_words<1>(p, nbytes, w); break;
+    }
+  }
+}
+
 template <int V>
 __device__ __forceinline__ void store_words(char* p, uint32_t nbytes, const uint32_t (&w)[16]) {
   if constexpr (V == 16) {
@@ -126,6 +143,21 @@ __device__ __forceinline__ void store_words(char* p, uint32_t nbytes, const uint
   }
 }
 
+template <int V>
+__device__ __forceinline__ void store_any(char* p, uint32_t nbytes, const uint32_t (&w)[16], uint32_t vec) {
+  if constexpr (V != 0) {
+    store_words<V>(p, nbytes, w);
+  } else {
+    switch (vec) {
+      case 16: store_words<16>(p, nbytes, w); break;
+      case 8: store_words<8>(p, nbytes, w); break;
+      case 4: store_words<4>(p, nbytes, w); break;
+      case 2: store_words<2>(p, nbytes, w); break;
+      default: store_words<1>(p, nbytes, w); break;
+    }
+  }
+}
+
 // AoS record -> field-major columns, one record per lane.
 //   r      destination record index (field-major side)
 //   ld_ok  the lane has a source record at `rec`
@@ -142,7 +174,7 @@ __device__ __forceinline__ void aos_to_fm_lane(const ConvPlan& p, uint64_t r, bo
 #pragma unroll
     for (int k = 0; k < 16; ++k) w[k] = 0;
     const uint32_t nb = min(64u, stride - win * 4);
-    if (ld_ok) load_words<V>(rec + win * 4, nb, w);
+    if (ld_ok) load_any<V>(rec + win * 4, nb, w, p.vec);
     const uint32_t nw = min((uint32_t)MRN_WIN_WORDS, aw - win);
 #pragma unroll
     for (int k = 0; k < 16; ++k)
@@ -211,7 +243,7 @@ __device__ __forceinline__ void fm_to_aos_lane(const ConvPlan& p, uint64_t r, bo
       uint32_t w[16];
 #pragma unroll
       for (int k = 0; k < 16; ++k) w[k] = k < (int)nw ? tw[k * MRN_TW_PITCH + lane] : 0u;
-      store_words<V>(rec + win * 4, min(64u, stride - win * 4), w);
+      store_any<V>(rec + win * 4, min(64u, stride - win * 4), w, p.vec);
     }
   }
 }

@@ -60,6 +60,8 @@ uint64_t tune_key(uint64_t hash, const mrn_layout& a, const mrn_layout& b);
 int build_plan(const mrn_view& src, const mrn_view& dst, ConvPlan* p);
 // Builds the plan of a validated jagged view pair.
 int build_jagged_plan(const mrn_view& src, const mrn_view& dst, JagPlan* jp);
+// Alignment holes of a single-block SoA or AoSoA destination view.
+void gap_plan_of(const mrn_view& dst, GapPlan* g);
 // Zeroes the alignment holes of a single-block SoA or AoSoA device view.
 int zero_dst_gaps(const mrn_view& dst, void* stream);
 // Host-side validation of a device view pair; fills *is_jagged.
@@ -79,6 +81,12 @@ uint64_t jagged_scratch_bytes(uint64_t n);
 int launch_jagged_a2s(JagPlan& jp, void* scratch, void* stream);
 int launch_jagged_s2a(const JagPlan& jp, void* stream);
 int launch_jagged_count(const ConvPlan& parent, uint64_t* dev_total, void* stream);
+
+// Persistent launch of a batch (mrn_batch.cpp owns the device tables).
+int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, unsigned int njobs,
+                 unsigned long long total_tiles, unsigned int* counter, unsigned long long* states,
+                 unsigned int ctas_per_sm, void* stream);
+int batch_occupancy();
 
 // Cached launch shape for a plan (autotuner), or the default.
 LaunchShape tuned_shape(const ConvPlan& p);

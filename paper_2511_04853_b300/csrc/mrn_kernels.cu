@@ -15,25 +15,22 @@ __device__ __forceinline__ void flag_error(int code) { atomicOr(&g_mrn_status_bi
 
 // ------------------------------------------------------------- conversion
 
-// One warp per 32 records, grid-stride over warps.
-template <int V, int DIR>
-__global__ void __launch_bounds__(256) k_convert(const __grid_constant__ ConvPlan p) {
-  extern __shared__ uint32_t smem[];
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  uint32_t* tw = smem + warp * MRN_TW_WORDS_PER_WARP;
-  const uint64_t wpb = blockDim.x >> 5;
-  const uint64_t total_warps = (uint64_t)gridDim.x * wpb;
-  const uint64_t nrec = DIR == DIR_FM_AOS ? p.n : p.n_fm_pad;
-  for (uint64_t w = (uint64_t)blockIdx.x * wpb + warp; w * 32 < nrec; w += total_warps) {
-    const uint64_t r = w * 32 + lane;
+// Records [t0, t1) of a plan; the CTA's warps take 32-record groups in turn.
+template <int V>
+__device__ __forceinline__ void conv_range(const ConvPlan& p, uint64_t t0, uint64_t t1, uint32_t* tw,
+                                           int lane, int warp, int nwarps) {
+  const uint32_t dir = p.dir;
+  const uint64_t nrec = dir == DIR_FM_AOS ? p.n : p.n_fm_pad;
+  if (t1 > nrec) t1 = nrec;
+  for (uint64_t g = t0 + (uint64_t)warp * 32; g < t1; g += (uint64_t)nwarps * 32) {
+    const uint64_t r = g + lane;
     const bool ld_ok = r < p.n;
     const bool st_ok = r < nrec;
-    if constexpr (DIR == DIR_AOS_FM) {
+    if (dir == DIR_AOS_FM) {
       uint32_t jl = 0;
       uint64_t jb = 0;
       aos_to_fm_lane<V>(p, r, ld_ok, st_ok, p.src.base + r * p.stride, tw, lane, &jl, &jb);
-    } else if constexpr (DIR == DIR_FM_AOS) {
+    } else if (dir == DIR_FM_AOS) {
       fm_to_aos_lane<V>(p, r, ld_ok, p.dst.base + r * p.stride, tw, lane, 0u, 0ull);
     } else {
       fm_to_fm_lane(p, r, ld_ok, st_ok);
@@ -41,15 +38,32 @@ __global__ void __launch_bounds__(256) k_convert(const __grid_constant__ ConvPla
   }
 }
 
+// One conversion: CTAs take tiles of `tile_records` records, grid-stride.
+template <int V>
+__global__ void __launch_bounds__(256) k_convert(const __grid_constant__ ConvPlan p, uint32_t tile_records) {
+  extern __shared__ uint32_t smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  uint32_t* tw = smem + warp * MRN_TW_WORDS_PER_WARP;
+  const uint64_t nrec = p.dir == DIR_FM_AOS ? p.n : p.n_fm_pad;
+  const uint64_t ntiles = (nrec + tile_records - 1) / tile_records;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
+    conv_range<V>(p, t * tile_records, (t + 1) * tile_records, tw, lane, warp, nwarps);
+}
+
+__device__ __forceinline__ void zero_gap_item(const GapPlan& g, uint64_t t) {
+  const uint64_t b = t / g.ngaps;
+  const uint32_t k = (uint32_t)(t - b * g.ngaps);
+  char* p = g.base + b * g.block_bytes + g.off[k];
+  for (uint32_t i = 0; i < g.len[k]; ++i) p[i] = 0;
+}
+
 __global__ void k_zero_gaps(const __grid_constant__ GapPlan g) {
   const uint64_t total = g.nblocks * g.ngaps;
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t b = t / g.ngaps;
-    const uint32_t k = (uint32_t)(t - b * g.ngaps);
-    char* p = g.base + b * g.block_bytes + g.off[k];
-    for (uint32_t i = 0; i < g.len[k]; ++i) p[i] = 0;
-  }
+       t += (uint64_t)gridDim.x * blockDim.x)
+    zero_gap_item(g, t);
 }
 
 // ------------------------------------------------------------------ jagged
@@ -66,28 +80,26 @@ __device__ __forceinline__ uint64_t read_offset(const char* offs, uint32_t osz, 
   return __ldg(reinterpret_cast<const unsigned long long*>(offs) + i);
 }
 
-// AoS parents (+ child pool) -> SoA parents, offsets, child columns, in one
-// pass: each CTA takes the next tile of 256 parents (dynamic tile id, so all
-// of a tile's predecessors are already running), converts the parents,
-// scans their lengths, obtains the tile's child base by a decoupled
-// look-back over the predecessors' published sums (every wait bounded by
-// timeout_ns), writes the offsets and gathers its children, load-balanced
-// over the tile's threads.
+struct JagShared {
+  unsigned long long excl[MRN_JAG_TILE + 1];
+  unsigned long long beg[MRN_JAG_TILE];
+  unsigned long long warp[8];
+  unsigned long long base;
+};
+
+// One tile of 256 parents of a jagged AoS -> SoA conversion (256 threads):
+// converts the parents, scans their lengths, obtains the tile's child base
+// by a decoupled look-back over the predecessors' published sums in `st`
+// (every wait bounded by jp.timeout_ns), writes the offsets and gathers the
+// tile's children, load-balanced over the tile's threads.  Tiles must be
+// handed out in increasing order (dynamic tile ids), so that every
+// predecessor is already running.
 template <int VP, int VC>
-__global__ void __launch_bounds__(256) k_jagged_a2s(const __grid_constant__ JagPlan jp) {
-  __shared__ uint32_t tw_all[8 * MRN_TW_WORDS_PER_WARP];
-  __shared__ unsigned long long s_excl[MRN_JAG_TILE + 1];
-  __shared__ unsigned long long s_beg[MRN_JAG_TILE];
-  __shared__ unsigned long long s_warp[8];
-  __shared__ unsigned long long s_base;
-  __shared__ unsigned int s_tile;
+__device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile, unsigned long long* st,
+                                                uint32_t* tw_all, JagShared& sh) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t* tw = tw_all + warp * MRN_TW_WORDS_PER_WARP;
   const ConvPlan& P = jp.parent;
-
-  if (tid == 0) s_tile = atomicAdd(jp.tile_counter, 1u);
-  __syncthreads();
-  const uint64_t tile = s_tile;
   const uint64_t r = tile * MRN_JAG_TILE + tid;
   const bool ok = r < P.n;
 
@@ -108,29 +120,27 @@ __global__ void __launch_bounds__(256) k_jagged_a2s(const __grid_constant__ JagP
     const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
-  if (lane == 31) s_warp[warp] = x;
+  if (lane == 31) sh.warp[warp] = x;
   __syncthreads();
   if (warp == 0) {
-    unsigned long long t = lane < 8 ? s_warp[lane] : 0ull;
+    unsigned long long t = lane < 8 ? sh.warp[lane] : 0ull;
 #pragma unroll
     for (int o = 1; o < 8; o <<= 1) {
       const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
       if (lane >= o) t += y;
     }
-    if (lane < 8) s_warp[lane] = t;
+    if (lane < 8) sh.warp[lane] = t;
   }
   __syncthreads();
-  const unsigned long long excl = x - len + (warp > 0 ? s_warp[warp - 1] : 0ull);
-  const unsigned long long agg = s_warp[7];
-  s_excl[tid] = excl;
-  if (tid == MRN_JAG_TILE - 1) s_excl[MRN_JAG_TILE] = agg;
-  s_beg[tid] = bad ? ~0ull : beg;
+  const unsigned long long excl = x - len + (warp > 0 ? sh.warp[warp - 1] : 0ull);
+  const unsigned long long agg = sh.warp[7];
+  sh.excl[tid] = excl;
+  if (tid == MRN_JAG_TILE - 1) sh.excl[MRN_JAG_TILE] = agg;
+  sh.beg[tid] = bad ? ~0ull : beg;
 
-  // Decoupled look-back for the tile's base (number of children of all
-  // earlier tiles).
+  // Decoupled look-back for the number of children of all earlier tiles.
   if (tid == 0) {
     unsigned long long prefix = 0;
-    unsigned long long* st = jp.tile_state;
     const bool publish = (long long)tile != jp.skip_publish_tile;
     if (tile == 0) {
       if (publish) st_release_u64(&st[0], MRN_TS_PREFIX | (agg & MRN_TS_VALUE));
@@ -157,10 +167,10 @@ __global__ void __launch_bounds__(256) k_jagged_a2s(const __grid_constant__ JagP
       }
       if (publish) st_release_u64(&st[tile], MRN_TS_PREFIX | ((prefix + agg) & MRN_TS_VALUE));
     }
-    s_base = prefix;
+    sh.base = prefix;
   }
   __syncthreads();
-  const unsigned long long base = s_base;
+  const unsigned long long base = sh.base;
 
   // Offsets: offset_base + children before this parent.
   if (ok) {
@@ -177,7 +187,7 @@ __global__ void __launch_bounds__(256) k_jagged_a2s(const __grid_constant__ JagP
   }
 
   // Children: slot j of the tile belongs to the last parent p with
-  // s_excl[p] <= j; each warp moves 32 consecutive slots.
+  // excl[p] <= j; each warp moves 32 consecutive slots.
   for (unsigned long long j0 = (unsigned long long)warp * 32; j0 < agg; j0 += MRN_JAG_TILE) {
     const unsigned long long j = j0 + lane;
     const bool cok = j < agg;
@@ -185,11 +195,11 @@ __global__ void __launch_bounds__(256) k_jagged_a2s(const __grid_constant__ JagP
     if (cok) {
       while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (s_excl[mid] <= j) lo = mid; else hi = mid;
+        if (sh.excl[mid] <= j) lo = mid; else hi = mid;
       }
     }
-    const unsigned long long pb = s_beg[lo];
-    const unsigned long long src_idx = pb + (j - s_excl[lo]);
+    const unsigned long long pb = sh.beg[lo];
+    const unsigned long long src_idx = pb + (j - sh.excl[lo]);
     const unsigned long long dst_idx = base + j;
     const bool st_ok = cok && dst_idx < jp.capacity;
     if (cok && !st_ok) flag_error(MRN_ESIZE);
@@ -201,38 +211,52 @@ __global__ void __launch_bounds__(256) k_jagged_a2s(const __grid_constant__ JagP
   }
 }
 
-// SoA parents, offsets, child columns -> AoS parents and a canonical child
-// pool.  Warps [0, parent_warps) build parent records (length and begin from
-// the offsets), the remaining warps convert the m_src children.
+template <int VP, int VC>
+__global__ void __launch_bounds__(256) k_jagged_a2s(const __grid_constant__ JagPlan jp) {
+  __shared__ uint32_t tw_all[8 * MRN_TW_WORDS_PER_WARP];
+  __shared__ JagShared sh;
+  __shared__ unsigned int s_tile;
+  if (threadIdx.x == 0) s_tile = atomicAdd(jp.tile_counter, 1u);
+  __syncthreads();
+  jagged_a2s_tile<VP, VC>(jp, s_tile, jp.tile_state, tw_all, sh);
+}
+
+// One 32-record group of a jagged SoA -> AoS conversion: groups
+// [0, parent_groups) build parent records (length and begin from the
+// offsets), the following groups convert the m_src children into the pool.
+template <int VP, int VC>
+__device__ __forceinline__ void jagged_s2a_group(const JagPlan& jp, uint64_t w, uint64_t parent_groups,
+                                                 uint32_t* tw, int lane) {
+  if (w < parent_groups) {
+    const ConvPlan& P = jp.parent;
+    const uint64_t r = w * 32 + lane;
+    const bool ok = r < P.n;
+    uint64_t a = 0, b = 0;
+    if (ok) {
+      a = read_offset(jp.offsets, jp.off_size, r);
+      b = read_offset(jp.offsets, jp.off_size, r + 1);
+      if (b < a || b - a > 0xffffffffull) flag_error(MRN_EINVAL);
+    }
+    fm_to_aos_lane<VP>(P, r, ok, P.dst.base + r * P.stride, tw, lane, (uint32_t)(b - a), a);
+  } else {
+    const ConvPlan& C = jp.child;
+    const uint64_t j = (w - parent_groups) * 32 + lane;
+    const bool ok = j < jp.m_src;
+    fm_to_aos_lane<VC>(C, j, ok, C.dst.base + j * C.stride, tw, lane, 0u, 0ull);
+  }
+}
+
 template <int VP, int VC>
 __global__ void __launch_bounds__(256) k_jagged_s2a(const __grid_constant__ JagPlan jp,
-                                                    unsigned long long parent_warps) {
+                                                    unsigned long long parent_groups) {
   extern __shared__ uint32_t smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* tw = smem + warp * MRN_TW_WORDS_PER_WARP;
   const uint64_t wpb = blockDim.x >> 5;
-  const uint64_t child_warps = (jp.m_src + 31) / 32;
-  const uint64_t all = parent_warps + child_warps;
+  const uint64_t all = parent_groups + (jp.m_src + 31) / 32;
   const uint64_t total_warps = (uint64_t)gridDim.x * wpb;
-  for (uint64_t w = (uint64_t)blockIdx.x * wpb + warp; w < all; w += total_warps) {
-    if (w < parent_warps) {
-      const ConvPlan& P = jp.parent;
-      const uint64_t r = w * 32 + lane;
-      const bool ok = r < P.n;
-      uint64_t a = 0, b = 0;
-      if (ok) {
-        a = read_offset(jp.offsets, jp.off_size, r);
-        b = read_offset(jp.offsets, jp.off_size, r + 1);
-        if (b < a || b - a > 0xffffffffull) flag_error(MRN_EINVAL);
-      }
-      fm_to_aos_lane<VP>(P, r, ok, P.dst.base + r * P.stride, tw, lane, (uint32_t)(b - a), a);
-    } else {
-      const ConvPlan& C = jp.child;
-      const uint64_t j = (w - parent_warps) * 32 + lane;
-      const bool ok = j < jp.m_src;
-      fm_to_aos_lane<VC>(C, j, ok, C.dst.base + j * C.stride, tw, lane, 0u, 0ull);
-    }
-  }
+  for (uint64_t w = (uint64_t)blockIdx.x * wpb + warp; w < all; w += total_warps)
+    jagged_s2a_group<VP, VC>(jp, w, parent_groups, tw, lane);
 }
 
 // Sum of the jagged lengths of AoS parents.
@@ -249,6 +273,55 @@ __global__ void k_jagged_count(const char* base, uint64_t n, uint32_t stride, ui
 
 __global__ void k_write_offset0(char* offs, uint32_t osz, unsigned long long v) {
   write_offset(offs, osz, 0, v);
+}
+
+// ----------------------------------------------------------------- batched
+
+// Every job of a batch in one persistent launch: each CTA repeatedly takes
+// the next global tile (atomic counter, so tiles start in increasing order),
+// finds its job by binary search over the jobs' first tiles and runs that
+// tile.  Jagged AoS -> SoA jobs keep their look-back state in `states`,
+// indexed by global tile.
+__global__ void __launch_bounds__(256) k_batch(const BatchJob* __restrict__ jobs,
+                                               const unsigned long long* __restrict__ first_tile,
+                                               unsigned int njobs, unsigned long long total_tiles,
+                                               unsigned int* counter, unsigned long long* states) {
+  __shared__ uint32_t tw_all[8 * MRN_TW_WORDS_PER_WARP];
+  __shared__ JagShared sh;
+  __shared__ unsigned long long s_t;
+  __shared__ unsigned int s_j;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* tw = tw_all + warp * MRN_TW_WORDS_PER_WARP;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned long long t = atomicAdd(counter, 1u);
+      s_t = t;
+      if (t < total_tiles) {
+        unsigned int lo = 0, hi = njobs;
+        while (hi - lo > 1) {
+          const unsigned int mid = (lo + hi) >> 1;
+          if (first_tile[mid] <= t) lo = mid; else hi = mid;
+        }
+        s_j = lo;
+      }
+    }
+    __syncthreads();
+    const unsigned long long t = s_t;
+    if (t >= total_tiles) break;
+    const BatchJob& J = jobs[s_j];
+    const unsigned long long local = t - J.tile_begin;
+    if (J.kind == JOB_CONVERT) {
+      conv_range<0>(J.jp.parent, local * J.tile_records, (local + 1) * J.tile_records, tw, lane, warp, 8);
+    } else if (J.kind == JOB_JAG_A2S) {
+      jagged_a2s_tile<0, 0>(J.jp, local, states + J.tile_begin, tw_all, sh);
+    } else if (J.kind == JOB_JAG_S2A) {
+      jagged_s2a_group<0, 0>(J.jp, local * 8 + warp, J.parent_groups, tw, lane);
+    } else {
+      const uint64_t k = local * 256 + threadIdx.x;
+      if (k < J.gp.nblocks * J.gp.ngaps) zero_gap_item(J.gp, k);
+    }
+    __syncthreads();
+  }
 }
 
 // ================================================================== host
@@ -268,26 +341,14 @@ int cuda_status(cudaError_t e) {
   return MRN_ECUDA;
 }
 
-template <int V, int DIR>
-void* conv_kernel_ptr() {
-  return reinterpret_cast<void*>(&k_convert<V, DIR>);
-}
-
-template <int DIR>
-void* conv_kernel_for(uint32_t vec) {
+void* conv_kernel(uint32_t vec) {
   switch (vec) {
-    case 16: return conv_kernel_ptr<16, DIR>();
-    case 8: return conv_kernel_ptr<8, DIR>();
-    case 4: return conv_kernel_ptr<4, DIR>();
-    case 2: return conv_kernel_ptr<2, DIR>();
-    default: return conv_kernel_ptr<1, DIR>();
+    case 16: return reinterpret_cast<void*>(&k_convert<16>);
+    case 8: return reinterpret_cast<void*>(&k_convert<8>);
+    case 4: return reinterpret_cast<void*>(&k_convert<4>);
+    case 2: return reinterpret_cast<void*>(&k_convert<2>);
+    default: return reinterpret_cast<void*>(&k_convert<1>);
   }
-}
-
-void* conv_kernel(uint32_t dir, uint32_t vec) {
-  if (dir == DIR_AOS_FM) return conv_kernel_for<DIR_AOS_FM>(vec);
-  if (dir == DIR_FM_AOS) return conv_kernel_for<DIR_FM_AOS>(vec);
-  return conv_kernel_ptr<1, DIR_FM_FM>();
 }
 
 // Resident CTAs per SM of a kernel (cached per kernel and shape).
@@ -341,15 +402,17 @@ int launch_convert(const ConvPlan& p, void* stream, const LaunchShape* shape) {
   const uint64_t nrec = p.dir == DIR_FM_AOS ? p.n : p.n_fm_pad;
   if (nrec == 0) return MRN_OK;
   LaunchShape sh = shape ? *shape : LaunchShape{};
-  if (sh.threads != 128 && sh.threads != 256) sh.threads = 256;
-  void* fn = conv_kernel(p.dir, p.vec);
+  if (sh.threads != 64 && sh.threads != 128 && sh.threads != 256) sh.threads = 256;
+  if (sh.tile_records == 0 || sh.tile_records % 32) sh.tile_records = sh.threads * 2;
+  void* fn = conv_kernel(p.dir == DIR_FM_FM ? 1 : p.vec);
   const size_t smem = (sh.threads / 32) * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t);
-  const int per_sm = sh.ctas_per_sm ? (int)sh.ctas_per_sm : occupancy(fn, (int)sh.threads, smem);
-  const uint64_t warps = (nrec + 31) / 32;
-  const uint64_t need = (warps + sh.threads / 32 - 1) / (sh.threads / 32);
+  const int occ = occupancy(fn, (int)sh.threads, smem);
+  const int per_sm = sh.ctas_per_sm ? std::min((int)sh.ctas_per_sm, occ) : occ;
+  const uint64_t need = (nrec + sh.tile_records - 1) / sh.tile_records;
   const uint64_t cap = (uint64_t)device_sm_count() * (uint64_t)per_sm;
   const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(need, cap));
-  void* args[] = {const_cast<ConvPlan*>(&p)};
+  uint32_t tr = sh.tile_records;
+  void* args[] = {const_cast<ConvPlan*>(&p), &tr};
   cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(sh.threads), args, smem,
                                    static_cast<cudaStream_t>(stream));
   return cuda_status(e);
@@ -441,8 +504,8 @@ int launch_jagged_s2a(const JagPlan& jp, void* stream) {
   const int per_sm = occupancy(fn, 256, kConvSmem);
   const uint64_t need = (pw + cw + 7) / 8;
   const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)device_sm_count() * per_sm));
-  unsigned long long pwu = pw;
-  void* args[] = {const_cast<JagPlan*>(&jp), &pwu};
+  unsigned long long pgroups = pw;
+  void* args[] = {const_cast<JagPlan*>(&jp), &pgroups};
   return cuda_status(cudaLaunchKernel(fn, dim3(grid), dim3(256), args, kConvSmem,
                                       static_cast<cudaStream_t>(stream)));
 }
@@ -455,6 +518,21 @@ int launch_jagged_count(const ConvPlan& parent, uint64_t* dev_total, void* strea
       1, std::min<uint64_t>((parent.n + 255) / 256, (uint64_t)device_sm_count() * 8));
   k_jagged_count<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(
       parent.src.base, parent.n, parent.stride, len_off, reinterpret_cast<unsigned long long*>(dev_total));
+  return cuda_status(cudaGetLastError());
+}
+
+int batch_occupancy() { return occupancy(reinterpret_cast<void*>(&k_batch), 256, 0); }
+
+int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, unsigned int njobs,
+                 unsigned long long total_tiles, unsigned int* counter, unsigned long long* states,
+                 unsigned int ctas_per_sm, void* stream) {
+  if (total_tiles == 0) return MRN_OK;
+  const int occ = batch_occupancy();
+  const int per_sm = ctas_per_sm ? std::min((int)ctas_per_sm, occ) : occ;
+  const uint64_t cap = (uint64_t)device_sm_count() * (uint64_t)per_sm;
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(cap, total_tiles));
+  k_batch<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(jobs, first_tile, njobs, total_tiles,
+                                                                 counter, states);
   return cuda_status(cudaGetLastError());
 }
 

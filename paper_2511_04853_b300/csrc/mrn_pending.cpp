@@ -2,12 +2,6 @@
 #include "mrn_internal.h"
 
 extern "C" {
-int mrn_batch_create(const mrn_job*, size_t, int, mrn_batch**) { return MRN_EUNSUPPORTED; }
-int mrn_batch_launch(mrn_batch*, void*) { return MRN_EUNSUPPORTED; }
-int mrn_batch_launch_per_job(mrn_batch*, void*) { return MRN_EUNSUPPORTED; }
-int mrn_batch_update(mrn_batch*, size_t, const mrn_view*, const mrn_view*) { return MRN_EUNSUPPORTED; }
-void mrn_batch_destroy(mrn_batch*) {}
-int mrn_autotune(const mrn_schema*, mrn_layout, mrn_layout, uint64_t, mrn_tune_result*) { return MRN_EUNSUPPORTED; }
 int mrn_server_create(const mrn_server_opts*, mrn_server**) { return MRN_EUNSUPPORTED; }
 int mrn_server_submit(mrn_server*, const mrn_view*, const mrn_view*, uint64_t*) { return MRN_EUNSUPPORTED; }
 int mrn_server_poll(mrn_server*, uint64_t, int*, int*) { return MRN_EUNSUPPORTED; }

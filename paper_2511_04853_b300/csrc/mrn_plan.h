@@ -82,3 +82,19 @@ struct GapPlan {
 };
 
 #define MRN_JAG_TILE 256  // parents per tile of the jagged scan
+
+// One job of a batched launch: a plain conversion (plan in jp.parent), a
+// jagged conversion, or the zero-fill of a destination's alignment holes,
+// and its slice of the batch's global tile sequence.
+enum MrnJobKind : uint32_t { JOB_CONVERT = 0, JOB_JAG_A2S = 1, JOB_JAG_S2A = 2, JOB_ZERO = 3 };
+struct BatchJob {
+  uint32_t kind;
+  uint32_t tile_records;        // JOB_CONVERT: records per tile (multiple of 256)
+  uint64_t tile_begin;          // first tile of this job in the batch
+  uint64_t ntiles;
+  uint64_t parent_groups;       // JOB_JAG_S2A: 32-record groups of parents
+  union {
+    JagPlan jp;                 // JOB_CONVERT uses jp.parent
+    GapPlan gp;                 // JOB_ZERO
+  };
+};

@@ -33,3 +33,113 @@ extern "C" int mrn_autotune_clear(void) {
   mrn::clear_tuned_shapes();
   return MRN_OK;
 }
+
+// ------------------------------------------------------------ autotuner
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+namespace mrn {
+namespace {
+
+// Average device time of `reps` launches of plan p with shape sh (ms).
+float time_shape(const ConvPlan& p, const LaunchShape& sh, cudaStream_t s, cudaEvent_t a, cudaEvent_t b,
+                 int reps) {
+  for (int i = 0; i < 2; ++i)
+    if (launch_convert(p, s, &sh)) return -1.f;
+  cudaEventRecord(a, s);
+  for (int i = 0; i < reps; ++i) launch_convert(p, s, &sh);
+  cudaEventRecord(b, s);
+  if (cudaEventSynchronize(b) != cudaSuccess) return -1.f;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms / reps;
+}
+
+}  // namespace
+}  // namespace mrn
+
+using namespace mrn;
+
+extern "C" int mrn_autotune(const mrn_schema* s, mrn_layout src_l, mrn_layout dst_l, uint64_t n_hint,
+                            mrn_tune_result* out) {
+  if (!s || !s->finalized || n_hint == 0) return MRN_EINVAL;
+  if (src_l.kind < MRN_AOS || src_l.kind > MRN_AOSOA || dst_l.kind < MRN_AOS || dst_l.kind > MRN_AOSOA ||
+      (src_l.kind == MRN_AOSOA && src_l.block < 1) || (dst_l.kind == MRN_AOSOA && dst_l.block < 1))
+    return MRN_EINVAL;
+  if (s->has_jagged) return MRN_EUNSUPPORTED;  // jagged tiles are fixed at 256 parents
+  if (src_l.kind == MRN_AOS && dst_l.kind == MRN_AOS) return MRN_EUNSUPPORTED;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MRN_ECUDA;
+  const uint64_t sb = base_bytes(s, src_l, n_hint, 0), db = base_bytes(s, dst_l, n_hint, 0);
+  char *a = nullptr, *b = nullptr;
+  if (cudaMalloc(&a, sb) != cudaSuccess) return MRN_ENOMEM;
+  if (cudaMalloc(&b, db) != cudaSuccess) {
+    cudaFree(a);
+    return MRN_ENOMEM;
+  }
+  cudaMemset(a, 0x5a, sb);
+  mrn_view vs, vd;
+  std::memset(&vs, 0, sizeof(vs));
+  vs.schema = s;
+  vs.layout = src_l;
+  vs.mem = MRN_MEM_DEVICE;
+  vs.device = dev;
+  vs.n_records = n_hint;
+  vs.base = a;
+  vd = vs;
+  vd.layout = dst_l;
+  vd.base = b;
+  ConvPlan p;
+  int rc = build_plan(vs, vd, &p);
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  mrn_tune_result best;
+  std::memset(&best, 0, sizeof(best));
+  if (!rc && (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+              cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    rc = MRN_ECUDA;
+  if (!rc) {
+    const double bytes = (double)sb + (double)db;
+    const int reps = 5;
+    const float t_def = time_shape(p, LaunchShape{}, st, e0, e1, reps);
+    best.default_gbps = t_def > 0 ? bytes / (t_def * 1e-3) / 1e9 : 0;
+    float best_t = 1e30f;
+    const uint32_t threads_c[] = {128, 256};
+    const uint32_t mult_c[] = {1, 2, 4, 8};
+    const uint32_t cps_c[] = {0, 2, 4, 6};
+    for (uint32_t th : threads_c)
+      for (uint32_t mu : mult_c)
+        for (uint32_t cps : cps_c) {
+          LaunchShape sh;
+          sh.threads = th;
+          sh.tile_records = th * mu;
+          sh.ctas_per_sm = cps;
+          const float t = time_shape(p, sh, st, e0, e1, reps);
+          if (t > 0 && t < best_t) {
+            best_t = t;
+            best.threads = th;
+            best.tile_records = th * mu;
+            best.ctas_per_sm = cps;
+          }
+        }
+    if (best_t < 1e29f) {
+      best.gbps = bytes / (best_t * 1e-3) / 1e9;
+      LaunchShape sh;
+      sh.threads = best.threads;
+      sh.tile_records = best.tile_records;
+      sh.ctas_per_sm = best.ctas_per_sm;
+      store_tuned_shape(p.tune_key, sh);
+    } else {
+      rc = MRN_ECUDA;
+    }
+  }
+  if (st) cudaStreamSynchronize(st);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  cudaFree(a);
+  cudaFree(b);
+  if (!rc && out) *out = best;
+  return rc;
+}

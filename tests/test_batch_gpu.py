@@ -1,0 +1,120 @@
+"""GPU parity of the batched form: many collections of mixed schemas, sizes
+and layout pairs in one persistent launch (with and without a CUDA graph)
+must each equal the oracle, and equal the one-launch-per-collection result;
+graph replays after the inputs change, job-table updates and the autotuner
+must keep the results exact."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+import paper_2511_04853_b300 as mrn
+from gpu_util import dev, dev_dest, garbage, host
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ["points", "cells", "tracks"]
+KINDS = [("aos", 0), ("soa", 0), ("aosoa", 32), ("aosoa", 128), ("aosoa", 5)]
+
+
+def make_jobs(seed, count, max_n=20000):
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for j in range(count):
+        name = NAMES[rng.integers(0, 3)]
+        n = int(round(10 ** rng.uniform(0, np.log10(max_n))))
+        desc = datagen.WORKLOAD_SCHEMAS[name]
+        s, o = mrn.Schema(desc), oracle.Schema(desc)
+        d = datagen.workload(name, n, seed * 1000 + j)
+        if name == "tracks":
+            o_aos = oracle.pack(o, d, "aos")
+            o_soa = oracle.convert(o, o_aos, "soa", m=d["m"])
+            if rng.integers(0, 2) == 0:
+                src = mrn.View(s, "aos", n, base=dev(o_aos.base), child_pool=dev(o_aos.pool), m=d["m"])
+                dst = dev_dest(s, "soa", n, d["m"])
+                want = o_soa.base
+            else:
+                src = mrn.View(s, "soa", n, base=dev(o_soa.base), m=d["m"])
+                dst = dev_dest(s, "aos", n, d["m"])
+                want = np.concatenate([o_aos.base[: n * 24], o_aos.pool[: d["m"] * 8]])
+        else:
+            sk, sb = KINDS[rng.integers(0, len(KINDS))]
+            dk, db = KINDS[rng.integers(0, len(KINDS))]
+            if (sk, sb) == (dk, db) or (sk == dk == "aos"):
+                sk, sb, dk, db = "aos", 0, "soa", 0
+            o_src = oracle.pack(o, d, sk, sb)
+            o_dst = oracle.convert(o, o_src, dk, db)
+            src = mrn.View(s, sk, n, block=sb, base=dev(o_src.base))
+            dst = dev_dest(s, dk, n, 0, db)
+            want = o_dst.base
+        jobs.append((src, dst, want, name))
+    return jobs
+
+
+def result(dst, want, name):
+    if name == "tracks" and dst.tensors[1] is not None:
+        n = dst.s.n_records
+        return np.concatenate([host(dst.tensors[0], n * 24), host(dst.tensors[1], dst.s.n_children * 8)])
+    return host(dst.tensors[0], want.size)
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_mixed_batch_matches_oracle(use_graph):
+    jobs = make_jobs(7, 60)
+    b = mrn.Batch([(s, d) for s, d, _, _ in jobs], use_graph=use_graph)
+    b.launch()
+    assert mrn.sync() == mrn.OK
+    for i, (s, d, want, name) in enumerate(jobs):
+        assert np.array_equal(result(d, want, name), want), "job %d (%s)" % (i, name)
+    # the per-collection baseline gives the same bytes
+    for _, d, _, _ in jobs:
+        d.tensors[0].fill_(0xA5)
+    b.launch_per_job()
+    assert mrn.sync() == mrn.OK
+    for i, (s, d, want, name) in enumerate(jobs):
+        assert np.array_equal(result(d, want, name), want), "per-job %d" % i
+
+
+def test_graph_replay_sees_new_inputs():
+    n = 30000
+    s, o = mrn.Schema(datagen.CELLS), oracle.Schema(datagen.CELLS)
+    src_t = garbage(n * 24)
+    dst = dev_dest(s, "aosoa", n, 0, 32)
+    b = mrn.Batch([(mrn.View(s, "aos", n, base=src_t), dst)], use_graph=True)
+    for seed in (1, 2, 3):
+        d = datagen.workload("cells", n, seed)
+        o_aos = oracle.pack(o, d, "aos")
+        src_t.copy_(dev(o_aos.base))
+        b.launch()
+        assert mrn.sync() == mrn.OK
+        want = oracle.convert(o, o_aos, "aosoa", 32).base
+        assert np.array_equal(host(dst.tensors[0], want.size), want)
+
+
+def test_update_repoints_a_job():
+    n = 5000
+    s, o = mrn.Schema(datagen.POINTS), oracle.Schema(datagen.POINTS)
+    d1, d2 = datagen.workload("points", n, 1), datagen.workload("points", n, 2)
+    a1, a2 = oracle.pack(o, d1, "aos"), oracle.pack(o, d2, "aos")
+    dst1, dst2 = dev_dest(s, "soa", n), dev_dest(s, "soa", n)
+    b = mrn.Batch([(mrn.View(s, "aos", n, base=dev(a1.base)), dst1)], use_graph=True)
+    b.update(0, mrn.View(s, "aos", n, base=dev(a2.base)), dst2)
+    b.launch()
+    assert mrn.sync() == mrn.OK
+    want = oracle.convert(o, a2, "soa").base
+    assert np.array_equal(host(dst2.tensors[0], want.size), want)
+
+
+def test_autotune_then_convert_still_exact():
+    s, o = mrn.Schema(datagen.CELLS), oracle.Schema(datagen.CELLS)
+    r = mrn.autotune(s, "aos", "soa", 1 << 20)
+    assert r["gbps"] > 0 and r["tile_records"] % 32 == 0 and r["threads"] in (128, 256)
+    n = 200000
+    d = datagen.workload("cells", n, 1)
+    o_aos = oracle.pack(o, d, "aos")
+    dst = dev_dest(s, "soa", n)
+    mrn.convert(mrn.View(s, "aos", n, base=dev(o_aos.base)), dst)
+    assert mrn.sync() == mrn.OK
+    want = oracle.convert(o, o_aos, "soa").base
+    assert np.array_equal(host(dst.tensors[0], want.size), want)
+    mrn.autotune_clear()

@@ -1,0 +1,130 @@
+"""GPU parity of transfer-and-convert between host and device views (the
+chunked copy/convert pipeline): every chunk size, direction and layout pair
+must give the oracle's bytes."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+import paper_2511_04853_b300 as mrn
+from gpu_util import dev, garbage, host, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def pinned(nbytes, fill=0xA5):
+    return torch().full((max(1, int(nbytes)),), fill, dtype=torch().uint8).pin_memory()
+
+
+def host_side(arr, pin=True):
+    a = np.ascontiguousarray(arr).view(np.uint8).reshape(-1)
+    if a.size == 0:
+        a = np.zeros(1, np.uint8)
+    t = torch().from_numpy(a.copy())
+    return t.pin_memory() if pin else t
+
+
+def cells(n, seed=1):
+    return mrn.Schema(datagen.CELLS), oracle.Schema(datagen.CELLS), datagen.workload("cells", n, seed)
+
+
+@pytest.mark.parametrize("chunk", [64 << 10, 1 << 20, 16 << 20])
+@pytest.mark.parametrize("n", [1, 200000, 70001])
+def test_h2d_aos_to_soa_chunk_sweep(chunk, n):
+    s, o, d = cells(n)
+    o_aos = oracle.pack(o, d, "aos")
+    o_soa = oracle.convert(o, o_aos, "soa")
+    dst = garbage(s.required_bytes("soa", n))
+    mrn.transfer_convert(mrn.View(s, "aos", n, base=host_side(o_aos.base), mem="pinned"),
+                         mrn.View(s, "soa", n, base=dst), chunk_bytes=chunk, n_slots=4)
+    assert mrn.sync() == mrn.OK
+    assert np.array_equal(host(dst, o_soa.base.size), o_soa.base)
+
+
+@pytest.mark.parametrize("pair", [("soa", 0, "aos", 0), ("aosoa", 32, "aos", 0), ("aos", 0, "aosoa", 32),
+                                  ("aos", 0, "soa", 0), ("soa", 0, "aosoa", 128)])
+@pytest.mark.parametrize("chunk", [256 << 10, 4 << 20])
+def test_d2h_layout_pairs(pair, chunk):
+    sk, sb, dk, db = pair
+    n = 100003
+    s, o, d = cells(n, seed=3)
+    o_src = oracle.pack(o, d, sk, sb)
+    o_dst = oracle.convert(o, o_src, dk, db)
+    hdst = pinned(o.base_bytes(dk, db, n))
+    mrn.transfer_convert(mrn.View(s, sk, n, block=sb, base=dev(o_src.base)),
+                         mrn.View(s, dk, n, block=db, base=hdst, mem="pinned"), chunk_bytes=chunk)
+    assert mrn.sync() == mrn.OK
+    assert np.array_equal(hdst.numpy()[: o_dst.base.size], o_dst.base)
+
+
+@pytest.mark.parametrize("pair", [("aosoa", 32, "soa", 0), ("soa", 0, "aosoa", 32), ("aosoa", 128, "aos", 0)])
+def test_h2d_layout_pairs(pair):
+    sk, sb, dk, db = pair
+    n = 50001
+    s, o, d = cells(n, seed=4)
+    o_src = oracle.pack(o, d, sk, sb)
+    o_dst = oracle.convert(o, o_src, dk, db)
+    dst = garbage(s.required_bytes(dk, n, 0, db))
+    mrn.transfer_convert(mrn.View(s, sk, n, block=sb, base=host_side(o_src.base), mem="pinned"),
+                         mrn.View(s, dk, n, block=db, base=dst), chunk_bytes=1 << 20)
+    assert mrn.sync() == mrn.OK
+    assert np.array_equal(host(dst, o_dst.base.size), o_dst.base)
+
+
+def test_points_gaps_and_pageable_memory():
+    """10,000 points to a single-block SoA whose columns have alignment
+    holes, from pageable host memory, and back into pageable memory."""
+    n = 10000
+    s, o = mrn.Schema(datagen.POINTS), oracle.Schema(datagen.POINTS)
+    d = datagen.workload("points", n, 0)
+    o_aos = oracle.pack(o, d, "aos")
+    o_soa = oracle.convert(o, o_aos, "soa")
+    dst = garbage(s.required_bytes("soa", n))
+    mrn.transfer_convert(mrn.View(s, "aos", n, base=host_side(o_aos.base, pin=False), mem="host"),
+                         mrn.View(s, "soa", n, base=dst), chunk_bytes=32 << 10)
+    assert mrn.sync() == mrn.OK
+    assert np.array_equal(host(dst, o_soa.base.size), o_soa.base)
+    back = np.full(o_soa.base.size, 0xA5, np.uint8)
+    mrn.transfer_convert(mrn.View(s, "aos", n, base=dev(o_aos.base)),
+                         mrn.View(s, "soa", n, base=back, mem="host"), chunk_bytes=64 << 10)
+    assert mrn.sync() == mrn.OK
+    assert np.array_equal(back, o_soa.base)
+
+
+def test_same_layout_is_a_copy():
+    n = 12345
+    s, o, d = cells(n)
+    o_aos = oracle.pack(o, d, "aos")
+    dst = garbage(n * 24)
+    mrn.transfer_convert(mrn.View(s, "aos", n, base=host_side(o_aos.base), mem="pinned"),
+                         mrn.View(s, "aos", n, base=dst))
+    assert mrn.sync() == mrn.OK
+    assert np.array_equal(host(dst, n * 24), o_aos.base)
+
+
+def test_jagged_both_directions():
+    n = 30000
+    s, o = mrn.Schema(datagen.TRACKS), oracle.Schema(datagen.TRACKS)
+    d = datagen.workload("tracks", n, 2)
+    o_aos = oracle.pack(o, d, "aos")
+    o_soa = oracle.convert(o, o_aos, "soa", m=d["m"])
+    dst = garbage(s.required_bytes("soa", n, d["m"]))
+    mrn.transfer_convert(mrn.View(s, "aos", n, base=host_side(o_aos.base), child_pool=host_side(o_aos.pool),
+                                  m=d["m"], mem="pinned"),
+                         mrn.View(s, "soa", n, base=dst, m=d["m"]))
+    assert mrn.sync() == mrn.OK
+    assert np.array_equal(host(dst, o_soa.base.size), o_soa.base)
+    hb, hp = pinned(n * 24), pinned(d["m"] * 8)
+    mrn.transfer_convert(mrn.View(s, "soa", n, base=dst, m=d["m"]),
+                         mrn.View(s, "aos", n, base=hb, child_pool=hp, m=d["m"], mem="pinned"))
+    assert mrn.sync() == mrn.OK
+    assert np.array_equal(hb.numpy()[: n * 24], o_aos.base[: n * 24])
+    assert np.array_equal(hp.numpy()[: d["m"] * 8], o_aos.pool[: d["m"] * 8])
+
+
+def test_host_to_host_rejected():
+    s = mrn.Schema(datagen.CELLS)
+    a = np.zeros(240, np.uint8)
+    st = mrn.lib().mrn_transfer_convert(mrn.View(s, "aos", 10, base=a, mem="host").ref,
+                                        mrn.View(s, "soa", 10, base=a, mem="host").ref, None, None)
+    assert st == mrn.EINVAL
