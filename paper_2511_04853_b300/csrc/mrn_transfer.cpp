@@ -38,6 +38,8 @@ uint64_t gcd64(uint64_t a, uint64_t b) {
 
 uint64_t lcm64(uint64_t a, uint64_t b) { return a / gcd64(a, b) * b; }
 
+}  // namespace
+
 // A device view with the same structure as `like`, its parts packed into
 // `stage` (each part 256-byte aligned).  Returns the bytes used.
 uint64_t staged_view(const mrn_view& like, char* stage, mrn_view* out, std::vector<void*>& cols,
@@ -79,6 +81,8 @@ uint64_t staged_view(const mrn_view& like, char* stage, mrn_view* out, std::vect
   }
   return pos;
 }
+
+namespace {
 
 int copy_parts(const std::vector<ViewPart>& from, const std::vector<ViewPart>& to, cudaMemcpyKind kind,
                cudaStream_t s) {

@@ -23,6 +23,10 @@ std::vector<ViewPart> view_parts(const mrn_view& v);
 // own.  SoA sub-views use per-column pointers stored in `cols`.  AoSoA
 // sub-views need r0 to be a multiple of B.
 mrn_view sub_view(const mrn_view& v, uint64_t r0, uint64_t cnt, std::vector<void*>& cols);
+// A device view shaped like `like` (same schema, layout, sizes) with its
+// parts packed at `stage` (stage == nullptr: size only).  Returns the bytes.
+uint64_t staged_view(const mrn_view& like, char* stage, mrn_view* out, std::vector<void*>& cols,
+                     std::vector<void*>& ccols);
 // Bytes per record of a layout (AoSoA: block bytes / B, rounded up).
 uint64_t record_bytes(const mrn_schema* s, const mrn_layout& l);
 
