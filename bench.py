@@ -1,0 +1,659 @@
+"""Benchmark of the layout-conversion hot path on one B300 (or N replicas).
+
+Step: one pass over a batch of R calorimeter-cell collections (200,000
+records of {f32 energy, time, eta, phi; u32 cell_id; u16 gain, quality},
+24-byte AoS records), each converted AoS -> SoA, SoA -> AoSoA(32) and
+AoSoA(32) -> AoS (three independent conversions per collection, each
+reading its own resident input), all 3R conversions in ONE persistent kernel
+launch replayed from a CUDA graph.  Inputs are resident in HBM; the batch
+(R * 6 buffers of 4.8 MB) is larger than the 126 MB L2, so every step
+streams from HBM.
+
+value         algorithmic bytes (read + write of every conversion) / step time
+e2e           the same bytes through the C ABI with pinned HOST buffers: per
+              collection host AoS -> device SoA (transfer-and-convert),
+              SoA -> AoSoA(32) on the device, device AoSoA(32) -> host AoS
+roofline      the persistent kernel against the measured HBM copy bandwidth
+cpu_baseline  the CPU oracle (plain C, one thread) on a bounded sample
+batched_vs_per_call  the same step with one launch per conversion
+served        Poisson arrivals of transfer-and-convert requests at fractions
+              of the measured saturation rate: p50/p99 latency, throughput
+
+--impl reference runs the CPU oracle as the reference arm on the same
+workload and metric.  Under torchrun (N > 1) every rank runs an independent
+replica (the path has no exchange step); value = all ranks' bytes / the
+slowest rank's time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_RECORDS = 200_000
+BATCH = 16
+BLOCK = 32
+FALLBACK_HBM_GBS = 6400.0
+METRIC = "layout-convert HBM GB/s"
+KERNEL_SOURCES = ["paper_2511_04853_b300/csrc/mrn_kernels.cu", "paper_2511_04853_b300/csrc/mrn_device.cuh",
+                  "paper_2511_04853_b300/csrc/mrn_plan.h"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--device-only", action="store_true",
+                    help="profiling runs: only the timed device step (no e2e, baselines or extras)")
+    ap.add_argument("--serve-rates", default="0.25,0.5,0.9,1.2",
+                    help="served arrival rates as fractions of the measured saturation rate")
+    return ap.parse_args()
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def bytes_per_collection(stride=24, n=N_RECORDS):
+    # three conversions, each reads and writes the collection once
+    return 3 * 2 * n * stride
+
+
+def workload_config(batch):
+    return {"workload": "calorimeter cells: %d collections x 200,000 records (24-byte AoS: f32 energy, "
+                        "time, eta, phi; u32 cell_id; u16 gain, quality); per collection AoS->SoA, "
+                        "SoA->AoSoA(32), AoSoA(32)->AoS" % batch,
+            "records_per_collection": N_RECORDS, "collections_per_step": batch,
+            "launch": "one persistent kernel per step (CUDA graph replay)",
+            "l2": "inputs larger than L2 (%d MB touched per step, L2 126 MB)"
+                  % (batch * bytes_per_collection() // 10**6),
+            "parallelism": "replicas"}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.lines = index, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                pw.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(pw) if pw else None}
+
+
+# --------------------------------------------------------------- reference
+
+def oracle_step_setup(n_records, seed=1):
+    import datagen
+    import oracle
+    o = oracle.Schema(datagen.CELLS)
+    d = datagen.workload("cells", n_records, seed)
+    aos = oracle.pack(o, d, "aos")
+    soa = oracle.convert(o, aos, "soa")
+    blk = oracle.convert(o, soa, "aosoa", BLOCK)
+    outs = [oracle.alloc(o, "soa", n_records), oracle.alloc(o, "aosoa", n_records, 0, BLOCK),
+            oracle.alloc(o, "aos", n_records)]
+
+    def step():
+        for src, dst in zip([aos, soa, blk], outs):
+            st, _ = oracle.convert_into(o, src, dst)
+            assert st == 0
+    return step
+
+
+def cpu_oracle_rate(seconds, n_records):
+    """The oracle (plain C, one thread) on the step's three conversions of
+    one collection of n_records, repeated for about `seconds`; GB/s."""
+    step = oracle_step_setup(n_records)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        step()
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return reps * bytes_per_collection(24, n_records) / el / 1e9, reps, el
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    # size each step so the whole --steps/--warmup run stays near a minute
+    probe, _, _ = cpu_oracle_rate(0.5, 20000)
+    per_step_s = 60.0 / max(1, args.steps + args.warmup)
+    n_rec = int(max(1000, min(N_RECORDS, per_step_s * probe * 1e9 / bytes_per_collection(24, 1))))
+    step = oracle_step_setup(n_rec)
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    val = args.steps * bytes_per_collection(24, n_rec) / el / 1e9
+    sample = "%d-record cells collection x 3 conversions per step" % n_rec
+    line = {"impl": "reference", "metric": METRIC, "value": round(val, 3), "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(el / args.steps * 1e3, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": workload_config(args.batch),
+            "cpu_baseline": {"value": round(val, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(val, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- mine
+
+def make_inputs(mrn, torch, s, batch):
+    """R collections resident on the device: AoS, SoA and AoSoA(32) inputs
+    and garbage-filled outputs.  Values come from the seeded generator; the
+    layouts are built with the library's own kernels."""
+    import datagen
+    import numpy as np
+    colls = []
+    for i in range(batch):
+        d = datagen.workload("cells", N_RECORDS, 1 + i)
+        soa = torch.zeros(s.required_bytes("soa", N_RECORDS), dtype=torch.uint8, device="cuda")
+        for c, v in enumerate(d["columns"]):
+            off = s.soa_region_offset(N_RECORDS, 0, c)
+            b = torch.from_numpy(np.ascontiguousarray(v).view(np.uint8)).cuda()
+            soa[off: off + b.numel()].copy_(b)
+        aos = torch.empty(s.required_bytes("aos", N_RECORDS), dtype=torch.uint8, device="cuda")
+        blk = torch.empty(s.required_bytes("aosoa", N_RECORDS, 0, BLOCK), dtype=torch.uint8, device="cuda")
+        mrn.convert(mrn.View(s, "soa", N_RECORDS, base=soa), mrn.View(s, "aos", N_RECORDS, base=aos))
+        mrn.convert(mrn.View(s, "soa", N_RECORDS, base=soa),
+                    mrn.View(s, "aosoa", N_RECORDS, block=BLOCK, base=blk))
+        outs = [torch.full_like(soa, 0xA5), torch.full_like(blk, 0xA5), torch.full_like(aos, 0xA5)]
+        colls.append({"aos": aos, "soa": soa, "blk": blk, "out": outs})
+    assert mrn.sync() == mrn.OK
+    return colls
+
+
+def pairs_for(mrn, s, colls):
+    n = N_RECORDS
+    out = []
+    for c in colls:
+        out.append((mrn.View(s, "aos", n, base=c["aos"]), mrn.View(s, "soa", n, base=c["out"][0])))
+        out.append((mrn.View(s, "soa", n, base=c["soa"]), mrn.View(s, "aosoa", n, block=BLOCK, base=c["out"][1])))
+        out.append((mrn.View(s, "aosoa", n, block=BLOCK, base=c["blk"]), mrn.View(s, "aos", n, base=c["out"][2])))
+    return out
+
+
+def check_outputs(torch, colls):
+    """Each output must equal the input that mirrors it (bit-exact): the
+    three conversions of a collection form a cycle."""
+    for c in colls:
+        assert torch.equal(c["out"][0], c["soa"]), "AoS->SoA output differs from the SoA input"
+        assert torch.equal(c["out"][1], c["blk"]), "SoA->AoSoA output differs from the AoSoA input"
+        assert torch.equal(c["out"][2], c["aos"]), "AoSoA->AoS output differs from the AoS input"
+
+
+def traffic_record():
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        j = json.load(f)
+    if j.get("kernel_source_hash") != kernel_hash():
+        return None
+    return j
+
+
+def run_mine(args, rank, world):
+    import torch
+    import torch.distributed as dist
+    import paper_2511_04853_b300 as mrn
+    import datagen
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    s = mrn.Schema(datagen.CELLS)
+    colls = make_inputs(mrn, torch, s, args.batch)
+    batch = mrn.Batch(pairs_for(mrn, s, colls), use_graph=True)
+    step_bytes = args.batch * bytes_per_collection()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # the measured path is checked before it is timed
+    batch.launch()
+    assert mrn.sync() == mrn.OK
+    check_outputs(torch, colls)
+
+    # ---- device step: one persistent launch (graph replay) per step
+    for _ in range(args.warmup):
+        batch.launch()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        batch.launch()
+        ev[k][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    ms_step = total_ms / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * step_bytes / (ms_step * 1e-3) / 1e9
+    assert mrn.sync() == mrn.OK
+    check_outputs(torch, colls)
+
+    if args.device_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
+                              "mode": "device-only (profiling)", "config": workload_config(args.batch)}),
+                  flush=True)
+        return
+
+    extra = {}
+    if rank == 0:
+        # ---- per-call baseline: the same 3R conversions, one launch each
+        for _ in range(3):
+            batch.launch_per_job()
+        torch.cuda.synchronize()
+        reps = max(3, min(50, args.steps // 10))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            batch.launch_per_job()
+        b.record(stream)
+        torch.cuda.synchronize()
+        per_call_ms = a.elapsed_time(b) / reps
+        assert mrn.sync() == mrn.OK
+        check_outputs(torch, colls)
+        extra["batched_vs_per_call"] = {"per_call_ms_per_step": round(per_call_ms, 4),
+                                        "batched_ms_per_step": round(ms_step, 4),
+                                        "speedup": round(per_call_ms / ms_step, 3),
+                                        "per_call_launches_per_step": 3 * args.batch}
+
+    # ---- end to end through pinned host buffers
+    e2e = run_e2e(mrn, torch, s, colls, args, world)
+    del batch
+    if rank != 0:
+        return
+    for c in colls:
+        c["out"] = None
+    peak, peak_src = peaks()
+    lm = statistics.mean(launch_ms)
+    achieved = step_bytes / (lm * 1e-3) / 1e9
+    tr = traffic_record()
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": tr["bytes_per_launch"] if tr else None,
+            "kernel": "k_batch (persistent; %d conversions per launch)" % (3 * args.batch),
+            "algorithmic_bytes_per_launch": step_bytes, "launch_ms_mean": round(lm, 5),
+            "launch_ms_median": round(statistics.median(launch_ms), 5),
+            "peak_source": ("of measured (MEASURED_PEAKS.json hbm_gbs, copy read+write)" if peak_src == "measured"
+                            else "of fallback 6.4 TB/s")}
+    del colls
+    torch.cuda.empty_cache()
+    extra.update(secondary(mrn, torch, stream, peak))
+    extra["served"] = run_served(mrn, torch, args)
+    cpu_val, cpu_reps, cpu_s = cpu_oracle_rate(10.0, N_RECORDS)
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic (seeded generator; distributions of the calorimeter-cell workload)",
+            "config": workload_config(args.batch),
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "roofline": roof,
+            "cpu_baseline": {"value": round(cpu_val, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": "3 conversions of one 200,000-record collection x %d (%.1f s)"
+                                       % (cpu_reps, cpu_s)},
+            "clocks": clocks}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def run_e2e(mrn, torch, s, colls, args, world):
+    """Host pinned AoS -> device SoA, SoA -> AoSoA(32), device AoSoA(32) ->
+    host pinned AoS for every collection of the batch, per step."""
+    n = N_RECORDS
+    h_in = [c["aos"].cpu().pin_memory() for c in colls]
+    h_out = [torch.empty_like(h).pin_memory() for h in h_in]
+    d_soa = [torch.empty_like(c["soa"]) for c in colls]
+    d_blk = [torch.empty_like(c["blk"]) for c in colls]
+    views = []
+    for i in range(len(colls)):
+        views.append((mrn.View(s, "aos", n, base=h_in[i], mem="pinned"), mrn.View(s, "soa", n, base=d_soa[i]),
+                      mrn.View(s, "aosoa", n, block=BLOCK, base=d_blk[i]),
+                      mrn.View(s, "aos", n, base=h_out[i], mem="pinned")))
+
+    def step():
+        for hin, soa, blk, hout in views:
+            mrn.transfer_convert(hin, soa, chunk_bytes=1 << 20, n_slots=4)
+            mrn.convert(soa, blk)
+            mrn.transfer_convert(blk, hout, chunk_bytes=1 << 20, n_slots=4)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    for i in range(len(colls)):
+        assert torch.equal(h_out[i], h_in[i]), "end-to-end round trip differs"
+    k = max(3, min(20, args.steps // 100))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k):
+        step()
+    torch.cuda.synchronize()
+    el = (time.perf_counter() - t0) / k
+    assert mrn.sync() == mrn.OK
+    step_bytes = len(colls) * bytes_per_collection()
+    return {"value": round(world * step_bytes / el / 1e9, 2), "unit": "GB/s",
+            "h2d_bytes_per_step": len(colls) * n * 24, "d2h_bytes_per_step": len(colls) * n * 24,
+            "ms_per_step": round(el * 1e3, 3), "steps": k,
+            "path": "mrn_transfer_convert (1 MiB chunks, 4 slots) + mrn_convert, pinned host buffers"}
+
+
+def secondary(mrn, torch, stream, peak):
+    """Single-collection launches at the workload sizes and scale-up
+    collections (2^26 records), L2 flushed before each launch, against the
+    HBM roofline; the host link bandwidth."""
+    import numpy as np
+    import datagen
+    out = {}
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def time_conv(src, dst, reps):
+        ts = []
+        for i in range(reps + 2):
+            flush.fill_(i & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mrn.convert(src, dst)
+            b.record(stream)
+            b.synchronize()
+            if i >= 2:
+                ts.append(a.elapsed_time(b))
+        return statistics.median(ts), sorted(ts)[:max(1, len(ts) // 5)]
+
+    def row(alg, med, fastest):
+        return {"us_median": round(med * 1e3, 2), "gbps": round(alg / (med * 1e-3) / 1e9, 1),
+                "frac_of_hbm": round(alg / (med * 1e-3) / 1e9 / peak, 3),
+                "gbps_mean_fastest_fifth": round(alg / (statistics.mean(fastest) * 1e-3) / 1e9, 1)}
+
+    rows = {}
+    for name, n, pairs in [("points", 10000, [("aos", 0, "soa", 0), ("soa", 0, "aos", 0)]),
+                           ("cells", 200000, [("aos", 0, "soa", 0), ("soa", 0, "aosoa", 32),
+                                              ("aosoa", 32, "aos", 0)]),
+                           ("cells", 1 << 26, [("aos", 0, "soa", 0), ("soa", 0, "aos", 0),
+                                               ("soa", 0, "aosoa", 32), ("aosoa", 32, "aos", 0)]),
+                           ("points", 1 << 26, [("aos", 0, "soa", 0), ("soa", 0, "aos", 0)])]:
+        s = mrn.Schema(datagen.WORKLOAD_SCHEMAS[name])
+        bufs = {}
+        for sk, sb, dk, db in pairs:
+            for k, bk in ((sk, sb), (dk, db)):
+                if (k, bk) not in bufs:
+                    bufs[(k, bk)] = torch.full((s.required_bytes(k, n, 0, bk),), 0x3C, dtype=torch.uint8,
+                                               device="cuda")
+        for sk, sb, dk, db in pairs:
+            src = mrn.View(s, sk, n, block=sb, base=bufs[(sk, sb)])
+            dst = mrn.View(s, dk, n, block=db, base=bufs[(dk, db)])
+            med, fastest = time_conv(src, dst, 10 if n > 1e6 else 30)
+            key = "%s_%d_%s%s_to_%s%s" % (name, n, sk, sb or "", dk, db or "")
+            rows[key] = row(2 * n * s.stride, med, fastest)
+        del bufs
+    # jagged tracks, AoS -> SoA and back (canonical child pool)
+    s = mrn.Schema(datagen.TRACKS)
+    for n in (100000, 1 << 22):
+        d = datagen.workload("tracks", n, 2)
+        m = d["m"]
+        recs = torch.zeros(n * 24, dtype=torch.uint8, device="cuda")
+        lens = torch.from_numpy(d["lengths"].astype(np.int32)).cuda()
+        begs = torch.cumsum(lens.to(torch.int64), 0) - lens.to(torch.int64)
+        rv = recs.view(n, 24)
+        rv[:, 12:16].copy_(lens.view(torch.uint8).view(n, 4))
+        rv[:, 16:24].copy_(begs.view(torch.uint8).view(n, 8))
+        pool = torch.full((max(1, m * 8),), 7, dtype=torch.uint8, device="cuda")
+        soa = torch.empty(s.required_bytes("soa", n, m), dtype=torch.uint8, device="cuda")
+        src = mrn.View(s, "aos", n, base=recs, child_pool=pool, m=m)
+        dst = mrn.View(s, "soa", n, base=soa, m=m)
+        alg = n * 24 + m * 8 + n * 12 + (n + 1) * 4 + m * 8
+        med, fastest = time_conv(src, dst, 10)
+        rows["tracks_%d_aos_to_soa" % n] = dict(row(alg, med, fastest), children=m)
+        back = mrn.View(s, "aos", n, base=recs, child_pool=pool, m=m)
+        med, fastest = time_conv(dst, back, 10)
+        rows["tracks_%d_soa_to_aos" % n] = row(alg, med, fastest)
+        assert mrn.sync() == mrn.OK
+        del recs, pool, soa
+    out["single_collection"] = rows
+    del flush
+    # host link: pinned 1 GiB copies, best of 5
+    h = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
+    dbuf = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    best_h2d = best_d2h = 1e9
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dbuf.copy_(h, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        best_h2d = min(best_h2d, a.elapsed_time(b))
+        a.record(stream)
+        h.copy_(dbuf, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        best_d2h = min(best_d2h, a.elapsed_time(b))
+    out["host_link_gbps"] = {"h2d": round((1 << 30) / (best_h2d * 1e-3) / 1e9, 1),
+                             "d2h": round((1 << 30) / (best_d2h * 1e-3) / 1e9, 1)}
+    del h, dbuf
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_served(mrn, torch, args):
+    """Poisson arrivals of transfer-and-convert requests: source sizes
+    log-uniform 10 KB - 256 MB, schemas points / cells / tracks, random
+    source and target layouts, host->device or device->host, 64 GB budget.
+    The saturation rate is measured first (a closed burst), then each
+    fraction of it is offered for up to 3 s / 1500 requests."""
+    import numpy as np
+    import datagen
+    rng = np.random.default_rng(4)
+    kinds = [("aos", 0), ("soa", 0), ("aosoa", 32), ("aosoa", 128)]
+    max_bytes = 256 << 20
+    pools = {}
+    for name in ("points", "cells"):
+        s = mrn.Schema(datagen.WORKLOAD_SCHEMAS[name])
+        nmax = max_bytes // s.stride
+        hb, db = {}, {}
+        for k, b in kinds:
+            nb = s.required_bytes(k, nmax, 0, b)
+            hb[(k, b)] = torch.full((nb,), 1, dtype=torch.uint8).pin_memory()
+            db[(k, b)] = torch.full((nb,), 2, dtype=torch.uint8, device="cuda")
+        pools[name] = (s, nmax, hb, db)
+    # tracks: canonical AoS parents + pool on host, per-column SoA on device
+    st = mrn.Schema(datagen.TRACKS)
+    nt = 4_000_000
+    dt = datagen.workload("tracks", nt, 9)
+    lens = dt["lengths"].astype(np.uint64)
+    csum = np.concatenate([[0], np.cumsum(lens)])
+    recs = np.zeros((nt, 24), np.uint8)
+    recs[:, 12:16] = lens.astype(np.uint32).view(np.uint8).reshape(nt, 4)
+    recs[:, 16:24] = csum[:-1].astype(np.uint64).view(np.uint8).reshape(nt, 8)
+    mt = int(csum[-1])
+    t_host = (torch.from_numpy(recs.reshape(-1)).pin_memory(), torch.zeros(mt * 8, dtype=torch.uint8).pin_memory())
+    t_cols = [torch.zeros(nt * 4, dtype=torch.uint8, device="cuda") for _ in range(3)]
+    t_offs = torch.from_numpy(csum.astype(np.uint32).view(np.uint8)).cuda()
+    t_kids = [torch.zeros(mt * 4, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    t_dev_dst = torch.empty(st.required_bytes("soa", nt, mt), dtype=torch.uint8, device="cuda")
+
+    def make_request():
+        name = ["points", "cells", "tracks"][rng.integers(0, 3)]
+        size = int(10 ** rng.uniform(np.log10(10e3), np.log10(max_bytes)))
+        h2d = rng.integers(0, 2) == 0
+        if name == "tracks":
+            n = max(1, min(nt - 1, size // 184))  # ~184 source bytes per parent at mean length 20
+            m = int(csum[n])
+            if h2d:
+                src = mrn.View(st, "aos", n, base=t_host[0], child_pool=t_host[1], m=m, mem="pinned")
+                dst = mrn.View(st, "soa", n, base=t_dev_dst, m=m)
+            else:
+                src = mrn.View(st, "soa", n, columns=t_cols, offsets=t_offs, child_columns=t_kids, m=m)
+                dst = mrn.View(st, "aos", n, base=t_host[0], child_pool=t_host[1], m=m, mem="pinned")
+            return src, dst, n * 24 + m * 8
+        s, nmax, hb, db = pools[name]
+        n = max(1, min(nmax, size // s.stride))
+        sk, sb = kinds[rng.integers(0, 4)]
+        dk, dbk = kinds[rng.integers(0, 4)]
+        if h2d:
+            src = mrn.View(s, sk, n, block=sb, base=hb[(sk, sb)], mem="pinned")
+            dst = mrn.View(s, dk, n, block=dbk, base=db[(dk, dbk)])
+        else:
+            src = mrn.View(s, sk, n, block=sb, base=db[(sk, sb)])
+            dst = mrn.View(s, dk, n, block=dbk, base=hb[(dk, dbk)], mem="pinned")
+        return src, dst, n * s.stride
+
+    budget = 64 << 30
+    out = {"budget_bytes": budget, "slots": 8, "chunk_bytes": 4 << 20,
+           "sizes": "log-uniform 10 KB - 256 MB of source", "schemas": "points, cells, tracks",
+           "directions": "host->device, device->host"}
+    # saturation: a closed burst of 400 requests
+    sv = mrn.Server(budget, max_slots=8, chunk_bytes=4 << 20)
+    reqs = [make_request() for _ in range(400)]
+    t0 = time.perf_counter()
+    tickets = [sv.submit(a, b)[1] for a, b, _ in reqs]
+    for t in tickets:
+        assert sv.wait(t, 600.0) == mrn.OK
+    el = time.perf_counter() - t0
+    sat = len(reqs) / el
+    total = sum(x for _, _, x in reqs)
+    out["saturation"] = {"req_per_s": round(sat, 1), "source_gbps": round(total / el / 1e9, 2)}
+    sv.close()
+    rates = []
+    for frac in [float(x) for x in args.serve_rates.split(",") if x]:
+        lam = frac * sat
+        sv = mrn.Server(budget, max_slots=8, chunk_bytes=4 << 20)
+        nreq = int(min(1500, max(50, lam * 3.0)))
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, nreq))
+        batch = [make_request() for _ in range(nreq)]
+        tickets, late = [], 0.0
+        t0 = time.perf_counter()
+        for (src, dst, _), ta in zip(batch, arrivals):
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            else:
+                late = max(late, now - ta)
+            rc, t = sv.submit(src, dst)
+            if rc == mrn.OK:
+                tickets.append(t)
+        for t in tickets:
+            assert sv.wait(t, 600.0) == mrn.OK
+        el = time.perf_counter() - t0
+        stt = sv.stats()
+        sv.close()
+        rates.append({"frac_of_saturation": frac, "offered_req_per_s": round(lam, 1), "requests": nreq,
+                      "p50_ms": round(stt["p50_ms"], 3), "p99_ms": round(stt["p99_ms"], 3),
+                      "max_ms": round(stt["max_ms"], 3),
+                      "throughput_source_gbps": round(stt["bytes_in"] / el / 1e9, 2),
+                      "completed": stt["completed"], "rejected": stt["rejected"],
+                      "peak_device_bytes": stt["peak_device_bytes"],
+                      "client_max_lateness_ms": round(late * 1e3, 3)})
+    out["rates"] = rates
+    del pools, t_host, t_cols, t_offs, t_kids, t_dev_dst
+    torch.cuda.empty_cache()
+    return out
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    run_mine(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
