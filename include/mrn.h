@@ -220,11 +220,13 @@ int mrn_sync_bits(void* stream, uint32_t* bits);
  * values an AoS -> SoA conversion writes).  Synchronous; *m receives it. */
 int mrn_jagged_count(const mrn_view* src, uint64_t* m, void* stream);
 
-/* Test and fault-injection settings of the jagged AoS -> SoA scan (host
- * side; they take effect for conversions planned afterwards):
+/* Test and fault-injection settings (host side; they take effect for
+ * conversions planned afterwards):
  *   key 1: index of a tile that never publishes its sum (-1: none), so that
  *          its successors' bounded waits expire and record MRN_ETIMEOUT;
- *   key 2: bound of each look-back wait in nanoseconds (default 2e9). */
+ *   key 2: bound of each look-back wait in nanoseconds (default 2e9);
+ *   key 3: 1 = single conversions use the direct kernel (vector loads and
+ *          stores per lane) even where the TMA-staged kernel applies. */
 int mrn_debug_set(int key, long long value);
 
 /* ------------------------------------------------------- transfer+convert */
@@ -276,17 +278,19 @@ void mrn_batch_destroy(mrn_batch* b);
 
 typedef struct mrn_tune_result {
   uint32_t threads;       /* threads per CTA                                  */
-  uint32_t ctas_per_sm;   /* resident CTAs per SM of the grid                 */
+  uint32_t ctas_per_sm;   /* resident CTAs per SM of the grid (0: occupancy)  */
   uint32_t tile_records;  /* records per tile                                 */
-  uint32_t reserved;
+  uint32_t staged;        /* 1: tiles staged through shared memory by TMA
+                             bulk copies; 0: direct vector loads and stores  */
   double gbps;            /* algorithmic GB/s of the winner                   */
   double default_gbps;    /* algorithmic GB/s of the default configuration    */
 } mrn_tune_result;
 
-/* Times candidate launch shapes (threads per CTA, CTAs per SM, records per
- * tile) for converting n_hint records of `s` from `src` to `dst` layouts on
- * scratch device buffers, and caches the fastest for this (schema hash,
- * layout pair).  Later conversions and batches use the cached shape.
+/* Times candidate launch shapes for converting n_hint records of `s` from
+ * `src` to `dst` layouts on scratch device buffers: the TMA-staged kernel
+ * (when buffers and tile fit) at two grid sizes, and the direct kernel over
+ * threads per CTA, CTAs per SM and records per tile.  Caches the fastest for
+ * this (schema hash, layout pair); later conversions and batches use it.
  * Synchronous.  `out` may be NULL. */
 int mrn_autotune(const mrn_schema* s, mrn_layout src, mrn_layout dst, uint64_t n_hint,
                  mrn_tune_result* out);

@@ -14,6 +14,8 @@ namespace mrn {
 // through mrn_debug_set.
 std::atomic<long long> g_skip_publish_tile{-1};
 std::atomic<unsigned long long> g_timeout_ns{2000000000ull};
+// When set, conversions use the direct kernel even when they could be staged.
+std::atomic<int> g_force_direct{0};
 
 namespace {
 
@@ -220,8 +222,74 @@ uint64_t tune_key(uint64_t hash, const mrn_layout& a, const mrn_layout& b) {
   return h;
 }
 
+namespace {
+
+uint64_t gcd_u64(uint64_t a, uint64_t b) {
+  while (b) {
+    const uint64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
+
+// Bytes of one tile of T records of a side in shared memory (and, for SoA /
+// AoSoA, each column's offset in the tile / start in a block).
+uint64_t tile_bytes(const mrn_schema* s, const SidePlan& sp, uint32_t T, uint32_t* off) {
+  if (sp.kind == K_AOS) return (uint64_t)T * s->stride;
+  if (sp.kind == K_AOSOA) {
+    if (off)
+      for (uint32_t c = 0; c < s->cols.size(); ++c) off[c] = (uint32_t)aosoa_col_start(s, sp.block, c);
+    return (uint64_t)(T / sp.block) * sp.block_bytes;
+  }
+  uint64_t pos = 0;
+  for (uint32_t c = 0; c < s->cols.size(); ++c) {
+    if (off) off[c] = (uint32_t)pos;
+    pos += (uint64_t)T * s->cols[c].size;
+  }
+  return pos;
+}
+
+bool side_stageable(const mrn_schema* s, const SidePlan& sp) {
+  if (sp.kind == K_AOS) return aligned16(sp.base);
+  if (sp.kind == K_AOSOA) return aligned16(sp.base) && sp.block_bytes % 16 == 0;
+  for (uint32_t c = 0; c < s->cols.size(); ++c)
+    if (!aligned16(sp.col[c])) return false;
+  return true;
+}
+
+// Chooses the shared-memory tile of a plan: the largest T, a multiple of 32
+// and of every AoSoA block size, whose source and destination tiles each fit
+// one stage buffer.  Leaves tg.tma = 0 when the plan cannot be staged (an
+// unaligned buffer or block, or a record too wide for a stage).
+void tile_geometry(const mrn_schema* s, ConvPlan* p) {
+  TileGeom& g = p->tg;
+  std::memset(&g, 0, sizeof(g));
+  if (!side_stageable(s, p->src) || !side_stageable(s, p->dst)) return;
+  uint64_t q = 32;
+  for (const SidePlan* sp : {&p->src, &p->dst})
+    if (sp->kind == K_AOSOA) q = q / gcd_u64(q, sp->block) * sp->block;
+  uint32_t T = 0;
+  for (uint64_t cand = q; cand <= 4096; cand += q) {
+    if (tile_bytes(s, p->src, (uint32_t)cand, nullptr) > MRN_STAGE_BYTES ||
+        tile_bytes(s, p->dst, (uint32_t)cand, nullptr) > MRN_STAGE_BYTES)
+      break;
+    T = (uint32_t)cand;
+  }
+  if (T == 0) return;
+  g.T = T;
+  g.src_bytes = (uint32_t)tile_bytes(s, p->src, T, g.src_off);
+  g.dst_bytes = (uint32_t)tile_bytes(s, p->dst, T, g.dst_off);
+  g.tma = 1;
+}
+
+}  // namespace
+
 int build_plan(const mrn_view& src, const mrn_view& dst, ConvPlan* p) {
   int rc = level_plan(src.schema, src, dst, false, src.n_records, p);
+  if (!rc) tile_geometry(src.schema, p);
   mrn_layout a = src.layout, b = dst.layout;
   if (a.kind != MRN_AOSOA) a.block = 0;
   if (b.kind != MRN_AOSOA) b.block = 0;
@@ -324,7 +392,8 @@ int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
   }
   ConvPlan p;
   if ((rc = build_plan(*src, *dst, &p))) return rc;
-  const LaunchShape sh = tuned_shape(p);
+  LaunchShape sh = tuned_shape(p);
+  if (g_force_direct.load()) sh.generic = 1;
   if ((rc = launch_convert(p, stream, &sh))) return rc;
   GapPlan g;
   gap_plan(s, *dst, &g);
@@ -377,6 +446,7 @@ int mrn_debug_set(int key, long long value) {
       if (value <= 0) return MRN_EINVAL;
       g_timeout_ns.store((unsigned long long)value);
       return MRN_OK;
+    case 3: g_force_direct.store(value ? 1 : 0); return MRN_OK;
     default: return MRN_EINVAL;
   }
 }

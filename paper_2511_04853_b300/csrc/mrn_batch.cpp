@@ -80,8 +80,14 @@ int plan_job(const mrn_view& src, const mrn_view& dst, std::vector<BatchJob>* ou
     if ((rc = build_plan(src, dst, &j.jp.parent))) return rc;
     j.kind = JOB_CONVERT;
     const LaunchShape sh = tuned_shape(j.jp.parent);
-    uint32_t tr = sh.tile_records ? sh.tile_records : 1024;
-    tr = std::max<uint32_t>(256, tr / 256 * 256);
+    uint32_t tr;
+    if (j.jp.parent.tg.tma && !sh.generic) {
+      tr = j.jp.parent.tg.T;  // batch tiles coincide with staged tiles
+    } else {
+      j.jp.parent.tg.tma = 0;
+      tr = sh.tile_records ? sh.tile_records : 1024;
+      tr = std::max<uint32_t>(256, tr / 256 * 256);
+    }
     j.tile_records = tr;
     const ConvPlan& p = j.jp.parent;
     const uint64_t nrec = p.dir == DIR_FM_AOS ? p.n : p.n_fm_pad;

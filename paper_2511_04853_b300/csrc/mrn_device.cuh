@@ -30,6 +30,13 @@ __device__ __forceinline__ uint32_t lowbits_mask(uint32_t size) {
   return size >= 4 ? 0xffffffffu : ((1u << (8 * size)) - 1u);
 }
 
+// A load through the read-only data path (global memory, G) or a plain
+// load (shared memory).
+template <bool G, class T>
+__device__ __forceinline__ T ldx(const T* p) {
+  if constexpr (G) return __ldg(p); else return *p;
+}
+
 // Address of element i of field-major column c.
 __device__ __forceinline__ char* fm_addr(const SidePlan& sp, int c, uint32_t size, uint64_t i) {
   char* col = sp.col[c];
@@ -45,12 +52,13 @@ __device__ __forceinline__ char* fm_addr(const SidePlan& sp, int c, uint32_t siz
   return col + blk * sp.block_bytes + slot * size;
 }
 
+template <bool G = true>
 __device__ __forceinline__ uint64_t ld_elem(const char* a, uint32_t size) {
   switch (size) {
-    case 1: return __ldg(reinterpret_cast<const unsigned char*>(a));
-    case 2: return __ldg(reinterpret_cast<const unsigned short*>(a));
-    case 4: return __ldg(reinterpret_cast<const unsigned int*>(a));
-    default: return __ldg(reinterpret_cast<const unsigned long long*>(a));
+    case 1: return ldx<G>(reinterpret_cast<const unsigned char*>(a));
+    case 2: return ldx<G>(reinterpret_cast<const unsigned short*>(a));
+    case 4: return ldx<G>(reinterpret_cast<const unsigned int*>(a));
+    default: return ldx<G>(reinterpret_cast<const unsigned long long*>(a));
   }
 }
 
@@ -65,52 +73,52 @@ __device__ __forceinline__ void st_elem(char* a, uint32_t size, uint64_t v) {
 
 // Loads nbytes (<= 64, a multiple of V) of a record window into w[0..15]
 // with V-byte accesses; w must be zero on entry for V < 4.
-template <int V>
+template <int V, bool G = true>
 __device__ __forceinline__ void load_words(const char* p, uint32_t nbytes, uint32_t (&w)[16]) {
   if constexpr (V == 16) {
 #pragma unroll
     for (int k = 0; k < 4; ++k)
       if (k * 16 < (int)nbytes) {
-        uint4 v = __ldg(reinterpret_cast<const uint4*>(p) + k);
+        uint4 v = ldx<G>(reinterpret_cast<const uint4*>(p) + k);
         w[4 * k] = v.x; w[4 * k + 1] = v.y; w[4 * k + 2] = v.z; w[4 * k + 3] = v.w;
       }
   } else if constexpr (V == 8) {
 #pragma unroll
     for (int k = 0; k < 8; ++k)
       if (k * 8 < (int)nbytes) {
-        uint2 v = __ldg(reinterpret_cast<const uint2*>(p) + k);
+        uint2 v = ldx<G>(reinterpret_cast<const uint2*>(p) + k);
         w[2 * k] = v.x; w[2 * k + 1] = v.y;
       }
   } else if constexpr (V == 4) {
 #pragma unroll
     for (int k = 0; k < 16; ++k)
-      if (k * 4 < (int)nbytes) w[k] = __ldg(reinterpret_cast<const unsigned int*>(p) + k);
+      if (k * 4 < (int)nbytes) w[k] = ldx<G>(reinterpret_cast<const unsigned int*>(p) + k);
   } else if constexpr (V == 2) {
 #pragma unroll
     for (int k = 0; k < 32; ++k)
       if (k * 2 < (int)nbytes)
-        w[k >> 1] |= (uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p) + k) << ((k & 1) * 16);
+        w[k >> 1] |= (uint32_t)ldx<G>(reinterpret_cast<const unsigned short*>(p) + k) << ((k & 1) * 16);
   } else {
 #pragma unroll
     for (int k = 0; k < 64; ++k)
       if (k < (int)nbytes)
-        w[k >> 2] |= (uint32_t)__ldg(reinterpret_cast<const unsigned char*>(p) + k) << ((k & 3) * 8);
+        w[k >> 2] |= (uint32_t)ldx<G>(reinterpret_cast<const unsigned char*>(p) + k) << ((k & 3) * 8);
   }
 }
 
 // V == 0: the access width is chosen at run time from `vec` (a uniform
 // branch per 64-byte window), for kernels that serve many plans at once.
-template <int V>
+template <int V, bool G = true>
 __device__ __forceinline__ void load_any(const char* p, uint32_t nbytes, uint32_t (&w)[16], uint32_t vec) {
   if constexpr (V != 0) {
-    load_words<V>(p, nbytes, w);
+    load_words<V, G>(p, nbytes, w);
   } else {
     switch (vec) {
-      case 16: load_words<16>(p, nbytes, w); break;
-      case 8: load_words<8>(p, nbytes, w); break;
-      case 4: load_words<4>(p, nbytes, w); break;
-      case 2: load_words<2>(p, nbytes, w); break;
-      default: load_words<1>(p, nbytes, w); break;
+      case 16: load_words<16, G>(p, nbytes, w); break;
+      case 8: load_words<8, G>(p, nbytes, w); break;
+      case 4: load_words<4, G>(p, nbytes, w); break;
+      case 2: load_words<2, G>(p, nbytes, w); break;
+      default: load_words<1, G>(p, nbytes, w); break;
     }
   }
 }
@@ -279,3 +287,175 @@ __device__ __forceinline__ unsigned long long global_ns() {
 #define MRN_TS_AGG (1ull << 62)
 #define MRN_TS_PREFIX (2ull << 62)
 #define MRN_TS_VALUE ((1ull << 62) - 1)
+
+// ------------------------------------------------------- TMA bulk copies
+// One-dimensional bulk copies between global and shared memory, completed
+// on an mbarrier (loads) or a bulk group (stores).  Global and shared
+// addresses are 16-byte aligned and sizes are multiples of 16.
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for phase `parity` of an mbarrier, bounded by ~2 s of wall clock
+// and an iteration count; false when the bound expired.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long deadline = global_ns() + 2000000000ull;
+  for (uint32_t i = 0; i < (1u << 24); ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63) == 63 && global_ns() > deadline) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src, uint32_t bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst_smem)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src_smem, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src_smem)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// Waits until at most N bulk store groups still read shared memory.
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+// Waits until every bulk store group has completed.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Orders this thread's generic-proxy shared-memory writes before later
+// async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// ------------------------------------------------ shared-memory tiles
+
+// Element r (tile-local) of field-major column c inside a tile.
+__device__ __forceinline__ char* tile_fm(const SidePlan& sp, const uint32_t* off, char* tile, int c,
+                                         uint32_t size, uint32_t r) {
+  if (sp.kind == K_SOA) return tile + off[c] + r * size;
+  uint32_t blk, slot;
+  if (sp.block_shift != MRN_NO_SHIFT) {
+    blk = r >> sp.block_shift;
+    slot = r & (sp.block - 1);
+  } else {
+    blk = r / sp.block;
+    slot = r - blk * sp.block;
+  }
+  return tile + (uint64_t)blk * sp.block_bytes + off[c] + slot * size;
+}
+
+// Tile transforms, one record per lane; every record of the tile exists.
+template <int V>
+__device__ __forceinline__ void tile_aos_to_fm(const ConvPlan& p, const char* stile, char* dtile, uint32_t r,
+                                               uint32_t* tw, int lane) {
+  const char* rec = stile + (uint64_t)r * p.stride;
+  uint32_t ci = 0;
+  const uint32_t naos = p.naos, stride = p.stride, aw = p.aos_words;
+  for (uint32_t win = 0; win < aw; win += MRN_WIN_WORDS) {
+    uint32_t w[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) w[k] = 0;
+    load_any<V, false>(rec + win * 4, min(64u, stride - win * 4), w, p.vec);
+    const uint32_t nw = min((uint32_t)MRN_WIN_WORDS, aw - win);
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (k < (int)nw) tw[k * MRN_TW_PITCH + lane] = w[k];
+    const uint32_t wend = (win + MRN_WIN_WORDS) * 4;
+    for (; ci < naos; ++ci) {
+      const ColPlan cp = p.aos_cols[ci];
+      if (cp.aos_off >= wend) break;
+      const uint32_t wi = cp.aos_off / 4 - win;
+      const uint32_t lo = tw[wi * MRN_TW_PITCH + lane];
+      char* d = tile_fm(p.dst, p.tg.dst_off, dtile, cp.fm, cp.size, r);
+      const uint32_t sh = (cp.aos_off & 3) * 8;
+      switch (cp.size) {
+        case 1: *reinterpret_cast<unsigned char*>(d) = (unsigned char)(lo >> sh); break;
+        case 2: *reinterpret_cast<unsigned short*>(d) = (unsigned short)(lo >> sh); break;
+        case 4: *reinterpret_cast<unsigned int*>(d) = lo; break;
+        default: *reinterpret_cast<uint2*>(d) = make_uint2(lo, tw[(wi + 1) * MRN_TW_PITCH + lane]); break;
+      }
+    }
+  }
+}
+
+template <int V>
+__device__ __forceinline__ void tile_fm_to_aos(const ConvPlan& p, const char* stile, char* dtile, uint32_t r,
+                                               uint32_t* tw, int lane) {
+  char* rec = dtile + (uint64_t)r * p.stride;
+  uint32_t ci = 0;
+  const uint32_t naos = p.naos, stride = p.stride, aw = p.aos_words;
+  for (uint32_t win = 0; win < aw; win += MRN_WIN_WORDS) {
+    const uint32_t nw = min((uint32_t)MRN_WIN_WORDS, aw - win);
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (k < (int)nw) tw[k * MRN_TW_PITCH + lane] = 0;
+    const uint32_t wend = (win + MRN_WIN_WORDS) * 4;
+    for (; ci < naos; ++ci) {
+      const ColPlan cp = p.aos_cols[ci];
+      if (cp.aos_off >= wend) break;
+      const uint32_t wi = cp.aos_off / 4 - win;
+      const uint64_t v = ld_elem<false>(tile_fm(p.src, p.tg.src_off, const_cast<char*>(stile), cp.fm, cp.size, r),
+                                        cp.size);
+      uint32_t* t = tw + wi * MRN_TW_PITCH + lane;
+      if (cp.size == 8) {
+        t[0] = (uint32_t)v;
+        t[MRN_TW_PITCH] = (uint32_t)(v >> 32);
+      } else if (cp.size == 4) {
+        t[0] = (uint32_t)v;
+      } else {
+        t[0] |= (uint32_t)v << ((cp.aos_off & 3) * 8);
+      }
+    }
+    uint32_t w[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) w[k] = k < (int)nw ? tw[k * MRN_TW_PITCH + lane] : 0u;
+    store_any<V>(rec + win * 4, min(64u, stride - win * 4), w, p.vec);
+  }
+}
+
+__device__ __forceinline__ void tile_fm_to_fm(const ConvPlan& p, const char* stile, char* dtile, uint32_t r) {
+  for (uint32_t c = 0; c < p.ncols; ++c) {
+    const uint32_t sz = p.fm_size[c];
+    const uint64_t v = ld_elem<false>(tile_fm(p.src, p.tg.src_off, const_cast<char*>(stile), c, sz, r), sz);
+    st_elem(tile_fm(p.dst, p.tg.dst_off, dtile, c, sz, r), sz, v);
+  }
+}

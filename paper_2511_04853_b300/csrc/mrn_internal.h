@@ -69,9 +69,10 @@ int validate_pair(const mrn_view* src, const mrn_view* dst, bool need_device, bo
 
 // ---- kernel launchers (mrn_kernels.cu); all asynchronous on `stream`
 struct LaunchShape {
-  uint32_t threads = 256;
+  uint32_t threads = 256;    // direct kernel: threads per CTA
   uint32_t ctas_per_sm = 0;  // 0: fill the SM (occupancy)
-  uint32_t tile_records = 0; // 0: default
+  uint32_t tile_records = 0; // direct kernel: records per tile (0: default)
+  uint32_t generic = 0;      // 1: direct kernel even when the plan can be staged
 };
 int launch_convert(const ConvPlan& p, void* stream, const LaunchShape* shape);
 int launch_zero_gaps(const GapPlan& g, void* stream);

@@ -52,6 +52,150 @@ __global__ void __launch_bounds__(256) k_convert(const __grid_constant__ ConvPla
     conv_range<V>(p, t * tile_records, (t + 1) * tile_records, tw, lane, warp, nwarps);
 }
 
+// ------------------------------------------------- TMA-staged conversion
+
+// Shared memory of the staged kernels: two source and two destination tile
+// buffers (double buffering), the lane-private word columns of 8 warps and
+// two mbarriers.
+constexpr uint32_t kStage = MRN_STAGE_BYTES;
+constexpr size_t kTmaSmem = 4 * (size_t)kStage + 8 * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t) + 64;
+
+struct TmaSmem {
+  char* src[2];
+  char* dst[2];
+  uint32_t* tw_all;
+  unsigned long long* bar;
+};
+
+__device__ __forceinline__ TmaSmem tma_smem(char* smem) {
+  TmaSmem m;
+  m.src[0] = smem;
+  m.src[1] = smem + kStage;
+  m.dst[0] = smem + 2 * kStage;
+  m.dst[1] = smem + 3 * kStage;
+  m.tw_all = reinterpret_cast<uint32_t*>(smem + 4 * kStage);
+  m.bar = reinterpret_cast<unsigned long long*>(smem + 4 * kStage + 8 * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t));
+  return m;
+}
+
+// Thread 0: bulk loads of source tile lt into a stage buffer.
+__device__ __forceinline__ void tma_load_tile(const ConvPlan& p, uint64_t lt, char* stage,
+                                              unsigned long long* bar) {
+  const TileGeom& g = p.tg;
+  const uint64_t t0 = lt * g.T;
+  const SidePlan& sp = p.src;
+  mbar_expect_tx(bar, g.src_bytes);
+  if (sp.kind == K_AOS) {
+    bulk_g2s(stage, sp.base + t0 * p.stride, g.src_bytes, bar);
+  } else if (sp.kind == K_AOSOA) {
+    bulk_g2s(stage, sp.base + (t0 / sp.block) * sp.block_bytes, g.src_bytes, bar);
+  } else {
+    for (uint32_t c = 0; c < p.ncols; ++c)
+      bulk_g2s(stage + g.src_off[c], sp.col[c] + t0 * p.fm_size[c], g.T * p.fm_size[c], bar);
+  }
+}
+
+// Thread 0: bulk stores of destination tile lt from a stage buffer.
+__device__ __forceinline__ void tma_store_tile(const ConvPlan& p, uint64_t lt, const char* tile) {
+  const TileGeom& g = p.tg;
+  const uint64_t t0 = lt * g.T;
+  const SidePlan& sp = p.dst;
+  if (sp.kind == K_AOS) {
+    bulk_s2g(sp.base + t0 * p.stride, tile, g.dst_bytes);
+  } else if (sp.kind == K_AOSOA) {
+    bulk_s2g(sp.base + (t0 / sp.block) * sp.block_bytes, tile, g.dst_bytes);
+  } else {
+    for (uint32_t c = 0; c < p.ncols; ++c)
+      bulk_s2g(sp.col[c] + t0 * p.fm_size[c], tile + g.dst_off[c], g.T * p.fm_size[c]);
+  }
+  bulk_commit();
+}
+
+// All threads: source tile -> destination tile in shared memory.
+__device__ __forceinline__ void tma_transform(const ConvPlan& p, const char* st, char* dt, uint32_t* tw,
+                                              int lane, int warp) {
+  const uint32_t T = p.tg.T;
+  for (uint32_t g = (uint32_t)warp * 32; g < T; g += 8 * 32) {
+    const uint32_t r = g + lane;
+    if (p.dir == DIR_AOS_FM)
+      tile_aos_to_fm<0>(p, st, dt, r, tw, lane);
+    else if (p.dir == DIR_FM_AOS)
+      tile_fm_to_aos<0>(p, st, dt, r, tw, lane);
+    else
+      tile_fm_to_fm(p, st, dt, r);
+  }
+}
+
+// A staged tile whose mbarrier did not complete within its bound: record
+// the error, let copies still in flight land (bounded) and stop the CTA.
+// pending / parity: bit s = stage s has loads in flight / their phase parity.
+__device__ __forceinline__ void tma_abort(TmaSmem& m, uint32_t pending, uint32_t parity) {
+  if (threadIdx.x == 0) {
+    flag_error(MRN_ETIMEOUT);
+    for (int s = 0; s < 2; ++s)
+      if ((pending >> s) & 1) mbar_wait_bounded(&m.bar[s], (parity >> s) & 1);
+    bulk_wait_all();
+  }
+}
+
+// One conversion with full tiles staged through shared memory by TMA bulk
+// copies (double-buffered: tile k+2's loads and tile k's stores are in
+// flight while tile k+1 is transformed); the partial last tile, if any,
+// takes the direct path.  CTA b takes tiles b, b + grid, ...
+__global__ void __launch_bounds__(256, 2) k_convert_tma(const __grid_constant__ ConvPlan p) {
+  extern __shared__ __align__(128) char staged_smem[];
+  __shared__ int s_abort;
+  TmaSmem m = tma_smem(staged_smem);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t* tw = m.tw_all + warp * MRN_TW_WORDS_PER_WARP;
+  const uint32_t T = p.tg.T;
+  const uint64_t nrec = p.dir == DIR_FM_AOS ? p.n : p.n_fm_pad;
+  const uint64_t ntiles = (nrec + T - 1) / T;
+  const uint64_t nfull = p.n / T;
+  const uint64_t G = gridDim.x, b = blockIdx.x;
+  uint32_t pending = 0, parity = 0;
+  if (tid == 0) {
+    mbar_init(&m.bar[0], 1);
+    mbar_init(&m.bar[1], 1);
+    fence_mbar_init();
+    s_abort = 0;
+    for (uint64_t k = 0; k < 2; ++k) {
+      const uint64_t t = b + k * G;
+      if (t < nfull) tma_load_tile(p, t, m.src[k], &m.bar[k]);
+    }
+  }
+  pending = (b < nfull ? 1u : 0u) | (b + G < nfull ? 2u : 0u);
+  __syncthreads();
+  for (uint64_t k = 0;; ++k) {
+    const uint64_t t = b + k * G;
+    if (t >= ntiles) break;
+    if (t < nfull) {
+      const int s = (int)(k & 1);
+      if (!mbar_wait_bounded(&m.bar[s], (parity >> s) & 1)) s_abort = 1;
+      if (tid == 0) bulk_wait_read<1>();  // destination buffer s is free
+      __syncthreads();
+      if (s_abort) {
+        tma_abort(m, pending, parity);
+        return;
+      }
+      pending &= ~(1u << s);
+      parity ^= 1u << s;
+      tma_transform(p, m.src[s], m.dst[s], tw, lane, warp);
+      fence_proxy_async_smem();
+      __syncthreads();
+      const uint64_t nt = t + 2 * G;
+      if (tid == 0) {
+        tma_store_tile(p, t, m.dst[s]);
+        if (nt < nfull) tma_load_tile(p, nt, m.src[s], &m.bar[s]);
+      }
+      if (nt < nfull) pending |= 1u << s;
+    } else {
+      conv_range<0>(p, t * T, (t + 1) * T, tw, lane, warp, 8);
+    }
+  }
+  if (tid == 0) bulk_wait_all();
+}
+
 __device__ __forceinline__ void zero_gap_item(const GapPlan& g, uint64_t t) {
   const uint64_t b = t / g.ngaps;
   const uint32_t k = (uint32_t)(t - b * g.ngaps);
@@ -277,51 +421,114 @@ __global__ void k_write_offset0(char* offs, uint32_t osz, unsigned long long v) 
 
 // ----------------------------------------------------------------- batched
 
-// Every job of a batch in one persistent launch: each CTA repeatedly takes
-// the next global tile (atomic counter, so tiles start in increasing order),
-// finds its job by binary search over the jobs' first tiles and runs that
-// tile.  Jagged AoS -> SoA jobs keep their look-back state in `states`,
-// indexed by global tile.
-__global__ void __launch_bounds__(256) k_batch(const BatchJob* __restrict__ jobs,
+// Every job of a batch in one persistent launch.  CTA b takes global tiles
+// b, b + grid, ... in increasing order (so a jagged tile's predecessors are
+// always taken earlier by running CTAs and its look-back terminates).  Full
+// tiles of jobs with a TMA tile geometry are staged through shared memory
+// as in k_convert_tma, with thread 0 deciding two tiles ahead; every other
+// tile (jagged, zero-fill, partial or unstaged conversions) runs directly.
+struct TileSlot {
+  unsigned int job;
+  unsigned int staged;
+  unsigned int stage;
+  unsigned int parity;
+  unsigned long long local;
+};
+
+__device__ __forceinline__ unsigned int find_job(const unsigned long long* first_tile, unsigned int njobs,
+                                                 unsigned long long t) {
+  unsigned int lo = 0, hi = njobs;
+  while (hi - lo > 1) {
+    const unsigned int mid = (lo + hi) >> 1;
+    if (__ldg(first_tile + mid) <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256, 2) k_batch(const BatchJob* __restrict__ jobs,
                                                const unsigned long long* __restrict__ first_tile,
                                                unsigned int njobs, unsigned long long total_tiles,
                                                unsigned int* counter, unsigned long long* states) {
-  __shared__ uint32_t tw_all[8 * MRN_TW_WORDS_PER_WARP];
+  extern __shared__ __align__(128) char staged_smem[];
   __shared__ JagShared sh;
-  __shared__ unsigned long long s_t;
-  __shared__ unsigned int s_j;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t* tw = tw_all + warp * MRN_TW_WORDS_PER_WARP;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const unsigned long long t = atomicAdd(counter, 1u);
-      s_t = t;
-      if (t < total_tiles) {
-        unsigned int lo = 0, hi = njobs;
-        while (hi - lo > 1) {
-          const unsigned int mid = (lo + hi) >> 1;
-          if (first_tile[mid] <= t) lo = mid; else hi = mid;
-        }
-        s_j = lo;
-      }
+  __shared__ TileSlot ring[4];
+  __shared__ int s_abort;
+  (void)counter;
+  TmaSmem m = tma_smem(staged_smem);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t* tw = m.tw_all + warp * MRN_TW_WORDS_PER_WARP;
+  const uint64_t G = gridDim.x, b = blockIdx.x;
+  uint32_t seq = 0;  // staged tiles issued (thread 0)
+  uint32_t pending = 0, parity = 0;
+
+  // Thread 0: decides tile k of this CTA and issues its loads if staged.
+  auto decide = [&](uint64_t k) {
+    const uint64_t t = b + k * G;
+    if (t >= total_tiles) return;
+    TileSlot ts;
+    ts.job = find_job(first_tile, njobs, t);
+    const BatchJob& J = jobs[ts.job];
+    ts.local = t - J.tile_begin;
+    const ConvPlan& P = J.jp.parent;
+    ts.staged = J.kind == JOB_CONVERT && P.tg.tma && (ts.local + 1) * P.tg.T <= P.n;
+    ts.stage = seq & 1;
+    ts.parity = (seq >> 1) & 1;
+    if (ts.staged) {
+      tma_load_tile(P, ts.local, m.src[ts.stage], &m.bar[ts.stage]);
+      pending |= 1u << ts.stage;
+      parity = (parity & ~(1u << ts.stage)) | (ts.parity << ts.stage);
+      ++seq;
     }
-    __syncthreads();
-    const unsigned long long t = s_t;
-    if (t >= total_tiles) break;
-    const BatchJob& J = jobs[s_j];
-    const unsigned long long local = t - J.tile_begin;
-    if (J.kind == JOB_CONVERT) {
-      conv_range<0>(J.jp.parent, local * J.tile_records, (local + 1) * J.tile_records, tw, lane, warp, 8);
-    } else if (J.kind == JOB_JAG_A2S) {
-      jagged_a2s_tile<0, 0>(J.jp, local, states + J.tile_begin, tw_all, sh);
-    } else if (J.kind == JOB_JAG_S2A) {
-      jagged_s2a_group<0, 0>(J.jp, local * 8 + warp, J.parent_groups, tw, lane);
-    } else {
-      const uint64_t k = local * 256 + threadIdx.x;
-      if (k < J.gp.nblocks * J.gp.ngaps) zero_gap_item(J.gp, k);
-    }
-    __syncthreads();
+    ring[k & 3] = ts;
+  };
+
+  if (tid == 0) {
+    mbar_init(&m.bar[0], 1);
+    mbar_init(&m.bar[1], 1);
+    fence_mbar_init();
+    s_abort = 0;
+    decide(0);
+    decide(1);
   }
+  __syncthreads();
+  for (uint64_t k = 0;; ++k) {
+    const uint64_t t = b + k * G;
+    if (t >= total_tiles) break;
+    const TileSlot ts = ring[k & 3];
+    const BatchJob& J = jobs[ts.job];
+    if (ts.staged) {
+      const ConvPlan& P = J.jp.parent;
+      const int s = (int)ts.stage;
+      if (!mbar_wait_bounded(&m.bar[s], ts.parity)) s_abort = 1;
+      if (tid == 0) bulk_wait_read<1>();
+      __syncthreads();
+      if (s_abort) {
+        tma_abort(m, pending, parity);
+        return;
+      }
+      pending &= ~(1u << s);
+      tma_transform(P, m.src[s], m.dst[s], tw, lane, warp);
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (tid == 0) tma_store_tile(P, ts.local, m.dst[s]);
+    } else {
+      const unsigned long long local = ts.local;
+      if (J.kind == JOB_CONVERT) {
+        const uint32_t tr = J.tile_records;
+        conv_range<0>(J.jp.parent, local * tr, (local + 1) * tr, tw, lane, warp, 8);
+      } else if (J.kind == JOB_JAG_A2S) {
+        jagged_a2s_tile<0, 0>(J.jp, local, states + J.tile_begin, m.tw_all, sh);
+      } else if (J.kind == JOB_JAG_S2A) {
+        jagged_s2a_group<0, 0>(J.jp, local * 8 + warp, J.parent_groups, tw, lane);
+      } else {
+        const uint64_t q = local * 256 + tid;
+        if (q < J.gp.nblocks * J.gp.ngaps) zero_gap_item(J.gp, q);
+      }
+      __syncthreads();
+    }
+    if (tid == 0) decide(k + 2);
+  }
+  if (tid == 0) bulk_wait_all();
 }
 
 // ================================================================== host
@@ -398,10 +605,33 @@ int read_and_clear_status(void* stream, uint32_t* bits) {
   return MRN_OK;
 }
 
+// Opts a kernel into the staged kernels' dynamic shared memory (once).
+void allow_tma_smem(const void* fn) {
+  static std::mutex mu;
+  static std::vector<const void*> done;
+  std::lock_guard<std::mutex> lk(mu);
+  for (const void* f : done)
+    if (f == fn) return;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
+  done.push_back(fn);
+}
+
 int launch_convert(const ConvPlan& p, void* stream, const LaunchShape* shape) {
   const uint64_t nrec = p.dir == DIR_FM_AOS ? p.n : p.n_fm_pad;
   if (nrec == 0) return MRN_OK;
   LaunchShape sh = shape ? *shape : LaunchShape{};
+  if (p.tg.tma && !sh.generic) {
+    const void* fn = reinterpret_cast<const void*>(&k_convert_tma);
+    allow_tma_smem(fn);
+    const int occ = occupancy(fn, 256, kTmaSmem);
+    const int per_sm = sh.ctas_per_sm ? std::min((int)sh.ctas_per_sm, occ) : occ;
+    const uint64_t ntiles = (nrec + p.tg.T - 1) / p.tg.T;
+    const unsigned grid = (unsigned)std::max<uint64_t>(
+        1, std::min<uint64_t>(ntiles, (uint64_t)device_sm_count() * (uint64_t)per_sm));
+    void* args[] = {const_cast<ConvPlan*>(&p)};
+    return cuda_status(cudaLaunchKernel(fn, dim3(grid), dim3(256), args, kTmaSmem,
+                                        static_cast<cudaStream_t>(stream)));
+  }
   if (sh.threads != 64 && sh.threads != 128 && sh.threads != 256) sh.threads = 256;
   if (sh.tile_records == 0 || sh.tile_records % 32) sh.tile_records = sh.threads * 2;
   void* fn = conv_kernel(p.dir == DIR_FM_FM ? 1 : p.vec);
@@ -521,7 +751,11 @@ int launch_jagged_count(const ConvPlan& parent, uint64_t* dev_total, void* strea
   return cuda_status(cudaGetLastError());
 }
 
-int batch_occupancy() { return occupancy(reinterpret_cast<void*>(&k_batch), 256, 0); }
+int batch_occupancy() {
+  const void* fn = reinterpret_cast<const void*>(&k_batch);
+  allow_tma_smem(fn);
+  return occupancy(fn, 256, kTmaSmem);
+}
 
 int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, unsigned int njobs,
                  unsigned long long total_tiles, unsigned int* counter, unsigned long long* states,
@@ -531,8 +765,8 @@ int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, uns
   const int per_sm = ctas_per_sm ? std::min((int)ctas_per_sm, occ) : occ;
   const uint64_t cap = (uint64_t)device_sm_count() * (uint64_t)per_sm;
   const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(cap, total_tiles));
-  k_batch<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(jobs, first_tile, njobs, total_tiles,
-                                                                 counter, states);
+  k_batch<<<grid, 256, kTmaSmem, static_cast<cudaStream_t>(stream)>>>(jobs, first_tile, njobs, total_tiles,
+                                                                        counter, states);
   return cuda_status(cudaGetLastError());
 }
 

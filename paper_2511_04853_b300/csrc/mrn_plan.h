@@ -33,6 +33,20 @@ struct ColPlan {
 #define FM_JLEN (-1)    // the jagged member's uint32 length
 #define FM_JBEGIN (-2)  // the jagged member's uint64 begin
 
+// Shared-memory tile geometry of a conversion that is staged with TMA bulk
+// copies: tiles of T records; a side's tile is one contiguous range (AoS:
+// T*stride bytes; AoSoA: T/B whole blocks) or, for SoA, one range per column
+// packed in column order (column c at off[c] inside the tile).
+#define MRN_STAGE_BYTES 16384u
+struct TileGeom {
+  uint32_t tma;        // 1: full tiles go through the TMA pipeline
+  uint32_t T;          // records per tile (multiple of 32 and of each AoSoA B)
+  uint32_t src_bytes;  // bytes of a source tile
+  uint32_t dst_bytes;  // bytes of a destination tile
+  uint32_t src_off[MRN_MAX_COLS];  // SoA: column offset in the tile; AoSoA: column start in a block
+  uint32_t dst_off[MRN_MAX_COLS];
+};
+
 struct ConvPlan {
   uint64_t n;          // records
   uint64_t n_fm_pad;   // records written on the destination (AoSoA: N rounded up to B)
@@ -46,6 +60,7 @@ struct ConvPlan {
   ColPlan aos_cols[MRN_MAX_COLS + 2];
   uint8_t fm_size[MRN_MAX_COLS];
   SidePlan src, dst;
+  TileGeom tg;
 };
 
 // Jagged AoS <-> SoA conversion: the parents' plan (data columns plus the

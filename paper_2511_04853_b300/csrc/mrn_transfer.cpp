@@ -235,6 +235,24 @@ uint64_t TransferEngine::staging_bytes(const mrn_view& src, const mrn_view& dst,
   return slot * (uint64_t)std::max(1, std::min(16, n_slots ? n_slots : 4));
 }
 
+namespace {
+// Zeroes the alignment holes of a host single-block SoA destination (the
+// bytes between and after its regions), on the calling thread.
+void zero_host_soa_gaps(const mrn_view& dst) {
+  if (dst.layout.kind != MRN_SOA || dst.columns || !dst.base) return;
+  if (dst.schema->has_jagged && (dst.offsets || dst.child_columns)) return;
+  char* base = static_cast<char*>(dst.base);
+  uint64_t prev = 0;
+  for (const auto& p : view_parts(dst)) {
+    const uint64_t st = p.ptr - base;
+    if (st > prev) std::memset(base + prev, 0, st - prev);
+    prev = st + p.bytes;
+  }
+  const uint64_t total = soa_total_bytes(dst.schema, dst.n_records, dst.n_children);
+  if (total > prev) std::memset(base + prev, 0, total - prev);
+}
+}  // namespace
+
 int TransferEngine::run(const mrn_view& src, const mrn_view& dst, uint64_t chunk_bytes, int n_slots,
                         cudaStream_t user, char* arena, uint64_t arena_bytes) {
   int rc = init();
@@ -246,9 +264,14 @@ int TransferEngine::run(const mrn_view& src, const mrn_view& dst, uint64_t chunk
   cudaStreamWaitEvent(s_conv_, ev_start_, 0);
   const bool h2d = is_host(src);
   const cudaMemcpyKind kind = h2d ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+  // Every destination byte that no property writes is zero: the holes of a
+  // single-block SoA destination are cleared here (host) or after the
+  // copies (device).
+  if (!h2d) zero_host_soa_gaps(dst);
   if (same_layout(src, dst)) {
-    // Equal layouts: the storage is copied verbatim, part by part.
+    // Equal layouts: the storage is copied part by part.
     rc = copy_parts(view_parts(src), view_parts(dst), kind, s_copy_);
+    if (!rc && h2d) rc = zero_dst_gaps(dst, s_copy_);
   } else {
     const uint64_t need = staging_bytes(src, dst, chunk_bytes, n_slots);
     char* stage = arena;
@@ -300,19 +323,6 @@ int TransferEngine::run_chunked(const mrn_view& src, const mrn_view& dst, uint64
   chunk_geometry(src, dst, chunk_bytes, &R, &slot_bytes);
   const uint64_t n = src.n_records;
   int rc;
-  // Host single-block SoA destination: its alignment holes are zeroed here.
-  if (!h2d && dst.layout.kind == MRN_SOA && !dst.columns && dst.base) {
-    auto parts = view_parts(dst);
-    uint64_t prev = 0;
-    char* base = static_cast<char*>(dst.base);
-    for (const auto& p : parts) {
-      const uint64_t st = p.ptr - base;
-      if (st > prev) std::memset(base + prev, 0, st - prev);
-      prev = st + p.bytes;
-    }
-    const uint64_t total = soa_total_bytes(dst.schema, dst.n_records, dst.n_children);
-    if (total > prev) std::memset(base + prev, 0, total - prev);
-  }
   std::vector<void*> hc, dc, sc, sc2;
   for (uint64_t k = 0, r0 = 0; r0 < n; ++k, r0 += R) {
     const uint64_t cnt = std::min(R, n - r0);

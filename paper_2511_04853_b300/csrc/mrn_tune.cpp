@@ -38,6 +38,7 @@ extern "C" int mrn_autotune_clear(void) {
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <vector>
 
 namespace mrn {
 namespace {
@@ -105,31 +106,38 @@ extern "C" int mrn_autotune(const mrn_schema* s, mrn_layout src_l, mrn_layout ds
     const float t_def = time_shape(p, LaunchShape{}, st, e0, e1, reps);
     best.default_gbps = t_def > 0 ? bytes / (t_def * 1e-3) / 1e9 : 0;
     float best_t = 1e30f;
-    const uint32_t threads_c[] = {128, 256};
-    const uint32_t mult_c[] = {1, 2, 4, 8};
-    const uint32_t cps_c[] = {0, 2, 4, 6};
-    for (uint32_t th : threads_c)
-      for (uint32_t mu : mult_c)
-        for (uint32_t cps : cps_c) {
+    std::vector<LaunchShape> cands;
+    if (p.tg.tma)
+      for (uint32_t cps : {0u, 1u}) {
+        LaunchShape sh;
+        sh.ctas_per_sm = cps;
+        cands.push_back(sh);
+      }
+    for (uint32_t th : {128u, 256u})
+      for (uint32_t mu : {1u, 2u, 4u, 8u})
+        for (uint32_t cps : {0u, 2u, 4u, 6u}) {
           LaunchShape sh;
+          sh.generic = 1;
           sh.threads = th;
           sh.tile_records = th * mu;
           sh.ctas_per_sm = cps;
-          const float t = time_shape(p, sh, st, e0, e1, reps);
-          if (t > 0 && t < best_t) {
-            best_t = t;
-            best.threads = th;
-            best.tile_records = th * mu;
-            best.ctas_per_sm = cps;
-          }
+          cands.push_back(sh);
         }
+    LaunchShape win;
+    for (const LaunchShape& sh : cands) {
+      const float t = time_shape(p, sh, st, e0, e1, reps);
+      if (t > 0 && t < best_t) {
+        best_t = t;
+        win = sh;
+      }
+    }
+    best.threads = win.generic ? win.threads : 256;
+    best.tile_records = win.generic ? win.tile_records : p.tg.T;
+    best.ctas_per_sm = win.ctas_per_sm;
+    best.staged = win.generic ? 0 : 1;
     if (best_t < 1e29f) {
       best.gbps = bytes / (best_t * 1e-3) / 1e9;
-      LaunchShape sh;
-      sh.threads = best.threads;
-      sh.tile_records = best.tile_records;
-      sh.ctas_per_sm = best.ctas_per_sm;
-      store_tuned_shape(p.tune_key, sh);
+      store_tuned_shape(p.tune_key, win);
     } else {
       rc = MRN_ECUDA;
     }

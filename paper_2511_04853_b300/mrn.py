@@ -56,7 +56,7 @@ class Job(ctypes.Structure):
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("threads", u32), ("ctas_per_sm", u32), ("tile_records", u32),
-                ("reserved", u32), ("gbps", ctypes.c_double),
+                ("staged", u32), ("gbps", ctypes.c_double),
                 ("default_gbps", ctypes.c_double)]
 
 
@@ -362,7 +362,7 @@ def autotune(schema, src_kind, dst_kind, n_hint, src_block=0, dst_block=0):
                              Layout(KIND.get(dst_kind, dst_kind), dst_block), n_hint,
                              ctypes.byref(r)), "mrn_autotune")
     return {"threads": r.threads, "ctas_per_sm": r.ctas_per_sm, "tile_records": r.tile_records,
-            "gbps": r.gbps, "default_gbps": r.default_gbps}
+            "staged": bool(r.staged), "gbps": r.gbps, "default_gbps": r.default_gbps}
 
 
 def autotune_clear():

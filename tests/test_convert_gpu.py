@@ -138,3 +138,29 @@ def test_misaligned_column_rejected():
     cols = [buf.data_ptr() + 1] * s.ncols
     dst = mrn.View(s, "soa", 10, columns=cols)
     assert mrn.convert_status(src, dst) == mrn.EALIGN
+
+
+@pytest.fixture
+def direct_path():
+    mrn.debug_set(3, 1)
+    yield
+    mrn.debug_set(3, 0)
+
+
+@pytest.mark.parametrize("name", ["points", "cells", "sensor", "wide"])
+@pytest.mark.parametrize("src,dst", [(("aos", 0), ("soa", 0)), (("soa", 0), ("aos", 0)),
+                                     (("aos", 0), ("aosoa", 32)), (("aosoa", 128), ("soa", 0))],
+                         ids=lambda k: "%s%d" % k)
+def test_direct_path_parity(direct_path, name, src, dst):
+    """The direct kernel (no TMA staging) gives the same bytes."""
+    check_pair(name, 5000, src[0], src[1], dst[0], dst[1])
+
+
+@pytest.mark.parametrize("n", [683, 2048, 100000])
+def test_staged_tiles_and_tail(n):
+    """Sizes around whole staged tiles: full tiles go through shared memory,
+    the remainder through the direct path."""
+    for (sk, sb), (dk, db) in [(("aos", 0), ("soa", 0)), (("soa", 0), ("aosoa", 128)),
+                               (("aosoa", 32), ("aos", 0))]:
+        check_pair("cells", n, sk, sb, dk, db, seed=7)
+        check_pair("points", n, sk, sb, dk, db, seed=7)
