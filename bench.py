@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--device-only", action="store_true",
                     help="profiling runs: only the timed device step (no e2e, baselines or extras)")
+    ap.add_argument("--case", default=None,
+                    help="profiling runs: repeat one conversion, e.g. cells:aos:soa:16777216 "
+                         "(schema:src[/B]:dst[/B]:records)")
     ap.add_argument("--serve-rates", default="0.25,0.5,0.9,1.2",
                     help="served arrival rates as fractions of the measured saturation rate")
     return ap.parse_args()
@@ -637,8 +640,42 @@ def run_served(mrn, torch, args):
     return out
 
 
+def run_case(args):
+    """Repeats one conversion (for profilers): schema:src:dst:records, a
+    layout written as aosoa/32 for blocks."""
+    import torch
+    import paper_2511_04853_b300 as mrn
+    import datagen
+    name, sk, dk, n = args.case.split(":")
+    n = int(n)
+
+    def lay(x):
+        k, _, b = x.partition("/")
+        return k, int(b or 0)
+    (sk, sb), (dk, db) = lay(sk), lay(dk)
+    s = mrn.Schema(datagen.WORKLOAD_SCHEMAS[name])
+    a = torch.full((s.required_bytes(sk, n, 0, sb),), 0x3C, dtype=torch.uint8, device="cuda")
+    b = torch.empty(s.required_bytes(dk, n, 0, db), dtype=torch.uint8, device="cuda")
+    src, dst = mrn.View(s, sk, n, block=sb, base=a), mrn.View(s, dk, n, block=db, base=b)
+    for _ in range(args.warmup):
+        mrn.convert(src, dst)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        mrn.convert(src, dst)
+    e1.record()
+    torch.cuda.synchronize()
+    assert mrn.sync() == mrn.OK
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"case": args.case, "ms": round(ms, 5),
+                      "gbps": round(2 * n * s.stride / (ms * 1e-3) / 1e9, 1)}), flush=True)
+
+
 def main():
     args = parse()
+    if args.case:
+        run_case(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
