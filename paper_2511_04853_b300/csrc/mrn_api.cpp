@@ -252,9 +252,21 @@ uint64_t tile_bytes(const mrn_schema* s, const SidePlan& sp, uint32_t T, uint32_
   return pos;
 }
 
-bool side_stageable(const mrn_schema* s, const SidePlan& sp) {
+// An AoSoA block without alignment holes or tail padding: a staged tile then
+// covers every byte of its blocks with column elements.
+bool aosoa_hole_free(const mrn_schema* s, uint32_t B) {
+  uint64_t pos = 0;
+  for (uint32_t c = 0; c < s->cols.size(); ++c) {
+    if (aosoa_col_start(s, B, c) != pos) return false;
+    pos += (uint64_t)B * s->cols[c].size;
+  }
+  return pos == aosoa_block_bytes(s, B);
+}
+
+bool side_stageable(const mrn_schema* s, const SidePlan& sp, bool is_dst) {
   if (sp.kind == K_AOS) return aligned16(sp.base);
-  if (sp.kind == K_AOSOA) return aligned16(sp.base) && sp.block_bytes % 16 == 0;
+  if (sp.kind == K_AOSOA)
+    return aligned16(sp.base) && sp.block_bytes % 16 == 0 && (!is_dst || aosoa_hole_free(s, sp.block));
   for (uint32_t c = 0; c < s->cols.size(); ++c)
     if (!aligned16(sp.col[c])) return false;
   return true;
@@ -267,7 +279,8 @@ bool side_stageable(const mrn_schema* s, const SidePlan& sp) {
 void tile_geometry(const mrn_schema* s, ConvPlan* p) {
   TileGeom& g = p->tg;
   std::memset(&g, 0, sizeof(g));
-  if (!side_stageable(s, p->src) || !side_stageable(s, p->dst)) return;
+  if (!side_stageable(s, p->src, false) || !side_stageable(s, p->dst, true)) return;
+  if (s->stride >= (1u << 24)) return;
   uint64_t q = 32;
   for (const SidePlan* sp : {&p->src, &p->dst})
     if (sp->kind == K_AOSOA) q = q / gcd_u64(q, sp->block) * sp->block;
@@ -282,6 +295,14 @@ void tile_geometry(const mrn_schema* s, ConvPlan* p) {
   g.T = T;
   g.src_bytes = (uint32_t)tile_bytes(s, p->src, T, g.src_off);
   g.dst_bytes = (uint32_t)tile_bytes(s, p->dst, T, g.dst_off);
+  uint32_t used = 0;
+  for (uint32_t c = 0; c < s->cols.size(); ++c) {
+    const uint32_t sz = s->cols[c].size;
+    const uint32_t lsz = sz == 1 ? 0 : sz == 2 ? 1 : sz == 4 ? 2 : 3;
+    g.col[c] = s->cols[c].aos_off | (lsz << 24);
+    used += sz;
+  }
+  g.pad = used != s->stride;
   g.tma = 1;
 }
 

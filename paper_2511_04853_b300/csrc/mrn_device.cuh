@@ -459,3 +459,62 @@ __device__ __forceinline__ void tile_fm_to_fm(const ConvPlan& p, const char* sti
     st_elem(tile_fm(p.dst, p.tg.dst_off, dtile, c, sz, r), sz, v);
   }
 }
+
+// Lean tile transform: per lane one record of the tile, per column one
+// shared-memory load and one store addressed from a compact descriptor
+// (uint4 {AoS offset | log2(size) << 24, source column offset, destination
+// column offset, 0}) kept in shared memory; source and destination kinds are
+// template parameters, so the column loop carries no layout branches.
+template <int K>
+struct TileSide {
+  char* base;    // AoS: the record; SoA: the tile; AoSoA: the record's block
+  uint32_t idx;  // SoA: record in tile; AoSoA: slot in block
+  __device__ __forceinline__ TileSide(char* tile, const SidePlan& sp, uint32_t stride, uint32_t r) {
+    if constexpr (K == K_AOS) {
+      base = tile + r * stride;
+      idx = 0;
+    } else if constexpr (K == K_SOA) {
+      base = tile;
+      idx = r;
+    } else {
+      const uint32_t blk = sp.block_shift != MRN_NO_SHIFT ? r >> sp.block_shift : r / sp.block;
+      idx = r - blk * sp.block;
+      base = tile + (uint64_t)blk * sp.block_bytes;
+    }
+  }
+  __device__ __forceinline__ char* at(uint32_t aos_off, uint32_t fm_off, uint32_t lsz) const {
+    if constexpr (K == K_AOS)
+      return base + aos_off;
+    else
+      return base + fm_off + (idx << lsz);
+  }
+};
+
+template <int SK, int DK>
+__device__ __forceinline__ void tile_convert(const ConvPlan& p, const uint4* sdesc, const char* st, char* dt,
+                                             uint32_t r) {
+  const TileSide<SK> S(const_cast<char*>(st), p.src, p.stride, r);
+  const TileSide<DK> D(dt, p.dst, p.stride, r);
+  if constexpr (DK == K_AOS) {
+    if (p.tg.pad) {  // padding bytes of the record are zero
+      uint32_t z[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) z[k] = 0;
+      for (uint32_t w = 0; w < p.stride; w += 64) store_any<0>(D.base + w, min(64u, p.stride - w), z, p.vec);
+    }
+  }
+  const uint32_t nc = p.ncols;
+#pragma unroll 4
+  for (uint32_t c = 0; c < nc; ++c) {
+    const uint4 d = sdesc[c];
+    const uint32_t aoff = d.x & 0xffffffu, lsz = d.x >> 24;
+    const char* a = S.at(aoff, d.y, lsz);
+    char* b = D.at(aoff, d.z, lsz);
+    switch (lsz) {
+      case 0: *reinterpret_cast<unsigned char*>(b) = *reinterpret_cast<const unsigned char*>(a); break;
+      case 1: *reinterpret_cast<unsigned short*>(b) = *reinterpret_cast<const unsigned short*>(a); break;
+      case 2: *reinterpret_cast<unsigned int*>(b) = *reinterpret_cast<const unsigned int*>(a); break;
+      default: *reinterpret_cast<uint2*>(b) = *reinterpret_cast<const uint2*>(a); break;
+    }
+  }
+}

@@ -112,18 +112,31 @@ __device__ __forceinline__ void tma_store_tile(const ConvPlan& p, uint64_t lt, c
 }
 
 // All threads: source tile -> destination tile in shared memory.
-__device__ __forceinline__ void tma_transform(const ConvPlan& p, const char* st, char* dt, uint32_t* tw,
-                                              int lane, int warp) {
+template <int SK, int DK>
+__device__ __forceinline__ void tma_transform_k(const ConvPlan& p, const uint4* sdesc, const char* st, char* dt,
+                                                int lane, int warp) {
   const uint32_t T = p.tg.T;
-  for (uint32_t g = (uint32_t)warp * 32; g < T; g += 8 * 32) {
-    const uint32_t r = g + lane;
-    if (p.dir == DIR_AOS_FM)
-      tile_aos_to_fm<0>(p, st, dt, r, tw, lane);
-    else if (p.dir == DIR_FM_AOS)
-      tile_fm_to_aos<0>(p, st, dt, r, tw, lane);
-    else
-      tile_fm_to_fm(p, st, dt, r);
+  for (uint32_t g = (uint32_t)warp * 32; g < T; g += 8 * 32) tile_convert<SK, DK>(p, sdesc, st, dt, g + lane);
+}
+
+__device__ __forceinline__ void tma_transform(const ConvPlan& p, const uint4* sdesc, const char* st, char* dt,
+                                              int lane, int warp) {
+  switch (p.src.kind * 3 + p.dst.kind) {
+    case K_AOS * 3 + K_SOA: tma_transform_k<K_AOS, K_SOA>(p, sdesc, st, dt, lane, warp); break;
+    case K_AOS * 3 + K_AOSOA: tma_transform_k<K_AOS, K_AOSOA>(p, sdesc, st, dt, lane, warp); break;
+    case K_SOA * 3 + K_AOS: tma_transform_k<K_SOA, K_AOS>(p, sdesc, st, dt, lane, warp); break;
+    case K_SOA * 3 + K_SOA: tma_transform_k<K_SOA, K_SOA>(p, sdesc, st, dt, lane, warp); break;
+    case K_SOA * 3 + K_AOSOA: tma_transform_k<K_SOA, K_AOSOA>(p, sdesc, st, dt, lane, warp); break;
+    case K_AOSOA * 3 + K_AOS: tma_transform_k<K_AOSOA, K_AOS>(p, sdesc, st, dt, lane, warp); break;
+    case K_AOSOA * 3 + K_SOA: tma_transform_k<K_AOSOA, K_SOA>(p, sdesc, st, dt, lane, warp); break;
+    default: tma_transform_k<K_AOSOA, K_AOSOA>(p, sdesc, st, dt, lane, warp); break;
   }
+}
+
+// Threads [0, ncols): the plan's column descriptors into shared memory.
+__device__ __forceinline__ void load_sdesc(const ConvPlan& p, uint4* sdesc) {
+  const uint32_t c = threadIdx.x;
+  if (c < p.ncols) sdesc[c] = make_uint4(p.tg.col[c], p.tg.src_off[c], p.tg.dst_off[c], 0u);
 }
 
 // A staged tile whose mbarrier did not complete within its bound: record
@@ -145,10 +158,12 @@ __device__ __forceinline__ void tma_abort(TmaSmem& m, uint32_t pending, uint32_t
 __global__ void __launch_bounds__(256, 2) k_convert_tma(const __grid_constant__ ConvPlan p) {
   extern __shared__ __align__(128) char staged_smem[];
   __shared__ int s_abort;
+  __shared__ uint4 sdesc[MRN_MAX_COLS];
   TmaSmem m = tma_smem(staged_smem);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t* tw = m.tw_all + warp * MRN_TW_WORDS_PER_WARP;
   const uint32_t T = p.tg.T;
+  load_sdesc(p, sdesc);
   const uint64_t nrec = p.dir == DIR_FM_AOS ? p.n : p.n_fm_pad;
   const uint64_t ntiles = (nrec + T - 1) / T;
   const uint64_t nfull = p.n / T;
@@ -180,7 +195,7 @@ __global__ void __launch_bounds__(256, 2) k_convert_tma(const __grid_constant__ 
       }
       pending &= ~(1u << s);
       parity ^= 1u << s;
-      tma_transform(p, m.src[s], m.dst[s], tw, lane, warp);
+      tma_transform(p, sdesc, m.src[s], m.dst[s], lane, warp);
       fence_proxy_async_smem();
       __syncthreads();
       const uint64_t nt = t + 2 * G;
@@ -453,6 +468,8 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchJob* __restrict__ j
   __shared__ JagShared sh;
   __shared__ TileSlot ring[4];
   __shared__ int s_abort;
+  __shared__ uint4 sdesc[MRN_MAX_COLS];
+  unsigned int desc_job = 0xffffffffu;  // job whose descriptors are in sdesc
   (void)counter;
   TmaSmem m = tma_smem(staged_smem);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -499,6 +516,10 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchJob* __restrict__ j
     if (ts.staged) {
       const ConvPlan& P = J.jp.parent;
       const int s = (int)ts.stage;
+      if (ts.job != desc_job) {
+        load_sdesc(P, sdesc);
+        desc_job = ts.job;
+      }
       if (!mbar_wait_bounded(&m.bar[s], ts.parity)) s_abort = 1;
       if (tid == 0) bulk_wait_read<1>();
       __syncthreads();
@@ -507,7 +528,7 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchJob* __restrict__ j
         return;
       }
       pending &= ~(1u << s);
-      tma_transform(P, m.src[s], m.dst[s], tw, lane, warp);
+      tma_transform(P, sdesc, m.src[s], m.dst[s], lane, warp);
       fence_proxy_async_smem();
       __syncthreads();
       if (tid == 0) tma_store_tile(P, ts.local, m.dst[s]);

@@ -37,14 +37,17 @@ struct ColPlan {
 // copies: tiles of T records; a side's tile is one contiguous range (AoS:
 // T*stride bytes; AoSoA: T/B whole blocks) or, for SoA, one range per column
 // packed in column order (column c at off[c] inside the tile).
-#define MRN_STAGE_BYTES 16384u
+#define MRN_STAGE_BYTES 12288u
 struct TileGeom {
   uint32_t tma;        // 1: full tiles go through the TMA pipeline
   uint32_t T;          // records per tile (multiple of 32 and of each AoSoA B)
   uint32_t src_bytes;  // bytes of a source tile
   uint32_t dst_bytes;  // bytes of a destination tile
+  uint32_t pad;        // 1: the AoS record has padding bytes (zeroed first)
+  uint32_t reserved;
   uint32_t src_off[MRN_MAX_COLS];  // SoA: column offset in the tile; AoSoA: column start in a block
   uint32_t dst_off[MRN_MAX_COLS];
+  uint32_t col[MRN_MAX_COLS];      // per data column: AoS offset | log2(size) << 24
 };
 
 struct ConvPlan {
