@@ -460,61 +460,109 @@ __device__ __forceinline__ void tile_fm_to_fm(const ConvPlan& p, const char* sti
   }
 }
 
-// Lean tile transform: per lane one record of the tile, per column one
-// shared-memory load and one store addressed from a compact descriptor
-// (uint4 {AoS offset | log2(size) << 24, source column offset, destination
-// column offset, 0}) kept in shared memory; source and destination kinds are
-// template parameters, so the column loop carries no layout branches.
-template <int K>
-struct TileSide {
-  char* base;    // AoS: the record; SoA: the tile; AoSoA: the record's block
-  uint32_t idx;  // SoA: record in tile; AoSoA: slot in block
-  __device__ __forceinline__ TileSide(char* tile, const SidePlan& sp, uint32_t stride, uint32_t r) {
-    if constexpr (K == K_AOS) {
-      base = tile + r * stride;
-      idx = 0;
-    } else if constexpr (K == K_SOA) {
-      base = tile;
-      idx = r;
-    } else {
-      const uint32_t blk = sp.block_shift != MRN_NO_SHIFT ? r >> sp.block_shift : r / sp.block;
-      idx = r - blk * sp.block;
-      base = tile + (uint64_t)blk * sp.block_bytes;
-    }
-  }
-  __device__ __forceinline__ char* at(uint32_t aos_off, uint32_t fm_off, uint32_t lsz) const {
-    if constexpr (K == K_AOS)
-      return base + aos_off;
-    else
-      return base + fm_off + (idx << lsz);
-  }
-};
+// 32-bit shared-memory accesses (the staged kernels address tiles with
+// shared-window offsets, not generic pointers).
+__device__ __forceinline__ uint32_t lds8(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint32_t lds16(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint32_t lds32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint2 lds64(uint32_t a) {
+  uint2 v;
+  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint4 lds128(uint32_t a) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void sts8(uint32_t a, uint32_t v) {
+  asm volatile("st.shared.u8 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void sts16(uint32_t a, uint32_t v) {
+  asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void sts32(uint32_t a, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void sts64(uint32_t a, uint2 v) {
+  asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(a), "r"(v.x), "r"(v.y) : "memory");
+}
+__device__ __forceinline__ void sts128_zero(uint32_t a) {
+  asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(a), "r"(0u) : "memory");
+}
 
+// Lane view of record r of a tile side of kind K: AoS -> the record's
+// address; SoA -> (tile, r); AoSoA -> (the record's block, slot).
+template <int K>
+__device__ __forceinline__ void tile_lane(const SidePlan& sp, uint32_t tile, uint32_t stride, uint32_t r,
+                                          uint32_t* base, uint32_t* idx) {
+  if constexpr (K == K_AOS) {
+    *base = tile + r * stride;
+    *idx = 0;
+  } else if constexpr (K == K_SOA) {
+    *base = tile;
+    *idx = r;
+  } else {
+    const uint32_t blk = sp.block_shift != MRN_NO_SHIFT ? r >> sp.block_shift : r / sp.block;
+    *idx = r - blk * sp.block;
+    *base = tile + blk * (uint32_t)sp.block_bytes;
+  }
+}
+
+// Staged tile transform, one record per lane: per column one shared load and
+// one shared store addressed from the column descriptor table `desc`
+// (uint4 {AoS offset | log2(size) << 24, source column offset, destination
+// column offset, 0} per column, in shared memory).  Layout kinds are template
+// parameters, so the column loop has no layout branches.
 template <int SK, int DK>
-__device__ __forceinline__ void tile_convert(const ConvPlan& p, const uint4* sdesc, const char* st, char* dt,
+__device__ __forceinline__ void tile_convert(const ConvPlan& p, uint32_t desc, uint32_t st, uint32_t dt,
                                              uint32_t r) {
-  const TileSide<SK> S(const_cast<char*>(st), p.src, p.stride, r);
-  const TileSide<DK> D(dt, p.dst, p.stride, r);
+  uint32_t sb, si, db, di;
+  tile_lane<SK>(p.src, st, p.stride, r, &sb, &si);
+  tile_lane<DK>(p.dst, dt, p.stride, r, &db, &di);
   if constexpr (DK == K_AOS) {
-    if (p.tg.pad) {  // padding bytes of the record are zero
-      uint32_t z[16];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) z[k] = 0;
-      for (uint32_t w = 0; w < p.stride; w += 64) store_any<0>(D.base + w, min(64u, p.stride - w), z, p.vec);
+    if (p.tg.pad) {  // the record's padding bytes are zero
+      const uint32_t S = p.stride, v = p.vec;
+      if (v == 16) {
+        for (uint32_t o = 0; o < S; o += 16) sts128_zero(db + o);
+      } else if (v == 8) {
+        for (uint32_t o = 0; o < S; o += 8) sts64(db + o, make_uint2(0, 0));
+      } else if (v == 4) {
+        for (uint32_t o = 0; o < S; o += 4) sts32(db + o, 0);
+      } else if (v == 2) {
+        for (uint32_t o = 0; o < S; o += 2) sts16(db + o, 0);
+      } else {
+        for (uint32_t o = 0; o < S; ++o) sts8(db + o, 0);
+      }
     }
   }
   const uint32_t nc = p.ncols;
-#pragma unroll 4
+#pragma unroll 2
   for (uint32_t c = 0; c < nc; ++c) {
-    const uint4 d = sdesc[c];
+    const uint4 d = lds128(desc + c * 16);
     const uint32_t aoff = d.x & 0xffffffu, lsz = d.x >> 24;
-    const char* a = S.at(aoff, d.y, lsz);
-    char* b = D.at(aoff, d.z, lsz);
-    switch (lsz) {
-      case 0: *reinterpret_cast<unsigned char*>(b) = *reinterpret_cast<const unsigned char*>(a); break;
-      case 1: *reinterpret_cast<unsigned short*>(b) = *reinterpret_cast<const unsigned short*>(a); break;
-      case 2: *reinterpret_cast<unsigned int*>(b) = *reinterpret_cast<const unsigned int*>(a); break;
-      default: *reinterpret_cast<uint2*>(b) = *reinterpret_cast<const uint2*>(a); break;
-    }
+    uint32_t a, b;
+    if constexpr (SK == K_AOS) a = sb + aoff; else a = sb + d.y + (si << lsz);
+    if constexpr (DK == K_AOS) b = db + aoff; else b = db + d.z + (di << lsz);
+    if (lsz == 2)
+      sts32(b, lds32(a));
+    else if (lsz == 3)
+      sts64(b, lds64(a));
+    else if (lsz == 1)
+      sts16(b, lds16(a));
+    else
+      sts8(b, lds8(a));
   }
 }

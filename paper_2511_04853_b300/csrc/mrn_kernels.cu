@@ -54,28 +54,23 @@ __global__ void __launch_bounds__(256) k_convert(const __grid_constant__ ConvPla
 
 // ------------------------------------------------- TMA-staged conversion
 
-// Shared memory of the staged kernels: two source and two destination tile
-// buffers (double buffering), the lane-private word columns of 8 warps and
-// two mbarriers.
+// Shared memory of the staged kernels: kNS source stages and two destination
+// tile buffers of kStage bytes each, then kNS mbarriers.  Tiles that take the
+// direct path use the destination buffers as their lane-word scratch (after
+// the bulk stores reading them have drained).
 constexpr uint32_t kStage = MRN_STAGE_BYTES;
-constexpr size_t kTmaSmem = 4 * (size_t)kStage + 8 * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t) + 64;
+constexpr uint32_t kNS = 4;
+constexpr size_t kTmaSmem = (size_t)(kNS + 2) * kStage + 128;
+static_assert(2 * kStage >= 8 * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t) + 4352,
+              "direct-tile scratch fits the destination buffers");
 
-struct TmaSmem {
-  char* src[2];
-  char* dst[2];
-  uint32_t* tw_all;
-  unsigned long long* bar;
-};
-
-__device__ __forceinline__ TmaSmem tma_smem(char* smem) {
-  TmaSmem m;
-  m.src[0] = smem;
-  m.src[1] = smem + kStage;
-  m.dst[0] = smem + 2 * kStage;
-  m.dst[1] = smem + 3 * kStage;
-  m.tw_all = reinterpret_cast<uint32_t*>(smem + 4 * kStage);
-  m.bar = reinterpret_cast<unsigned long long*>(smem + 4 * kStage + 8 * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t));
-  return m;
+__device__ __forceinline__ char* stage_src(char* smem, uint32_t s) { return smem + s * kStage; }
+__device__ __forceinline__ char* stage_dst(char* smem, uint32_t d) { return smem + (kNS + d) * kStage; }
+__device__ __forceinline__ unsigned long long* stage_bar(char* smem, uint32_t s) {
+  return reinterpret_cast<unsigned long long*>(smem + (kNS + 2) * kStage) + s;
+}
+__device__ __forceinline__ uint32_t* direct_scratch(char* smem) {
+  return reinterpret_cast<uint32_t*>(smem + kNS * kStage);
 }
 
 // Thread 0: bulk loads of source tile lt into a stage buffer.
@@ -95,7 +90,7 @@ __device__ __forceinline__ void tma_load_tile(const ConvPlan& p, uint64_t lt, ch
   }
 }
 
-// Thread 0: bulk stores of destination tile lt from a stage buffer.
+// Thread 0: bulk stores of destination tile lt from a tile buffer.
 __device__ __forceinline__ void tma_store_tile(const ConvPlan& p, uint64_t lt, const char* tile) {
   const TileGeom& g = p.tg;
   const uint64_t t0 = lt * g.T;
@@ -113,23 +108,24 @@ __device__ __forceinline__ void tma_store_tile(const ConvPlan& p, uint64_t lt, c
 
 // All threads: source tile -> destination tile in shared memory.
 template <int SK, int DK>
-__device__ __forceinline__ void tma_transform_k(const ConvPlan& p, const uint4* sdesc, const char* st, char* dt,
+__device__ __forceinline__ void tma_transform_k(const ConvPlan& p, uint32_t desc, uint32_t st, uint32_t dt,
                                                 int lane, int warp) {
   const uint32_t T = p.tg.T;
-  for (uint32_t g = (uint32_t)warp * 32; g < T; g += 8 * 32) tile_convert<SK, DK>(p, sdesc, st, dt, g + lane);
+  for (uint32_t g = (uint32_t)warp * 32; g < T; g += 8 * 32) tile_convert<SK, DK>(p, desc, st, dt, g + lane);
 }
 
-__device__ __forceinline__ void tma_transform(const ConvPlan& p, const uint4* sdesc, const char* st, char* dt,
+__device__ __forceinline__ void tma_transform(const ConvPlan& p, uint32_t desc, const char* st, char* dt,
                                               int lane, int warp) {
+  const uint32_t s = smem_u32(st), d = smem_u32(dt);
   switch (p.src.kind * 3 + p.dst.kind) {
-    case K_AOS * 3 + K_SOA: tma_transform_k<K_AOS, K_SOA>(p, sdesc, st, dt, lane, warp); break;
-    case K_AOS * 3 + K_AOSOA: tma_transform_k<K_AOS, K_AOSOA>(p, sdesc, st, dt, lane, warp); break;
-    case K_SOA * 3 + K_AOS: tma_transform_k<K_SOA, K_AOS>(p, sdesc, st, dt, lane, warp); break;
-    case K_SOA * 3 + K_SOA: tma_transform_k<K_SOA, K_SOA>(p, sdesc, st, dt, lane, warp); break;
-    case K_SOA * 3 + K_AOSOA: tma_transform_k<K_SOA, K_AOSOA>(p, sdesc, st, dt, lane, warp); break;
-    case K_AOSOA * 3 + K_AOS: tma_transform_k<K_AOSOA, K_AOS>(p, sdesc, st, dt, lane, warp); break;
-    case K_AOSOA * 3 + K_SOA: tma_transform_k<K_AOSOA, K_SOA>(p, sdesc, st, dt, lane, warp); break;
-    default: tma_transform_k<K_AOSOA, K_AOSOA>(p, sdesc, st, dt, lane, warp); break;
+    case K_AOS * 3 + K_SOA: tma_transform_k<K_AOS, K_SOA>(p, desc, s, d, lane, warp); break;
+    case K_AOS * 3 + K_AOSOA: tma_transform_k<K_AOS, K_AOSOA>(p, desc, s, d, lane, warp); break;
+    case K_SOA * 3 + K_AOS: tma_transform_k<K_SOA, K_AOS>(p, desc, s, d, lane, warp); break;
+    case K_SOA * 3 + K_SOA: tma_transform_k<K_SOA, K_SOA>(p, desc, s, d, lane, warp); break;
+    case K_SOA * 3 + K_AOSOA: tma_transform_k<K_SOA, K_AOSOA>(p, desc, s, d, lane, warp); break;
+    case K_AOSOA * 3 + K_AOS: tma_transform_k<K_AOSOA, K_AOS>(p, desc, s, d, lane, warp); break;
+    case K_AOSOA * 3 + K_SOA: tma_transform_k<K_AOSOA, K_SOA>(p, desc, s, d, lane, warp); break;
+    default: tma_transform_k<K_AOSOA, K_AOSOA>(p, desc, s, d, lane, warp); break;
   }
 }
 
@@ -140,72 +136,79 @@ __device__ __forceinline__ void load_sdesc(const ConvPlan& p, uint4* sdesc) {
 }
 
 // A staged tile whose mbarrier did not complete within its bound: record
-// the error, let copies still in flight land (bounded) and stop the CTA.
-// pending / parity: bit s = stage s has loads in flight / their phase parity.
-__device__ __forceinline__ void tma_abort(TmaSmem& m, uint32_t pending, uint32_t parity) {
+// the error, let this CTA's copies still in flight land (bounded) and stop.
+// pending: bit s = stage s has loads in flight; phase: bit s = their parity.
+__device__ __forceinline__ void tma_abort(char* smem, uint32_t pending, uint32_t phase) {
   if (threadIdx.x == 0) {
     flag_error(MRN_ETIMEOUT);
-    for (int s = 0; s < 2; ++s)
-      if ((pending >> s) & 1) mbar_wait_bounded(&m.bar[s], (parity >> s) & 1);
+    for (uint32_t s = 0; s < kNS; ++s)
+      if ((pending >> s) & 1) mbar_wait_bounded(stage_bar(smem, s), (phase >> s) & 1);
     bulk_wait_all();
   }
 }
 
+__device__ __forceinline__ void init_stage_bars(char* smem) {
+  for (uint32_t s = 0; s < kNS; ++s) mbar_init(stage_bar(smem, s), 1);
+  fence_mbar_init();
+}
+
 // One conversion with full tiles staged through shared memory by TMA bulk
-// copies (double-buffered: tile k+2's loads and tile k's stores are in
-// flight while tile k+1 is transformed); the partial last tile, if any,
-// takes the direct path.  CTA b takes tiles b, b + grid, ...
+// copies: kNS source stages keep up to kNS tiles' loads in flight while
+// tiles are transformed, and two destination buffers let a tile's bulk
+// stores overlap the next transform.  The partial last tile, if any, takes
+// the direct path.  CTA b takes tiles b, b + grid, ...
 __global__ void __launch_bounds__(256, 2) k_convert_tma(const __grid_constant__ ConvPlan p) {
   extern __shared__ __align__(128) char staged_smem[];
   __shared__ int s_abort;
   __shared__ uint4 sdesc[MRN_MAX_COLS];
-  TmaSmem m = tma_smem(staged_smem);
+  char* sm = staged_smem;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  uint32_t* tw = m.tw_all + warp * MRN_TW_WORDS_PER_WARP;
   const uint32_t T = p.tg.T;
-  load_sdesc(p, sdesc);
   const uint64_t nrec = p.dir == DIR_FM_AOS ? p.n : p.n_fm_pad;
   const uint64_t ntiles = (nrec + T - 1) / T;
   const uint64_t nfull = p.n / T;
   const uint64_t G = gridDim.x, b = blockIdx.x;
-  uint32_t pending = 0, parity = 0;
+  uint32_t pending = 0, phase = 0, dsel = 0;
   if (tid == 0) {
-    mbar_init(&m.bar[0], 1);
-    mbar_init(&m.bar[1], 1);
-    fence_mbar_init();
+    init_stage_bars(sm);
     s_abort = 0;
-    for (uint64_t k = 0; k < 2; ++k) {
-      const uint64_t t = b + k * G;
-      if (t < nfull) tma_load_tile(p, t, m.src[k], &m.bar[k]);
-    }
+    for (uint32_t k = 0; k < kNS; ++k)
+      if (b + k * G < nfull) tma_load_tile(p, b + k * G, stage_src(sm, k), stage_bar(sm, k));
   }
-  pending = (b < nfull ? 1u : 0u) | (b + G < nfull ? 2u : 0u);
+  for (uint32_t k = 0; k < kNS; ++k)
+    if (b + k * G < nfull) pending |= 1u << k;
+  load_sdesc(p, sdesc);
   __syncthreads();
+  const uint32_t desc = smem_u32(sdesc);
   for (uint64_t k = 0;; ++k) {
     const uint64_t t = b + k * G;
     if (t >= ntiles) break;
     if (t < nfull) {
-      const int s = (int)(k & 1);
-      if (!mbar_wait_bounded(&m.bar[s], (parity >> s) & 1)) s_abort = 1;
-      if (tid == 0) bulk_wait_read<1>();  // destination buffer s is free
+      const uint32_t s = (uint32_t)(k % kNS);
+      if (!mbar_wait_bounded(stage_bar(sm, s), (phase >> s) & 1)) s_abort = 1;
+      if (tid == 0) bulk_wait_read<1>();  // destination buffer dsel is free
       __syncthreads();
       if (s_abort) {
-        tma_abort(m, pending, parity);
+        tma_abort(sm, pending, phase);
         return;
       }
       pending &= ~(1u << s);
-      parity ^= 1u << s;
-      tma_transform(p, sdesc, m.src[s], m.dst[s], lane, warp);
+      phase ^= 1u << s;
+      tma_transform(p, desc, stage_src(sm, s), stage_dst(sm, dsel), lane, warp);
       fence_proxy_async_smem();
       __syncthreads();
-      const uint64_t nt = t + 2 * G;
+      const uint64_t nt = t + kNS * G;
       if (tid == 0) {
-        tma_store_tile(p, t, m.dst[s]);
-        if (nt < nfull) tma_load_tile(p, nt, m.src[s], &m.bar[s]);
+        tma_store_tile(p, t, stage_dst(sm, dsel));
+        if (nt < nfull) tma_load_tile(p, nt, stage_src(sm, s), stage_bar(sm, s));
       }
       if (nt < nfull) pending |= 1u << s;
+      dsel ^= 1;
     } else {
-      conv_range<0>(p, t * T, (t + 1) * T, tw, lane, warp, 8);
+      if (tid == 0) bulk_wait_read<0>();
+      __syncthreads();
+      conv_range<0>(p, t * T, (t + 1) * T, direct_scratch(sm) + warp * MRN_TW_WORDS_PER_WARP, lane, warp, 8);
+      __syncthreads();
     }
   }
   if (tid == 0) bulk_wait_all();
@@ -461,22 +464,22 @@ __device__ __forceinline__ unsigned int find_job(const unsigned long long* first
 }
 
 __global__ void __launch_bounds__(256, 2) k_batch(const BatchJob* __restrict__ jobs,
-                                               const unsigned long long* __restrict__ first_tile,
-                                               unsigned int njobs, unsigned long long total_tiles,
-                                               unsigned int* counter, unsigned long long* states) {
+                                                  const unsigned long long* __restrict__ first_tile,
+                                                  unsigned int njobs, unsigned long long total_tiles,
+                                                  unsigned int* counter, unsigned long long* states) {
   extern __shared__ __align__(128) char staged_smem[];
-  __shared__ JagShared sh;
-  __shared__ TileSlot ring[4];
+  __shared__ TileSlot ring[8];
   __shared__ int s_abort;
   __shared__ uint4 sdesc[MRN_MAX_COLS];
-  unsigned int desc_job = 0xffffffffu;  // job whose descriptors are in sdesc
   (void)counter;
-  TmaSmem m = tma_smem(staged_smem);
+  char* sm = staged_smem;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  uint32_t* tw = m.tw_all + warp * MRN_TW_WORDS_PER_WARP;
   const uint64_t G = gridDim.x, b = blockIdx.x;
-  uint32_t seq = 0;  // staged tiles issued (thread 0)
-  uint32_t pending = 0, parity = 0;
+  const uint32_t desc = smem_u32(sdesc);
+  unsigned int desc_job = 0xffffffffu;  // job whose descriptors are in sdesc
+  uint32_t seq = 0;                     // staged tiles issued (thread 0)
+  uint32_t pending = 0, phase = 0;      // per stage: loads in flight, parity (thread 0)
+  uint32_t dsel = 0;                    // destination buffer of the next staged tile
 
   // Thread 0: decides tile k of this CTA and issues its loads if staged.
   auto decide = [&](uint64_t k) {
@@ -488,57 +491,60 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchJob* __restrict__ j
     ts.local = t - J.tile_begin;
     const ConvPlan& P = J.jp.parent;
     ts.staged = J.kind == JOB_CONVERT && P.tg.tma && (ts.local + 1) * P.tg.T <= P.n;
-    ts.stage = seq & 1;
-    ts.parity = (seq >> 1) & 1;
+    ts.stage = seq % kNS;
+    ts.parity = (seq / kNS) & 1;
     if (ts.staged) {
-      tma_load_tile(P, ts.local, m.src[ts.stage], &m.bar[ts.stage]);
+      tma_load_tile(P, ts.local, stage_src(sm, ts.stage), stage_bar(sm, ts.stage));
       pending |= 1u << ts.stage;
-      parity = (parity & ~(1u << ts.stage)) | (ts.parity << ts.stage);
+      phase = (phase & ~(1u << ts.stage)) | (ts.parity << ts.stage);
       ++seq;
     }
-    ring[k & 3] = ts;
+    ring[k & 7] = ts;
   };
 
   if (tid == 0) {
-    mbar_init(&m.bar[0], 1);
-    mbar_init(&m.bar[1], 1);
-    fence_mbar_init();
+    init_stage_bars(sm);
     s_abort = 0;
-    decide(0);
-    decide(1);
+    for (uint32_t k = 0; k < kNS; ++k) decide(k);
   }
   __syncthreads();
   for (uint64_t k = 0;; ++k) {
     const uint64_t t = b + k * G;
     if (t >= total_tiles) break;
-    const TileSlot ts = ring[k & 3];
+    const TileSlot ts = ring[k & 7];
     const BatchJob& J = jobs[ts.job];
     if (ts.staged) {
       const ConvPlan& P = J.jp.parent;
-      const int s = (int)ts.stage;
+      const uint32_t s = ts.stage;
       if (ts.job != desc_job) {
         load_sdesc(P, sdesc);
         desc_job = ts.job;
       }
-      if (!mbar_wait_bounded(&m.bar[s], ts.parity)) s_abort = 1;
+      if (!mbar_wait_bounded(stage_bar(sm, s), ts.parity)) s_abort = 1;
       if (tid == 0) bulk_wait_read<1>();
       __syncthreads();
       if (s_abort) {
-        tma_abort(m, pending, parity);
+        tma_abort(sm, pending, phase);
         return;
       }
       pending &= ~(1u << s);
-      tma_transform(P, sdesc, m.src[s], m.dst[s], lane, warp);
+      tma_transform(P, desc, stage_src(sm, s), stage_dst(sm, dsel), lane, warp);
       fence_proxy_async_smem();
       __syncthreads();
-      if (tid == 0) tma_store_tile(P, ts.local, m.dst[s]);
+      if (tid == 0) tma_store_tile(P, ts.local, stage_dst(sm, dsel));
+      dsel ^= 1;
     } else {
+      if (tid == 0) bulk_wait_read<0>();  // the scratch aliases the destination buffers
+      __syncthreads();
+      uint32_t* tw_all = direct_scratch(sm);
+      uint32_t* tw = tw_all + warp * MRN_TW_WORDS_PER_WARP;
+      JagShared& sh = *reinterpret_cast<JagShared*>(tw_all + 8 * MRN_TW_WORDS_PER_WARP);
       const unsigned long long local = ts.local;
       if (J.kind == JOB_CONVERT) {
         const uint32_t tr = J.tile_records;
         conv_range<0>(J.jp.parent, local * tr, (local + 1) * tr, tw, lane, warp, 8);
       } else if (J.kind == JOB_JAG_A2S) {
-        jagged_a2s_tile<0, 0>(J.jp, local, states + J.tile_begin, m.tw_all, sh);
+        jagged_a2s_tile<0, 0>(J.jp, local, states + J.tile_begin, tw_all, sh);
       } else if (J.kind == JOB_JAG_S2A) {
         jagged_s2a_group<0, 0>(J.jp, local * 8 + warp, J.parent_groups, tw, lane);
       } else {
@@ -547,7 +553,7 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchJob* __restrict__ j
       }
       __syncthreads();
     }
-    if (tid == 0) decide(k + 2);
+    if (tid == 0) decide(k + kNS);
   }
   if (tid == 0) bulk_wait_all();
 }
