@@ -521,17 +521,26 @@ __device__ __forceinline__ void tile_lane(const SidePlan& sp, uint32_t tile, uin
   }
 }
 
-// Staged tile transform, one record per lane: per column one shared load and
-// one shared store addressed from the column descriptor table `desc`
-// (uint4 {AoS offset | log2(size) << 24, source column offset, destination
-// column offset, 0} per column, in shared memory).  Layout kinds are template
-// parameters, so the column loop has no layout branches.
-template <int SK, int DK>
-__device__ __forceinline__ void tile_convert(const ConvPlan& p, uint32_t desc, uint32_t st, uint32_t dt,
-                                             uint32_t r) {
-  uint32_t sb, si, db, di;
-  tile_lane<SK>(p.src, st, p.stride, r, &sb, &si);
-  tile_lane<DK>(p.dst, dt, p.stride, r, &db, &di);
+__device__ __forceinline__ uint2 lds_sz(uint32_t a, uint32_t lsz) {
+  if (lsz == 3) return lds64(a);
+  if (lsz == 2) return make_uint2(lds32(a), 0u);
+  if (lsz == 1) return make_uint2(lds16(a), 0u);
+  return make_uint2(lds8(a), 0u);
+}
+
+__device__ __forceinline__ void sts_sz(uint32_t a, uint2 v, uint32_t lsz) {
+  if (lsz == 3)
+    sts64(a, v);
+  else if (lsz == 2)
+    sts32(a, v.x);
+  else if (lsz == 1)
+    sts16(a, v.x);
+  else
+    sts8(a, v.x);
+}
+
+template <int DK>
+__device__ __forceinline__ void zero_record(const ConvPlan& p, uint32_t db) {
   if constexpr (DK == K_AOS) {
     if (p.tg.pad) {  // the record's padding bytes are zero
       const uint32_t S = p.stride, v = p.vec;
@@ -548,21 +557,75 @@ __device__ __forceinline__ void tile_convert(const ConvPlan& p, uint32_t desc, u
       }
     }
   }
+}
+
+// Staged tile transform: each lane converts records r0 and r1 (= r0 + 256,
+// when `two`) of the tile.  Per column one shared load and one shared store
+// per record, addressed from the column descriptor table `desc` (uint4
+// {AoS offset | log2(size) << 24, source column offset, destination column
+// offset, 0} per column, in shared memory); the loads of two columns of both
+// records are issued before their stores.  Layout kinds are template
+// parameters, so the column loop has no layout branches.
+template <int SK, int DK>
+__device__ __forceinline__ void tile_convert(const ConvPlan& p, uint32_t desc, uint32_t st, uint32_t dt,
+                                             uint32_t r0, bool two) {
+  const uint32_t r1 = two ? r0 + 256 : r0;
+  uint32_t sb0, si0, db0, di0, sb1, si1, db1, di1;
+  tile_lane<SK>(p.src, st, p.stride, r0, &sb0, &si0);
+  tile_lane<DK>(p.dst, dt, p.stride, r0, &db0, &di0);
+  tile_lane<SK>(p.src, st, p.stride, r1, &sb1, &si1);
+  tile_lane<DK>(p.dst, dt, p.stride, r1, &db1, &di1);
+  zero_record<DK>(p, db0);
+  if (two) zero_record<DK>(p, db1);
   const uint32_t nc = p.ncols;
-#pragma unroll 2
-  for (uint32_t c = 0; c < nc; ++c) {
-    const uint4 d = lds128(desc + c * 16);
-    const uint32_t aoff = d.x & 0xffffffu, lsz = d.x >> 24;
-    uint32_t a, b;
-    if constexpr (SK == K_AOS) a = sb + aoff; else a = sb + d.y + (si << lsz);
-    if constexpr (DK == K_AOS) b = db + aoff; else b = db + d.z + (di << lsz);
-    if (lsz == 2)
-      sts32(b, lds32(a));
-    else if (lsz == 3)
-      sts64(b, lds64(a));
-    else if (lsz == 1)
-      sts16(b, lds16(a));
-    else
-      sts8(b, lds8(a));
+  uint32_t c = 0;
+  for (; c + 1 < nc; c += 2) {
+    const uint4 d0 = lds128(desc + c * 16), d1 = lds128(desc + c * 16 + 16);
+    const uint32_t ao0 = d0.x & 0xffffffu, l0 = d0.x >> 24, ao1 = d1.x & 0xffffffu, l1 = d1.x >> 24;
+    uint32_t a00, a01, a10, a11, b00, b01, b10, b11;  // a<column><record>
+    if constexpr (SK == K_AOS) {
+      a00 = sb0 + ao0; a01 = sb1 + ao0; a10 = sb0 + ao1; a11 = sb1 + ao1;
+    } else {
+      a00 = sb0 + d0.y + (si0 << l0); a01 = sb1 + d0.y + (si1 << l0);
+      a10 = sb0 + d1.y + (si0 << l1); a11 = sb1 + d1.y + (si1 << l1);
+    }
+    if constexpr (DK == K_AOS) {
+      b00 = db0 + ao0; b01 = db1 + ao0; b10 = db0 + ao1; b11 = db1 + ao1;
+    } else {
+      b00 = db0 + d0.z + (di0 << l0); b01 = db1 + d0.z + (di1 << l0);
+      b10 = db0 + d1.z + (di0 << l1); b11 = db1 + d1.z + (di1 << l1);
+    }
+    const uint2 v00 = lds_sz(a00, l0), v10 = lds_sz(a10, l1);
+    uint2 v01 = v00, v11 = v10;
+    if (two) {
+      v01 = lds_sz(a01, l0);
+      v11 = lds_sz(a11, l1);
+    }
+    sts_sz(b00, v00, l0);
+    sts_sz(b10, v10, l1);
+    if (two) {
+      sts_sz(b01, v01, l0);
+      sts_sz(b11, v11, l1);
+    }
+  }
+  if (c < nc) {
+    const uint4 d0 = lds128(desc + c * 16);
+    const uint32_t ao0 = d0.x & 0xffffffu, l0 = d0.x >> 24;
+    uint32_t a00, a01, b00, b01;
+    if constexpr (SK == K_AOS) {
+      a00 = sb0 + ao0; a01 = sb1 + ao0;
+    } else {
+      a00 = sb0 + d0.y + (si0 << l0); a01 = sb1 + d0.y + (si1 << l0);
+    }
+    if constexpr (DK == K_AOS) {
+      b00 = db0 + ao0; b01 = db1 + ao0;
+    } else {
+      b00 = db0 + d0.z + (di0 << l0); b01 = db1 + d0.z + (di1 << l0);
+    }
+    const uint2 v00 = lds_sz(a00, l0);
+    uint2 v01 = v00;
+    if (two) v01 = lds_sz(a01, l0);
+    sts_sz(b00, v00, l0);
+    if (two) sts_sz(b01, v01, l0);
   }
 }

@@ -111,7 +111,8 @@ template <int SK, int DK>
 __device__ __forceinline__ void tma_transform_k(const ConvPlan& p, uint32_t desc, uint32_t st, uint32_t dt,
                                                 int lane, int warp) {
   const uint32_t T = p.tg.T;
-  for (uint32_t g = (uint32_t)warp * 32; g < T; g += 8 * 32) tile_convert<SK, DK>(p, desc, st, dt, g + lane);
+  for (uint32_t g = (uint32_t)warp * 32; g < T; g += 2 * 8 * 32)
+    tile_convert<SK, DK>(p, desc, st, dt, g + lane, g + 8 * 32 < T);
 }
 
 __device__ __forceinline__ void tma_transform(const ConvPlan& p, uint32_t desc, const char* st, char* dt,
