@@ -54,24 +54,20 @@ __global__ void __launch_bounds__(256) k_convert(const __grid_constant__ ConvPla
 
 // ------------------------------------------------- TMA-staged conversion
 
-// Shared memory of the staged kernels: kNS source stages and kND destination
+// Shared memory of the staged kernels: kNS source stages and two destination
 // tile buffers of kStage bytes each, then kNS mbarriers.  Tiles that take the
 // direct path use the destination buffers as their lane-word scratch (after
-// the bulk stores reading them have drained).  With three destination
-// buffers one CTA barrier per tile suffices: the buffer a tile writes was last
-// stored two tiles earlier, and thread 0 drains that store's reads before the
-// barrier of the tile in between.
+// the bulk stores reading them have drained).
 constexpr uint32_t kStage = MRN_STAGE_BYTES;
-constexpr uint32_t kNS = 3;
-constexpr uint32_t kND = 3;
-constexpr size_t kTmaSmem = (size_t)(kNS + kND) * kStage + 128;
+constexpr uint32_t kNS = 4;
+constexpr size_t kTmaSmem = (size_t)(kNS + 2) * kStage + 128;
 static_assert(2 * kStage >= 8 * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t) + 4352,
               "direct-tile scratch fits the destination buffers");
 
 __device__ __forceinline__ char* stage_src(char* smem, uint32_t s) { return smem + s * kStage; }
 __device__ __forceinline__ char* stage_dst(char* smem, uint32_t d) { return smem + (kNS + d) * kStage; }
 __device__ __forceinline__ unsigned long long* stage_bar(char* smem, uint32_t s) {
-  return reinterpret_cast<unsigned long long*>(smem + (kNS + kND) * kStage) + s;
+  return reinterpret_cast<unsigned long long*>(smem + (kNS + 2) * kStage) + s;
 }
 __device__ __forceinline__ uint32_t* direct_scratch(char* smem) {
   return reinterpret_cast<uint32_t*>(smem + kNS * kStage);
@@ -191,23 +187,24 @@ __global__ void __launch_bounds__(256, 2) k_convert_tma(const __grid_constant__ 
     if (t < nfull) {
       const uint32_t s = (uint32_t)(k % kNS);
       if (!mbar_wait_bounded(stage_bar(sm, s), (phase >> s) & 1)) s_abort = 1;
+      if (tid == 0) bulk_wait_read<1>();  // destination buffer dsel is free
+      __syncthreads();
+      if (s_abort) {
+        tma_abort(sm, pending, phase);
+        return;
+      }
+      pending &= ~(1u << s);
       phase ^= 1u << s;
       tma_transform(p, desc, stage_src(sm, s), stage_dst(sm, dsel), lane, warp);
       fence_proxy_async_smem();
       __syncthreads();
-      if (s_abort) {
-        tma_abort(sm, pending, phase ^ (1u << s));
-        return;
-      }
-      pending &= ~(1u << s);
       const uint64_t nt = t + kNS * G;
       if (tid == 0) {
         tma_store_tile(p, t, stage_dst(sm, dsel));
         if (nt < nfull) tma_load_tile(p, nt, stage_src(sm, s), stage_bar(sm, s));
-        bulk_wait_read<1>();  // the previous tile's buffer is free again
       }
       if (nt < nfull) pending |= 1u << s;
-      dsel = dsel + 1 == kND ? 0 : dsel + 1;
+      dsel ^= 1;
     } else {
       if (tid == 0) bulk_wait_read<0>();
       __syncthreads();
@@ -525,19 +522,18 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchJob* __restrict__ j
         desc_job = ts.job;
       }
       if (!mbar_wait_bounded(stage_bar(sm, s), ts.parity)) s_abort = 1;
-      tma_transform(P, desc, stage_src(sm, s), stage_dst(sm, dsel), lane, warp);
-      fence_proxy_async_smem();
+      if (tid == 0) bulk_wait_read<1>();
       __syncthreads();
       if (s_abort) {
         tma_abort(sm, pending, phase);
         return;
       }
       pending &= ~(1u << s);
-      if (tid == 0) {
-        tma_store_tile(P, ts.local, stage_dst(sm, dsel));
-        bulk_wait_read<1>();  // the previous staged tile's buffer is free again
-      }
-      dsel = dsel + 1 == kND ? 0 : dsel + 1;
+      tma_transform(P, desc, stage_src(sm, s), stage_dst(sm, dsel), lane, warp);
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (tid == 0) tma_store_tile(P, ts.local, stage_dst(sm, dsel));
+      dsel ^= 1;
     } else {
       if (tid == 0) bulk_wait_read<0>();  // the scratch aliases the destination buffers
       __syncthreads();
