@@ -216,6 +216,24 @@ int mrn_sync(void* stream);
 /* As mrn_sync, but returns every recorded code: bit k of *bits = code k. */
 int mrn_sync_bits(void* stream, uint32_t* bits);
 
+/* The jagged AoS -> SoA conversion of mrn_convert, without any device
+ * allocation by the library.  The paper has no counterpart: this exists for
+ * callers that cannot let a library allocate device memory (an application
+ * whose own pool owns the whole GPU, a process at the edge of device memory,
+ * a latency-critical loop that cannot take an allocator call).
+ * Semantics and outputs are those of mrn_convert for a jagged schema with an
+ * AoS source and a SoA destination; any other pair returns MRN_EINVAL.
+ * The scan's scratch is a fixed 256 KiB array inside the library, present on
+ * every device that loads the library until the process exits; it holds at
+ * most 8,380,416 parents per call, larger n_records returns MRN_ESIZE before
+ * anything is launched.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the array and each
+ * clears it on its stream before use, so calls that overlap on the GPU
+ * (different streams, no ordering between them) race and must not be
+ * issued. */
+int mrn_convert_jagged_noalloc(const mrn_view* src, const mrn_view* dst, void* stream);
+
 /* Sum of the jagged lengths of an AoS device view (the number of child
  * values an AoS -> SoA conversion writes).  Synchronous; *m receives it. */
 int mrn_jagged_count(const mrn_view* src, uint64_t* m, void* stream);

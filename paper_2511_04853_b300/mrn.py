@@ -94,6 +94,7 @@ SIGNATURES = [
     ("mrn_aosoa_block_bytes", ctypes.c_int, [vp, u32, ctypes.POINTER(sz)]),
     ("mrn_aosoa_column_offset", ctypes.c_int, [vp, u32, u32, ctypes.POINTER(sz)]),
     ("mrn_convert", ctypes.c_int, [ctypes.POINTER(ViewStruct), ctypes.POINTER(ViewStruct), vp]),
+    ("mrn_convert_jagged_noalloc", ctypes.c_int, [ctypes.POINTER(ViewStruct), ctypes.POINTER(ViewStruct), vp]),
     ("mrn_sync", ctypes.c_int, [vp]),
     ("mrn_sync_bits", ctypes.c_int, [vp, ctypes.POINTER(u32)]),
     ("mrn_jagged_count", ctypes.c_int, [ctypes.POINTER(ViewStruct), ctypes.POINTER(u64), vp]),
