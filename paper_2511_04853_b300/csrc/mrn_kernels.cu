@@ -440,12 +440,17 @@ __global__ void k_write_offset0(char* offs, uint32_t osz, unsigned long long v) 
 
 // ----------------------------------------------------------------- batched
 
-// Every job of a batch in one persistent launch.  CTA b takes global tiles
-// b, b + grid, ... in increasing order (so a jagged tile's predecessors are
-// always taken earlier by running CTAs and its look-back terminates).  Full
-// tiles of jobs with a TMA tile geometry are staged through shared memory
-// as in k_convert_tma, with thread 0 deciding two tiles ahead; every other
-// tile (jagged, zero-fill, partial or unstaged conversions) runs directly.
+// Every job of a batch in one persistent launch.  CTA b takes chunks of
+// kChunk consecutive global tiles in round-robin order (chunks b, b + grid,
+// ...), so its tiles increase and a jagged tile's predecessor lies either in
+// the same chunk or in a chunk another running CTA takes in the same round:
+// every look-back terminates.  Consecutive tiles of a chunk mostly share a
+// job, so thread 0 follows the jobs with a forward-only cursor.  Full tiles
+// of jobs with a TMA tile geometry are staged through shared memory as in
+// k_convert_tma, thread 0 deciding kNS tiles ahead; every other tile
+// (jagged, zero-fill, partial or unstaged conversions) runs directly.
+constexpr uint64_t kChunk = 4;
+
 struct TileSlot {
   unsigned int job;
   unsigned int staged;
@@ -454,14 +459,9 @@ struct TileSlot {
   unsigned long long local;
 };
 
-__device__ __forceinline__ unsigned int find_job(const unsigned long long* first_tile, unsigned int njobs,
-                                                 unsigned long long t) {
-  unsigned int lo = 0, hi = njobs;
-  while (hi - lo > 1) {
-    const unsigned int mid = (lo + hi) >> 1;
-    if (__ldg(first_tile + mid) <= t) lo = mid; else hi = mid;
-  }
-  return lo;
+// k-th tile of CTA b (chunks of kChunk tiles, round-robin over G CTAs).
+__device__ __forceinline__ uint64_t batch_tile(uint64_t k, uint64_t b, uint64_t G) {
+  return ((k / kChunk) * G + b) * kChunk + (k % kChunk);
 }
 
 __global__ void __launch_bounds__(256, 2) k_batch(const BatchJob* __restrict__ jobs,
@@ -481,13 +481,15 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchJob* __restrict__ j
   uint32_t seq = 0;                     // staged tiles issued (thread 0)
   uint32_t pending = 0, phase = 0;      // per stage: loads in flight, parity (thread 0)
   uint32_t dsel = 0;                    // destination buffer of the next staged tile
+  unsigned int cursor = 0;              // job of the last decided tile (thread 0)
 
   // Thread 0: decides tile k of this CTA and issues its loads if staged.
   auto decide = [&](uint64_t k) {
-    const uint64_t t = b + k * G;
+    const uint64_t t = batch_tile(k, b, G);
     if (t >= total_tiles) return;
+    while (cursor + 1 < njobs && __ldg(first_tile + cursor + 1) <= t) ++cursor;
     TileSlot ts;
-    ts.job = find_job(first_tile, njobs, t);
+    ts.job = cursor;
     const BatchJob& J = jobs[ts.job];
     ts.local = t - J.tile_begin;
     const ConvPlan& P = J.jp.parent;
@@ -510,7 +512,7 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchJob* __restrict__ j
   }
   __syncthreads();
   for (uint64_t k = 0;; ++k) {
-    const uint64_t t = b + k * G;
+    const uint64_t t = batch_tile(k, b, G);
     if (t >= total_tiles) break;
     const TileSlot ts = ring[k & 7];
     const BatchJob& J = jobs[ts.job];
@@ -792,7 +794,8 @@ int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, uns
   const int occ = batch_occupancy();
   const int per_sm = ctas_per_sm ? std::min((int)ctas_per_sm, occ) : occ;
   const uint64_t cap = (uint64_t)device_sm_count() * (uint64_t)per_sm;
-  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(cap, total_tiles));
+  const uint64_t chunks = (total_tiles + kChunk - 1) / kChunk;
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(cap, chunks));
   k_batch<<<grid, 256, kTmaSmem, static_cast<cudaStream_t>(stream)>>>(jobs, first_tile, njobs, total_tiles,
                                                                         counter, states);
   return cuda_status(cudaGetLastError());
