@@ -503,11 +503,19 @@ __device__ __forceinline__ void sts128_zero(uint32_t a) {
   asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(a), "r"(0u) : "memory");
 }
 
+// The fields of a plan the staged transform reads, copied into shared memory
+// next to the column descriptors.
+struct TileHdr {
+  uint32_t ncols, stride, vec, pad, T;
+  uint32_t sblock, sshift, sbb;  // source AoSoA block, log2 (or MRN_NO_SHIFT), bytes
+  uint32_t dblock, dshift, dbb;  // destination AoSoA block, log2, bytes
+};
+
 // Lane view of record r of a tile side of kind K: AoS -> the record's
 // address; SoA -> (tile, r); AoSoA -> (the record's block, slot).
 template <int K>
-__device__ __forceinline__ void tile_lane(const SidePlan& sp, uint32_t tile, uint32_t stride, uint32_t r,
-                                          uint32_t* base, uint32_t* idx) {
+__device__ __forceinline__ void tile_lane(uint32_t block, uint32_t shift, uint32_t bb, uint32_t tile,
+                                          uint32_t stride, uint32_t r, uint32_t* base, uint32_t* idx) {
   if constexpr (K == K_AOS) {
     *base = tile + r * stride;
     *idx = 0;
@@ -515,9 +523,9 @@ __device__ __forceinline__ void tile_lane(const SidePlan& sp, uint32_t tile, uin
     *base = tile;
     *idx = r;
   } else {
-    const uint32_t blk = sp.block_shift != MRN_NO_SHIFT ? r >> sp.block_shift : r / sp.block;
-    *idx = r - blk * sp.block;
-    *base = tile + blk * (uint32_t)sp.block_bytes;
+    const uint32_t blk = shift != MRN_NO_SHIFT ? r >> shift : r / block;
+    *idx = r - blk * block;
+    *base = tile + blk * bb;
   }
 }
 
@@ -540,10 +548,10 @@ __device__ __forceinline__ void sts_sz(uint32_t a, uint2 v, uint32_t lsz) {
 }
 
 template <int DK>
-__device__ __forceinline__ void zero_record(const ConvPlan& p, uint32_t db) {
+__device__ __forceinline__ void zero_record(const TileHdr& h, uint32_t db) {
   if constexpr (DK == K_AOS) {
-    if (p.tg.pad) {  // the record's padding bytes are zero
-      const uint32_t S = p.stride, v = p.vec;
+    if (h.pad) {  // the record's padding bytes are zero
+      const uint32_t S = h.stride, v = h.vec;
       if (v == 16) {
         for (uint32_t o = 0; o < S; o += 16) sts128_zero(db + o);
       } else if (v == 8) {
@@ -567,17 +575,17 @@ __device__ __forceinline__ void zero_record(const ConvPlan& p, uint32_t db) {
 // records are issued before their stores.  Layout kinds are template
 // parameters, so the column loop has no layout branches.
 template <int SK, int DK>
-__device__ __forceinline__ void tile_convert(const ConvPlan& p, uint32_t desc, uint32_t st, uint32_t dt,
+__device__ __forceinline__ void tile_convert(const TileHdr& h, uint32_t desc, uint32_t st, uint32_t dt,
                                              uint32_t r0, bool two) {
   const uint32_t r1 = two ? r0 + 256 : r0;
   uint32_t sb0, si0, db0, di0, sb1, si1, db1, di1;
-  tile_lane<SK>(p.src, st, p.stride, r0, &sb0, &si0);
-  tile_lane<DK>(p.dst, dt, p.stride, r0, &db0, &di0);
-  tile_lane<SK>(p.src, st, p.stride, r1, &sb1, &si1);
-  tile_lane<DK>(p.dst, dt, p.stride, r1, &db1, &di1);
-  zero_record<DK>(p, db0);
-  if (two) zero_record<DK>(p, db1);
-  const uint32_t nc = p.ncols;
+  tile_lane<SK>(h.sblock, h.sshift, h.sbb, st, h.stride, r0, &sb0, &si0);
+  tile_lane<DK>(h.dblock, h.dshift, h.dbb, dt, h.stride, r0, &db0, &di0);
+  tile_lane<SK>(h.sblock, h.sshift, h.sbb, st, h.stride, r1, &sb1, &si1);
+  tile_lane<DK>(h.dblock, h.dshift, h.dbb, dt, h.stride, r1, &db1, &di1);
+  zero_record<DK>(h, db0);
+  if (two) zero_record<DK>(h, db1);
+  const uint32_t nc = h.ncols;
   uint32_t c = 0;
   for (; c + 1 < nc; c += 2) {
     const uint4 d0 = lds128(desc + c * 16), d1 = lds128(desc + c * 16 + 16);

@@ -108,32 +108,49 @@ __device__ __forceinline__ void tma_store_tile(const ConvPlan& p, uint64_t lt, c
 
 // All threads: source tile -> destination tile in shared memory.
 template <int SK, int DK>
-__device__ __forceinline__ void tma_transform_k(const ConvPlan& p, uint32_t desc, uint32_t st, uint32_t dt,
+__device__ __forceinline__ void tma_transform_k(const TileHdr& h, uint32_t desc, uint32_t st, uint32_t dt,
                                                 int lane, int warp) {
-  const uint32_t T = p.tg.T;
-  for (uint32_t g = (uint32_t)warp * 32; g < T; g += 2 * 8 * 32)
-    tile_convert<SK, DK>(p, desc, st, dt, g + lane, g + 8 * 32 < T);
+  const TileHdr hh = h;
+  for (uint32_t g = (uint32_t)warp * 32; g < hh.T; g += 2 * 8 * 32)
+    tile_convert<SK, DK>(hh, desc, st, dt, g + lane, g + 8 * 32 < hh.T);
 }
 
-__device__ __forceinline__ void tma_transform(const ConvPlan& p, uint32_t desc, const char* st, char* dt,
-                                              int lane, int warp) {
+__device__ __forceinline__ void tma_transform(uint32_t kinds, const TileHdr& h, uint32_t desc, const char* st,
+                                              char* dt, int lane, int warp) {
   const uint32_t s = smem_u32(st), d = smem_u32(dt);
-  switch (p.src.kind * 3 + p.dst.kind) {
-    case K_AOS * 3 + K_SOA: tma_transform_k<K_AOS, K_SOA>(p, desc, s, d, lane, warp); break;
-    case K_AOS * 3 + K_AOSOA: tma_transform_k<K_AOS, K_AOSOA>(p, desc, s, d, lane, warp); break;
-    case K_SOA * 3 + K_AOS: tma_transform_k<K_SOA, K_AOS>(p, desc, s, d, lane, warp); break;
-    case K_SOA * 3 + K_SOA: tma_transform_k<K_SOA, K_SOA>(p, desc, s, d, lane, warp); break;
-    case K_SOA * 3 + K_AOSOA: tma_transform_k<K_SOA, K_AOSOA>(p, desc, s, d, lane, warp); break;
-    case K_AOSOA * 3 + K_AOS: tma_transform_k<K_AOSOA, K_AOS>(p, desc, s, d, lane, warp); break;
-    case K_AOSOA * 3 + K_SOA: tma_transform_k<K_AOSOA, K_SOA>(p, desc, s, d, lane, warp); break;
-    default: tma_transform_k<K_AOSOA, K_AOSOA>(p, desc, s, d, lane, warp); break;
+  switch (kinds) {
+    case K_AOS * 3 + K_SOA: tma_transform_k<K_AOS, K_SOA>(h, desc, s, d, lane, warp); break;
+    case K_AOS * 3 + K_AOSOA: tma_transform_k<K_AOS, K_AOSOA>(h, desc, s, d, lane, warp); break;
+    case K_SOA * 3 + K_AOS: tma_transform_k<K_SOA, K_AOS>(h, desc, s, d, lane, warp); break;
+    case K_SOA * 3 + K_SOA: tma_transform_k<K_SOA, K_SOA>(h, desc, s, d, lane, warp); break;
+    case K_SOA * 3 + K_AOSOA: tma_transform_k<K_SOA, K_AOSOA>(h, desc, s, d, lane, warp); break;
+    case K_AOSOA * 3 + K_AOS: tma_transform_k<K_AOSOA, K_AOS>(h, desc, s, d, lane, warp); break;
+    case K_AOSOA * 3 + K_SOA: tma_transform_k<K_AOSOA, K_SOA>(h, desc, s, d, lane, warp); break;
+    default: tma_transform_k<K_AOSOA, K_AOSOA>(h, desc, s, d, lane, warp); break;
   }
 }
 
-// Threads [0, ncols): the plan's column descriptors into shared memory.
-__device__ __forceinline__ void load_sdesc(const ConvPlan& p, uint4* sdesc) {
+// Threads [0, ncols): the plan's column descriptors into shared memory;
+// thread 0 also the header fields.  Returns the layout-kind pair.
+__device__ __forceinline__ uint32_t load_sdesc(const ConvPlan& p, uint4* sdesc, TileHdr* hdr) {
   const uint32_t c = threadIdx.x;
   if (c < p.ncols) sdesc[c] = make_uint4(p.tg.col[c], p.tg.src_off[c], p.tg.dst_off[c], 0u);
+  if (c == 0) {
+    TileHdr h;
+    h.ncols = p.ncols;
+    h.stride = p.stride;
+    h.vec = p.vec;
+    h.pad = p.tg.pad;
+    h.T = p.tg.T;
+    h.sblock = p.src.block;
+    h.sshift = p.src.block_shift;
+    h.sbb = (uint32_t)p.src.block_bytes;
+    h.dblock = p.dst.block;
+    h.dshift = p.dst.block_shift;
+    h.dbb = (uint32_t)p.dst.block_bytes;
+    *hdr = h;
+  }
+  return p.src.kind * 3 + p.dst.kind;
 }
 
 // A staged tile whose mbarrier did not complete within its bound: record
@@ -158,10 +175,11 @@ __device__ __forceinline__ void init_stage_bars(char* smem) {
 // tiles are transformed, and two destination buffers let a tile's bulk
 // stores overlap the next transform.  The partial last tile, if any, takes
 // the direct path.  CTA b takes tiles b, b + grid, ...
-__global__ void __launch_bounds__(256, 2) k_convert_tma(const __grid_constant__ ConvPlan p) {
+__global__ void __launch_bounds__(256, 3) k_convert_tma(const __grid_constant__ ConvPlan p) {
   extern __shared__ __align__(128) char staged_smem[];
   __shared__ int s_abort;
   __shared__ uint4 sdesc[MRN_MAX_COLS];
+  __shared__ TileHdr hdr;
   char* sm = staged_smem;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t T = p.tg.T;
@@ -178,7 +196,7 @@ __global__ void __launch_bounds__(256, 2) k_convert_tma(const __grid_constant__ 
   }
   for (uint32_t k = 0; k < kNS; ++k)
     if (b + k * G < nfull) pending |= 1u << k;
-  load_sdesc(p, sdesc);
+  const uint32_t kinds = load_sdesc(p, sdesc, &hdr);
   __syncthreads();
   const uint32_t desc = smem_u32(sdesc);
   for (uint64_t k = 0;; ++k) {
@@ -195,7 +213,7 @@ __global__ void __launch_bounds__(256, 2) k_convert_tma(const __grid_constant__ 
       }
       pending &= ~(1u << s);
       phase ^= 1u << s;
-      tma_transform(p, desc, stage_src(sm, s), stage_dst(sm, dsel), lane, warp);
+      tma_transform(kinds, hdr, desc, stage_src(sm, s), stage_dst(sm, dsel), lane, warp);
       fence_proxy_async_smem();
       __syncthreads();
       const uint64_t nt = t + kNS * G;
@@ -440,11 +458,11 @@ __global__ void k_write_offset0(char* offs, uint32_t osz, unsigned long long v) 
 
 // ----------------------------------------------------------------- batched
 
-// Every job of a batch in one persistent launch.  CTA b takes chunks of
-// kChunk consecutive global tiles in round-robin order (chunks b, b + grid,
-// ...), so its tiles increase and a jagged tile's predecessor lies either in
-// the same chunk or in a chunk another running CTA takes in the same round:
-// every look-back terminates.  Consecutive tiles of a chunk mostly share a
+// Every job of a batch in one persistent launch.  CTAs take chunks of kChunk
+// consecutive global tiles from an atomic counter, so chunks are handed out
+// in increasing order, each CTA's tiles increase, and a jagged tile's
+// predecessors were all taken earlier by running CTAs: every look-back
+// terminates.  Consecutive tiles of a chunk mostly share a
 // job, so thread 0 follows the jobs with a forward-only cursor.  Full tiles
 // of jobs with a TMA tile geometry are staged through shared memory as in
 // k_convert_tma, thread 0 deciding kNS tiles ahead; every other tile
@@ -452,6 +470,7 @@ __global__ void k_write_offset0(char* offs, uint32_t osz, unsigned long long v) 
 constexpr uint64_t kChunk = 4;
 
 struct TileSlot {
+  unsigned long long t;  // global tile, >= total_tiles: this CTA is done
   unsigned int job;
   unsigned int staged;
   unsigned int stage;
@@ -459,12 +478,8 @@ struct TileSlot {
   unsigned long long local;
 };
 
-// k-th tile of CTA b (chunks of kChunk tiles, round-robin over G CTAs).
-__device__ __forceinline__ uint64_t batch_tile(uint64_t k, uint64_t b, uint64_t G) {
-  return ((k / kChunk) * G + b) * kChunk + (k % kChunk);
-}
 
-__global__ void __launch_bounds__(256, 2) k_batch(const BatchJob* __restrict__ jobs,
+__global__ void __launch_bounds__(256, 3) k_batch(const BatchJob* __restrict__ jobs,
                                                   const unsigned long long* __restrict__ first_tile,
                                                   unsigned int njobs, unsigned long long total_tiles,
                                                   unsigned int* counter, unsigned long long* states) {
@@ -472,23 +487,36 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchJob* __restrict__ j
   __shared__ TileSlot ring[8];
   __shared__ int s_abort;
   __shared__ uint4 sdesc[MRN_MAX_COLS];
-  (void)counter;
+  __shared__ TileHdr hdr;
   char* sm = staged_smem;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint64_t G = gridDim.x, b = blockIdx.x;
   const uint32_t desc = smem_u32(sdesc);
   unsigned int desc_job = 0xffffffffu;  // job whose descriptors are in sdesc
   uint32_t seq = 0;                     // staged tiles issued (thread 0)
   uint32_t pending = 0, phase = 0;      // per stage: loads in flight, parity (thread 0)
   uint32_t dsel = 0;                    // destination buffer of the next staged tile
   unsigned int cursor = 0;              // job of the last decided tile (thread 0)
+  uint64_t next_t = 0, chunk_end = 0;   // tiles left in the current chunk (thread 0)
+  uint32_t kinds = 0;
 
-  // Thread 0: decides tile k of this CTA and issues its loads if staged.
+  // Thread 0: decides this CTA's k-th tile: the next tile of its current
+  // chunk, or of a new chunk taken from the counter (chunks are handed out
+  // in increasing order); issues its loads if staged.
   auto decide = [&](uint64_t k) {
-    const uint64_t t = batch_tile(k, b, G);
-    if (t >= total_tiles) return;
-    while (cursor + 1 < njobs && __ldg(first_tile + cursor + 1) <= t) ++cursor;
+    if (next_t == chunk_end) {
+      const uint64_t c = atomicAdd(counter, 1u);
+      next_t = c * kChunk;
+      chunk_end = next_t + kChunk;
+    }
+    const uint64_t t = next_t++;
     TileSlot ts;
+    ts.t = t;
+    if (t >= total_tiles) {
+      next_t = chunk_end = t;  // stay at the end
+      ring[k & 7] = ts;
+      return;
+    }
+    while (cursor + 1 < njobs && __ldg(first_tile + cursor + 1) <= t) ++cursor;
     ts.job = cursor;
     const BatchJob& J = jobs[ts.job];
     ts.local = t - J.tile_begin;
@@ -512,15 +540,14 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchJob* __restrict__ j
   }
   __syncthreads();
   for (uint64_t k = 0;; ++k) {
-    const uint64_t t = batch_tile(k, b, G);
-    if (t >= total_tiles) break;
     const TileSlot ts = ring[k & 7];
+    if (ts.t >= total_tiles) break;
     const BatchJob& J = jobs[ts.job];
     if (ts.staged) {
       const ConvPlan& P = J.jp.parent;
       const uint32_t s = ts.stage;
       if (ts.job != desc_job) {
-        load_sdesc(P, sdesc);
+        kinds = load_sdesc(P, sdesc, &hdr);
         desc_job = ts.job;
       }
       if (!mbar_wait_bounded(stage_bar(sm, s), ts.parity)) s_abort = 1;
@@ -531,7 +558,7 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchJob* __restrict__ j
         return;
       }
       pending &= ~(1u << s);
-      tma_transform(P, desc, stage_src(sm, s), stage_dst(sm, dsel), lane, warp);
+      tma_transform(kinds, hdr, desc, stage_src(sm, s), stage_dst(sm, dsel), lane, warp);
       fence_proxy_async_smem();
       __syncthreads();
       if (tid == 0) tma_store_tile(P, ts.local, stage_dst(sm, dsel));
