@@ -497,16 +497,31 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchJob* __restrict__ j
   uint32_t dsel = 0;                    // destination buffer of the next staged tile
   unsigned int cursor = 0;              // job of the last decided tile (thread 0)
   uint64_t next_t = 0, chunk_end = 0;   // tiles left in the current chunk (thread 0)
+  uint64_t pre_chunk = ~0ull;           // chunk taken ahead of its use (thread 0)
   uint32_t kinds = 0;
 
+  // Thread 0: takes a chunk from the counter one chunk ahead of its use and
+  // prefetches the plan of the job its first tile belongs to into L1, so
+  // the decisions for that chunk read plan fields from L1.
+  auto take_ahead = [&]() {
+    pre_chunk = atomicAdd(counter, 1u);
+    const uint64_t t = pre_chunk * kChunk;
+    if (t >= total_tiles) return;
+    unsigned int j = cursor;
+    while (j + 1 < njobs && __ldg(first_tile + j + 1) <= t) ++j;
+    const char* q = reinterpret_cast<const char*>(&jobs[j]);
+    for (uint32_t o = 0; o < sizeof(BatchJob) / 2; o += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(q + o));
+  };
+
   // Thread 0: decides this CTA's k-th tile: the next tile of its current
-  // chunk, or of a new chunk taken from the counter (chunks are handed out
-  // in increasing order); issues its loads if staged.
+  // chunk or of the chunk taken ahead (chunks are handed out in increasing
+  // order); issues its loads if staged.
   auto decide = [&](uint64_t k) {
     if (next_t == chunk_end) {
-      const uint64_t c = atomicAdd(counter, 1u);
-      next_t = c * kChunk;
+      if (pre_chunk == ~0ull) take_ahead();
+      next_t = pre_chunk * kChunk;
       chunk_end = next_t + kChunk;
+      if (next_t < total_tiles) take_ahead();
     }
     const uint64_t t = next_t++;
     TileSlot ts;
