@@ -276,7 +276,7 @@ bool side_stageable(const mrn_schema* s, const SidePlan& sp, bool is_dst) {
 // and of every AoSoA block size, whose source and destination tiles each fit
 // one stage buffer.  Leaves tg.tma = 0 when the plan cannot be staged (an
 // unaligned buffer or block, or a record too wide for a stage).
-void tile_geometry(const mrn_schema* s, ConvPlan* p) {
+void tile_geometry(const mrn_schema* s, ConvPlan* p, uint32_t stage_bytes) {
   TileGeom& g = p->tg;
   std::memset(&g, 0, sizeof(g));
   if (!side_stageable(s, p->src, false) || !side_stageable(s, p->dst, true)) return;
@@ -286,8 +286,8 @@ void tile_geometry(const mrn_schema* s, ConvPlan* p) {
     if (sp->kind == K_AOSOA) q = q / gcd_u64(q, sp->block) * sp->block;
   uint32_t T = 0;
   for (uint64_t cand = q; cand <= 4096; cand += q) {
-    if (tile_bytes(s, p->src, (uint32_t)cand, nullptr) > MRN_STAGE_BYTES ||
-        tile_bytes(s, p->dst, (uint32_t)cand, nullptr) > MRN_STAGE_BYTES)
+    if (tile_bytes(s, p->src, (uint32_t)cand, nullptr) > stage_bytes ||
+        tile_bytes(s, p->dst, (uint32_t)cand, nullptr) > stage_bytes)
       break;
     T = (uint32_t)cand;
   }
@@ -308,9 +308,11 @@ void tile_geometry(const mrn_schema* s, ConvPlan* p) {
 
 }  // namespace
 
+void plan_tiles(const mrn_schema* s, ConvPlan* p, uint32_t stage_bytes) { tile_geometry(s, p, stage_bytes); }
+
 int build_plan(const mrn_view& src, const mrn_view& dst, ConvPlan* p) {
   int rc = level_plan(src.schema, src, dst, false, src.n_records, p);
-  if (!rc) tile_geometry(src.schema, p);
+  if (!rc) tile_geometry(src.schema, p, MRN_STAGE_BYTES);
   mrn_layout a = src.layout, b = dst.layout;
   if (a.kind != MRN_AOSOA) a.block = 0;
   if (b.kind != MRN_AOSOA) b.block = 0;

@@ -78,6 +78,7 @@ int plan_job(const mrn_view& src, const mrn_view& dst, std::vector<BatchJob>* ou
   } else {
     if (src.layout.kind == MRN_AOS && dst.layout.kind == MRN_AOS) return MRN_EUNSUPPORTED;
     if ((rc = build_plan(src, dst, &j.jp.parent))) return rc;
+    plan_tiles(src.schema, &j.jp.parent, MRN_BATCH_STAGE_BYTES);
     j.kind = JOB_CONVERT;
     const LaunchShape sh = tuned_shape(j.jp.parent);
     uint32_t tr;

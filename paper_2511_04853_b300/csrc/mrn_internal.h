@@ -58,6 +58,9 @@ int status_from_bits(uint32_t bits);
 uint64_t tune_key(uint64_t hash, const mrn_layout& a, const mrn_layout& b);
 // Builds the conversion plan of a validated non-jagged view pair.
 int build_plan(const mrn_view& src, const mrn_view& dst, ConvPlan* p);
+// Recomputes the shared-memory tile geometry of a plan for stages of
+// `stage_bytes` (tg.tma = 0 when the plan cannot be staged).
+void plan_tiles(const mrn_schema* s, ConvPlan* p, uint32_t stage_bytes);
 // Builds the plan of a validated jagged view pair.
 int build_jagged_plan(const mrn_view& src, const mrn_view& dst, JagPlan* jp);
 // Alignment holes of a single-block SoA or AoSoA destination view.

@@ -261,6 +261,16 @@ __device__ __forceinline__ uint64_t read_offset(const char* offs, uint32_t osz, 
   return __ldg(reinterpret_cast<const unsigned long long*>(offs) + i);
 }
 
+// CTA-wide barrier, or (NAMED) barrier 1 over the 256 consumer threads of
+// the warp-specialized batch kernel.
+template <bool NAMED>
+__device__ __forceinline__ void cta_sync() {
+  if constexpr (NAMED)
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+  else
+    __syncthreads();
+}
+
 struct JagShared {
   unsigned long long excl[MRN_JAG_TILE + 1];
   unsigned long long beg[MRN_JAG_TILE];
@@ -275,7 +285,7 @@ struct JagShared {
 // tile's children, load-balanced over the tile's threads.  Tiles must be
 // handed out in increasing order (dynamic tile ids), so that every
 // predecessor is already running.
-template <int VP, int VC>
+template <int VP, int VC, bool NAMED = false>
 __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile, unsigned long long* st,
                                                 uint32_t* tw_all, JagShared& sh) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -302,7 +312,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
     if (lane >= o) x += y;
   }
   if (lane == 31) sh.warp[warp] = x;
-  __syncthreads();
+  cta_sync<NAMED>();
   if (warp == 0) {
     unsigned long long t = lane < 8 ? sh.warp[lane] : 0ull;
 #pragma unroll
@@ -312,7 +322,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
     }
     if (lane < 8) sh.warp[lane] = t;
   }
-  __syncthreads();
+  cta_sync<NAMED>();
   const unsigned long long excl = x - len + (warp > 0 ? sh.warp[warp - 1] : 0ull);
   const unsigned long long agg = sh.warp[7];
   sh.excl[tid] = excl;
@@ -350,7 +360,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
     }
     sh.base = prefix;
   }
-  __syncthreads();
+  cta_sync<NAMED>();
   const unsigned long long base = sh.base;
 
   // Offsets: offset_base + children before this parent.
@@ -458,149 +468,292 @@ __global__ void k_write_offset0(char* offs, uint32_t osz, unsigned long long v) 
 
 // ----------------------------------------------------------------- batched
 
-// Every job of a batch in one persistent launch.  CTAs take chunks of kChunk
-// consecutive global tiles from an atomic counter, so chunks are handed out
-// in increasing order, each CTA's tiles increase, and a jagged tile's
-// predecessors were all taken earlier by running CTAs: every look-back
-// terminates.  Consecutive tiles of a chunk mostly share a
-// job, so thread 0 follows the jobs with a forward-only cursor.  Full tiles
-// of jobs with a TMA tile geometry are staged through shared memory as in
-// k_convert_tma, thread 0 deciding kNS tiles ahead; every other tile
-// (jagged, zero-fill, partial or unstaged conversions) runs directly.
-constexpr uint64_t kChunk = 4;
+// ----------------------------------------------------------------- batched
+//
+// Every job of a batch in one persistent, warp-specialized launch of 288
+// threads per CTA.  Warp 8 (the producer; its lane 0 does the work) takes
+// chunks of kChunk consecutive global tiles from an atomic counter (chunks
+// are handed out in increasing order, so a jagged tile's predecessors are
+// all taken earlier by running CTAs and every look-back terminates), decides
+// each tile, issues the TMA loads of staged tiles kBNS stages ahead, and
+// issues their bulk stores once the consumers finish them.  Warps 0-7 (the
+// consumers) take the decided tiles in order: staged tiles are transformed
+// shared -> shared; every other tile (jagged, zero-fill, partial or unstaged
+// conversions) runs directly on global memory with a private scratch.
+// Producer and consumers meet only on mbarriers:
+//   ready[8]   ring slot written (producer -> consumers)
+//   rel[8]     ring slot read by all 8 consumer warps (before its reuse)
+//   full[s]    source stage loaded (TMA transaction count)
+//   empty[s]   source stage read by all 8 consumer warps
+//   done[d]    destination buffer written by all 8 consumer warps
+//   dfree[d]   destination buffer's bulk store has read it (producer)
+// Each stage carries its job's column descriptors, written by the producer
+// before the stage's loads.  Every wait is bounded; on expiry the CTA
+// records MRN_ETIMEOUT and stops.
+constexpr uint32_t kBStage = MRN_BATCH_STAGE_BYTES;
+constexpr uint32_t kBNS = 3;      // source stages
+constexpr uint32_t kBND = 2;      // destination buffers
+constexpr uint32_t kRing = 8;     // decided tiles in flight
+constexpr uint64_t kChunk = 2;    // consecutive tiles per counter grab
+constexpr uint32_t kBThreads = 288;
 
 struct TileSlot {
-  unsigned long long t;  // global tile, >= total_tiles: this CTA is done
+  unsigned long long t;  // global tile; >= total_tiles: no more tiles
+  unsigned long long local;
   unsigned int job;
   unsigned int staged;
-  unsigned int stage;
-  unsigned int parity;
-  unsigned long long local;
 };
 
+struct StageDesc {
+  TileHdr h;
+  unsigned int kinds;
+  unsigned int job;
+  uint4 d[MRN_MAX_COLS];
+};
 
-__global__ void __launch_bounds__(256, 3) k_batch(const BatchJob* __restrict__ jobs,
-                                                  const unsigned long long* __restrict__ first_tile,
-                                                  unsigned int njobs, unsigned long long total_tiles,
-                                                  unsigned int* counter, unsigned long long* states) {
-  extern __shared__ __align__(128) char staged_smem[];
-  __shared__ TileSlot ring[8];
-  __shared__ int s_abort;
-  __shared__ uint4 sdesc[MRN_MAX_COLS];
-  __shared__ TileHdr hdr;
-  char* sm = staged_smem;
+constexpr size_t kBScratch = 21504;  // 8 warps' lane words + JagShared
+static_assert(kBScratch >= 8 * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t) + sizeof(JagShared), "scratch");
+constexpr size_t kBOffDst = (size_t)kBNS * kBStage;
+constexpr size_t kBOffScratch = kBOffDst + (size_t)kBND * kBStage;
+constexpr size_t kBOffDesc = kBOffScratch + kBScratch;
+constexpr size_t kBOffBar = kBOffDesc + kBNS * sizeof(StageDesc);
+constexpr size_t kBNumBars = 2 * kBNS + 2 * kBND + 2 * kRing;
+constexpr size_t kBOffRing = kBOffBar + kBNumBars * 8;
+constexpr size_t kBOffFlag = kBOffRing + kRing * sizeof(TileSlot);
+constexpr size_t kBatchSmem = kBOffFlag + 16;
+
+struct BatchSmem {
+  char* base;
+  __device__ __forceinline__ char* src(uint32_t s) const { return base + (size_t)s * kBStage; }
+  __device__ __forceinline__ char* dst(uint32_t d) const { return base + kBOffDst + (size_t)d * kBStage; }
+  __device__ __forceinline__ uint32_t* scratch() const { return reinterpret_cast<uint32_t*>(base + kBOffScratch); }
+  __device__ __forceinline__ StageDesc* desc(uint32_t s) const {
+    return reinterpret_cast<StageDesc*>(base + kBOffDesc) + s;
+  }
+  __device__ __forceinline__ unsigned long long* bar(uint32_t i) const {
+    return reinterpret_cast<unsigned long long*>(base + kBOffBar) + i;
+  }
+  __device__ __forceinline__ unsigned long long* full(uint32_t s) const { return bar(s); }
+  __device__ __forceinline__ unsigned long long* empty(uint32_t s) const { return bar(kBNS + s); }
+  __device__ __forceinline__ unsigned long long* done(uint32_t d) const { return bar(2 * kBNS + d); }
+  __device__ __forceinline__ unsigned long long* dfree(uint32_t d) const { return bar(2 * kBNS + kBND + d); }
+  __device__ __forceinline__ unsigned long long* ready(uint32_t i) const { return bar(2 * kBNS + 2 * kBND + i); }
+  __device__ __forceinline__ unsigned long long* rel(uint32_t i) const {
+    return bar(2 * kBNS + 2 * kBND + kRing + i);
+  }
+  __device__ __forceinline__ TileSlot* ring(uint32_t i) const {
+    return reinterpret_cast<TileSlot*>(base + kBOffRing) + i;
+  }
+  __device__ __forceinline__ volatile int* abort_flag() const {
+    return reinterpret_cast<volatile int*>(base + kBOffFlag);
+  }
+};
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Producer: the plan's column descriptors and header into a stage's table.
+__device__ __forceinline__ void fill_stage_desc(const ConvPlan& p, StageDesc* sd, unsigned int job) {
+  if (sd->job == job) return;
+  for (uint32_t c = 0; c < p.ncols; ++c)
+    sd->d[c] = make_uint4(p.tg.col[c], p.tg.src_off[c], p.tg.dst_off[c], 0u);
+  TileHdr h;
+  h.ncols = p.ncols;
+  h.stride = p.stride;
+  h.vec = p.vec;
+  h.pad = p.tg.pad;
+  h.T = p.tg.T;
+  h.sblock = p.src.block;
+  h.sshift = p.src.block_shift;
+  h.sbb = (uint32_t)p.src.block_bytes;
+  h.dblock = p.dst.block;
+  h.dshift = p.dst.block_shift;
+  h.dbb = (uint32_t)p.dst.block_bytes;
+  sd->h = h;
+  sd->kinds = p.src.kind * 3 + p.dst.kind;
+  sd->job = job;
+}
+
+// Producer (one thread).  Returns when every decided tile is stored or the
+// batch was aborted.
+__device__ __forceinline__ void batch_producer(const BatchJob* __restrict__ jobs,
+                                               const unsigned long long* __restrict__ first_tile,
+                                               unsigned int njobs, unsigned long long total_tiles,
+                                               unsigned int* counter, const BatchSmem& m) {
+  uint64_t k_issue = 0, k_done = 0;  // tiles decided / completed (stored)
+  uint32_t c_issue = 0, c_done = 0;  // staged tiles loaded / stored
+  unsigned int cursor = 0;
+  uint64_t next_t = 0, chunk_end = 0;
+  bool ended = false, have = false;
+  TileSlot cand;                     // decided tile waiting for a free stage
+  uint32_t staged_mask = 0;          // bit (k % 32): decided tile k is staged
+  uint32_t pending = 0, phase = 0;   // stages with loads in flight / their parity
+  unsigned long long idle_since = global_ns();
+  for (;;) {
+    bool progress = false;
+    if (*m.abort_flag()) break;
+    // 1. complete the oldest decided tile: a staged tile is stored as soon
+    //    as its consumers are done with it.
+    if (k_done < k_issue) {
+      if (!((staged_mask >> (k_done & 31)) & 1)) {
+        ++k_done;
+        progress = true;
+      } else {
+        const uint32_t d = c_done % kBND;
+        if (mbar_try_wait(m.done(d), (c_done / kBND) & 1)) {
+          const TileSlot* ts = m.ring(k_done % kRing);
+          tma_store_tile(jobs[ts->job].jp.parent, ts->local, m.dst(d));
+          bulk_wait_read<0>();  // this buffer may be written again
+          mbar_arrive(m.dfree(d));
+          ++c_done;
+          ++k_done;
+          progress = true;
+        }
+      }
+    }
+    // 2. decide the next tile and issue its loads (ring slot and, when
+    //    staged, a source stage must be free).
+    if (!ended && k_issue < k_done + kRing) {
+      if (!have) {
+        if (next_t == chunk_end) {
+          next_t = (uint64_t)atomicAdd(counter, 1u) * kChunk;
+          chunk_end = next_t + kChunk;
+        }
+        cand.t = next_t++;
+        cand.staged = 0;
+        if (cand.t < total_tiles) {
+          while (cursor + 1 < njobs && __ldg(first_tile + cursor + 1) <= cand.t) ++cursor;
+          const BatchJob& J = jobs[cursor];
+          cand.job = cursor;
+          cand.local = cand.t - J.tile_begin;
+          const ConvPlan& P = J.jp.parent;
+          cand.staged = J.kind == JOB_CONVERT && P.tg.tma && (cand.local + 1) * P.tg.T <= P.n;
+        }
+        have = true;
+      }
+      bool go = true;
+      const uint32_t s = c_issue % kBNS;
+      if (k_issue >= kRing) go = mbar_try_wait(m.rel(k_issue % kRing), (uint32_t)(((k_issue / kRing) - 1) & 1));
+      if (go && cand.staged && c_issue >= kBNS) go = mbar_try_wait(m.empty(s), ((c_issue / kBNS) - 1) & 1);
+      if (go) {
+        const uint32_t slot = k_issue % kRing;
+        if (cand.staged) {
+          const ConvPlan& P = jobs[cand.job].jp.parent;
+          fill_stage_desc(P, m.desc(s), cand.job);
+          tma_load_tile(P, cand.local, m.src(s), m.full(s));
+          pending |= 1u << s;
+          phase = (phase & ~(1u << s)) | (((c_issue / kBNS) & 1) << s);
+          staged_mask |= 1u << (k_issue & 31);
+          ++c_issue;
+        } else {
+          staged_mask &= ~(1u << (k_issue & 31));
+        }
+        *m.ring(slot) = cand;
+        mbar_arrive(m.ready(slot));
+        if (cand.t >= total_tiles) ended = true;
+        ++k_issue;
+        have = false;
+        progress = true;
+      }
+    }
+    if (ended && k_done == k_issue) break;
+    if (progress) {
+      idle_since = global_ns();
+    } else {
+      if (global_ns() - idle_since > 2000000000ull) {
+        flag_error(MRN_ETIMEOUT);
+        *m.abort_flag() = 1;
+        break;
+      }
+      __nanosleep(32);
+    }
+  }
+  // loads still in flight land before the CTA may exit (bounded)
+  for (uint32_t s = 0; s < kBNS; ++s)
+    if ((pending >> s) & 1) mbar_wait_bounded(m.full(s), (phase >> s) & 1);
+  bulk_wait_all();
+}
+
+__global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restrict__ jobs,
+                                                        const unsigned long long* __restrict__ first_tile,
+                                                        unsigned int njobs, unsigned long long total_tiles,
+                                                        unsigned int* counter, unsigned long long* states) {
+  extern __shared__ __align__(128) char batch_smem[];
+  BatchSmem m{batch_smem};
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t desc = smem_u32(sdesc);
-  unsigned int desc_job = 0xffffffffu;  // job whose descriptors are in sdesc
-  uint32_t seq = 0;                     // staged tiles issued (thread 0)
-  uint32_t pending = 0, phase = 0;      // per stage: loads in flight, parity (thread 0)
-  uint32_t dsel = 0;                    // destination buffer of the next staged tile
-  unsigned int cursor = 0;              // job of the last decided tile (thread 0)
-  uint64_t next_t = 0, chunk_end = 0;   // tiles left in the current chunk (thread 0)
-  uint64_t pre_chunk = ~0ull;           // chunk taken ahead of its use (thread 0)
-  uint32_t kinds = 0;
-
-  // Thread 0: takes a chunk from the counter one chunk ahead of its use and
-  // prefetches the plan of the job its first tile belongs to into L1, so
-  // the decisions for that chunk read plan fields from L1.
-  auto take_ahead = [&]() {
-    pre_chunk = atomicAdd(counter, 1u);
-    const uint64_t t = pre_chunk * kChunk;
-    if (t >= total_tiles) return;
-    unsigned int j = cursor;
-    while (j + 1 < njobs && __ldg(first_tile + j + 1) <= t) ++j;
-    const char* q = reinterpret_cast<const char*>(&jobs[j]);
-    for (uint32_t o = 0; o < sizeof(BatchJob) / 2; o += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(q + o));
-  };
-
-  // Thread 0: decides this CTA's k-th tile: the next tile of its current
-  // chunk or of the chunk taken ahead (chunks are handed out in increasing
-  // order); issues its loads if staged.
-  auto decide = [&](uint64_t k) {
-    if (next_t == chunk_end) {
-      if (pre_chunk == ~0ull) take_ahead();
-      next_t = pre_chunk * kChunk;
-      chunk_end = next_t + kChunk;
-      if (next_t < total_tiles) take_ahead();
-    }
-    const uint64_t t = next_t++;
-    TileSlot ts;
-    ts.t = t;
-    if (t >= total_tiles) {
-      next_t = chunk_end = t;  // stay at the end
-      ring[k & 7] = ts;
-      return;
-    }
-    while (cursor + 1 < njobs && __ldg(first_tile + cursor + 1) <= t) ++cursor;
-    ts.job = cursor;
-    const BatchJob& J = jobs[ts.job];
-    ts.local = t - J.tile_begin;
-    const ConvPlan& P = J.jp.parent;
-    ts.staged = J.kind == JOB_CONVERT && P.tg.tma && (ts.local + 1) * P.tg.T <= P.n;
-    ts.stage = seq % kNS;
-    ts.parity = (seq / kNS) & 1;
-    if (ts.staged) {
-      tma_load_tile(P, ts.local, stage_src(sm, ts.stage), stage_bar(sm, ts.stage));
-      pending |= 1u << ts.stage;
-      phase = (phase & ~(1u << ts.stage)) | (ts.parity << ts.stage);
-      ++seq;
-    }
-    ring[k & 7] = ts;
-  };
-
   if (tid == 0) {
-    init_stage_bars(sm);
-    s_abort = 0;
-    for (uint32_t k = 0; k < kNS; ++k) decide(k);
+    for (uint32_t s = 0; s < kBNS; ++s) {
+      mbar_init(m.full(s), 1);
+      mbar_init(m.empty(s), 8);
+      m.desc(s)->job = 0xffffffffu;
+    }
+    for (uint32_t d = 0; d < kBND; ++d) {
+      mbar_init(m.done(d), 8);
+      mbar_init(m.dfree(d), 1);
+    }
+    for (uint32_t i = 0; i < kRing; ++i) {
+      mbar_init(m.ready(i), 1);
+      mbar_init(m.rel(i), 8);
+    }
+    *m.abort_flag() = 0;
+    fence_mbar_init();
   }
   __syncthreads();
+  if (warp == 8) {
+    if (lane == 0) batch_producer(jobs, first_tile, njobs, total_tiles, counter, m);
+    return;
+  }
+  // consumers
+  uint32_t* scratch = m.scratch();
+  uint32_t* tw = scratch + warp * MRN_TW_WORDS_PER_WARP;
+  JagShared& sh = *reinterpret_cast<JagShared*>(scratch + 8 * MRN_TW_WORDS_PER_WARP);
+  uint32_t c = 0;  // staged tiles consumed
   for (uint64_t k = 0;; ++k) {
-    const TileSlot ts = ring[k & 7];
-    if (ts.t >= total_tiles) break;
-    const BatchJob& J = jobs[ts.job];
+    const uint32_t slot = k % kRing;
+    if (!mbar_wait_bounded(m.ready(slot), (uint32_t)((k / kRing) & 1))) {
+      flag_error(MRN_ETIMEOUT);
+      *m.abort_flag() = 1;
+      return;
+    }
+    const TileSlot ts = *m.ring(slot);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(m.rel(slot));
+    if (ts.t >= total_tiles) return;
     if (ts.staged) {
-      const ConvPlan& P = J.jp.parent;
-      const uint32_t s = ts.stage;
-      if (ts.job != desc_job) {
-        kinds = load_sdesc(P, sdesc, &hdr);
-        desc_job = ts.job;
-      }
-      if (!mbar_wait_bounded(stage_bar(sm, s), ts.parity)) s_abort = 1;
-      if (tid == 0) bulk_wait_read<1>();
-      __syncthreads();
-      if (s_abort) {
-        tma_abort(sm, pending, phase);
+      const uint32_t s = c % kBNS, d = c % kBND;
+      bool ok = mbar_wait_bounded(m.full(s), (c / kBNS) & 1);
+      if (ok && c >= kBND) ok = mbar_wait_bounded(m.dfree(d), ((c / kBND) - 1) & 1);
+      if (!ok || *m.abort_flag()) {
+        flag_error(MRN_ETIMEOUT);
+        *m.abort_flag() = 1;
         return;
       }
-      pending &= ~(1u << s);
-      tma_transform(kinds, hdr, desc, stage_src(sm, s), stage_dst(sm, dsel), lane, warp);
+      const StageDesc* sd = m.desc(s);
+      tma_transform(sd->kinds, sd->h, smem_u32(sd->d), m.src(s), m.dst(d), lane, warp);
       fence_proxy_async_smem();
-      __syncthreads();
-      if (tid == 0) tma_store_tile(P, ts.local, stage_dst(sm, dsel));
-      dsel ^= 1;
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(m.empty(s));
+        mbar_arrive(m.done(d));
+      }
+      ++c;
     } else {
-      if (tid == 0) bulk_wait_read<0>();  // the scratch aliases the destination buffers
-      __syncthreads();
-      uint32_t* tw_all = direct_scratch(sm);
-      uint32_t* tw = tw_all + warp * MRN_TW_WORDS_PER_WARP;
-      JagShared& sh = *reinterpret_cast<JagShared*>(tw_all + 8 * MRN_TW_WORDS_PER_WARP);
+      const BatchJob& J = jobs[ts.job];
       const unsigned long long local = ts.local;
       if (J.kind == JOB_CONVERT) {
         const uint32_t tr = J.tile_records;
         conv_range<0>(J.jp.parent, local * tr, (local + 1) * tr, tw, lane, warp, 8);
       } else if (J.kind == JOB_JAG_A2S) {
-        jagged_a2s_tile<0, 0>(J.jp, local, states + J.tile_begin, tw_all, sh);
+        jagged_a2s_tile<0, 0, true>(J.jp, local, states + J.tile_begin, scratch, sh);
       } else if (J.kind == JOB_JAG_S2A) {
         jagged_s2a_group<0, 0>(J.jp, local * 8 + warp, J.parent_groups, tw, lane);
       } else {
         const uint64_t q = local * 256 + tid;
         if (q < J.gp.nblocks * J.gp.ngaps) zero_gap_item(J.gp, q);
       }
-      __syncthreads();
     }
-    if (tid == 0) decide(k + kNS);
   }
-  if (tid == 0) bulk_wait_all();
 }
 
 // ================================================================== host
@@ -825,8 +978,11 @@ int launch_jagged_count(const ConvPlan& parent, uint64_t* dev_total, void* strea
 
 int batch_occupancy() {
   const void* fn = reinterpret_cast<const void*>(&k_batch);
-  allow_tma_smem(fn);
-  return occupancy(fn, 256, kTmaSmem);
+  static std::once_flag once;
+  std::call_once(once, [fn] {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem);
+  });
+  return occupancy(fn, kBThreads, kBatchSmem);
 }
 
 int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, unsigned int njobs,
@@ -838,8 +994,8 @@ int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, uns
   const uint64_t cap = (uint64_t)device_sm_count() * (uint64_t)per_sm;
   const uint64_t chunks = (total_tiles + kChunk - 1) / kChunk;
   const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(cap, chunks));
-  k_batch<<<grid, 256, kTmaSmem, static_cast<cudaStream_t>(stream)>>>(jobs, first_tile, njobs, total_tiles,
-                                                                        counter, states);
+  k_batch<<<grid, kBThreads, kBatchSmem, static_cast<cudaStream_t>(stream)>>>(jobs, first_tile, njobs,
+                                                                                total_tiles, counter, states);
   return cuda_status(cudaGetLastError());
 }
 
