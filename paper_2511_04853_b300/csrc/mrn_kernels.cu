@@ -261,15 +261,12 @@ __device__ __forceinline__ uint64_t read_offset(const char* offs, uint32_t osz, 
   return __ldg(reinterpret_cast<const unsigned long long*>(offs) + i);
 }
 
-// CTA-wide barrier, or (NAMED) barrier 1 over the 256 consumer threads of
-// the warp-specialized batch kernel.
-template <bool NAMED>
-__device__ __forceinline__ void cta_sync() {
-  if constexpr (NAMED)
-    asm volatile("bar.sync 1, 256;" ::: "memory");
-  else
-    __syncthreads();
-}
+// Barrier of the 256 threads running a jagged tile: __syncthreads() in the
+// per-call kernel; a bounded mbarrier barrier among the consumer warps in the
+// batch kernel (see ConsumerSync).
+struct CtaSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
 
 struct JagShared {
   unsigned long long excl[MRN_JAG_TILE + 1];
@@ -285,9 +282,9 @@ struct JagShared {
 // tile's children, load-balanced over the tile's threads.  Tiles must be
 // handed out in increasing order (dynamic tile ids), so that every
 // predecessor is already running.
-template <int VP, int VC, bool NAMED = false>
+template <int VP, int VC, class Sync = CtaSync>
 __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile, unsigned long long* st,
-                                                uint32_t* tw_all, JagShared& sh) {
+                                                uint32_t* tw_all, JagShared& sh, const Sync& sync = Sync()) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t* tw = tw_all + warp * MRN_TW_WORDS_PER_WARP;
   const ConvPlan& P = jp.parent;
@@ -312,7 +309,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
     if (lane >= o) x += y;
   }
   if (lane == 31) sh.warp[warp] = x;
-  cta_sync<NAMED>();
+  sync();
   if (warp == 0) {
     unsigned long long t = lane < 8 ? sh.warp[lane] : 0ull;
 #pragma unroll
@@ -322,7 +319,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
     }
     if (lane < 8) sh.warp[lane] = t;
   }
-  cta_sync<NAMED>();
+  sync();
   const unsigned long long excl = x - len + (warp > 0 ? sh.warp[warp - 1] : 0ull);
   const unsigned long long agg = sh.warp[7];
   sh.excl[tid] = excl;
@@ -360,7 +357,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
     }
     sh.base = prefix;
   }
-  cta_sync<NAMED>();
+  sync();
   const unsigned long long base = sh.base;
 
   // Offsets: offset_base + children before this parent.
@@ -475,21 +472,21 @@ __global__ void k_write_offset0(char* offs, uint32_t osz, unsigned long long v) 
 // chunks of kChunk consecutive global tiles from an atomic counter (chunks
 // are handed out in increasing order, so a jagged tile's predecessors are
 // all taken earlier by running CTAs and every look-back terminates), decides
-// each tile, issues the TMA loads of staged tiles kBNS stages ahead, and
-// issues their bulk stores once the consumers finish them.  Warps 0-7 (the
-// consumers) take the decided tiles in order: staged tiles are transformed
-// shared -> shared; every other tile (jagged, zero-fill, partial or unstaged
-// conversions) runs directly on global memory with a private scratch.
-// Producer and consumers meet only on mbarriers:
-//   ready[8]   ring slot written (producer -> consumers)
-//   rel[8]     ring slot read by all 8 consumer warps (before its reuse)
-//   full[s]    source stage loaded (TMA transaction count)
-//   empty[s]   source stage read by all 8 consumer warps
-//   done[d]    destination buffer written by all 8 consumer warps
-//   dfree[d]   destination buffer's bulk store has read it (producer)
+// each tile and issues the TMA loads of staged tiles up to kBNS stages ahead.
+// Warps 0-7 (the consumers) take the decided tiles in order: staged tiles
+// are transformed shared -> shared and written back with bulk stores issued
+// by consumer thread 0; every other tile (jagged, zero-fill, partial or
+// unstaged conversions) runs directly on global memory with a private
+// scratch.  Producer and consumers meet only on mbarriers:
+//   cbar       barrier of the 8 consumer warps
+//   ready[i]   ring slot i written (producer -> consumers)
+//   rel[i]     ring slot i read by all 8 consumer warps (before its reuse)
+//   full[s]    source stage s loaded (TMA transaction count)
+//   empty[s]   source stage s read by all 8 consumer warps
 // Each stage carries its job's column descriptors, written by the producer
-// before the stage's loads.  Every wait is bounded; on expiry the CTA
-// records MRN_ETIMEOUT and stops.
+// before the stage's loads.  Every wait is bounded; on expiry the warp that
+// saw it records MRN_ETIMEOUT and stops, and the others follow at their next
+// (bounded) wait.
 constexpr uint32_t kBStage = MRN_BATCH_STAGE_BYTES;
 constexpr uint32_t kBNS = 3;      // source stages
 constexpr uint32_t kBND = 2;      // destination buffers
@@ -517,7 +514,7 @@ constexpr size_t kBOffDst = (size_t)kBNS * kBStage;
 constexpr size_t kBOffScratch = kBOffDst + (size_t)kBND * kBStage;
 constexpr size_t kBOffDesc = kBOffScratch + kBScratch;
 constexpr size_t kBOffBar = kBOffDesc + kBNS * sizeof(StageDesc);
-constexpr size_t kBNumBars = 2 * kBNS + 2 * kBND + 2 * kRing;
+constexpr size_t kBNumBars = 2 * kBNS + 2 * kRing + 1;
 constexpr size_t kBOffRing = kBOffBar + kBNumBars * 8;
 constexpr size_t kBOffFlag = kBOffRing + kRing * sizeof(TileSlot);
 constexpr size_t kBatchSmem = kBOffFlag + 16;
@@ -535,12 +532,9 @@ struct BatchSmem {
   }
   __device__ __forceinline__ unsigned long long* full(uint32_t s) const { return bar(s); }
   __device__ __forceinline__ unsigned long long* empty(uint32_t s) const { return bar(kBNS + s); }
-  __device__ __forceinline__ unsigned long long* done(uint32_t d) const { return bar(2 * kBNS + d); }
-  __device__ __forceinline__ unsigned long long* dfree(uint32_t d) const { return bar(2 * kBNS + kBND + d); }
-  __device__ __forceinline__ unsigned long long* ready(uint32_t i) const { return bar(2 * kBNS + 2 * kBND + i); }
-  __device__ __forceinline__ unsigned long long* rel(uint32_t i) const {
-    return bar(2 * kBNS + 2 * kBND + kRing + i);
-  }
+  __device__ __forceinline__ unsigned long long* ready(uint32_t i) const { return bar(2 * kBNS + i); }
+  __device__ __forceinline__ unsigned long long* rel(uint32_t i) const { return bar(2 * kBNS + kRing + i); }
+  __device__ __forceinline__ unsigned long long* cbar() const { return bar(2 * kBNS + 2 * kRing); }
   __device__ __forceinline__ TileSlot* ring(uint32_t i) const {
     return reinterpret_cast<TileSlot*>(base + kBOffRing) + i;
   }
@@ -552,6 +546,21 @@ struct BatchSmem {
 __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+
+// Barrier of the 8 consumer warps on an mbarrier (one arrival per warp,
+// bounded wait).  Every consumer thread passes the same sequence of these
+// barriers and counts them in `phase`; a failed wait clears `ok`.
+struct ConsumerSync {
+  unsigned long long* bar;
+  uint32_t* phase;
+  bool* ok;
+  __device__ __forceinline__ void operator()() const {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
+    if (!mbar_wait_bounded(bar, *phase & 1)) *ok = false;
+    ++*phase;
+  }
+};
 
 // Producer: the plan's column descriptors and header into a stage's table.
 __device__ __forceinline__ void fill_stage_desc(const ConvPlan& p, StageDesc* sd, unsigned int job) {
@@ -575,90 +584,58 @@ __device__ __forceinline__ void fill_stage_desc(const ConvPlan& p, StageDesc* sd
   sd->job = job;
 }
 
-// Producer (one thread).  Returns when every decided tile is stored or the
-// batch was aborted.
+// Producer (one thread): decides tiles in order and issues the loads of
+// staged ones; returns after publishing the end-of-work slot (or on abort,
+// once its loads in flight have landed).
 __device__ __forceinline__ void batch_producer(const BatchJob* __restrict__ jobs,
                                                const unsigned long long* __restrict__ first_tile,
                                                unsigned int njobs, unsigned long long total_tiles,
                                                unsigned int* counter, const BatchSmem& m) {
-  uint64_t k_issue = 0, k_done = 0;  // tiles decided / completed (stored)
-  uint32_t c_issue = 0, c_done = 0;  // staged tiles loaded / stored
+  uint64_t k_issue = 0;  // tiles decided
+  uint32_t c_issue = 0;  // staged tiles loaded
   unsigned int cursor = 0;
   uint64_t next_t = 0, chunk_end = 0;
-  bool ended = false, have = false;
-  TileSlot cand;                     // decided tile waiting for a free stage
-  uint32_t staged_mask = 0;          // bit (k % 32): decided tile k is staged
-  uint32_t pending = 0, phase = 0;   // stages with loads in flight / their parity
+  bool have = false;
+  TileSlot cand;
+  cand.t = 0;
   unsigned long long idle_since = global_ns();
   for (;;) {
-    bool progress = false;
     if (*m.abort_flag()) break;
-    // 1. complete the oldest decided tile: a staged tile is stored as soon
-    //    as its consumers are done with it.
-    if (k_done < k_issue) {
-      if (!((staged_mask >> (k_done & 31)) & 1)) {
-        ++k_done;
-        progress = true;
-      } else {
-        const uint32_t d = c_done % kBND;
-        if (mbar_try_wait(m.done(d), (c_done / kBND) & 1)) {
-          const TileSlot* ts = m.ring(k_done % kRing);
-          tma_store_tile(jobs[ts->job].jp.parent, ts->local, m.dst(d));
-          bulk_wait_read<0>();  // this buffer may be written again
-          mbar_arrive(m.dfree(d));
-          ++c_done;
-          ++k_done;
-          progress = true;
-        }
+    if (!have) {
+      if (next_t == chunk_end) {
+        next_t = (uint64_t)atomicAdd(counter, 1u) * kChunk;
+        chunk_end = next_t + kChunk;
       }
+      cand.t = next_t++;
+      cand.staged = 0;
+      cand.job = 0;
+      cand.local = 0;
+      if (cand.t < total_tiles) {
+        while (cursor + 1 < njobs && __ldg(first_tile + cursor + 1) <= cand.t) ++cursor;
+        const BatchJob& J = jobs[cursor];
+        cand.job = cursor;
+        cand.local = cand.t - J.tile_begin;
+        const ConvPlan& P = J.jp.parent;
+        cand.staged = J.kind == JOB_CONVERT && P.tg.tma && (cand.local + 1) * P.tg.T <= P.n;
+      }
+      have = true;
     }
-    // 2. decide the next tile and issue its loads (ring slot and, when
-    //    staged, a source stage must be free).
-    if (!ended && k_issue < k_done + kRing) {
-      if (!have) {
-        if (next_t == chunk_end) {
-          next_t = (uint64_t)atomicAdd(counter, 1u) * kChunk;
-          chunk_end = next_t + kChunk;
-        }
-        cand.t = next_t++;
-        cand.staged = 0;
-        if (cand.t < total_tiles) {
-          while (cursor + 1 < njobs && __ldg(first_tile + cursor + 1) <= cand.t) ++cursor;
-          const BatchJob& J = jobs[cursor];
-          cand.job = cursor;
-          cand.local = cand.t - J.tile_begin;
-          const ConvPlan& P = J.jp.parent;
-          cand.staged = J.kind == JOB_CONVERT && P.tg.tma && (cand.local + 1) * P.tg.T <= P.n;
-        }
-        have = true;
+    const uint32_t slot = k_issue % kRing;
+    const uint32_t s = c_issue % kBNS;
+    bool go = k_issue < kRing || mbar_try_wait(m.rel(slot), (uint32_t)(((k_issue / kRing) - 1) & 1));
+    if (go && cand.staged && c_issue >= kBNS) go = mbar_try_wait(m.empty(s), ((c_issue / kBNS) - 1) & 1);
+    if (go) {
+      if (cand.staged) {
+        const ConvPlan& P = jobs[cand.job].jp.parent;
+        fill_stage_desc(P, m.desc(s), cand.job);
+        tma_load_tile(P, cand.local, m.src(s), m.full(s));
+        ++c_issue;
       }
-      bool go = true;
-      const uint32_t s = c_issue % kBNS;
-      if (k_issue >= kRing) go = mbar_try_wait(m.rel(k_issue % kRing), (uint32_t)(((k_issue / kRing) - 1) & 1));
-      if (go && cand.staged && c_issue >= kBNS) go = mbar_try_wait(m.empty(s), ((c_issue / kBNS) - 1) & 1);
-      if (go) {
-        const uint32_t slot = k_issue % kRing;
-        if (cand.staged) {
-          const ConvPlan& P = jobs[cand.job].jp.parent;
-          fill_stage_desc(P, m.desc(s), cand.job);
-          tma_load_tile(P, cand.local, m.src(s), m.full(s));
-          pending |= 1u << s;
-          phase = (phase & ~(1u << s)) | (((c_issue / kBNS) & 1) << s);
-          staged_mask |= 1u << (k_issue & 31);
-          ++c_issue;
-        } else {
-          staged_mask &= ~(1u << (k_issue & 31));
-        }
-        *m.ring(slot) = cand;
-        mbar_arrive(m.ready(slot));
-        if (cand.t >= total_tiles) ended = true;
-        ++k_issue;
-        have = false;
-        progress = true;
-      }
-    }
-    if (ended && k_done == k_issue) break;
-    if (progress) {
+      *m.ring(slot) = cand;
+      mbar_arrive(m.ready(slot));
+      ++k_issue;
+      have = false;
+      if (cand.t >= total_tiles) return;
       idle_since = global_ns();
     } else {
       if (global_ns() - idle_since > 2000000000ull) {
@@ -666,13 +643,12 @@ __device__ __forceinline__ void batch_producer(const BatchJob* __restrict__ jobs
         *m.abort_flag() = 1;
         break;
       }
-      __nanosleep(32);
+      __nanosleep(20);
     }
   }
-  // loads still in flight land before the CTA may exit (bounded)
-  for (uint32_t s = 0; s < kBNS; ++s)
-    if ((pending >> s) & 1) mbar_wait_bounded(m.full(s), (phase >> s) & 1);
-  bulk_wait_all();
+  // aborted: the most recent loads land before the CTA may exit (bounded)
+  for (uint32_t q = (c_issue > kBNS ? c_issue - kBNS : 0); q < c_issue; ++q)
+    mbar_wait_bounded(m.full(q % kBNS), (q / kBNS) & 1);
 }
 
 __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restrict__ jobs,
@@ -688,14 +664,11 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
       mbar_init(m.empty(s), 8);
       m.desc(s)->job = 0xffffffffu;
     }
-    for (uint32_t d = 0; d < kBND; ++d) {
-      mbar_init(m.done(d), 8);
-      mbar_init(m.dfree(d), 1);
-    }
     for (uint32_t i = 0; i < kRing; ++i) {
       mbar_init(m.ready(i), 1);
       mbar_init(m.rel(i), 8);
     }
+    mbar_init(m.cbar(), 8);
     *m.abort_flag() = 0;
     fence_mbar_init();
   }
@@ -708,44 +681,44 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
   uint32_t* scratch = m.scratch();
   uint32_t* tw = scratch + warp * MRN_TW_WORDS_PER_WARP;
   JagShared& sh = *reinterpret_cast<JagShared*>(scratch + 8 * MRN_TW_WORDS_PER_WARP);
+  uint32_t cphase = 0;
+  bool ok = true;
+  const ConsumerSync sync{m.cbar(), &cphase, &ok};
   uint32_t c = 0;  // staged tiles consumed
   for (uint64_t k = 0;; ++k) {
     const uint32_t slot = k % kRing;
-    if (!mbar_wait_bounded(m.ready(slot), (uint32_t)((k / kRing) & 1))) {
-      flag_error(MRN_ETIMEOUT);
-      *m.abort_flag() = 1;
-      return;
-    }
+    if (!mbar_wait_bounded(m.ready(slot), (uint32_t)((k / kRing) & 1))) ok = false;
     const TileSlot ts = *m.ring(slot);
     __syncwarp();
     if (lane == 0) mbar_arrive(m.rel(slot));
-    if (ts.t >= total_tiles) return;
+    if (!ok || *m.abort_flag()) break;
     if (ts.staged) {
       const uint32_t s = c % kBNS, d = c % kBND;
-      bool ok = mbar_wait_bounded(m.full(s), (c / kBNS) & 1);
-      if (ok && c >= kBND) ok = mbar_wait_bounded(m.dfree(d), ((c / kBND) - 1) & 1);
-      if (!ok || *m.abort_flag()) {
-        flag_error(MRN_ETIMEOUT);
-        *m.abort_flag() = 1;
-        return;
+      if (!mbar_wait_bounded(m.full(s), (c / kBNS) & 1)) {
+        ok = false;
+        break;
       }
+      if (tid == 0) bulk_wait_read<1>();  // destination buffer d is free again
+      sync();
       const StageDesc* sd = m.desc(s);
       tma_transform(sd->kinds, sd->h, smem_u32(sd->d), m.src(s), m.dst(d), lane, warp);
       fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(m.empty(s));
-        mbar_arrive(m.done(d));
-      }
+      if (lane == 0) mbar_arrive(m.empty(s));
+      sync();
+      if (!ok) break;
+      if (tid == 0) tma_store_tile(jobs[ts.job].jp.parent, ts.local, m.dst(d));
       ++c;
     } else {
+      if (ts.t >= total_tiles) break;
       const BatchJob& J = jobs[ts.job];
       const unsigned long long local = ts.local;
       if (J.kind == JOB_CONVERT) {
         const uint32_t tr = J.tile_records;
         conv_range<0>(J.jp.parent, local * tr, (local + 1) * tr, tw, lane, warp, 8);
       } else if (J.kind == JOB_JAG_A2S) {
-        jagged_a2s_tile<0, 0, true>(J.jp, local, states + J.tile_begin, scratch, sh);
+        jagged_a2s_tile<0, 0, ConsumerSync>(J.jp, local, states + J.tile_begin, scratch, sh, sync);
+        if (!ok) break;
       } else if (J.kind == JOB_JAG_S2A) {
         jagged_s2a_group<0, 0>(J.jp, local * 8 + warp, J.parent_groups, tw, lane);
       } else {
@@ -754,6 +727,11 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
       }
     }
   }
+  if (!ok) {
+    if (lane == 0) flag_error(MRN_ETIMEOUT);
+    *m.abort_flag() = 1;
+  }
+  if (tid == 0) bulk_wait_all();
 }
 
 // ================================================================== host
