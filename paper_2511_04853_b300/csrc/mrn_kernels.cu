@@ -467,32 +467,35 @@ __global__ void k_write_offset0(char* offs, uint32_t osz, unsigned long long v) 
 
 // ----------------------------------------------------------------- batched
 //
-// Every job of a batch in one persistent, warp-specialized launch of 288
-// threads per CTA.  Warp 8 (the producer; its lane 0 does the work) takes
-// chunks of kChunk consecutive global tiles from an atomic counter (chunks
-// are handed out in increasing order, so a jagged tile's predecessors are
-// all taken earlier by running CTAs and every look-back terminates), decides
-// each tile and issues the TMA loads of staged tiles up to kBNS stages ahead.
-// Warps 0-7 (the consumers) take the decided tiles in order: staged tiles
-// are transformed shared -> shared and written back with bulk stores issued
-// by consumer thread 0; every other tile (jagged, zero-fill, partial or
-// unstaged conversions) runs directly on global memory with a private
-// scratch.  Producer and consumers meet only on mbarriers:
-//   cbar       barrier of the 8 consumer warps
-//   ready[i]   ring slot i written (producer -> consumers)
-//   rel[i]     ring slot i read by all 8 consumer warps (before its reuse)
-//   full[s]    source stage s loaded (TMA transaction count)
-//   empty[s]   source stage s read by all 8 consumer warps
-// Each stage carries its job's column descriptors, written by the producer
+// Every job of a batch in one persistent, warp-specialized launch of 320
+// threads per CTA.
+//  - Warp 8 (loader; lane 0 works) takes chunks of kChunk consecutive global
+//    tiles from an atomic counter (chunks are handed out in increasing order,
+//    so a jagged tile's predecessors are all taken earlier by running CTAs
+//    and every look-back terminates), decides each tile and issues the TMA
+//    loads of staged tiles up to kBNS stages ahead.
+//  - Warps 0-7 (consumers) take the decided tiles in order.  A staged tile
+//    is transformed shared -> shared, each warp on its own records; every
+//    other tile (jagged, zero-fill, partial or unstaged conversions) runs
+//    directly on global memory with a private scratch.
+//  - Warp 9 (storer; lane 0 works) writes each finished staged tile back
+//    with bulk stores and frees its destination buffer once they have read
+//    it.
+// The warps meet only on mbarriers:
+//   ready[i] / rel[i]   ring slot i written / read by all consumer warps
+//   full[s] / empty[s]  source stage s loaded / read by all consumer warps
+//   done[d] / dfree[d]  destination buffer d written / read by its stores
+//   cbar                barrier of the consumer warps (jagged tiles only)
+// Each stage carries its job's column descriptors, written by the loader
 // before the stage's loads.  Every wait is bounded; on expiry the warp that
-// saw it records MRN_ETIMEOUT and stops, and the others follow at their next
-// (bounded) wait.
+// saw it records MRN_ETIMEOUT and stops, and the others follow.
 constexpr uint32_t kBStage = MRN_BATCH_STAGE_BYTES;
 constexpr uint32_t kBNS = 3;      // source stages
 constexpr uint32_t kBND = 2;      // destination buffers
 constexpr uint32_t kRing = 8;     // decided tiles in flight
+constexpr uint32_t kSQ = 8;       // staged tiles between loader and storer
 constexpr uint64_t kChunk = 2;    // consecutive tiles per counter grab
-constexpr uint32_t kBThreads = 288;
+constexpr uint32_t kBThreads = 320;
 
 struct TileSlot {
   unsigned long long t;  // global tile; >= total_tiles: no more tiles
@@ -508,15 +511,22 @@ struct StageDesc {
   uint4 d[MRN_MAX_COLS];
 };
 
+struct StoreItem {
+  unsigned long long local;
+  unsigned int job;
+  unsigned int pad;
+};
+
 constexpr size_t kBScratch = 21504;  // 8 warps' lane words + JagShared
 static_assert(kBScratch >= 8 * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t) + sizeof(JagShared), "scratch");
 constexpr size_t kBOffDst = (size_t)kBNS * kBStage;
 constexpr size_t kBOffScratch = kBOffDst + (size_t)kBND * kBStage;
 constexpr size_t kBOffDesc = kBOffScratch + kBScratch;
 constexpr size_t kBOffBar = kBOffDesc + kBNS * sizeof(StageDesc);
-constexpr size_t kBNumBars = 2 * kBNS + 2 * kRing + 1;
+constexpr size_t kBNumBars = 2 * kBNS + 2 * kBND + 2 * kRing + 1;
 constexpr size_t kBOffRing = kBOffBar + kBNumBars * 8;
-constexpr size_t kBOffFlag = kBOffRing + kRing * sizeof(TileSlot);
+constexpr size_t kBOffSQ = kBOffRing + kRing * sizeof(TileSlot);
+constexpr size_t kBOffFlag = kBOffSQ + kSQ * sizeof(StoreItem);
 constexpr size_t kBatchSmem = kBOffFlag + 16;
 
 struct BatchSmem {
@@ -532,15 +542,22 @@ struct BatchSmem {
   }
   __device__ __forceinline__ unsigned long long* full(uint32_t s) const { return bar(s); }
   __device__ __forceinline__ unsigned long long* empty(uint32_t s) const { return bar(kBNS + s); }
-  __device__ __forceinline__ unsigned long long* ready(uint32_t i) const { return bar(2 * kBNS + i); }
-  __device__ __forceinline__ unsigned long long* rel(uint32_t i) const { return bar(2 * kBNS + kRing + i); }
-  __device__ __forceinline__ unsigned long long* cbar() const { return bar(2 * kBNS + 2 * kRing); }
+  __device__ __forceinline__ unsigned long long* done(uint32_t d) const { return bar(2 * kBNS + d); }
+  __device__ __forceinline__ unsigned long long* dfree(uint32_t d) const { return bar(2 * kBNS + kBND + d); }
+  __device__ __forceinline__ unsigned long long* ready(uint32_t i) const { return bar(2 * kBNS + 2 * kBND + i); }
+  __device__ __forceinline__ unsigned long long* rel(uint32_t i) const {
+    return bar(2 * kBNS + 2 * kBND + kRing + i);
+  }
+  __device__ __forceinline__ unsigned long long* cbar() const { return bar(2 * kBNS + 2 * kBND + 2 * kRing); }
   __device__ __forceinline__ TileSlot* ring(uint32_t i) const {
     return reinterpret_cast<TileSlot*>(base + kBOffRing) + i;
   }
-  __device__ __forceinline__ volatile int* abort_flag() const {
-    return reinterpret_cast<volatile int*>(base + kBOffFlag);
+  __device__ __forceinline__ StoreItem* sq(uint32_t i) const {
+    return reinterpret_cast<StoreItem*>(base + kBOffSQ) + i;
   }
+  // [0] abort, [1] loader finished, [2] staged tiles issued in total,
+  // [3] tiles decided so far (the storer's sign that the loader is alive)
+  __device__ __forceinline__ volatile int* flags() const { return reinterpret_cast<volatile int*>(base + kBOffFlag); }
 };
 
 __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
@@ -562,7 +579,7 @@ struct ConsumerSync {
   }
 };
 
-// Producer: the plan's column descriptors and header into a stage's table.
+// Loader: the plan's column descriptors and header into a stage's table.
 __device__ __forceinline__ void fill_stage_desc(const ConvPlan& p, StageDesc* sd, unsigned int job) {
   if (sd->job == job) return;
   for (uint32_t c = 0; c < p.ncols; ++c)
@@ -584,13 +601,13 @@ __device__ __forceinline__ void fill_stage_desc(const ConvPlan& p, StageDesc* sd
   sd->job = job;
 }
 
-// Producer (one thread): decides tiles in order and issues the loads of
-// staged ones; returns after publishing the end-of-work slot (or on abort,
-// once its loads in flight have landed).
-__device__ __forceinline__ void batch_producer(const BatchJob* __restrict__ jobs,
-                                               const unsigned long long* __restrict__ first_tile,
-                                               unsigned int njobs, unsigned long long total_tiles,
-                                               unsigned int* counter, const BatchSmem& m) {
+// Loader (one thread): decides tiles in order and issues the loads of
+// staged ones; returns after publishing the end-of-work slot, or on abort
+// once its loads in flight have landed.
+__device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
+                                             const unsigned long long* __restrict__ first_tile,
+                                             unsigned int njobs, unsigned long long total_tiles,
+                                             unsigned int* counter, const BatchSmem& m) {
   uint64_t k_issue = 0;  // tiles decided
   uint32_t c_issue = 0;  // staged tiles loaded
   unsigned int cursor = 0;
@@ -600,7 +617,7 @@ __device__ __forceinline__ void batch_producer(const BatchJob* __restrict__ jobs
   cand.t = 0;
   unsigned long long idle_since = global_ns();
   for (;;) {
-    if (*m.abort_flag()) break;
+    if (m.flags()[0]) break;
     if (!have) {
       if (next_t == chunk_end) {
         next_t = (uint64_t)atomicAdd(counter, 1u) * kChunk;
@@ -627,20 +644,31 @@ __device__ __forceinline__ void batch_producer(const BatchJob* __restrict__ jobs
     if (go) {
       if (cand.staged) {
         const ConvPlan& P = jobs[cand.job].jp.parent;
+        StoreItem it;
+        it.local = cand.local;
+        it.job = cand.job;
+        it.pad = 0;
+        *m.sq(c_issue % kSQ) = it;
         fill_stage_desc(P, m.desc(s), cand.job);
         tma_load_tile(P, cand.local, m.src(s), m.full(s));
         ++c_issue;
       }
       *m.ring(slot) = cand;
+      if (cand.t >= total_tiles) {
+        m.flags()[2] = (int)c_issue;
+        __threadfence_block();
+        m.flags()[1] = 1;
+      }
       mbar_arrive(m.ready(slot));
       ++k_issue;
+      m.flags()[3] = (int)k_issue;
       have = false;
       if (cand.t >= total_tiles) return;
       idle_since = global_ns();
     } else {
       if (global_ns() - idle_since > 2000000000ull) {
         flag_error(MRN_ETIMEOUT);
-        *m.abort_flag() = 1;
+        m.flags()[0] = 1;
         break;
       }
       __nanosleep(20);
@@ -649,6 +677,43 @@ __device__ __forceinline__ void batch_producer(const BatchJob* __restrict__ jobs
   // aborted: the most recent loads land before the CTA may exit (bounded)
   for (uint32_t q = (c_issue > kBNS ? c_issue - kBNS : 0); q < c_issue; ++q)
     mbar_wait_bounded(m.full(q % kBNS), (q / kBNS) & 1);
+}
+
+// Storer (one thread): stores staged tiles in order as the consumers finish
+// them; each destination buffer is freed once its stores have read it.
+__device__ __forceinline__ void batch_storer(const BatchJob* __restrict__ jobs, const BatchSmem& m) {
+  uint32_t c = 0;
+  int seen = 0;
+  unsigned long long idle_since = global_ns();
+  for (;;) {
+    if (m.flags()[0]) break;
+    const uint32_t d = c % kBND;
+    if (mbar_try_wait(m.done(d), (c / kBND) & 1)) {
+      const StoreItem it = *m.sq(c % kSQ);
+      tma_store_tile(jobs[it.job].jp.parent, it.local, m.dst(d));
+      bulk_wait_read<0>();
+      mbar_arrive(m.dfree(d));
+      ++c;
+      idle_since = global_ns();
+      continue;
+    }
+    if (m.flags()[1]) {
+      __threadfence_block();
+      if ((int)c >= m.flags()[2]) break;  // every staged tile is stored
+    }
+    const int decided = m.flags()[3];
+    if (decided != seen) {
+      seen = decided;
+      idle_since = global_ns();
+    }
+    if (global_ns() - idle_since > 4000000000ull) {
+      flag_error(MRN_ETIMEOUT);
+      m.flags()[0] = 1;
+      break;
+    }
+    __nanosleep(20);
+  }
+  bulk_wait_all();
 }
 
 __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restrict__ jobs,
@@ -664,17 +729,28 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
       mbar_init(m.empty(s), 8);
       m.desc(s)->job = 0xffffffffu;
     }
+    for (uint32_t d = 0; d < kBND; ++d) {
+      mbar_init(m.done(d), 8);
+      mbar_init(m.dfree(d), 1);
+    }
     for (uint32_t i = 0; i < kRing; ++i) {
       mbar_init(m.ready(i), 1);
       mbar_init(m.rel(i), 8);
     }
     mbar_init(m.cbar(), 8);
-    *m.abort_flag() = 0;
+    m.flags()[0] = 0;
+    m.flags()[1] = 0;
+    m.flags()[2] = 0;
+    m.flags()[3] = 0;
     fence_mbar_init();
   }
   __syncthreads();
   if (warp == 8) {
-    if (lane == 0) batch_producer(jobs, first_tile, njobs, total_tiles, counter, m);
+    if (lane == 0) batch_loader(jobs, first_tile, njobs, total_tiles, counter, m);
+    return;
+  }
+  if (warp == 9) {
+    if (lane == 0) batch_storer(jobs, m);
     return;
   }
   // consumers
@@ -691,23 +767,22 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
     const TileSlot ts = *m.ring(slot);
     __syncwarp();
     if (lane == 0) mbar_arrive(m.rel(slot));
-    if (!ok || *m.abort_flag()) break;
+    if (!ok || m.flags()[0]) break;
     if (ts.staged) {
       const uint32_t s = c % kBNS, d = c % kBND;
-      if (!mbar_wait_bounded(m.full(s), (c / kBNS) & 1)) {
+      if (!mbar_wait_bounded(m.full(s), (c / kBNS) & 1) ||
+          (c >= kBND && !mbar_wait_bounded(m.dfree(d), ((c / kBND) - 1) & 1))) {
         ok = false;
         break;
       }
-      if (tid == 0) bulk_wait_read<1>();  // destination buffer d is free again
-      sync();
       const StageDesc* sd = m.desc(s);
       tma_transform(sd->kinds, sd->h, smem_u32(sd->d), m.src(s), m.dst(d), lane, warp);
       fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(m.empty(s));
-      sync();
-      if (!ok) break;
-      if (tid == 0) tma_store_tile(jobs[ts.job].jp.parent, ts.local, m.dst(d));
+      if (lane == 0) {
+        mbar_arrive(m.empty(s));
+        mbar_arrive(m.done(d));
+      }
       ++c;
     } else {
       if (ts.t >= total_tiles) break;
@@ -729,9 +804,8 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
   }
   if (!ok) {
     if (lane == 0) flag_error(MRN_ETIMEOUT);
-    *m.abort_flag() = 1;
+    m.flags()[0] = 1;
   }
-  if (tid == 0) bulk_wait_all();
 }
 
 // ================================================================== host
