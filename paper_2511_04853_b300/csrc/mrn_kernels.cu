@@ -579,11 +579,51 @@ struct ConsumerSync {
   }
 };
 
-// Loader: the plan's column descriptors and header into a stage's table.
-__device__ __forceinline__ void fill_stage_desc(const ConvPlan& p, StageDesc* sd, unsigned int job) {
+// Warp-wide bulk loads of source tile lt: lane 0 sets the transaction
+// count, then lane c copies SoA column c (lane 0 copies an AoS / AoSoA
+// tile, which is one range).
+__device__ __forceinline__ void tma_load_tile_warp(const ConvPlan& p, uint64_t lt, char* stage,
+                                                   unsigned long long* bar, int lane) {
+  const TileGeom& g = p.tg;
+  const uint64_t t0 = lt * g.T;
+  const SidePlan& sp = p.src;
+  if (lane == 0) mbar_expect_tx(bar, g.src_bytes);
+  __syncwarp();
+  if (sp.kind == K_AOS) {
+    if (lane == 0) bulk_g2s(stage, sp.base + t0 * p.stride, g.src_bytes, bar);
+  } else if (sp.kind == K_AOSOA) {
+    if (lane == 0) bulk_g2s(stage, sp.base + (t0 / sp.block) * sp.block_bytes, g.src_bytes, bar);
+  } else {
+    for (uint32_t c = lane; c < p.ncols; c += 32)
+      bulk_g2s(stage + g.src_off[c], sp.col[c] + t0 * p.fm_size[c], g.T * p.fm_size[c], bar);
+  }
+}
+
+// Warp-wide bulk stores of destination tile lt; every lane commits its own
+// bulk group.
+__device__ __forceinline__ void tma_store_tile_warp(const ConvPlan& p, uint64_t lt, const char* tile, int lane) {
+  const TileGeom& g = p.tg;
+  const uint64_t t0 = lt * g.T;
+  const SidePlan& sp = p.dst;
+  if (sp.kind == K_AOS) {
+    if (lane == 0) bulk_s2g(sp.base + t0 * p.stride, tile, g.dst_bytes);
+  } else if (sp.kind == K_AOSOA) {
+    if (lane == 0) bulk_s2g(sp.base + (t0 / sp.block) * sp.block_bytes, tile, g.dst_bytes);
+  } else {
+    for (uint32_t c = lane; c < p.ncols; c += 32)
+      bulk_s2g(sp.col[c] + t0 * p.fm_size[c], tile + g.dst_off[c], g.T * p.fm_size[c]);
+  }
+  bulk_commit();
+}
+
+// Loader warp: the plan's column descriptors and header into a stage's table
+// (lane c writes column c).
+__device__ __forceinline__ void fill_stage_desc(const ConvPlan& p, StageDesc* sd, unsigned int job, int lane) {
   if (sd->job == job) return;
-  for (uint32_t c = 0; c < p.ncols; ++c)
+  for (uint32_t c = lane; c < p.ncols; c += 32)
     sd->d[c] = make_uint4(p.tg.col[c], p.tg.src_off[c], p.tg.dst_off[c], 0u);
+  __syncwarp();
+  if (lane != 0) return;
   TileHdr h;
   h.ncols = p.ncols;
   h.stride = p.stride;
@@ -601,13 +641,13 @@ __device__ __forceinline__ void fill_stage_desc(const ConvPlan& p, StageDesc* sd
   sd->job = job;
 }
 
-// Loader (one thread): decides tiles in order and issues the loads of
-// staged ones; returns after publishing the end-of-work slot, or on abort
-// once its loads in flight have landed.
+// Loader warp: decides tiles in order (lane 0 decides, the warp follows)
+// and issues the loads of staged ones; returns after publishing the
+// end-of-work slot, or on abort once its loads in flight have landed.
 __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
                                              const unsigned long long* __restrict__ first_tile,
                                              unsigned int njobs, unsigned long long total_tiles,
-                                             unsigned int* counter, const BatchSmem& m) {
+                                             unsigned int* counter, const BatchSmem& m, int lane) {
   uint64_t k_issue = 0;  // tiles decided
   uint32_t c_issue = 0;  // staged tiles loaded
   unsigned int cursor = 0;
@@ -620,7 +660,9 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
     if (m.flags()[0]) break;
     if (!have) {
       if (next_t == chunk_end) {
-        next_t = (uint64_t)atomicAdd(counter, 1u) * kChunk;
+        unsigned int cidx = 0;
+        if (lane == 0) cidx = atomicAdd(counter, 1u);
+        next_t = (uint64_t)__shfl_sync(0xffffffffu, cidx, 0) * kChunk;
         chunk_end = next_t + kChunk;
       }
       cand.t = next_t++;
@@ -639,78 +681,103 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
     }
     const uint32_t slot = k_issue % kRing;
     const uint32_t s = c_issue % kBNS;
-    bool go = k_issue < kRing || mbar_try_wait(m.rel(slot), (uint32_t)(((k_issue / kRing) - 1) & 1));
-    if (go && cand.staged && c_issue >= kBNS) go = mbar_try_wait(m.empty(s), ((c_issue / kBNS) - 1) & 1);
+    int go = 0;
+    if (lane == 0) {
+      go = k_issue < kRing || mbar_try_wait(m.rel(slot), (uint32_t)(((k_issue / kRing) - 1) & 1));
+      if (go && cand.staged && c_issue >= kBNS) go = mbar_try_wait(m.empty(s), ((c_issue / kBNS) - 1) & 1);
+    }
+    go = __shfl_sync(0xffffffffu, go, 0);
     if (go) {
       if (cand.staged) {
         const ConvPlan& P = jobs[cand.job].jp.parent;
-        StoreItem it;
-        it.local = cand.local;
-        it.job = cand.job;
-        it.pad = 0;
-        *m.sq(c_issue % kSQ) = it;
-        fill_stage_desc(P, m.desc(s), cand.job);
-        tma_load_tile(P, cand.local, m.src(s), m.full(s));
+        if (lane == 0) {
+          StoreItem it;
+          it.local = cand.local;
+          it.job = cand.job;
+          it.pad = 0;
+          *m.sq(c_issue % kSQ) = it;
+        }
+        fill_stage_desc(P, m.desc(s), cand.job, lane);
+        __syncwarp();
+        tma_load_tile_warp(P, cand.local, m.src(s), m.full(s), lane);
         ++c_issue;
       }
-      *m.ring(slot) = cand;
-      if (cand.t >= total_tiles) {
-        m.flags()[2] = (int)c_issue;
-        __threadfence_block();
-        m.flags()[1] = 1;
+      if (lane == 0) {
+        *m.ring(slot) = cand;
+        if (cand.t >= total_tiles) {
+          m.flags()[2] = (int)c_issue;
+          __threadfence_block();
+          m.flags()[1] = 1;
+        }
+        mbar_arrive(m.ready(slot));
+        m.flags()[3] = (int)(k_issue + 1);
       }
-      mbar_arrive(m.ready(slot));
       ++k_issue;
-      m.flags()[3] = (int)k_issue;
       have = false;
       if (cand.t >= total_tiles) return;
       idle_since = global_ns();
     } else {
-      if (global_ns() - idle_since > 2000000000ull) {
-        flag_error(MRN_ETIMEOUT);
-        m.flags()[0] = 1;
+      int late = global_ns() - idle_since > 2000000000ull;
+      late = __shfl_sync(0xffffffffu, late, 0);
+      if (late) {
+        if (lane == 0) {
+          flag_error(MRN_ETIMEOUT);
+          m.flags()[0] = 1;
+        }
         break;
       }
       __nanosleep(20);
     }
   }
   // aborted: the most recent loads land before the CTA may exit (bounded)
-  for (uint32_t q = (c_issue > kBNS ? c_issue - kBNS : 0); q < c_issue; ++q)
-    mbar_wait_bounded(m.full(q % kBNS), (q / kBNS) & 1);
+  if (lane == 0)
+    for (uint32_t q = (c_issue > kBNS ? c_issue - kBNS : 0); q < c_issue; ++q)
+      mbar_wait_bounded(m.full(q % kBNS), (q / kBNS) & 1);
 }
 
-// Storer (one thread): stores staged tiles in order as the consumers finish
-// them; each destination buffer is freed once its stores have read it.
-__device__ __forceinline__ void batch_storer(const BatchJob* __restrict__ jobs, const BatchSmem& m) {
+// Storer warp: stores staged tiles in order as the consumers finish them
+// (lane c stores SoA column c); each destination buffer is freed once its
+// stores have read it.
+__device__ __forceinline__ void batch_storer(const BatchJob* __restrict__ jobs, const BatchSmem& m, int lane) {
   uint32_t c = 0;
   int seen = 0;
   unsigned long long idle_since = global_ns();
   for (;;) {
     if (m.flags()[0]) break;
     const uint32_t d = c % kBND;
-    if (mbar_try_wait(m.done(d), (c / kBND) & 1)) {
+    int ready = 0;
+    if (lane == 0) ready = mbar_try_wait(m.done(d), (c / kBND) & 1);
+    ready = __shfl_sync(0xffffffffu, ready, 0);
+    if (ready) {
+      __syncwarp();  // orders lane 0's acquire before the other lanes' stores
       const StoreItem it = *m.sq(c % kSQ);
-      tma_store_tile(jobs[it.job].jp.parent, it.local, m.dst(d));
+      tma_store_tile_warp(jobs[it.job].jp.parent, it.local, m.dst(d), lane);
       bulk_wait_read<0>();
-      mbar_arrive(m.dfree(d));
+      __syncwarp();
+      if (lane == 0) mbar_arrive(m.dfree(d));
       ++c;
       idle_since = global_ns();
       continue;
     }
-    if (m.flags()[1]) {
-      __threadfence_block();
-      if ((int)c >= m.flags()[2]) break;  // every staged tile is stored
+    int stop = 0, late = 0;
+    if (lane == 0) {
+      if (m.flags()[1]) {
+        __threadfence_block();
+        stop = (int)c >= m.flags()[2];  // every staged tile is stored
+      }
+      const int decided = m.flags()[3];
+      if (decided != seen) {
+        seen = decided;
+        idle_since = global_ns();
+      }
+      late = global_ns() - idle_since > 4000000000ull;
+      if (late && !stop) {
+        flag_error(MRN_ETIMEOUT);
+        m.flags()[0] = 1;
+      }
     }
-    const int decided = m.flags()[3];
-    if (decided != seen) {
-      seen = decided;
-      idle_since = global_ns();
-    }
-    if (global_ns() - idle_since > 4000000000ull) {
-      flag_error(MRN_ETIMEOUT);
-      m.flags()[0] = 1;
-      break;
-    }
+    stop = __shfl_sync(0xffffffffu, stop | late, 0);
+    if (stop) break;
     __nanosleep(20);
   }
   bulk_wait_all();
@@ -746,11 +813,11 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
   }
   __syncthreads();
   if (warp == 8) {
-    if (lane == 0) batch_loader(jobs, first_tile, njobs, total_tiles, counter, m);
+    batch_loader(jobs, first_tile, njobs, total_tiles, counter, m, lane);
     return;
   }
   if (warp == 9) {
-    if (lane == 0) batch_storer(jobs, m);
+    batch_storer(jobs, m, lane);
     return;
   }
   // consumers
