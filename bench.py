@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--case", default=None,
                     help="profiling runs: repeat one conversion, e.g. cells:aos:soa:16777216 "
                          "(schema:src[/B]:dst[/B]:records)")
+    ap.add_argument("--mixed-jobs", type=int, default=4096,
+                    help="collections in the mixed batch (0 skips it)")
+    ap.add_argument("--mixed-only", action="store_true", help="run the mixed batch alone")
     ap.add_argument("--serve-rates", default="0.25,0.5,0.9,1.2",
                     help="served arrival rates as fractions of the measured saturation rate")
     return ap.parse_args()
@@ -207,6 +210,172 @@ def run_reference(args, rank, world):
                              "sample": sample},
             "e2e": {"value": round(val, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------- mixed 4,096-job batch
+
+MIXED_TARGETS = [("soa", 0), ("aosoa", 32), ("aosoa", 128)]
+MIXED_SCHEMAS = ["points", "cells", "tracks"]
+
+
+def mixed_plan(jobs, seed=3, lo=3.0, hi=6.0):
+    """Job list of the mixed batch: sizes round(10^U(lo, hi)) records,
+    schema uniform over points / cells / tracks, AoS source, target uniform
+    over SoA / AoSoA(32) / AoSoA(128).  Jagged parents have no AoSoA form in
+    this library, so track jobs always target SoA."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    ns = np.rint(10.0 ** rng.uniform(lo, hi, jobs)).astype(np.int64)
+    sch = rng.integers(0, 3, jobs)
+    tgt = rng.integers(0, 3, jobs)
+    out = []
+    for i in range(jobs):
+        name = MIXED_SCHEMAS[sch[i]]
+        out.append((name, int(ns[i]), MIXED_TARGETS[0] if name == "tracks" else MIXED_TARGETS[tgt[i]]))
+    return out
+
+
+def device_aos(torch, s, name, n, seed):
+    """AoS source of one collection, generated on the device with the
+    workload's value distributions (padding bytes zero).  Returns the record
+    buffer, the child pool (tracks) and the child count."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    kw = {"device": "cuda", "generator": g}
+    rec = torch.zeros(max(1, n * s.stride), dtype=torch.uint8, device="cuda")
+    rv = rec[: n * s.stride].view(n, s.stride)
+    off = {c["name"]: c["aos_offset"] for c in s.columns}
+
+    def put(field, t):
+        b = t.contiguous().view(torch.uint8).view(n, -1)
+        rv[:, off[field]: off[field] + b.shape[1]].copy_(b)
+
+    def uni(a, b):
+        return torch.rand(n, **kw) * (b - a) + a
+
+    def bits32(shape):
+        return torch.randint(-2 ** 31, 2 ** 31, shape, dtype=torch.int64, **kw).to(torch.int32)
+
+    def low16(t):
+        return t.to(torch.int32).view(torch.uint8).view(n, 4)[:, :2]
+
+    pool, m = None, 0
+    if name == "points":
+        put("x", uni(-1, 1)), put("y", uni(-1, 1)), put("z", uni(-1, 1))
+        put("id", bits32((n,))), put("key", bits32((n, 2)))
+        put("flag", torch.randint(0, 256, (n,), dtype=torch.uint8, **kw))
+    elif name == "cells":
+        put("energy", torch.empty(n, device="cuda").exponential_(2.0, generator=g))
+        put("time", torch.randn(n, **kw) * 5.0)
+        put("eta", uni(-4.9, 4.9)), put("phi", uni(-3.141592653589793, 3.141592653589793))
+        put("cell_id", torch.randperm(n, **kw).to(torch.int32))
+        put("gain", low16(torch.randint(0, 4, (n,), **kw)))
+        put("quality", low16(torch.randint(0, 65536, (n,), **kw)))
+    else:
+        put("pt", torch.empty(n, device="cuda").exponential_(0.1, generator=g))
+        put("eta", uni(-2.5, 2.5))
+        put("label", torch.randint(0, 10, (n,), dtype=torch.int32, **kw))
+        lens = torch.poisson(torch.full((n,), 20.0, device="cuda"), generator=g).clamp_(max=256).to(torch.int64)
+        begs = torch.cumsum(lens, 0) - lens
+        rv[:, s.info.jag_length_offset: s.info.jag_length_offset + 4].copy_(
+            lens.to(torch.int32).view(torch.uint8).view(n, 4))
+        rv[:, s.info.jag_begin_offset: s.info.jag_begin_offset + 8].copy_(begs.view(torch.uint8).view(n, 8))
+        m = int(lens.sum().item())
+        pool = torch.empty(max(1, m), 2, dtype=torch.int32, device="cuda")
+        pool[:m, 0] = bits32((m,))
+        pool[:m, 1] = torch.rand(m, **kw).view(torch.int32)
+        pool = pool.view(torch.uint8).view(-1)
+    return rec, pool, m
+
+
+def run_mixed(mrn, torch, stream, peak, args):
+    """The mixed batch (4,096 collections by default) in one persistent
+    launch per step under a CUDA graph, with the autotuner's shapes and
+    without them, against one launch per collection on the same stream."""
+    import datagen
+    plan = mixed_plan(args.mixed_jobs)
+    schemas = {k: mrn.Schema(datagen.WORKLOAD_SCHEMAS[k]) for k in MIXED_SCHEMAS}
+    pairs, outs, alg = [], [], 0
+    t_setup = time.perf_counter()
+    for i, (name, n, (dk, db)) in enumerate(plan):
+        s = schemas[name]
+        rec, pool, m = device_aos(torch, s, name, n, 1000 + i)
+        out = torch.empty(s.required_bytes(dk, n, m, db), dtype=torch.uint8, device="cuda")
+        src = mrn.View(s, "aos", n, base=rec, child_pool=pool, m=m)
+        dst = mrn.View(s, dk, n, block=db, base=out, m=m)
+        pairs.append((src, dst))
+        outs.append(out)
+        if name == "tracks":
+            alg += 24 * n + 8 * m + 12 * n + 4 * (n + 1) + 8 * m
+        else:
+            alg += n * (s.stride + sum(c["size"] for c in s.columns))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+
+    def timed(fn, reps):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        assert mrn.sync() == mrn.OK
+        return a.elapsed_time(b) / reps
+
+    res = {"workload": "%d collections, records round(10^U(3,6)), schema uniform over points / cells / "
+                       "tracks (jagged, Poisson(20) children clipped at 256), AoS source, target uniform over "
+                       "SoA / AoSoA(32) / AoSoA(128) (tracks: SoA)" % len(plan),
+           "records": sum(n for _, n, _ in plan), "algorithmic_bytes": alg, "setup_s": round(setup_s, 1)}
+    # autotuner off: the library's default shapes
+    mrn.autotune_clear()
+    plain = mrn.Batch(pairs, use_graph=True)
+    plain.launch()
+    torch.cuda.synchronize()
+    assert mrn.sync() == mrn.OK
+    want = [o.clone() for o in outs]
+    for o in outs:
+        o.fill_(0xA5)
+    ms_plain = timed(plain.launch, 5)
+    del plain
+    # one launch per collection, same kernels, same stream
+    per = mrn.Batch(pairs, use_graph=False)
+    for o in outs:
+        o.fill_(0xA5)
+    ms_per = timed(per.launch_per_job, 3)
+    for o, w in zip(outs, want):
+        assert torch.equal(o, w), "per-call output differs from the batched output"
+    del per
+    # autotuned shapes for every non-jagged (schema, target) pair
+    tuned = {}
+    for name in ("points", "cells"):
+        for dk, db in MIXED_TARGETS:
+            r = mrn.autotune(schemas[name], "aos", dk, 1 << 22, 0, db)
+            tuned["%s_aos_to_%s%s" % (name, dk, db or "")] = {k: r[k] for k in ("staged", "threads",
+                                                                               "tile_records", "ctas_per_sm")}
+    tb = mrn.Batch(pairs, use_graph=True)
+    for o in outs:
+        o.fill_(0xA5)
+    ms_tuned = timed(tb.launch, 5)
+    for o, w in zip(outs, want):
+        assert torch.equal(o, w), "autotuned batch output differs"
+    del tb
+    mrn.autotune_clear()
+    best = min(ms_plain, ms_tuned)
+    res.update({"ms_per_launch_default_shapes": round(ms_plain, 3),
+                "ms_per_launch_autotuned": round(ms_tuned, 3),
+                "gbps": round(alg / (best * 1e-3) / 1e9, 1),
+                "frac_of_hbm": round(alg / (best * 1e-3) / 1e9 / peak, 3),
+                "gbps_default_shapes": round(alg / (ms_plain * 1e-3) / 1e9, 1),
+                "gbps_autotuned": round(alg / (ms_tuned * 1e-3) / 1e9, 1),
+                "per_call_ms": round(ms_per, 3), "per_call_launches": len(plan),
+                "speedup_vs_per_call": round(ms_per / best, 3),
+                "autotuned_shapes": tuned})
+    del want, outs, pairs
+    torch.cuda.empty_cache()
+    return res
 
 
 # -------------------------------------------------------------------- mine
@@ -371,6 +540,8 @@ def run_mine(args, rank, world):
     del colls
     torch.cuda.empty_cache()
     extra.update(secondary(mrn, torch, stream, peak))
+    if args.mixed_jobs > 0:
+        extra["batched_mixed"] = run_mixed(mrn, torch, stream, peak, args)
     extra["served"] = run_served(mrn, torch, args)
     cpu_val, cpu_reps, cpu_s = cpu_oracle_rate(10.0, N_RECORDS)
     line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
@@ -680,6 +851,11 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.mixed_only:
+        import torch
+        import paper_2511_04853_b300 as mrn
+        print(json.dumps(run_mixed(mrn, torch, torch.cuda.current_stream(), peaks()[0], args)), flush=True)
         return
     if world > 1:
         import torch

@@ -331,6 +331,7 @@ int build_jagged_plan(const mrn_view& src, const mrn_view& dst, JagPlan* jp) {
   rc = level_plan(s, src, dst, true, m, &jp->child);
   if (rc) return rc;
   jp->off_size = s->off_size;
+  jp->len_off = s->len_off;
   char* offs = static_cast<char*>(soa.offsets);
   if (!offs) {
     if (!soa.base) return MRN_EINVAL;

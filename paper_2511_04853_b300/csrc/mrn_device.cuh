@@ -504,29 +504,37 @@ __device__ __forceinline__ void sts128_zero(uint32_t a) {
 }
 
 // The fields of a plan the staged transform reads, copied into shared memory
-// next to the column descriptors.
+// next to the column descriptors.  Each side of a tile is described by one
+// row geometry, whatever its layout: record r lies in row block
+// r >> shift (r / block when shift is MRN_NO_SHIFT) at byte bb * row block,
+// slot r - block * row block.  AoS: block 1, shift 0, bb = stride (every
+// record its own row, slot 0); SoA: shift 31 (one row, slot r); AoSoA(B):
+// block B, bb = block bytes.
 struct TileHdr {
   uint32_t ncols, stride, vec, pad, T;
-  uint32_t sblock, sshift, sbb;  // source AoSoA block, log2 (or MRN_NO_SHIFT), bytes
-  uint32_t dblock, dshift, dbb;  // destination AoSoA block, log2, bytes
+  uint32_t sblock, sshift, sbb;  // source row geometry
+  uint32_t dblock, dshift, dbb;  // destination row geometry
 };
 
-// Lane view of record r of a tile side of kind K: AoS -> the record's
-// address; SoA -> (tile, r); AoSoA -> (the record's block, slot).
-template <int K>
-__device__ __forceinline__ void tile_lane(uint32_t block, uint32_t shift, uint32_t bb, uint32_t tile,
-                                          uint32_t stride, uint32_t r, uint32_t* base, uint32_t* idx) {
-  if constexpr (K == K_AOS) {
-    *base = tile + r * stride;
-    *idx = 0;
-  } else if constexpr (K == K_SOA) {
-    *base = tile;
-    *idx = r;
+// Row geometry of one side of a plan (see TileHdr).
+__device__ __forceinline__ void tile_side_geometry(uint32_t kind, uint32_t block, uint32_t shift, uint64_t bb,
+                                                   uint32_t stride, uint32_t* gb, uint32_t* gs, uint32_t* gbb) {
+  if (kind == K_AOS) {
+    *gb = 1, *gs = 0, *gbb = stride;
+  } else if (kind == K_SOA) {
+    *gb = 1, *gs = 31, *gbb = 0;
   } else {
-    const uint32_t blk = shift != MRN_NO_SHIFT ? r >> shift : r / block;
-    *idx = r - blk * block;
-    *base = tile + blk * bb;
+    *gb = block, *gs = shift, *gbb = (uint32_t)bb;
   }
+}
+
+// Lane view of record r of a tile side: the byte address of its row and
+// its slot in the row.
+__device__ __forceinline__ void tile_row(uint32_t block, uint32_t shift, uint32_t bb, uint32_t tile, uint32_t r,
+                                         uint32_t* base, uint32_t* idx) {
+  const uint32_t blk = shift != MRN_NO_SHIFT ? r >> shift : r / block;
+  *idx = r - blk * block;
+  *base = tile + blk * bb;
 }
 
 __device__ __forceinline__ uint2 lds_sz(uint32_t a, uint32_t lsz) {
@@ -547,22 +555,21 @@ __device__ __forceinline__ void sts_sz(uint32_t a, uint2 v, uint32_t lsz) {
     sts8(a, v.x);
 }
 
-template <int DK>
+// Zeroes an AoS destination record whose padding bytes no column writes
+// (h.pad is set only for such destinations).
 __device__ __forceinline__ void zero_record(const TileHdr& h, uint32_t db) {
-  if constexpr (DK == K_AOS) {
-    if (h.pad) {  // the record's padding bytes are zero
-      const uint32_t S = h.stride, v = h.vec;
-      if (v == 16) {
-        for (uint32_t o = 0; o < S; o += 16) sts128_zero(db + o);
-      } else if (v == 8) {
-        for (uint32_t o = 0; o < S; o += 8) sts64(db + o, make_uint2(0, 0));
-      } else if (v == 4) {
-        for (uint32_t o = 0; o < S; o += 4) sts32(db + o, 0);
-      } else if (v == 2) {
-        for (uint32_t o = 0; o < S; o += 2) sts16(db + o, 0);
-      } else {
-        for (uint32_t o = 0; o < S; ++o) sts8(db + o, 0);
-      }
+  if (h.pad) {
+    const uint32_t S = h.stride, v = h.vec;
+    if (v == 16) {
+      for (uint32_t o = 0; o < S; o += 16) sts128_zero(db + o);
+    } else if (v == 8) {
+      for (uint32_t o = 0; o < S; o += 8) sts64(db + o, make_uint2(0, 0));
+    } else if (v == 4) {
+      for (uint32_t o = 0; o < S; o += 4) sts32(db + o, 0);
+    } else if (v == 2) {
+      for (uint32_t o = 0; o < S; o += 2) sts16(db + o, 0);
+    } else {
+      for (uint32_t o = 0; o < S; ++o) sts8(db + o, 0);
     }
   }
 }
@@ -570,39 +577,31 @@ __device__ __forceinline__ void zero_record(const TileHdr& h, uint32_t db) {
 // Staged tile transform: each lane converts records r0 and r1 (= r0 + 256,
 // when `two`) of the tile.  Per column one shared load and one shared store
 // per record, addressed from the column descriptor table `desc` (uint4
-// {AoS offset | log2(size) << 24, source column offset, destination column
-// offset, 0} per column, in shared memory); the loads of two columns of both
-// records are issued before their stores.  Layout kinds are template
-// parameters, so the column loop has no layout branches.
-template <int SK, int DK>
+// {log2(size), source column offset, destination column offset, 0} per
+// column, in shared memory; a column offset on an AoS side is the field's
+// offset in the record) as row + column offset + (slot << log2(size)); the
+// loads of two columns of both records are issued before their stores.  One
+// body serves every pair of layouts, so tiles of different layout pairs
+// running side by side share their instructions.
 __device__ __forceinline__ void tile_convert(const TileHdr& h, uint32_t desc, uint32_t st, uint32_t dt,
                                              uint32_t r0, bool two) {
   const uint32_t r1 = two ? r0 + 256 : r0;
   uint32_t sb0, si0, db0, di0, sb1, si1, db1, di1;
-  tile_lane<SK>(h.sblock, h.sshift, h.sbb, st, h.stride, r0, &sb0, &si0);
-  tile_lane<DK>(h.dblock, h.dshift, h.dbb, dt, h.stride, r0, &db0, &di0);
-  tile_lane<SK>(h.sblock, h.sshift, h.sbb, st, h.stride, r1, &sb1, &si1);
-  tile_lane<DK>(h.dblock, h.dshift, h.dbb, dt, h.stride, r1, &db1, &di1);
-  zero_record<DK>(h, db0);
-  if (two) zero_record<DK>(h, db1);
+  tile_row(h.sblock, h.sshift, h.sbb, st, r0, &sb0, &si0);
+  tile_row(h.dblock, h.dshift, h.dbb, dt, r0, &db0, &di0);
+  tile_row(h.sblock, h.sshift, h.sbb, st, r1, &sb1, &si1);
+  tile_row(h.dblock, h.dshift, h.dbb, dt, r1, &db1, &di1);
+  zero_record(h, db0);
+  if (two) zero_record(h, db1);
   const uint32_t nc = h.ncols;
   uint32_t c = 0;
   for (; c + 1 < nc; c += 2) {
     const uint4 d0 = lds128(desc + c * 16), d1 = lds128(desc + c * 16 + 16);
-    const uint32_t ao0 = d0.x & 0xffffffu, l0 = d0.x >> 24, ao1 = d1.x & 0xffffffu, l1 = d1.x >> 24;
-    uint32_t a00, a01, a10, a11, b00, b01, b10, b11;  // a<column><record>
-    if constexpr (SK == K_AOS) {
-      a00 = sb0 + ao0; a01 = sb1 + ao0; a10 = sb0 + ao1; a11 = sb1 + ao1;
-    } else {
-      a00 = sb0 + d0.y + (si0 << l0); a01 = sb1 + d0.y + (si1 << l0);
-      a10 = sb0 + d1.y + (si0 << l1); a11 = sb1 + d1.y + (si1 << l1);
-    }
-    if constexpr (DK == K_AOS) {
-      b00 = db0 + ao0; b01 = db1 + ao0; b10 = db0 + ao1; b11 = db1 + ao1;
-    } else {
-      b00 = db0 + d0.z + (di0 << l0); b01 = db1 + d0.z + (di1 << l0);
-      b10 = db0 + d1.z + (di0 << l1); b11 = db1 + d1.z + (di1 << l1);
-    }
+    const uint32_t l0 = d0.x, l1 = d1.x;
+    const uint32_t a00 = sb0 + d0.y + (si0 << l0), a01 = sb1 + d0.y + (si1 << l0);
+    const uint32_t a10 = sb0 + d1.y + (si0 << l1), a11 = sb1 + d1.y + (si1 << l1);
+    const uint32_t b00 = db0 + d0.z + (di0 << l0), b01 = db1 + d0.z + (di1 << l0);
+    const uint32_t b10 = db0 + d1.z + (di0 << l1), b11 = db1 + d1.z + (di1 << l1);
     const uint2 v00 = lds_sz(a00, l0), v10 = lds_sz(a10, l1);
     uint2 v01 = v00, v11 = v10;
     if (two) {
@@ -618,18 +617,9 @@ __device__ __forceinline__ void tile_convert(const TileHdr& h, uint32_t desc, ui
   }
   if (c < nc) {
     const uint4 d0 = lds128(desc + c * 16);
-    const uint32_t ao0 = d0.x & 0xffffffu, l0 = d0.x >> 24;
-    uint32_t a00, a01, b00, b01;
-    if constexpr (SK == K_AOS) {
-      a00 = sb0 + ao0; a01 = sb1 + ao0;
-    } else {
-      a00 = sb0 + d0.y + (si0 << l0); a01 = sb1 + d0.y + (si1 << l0);
-    }
-    if constexpr (DK == K_AOS) {
-      b00 = db0 + ao0; b01 = db1 + ao0;
-    } else {
-      b00 = db0 + d0.z + (di0 << l0); b01 = db1 + d0.z + (di1 << l0);
-    }
+    const uint32_t l0 = d0.x;
+    const uint32_t a00 = sb0 + d0.y + (si0 << l0), a01 = sb1 + d0.y + (si1 << l0);
+    const uint32_t b00 = db0 + d0.z + (di0 << l0), b01 = db1 + d0.z + (di1 << l0);
     const uint2 v00 = lds_sz(a00, l0);
     uint2 v01 = v00;
     if (two) v01 = lds_sz(a01, l0);

@@ -107,50 +107,41 @@ __device__ __forceinline__ void tma_store_tile(const ConvPlan& p, uint64_t lt, c
 }
 
 // All threads: source tile -> destination tile in shared memory.
-template <int SK, int DK>
-__device__ __forceinline__ void tma_transform_k(const TileHdr& h, uint32_t desc, uint32_t st, uint32_t dt,
-                                                int lane, int warp) {
+__device__ __forceinline__ void tma_transform(const TileHdr& h, uint32_t desc, const char* st, char* dt, int lane,
+                                              int warp) {
+  const uint32_t s = smem_u32(st), d = smem_u32(dt);
   const TileHdr hh = h;
   for (uint32_t g = (uint32_t)warp * 32; g < hh.T; g += 2 * 8 * 32)
-    tile_convert<SK, DK>(hh, desc, st, dt, g + lane, g + 8 * 32 < hh.T);
+    tile_convert(hh, desc, s, d, g + lane, g + 8 * 32 < hh.T);
 }
 
-__device__ __forceinline__ void tma_transform(uint32_t kinds, const TileHdr& h, uint32_t desc, const char* st,
-                                              char* dt, int lane, int warp) {
-  const uint32_t s = smem_u32(st), d = smem_u32(dt);
-  switch (kinds) {
-    case K_AOS * 3 + K_SOA: tma_transform_k<K_AOS, K_SOA>(h, desc, s, d, lane, warp); break;
-    case K_AOS * 3 + K_AOSOA: tma_transform_k<K_AOS, K_AOSOA>(h, desc, s, d, lane, warp); break;
-    case K_SOA * 3 + K_AOS: tma_transform_k<K_SOA, K_AOS>(h, desc, s, d, lane, warp); break;
-    case K_SOA * 3 + K_SOA: tma_transform_k<K_SOA, K_SOA>(h, desc, s, d, lane, warp); break;
-    case K_SOA * 3 + K_AOSOA: tma_transform_k<K_SOA, K_AOSOA>(h, desc, s, d, lane, warp); break;
-    case K_AOSOA * 3 + K_AOS: tma_transform_k<K_AOSOA, K_AOS>(h, desc, s, d, lane, warp); break;
-    case K_AOSOA * 3 + K_SOA: tma_transform_k<K_AOSOA, K_SOA>(h, desc, s, d, lane, warp); break;
-    default: tma_transform_k<K_AOSOA, K_AOSOA>(h, desc, s, d, lane, warp); break;
-  }
+// Column c's staged-transform descriptor (see tile_convert).
+__device__ __forceinline__ uint4 tile_desc(const ConvPlan& p, uint32_t c) {
+  const uint32_t col = p.tg.col[c], aos_off = col & 0xffffffu;
+  return make_uint4(col >> 24, p.src.kind == K_AOS ? aos_off : p.tg.src_off[c],
+                    p.dst.kind == K_AOS ? aos_off : p.tg.dst_off[c], 0u);
+}
+
+__device__ __forceinline__ TileHdr tile_hdr(const ConvPlan& p) {
+  TileHdr h;
+  h.ncols = p.ncols;
+  h.stride = p.stride;
+  h.vec = p.vec;
+  h.pad = p.dst.kind == K_AOS ? p.tg.pad : 0u;
+  h.T = p.tg.T;
+  tile_side_geometry(p.src.kind, p.src.block, p.src.block_shift, p.src.block_bytes, p.stride, &h.sblock, &h.sshift,
+                     &h.sbb);
+  tile_side_geometry(p.dst.kind, p.dst.block, p.dst.block_shift, p.dst.block_bytes, p.stride, &h.dblock, &h.dshift,
+                     &h.dbb);
+  return h;
 }
 
 // Threads [0, ncols): the plan's column descriptors into shared memory;
-// thread 0 also the header fields.  Returns the layout-kind pair.
-__device__ __forceinline__ uint32_t load_sdesc(const ConvPlan& p, uint4* sdesc, TileHdr* hdr) {
+// thread 0 also the header.
+__device__ __forceinline__ void load_sdesc(const ConvPlan& p, uint4* sdesc, TileHdr* hdr) {
   const uint32_t c = threadIdx.x;
-  if (c < p.ncols) sdesc[c] = make_uint4(p.tg.col[c], p.tg.src_off[c], p.tg.dst_off[c], 0u);
-  if (c == 0) {
-    TileHdr h;
-    h.ncols = p.ncols;
-    h.stride = p.stride;
-    h.vec = p.vec;
-    h.pad = p.tg.pad;
-    h.T = p.tg.T;
-    h.sblock = p.src.block;
-    h.sshift = p.src.block_shift;
-    h.sbb = (uint32_t)p.src.block_bytes;
-    h.dblock = p.dst.block;
-    h.dshift = p.dst.block_shift;
-    h.dbb = (uint32_t)p.dst.block_bytes;
-    *hdr = h;
-  }
-  return p.src.kind * 3 + p.dst.kind;
+  if (c < p.ncols) sdesc[c] = tile_desc(p, c);
+  if (c == 0) *hdr = tile_hdr(p);
 }
 
 // A staged tile whose mbarrier did not complete within its bound: record
@@ -196,7 +187,7 @@ __global__ void __launch_bounds__(256, 3) k_convert_tma(const __grid_constant__ 
   }
   for (uint32_t k = 0; k < kNS; ++k)
     if (b + k * G < nfull) pending |= 1u << k;
-  const uint32_t kinds = load_sdesc(p, sdesc, &hdr);
+  load_sdesc(p, sdesc, &hdr);
   __syncthreads();
   const uint32_t desc = smem_u32(sdesc);
   for (uint64_t k = 0;; ++k) {
@@ -213,7 +204,7 @@ __global__ void __launch_bounds__(256, 3) k_convert_tma(const __grid_constant__ 
       }
       pending &= ~(1u << s);
       phase ^= 1u << s;
-      tma_transform(kinds, hdr, desc, stage_src(sm, s), stage_dst(sm, dsel), lane, warp);
+      tma_transform(hdr, desc, stage_src(sm, s), stage_dst(sm, dsel), lane, warp);
       fence_proxy_async_smem();
       __syncthreads();
       const uint64_t nt = t + kNS * G;
@@ -272,17 +263,142 @@ struct JagShared {
   unsigned long long excl[MRN_JAG_TILE + 1];
   unsigned long long beg[MRN_JAG_TILE];
   unsigned long long warp[8];
+  unsigned long long kmin[8], kmax[8];  // per warp: min / max of begin - exclusive offset
   unsigned long long base;
 };
 
+// Loads and stores of one child column element of `size` bytes.
+template <int S>
+__device__ __forceinline__ unsigned long long ld_elem(const char* p) {
+  if constexpr (S == 8) return __ldg(reinterpret_cast<const unsigned long long*>(p));
+  if constexpr (S == 4) return __ldg(reinterpret_cast<const unsigned int*>(p));
+  if constexpr (S == 2) return __ldg(reinterpret_cast<const unsigned short*>(p));
+  return __ldg(reinterpret_cast<const unsigned char*>(p));
+}
+
+template <int S>
+__device__ __forceinline__ void st_elem(char* p, unsigned long long v) {
+  if constexpr (S == 8) *reinterpret_cast<unsigned long long*>(p) = v;
+  if constexpr (S == 4) *reinterpret_cast<unsigned int*>(p) = (unsigned int)v;
+  if constexpr (S == 2) *reinterpret_cast<unsigned short*>(p) = (unsigned short)v;
+  if constexpr (S == 1) *reinterpret_cast<unsigned char*>(p) = (unsigned char)v;
+}
+
+constexpr int kJagSlots = 4;  // child slots per lane per pass
+
+// One child column for the kJagSlots slots of a lane: all loads, then all
+// stores (zeros where the slot has no valid source).
+template <int S>
+__device__ __forceinline__ void child_column(const char* src, uint32_t stride, char* col, const uint64_t* si,
+                                             const uint64_t* di, uint32_t ld_ok, uint32_t st_ok) {
+  unsigned long long v[kJagSlots];
+#pragma unroll
+  for (int u = 0; u < kJagSlots; ++u) v[u] = (ld_ok >> u) & 1 ? ld_elem<S>(src + si[u] * stride) : 0ull;
+#pragma unroll
+  for (int u = 0; u < kJagSlots; ++u)
+    if ((st_ok >> u) & 1) st_elem<S>(col + di[u] * S, v[u]);
+}
+
+// The children of a jagged tile: slot j (0 <= j < agg) is child
+// j - excl[p] of the last parent p with excl[p] <= j; it moves from pool
+// record beg[p] + j - excl[p] to row base + j of every child column (the
+// destination of a jagged conversion is always SoA).  Each lane moves
+// kJagSlots slots per pass, a column at a time.  When the tile's children
+// form one run of the pool (Run: beg[p] - excl[p] is the same `key` for
+// every parent with children), the parent lookup is skipped.
+template <bool Run>
+__device__ __forceinline__ void jagged_children(const JagPlan& jp, const JagShared& sh, unsigned long long agg,
+                                                unsigned long long base, unsigned long long key, int lane,
+                                                int warp) {
+  const ConvPlan& C = jp.child;
+  const uint32_t nc = C.naos, stride = C.stride;
+  constexpr unsigned long long kPass = 32 * kJagSlots;
+  for (unsigned long long j0 = (unsigned long long)warp * kPass; j0 < agg; j0 += 8 * kPass) {
+    uint64_t si[kJagSlots], di[kJagSlots];
+    uint32_t ld_ok = 0, st_ok = 0;
+#pragma unroll
+    for (int u = 0; u < kJagSlots; ++u) {
+      const unsigned long long j = j0 + u * 32 + lane;
+      const bool cok = j < agg;
+      bool good = cok;
+      si[u] = key + j;
+      if (!Run && cok) {
+        int lo = 0, hi = MRN_JAG_TILE;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (sh.excl[mid] <= j) lo = mid; else hi = mid;
+        }
+        const unsigned long long pb = sh.beg[lo];
+        good = pb != ~0ull;
+        si[u] = pb + (j - sh.excl[lo]);
+      }
+      di[u] = base + j;
+      const bool sok = cok && di[u] < jp.capacity;
+      if (cok && !sok) flag_error(MRN_ESIZE);
+      st_ok |= (uint32_t)sok << u;
+      ld_ok |= (uint32_t)(sok && good) << u;
+    }
+    if (!st_ok) continue;
+    for (uint32_t ci = 0; ci < nc; ++ci) {
+      const ColPlan cp = C.aos_cols[ci];
+      const char* src = C.src.base + cp.aos_off;
+      char* col = C.dst.col[cp.fm];
+      switch (cp.size) {
+        case 8: child_column<8>(src, stride, col, si, di, ld_ok, st_ok); break;
+        case 4: child_column<4>(src, stride, col, si, di, ld_ok, st_ok); break;
+        case 2: child_column<2>(src, stride, col, si, di, ld_ok, st_ok); break;
+        default: child_column<1>(src, stride, col, si, di, ld_ok, st_ok); break;
+      }
+    }
+  }
+}
+
+// Child count of all tiles before `tile`, by a decoupled look-back over the
+// published tile words st[] (warp-wide: 32 predecessors per step; each wait
+// bounded by jp.timeout_ns and an iteration count).  Run by one whole warp;
+// every lane returns the sum.
+__device__ __forceinline__ unsigned long long jagged_lookback(const JagPlan& jp, uint64_t tile,
+                                                              const unsigned long long* st, int lane) {
+  unsigned long long prefix = 0;
+  long long j = (long long)tile - 1;  // highest tile not yet accumulated
+  const unsigned long long deadline = global_ns() + jp.timeout_ns;
+  unsigned int spins = 0;
+  while (j >= 0) {
+    const long long jj = j - lane;
+    const unsigned long long v = jj >= 0 ? ld_acquire_u64(&st[jj]) : MRN_TS_PREFIX;
+    const unsigned long long fl = v & ~MRN_TS_VALUE;
+    const unsigned int pref = __ballot_sync(0xffffffffu, fl == MRN_TS_PREFIX);
+    const unsigned int zero = __ballot_sync(0xffffffffu, fl == 0);
+    const unsigned int upto = pref ? ((pref & (0u - pref)) << 1) - 1u : 0xffffffffu;  // lanes to sum
+    if (zero & upto) {
+      if (global_ns() > deadline || ++spins > (1u << 24)) {
+        if (lane == 0) flag_error(MRN_ETIMEOUT);
+        break;
+      }
+      __nanosleep(64);
+      continue;
+    }
+    unsigned long long x = ((upto >> lane) & 1u) ? (v & MRN_TS_VALUE) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    prefix += x;
+    if (pref) break;
+    j -= 32;
+  }
+  return prefix;
+}
+
 // One tile of 256 parents of a jagged AoS -> SoA conversion (256 threads):
 // converts the parents, scans their lengths, obtains the tile's child base
-// by a decoupled look-back over the predecessors' published sums in `st`
-// (every wait bounded by jp.timeout_ns), writes the offsets and gathers the
-// tile's children, load-balanced over the tile's threads.  Tiles must be
-// handed out in increasing order (dynamic tile ids), so that every
-// predecessor is already running.
-template <int VP, int VC, class Sync = CtaSync>
+// by a decoupled look-back over the predecessors' published sums in `st`,
+// writes the offsets and gathers the tile's children, load-balanced over the
+// tile's threads.  Every predecessor's word must be published independently
+// of this tile's progress: either each tile publishes its own sum first
+// (Published = false; tiles handed out in increasing order, so every
+// predecessor is already running), or whoever hands out the tiles has
+// published every sum beforehand (Published = true: the tile only publishes
+// its inclusive prefix).
+template <int VP, int VC, class Sync = CtaSync, bool Published = false>
 __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile, unsigned long long* st,
                                                 uint32_t* tw_all, JagShared& sh, const Sync& sync = Sync()) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -325,37 +441,37 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
   sh.excl[tid] = excl;
   if (tid == MRN_JAG_TILE - 1) sh.excl[MRN_JAG_TILE] = agg;
   sh.beg[tid] = bad ? ~0ull : beg;
+  // Run test: beg - excl equal for every parent with children (a bad
+  // parent fails it: min 0, max all ones).
+  unsigned long long kmin = ~0ull, kmax = 0ull;
+  if (bad) {
+    kmin = 0ull;
+    kmax = ~0ull;
+  } else if (len > 0) {
+    kmin = kmax = beg - excl;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+    kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+  }
+  if (lane == 0) {
+    sh.kmin[warp] = kmin;
+    sh.kmax[warp] = kmax;
+  }
 
   // Decoupled look-back for the number of children of all earlier tiles.
-  if (tid == 0) {
-    unsigned long long prefix = 0;
+  if (warp == 0) {
     const bool publish = (long long)tile != jp.skip_publish_tile;
+    unsigned long long prefix = 0;
     if (tile == 0) {
-      if (publish) st_release_u64(&st[0], MRN_TS_PREFIX | (agg & MRN_TS_VALUE));
+      if (!Published && publish && lane == 0) st_release_u64(&st[0], MRN_TS_PREFIX | (agg & MRN_TS_VALUE));
     } else {
-      if (publish) st_release_u64(&st[tile], MRN_TS_AGG | (agg & MRN_TS_VALUE));
-      long long j = (long long)tile - 1;
-      const unsigned long long deadline = global_ns() + jp.timeout_ns;
-      unsigned int spins = 0;
-      while (j >= 0) {
-        const unsigned long long v = ld_acquire_u64(&st[j]);
-        const unsigned long long fl = v & ~MRN_TS_VALUE;
-        if (fl == 0) {
-          // bounded wait: by wall clock and by iteration count
-          if (global_ns() > deadline || ++spins > (1u << 26)) {
-            flag_error(MRN_ETIMEOUT);
-            break;
-          }
-          __nanosleep(64);
-          continue;
-        }
-        prefix += v & MRN_TS_VALUE;
-        if (fl == MRN_TS_PREFIX) break;
-        --j;
-      }
-      if (publish) st_release_u64(&st[tile], MRN_TS_PREFIX | ((prefix + agg) & MRN_TS_VALUE));
+      if (!Published && publish && lane == 0) st_release_u64(&st[tile], MRN_TS_AGG | (agg & MRN_TS_VALUE));
+      prefix = jagged_lookback(jp, tile, st, lane);
+      if (publish && lane == 0) st_release_u64(&st[tile], MRN_TS_PREFIX | ((prefix + agg) & MRN_TS_VALUE));
     }
-    sh.base = prefix;
+    if (lane == 0) sh.base = prefix;
   }
   sync();
   const unsigned long long base = sh.base;
@@ -374,29 +490,18 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
     }
   }
 
-  // Children: slot j of the tile belongs to the last parent p with
-  // excl[p] <= j; each warp moves 32 consecutive slots.
-  for (unsigned long long j0 = (unsigned long long)warp * 32; j0 < agg; j0 += MRN_JAG_TILE) {
-    const unsigned long long j = j0 + lane;
-    const bool cok = j < agg;
-    int lo = 0, hi = MRN_JAG_TILE;
-    if (cok) {
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (sh.excl[mid] <= j) lo = mid; else hi = mid;
-      }
-    }
-    const unsigned long long pb = sh.beg[lo];
-    const unsigned long long src_idx = pb + (j - sh.excl[lo]);
-    const unsigned long long dst_idx = base + j;
-    const bool st_ok = cok && dst_idx < jp.capacity;
-    if (cok && !st_ok) flag_error(MRN_ESIZE);
-    const bool ld_ok = st_ok && pb != ~0ull;
-    uint32_t dl;
-    uint64_t db;
-    aos_to_fm_lane<VC>(jp.child, dst_idx, ld_ok, st_ok,
-                       jp.child.src.base + src_idx * jp.child.stride, tw, lane, &dl, &db);
+  // Children, as one run of the pool when they form one.
+  kmin = ~0ull;
+  kmax = 0ull;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    kmin = min(kmin, sh.kmin[w]);
+    kmax = max(kmax, sh.kmax[w]);
   }
+  if (kmin == kmax)
+    jagged_children<true>(jp, sh, agg, base, kmin, lane, warp);
+  else
+    jagged_children<false>(jp, sh, agg, base, 0ull, lane, warp);
 }
 
 template <int VP, int VC>
@@ -469,18 +574,19 @@ __global__ void k_write_offset0(char* offs, uint32_t osz, unsigned long long v) 
 //
 // Every job of a batch in one persistent, warp-specialized launch of 320
 // threads per CTA.
-//  - Warp 8 (loader; lane 0 works) takes chunks of kChunk consecutive global
-//    tiles from an atomic counter (chunks are handed out in increasing order,
-//    so a jagged tile's predecessors are all taken earlier by running CTAs
-//    and every look-back terminates), decides each tile and issues the TMA
-//    loads of staged tiles up to kBNS stages ahead.
+//  - Warp 8 (loader) takes chunks of kChunk consecutive global tiles from an
+//    atomic counter (chunks are handed out in increasing order), publishes
+//    the child counts of the chunk's jagged tiles at once (so a jagged
+//    tile's look-back waits only for chunks taken earlier), decides each
+//    tile and issues the TMA loads of staged tiles up to kBNS stages ahead
+//    (lane c loads SoA column c).
 //  - Warps 0-7 (consumers) take the decided tiles in order.  A staged tile
 //    is transformed shared -> shared, each warp on its own records; every
 //    other tile (jagged, zero-fill, partial or unstaged conversions) runs
 //    directly on global memory with a private scratch.
-//  - Warp 9 (storer; lane 0 works) writes each finished staged tile back
-//    with bulk stores and frees its destination buffer once they have read
-//    it.
+//  - Warp 9 (storer) writes each finished staged tile back with bulk stores
+//    (lane c stores SoA column c) and frees its destination buffer once they
+//    have read it.
 // The warps meet only on mbarriers:
 //   ready[i] / rel[i]   ring slot i written / read by all consumer warps
 //   full[s] / empty[s]  source stage s loaded / read by all consumer warps
@@ -506,7 +612,7 @@ struct TileSlot {
 
 struct StageDesc {
   TileHdr h;
-  unsigned int kinds;
+  unsigned int pad;
   unsigned int job;
   uint4 d[MRN_MAX_COLS];
 };
@@ -620,25 +726,37 @@ __device__ __forceinline__ void tma_store_tile_warp(const ConvPlan& p, uint64_t 
 // (lane c writes column c).
 __device__ __forceinline__ void fill_stage_desc(const ConvPlan& p, StageDesc* sd, unsigned int job, int lane) {
   if (sd->job == job) return;
-  for (uint32_t c = lane; c < p.ncols; c += 32)
-    sd->d[c] = make_uint4(p.tg.col[c], p.tg.src_off[c], p.tg.dst_off[c], 0u);
+  for (uint32_t c = lane; c < p.ncols; c += 32) sd->d[c] = tile_desc(p, c);
   __syncwarp();
   if (lane != 0) return;
-  TileHdr h;
-  h.ncols = p.ncols;
-  h.stride = p.stride;
-  h.vec = p.vec;
-  h.pad = p.tg.pad;
-  h.T = p.tg.T;
-  h.sblock = p.src.block;
-  h.sshift = p.src.block_shift;
-  h.sbb = (uint32_t)p.src.block_bytes;
-  h.dblock = p.dst.block;
-  h.dshift = p.dst.block_shift;
-  h.dbb = (uint32_t)p.dst.block_bytes;
-  sd->h = h;
-  sd->kinds = p.src.kind * 3 + p.dst.kind;
+  sd->h = tile_hdr(p);
   sd->job = job;
+}
+
+// Loader warp, on taking tiles [t0, t1): publishes the child count of each
+// jagged AoS -> SoA tile among them (the inclusive prefix for a job's first
+// tile), before any of them is decided.  A tile's look-back then waits only
+// for chunks taken before its own, never for another CTA's consumers.
+__device__ __forceinline__ void publish_jagged_sums(const BatchJob* __restrict__ jobs,
+                                                    const unsigned long long* __restrict__ first_tile,
+                                                    unsigned int njobs, unsigned long long total_tiles,
+                                                    unsigned long long* states, uint64_t t0, uint64_t t1,
+                                                    unsigned int* cursor, int lane) {
+  for (uint64_t t = t0; t < t1 && t < total_tiles; ++t) {
+    while (*cursor + 1 < njobs && __ldg(first_tile + *cursor + 1) <= t) ++*cursor;
+    const BatchJob& J = jobs[*cursor];
+    if (J.kind != JOB_JAG_A2S) continue;
+    const JagPlan& jp = J.jp;
+    const uint64_t local = t - J.tile_begin;
+    const uint64_t r0 = local * MRN_JAG_TILE, n = jp.parent.n;
+    unsigned long long sum = 0;
+    for (uint64_t r = r0 + lane; r < r0 + MRN_JAG_TILE && r < n; r += 32)
+      sum += __ldg(reinterpret_cast<const unsigned int*>(jp.parent.src.base + r * jp.parent.stride + jp.len_off));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0 && (long long)local != jp.skip_publish_tile)
+      st_release_u64(&states[J.tile_begin + local], (local == 0 ? MRN_TS_PREFIX : MRN_TS_AGG) | (sum & MRN_TS_VALUE));
+  }
 }
 
 // Loader warp: decides tiles in order (lane 0 decides, the warp follows)
@@ -647,11 +765,13 @@ __device__ __forceinline__ void fill_stage_desc(const ConvPlan& p, StageDesc* sd
 __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
                                              const unsigned long long* __restrict__ first_tile,
                                              unsigned int njobs, unsigned long long total_tiles,
-                                             unsigned int* counter, const BatchSmem& m, int lane) {
+                                             unsigned int* counter, unsigned long long* states,
+                                             const BatchSmem& m, int lane) {
   uint64_t k_issue = 0;  // tiles decided
   uint32_t c_issue = 0;  // staged tiles loaded
   unsigned int cursor = 0;
   uint64_t next_t = 0, chunk_end = 0;
+  unsigned int pcursor = 0;
   bool have = false;
   TileSlot cand;
   cand.t = 0;
@@ -664,6 +784,7 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
         if (lane == 0) cidx = atomicAdd(counter, 1u);
         next_t = (uint64_t)__shfl_sync(0xffffffffu, cidx, 0) * kChunk;
         chunk_end = next_t + kChunk;
+        publish_jagged_sums(jobs, first_tile, njobs, total_tiles, states, next_t, chunk_end, &pcursor, lane);
       }
       cand.t = next_t++;
       cand.staged = 0;
@@ -813,7 +934,7 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
   }
   __syncthreads();
   if (warp == 8) {
-    batch_loader(jobs, first_tile, njobs, total_tiles, counter, m, lane);
+    batch_loader(jobs, first_tile, njobs, total_tiles, counter, states, m, lane);
     return;
   }
   if (warp == 9) {
@@ -843,7 +964,7 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
         break;
       }
       const StageDesc* sd = m.desc(s);
-      tma_transform(sd->kinds, sd->h, smem_u32(sd->d), m.src(s), m.dst(d), lane, warp);
+      tma_transform(sd->h, smem_u32(sd->d), m.src(s), m.dst(d), lane, warp);
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
@@ -859,7 +980,7 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
         const uint32_t tr = J.tile_records;
         conv_range<0>(J.jp.parent, local * tr, (local + 1) * tr, tw, lane, warp, 8);
       } else if (J.kind == JOB_JAG_A2S) {
-        jagged_a2s_tile<0, 0, ConsumerSync>(J.jp, local, states + J.tile_begin, scratch, sh, sync);
+        jagged_a2s_tile<0, 0, ConsumerSync, true>(J.jp, local, states + J.tile_begin, scratch, sh, sync);
         if (!ok) break;
       } else if (J.kind == JOB_JAG_S2A) {
         jagged_s2a_group<0, 0>(J.jp, local * 8 + warp, J.parent_groups, tw, lane);

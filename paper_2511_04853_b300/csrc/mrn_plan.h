@@ -75,7 +75,7 @@ struct JagPlan {
   ConvPlan child;
   char* offsets;             // SoA offsets column (N+1 entries)
   uint32_t off_size;         // 4 or 8
-  uint32_t reserved;
+  uint32_t len_off;          // AoS -> SoA: byte offset of the length in a parent record
   uint64_t offset_base;      // added to every offset written (AoS -> SoA)
   uint64_t pool_n;           // AoS -> SoA: child records in the source pool
   uint64_t capacity;         // AoS -> SoA: child capacity of the destination
