@@ -72,7 +72,7 @@ int plan_job(const mrn_view& src, const mrn_view& dst, std::vector<BatchJob>* ou
     } else {
       j.kind = JOB_JAG_S2A;
       j.parent_groups = (src.n_records + 31) / 32;
-      const uint64_t groups = j.parent_groups + (j.jp.m_src + 31) / 32;
+      const uint64_t groups = j.parent_groups + (j.jp.m_src + MRN_JAG_CHILD_GROUP - 1) / MRN_JAG_CHILD_GROUP;
       j.ntiles = (groups + 7) / 8;
     }
   } else {

@@ -267,9 +267,9 @@ struct JagShared {
   unsigned long long base;
 };
 
-// Loads and stores of one child column element of `size` bytes.
+// Loads and stores of one column element of S bytes.
 template <int S>
-__device__ __forceinline__ unsigned long long ld_elem(const char* p) {
+__device__ __forceinline__ unsigned long long ld_sized(const char* p) {
   if constexpr (S == 8) return __ldg(reinterpret_cast<const unsigned long long*>(p));
   if constexpr (S == 4) return __ldg(reinterpret_cast<const unsigned int*>(p));
   if constexpr (S == 2) return __ldg(reinterpret_cast<const unsigned short*>(p));
@@ -277,14 +277,69 @@ __device__ __forceinline__ unsigned long long ld_elem(const char* p) {
 }
 
 template <int S>
-__device__ __forceinline__ void st_elem(char* p, unsigned long long v) {
+__device__ __forceinline__ void st_sized(char* p, unsigned long long v) {
   if constexpr (S == 8) *reinterpret_cast<unsigned long long*>(p) = v;
   if constexpr (S == 4) *reinterpret_cast<unsigned int*>(p) = (unsigned int)v;
   if constexpr (S == 2) *reinterpret_cast<unsigned short*>(p) = (unsigned short)v;
   if constexpr (S == 1) *reinterpret_cast<unsigned char*>(p) = (unsigned char)v;
 }
 
-constexpr int kJagSlots = 4;  // child slots per lane per pass
+// A record of at most 16 bytes held as two little-endian 64-bit halves,
+// moved with the widest access its alignment `vec` allows.  A field never
+// straddles the halves (natural alignment).
+__device__ __forceinline__ void load_small(const char* p, uint32_t stride, uint32_t vec, uint64_t* lo,
+                                           uint64_t* hi) {
+  uint64_t a = 0, b = 0;
+  if (vec >= 8) {
+    a = __ldg(reinterpret_cast<const unsigned long long*>(p));
+    if (stride > 8) b = __ldg(reinterpret_cast<const unsigned long long*>(p + 8));
+  } else if (vec == 4) {
+#pragma unroll
+    for (uint32_t k = 0; k < 4; ++k)
+      if (4 * k < stride) {
+        const uint64_t w = __ldg(reinterpret_cast<const unsigned int*>(p + 4 * k));
+        if (k < 2) a |= w << (32 * k); else b |= w << (32 * (k - 2));
+      }
+  } else {
+#pragma unroll
+    for (uint32_t k = 0; k < 16; ++k)
+      if (k < stride) {
+        const uint64_t w = __ldg(reinterpret_cast<const unsigned char*>(p + k));
+        if (k < 8) a |= w << (8 * k); else b |= w << (8 * (k - 8));
+      }
+  }
+  *lo = a;
+  *hi = b;
+}
+
+__device__ __forceinline__ void store_small(char* p, uint32_t stride, uint32_t vec, uint64_t lo, uint64_t hi) {
+  if (vec >= 8) {
+    *reinterpret_cast<unsigned long long*>(p) = lo;
+    if (stride > 8) *reinterpret_cast<unsigned long long*>(p + 8) = hi;
+  } else if (vec == 4) {
+#pragma unroll
+    for (uint32_t k = 0; k < 4; ++k)
+      if (4 * k < stride)
+        *reinterpret_cast<unsigned int*>(p + 4 * k) = (unsigned int)(k < 2 ? lo >> (32 * k) : hi >> (32 * (k - 2)));
+  } else {
+#pragma unroll
+    for (uint32_t k = 0; k < 16; ++k)
+      if (k < stride)
+        *reinterpret_cast<unsigned char*>(p + k) = (unsigned char)(k < 8 ? lo >> (8 * k) : hi >> (8 * (k - 8)));
+  }
+}
+
+__device__ __forceinline__ uint64_t small_field(uint64_t lo, uint64_t hi, uint32_t off, uint32_t size) {
+  const uint64_t v = off < 8 ? lo >> (8 * off) : hi >> (8 * (off - 8));
+  return size == 8 ? v : v & ((1ull << (8 * size)) - 1);
+}
+
+template <int S>
+__device__ __forceinline__ void st_col(char* col, uint64_t i, uint64_t v) {
+  st_sized<S>(col + i * S, v);
+}
+
+constexpr int kJagSlots = MRN_JAG_CHILD_GROUP / 32;  // child slots per lane per pass
 
 // One child column for the kJagSlots slots of a lane: all loads, then all
 // stores (zeros where the slot has no valid source).
@@ -293,25 +348,27 @@ __device__ __forceinline__ void child_column(const char* src, uint32_t stride, c
                                              const uint64_t* di, uint32_t ld_ok, uint32_t st_ok) {
   unsigned long long v[kJagSlots];
 #pragma unroll
-  for (int u = 0; u < kJagSlots; ++u) v[u] = (ld_ok >> u) & 1 ? ld_elem<S>(src + si[u] * stride) : 0ull;
+  for (int u = 0; u < kJagSlots; ++u) v[u] = (ld_ok >> u) & 1 ? ld_sized<S>(src + si[u] * stride) : 0ull;
 #pragma unroll
   for (int u = 0; u < kJagSlots; ++u)
-    if ((st_ok >> u) & 1) st_elem<S>(col + di[u] * S, v[u]);
+    if ((st_ok >> u) & 1) st_col<S>(col, di[u], v[u]);
 }
 
 // The children of a jagged tile: slot j (0 <= j < agg) is child
 // j - excl[p] of the last parent p with excl[p] <= j; it moves from pool
 // record beg[p] + j - excl[p] to row base + j of every child column (the
 // destination of a jagged conversion is always SoA).  Each lane moves
-// kJagSlots slots per pass, a column at a time.  When the tile's children
-// form one run of the pool (Run: beg[p] - excl[p] is the same `key` for
-// every parent with children), the parent lookup is skipped.
+// kJagSlots slots per pass: records of at most 16 bytes are loaded whole
+// and split in registers, wider ones column by column.  When the tile's
+// children form one run of the pool (Run: beg[p] - excl[p] is the same `key`
+// for every parent with children), the parent lookup is skipped.
 template <bool Run>
 __device__ __forceinline__ void jagged_children(const JagPlan& jp, const JagShared& sh, unsigned long long agg,
                                                 unsigned long long base, unsigned long long key, int lane,
                                                 int warp) {
   const ConvPlan& C = jp.child;
-  const uint32_t nc = C.naos, stride = C.stride;
+  const uint32_t nc = C.naos, stride = C.stride, vec = C.vec;
+  const char* pool = C.src.base;
   constexpr unsigned long long kPass = 32 * kJagSlots;
   for (unsigned long long j0 = (unsigned long long)warp * kPass; j0 < agg; j0 += 8 * kPass) {
     uint64_t si[kJagSlots], di[kJagSlots];
@@ -339,9 +396,33 @@ __device__ __forceinline__ void jagged_children(const JagPlan& jp, const JagShar
       ld_ok |= (uint32_t)(sok && good) << u;
     }
     if (!st_ok) continue;
+    if (stride <= 16) {
+      uint64_t rl[kJagSlots], rh[kJagSlots];
+#pragma unroll
+      for (int u = 0; u < kJagSlots; ++u) {
+        rl[u] = rh[u] = 0;
+        if ((ld_ok >> u) & 1) load_small(pool + si[u] * stride, stride, vec, &rl[u], &rh[u]);
+      }
+      for (uint32_t ci = 0; ci < nc; ++ci) {
+        const ColPlan cp = C.aos_cols[ci];
+        char* col = C.dst.col[cp.fm];
+#pragma unroll
+        for (int u = 0; u < kJagSlots; ++u) {
+          if (!((st_ok >> u) & 1)) continue;
+          const uint64_t v = small_field(rl[u], rh[u], cp.aos_off, cp.size);
+          switch (cp.size) {
+            case 8: st_col<8>(col, di[u], v); break;
+            case 4: st_col<4>(col, di[u], v); break;
+            case 2: st_col<2>(col, di[u], v); break;
+            default: st_col<1>(col, di[u], v); break;
+          }
+        }
+      }
+      continue;
+    }
     for (uint32_t ci = 0; ci < nc; ++ci) {
       const ColPlan cp = C.aos_cols[ci];
-      const char* src = C.src.base + cp.aos_off;
+      const char* src = pool + cp.aos_off;
       char* col = C.dst.col[cp.fm];
       switch (cp.size) {
         case 8: child_column<8>(src, stride, col, si, di, ld_ok, st_ok); break;
@@ -350,6 +431,51 @@ __device__ __forceinline__ void jagged_children(const JagPlan& jp, const JagShar
         default: child_column<1>(src, stride, col, si, di, ld_ok, st_ok); break;
       }
     }
+  }
+}
+
+// Children of a jagged SoA -> AoS conversion, records [j0, j0 + 32 *
+// kJagSlots) of one warp: records of at most 16 bytes are assembled in
+// registers from the child columns and stored whole; wider ones go through
+// the lane-word path.
+template <int VC>
+__device__ __forceinline__ void jagged_s2a_children(const JagPlan& jp, uint64_t j0, uint32_t* tw, int lane) {
+  const ConvPlan& C = jp.child;
+  const uint32_t stride = C.stride;
+  if (stride > 16) {
+#pragma unroll 1
+    for (int u = 0; u < kJagSlots; ++u) {
+      const uint64_t j = j0 + u * 32 + lane;
+      fm_to_aos_lane<VC>(C, j, j < jp.m_src, C.dst.base + j * stride, tw, lane, 0u, 0ull);
+    }
+    return;
+  }
+  const uint32_t nc = C.naos, vec = C.vec;
+  uint64_t rl[kJagSlots], rh[kJagSlots];
+#pragma unroll
+  for (int u = 0; u < kJagSlots; ++u) rl[u] = rh[u] = 0;
+  for (uint32_t ci = 0; ci < nc; ++ci) {
+    const ColPlan cp = C.aos_cols[ci];
+    const char* col = C.src.col[cp.fm];
+    const uint32_t sh = 8 * (cp.aos_off & 7);
+#pragma unroll
+    for (int u = 0; u < kJagSlots; ++u) {
+      const uint64_t j = j0 + u * 32 + lane;
+      if (j >= jp.m_src) continue;
+      uint64_t v;
+      switch (cp.size) {
+        case 8: v = ld_sized<8>(col + j * 8); break;
+        case 4: v = ld_sized<4>(col + j * 4); break;
+        case 2: v = ld_sized<2>(col + j * 2); break;
+        default: v = ld_sized<1>(col + j); break;
+      }
+      if (cp.aos_off < 8) rl[u] |= v << sh; else rh[u] |= v << sh;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kJagSlots; ++u) {
+    const uint64_t j = j0 + u * 32 + lane;
+    if (j < jp.m_src) store_small(C.dst.base + j * stride, stride, vec, rl[u], rh[u]);
   }
 }
 
@@ -514,9 +640,10 @@ __global__ void __launch_bounds__(256) k_jagged_a2s(const __grid_constant__ JagP
   jagged_a2s_tile<VP, VC>(jp, s_tile, jp.tile_state, tw_all, sh);
 }
 
-// One 32-record group of a jagged SoA -> AoS conversion: groups
-// [0, parent_groups) build parent records (length and begin from the
-// offsets), the following groups convert the m_src children into the pool.
+// One warp group of a jagged SoA -> AoS conversion: groups [0,
+// parent_groups) build 32 parent records each (length and begin from the
+// offsets), the following groups convert MRN_JAG_CHILD_GROUP of the m_src
+// children each into the pool.
 template <int VP, int VC>
 __device__ __forceinline__ void jagged_s2a_group(const JagPlan& jp, uint64_t w, uint64_t parent_groups,
                                                  uint32_t* tw, int lane) {
@@ -532,10 +659,7 @@ __device__ __forceinline__ void jagged_s2a_group(const JagPlan& jp, uint64_t w, 
     }
     fm_to_aos_lane<VP>(P, r, ok, P.dst.base + r * P.stride, tw, lane, (uint32_t)(b - a), a);
   } else {
-    const ConvPlan& C = jp.child;
-    const uint64_t j = (w - parent_groups) * 32 + lane;
-    const bool ok = j < jp.m_src;
-    fm_to_aos_lane<VC>(C, j, ok, C.dst.base + j * C.stride, tw, lane, 0u, 0ull);
+    jagged_s2a_children<VC>(jp, (w - parent_groups) * MRN_JAG_CHILD_GROUP, tw, lane);
   }
 }
 
@@ -546,7 +670,7 @@ __global__ void __launch_bounds__(256) k_jagged_s2a(const __grid_constant__ JagP
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* tw = smem + warp * MRN_TW_WORDS_PER_WARP;
   const uint64_t wpb = blockDim.x >> 5;
-  const uint64_t all = parent_groups + (jp.m_src + 31) / 32;
+  const uint64_t all = parent_groups + (jp.m_src + MRN_JAG_CHILD_GROUP - 1) / MRN_JAG_CHILD_GROUP;
   const uint64_t total_warps = (uint64_t)gridDim.x * wpb;
   for (uint64_t w = (uint64_t)blockIdx.x * wpb + warp; w < all; w += total_warps)
     jagged_s2a_group<VP, VC>(jp, w, parent_groups, tw, lane);
@@ -1193,7 +1317,7 @@ int launch_jagged_a2s(JagPlan& jp, void* scratch, void* stream) {
 
 int launch_jagged_s2a(const JagPlan& jp, void* stream) {
   const uint64_t pw = (jp.parent.n + 31) / 32;
-  const uint64_t cw = (jp.m_src + 31) / 32;
+  const uint64_t cw = (jp.m_src + MRN_JAG_CHILD_GROUP - 1) / MRN_JAG_CHILD_GROUP;
   if (pw + cw == 0) return MRN_OK;
   void* fn = jag_s2a(jp.parent.vec, jp.child.vec);
   const int per_sm = occupancy(fn, 256, kConvSmem);

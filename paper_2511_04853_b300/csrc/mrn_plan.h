@@ -101,6 +101,7 @@ struct GapPlan {
 };
 
 #define MRN_JAG_TILE 256  // parents per tile of the jagged scan
+#define MRN_JAG_CHILD_GROUP 128  // child records per warp group of a jagged SoA -> AoS conversion
 
 // One job of a batched launch: a plain conversion (plan in jp.parent), a
 // jagged conversion, or the zero-fill of a destination's alignment holes,

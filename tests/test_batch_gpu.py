@@ -118,3 +118,61 @@ def test_autotune_then_convert_still_exact():
     want = oracle.convert(o, o_aos, "soa").base
     assert np.array_equal(host(dst.tensors[0], want.size), want)
     mrn.autotune_clear()
+
+
+def test_jagged_jobs_shuffled_pools_many_tiles():
+    """Jagged jobs of many tiles (look-back across CTAs), canonical and
+    shuffled child pools, between plain conversions, in one launch."""
+    pairs, checks = [], []
+    for j, n in enumerate([3000, 41000, 257, 25000, 60000]):
+        s, o = mrn.Schema(datagen.TRACKS), oracle.Schema(datagen.TRACKS)
+        d = datagen.workload("tracks", n, 500 + j)
+        o_aos = oracle.pack(o, d, "aos")
+        if j % 2:
+            order = np.random.default_rng(j).permutation(n)
+            o_aos = oracle.shuffle_pool(o, o_aos, order, gap=1)
+        want = oracle.convert(o, o_aos, "soa", m=d["m"]).base
+        src = mrn.View(s, "aos", n, base=dev(o_aos.base), child_pool=dev(o_aos.pool), m=o_aos.m)
+        dst = dev_dest(s, "soa", n, d["m"])
+        pairs.append((src, dst))
+        checks.append((dst, want))
+        c_s, c_o = mrn.Schema(datagen.CELLS), oracle.Schema(datagen.CELLS)
+        cd = datagen.workload("cells", 5000 + j, 600 + j)
+        c_src = oracle.pack(c_o, cd, "aos")
+        c_dst = dev_dest(c_s, "aosoa", 5000 + j, 0, 32)
+        pairs.append((mrn.View(c_s, "aos", 5000 + j, base=dev(c_src.base)), c_dst))
+        checks.append((c_dst, oracle.convert(c_o, c_src, "aosoa", 32).base))
+    b = mrn.Batch(pairs, use_graph=True)
+    for _ in range(2):
+        for dst, _ in checks:
+            dst.tensors[0].fill_(0xA5)
+        b.launch()
+        assert mrn.sync() == mrn.OK
+        for k, (dst, want) in enumerate(checks):
+            assert np.array_equal(host(dst.tensors[0], want.size), want), "job %d" % k
+
+
+def test_batch_lookback_wait_is_bounded():
+    """Host-side fault injection: jagged tile 1 of a batched job never
+    publishes its sum, so tile 2's look-back must expire (1 ms bound) and
+    report MRN_ETIMEOUT; batches built afterwards run normally."""
+    n = 4 * 256
+    s, o = mrn.Schema(datagen.TRACKS), oracle.Schema(datagen.TRACKS)
+    d = datagen.workload("tracks", n, 3)
+    o_aos = oracle.pack(o, d, "aos")
+    src = mrn.View(s, "aos", n, base=dev(o_aos.base), child_pool=dev(o_aos.pool), m=d["m"])
+    try:
+        mrn.debug_set(2, 1_000_000)
+        mrn.debug_set(1, 1)
+        b = mrn.Batch([(src, dev_dest(s, "soa", n, d["m"]))], use_graph=False)
+    finally:
+        mrn.debug_set(1, -1)
+        mrn.debug_set(2, 2_000_000_000)
+    b.launch()
+    assert mrn.sync() == mrn.ETIMEOUT
+    dst = dev_dest(s, "soa", n, d["m"])
+    b2 = mrn.Batch([(src, dst)], use_graph=False)
+    b2.launch()
+    assert mrn.sync() == mrn.OK
+    want = oracle.convert(o, o_aos, "soa", m=d["m"]).base
+    assert np.array_equal(host(dst.tensors[0], want.size), want)

@@ -58,6 +58,28 @@ def test_tracks_raw_bits_and_shuffled_pool_with_gaps():
     a2s_check(s, o, shuffled, m_cap=d["m"])
 
 
+def test_stray_empty_begins_and_one_tile_out_of_order():
+    """A tile whose children form one run of the pool is gathered without a
+    parent lookup; empty parents may carry any begin within the pool without
+    breaking the run, and a tile whose runs are out of order (tile 1 here)
+    takes the general path.  Both must equal the oracle."""
+    n = 4 * 256 + 17
+    s, o, d = tracks(n, seed=11, mean_len=2.0)
+    o_aos = oracle.pack(o, d, "aos")
+    lens = d["lengths"]
+    assert (lens == 0).sum() > 50
+    order = np.arange(n)
+    cand = [i for i in range(256, 512) if lens[i] > 0]
+    i, j = cand[3], cand[10]
+    order[i], order[j] = j, i
+    sh = oracle.shuffle_pool(o, o_aos, order, gap=0)
+    rng = np.random.default_rng(4)
+    recs = sh.base[: n * 24].reshape(n, 24)
+    for k in np.nonzero(lens == 0)[0]:
+        recs[k, 16:24] = np.array([rng.integers(0, d["m"] + 1)], np.uint64).view(np.uint8)
+    a2s_check(s, o, sh, m_cap=d["m"])
+
+
 @pytest.mark.parametrize("n", [0, 1, 255, 256, 257, 1000, 5003])
 @pytest.mark.parametrize("osz", ["u32", "u64"])
 def test_sizes_and_offset_types(n, osz):
