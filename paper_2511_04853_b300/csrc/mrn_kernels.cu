@@ -720,7 +720,7 @@ __global__ void k_write_offset0(char* offs, uint32_t osz, unsigned long long v) 
 // before the stage's loads.  Every wait is bounded; on expiry the warp that
 // saw it records MRN_ETIMEOUT and stops, and the others follow.
 constexpr uint32_t kBStage = MRN_BATCH_STAGE_BYTES;
-constexpr uint32_t kBNS = 3;      // source stages
+constexpr uint32_t kBNS = 2;      // source stages
 constexpr uint32_t kBND = 2;      // destination buffers
 constexpr uint32_t kRing = 8;     // decided tiles in flight
 constexpr uint32_t kSQ = 8;       // staged tiles between loader and storer
