@@ -312,7 +312,7 @@ void plan_tiles(const mrn_schema* s, ConvPlan* p, uint32_t stage_bytes) { tile_g
 
 int build_plan(const mrn_view& src, const mrn_view& dst, ConvPlan* p) {
   int rc = level_plan(src.schema, src, dst, false, src.n_records, p);
-  if (!rc) tile_geometry(src.schema, p, MRN_STAGE_BYTES);
+  if (!rc) tile_geometry(src.schema, p, MRN_BATCH_STAGE_BYTES);
   mrn_layout a = src.layout, b = dst.layout;
   if (a.kind != MRN_AOSOA) a.block = 0;
   if (b.kind != MRN_AOSOA) b.block = 0;

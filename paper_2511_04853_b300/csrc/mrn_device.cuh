@@ -13,8 +13,10 @@
 //    lane-private shared-memory column (word k of lane l at k*33 + l, so a
 //    warp's accesses to word k hit 32 distinct banks); fields are extracted
 //    from / merged into those words by their byte offset, which the schema
-//    only knows at run time.  Records longer than 64 bytes are processed in
-//    64-byte windows (a naturally aligned field never straddles one).
+//    only knows at run time.  Records longer than a window (W words: 64
+//    bytes for the per-call kernels, 32 for the batch kernel, whose shared
+//    memory is tighter) are processed window by window (a naturally aligned
+//    field never straddles one).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -25,6 +27,7 @@
 #define MRN_WIN_WORDS 16
 #define MRN_TW_PITCH 33
 #define MRN_TW_WORDS_PER_WARP (MRN_WIN_WORDS * MRN_TW_PITCH)
+#define MRN_TW_WORDS(W) ((W) * MRN_TW_PITCH)
 
 __device__ __forceinline__ uint32_t lowbits_mask(uint32_t size) {
   return size >= 4 ? 0xffffffffu : ((1u << (8 * size)) - 1u);
@@ -71,97 +74,97 @@ __device__ __forceinline__ void st_elem(char* a, uint32_t size, uint64_t v) {
   }
 }
 
-// Loads nbytes (<= 64, a multiple of V) of a record window into w[0..15]
+// Loads nbytes (<= 4W, a multiple of V) of a record window into w[0..W-1]
 // with V-byte accesses; w must be zero on entry for V < 4.
-template <int V, bool G = true>
-__device__ __forceinline__ void load_words(const char* p, uint32_t nbytes, uint32_t (&w)[16]) {
+template <int V, int W, bool G = true>
+__device__ __forceinline__ void load_words(const char* p, uint32_t nbytes, uint32_t (&w)[W]) {
   if constexpr (V == 16) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < W / 4; ++k)
       if (k * 16 < (int)nbytes) {
         uint4 v = ldx<G>(reinterpret_cast<const uint4*>(p) + k);
         w[4 * k] = v.x; w[4 * k + 1] = v.y; w[4 * k + 2] = v.z; w[4 * k + 3] = v.w;
       }
   } else if constexpr (V == 8) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < W / 2; ++k)
       if (k * 8 < (int)nbytes) {
         uint2 v = ldx<G>(reinterpret_cast<const uint2*>(p) + k);
         w[2 * k] = v.x; w[2 * k + 1] = v.y;
       }
   } else if constexpr (V == 4) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
+    for (int k = 0; k < W; ++k)
       if (k * 4 < (int)nbytes) w[k] = ldx<G>(reinterpret_cast<const unsigned int*>(p) + k);
   } else if constexpr (V == 2) {
 #pragma unroll
-    for (int k = 0; k < 32; ++k)
+    for (int k = 0; k < 2 * W; ++k)
       if (k * 2 < (int)nbytes)
         w[k >> 1] |= (uint32_t)ldx<G>(reinterpret_cast<const unsigned short*>(p) + k) << ((k & 1) * 16);
   } else {
 #pragma unroll
-    for (int k = 0; k < 64; ++k)
+    for (int k = 0; k < 4 * W; ++k)
       if (k < (int)nbytes)
         w[k >> 2] |= (uint32_t)ldx<G>(reinterpret_cast<const unsigned char*>(p) + k) << ((k & 3) * 8);
   }
 }
 
 // V == 0: the access width is chosen at run time from `vec` (a uniform
-// branch per 64-byte window), for kernels that serve many plans at once.
-template <int V, bool G = true>
-__device__ __forceinline__ void load_any(const char* p, uint32_t nbytes, uint32_t (&w)[16], uint32_t vec) {
+// branch per window), for kernels that serve many plans at once.
+template <int V, int W, bool G = true>
+__device__ __forceinline__ void load_any(const char* p, uint32_t nbytes, uint32_t (&w)[W], uint32_t vec) {
   if constexpr (V != 0) {
-    load_words<V, G>(p, nbytes, w);
+    load_words<V, W, G>(p, nbytes, w);
   } else {
     switch (vec) {
-      case 16: load_words<16, G>(p, nbytes, w); break;
-      case 8: load_words<8, G>(p, nbytes, w); break;
-      case 4: load_words<4, G>(p, nbytes, w); break;
-      case 2: load_words<2, G>(p, nbytes, w); break;
-      default: load_words<1, G>(p, nbytes, w); break;
+      case 16: load_words<16, W, G>(p, nbytes, w); break;
+      case 8: load_words<8, W, G>(p, nbytes, w); break;
+      case 4: load_words<4, W, G>(p, nbytes, w); break;
+      case 2: load_words<2, W, G>(p, nbytes, w); break;
+      default: load_words<1, W, G>(p, nbytes, w); break;
     }
   }
 }
 
-template <int V>
-__device__ __forceinline__ void store_words(char* p, uint32_t nbytes, const uint32_t (&w)[16]) {
+template <int V, int W>
+__device__ __forceinline__ void store_words(char* p, uint32_t nbytes, const uint32_t (&w)[W]) {
   if constexpr (V == 16) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < W / 4; ++k)
       if (k * 16 < (int)nbytes)
         reinterpret_cast<uint4*>(p)[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
   } else if constexpr (V == 8) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < W / 2; ++k)
       if (k * 8 < (int)nbytes) reinterpret_cast<uint2*>(p)[k] = make_uint2(w[2 * k], w[2 * k + 1]);
   } else if constexpr (V == 4) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
+    for (int k = 0; k < W; ++k)
       if (k * 4 < (int)nbytes) reinterpret_cast<unsigned int*>(p)[k] = w[k];
   } else if constexpr (V == 2) {
 #pragma unroll
-    for (int k = 0; k < 32; ++k)
+    for (int k = 0; k < 2 * W; ++k)
       if (k * 2 < (int)nbytes)
         reinterpret_cast<unsigned short*>(p)[k] = (unsigned short)(w[k >> 1] >> ((k & 1) * 16));
   } else {
 #pragma unroll
-    for (int k = 0; k < 64; ++k)
+    for (int k = 0; k < 4 * W; ++k)
       if (k < (int)nbytes)
         reinterpret_cast<unsigned char*>(p)[k] = (unsigned char)(w[k >> 2] >> ((k & 3) * 8));
   }
 }
 
-template <int V>
-__device__ __forceinline__ void store_any(char* p, uint32_t nbytes, const uint32_t (&w)[16], uint32_t vec) {
+template <int V, int W>
+__device__ __forceinline__ void store_any(char* p, uint32_t nbytes, const uint32_t (&w)[W], uint32_t vec) {
   if constexpr (V != 0) {
-    store_words<V>(p, nbytes, w);
+    store_words<V, W>(p, nbytes, w);
   } else {
     switch (vec) {
-      case 16: store_words<16>(p, nbytes, w); break;
-      case 8: store_words<8>(p, nbytes, w); break;
-      case 4: store_words<4>(p, nbytes, w); break;
-      case 2: store_words<2>(p, nbytes, w); break;
-      default: store_words<1>(p, nbytes, w); break;
+      case 16: store_words<16, W>(p, nbytes, w); break;
+      case 8: store_words<8, W>(p, nbytes, w); break;
+      case 4: store_words<4, W>(p, nbytes, w); break;
+      case 2: store_words<2, W>(p, nbytes, w); break;
+      default: store_words<1, W>(p, nbytes, w); break;
     }
   }
 }
@@ -171,23 +174,23 @@ __device__ __forceinline__ void store_any(char* p, uint32_t nbytes, const uint32
 //   ld_ok  the lane has a source record at `rec`
 //   st_ok  the lane writes destination record r (zeros when !ld_ok)
 // The jagged descriptor, if the plan has one, is returned in *jlen / *jbeg.
-template <int V>
+template <int V, int W = MRN_WIN_WORDS>
 __device__ __forceinline__ void aos_to_fm_lane(const ConvPlan& p, uint64_t r, bool ld_ok, bool st_ok,
                                                const char* rec, uint32_t* tw, int lane,
                                                uint32_t* jlen, uint64_t* jbeg) {
   uint32_t ci = 0;
   const uint32_t naos = p.naos, stride = p.stride, aw = p.aos_words;
-  for (uint32_t win = 0; win < aw; win += MRN_WIN_WORDS) {
-    uint32_t w[16];
+  for (uint32_t win = 0; win < aw; win += W) {
+    uint32_t w[W];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) w[k] = 0;
-    const uint32_t nb = min(64u, stride - win * 4);
-    if (ld_ok) load_any<V>(rec + win * 4, nb, w, p.vec);
-    const uint32_t nw = min((uint32_t)MRN_WIN_WORDS, aw - win);
+    for (int k = 0; k < W; ++k) w[k] = 0;
+    const uint32_t nb = min(4u * W, stride - win * 4);
+    if (ld_ok) load_any<V, W>(rec + win * 4, nb, w, p.vec);
+    const uint32_t nw = min((uint32_t)W, aw - win);
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
+    for (int k = 0; k < W; ++k)
       if (k < (int)nw) tw[k * MRN_TW_PITCH + lane] = w[k];
-    const uint32_t wend = (win + MRN_WIN_WORDS) * 4;
+    const uint32_t wend = (win + W) * 4;
     for (; ci < naos; ++ci) {
       const ColPlan cp = p.aos_cols[ci];
       if (cp.aos_off >= wend) break;
@@ -217,17 +220,17 @@ __device__ __forceinline__ void aos_to_fm_lane(const ConvPlan& p, uint64_t r, bo
 
 // Field-major columns -> AoS record, one record per lane; padding bytes are
 // written as zero.  The jagged descriptor (if any) is taken from jlen/jbeg.
-template <int V>
+template <int V, int W = MRN_WIN_WORDS>
 __device__ __forceinline__ void fm_to_aos_lane(const ConvPlan& p, uint64_t r, bool ok, char* rec,
                                                uint32_t* tw, int lane, uint32_t jlen, uint64_t jbeg) {
   uint32_t ci = 0;
   const uint32_t naos = p.naos, stride = p.stride, aw = p.aos_words;
-  for (uint32_t win = 0; win < aw; win += MRN_WIN_WORDS) {
-    const uint32_t nw = min((uint32_t)MRN_WIN_WORDS, aw - win);
+  for (uint32_t win = 0; win < aw; win += W) {
+    const uint32_t nw = min((uint32_t)W, aw - win);
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
+    for (int k = 0; k < W; ++k)
       if (k < (int)nw) tw[k * MRN_TW_PITCH + lane] = 0;
-    const uint32_t wend = (win + MRN_WIN_WORDS) * 4;
+    const uint32_t wend = (win + W) * 4;
     for (; ci < naos; ++ci) {
       const ColPlan cp = p.aos_cols[ci];
       if (cp.aos_off >= wend) break;
@@ -248,10 +251,10 @@ __device__ __forceinline__ void fm_to_aos_lane(const ConvPlan& p, uint64_t r, bo
       }
     }
     if (ok) {
-      uint32_t w[16];
+      uint32_t w[W];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) w[k] = k < (int)nw ? tw[k * MRN_TW_PITCH + lane] : 0u;
-      store_any<V>(rec + win * 4, min(64u, stride - win * 4), w, p.vec);
+      for (int k = 0; k < W; ++k) w[k] = k < (int)nw ? tw[k * MRN_TW_PITCH + lane] : 0u;
+      store_any<V, W>(rec + win * 4, min(4u * W, stride - win * 4), w, p.vec);
     }
   }
 }
@@ -364,100 +367,6 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 // async-proxy (bulk copy) accesses.
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// ------------------------------------------------ shared-memory tiles
-
-// Element r (tile-local) of field-major column c inside a tile.
-__device__ __forceinline__ char* tile_fm(const SidePlan& sp, const uint32_t* off, char* tile, int c,
-                                         uint32_t size, uint32_t r) {
-  if (sp.kind == K_SOA) return tile + off[c] + r * size;
-  uint32_t blk, slot;
-  if (sp.block_shift != MRN_NO_SHIFT) {
-    blk = r >> sp.block_shift;
-    slot = r & (sp.block - 1);
-  } else {
-    blk = r / sp.block;
-    slot = r - blk * sp.block;
-  }
-  return tile + (uint64_t)blk * sp.block_bytes + off[c] + slot * size;
-}
-
-// Tile transforms, one record per lane; every record of the tile exists.
-template <int V>
-__device__ __forceinline__ void tile_aos_to_fm(const ConvPlan& p, const char* stile, char* dtile, uint32_t r,
-                                               uint32_t* tw, int lane) {
-  const char* rec = stile + (uint64_t)r * p.stride;
-  uint32_t ci = 0;
-  const uint32_t naos = p.naos, stride = p.stride, aw = p.aos_words;
-  for (uint32_t win = 0; win < aw; win += MRN_WIN_WORDS) {
-    uint32_t w[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) w[k] = 0;
-    load_any<V, false>(rec + win * 4, min(64u, stride - win * 4), w, p.vec);
-    const uint32_t nw = min((uint32_t)MRN_WIN_WORDS, aw - win);
-#pragma unroll
-    for (int k = 0; k < 16; ++k)
-      if (k < (int)nw) tw[k * MRN_TW_PITCH + lane] = w[k];
-    const uint32_t wend = (win + MRN_WIN_WORDS) * 4;
-    for (; ci < naos; ++ci) {
-      const ColPlan cp = p.aos_cols[ci];
-      if (cp.aos_off >= wend) break;
-      const uint32_t wi = cp.aos_off / 4 - win;
-      const uint32_t lo = tw[wi * MRN_TW_PITCH + lane];
-      char* d = tile_fm(p.dst, p.tg.dst_off, dtile, cp.fm, cp.size, r);
-      const uint32_t sh = (cp.aos_off & 3) * 8;
-      switch (cp.size) {
-        case 1: *reinterpret_cast<unsigned char*>(d) = (unsigned char)(lo >> sh); break;
-        case 2: *reinterpret_cast<unsigned short*>(d) = (unsigned short)(lo >> sh); break;
-        case 4: *reinterpret_cast<unsigned int*>(d) = lo; break;
-        default: *reinterpret_cast<uint2*>(d) = make_uint2(lo, tw[(wi + 1) * MRN_TW_PITCH + lane]); break;
-      }
-    }
-  }
-}
-
-template <int V>
-__device__ __forceinline__ void tile_fm_to_aos(const ConvPlan& p, const char* stile, char* dtile, uint32_t r,
-                                               uint32_t* tw, int lane) {
-  char* rec = dtile + (uint64_t)r * p.stride;
-  uint32_t ci = 0;
-  const uint32_t naos = p.naos, stride = p.stride, aw = p.aos_words;
-  for (uint32_t win = 0; win < aw; win += MRN_WIN_WORDS) {
-    const uint32_t nw = min((uint32_t)MRN_WIN_WORDS, aw - win);
-#pragma unroll
-    for (int k = 0; k < 16; ++k)
-      if (k < (int)nw) tw[k * MRN_TW_PITCH + lane] = 0;
-    const uint32_t wend = (win + MRN_WIN_WORDS) * 4;
-    for (; ci < naos; ++ci) {
-      const ColPlan cp = p.aos_cols[ci];
-      if (cp.aos_off >= wend) break;
-      const uint32_t wi = cp.aos_off / 4 - win;
-      const uint64_t v = ld_elem<false>(tile_fm(p.src, p.tg.src_off, const_cast<char*>(stile), cp.fm, cp.size, r),
-                                        cp.size);
-      uint32_t* t = tw + wi * MRN_TW_PITCH + lane;
-      if (cp.size == 8) {
-        t[0] = (uint32_t)v;
-        t[MRN_TW_PITCH] = (uint32_t)(v >> 32);
-      } else if (cp.size == 4) {
-        t[0] = (uint32_t)v;
-      } else {
-        t[0] |= (uint32_t)v << ((cp.aos_off & 3) * 8);
-      }
-    }
-    uint32_t w[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) w[k] = k < (int)nw ? tw[k * MRN_TW_PITCH + lane] : 0u;
-    store_any<V>(rec + win * 4, min(64u, stride - win * 4), w, p.vec);
-  }
-}
-
-__device__ __forceinline__ void tile_fm_to_fm(const ConvPlan& p, const char* stile, char* dtile, uint32_t r) {
-  for (uint32_t c = 0; c < p.ncols; ++c) {
-    const uint32_t sz = p.fm_size[c];
-    const uint64_t v = ld_elem<false>(tile_fm(p.src, p.tg.src_off, const_cast<char*>(stile), c, sz, r), sz);
-    st_elem(tile_fm(p.dst, p.tg.dst_off, dtile, c, sz, r), sz, v);
-  }
 }
 
 // 32-bit shared-memory accesses (the staged kernels address tiles with

@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 
 #include "mrn_device.cuh"
@@ -16,7 +17,7 @@ __device__ __forceinline__ void flag_error(int code) { atomicOr(&g_mrn_status_bi
 // ------------------------------------------------------------- conversion
 
 // Records [t0, t1) of a plan; the CTA's warps take 32-record groups in turn.
-template <int V>
+template <int V, int W = MRN_WIN_WORDS>
 __device__ __forceinline__ void conv_range(const ConvPlan& p, uint64_t t0, uint64_t t1, uint32_t* tw,
                                            int lane, int warp, int nwarps) {
   const uint32_t dir = p.dir;
@@ -29,9 +30,9 @@ __device__ __forceinline__ void conv_range(const ConvPlan& p, uint64_t t0, uint6
     if (dir == DIR_AOS_FM) {
       uint32_t jl = 0;
       uint64_t jb = 0;
-      aos_to_fm_lane<V>(p, r, ld_ok, st_ok, p.src.base + r * p.stride, tw, lane, &jl, &jb);
+      aos_to_fm_lane<V, W>(p, r, ld_ok, st_ok, p.src.base + r * p.stride, tw, lane, &jl, &jb);
     } else if (dir == DIR_FM_AOS) {
-      fm_to_aos_lane<V>(p, r, ld_ok, p.dst.base + r * p.stride, tw, lane, 0u, 0ull);
+      fm_to_aos_lane<V, W>(p, r, ld_ok, p.dst.base + r * p.stride, tw, lane, 0u, 0ull);
     } else {
       fm_to_fm_lane(p, r, ld_ok, st_ok);
     }
@@ -52,59 +53,7 @@ __global__ void __launch_bounds__(256) k_convert(const __grid_constant__ ConvPla
     conv_range<V>(p, t * tile_records, (t + 1) * tile_records, tw, lane, warp, nwarps);
 }
 
-// ------------------------------------------------- TMA-staged conversion
-
-// Shared memory of the staged kernels: kNS source stages and two destination
-// tile buffers of kStage bytes each, then kNS mbarriers.  Tiles that take the
-// direct path use the destination buffers as their lane-word scratch (after
-// the bulk stores reading them have drained).
-constexpr uint32_t kStage = MRN_STAGE_BYTES;
-constexpr uint32_t kNS = 4;
-constexpr size_t kTmaSmem = (size_t)(kNS + 2) * kStage + 128;
-static_assert(2 * kStage >= 8 * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t) + 4352,
-              "direct-tile scratch fits the destination buffers");
-
-__device__ __forceinline__ char* stage_src(char* smem, uint32_t s) { return smem + s * kStage; }
-__device__ __forceinline__ char* stage_dst(char* smem, uint32_t d) { return smem + (kNS + d) * kStage; }
-__device__ __forceinline__ unsigned long long* stage_bar(char* smem, uint32_t s) {
-  return reinterpret_cast<unsigned long long*>(smem + (kNS + 2) * kStage) + s;
-}
-__device__ __forceinline__ uint32_t* direct_scratch(char* smem) {
-  return reinterpret_cast<uint32_t*>(smem + kNS * kStage);
-}
-
-// Thread 0: bulk loads of source tile lt into a stage buffer.
-__device__ __forceinline__ void tma_load_tile(const ConvPlan& p, uint64_t lt, char* stage,
-                                              unsigned long long* bar) {
-  const TileGeom& g = p.tg;
-  const uint64_t t0 = lt * g.T;
-  const SidePlan& sp = p.src;
-  mbar_expect_tx(bar, g.src_bytes);
-  if (sp.kind == K_AOS) {
-    bulk_g2s(stage, sp.base + t0 * p.stride, g.src_bytes, bar);
-  } else if (sp.kind == K_AOSOA) {
-    bulk_g2s(stage, sp.base + (t0 / sp.block) * sp.block_bytes, g.src_bytes, bar);
-  } else {
-    for (uint32_t c = 0; c < p.ncols; ++c)
-      bulk_g2s(stage + g.src_off[c], sp.col[c] + t0 * p.fm_size[c], g.T * p.fm_size[c], bar);
-  }
-}
-
-// Thread 0: bulk stores of destination tile lt from a tile buffer.
-__device__ __forceinline__ void tma_store_tile(const ConvPlan& p, uint64_t lt, const char* tile) {
-  const TileGeom& g = p.tg;
-  const uint64_t t0 = lt * g.T;
-  const SidePlan& sp = p.dst;
-  if (sp.kind == K_AOS) {
-    bulk_s2g(sp.base + t0 * p.stride, tile, g.dst_bytes);
-  } else if (sp.kind == K_AOSOA) {
-    bulk_s2g(sp.base + (t0 / sp.block) * sp.block_bytes, tile, g.dst_bytes);
-  } else {
-    for (uint32_t c = 0; c < p.ncols; ++c)
-      bulk_s2g(sp.col[c] + t0 * p.fm_size[c], tile + g.dst_off[c], g.T * p.fm_size[c]);
-  }
-  bulk_commit();
-}
+// ------------------------------------------------- staged tile transform
 
 // All threads: source tile -> destination tile in shared memory.
 __device__ __forceinline__ void tma_transform(const TileHdr& h, uint32_t desc, const char* st, char* dt, int lane,
@@ -134,94 +83,6 @@ __device__ __forceinline__ TileHdr tile_hdr(const ConvPlan& p) {
   tile_side_geometry(p.dst.kind, p.dst.block, p.dst.block_shift, p.dst.block_bytes, p.stride, &h.dblock, &h.dshift,
                      &h.dbb);
   return h;
-}
-
-// Threads [0, ncols): the plan's column descriptors into shared memory;
-// thread 0 also the header.
-__device__ __forceinline__ void load_sdesc(const ConvPlan& p, uint4* sdesc, TileHdr* hdr) {
-  const uint32_t c = threadIdx.x;
-  if (c < p.ncols) sdesc[c] = tile_desc(p, c);
-  if (c == 0) *hdr = tile_hdr(p);
-}
-
-// A staged tile whose mbarrier did not complete within its bound: record
-// the error, let this CTA's copies still in flight land (bounded) and stop.
-// pending: bit s = stage s has loads in flight; phase: bit s = their parity.
-__device__ __forceinline__ void tma_abort(char* smem, uint32_t pending, uint32_t phase) {
-  if (threadIdx.x == 0) {
-    flag_error(MRN_ETIMEOUT);
-    for (uint32_t s = 0; s < kNS; ++s)
-      if ((pending >> s) & 1) mbar_wait_bounded(stage_bar(smem, s), (phase >> s) & 1);
-    bulk_wait_all();
-  }
-}
-
-__device__ __forceinline__ void init_stage_bars(char* smem) {
-  for (uint32_t s = 0; s < kNS; ++s) mbar_init(stage_bar(smem, s), 1);
-  fence_mbar_init();
-}
-
-// One conversion with full tiles staged through shared memory by TMA bulk
-// copies: kNS source stages keep up to kNS tiles' loads in flight while
-// tiles are transformed, and two destination buffers let a tile's bulk
-// stores overlap the next transform.  The partial last tile, if any, takes
-// the direct path.  CTA b takes tiles b, b + grid, ...
-__global__ void __launch_bounds__(256, 3) k_convert_tma(const __grid_constant__ ConvPlan p) {
-  extern __shared__ __align__(128) char staged_smem[];
-  __shared__ int s_abort;
-  __shared__ uint4 sdesc[MRN_MAX_COLS];
-  __shared__ TileHdr hdr;
-  char* sm = staged_smem;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t T = p.tg.T;
-  const uint64_t nrec = p.dir == DIR_FM_AOS ? p.n : p.n_fm_pad;
-  const uint64_t ntiles = (nrec + T - 1) / T;
-  const uint64_t nfull = p.n / T;
-  const uint64_t G = gridDim.x, b = blockIdx.x;
-  uint32_t pending = 0, phase = 0, dsel = 0;
-  if (tid == 0) {
-    init_stage_bars(sm);
-    s_abort = 0;
-    for (uint32_t k = 0; k < kNS; ++k)
-      if (b + k * G < nfull) tma_load_tile(p, b + k * G, stage_src(sm, k), stage_bar(sm, k));
-  }
-  for (uint32_t k = 0; k < kNS; ++k)
-    if (b + k * G < nfull) pending |= 1u << k;
-  load_sdesc(p, sdesc, &hdr);
-  __syncthreads();
-  const uint32_t desc = smem_u32(sdesc);
-  for (uint64_t k = 0;; ++k) {
-    const uint64_t t = b + k * G;
-    if (t >= ntiles) break;
-    if (t < nfull) {
-      const uint32_t s = (uint32_t)(k % kNS);
-      if (!mbar_wait_bounded(stage_bar(sm, s), (phase >> s) & 1)) s_abort = 1;
-      if (tid == 0) bulk_wait_read<1>();  // destination buffer dsel is free
-      __syncthreads();
-      if (s_abort) {
-        tma_abort(sm, pending, phase);
-        return;
-      }
-      pending &= ~(1u << s);
-      phase ^= 1u << s;
-      tma_transform(hdr, desc, stage_src(sm, s), stage_dst(sm, dsel), lane, warp);
-      fence_proxy_async_smem();
-      __syncthreads();
-      const uint64_t nt = t + kNS * G;
-      if (tid == 0) {
-        tma_store_tile(p, t, stage_dst(sm, dsel));
-        if (nt < nfull) tma_load_tile(p, nt, stage_src(sm, s), stage_bar(sm, s));
-      }
-      if (nt < nfull) pending |= 1u << s;
-      dsel ^= 1;
-    } else {
-      if (tid == 0) bulk_wait_read<0>();
-      __syncthreads();
-      conv_range<0>(p, t * T, (t + 1) * T, direct_scratch(sm) + warp * MRN_TW_WORDS_PER_WARP, lane, warp, 8);
-      __syncthreads();
-    }
-  }
-  if (tid == 0) bulk_wait_all();
 }
 
 __device__ __forceinline__ void zero_gap_item(const GapPlan& g, uint64_t t) {
@@ -259,9 +120,15 @@ struct CtaSync {
   __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };
 
+// Shared state of a jagged tile.  The per-parent arrays (JagShared) are
+// written only after every warp has finished its parent conversion, so the
+// batch kernel lays them over its lane-word scratch; the small per-warp
+// values (JagWarp) are written earlier and need their own space.
 struct JagShared {
   unsigned long long excl[MRN_JAG_TILE + 1];
   unsigned long long beg[MRN_JAG_TILE];
+};
+struct JagWarp {
   unsigned long long warp[8];
   unsigned long long kmin[8], kmax[8];  // per warp: min / max of begin - exclusive offset
   unsigned long long base;
@@ -438,7 +305,7 @@ __device__ __forceinline__ void jagged_children(const JagPlan& jp, const JagShar
 // kJagSlots) of one warp: records of at most 16 bytes are assembled in
 // registers from the child columns and stored whole; wider ones go through
 // the lane-word path.
-template <int VC>
+template <int VC, int W = MRN_WIN_WORDS>
 __device__ __forceinline__ void jagged_s2a_children(const JagPlan& jp, uint64_t j0, uint32_t* tw, int lane) {
   const ConvPlan& C = jp.child;
   const uint32_t stride = C.stride;
@@ -446,7 +313,7 @@ __device__ __forceinline__ void jagged_s2a_children(const JagPlan& jp, uint64_t 
 #pragma unroll 1
     for (int u = 0; u < kJagSlots; ++u) {
       const uint64_t j = j0 + u * 32 + lane;
-      fm_to_aos_lane<VC>(C, j, j < jp.m_src, C.dst.base + j * stride, tw, lane, 0u, 0ull);
+      fm_to_aos_lane<VC, W>(C, j, j < jp.m_src, C.dst.base + j * stride, tw, lane, 0u, 0ull);
     }
     return;
   }
@@ -524,18 +391,19 @@ __device__ __forceinline__ unsigned long long jagged_lookback(const JagPlan& jp,
 // predecessor is already running), or whoever hands out the tiles has
 // published every sum beforehand (Published = true: the tile only publishes
 // its inclusive prefix).
-template <int VP, int VC, class Sync = CtaSync, bool Published = false>
+template <int VP, int VC, class Sync = CtaSync, bool Published = false, int W = MRN_WIN_WORDS>
 __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile, unsigned long long* st,
-                                                uint32_t* tw_all, JagShared& sh, const Sync& sync = Sync()) {
+                                                uint32_t* tw_all, JagShared& sh, JagWarp& sw,
+                                                const Sync& sync = Sync()) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  uint32_t* tw = tw_all + warp * MRN_TW_WORDS_PER_WARP;
+  uint32_t* tw = tw_all + warp * MRN_TW_WORDS(W);
   const ConvPlan& P = jp.parent;
   const uint64_t r = tile * MRN_JAG_TILE + tid;
   const bool ok = r < P.n;
 
   uint32_t len = 0;
   uint64_t beg = 0;
-  aos_to_fm_lane<VP>(P, r, ok, ok, P.src.base + r * P.stride, tw, lane, &len, &beg);
+  aos_to_fm_lane<VP, W>(P, r, ok, ok, P.src.base + r * P.stride, tw, lane, &len, &beg);
   if (!ok) len = 0;
   bool bad = false;
   if (ok && (beg > jp.pool_n || (uint64_t)len > jp.pool_n - beg)) {
@@ -550,20 +418,20 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
     const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
-  if (lane == 31) sh.warp[warp] = x;
+  if (lane == 31) sw.warp[warp] = x;
   sync();
   if (warp == 0) {
-    unsigned long long t = lane < 8 ? sh.warp[lane] : 0ull;
+    unsigned long long t = lane < 8 ? sw.warp[lane] : 0ull;
 #pragma unroll
     for (int o = 1; o < 8; o <<= 1) {
       const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
       if (lane >= o) t += y;
     }
-    if (lane < 8) sh.warp[lane] = t;
+    if (lane < 8) sw.warp[lane] = t;
   }
   sync();
-  const unsigned long long excl = x - len + (warp > 0 ? sh.warp[warp - 1] : 0ull);
-  const unsigned long long agg = sh.warp[7];
+  const unsigned long long excl = x - len + (warp > 0 ? sw.warp[warp - 1] : 0ull);
+  const unsigned long long agg = sw.warp[7];
   sh.excl[tid] = excl;
   if (tid == MRN_JAG_TILE - 1) sh.excl[MRN_JAG_TILE] = agg;
   sh.beg[tid] = bad ? ~0ull : beg;
@@ -582,8 +450,8 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
     kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
   }
   if (lane == 0) {
-    sh.kmin[warp] = kmin;
-    sh.kmax[warp] = kmax;
+    sw.kmin[warp] = kmin;
+    sw.kmax[warp] = kmax;
   }
 
   // Decoupled look-back for the number of children of all earlier tiles.
@@ -597,10 +465,10 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
       prefix = jagged_lookback(jp, tile, st, lane);
       if (publish && lane == 0) st_release_u64(&st[tile], MRN_TS_PREFIX | ((prefix + agg) & MRN_TS_VALUE));
     }
-    if (lane == 0) sh.base = prefix;
+    if (lane == 0) sw.base = prefix;
   }
   sync();
-  const unsigned long long base = sh.base;
+  const unsigned long long base = sw.base;
 
   // Offsets: offset_base + children before this parent.
   if (ok) {
@@ -621,8 +489,8 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
   kmax = 0ull;
 #pragma unroll
   for (int w = 0; w < 8; ++w) {
-    kmin = min(kmin, sh.kmin[w]);
-    kmax = max(kmax, sh.kmax[w]);
+    kmin = min(kmin, sw.kmin[w]);
+    kmax = max(kmax, sw.kmax[w]);
   }
   if (kmin == kmax)
     jagged_children<true>(jp, sh, agg, base, kmin, lane, warp);
@@ -634,17 +502,18 @@ template <int VP, int VC>
 __global__ void __launch_bounds__(256) k_jagged_a2s(const __grid_constant__ JagPlan jp) {
   __shared__ uint32_t tw_all[8 * MRN_TW_WORDS_PER_WARP];
   __shared__ JagShared sh;
+  __shared__ JagWarp sw;
   __shared__ unsigned int s_tile;
   if (threadIdx.x == 0) s_tile = atomicAdd(jp.tile_counter, 1u);
   __syncthreads();
-  jagged_a2s_tile<VP, VC>(jp, s_tile, jp.tile_state, tw_all, sh);
+  jagged_a2s_tile<VP, VC>(jp, s_tile, jp.tile_state, tw_all, sh, sw);
 }
 
 // One warp group of a jagged SoA -> AoS conversion: groups [0,
 // parent_groups) build 32 parent records each (length and begin from the
 // offsets), the following groups convert MRN_JAG_CHILD_GROUP of the m_src
 // children each into the pool.
-template <int VP, int VC>
+template <int VP, int VC, int W = MRN_WIN_WORDS>
 __device__ __forceinline__ void jagged_s2a_group(const JagPlan& jp, uint64_t w, uint64_t parent_groups,
                                                  uint32_t* tw, int lane) {
   if (w < parent_groups) {
@@ -657,9 +526,9 @@ __device__ __forceinline__ void jagged_s2a_group(const JagPlan& jp, uint64_t w, 
       b = read_offset(jp.offsets, jp.off_size, r + 1);
       if (b < a || b - a > 0xffffffffull) flag_error(MRN_EINVAL);
     }
-    fm_to_aos_lane<VP>(P, r, ok, P.dst.base + r * P.stride, tw, lane, (uint32_t)(b - a), a);
+    fm_to_aos_lane<VP, W>(P, r, ok, P.dst.base + r * P.stride, tw, lane, (uint32_t)(b - a), a);
   } else {
-    jagged_s2a_children<VC>(jp, (w - parent_groups) * MRN_JAG_CHILD_GROUP, tw, lane);
+    jagged_s2a_children<VC, W>(jp, (w - parent_groups) * MRN_JAG_CHILD_GROUP, tw, lane);
   }
 }
 
@@ -720,7 +589,7 @@ __global__ void k_write_offset0(char* offs, uint32_t osz, unsigned long long v) 
 // before the stage's loads.  Every wait is bounded; on expiry the warp that
 // saw it records MRN_ETIMEOUT and stops, and the others follow.
 constexpr uint32_t kBStage = MRN_BATCH_STAGE_BYTES;
-constexpr uint32_t kBNS = 2;      // source stages
+constexpr uint32_t kBNS = 3;      // source stages
 constexpr uint32_t kBND = 2;      // destination buffers
 constexpr uint32_t kRing = 8;     // decided tiles in flight
 constexpr uint32_t kSQ = 8;       // staged tiles between loader and storer
@@ -747,8 +616,12 @@ struct StoreItem {
   unsigned int pad;
 };
 
-constexpr size_t kBScratch = 21504;  // 8 warps' lane words + JagShared
-static_assert(kBScratch >= 8 * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t) + sizeof(JagShared), "scratch");
+// Consumer scratch: 8 warps' lane words in 32-byte windows (a jagged tile's
+// JagShared lies over them), then a jagged tile's JagWarp.
+constexpr uint32_t kBWin = 8;
+constexpr size_t kBTw = 8 * MRN_TW_WORDS(kBWin) * sizeof(uint32_t);
+static_assert(sizeof(JagShared) <= kBTw, "jagged tile arrays fit the lane-word scratch");
+constexpr size_t kBScratch = (kBTw + sizeof(JagWarp) + 15) / 16 * 16;
 constexpr size_t kBOffDst = (size_t)kBNS * kBStage;
 constexpr size_t kBOffScratch = kBOffDst + (size_t)kBND * kBStage;
 constexpr size_t kBOffDesc = kBOffScratch + kBScratch;
@@ -886,6 +759,7 @@ __device__ __forceinline__ void publish_jagged_sums(const BatchJob* __restrict__
 // Loader warp: decides tiles in order (lane 0 decides, the warp follows)
 // and issues the loads of staged ones; returns after publishing the
 // end-of-work slot, or on abort once its loads in flight have landed.
+template <bool kStatic>
 __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
                                              const unsigned long long* __restrict__ first_tile,
                                              unsigned int njobs, unsigned long long total_tiles,
@@ -896,6 +770,7 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
   unsigned int cursor = 0;
   uint64_t next_t = 0, chunk_end = 0;
   unsigned int pcursor = 0;
+  uint32_t n_chunks = 0;  // static assignment: chunks taken so far
   bool have = false;
   TileSlot cand;
   cand.t = 0;
@@ -904,11 +779,17 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
     if (m.flags()[0]) break;
     if (!have) {
       if (next_t == chunk_end) {
-        unsigned int cidx = 0;
-        if (lane == 0) cidx = atomicAdd(counter, 1u);
-        next_t = (uint64_t)__shfl_sync(0xffffffffu, cidx, 0) * kChunk;
+        if constexpr (kStatic) {
+          next_t = ((uint64_t)n_chunks * gridDim.x + blockIdx.x) * kChunk;
+          ++n_chunks;
+        } else {
+          unsigned int cidx = 0;
+          if (lane == 0) cidx = atomicAdd(counter, 1u);
+          next_t = (uint64_t)__shfl_sync(0xffffffffu, cidx, 0) * kChunk;
+          publish_jagged_sums(jobs, first_tile, njobs, total_tiles, states, next_t, next_t + kChunk, &pcursor,
+                              lane);
+        }
         chunk_end = next_t + kChunk;
-        publish_jagged_sums(jobs, first_tile, njobs, total_tiles, states, next_t, chunk_end, &pcursor, lane);
       }
       cand.t = next_t++;
       cand.staged = 0;
@@ -1028,11 +909,11 @@ __device__ __forceinline__ void batch_storer(const BatchJob* __restrict__ jobs, 
   bulk_wait_all();
 }
 
-__global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restrict__ jobs,
-                                                        const unsigned long long* __restrict__ first_tile,
-                                                        unsigned int njobs, unsigned long long total_tiles,
-                                                        unsigned int* counter, unsigned long long* states) {
-  extern __shared__ __align__(128) char batch_smem[];
+template <bool kStatic>
+__device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
+                                           const unsigned long long* __restrict__ first_tile, unsigned int njobs,
+                                           unsigned long long total_tiles, unsigned int* counter,
+                                           unsigned long long* states, char* batch_smem) {
   BatchSmem m{batch_smem};
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
@@ -1058,7 +939,7 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
   }
   __syncthreads();
   if (warp == 8) {
-    batch_loader(jobs, first_tile, njobs, total_tiles, counter, states, m, lane);
+    batch_loader<kStatic>(jobs, first_tile, njobs, total_tiles, counter, states, m, lane);
     return;
   }
   if (warp == 9) {
@@ -1067,8 +948,9 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
   }
   // consumers
   uint32_t* scratch = m.scratch();
-  uint32_t* tw = scratch + warp * MRN_TW_WORDS_PER_WARP;
-  JagShared& sh = *reinterpret_cast<JagShared*>(scratch + 8 * MRN_TW_WORDS_PER_WARP);
+  uint32_t* tw = scratch + warp * MRN_TW_WORDS(kBWin);
+  JagShared& sh = *reinterpret_cast<JagShared*>(scratch);
+  JagWarp& sw = *reinterpret_cast<JagWarp*>(reinterpret_cast<char*>(scratch) + kBTw);
   uint32_t cphase = 0;
   bool ok = true;
   const ConsumerSync sync{m.cbar(), &cphase, &ok};
@@ -1102,12 +984,16 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
       const unsigned long long local = ts.local;
       if (J.kind == JOB_CONVERT) {
         const uint32_t tr = J.tile_records;
-        conv_range<0>(J.jp.parent, local * tr, (local + 1) * tr, tw, lane, warp, 8);
+        conv_range<0, kBWin>(J.jp.parent, local * tr, (local + 1) * tr, tw, lane, warp, 8);
       } else if (J.kind == JOB_JAG_A2S) {
-        jagged_a2s_tile<0, 0, ConsumerSync, true>(J.jp, local, states + J.tile_begin, scratch, sh, sync);
+        jagged_a2s_tile<0, 0, ConsumerSync, true, kBWin>(J.jp, local, states + J.tile_begin, scratch, sh, sw,
+                                                         sync);
+        // the tile's arrays lie over the lane words: every warp is done
+        // reading them before any warp's next tile writes its lane words
+        sync();
         if (!ok) break;
       } else if (J.kind == JOB_JAG_S2A) {
-        jagged_s2a_group<0, 0>(J.jp, local * 8 + warp, J.parent_groups, tw, lane);
+        jagged_s2a_group<0, 0, kBWin>(J.jp, local * 8 + warp, J.parent_groups, tw, lane);
       } else {
         const uint64_t q = local * 256 + tid;
         if (q < J.gp.nblocks * J.gp.ngaps) zero_gap_item(J.gp, q);
@@ -1118,6 +1004,23 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
     if (lane == 0) flag_error(MRN_ETIMEOUT);
     m.flags()[0] = 1;
   }
+}
+
+// Batched conversions: tiles handed out dynamically in increasing order.
+__global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restrict__ jobs,
+                                                        const unsigned long long* __restrict__ first_tile,
+                                                        unsigned int njobs, unsigned long long total_tiles,
+                                                        unsigned int* counter, unsigned long long* states) {
+  extern __shared__ __align__(128) char batch_smem[];
+  batch_main<false>(jobs, first_tile, njobs, total_tiles, counter, states, batch_smem);
+}
+
+// One staged conversion through the same warp-specialized pipeline: the
+// job travels as a kernel parameter and chunk c of tiles belongs to CTA
+// c % gridDim.x (no scratch, no counter; the job has no jagged tiles).
+__global__ void __launch_bounds__(kBThreads, 3) k_convert_ws(const __grid_constant__ BatchJob job) {
+  extern __shared__ __align__(128) char batch_smem[];
+  batch_main<true>(&job, nullptr, 1u, job.ntiles, nullptr, nullptr, batch_smem);
 }
 
 // ================================================================== host
@@ -1194,15 +1097,18 @@ int read_and_clear_status(void* stream, uint32_t* bits) {
   return MRN_OK;
 }
 
-// Opts a kernel into the staged kernels' dynamic shared memory (once).
-void allow_tma_smem(const void* fn) {
+// Opts a kernel into the batch pipeline's dynamic shared memory, once per
+// kernel and device.
+void allow_batch_smem(const void* fn) {
   static std::mutex mu;
-  static std::vector<const void*> done;
+  static std::vector<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(mu);
-  for (const void* f : done)
-    if (f == fn) return;
-  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
-  done.push_back(fn);
+  for (const auto& f : done)
+    if (f.first == fn && f.second == dev) return;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem);
+  done.emplace_back(fn, dev);
 }
 
 int launch_convert(const ConvPlan& p, void* stream, const LaunchShape* shape) {
@@ -1210,15 +1116,22 @@ int launch_convert(const ConvPlan& p, void* stream, const LaunchShape* shape) {
   if (nrec == 0) return MRN_OK;
   LaunchShape sh = shape ? *shape : LaunchShape{};
   if (p.tg.tma && !sh.generic) {
-    const void* fn = reinterpret_cast<const void*>(&k_convert_tma);
-    allow_tma_smem(fn);
-    const int occ = occupancy(fn, 256, kTmaSmem);
+    // the warp-specialized pipeline of the batch kernel, one job
+    BatchJob job;
+    std::memset(&job, 0, sizeof(job));
+    job.kind = JOB_CONVERT;
+    job.jp.parent = p;
+    job.tile_records = p.tg.T;
+    job.ntiles = (nrec + p.tg.T - 1) / p.tg.T;
+    const void* fn = reinterpret_cast<const void*>(&k_convert_ws);
+    allow_batch_smem(fn);
+    const int occ = occupancy(fn, kBThreads, kBatchSmem);
     const int per_sm = sh.ctas_per_sm ? std::min((int)sh.ctas_per_sm, occ) : occ;
-    const uint64_t ntiles = (nrec + p.tg.T - 1) / p.tg.T;
+    const uint64_t chunks = (job.ntiles + kChunk - 1) / kChunk;
     const unsigned grid = (unsigned)std::max<uint64_t>(
-        1, std::min<uint64_t>(ntiles, (uint64_t)device_sm_count() * (uint64_t)per_sm));
-    void* args[] = {const_cast<ConvPlan*>(&p)};
-    return cuda_status(cudaLaunchKernel(fn, dim3(grid), dim3(256), args, kTmaSmem,
+        1, std::min<uint64_t>(chunks, (uint64_t)device_sm_count() * (uint64_t)per_sm));
+    void* args[] = {&job};
+    return cuda_status(cudaLaunchKernel(fn, dim3(grid), dim3(kBThreads), args, kBatchSmem,
                                         static_cast<cudaStream_t>(stream)));
   }
   if (sh.threads != 64 && sh.threads != 128 && sh.threads != 256) sh.threads = 256;
@@ -1342,10 +1255,7 @@ int launch_jagged_count(const ConvPlan& parent, uint64_t* dev_total, void* strea
 
 int batch_occupancy() {
   const void* fn = reinterpret_cast<const void*>(&k_batch);
-  static std::once_flag once;
-  std::call_once(once, [fn] {
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem);
-  });
+  allow_batch_smem(fn);
   return occupancy(fn, kBThreads, kBatchSmem);
 }
 

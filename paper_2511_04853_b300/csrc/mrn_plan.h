@@ -37,8 +37,7 @@ struct ColPlan {
 // copies: tiles of T records; a side's tile is one contiguous range (AoS:
 // T*stride bytes; AoSoA: T/B whole blocks) or, for SoA, one range per column
 // packed in column order (column c at off[c] inside the tile).
-#define MRN_STAGE_BYTES 12288u        // stage of single conversions
-#define MRN_BATCH_STAGE_BYTES 12288u  // stage of the warp-specialized batch kernel
+#define MRN_BATCH_STAGE_BYTES 12288u  // stage of the warp-specialized pipeline
 struct TileGeom {
   uint32_t tma;        // 1: full tiles go through the TMA pipeline
   uint32_t T;          // records per tile (multiple of 32 and of each AoSoA B)
