@@ -651,15 +651,7 @@ def secondary(mrn, torch, stream, peak):
     # jagged tracks, AoS -> SoA and back (canonical child pool)
     s = mrn.Schema(datagen.TRACKS)
     for n in (100000, 1 << 22):
-        d = datagen.workload("tracks", n, 2)
-        m = d["m"]
-        recs = torch.zeros(n * 24, dtype=torch.uint8, device="cuda")
-        lens = torch.from_numpy(d["lengths"].astype(np.int32)).cuda()
-        begs = torch.cumsum(lens.to(torch.int64), 0) - lens.to(torch.int64)
-        rv = recs.view(n, 24)
-        rv[:, 12:16].copy_(lens.view(torch.uint8).view(n, 4))
-        rv[:, 16:24].copy_(begs.view(torch.uint8).view(n, 8))
-        pool = torch.full((max(1, m * 8),), 7, dtype=torch.uint8, device="cuda")
+        m, recs, pool = jagged_aos(torch, s, n)
         soa = torch.empty(s.required_bytes("soa", n, m), dtype=torch.uint8, device="cuda")
         src = mrn.View(s, "aos", n, base=recs, child_pool=pool, m=m)
         dst = mrn.View(s, "soa", n, base=soa, m=m)
@@ -813,7 +805,8 @@ def run_served(mrn, torch, args):
 
 def run_case(args):
     """Repeats one conversion (for profilers): schema:src:dst:records, a
-    layout written as aosoa/32 for blocks."""
+    layout written as aosoa/32 for blocks.  For the jagged tracks schema the
+    AoS side is a canonical pool (Poisson(20) children clipped at 256)."""
     import torch
     import paper_2511_04853_b300 as mrn
     import datagen
@@ -825,9 +818,20 @@ def run_case(args):
         return k, int(b or 0)
     (sk, sb), (dk, db) = lay(sk), lay(dk)
     s = mrn.Schema(datagen.WORKLOAD_SCHEMAS[name])
-    a = torch.full((s.required_bytes(sk, n, 0, sb),), 0x3C, dtype=torch.uint8, device="cuda")
-    b = torch.empty(s.required_bytes(dk, n, 0, db), dtype=torch.uint8, device="cuda")
-    src, dst = mrn.View(s, sk, n, block=sb, base=a), mrn.View(s, dk, n, block=db, base=b)
+    if s.has_jagged:
+        m, aos, pool = jagged_aos(torch, s, n)
+        soa = torch.empty(s.required_bytes("soa", n, m), dtype=torch.uint8, device="cuda")
+        a_view = mrn.View(s, "aos", n, base=aos, child_pool=pool, m=m)
+        s_view = mrn.View(s, "soa", n, base=soa, m=m)
+        src, dst = (a_view, s_view) if sk == "aos" else (s_view, a_view)
+        if sk != "aos":
+            mrn.convert(a_view, s_view)
+        nbytes = n * 24 + m * 8 + n * 12 + (n + 1) * 4 + m * 8
+    else:
+        a = torch.full((s.required_bytes(sk, n, 0, sb),), 0x3C, dtype=torch.uint8, device="cuda")
+        b = torch.empty(s.required_bytes(dk, n, 0, db), dtype=torch.uint8, device="cuda")
+        src, dst = mrn.View(s, sk, n, block=sb, base=a), mrn.View(s, dk, n, block=db, base=b)
+        nbytes = 2 * n * s.stride
     for _ in range(args.warmup):
         mrn.convert(src, dst)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -839,7 +843,25 @@ def run_case(args):
     assert mrn.sync() == mrn.OK
     ms = e0.elapsed_time(e1) / args.steps
     print(json.dumps({"case": args.case, "ms": round(ms, 5),
-                      "gbps": round(2 * n * s.stride / (ms * 1e-3) / 1e9, 1)}), flush=True)
+                      "gbps": round(nbytes / (ms * 1e-3) / 1e9, 1)}), flush=True)
+
+
+def jagged_aos(torch, s, n, seed=2):
+    """Jagged AoS parents (tracks record: length at 12, begin at 16) with a
+    canonical child pool, lengths min(Poisson(20), 256) from the seeded
+    generator; returns (children, records, pool)."""
+    import numpy as np
+    import datagen
+    d = datagen.workload("tracks", n, seed)
+    m = d["m"]
+    recs = torch.zeros(max(1, n * 24), dtype=torch.uint8, device="cuda")
+    lens = torch.from_numpy(d["lengths"].astype(np.int32)).cuda()
+    begs = torch.cumsum(lens.to(torch.int64), 0) - lens.to(torch.int64)
+    rv = recs[: n * 24].view(n, 24)
+    rv[:, 12:16].copy_(lens.view(torch.uint8).view(n, 4))
+    rv[:, 16:24].copy_(begs.view(torch.uint8).view(n, 8))
+    pool = torch.full((max(1, m * 8),), 7, dtype=torch.uint8, device="cuda")
+    return m, recs, pool
 
 
 def main():

@@ -295,12 +295,22 @@ void tile_geometry(const mrn_schema* s, ConvPlan* p, uint32_t stage_bytes) {
   g.T = T;
   g.src_bytes = (uint32_t)tile_bytes(s, p->src, T, g.src_off);
   g.dst_bytes = (uint32_t)tile_bytes(s, p->dst, T, g.dst_off);
-  uint32_t used = 0;
+  uint32_t used = 0, k = 0;
   for (uint32_t c = 0; c < s->cols.size(); ++c) {
     const uint32_t sz = s->cols[c].size;
     const uint32_t lsz = sz == 1 ? 0 : sz == 2 ? 1 : sz == 4 ? 2 : 3;
     g.col[c] = s->cols[c].aos_off | (lsz << 24);
     used += sz;
+  }
+  // the transform walks the columns one size class at a time
+  for (uint32_t lsz = 4; lsz-- > 0;) {
+    uint32_t cnt = 0;
+    for (uint32_t c = 0; c < s->cols.size(); ++c)
+      if ((g.col[c] >> 24) == lsz) {
+        g.order[k++] = (uint8_t)c;
+        ++cnt;
+      }
+    g.nsize |= cnt << (8 * (3 - lsz));
   }
   g.pad = used != s->stride;
   g.tma = 1;

@@ -420,7 +420,7 @@ __device__ __forceinline__ void sts128_zero(uint32_t a) {
 // record its own row, slot 0); SoA: shift 31 (one row, slot r); AoSoA(B):
 // block B, bb = block bytes.
 struct TileHdr {
-  uint32_t ncols, stride, vec, pad, T;
+  uint32_t ncols, stride, vec, pad, T, nsize;
   uint32_t sblock, sshift, sbb;  // source row geometry
   uint32_t dblock, dshift, dbb;  // destination row geometry
 };
@@ -446,24 +446,6 @@ __device__ __forceinline__ void tile_row(uint32_t block, uint32_t shift, uint32_
   *base = tile + blk * bb;
 }
 
-__device__ __forceinline__ uint2 lds_sz(uint32_t a, uint32_t lsz) {
-  if (lsz == 3) return lds64(a);
-  if (lsz == 2) return make_uint2(lds32(a), 0u);
-  if (lsz == 1) return make_uint2(lds16(a), 0u);
-  return make_uint2(lds8(a), 0u);
-}
-
-__device__ __forceinline__ void sts_sz(uint32_t a, uint2 v, uint32_t lsz) {
-  if (lsz == 3)
-    sts64(a, v);
-  else if (lsz == 2)
-    sts32(a, v.x);
-  else if (lsz == 1)
-    sts16(a, v.x);
-  else
-    sts8(a, v.x);
-}
-
 // Zeroes an AoS destination record whose padding bytes no column writes
 // (h.pad is set only for such destinations).
 __device__ __forceinline__ void zero_record(const TileHdr& h, uint32_t db) {
@@ -483,15 +465,67 @@ __device__ __forceinline__ void zero_record(const TileHdr& h, uint32_t db) {
   }
 }
 
+// Shared loads and stores of 2^L bytes.
+template <int L>
+__device__ __forceinline__ uint2 lds_l(uint32_t a) {
+  if constexpr (L == 3) return lds64(a);
+  if constexpr (L == 2) return make_uint2(lds32(a), 0u);
+  if constexpr (L == 1) return make_uint2(lds16(a), 0u);
+  return make_uint2(lds8(a), 0u);
+}
+
+template <int L>
+__device__ __forceinline__ void sts_l(uint32_t a, uint2 v) {
+  if constexpr (L == 3) sts64(a, v);
+  if constexpr (L == 2) sts32(a, v.x);
+  if constexpr (L == 1) sts16(a, v.x);
+  if constexpr (L == 0) sts8(a, v.x);
+}
+
+// The columns [c0, c1) of the descriptor table, all of 2^L bytes, for the
+// lane's records: row + column offset + (slot << L) on both sides, the
+// loads of two columns of both records before their stores.
+template <int L>
+__device__ __forceinline__ void tile_class(uint32_t desc, uint32_t c0, uint32_t c1, uint32_t sb0, uint32_t si0,
+                                           uint32_t sb1, uint32_t si1, uint32_t db0, uint32_t di0, uint32_t db1,
+                                           uint32_t di1, bool two) {
+  const uint32_t so0 = si0 << L, so1 = si1 << L, do0 = di0 << L, do1 = di1 << L;
+  uint32_t c = c0;
+  for (; c + 1 < c1; c += 2) {
+    const uint4 d0 = lds128(desc + c * 16), d1 = lds128(desc + c * 16 + 16);
+    const uint2 v00 = lds_l<L>(sb0 + d0.y + so0), v10 = lds_l<L>(sb0 + d1.y + so0);
+    uint2 v01 = v00, v11 = v10;
+    if (two) {
+      v01 = lds_l<L>(sb1 + d0.y + so1);
+      v11 = lds_l<L>(sb1 + d1.y + so1);
+    }
+    sts_l<L>(db0 + d0.z + do0, v00);
+    sts_l<L>(db0 + d1.z + do0, v10);
+    if (two) {
+      sts_l<L>(db1 + d0.z + do1, v01);
+      sts_l<L>(db1 + d1.z + do1, v11);
+    }
+  }
+  if (c < c1) {
+    const uint4 d0 = lds128(desc + c * 16);
+    const uint2 v00 = lds_l<L>(sb0 + d0.y + so0);
+    uint2 v01 = v00;
+    if (two) v01 = lds_l<L>(sb1 + d0.y + so1);
+    sts_l<L>(db0 + d0.z + do0, v00);
+    if (two) sts_l<L>(db1 + d0.z + do1, v01);
+  }
+}
+
 // Staged tile transform: each lane converts records r0 and r1 (= r0 + 256,
 // when `two`) of the tile.  Per column one shared load and one shared store
 // per record, addressed from the column descriptor table `desc` (uint4
 // {log2(size), source column offset, destination column offset, 0} per
-// column, in shared memory; a column offset on an AoS side is the field's
-// offset in the record) as row + column offset + (slot << log2(size)); the
-// loads of two columns of both records are issued before their stores.  One
-// body serves every pair of layouts, so tiles of different layout pairs
-// running side by side share their instructions.
+// column, in shared memory, ordered by decreasing size with h.nsize giving
+// the size classes; a column offset on an AoS side is the field's offset in
+// the record) as row + column offset + (slot << log2(size)).  One body
+// serves every pair of layouts, so tiles of different layout pairs running
+// side by side share their instructions; each size class is a loop of its
+// own, so no element access branches on its size.
 __device__ __forceinline__ void tile_convert(const TileHdr& h, uint32_t desc, uint32_t st, uint32_t dt,
                                              uint32_t r0, bool two) {
   const uint32_t r1 = two ? r0 + 256 : r0;
@@ -502,37 +536,9 @@ __device__ __forceinline__ void tile_convert(const TileHdr& h, uint32_t desc, ui
   tile_row(h.dblock, h.dshift, h.dbb, dt, r1, &db1, &di1);
   zero_record(h, db0);
   if (two) zero_record(h, db1);
-  const uint32_t nc = h.ncols;
-  uint32_t c = 0;
-  for (; c + 1 < nc; c += 2) {
-    const uint4 d0 = lds128(desc + c * 16), d1 = lds128(desc + c * 16 + 16);
-    const uint32_t l0 = d0.x, l1 = d1.x;
-    const uint32_t a00 = sb0 + d0.y + (si0 << l0), a01 = sb1 + d0.y + (si1 << l0);
-    const uint32_t a10 = sb0 + d1.y + (si0 << l1), a11 = sb1 + d1.y + (si1 << l1);
-    const uint32_t b00 = db0 + d0.z + (di0 << l0), b01 = db1 + d0.z + (di1 << l0);
-    const uint32_t b10 = db0 + d1.z + (di0 << l1), b11 = db1 + d1.z + (di1 << l1);
-    const uint2 v00 = lds_sz(a00, l0), v10 = lds_sz(a10, l1);
-    uint2 v01 = v00, v11 = v10;
-    if (two) {
-      v01 = lds_sz(a01, l0);
-      v11 = lds_sz(a11, l1);
-    }
-    sts_sz(b00, v00, l0);
-    sts_sz(b10, v10, l1);
-    if (two) {
-      sts_sz(b01, v01, l0);
-      sts_sz(b11, v11, l1);
-    }
-  }
-  if (c < nc) {
-    const uint4 d0 = lds128(desc + c * 16);
-    const uint32_t l0 = d0.x;
-    const uint32_t a00 = sb0 + d0.y + (si0 << l0), a01 = sb1 + d0.y + (si1 << l0);
-    const uint32_t b00 = db0 + d0.z + (di0 << l0), b01 = db1 + d0.z + (di1 << l0);
-    const uint2 v00 = lds_sz(a00, l0);
-    uint2 v01 = v00;
-    if (two) v01 = lds_sz(a01, l0);
-    sts_sz(b00, v00, l0);
-    if (two) sts_sz(b01, v01, l0);
-  }
+  const uint32_t e8 = h.nsize & 0xff, e4 = e8 + ((h.nsize >> 8) & 0xff), e2 = e4 + ((h.nsize >> 16) & 0xff);
+  tile_class<3>(desc, 0, e8, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
+  tile_class<2>(desc, e8, e4, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
+  tile_class<1>(desc, e4, e2, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
+  tile_class<0>(desc, e2, h.ncols, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
 }

@@ -64,8 +64,10 @@ __device__ __forceinline__ void tma_transform(const TileHdr& h, uint32_t desc, c
     tile_convert(hh, desc, s, d, g + lane, g + 8 * 32 < hh.T);
 }
 
-// Column c's staged-transform descriptor (see tile_convert).
-__device__ __forceinline__ uint4 tile_desc(const ConvPlan& p, uint32_t c) {
+// Entry k of the staged-transform descriptor table: the k-th column in
+// size-class order (see tile_convert).
+__device__ __forceinline__ uint4 tile_desc(const ConvPlan& p, uint32_t k) {
+  const uint32_t c = p.tg.order[k];
   const uint32_t col = p.tg.col[c], aos_off = col & 0xffffffu;
   return make_uint4(col >> 24, p.src.kind == K_AOS ? aos_off : p.tg.src_off[c],
                     p.dst.kind == K_AOS ? aos_off : p.tg.dst_off[c], 0u);
@@ -78,6 +80,7 @@ __device__ __forceinline__ TileHdr tile_hdr(const ConvPlan& p) {
   h.vec = p.vec;
   h.pad = p.dst.kind == K_AOS ? p.tg.pad : 0u;
   h.T = p.tg.T;
+  h.nsize = p.tg.nsize;
   tile_side_geometry(p.src.kind, p.src.block, p.src.block_shift, p.src.block_bytes, p.stride, &h.sblock, &h.sshift,
                      &h.sbb);
   tile_side_geometry(p.dst.kind, p.dst.block, p.dst.block_shift, p.dst.block_bytes, p.stride, &h.dblock, &h.dshift,

@@ -44,10 +44,11 @@ struct TileGeom {
   uint32_t src_bytes;  // bytes of a source tile
   uint32_t dst_bytes;  // bytes of a destination tile
   uint32_t pad;        // 1: the AoS record has padding bytes (zeroed first)
-  uint32_t reserved;
+  uint32_t nsize;      // columns of 8, 4, 2 and 1 bytes: n8 | n4 << 8 | n2 << 16 | n1 << 24
   uint32_t src_off[MRN_MAX_COLS];  // SoA: column offset in the tile; AoSoA: column start in a block
   uint32_t dst_off[MRN_MAX_COLS];
   uint32_t col[MRN_MAX_COLS];      // per data column: AoS offset | log2(size) << 24
+  uint8_t order[MRN_MAX_COLS];     // data columns by decreasing size (stable)
 };
 
 struct ConvPlan {
