@@ -570,7 +570,7 @@ __global__ void k_write_offset0(char* offs, uint32_t osz, unsigned long long v) 
 //
 // Every job of a batch in one persistent, warp-specialized launch of 320
 // threads per CTA.
-//  - Warp 8 (loader) takes chunks of kChunk consecutive global tiles from an
+//  - Warp 8 (loader) takes chunks of `chunk` consecutive global tiles from an
 //    atomic counter (chunks are handed out in increasing order), publishes
 //    the child counts of the chunk's jagged tiles at once (so a jagged
 //    tile's look-back waits only for chunks taken earlier), decides each
@@ -596,7 +596,7 @@ constexpr uint32_t kBNS = 3;      // source stages
 constexpr uint32_t kBND = 2;      // destination buffers
 constexpr uint32_t kRing = 8;     // decided tiles in flight
 constexpr uint32_t kSQ = 8;       // staged tiles between loader and storer
-constexpr uint64_t kChunk = 2;    // consecutive tiles per counter grab
+constexpr uint64_t kChunk = 8;    // most consecutive tiles per chunk
 constexpr uint32_t kBThreads = 320;
 
 struct TileSlot {
@@ -767,7 +767,7 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
                                              const unsigned long long* __restrict__ first_tile,
                                              unsigned int njobs, unsigned long long total_tiles,
                                              unsigned int* counter, unsigned long long* states,
-                                             const BatchSmem& m, int lane) {
+                                             uint32_t chunk, const BatchSmem& m, int lane) {
   uint64_t k_issue = 0;  // tiles decided
   uint32_t c_issue = 0;  // staged tiles loaded
   unsigned int cursor = 0;
@@ -783,16 +783,16 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
     if (!have) {
       if (next_t == chunk_end) {
         if constexpr (kStatic) {
-          next_t = ((uint64_t)n_chunks * gridDim.x + blockIdx.x) * kChunk;
+          next_t = ((uint64_t)n_chunks * gridDim.x + blockIdx.x) * chunk;
           ++n_chunks;
         } else {
           unsigned int cidx = 0;
           if (lane == 0) cidx = atomicAdd(counter, 1u);
-          next_t = (uint64_t)__shfl_sync(0xffffffffu, cidx, 0) * kChunk;
-          publish_jagged_sums(jobs, first_tile, njobs, total_tiles, states, next_t, next_t + kChunk, &pcursor,
+          next_t = (uint64_t)__shfl_sync(0xffffffffu, cidx, 0) * chunk;
+          publish_jagged_sums(jobs, first_tile, njobs, total_tiles, states, next_t, next_t + chunk, &pcursor,
                               lane);
         }
-        chunk_end = next_t + kChunk;
+        chunk_end = next_t + chunk;
       }
       cand.t = next_t++;
       cand.staged = 0;
@@ -916,7 +916,7 @@ template <bool kStatic>
 __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
                                            const unsigned long long* __restrict__ first_tile, unsigned int njobs,
                                            unsigned long long total_tiles, unsigned int* counter,
-                                           unsigned long long* states, char* batch_smem) {
+                                           unsigned long long* states, uint32_t chunk, char* batch_smem) {
   BatchSmem m{batch_smem};
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
@@ -942,7 +942,7 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
   }
   __syncthreads();
   if (warp == 8) {
-    batch_loader<kStatic>(jobs, first_tile, njobs, total_tiles, counter, states, m, lane);
+    batch_loader<kStatic>(jobs, first_tile, njobs, total_tiles, counter, states, chunk, m, lane);
     return;
   }
   if (warp == 9) {
@@ -1013,17 +1013,19 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
 __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restrict__ jobs,
                                                         const unsigned long long* __restrict__ first_tile,
                                                         unsigned int njobs, unsigned long long total_tiles,
-                                                        unsigned int* counter, unsigned long long* states) {
+                                                        unsigned int* counter, unsigned long long* states,
+                                                        uint32_t chunk) {
   extern __shared__ __align__(128) char batch_smem[];
-  batch_main<false>(jobs, first_tile, njobs, total_tiles, counter, states, batch_smem);
+  batch_main<false>(jobs, first_tile, njobs, total_tiles, counter, states, chunk, batch_smem);
 }
 
 // One staged conversion through the same warp-specialized pipeline: the
 // job travels as a kernel parameter and chunk c of tiles belongs to CTA
 // c % gridDim.x (no scratch, no counter; the job has no jagged tiles).
-__global__ void __launch_bounds__(kBThreads, 3) k_convert_ws(const __grid_constant__ BatchJob job) {
+__global__ void __launch_bounds__(kBThreads, 3) k_convert_ws(const __grid_constant__ BatchJob job,
+                                                             uint32_t chunk) {
   extern __shared__ __align__(128) char batch_smem[];
-  batch_main<true>(&job, nullptr, 1u, job.ntiles, nullptr, nullptr, batch_smem);
+  batch_main<true>(&job, nullptr, 1u, job.ntiles, nullptr, nullptr, chunk, batch_smem);
 }
 
 // ================================================================== host
@@ -1114,6 +1116,12 @@ void allow_batch_smem(const void* fn) {
   done.emplace_back(fn, dev);
 }
 
+// Tiles per chunk: up to kChunk (fewer job switches per CTA), but small
+// enough that every CTA of the grid gets about four chunks.
+uint32_t chunk_for(uint64_t tiles, uint64_t ctas) {
+  return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(kChunk, tiles / (4 * std::max<uint64_t>(1, ctas))));
+}
+
 int launch_convert(const ConvPlan& p, void* stream, const LaunchShape* shape) {
   const uint64_t nrec = p.dir == DIR_FM_AOS ? p.n : p.n_fm_pad;
   if (nrec == 0) return MRN_OK;
@@ -1130,10 +1138,11 @@ int launch_convert(const ConvPlan& p, void* stream, const LaunchShape* shape) {
     allow_batch_smem(fn);
     const int occ = occupancy(fn, kBThreads, kBatchSmem);
     const int per_sm = sh.ctas_per_sm ? std::min((int)sh.ctas_per_sm, occ) : occ;
-    const uint64_t chunks = (job.ntiles + kChunk - 1) / kChunk;
-    const unsigned grid = (unsigned)std::max<uint64_t>(
-        1, std::min<uint64_t>(chunks, (uint64_t)device_sm_count() * (uint64_t)per_sm));
-    void* args[] = {&job};
+    const uint64_t cap = (uint64_t)device_sm_count() * (uint64_t)per_sm;
+    uint32_t chunk = chunk_for(job.ntiles, cap);
+    const uint64_t chunks = (job.ntiles + chunk - 1) / chunk;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(chunks, cap));
+    void* args[] = {&job, &chunk};
     return cuda_status(cudaLaunchKernel(fn, dim3(grid), dim3(kBThreads), args, kBatchSmem,
                                         static_cast<cudaStream_t>(stream)));
   }
@@ -1269,10 +1278,11 @@ int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, uns
   const int occ = batch_occupancy();
   const int per_sm = ctas_per_sm ? std::min((int)ctas_per_sm, occ) : occ;
   const uint64_t cap = (uint64_t)device_sm_count() * (uint64_t)per_sm;
-  const uint64_t chunks = (total_tiles + kChunk - 1) / kChunk;
+  const uint32_t chunk = chunk_for(total_tiles, cap);
+  const uint64_t chunks = (total_tiles + chunk - 1) / chunk;
   const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(cap, chunks));
   k_batch<<<grid, kBThreads, kBatchSmem, static_cast<cudaStream_t>(stream)>>>(jobs, first_tile, njobs,
-                                                                                total_tiles, counter, states);
+                                                                                total_tiles, counter, states, chunk);
   return cuda_status(cudaGetLastError());
 }
 
