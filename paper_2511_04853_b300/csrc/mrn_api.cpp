@@ -330,6 +330,13 @@ int build_plan(const mrn_view& src, const mrn_view& dst, ConvPlan* p) {
   return rc;
 }
 
+int jagged_children_plan(const mrn_schema* s, const JagPlan& jp, ConvPlan* out) {
+  *out = jp.child;
+  out->n = out->n_fm_pad = jp.m_src;
+  tile_geometry(s->child.get(), out, MRN_BATCH_STAGE_BYTES);
+  return MRN_OK;
+}
+
 int build_jagged_plan(const mrn_view& src, const mrn_view& dst, JagPlan* jp) {
   const mrn_schema* s = src.schema;
   std::memset(jp, 0, sizeof(*jp));
@@ -409,7 +416,14 @@ int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
       if (scratch) cudaFreeAsync(scratch, st);
       if (rc) return rc;
     } else {
+      // The children are stored contiguously on both sides (Sec. V, jagged
+      // vector property): child row j -> pool record j is a plain SoA -> AoS
+      // conversion of the child schema; the kernel builds only the parents.
+      ConvPlan kids;
+      if ((rc = jagged_children_plan(s, jp, &kids))) return rc;
+      jp.m_src = 0;
       if ((rc = launch_jagged_s2a(jp, stream))) return rc;
+      if ((rc = launch_convert(kids, stream, nullptr))) return rc;
     }
     GapPlan g;
     gap_plan(s, *dst, &g);

@@ -56,6 +56,26 @@ void own_view(const mrn_view& v, std::vector<void*>* c0, std::vector<void*>* c1,
   }
 }
 
+// Tiles of a conversion job: the staged tiles of its plan, or (plans that
+// cannot be staged, or for which the autotuner chose the direct path)
+// direct tiles of the tuned size.
+void convert_tiles(BatchJob* j) {
+  j->kind = JOB_CONVERT;
+  const LaunchShape sh = tuned_shape(j->jp.parent);
+  uint32_t tr;
+  if (j->jp.parent.tg.tma && !sh.generic) {
+    tr = j->jp.parent.tg.T;  // batch tiles coincide with staged tiles
+  } else {
+    j->jp.parent.tg.tma = 0;
+    tr = sh.tile_records ? sh.tile_records : 1024;
+    tr = std::max<uint32_t>(256, tr / 256 * 256);
+  }
+  j->tile_records = tr;
+  const ConvPlan& p = j->jp.parent;
+  const uint64_t nrec = p.dir == DIR_FM_AOS ? p.n : p.n_fm_pad;
+  j->ntiles = (nrec + tr - 1) / tr;
+}
+
 // Plans one job (everything but tile_begin), followed by a zero-fill job
 // when the destination has alignment holes.
 int plan_job(const mrn_view& src, const mrn_view& dst, std::vector<BatchJob>* out) {
@@ -70,29 +90,22 @@ int plan_job(const mrn_view& src, const mrn_view& dst, std::vector<BatchJob>* ou
       j.kind = JOB_JAG_A2S;
       j.ntiles = (src.n_records + MRN_JAG_TILE - 1) / MRN_JAG_TILE;
     } else {
+      // children: a plain conversion job; this job builds the parents
+      BatchJob kids;
+      std::memset(&kids, 0, sizeof(kids));
+      if ((rc = jagged_children_plan(src.schema, j.jp, &kids.jp.parent))) return rc;
+      convert_tiles(&kids);
+      if (kids.ntiles) out->push_back(kids);
+      j.jp.m_src = 0;
       j.kind = JOB_JAG_S2A;
       j.parent_groups = (src.n_records + 31) / 32;
-      const uint64_t groups = j.parent_groups + (j.jp.m_src + MRN_JAG_CHILD_GROUP - 1) / MRN_JAG_CHILD_GROUP;
-      j.ntiles = (groups + 7) / 8;
+      j.ntiles = (j.parent_groups + 7) / 8;
     }
   } else {
     if (src.layout.kind == MRN_AOS && dst.layout.kind == MRN_AOS) return MRN_EUNSUPPORTED;
     if ((rc = build_plan(src, dst, &j.jp.parent))) return rc;
     plan_tiles(src.schema, &j.jp.parent, MRN_BATCH_STAGE_BYTES);
-    j.kind = JOB_CONVERT;
-    const LaunchShape sh = tuned_shape(j.jp.parent);
-    uint32_t tr;
-    if (j.jp.parent.tg.tma && !sh.generic) {
-      tr = j.jp.parent.tg.T;  // batch tiles coincide with staged tiles
-    } else {
-      j.jp.parent.tg.tma = 0;
-      tr = sh.tile_records ? sh.tile_records : 1024;
-      tr = std::max<uint32_t>(256, tr / 256 * 256);
-    }
-    j.tile_records = tr;
-    const ConvPlan& p = j.jp.parent;
-    const uint64_t nrec = p.dir == DIR_FM_AOS ? p.n : p.n_fm_pad;
-    j.ntiles = (nrec + tr - 1) / tr;
+    convert_tiles(&j);
   }
   out->push_back(j);
   GapPlan g;

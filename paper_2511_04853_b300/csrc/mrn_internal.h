@@ -63,6 +63,9 @@ int build_plan(const mrn_view& src, const mrn_view& dst, ConvPlan* p);
 void plan_tiles(const mrn_schema* s, ConvPlan* p, uint32_t stage_bytes);
 // Builds the plan of a validated jagged view pair.
 int build_jagged_plan(const mrn_view& src, const mrn_view& dst, JagPlan* jp);
+// The children of a jagged SoA -> AoS plan as a plain conversion of the
+// child schema (child row j -> pool record j, j < m_src), with tiles.
+int jagged_children_plan(const mrn_schema* s, const JagPlan& jp, ConvPlan* out);
 // Alignment holes of a single-block SoA or AoSoA destination view.
 void gap_plan_of(const mrn_view& dst, GapPlan* g);
 // Zeroes the alignment holes of a single-block SoA or AoSoA device view.

@@ -211,17 +211,17 @@ __device__ __forceinline__ void st_col(char* col, uint64_t i, uint64_t v) {
 
 constexpr int kJagSlots = MRN_JAG_CHILD_GROUP / 32;  // child slots per lane per pass
 
-// One child column for the kJagSlots slots of a lane: all loads, then all
-// stores (zeros where the slot has no valid source).
-template <int S>
+// One child column of Z bytes for the S slots of a lane: all loads, then
+// all stores (zeros where the slot has no valid source).
+template <int Z, int S>
 __device__ __forceinline__ void child_column(const char* src, uint32_t stride, char* col, const uint64_t* si,
                                              const uint64_t* di, uint32_t ld_ok, uint32_t st_ok) {
-  unsigned long long v[kJagSlots];
+  unsigned long long v[S];
 #pragma unroll
-  for (int u = 0; u < kJagSlots; ++u) v[u] = (ld_ok >> u) & 1 ? ld_sized<S>(src + si[u] * stride) : 0ull;
+  for (int u = 0; u < S; ++u) v[u] = (ld_ok >> u) & 1 ? ld_sized<Z>(src + si[u] * stride) : 0ull;
 #pragma unroll
-  for (int u = 0; u < kJagSlots; ++u)
-    if ((st_ok >> u) & 1) st_col<S>(col, di[u], v[u]);
+  for (int u = 0; u < S; ++u)
+    if ((st_ok >> u) & 1) st_col<Z>(col, di[u], v[u]);
 }
 
 // The children of a jagged tile: slot j (0 <= j < agg) is child
@@ -232,19 +232,19 @@ __device__ __forceinline__ void child_column(const char* src, uint32_t stride, c
 // and split in registers, wider ones column by column.  When the tile's
 // children form one run of the pool (Run: beg[p] - excl[p] is the same `key`
 // for every parent with children), the parent lookup is skipped.
-template <bool Run>
+template <bool Run, int S = kJagSlots>
 __device__ __forceinline__ void jagged_children(const JagPlan& jp, const JagShared& sh, unsigned long long agg,
                                                 unsigned long long base, unsigned long long key, int lane,
                                                 int warp) {
   const ConvPlan& C = jp.child;
   const uint32_t nc = C.naos, stride = C.stride, vec = C.vec;
   const char* pool = C.src.base;
-  constexpr unsigned long long kPass = 32 * kJagSlots;
+  constexpr unsigned long long kPass = 32 * S;
   for (unsigned long long j0 = (unsigned long long)warp * kPass; j0 < agg; j0 += 8 * kPass) {
-    uint64_t si[kJagSlots], di[kJagSlots];
+    uint64_t si[S], di[S];
     uint32_t ld_ok = 0, st_ok = 0;
 #pragma unroll
-    for (int u = 0; u < kJagSlots; ++u) {
+    for (int u = 0; u < S; ++u) {
       const unsigned long long j = j0 + u * 32 + lane;
       const bool cok = j < agg;
       bool good = cok;
@@ -267,9 +267,9 @@ __device__ __forceinline__ void jagged_children(const JagPlan& jp, const JagShar
     }
     if (!st_ok) continue;
     if (stride <= 16) {
-      uint64_t rl[kJagSlots], rh[kJagSlots];
+      uint64_t rl[S], rh[S];
 #pragma unroll
-      for (int u = 0; u < kJagSlots; ++u) {
+      for (int u = 0; u < S; ++u) {
         rl[u] = rh[u] = 0;
         if ((ld_ok >> u) & 1) load_small(pool + si[u] * stride, stride, vec, &rl[u], &rh[u]);
       }
@@ -277,7 +277,7 @@ __device__ __forceinline__ void jagged_children(const JagPlan& jp, const JagShar
         const ColPlan cp = C.aos_cols[ci];
         char* col = C.dst.col[cp.fm];
 #pragma unroll
-        for (int u = 0; u < kJagSlots; ++u) {
+        for (int u = 0; u < S; ++u) {
           if (!((st_ok >> u) & 1)) continue;
           const uint64_t v = small_field(rl[u], rh[u], cp.aos_off, cp.size);
           switch (cp.size) {
@@ -295,10 +295,10 @@ __device__ __forceinline__ void jagged_children(const JagPlan& jp, const JagShar
       const char* src = pool + cp.aos_off;
       char* col = C.dst.col[cp.fm];
       switch (cp.size) {
-        case 8: child_column<8>(src, stride, col, si, di, ld_ok, st_ok); break;
-        case 4: child_column<4>(src, stride, col, si, di, ld_ok, st_ok); break;
-        case 2: child_column<2>(src, stride, col, si, di, ld_ok, st_ok); break;
-        default: child_column<1>(src, stride, col, si, di, ld_ok, st_ok); break;
+        case 8: child_column<8, S>(src, stride, col, si, di, ld_ok, st_ok); break;
+        case 4: child_column<4, S>(src, stride, col, si, di, ld_ok, st_ok); break;
+        case 2: child_column<2, S>(src, stride, col, si, di, ld_ok, st_ok); break;
+        default: child_column<1, S>(src, stride, col, si, di, ld_ok, st_ok); break;
       }
     }
   }
@@ -394,7 +394,7 @@ __device__ __forceinline__ unsigned long long jagged_lookback(const JagPlan& jp,
 // predecessor is already running), or whoever hands out the tiles has
 // published every sum beforehand (Published = true: the tile only publishes
 // its inclusive prefix).
-template <int VP, int VC, class Sync = CtaSync, bool Published = false, int W = MRN_WIN_WORDS>
+template <int VP, int VC, class Sync = CtaSync, bool Published = false, int W = MRN_WIN_WORDS, int RS = kJagSlots>
 __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile, unsigned long long* st,
                                                 uint32_t* tw_all, JagShared& sh, JagWarp& sw,
                                                 const Sync& sync = Sync()) {
@@ -496,7 +496,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
     kmax = max(kmax, sw.kmax[w]);
   }
   if (kmin == kmax)
-    jagged_children<true>(jp, sh, agg, base, kmin, lane, warp);
+    jagged_children<true, RS>(jp, sh, agg, base, kmin, lane, warp);
   else
     jagged_children<false>(jp, sh, agg, base, 0ull, lane, warp);
 }
