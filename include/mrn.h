@@ -225,7 +225,7 @@ int mrn_sync_bits(void* stream, uint32_t* bits);
  * AoS source and a SoA destination; any other pair returns MRN_EINVAL.
  * The scan's scratch is a fixed 256 KiB array inside the library, present on
  * every device that loads the library until the process exits; it holds at
- * most 8,380,416 parents per call, larger n_records returns MRN_ESIZE before
+ * most 16,760,832 parents per call, larger n_records returns MRN_ESIZE before
  * anything is launched.  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make that
  * first call before any stream capture.  All calls share the array and each

@@ -384,38 +384,60 @@ __device__ __forceinline__ unsigned long long jagged_lookback(const JagPlan& jp,
   return prefix;
 }
 
-// One tile of 256 parents of a jagged AoS -> SoA conversion (256 threads):
-// converts the parents, scans their lengths, obtains the tile's child base
-// by a decoupled look-back over the predecessors' published sums in `st`,
-// writes the offsets and gathers the tile's children, load-balanced over the
-// tile's threads.  Every predecessor's word must be published independently
-// of this tile's progress: either each tile publishes its own sum first
-// (Published = false; tiles handed out in increasing order, so every
-// predecessor is already running), or whoever hands out the tiles has
-// published every sum beforehand (Published = true: the tile only publishes
-// its inclusive prefix).
+// One tile of MRN_JAG_TILE (512) parents of a jagged AoS -> SoA conversion
+// (256 threads, two parents each): converts the parents, scans their
+// lengths, obtains the tile's child base by a decoupled look-back over the
+// predecessors' published sums in `st`, writes the offsets and gathers the
+// tile's children, load-balanced over the tile's threads.  Every
+// predecessor's word must be published independently of this tile's
+// progress: either each tile publishes its own sum first (Published =
+// false; tiles handed out in increasing order, so every predecessor is
+// already running), or whoever hands out the tiles has published every sum
+// beforehand (Published = true: the tile only publishes its inclusive
+// prefix).
 template <int VP, int VC, class Sync = CtaSync, bool Published = false, int W = MRN_WIN_WORDS, int RS = kJagSlots>
 __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile, unsigned long long* st,
                                                 uint32_t* tw_all, JagShared& sh, JagWarp& sw,
                                                 const Sync& sync = Sync()) {
+  static_assert(MRN_JAG_TILE == 2 * MRN_JAG_THREADS, "two parents per thread");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t* tw = tw_all + warp * MRN_TW_WORDS(W);
   const ConvPlan& P = jp.parent;
-  const uint64_t r = tile * MRN_JAG_TILE + tid;
-  const bool ok = r < P.n;
+  const uint64_t t0 = tile * MRN_JAG_TILE;
 
-  uint32_t len = 0;
-  uint64_t beg = 0;
-  aos_to_fm_lane<VP, W>(P, r, ok, ok, P.src.base + r * P.stride, tw, lane, &len, &beg);
-  if (!ok) len = 0;
-  bool bad = false;
-  if (ok && (beg > jp.pool_n || (uint64_t)len > jp.pool_n - beg)) {
-    flag_error(MRN_EINVAL);
-    bad = true;
+  // Parents q = tid and q = 256 + tid of the tile (consecutive records per
+  // warp); then their lengths go to excl[] for the scan and their begins
+  // (all ones for a parent whose children lie outside the pool) to beg[],
+  // once every warp is done with its lane words (the batch kernel lays
+  // these arrays over them).
+  uint32_t len[2];
+  uint64_t beg[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const uint64_t r = t0 + k * MRN_JAG_THREADS + tid;
+    const bool ok = r < P.n;
+    len[k] = 0;
+    beg[k] = 0;
+    aos_to_fm_lane<VP, W>(P, r, ok, ok, P.src.base + r * P.stride, tw, lane, &len[k], &beg[k]);
+    if (!ok) len[k] = 0;
+    if (ok && (beg[k] > jp.pool_n || (uint64_t)len[k] > jp.pool_n - beg[k])) {
+      flag_error(MRN_EINVAL);
+      beg[k] = ~0ull;
+    }
   }
+  sync();
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    sh.excl[k * MRN_JAG_THREADS + tid] = len[k];
+    sh.beg[k * MRN_JAG_THREADS + tid] = beg[k];
+  }
+  sync();
 
-  // CTA-wide exclusive scan of the lengths (64-bit sums).
-  unsigned long long x = len;
+  // CTA-wide exclusive scan in parent order: thread t owns parents 2t and
+  // 2t + 1 (64-bit sums).
+  const unsigned long long l0 = sh.excl[2 * tid], l1 = sh.excl[2 * tid + 1];
+  const unsigned long long b0 = sh.beg[2 * tid], b1 = sh.beg[2 * tid + 1];
+  unsigned long long x = l0 + l1;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
@@ -433,19 +455,20 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
     if (lane < 8) sw.warp[lane] = t;
   }
   sync();
-  const unsigned long long excl = x - len + (warp > 0 ? sw.warp[warp - 1] : 0ull);
+  const unsigned long long e0 = x - (l0 + l1) + (warp > 0 ? sw.warp[warp - 1] : 0ull), e1 = e0 + l0;
   const unsigned long long agg = sw.warp[7];
-  sh.excl[tid] = excl;
-  if (tid == MRN_JAG_TILE - 1) sh.excl[MRN_JAG_TILE] = agg;
-  sh.beg[tid] = bad ? ~0ull : beg;
-  // Run test: beg - excl equal for every parent with children (a bad
-  // parent fails it: min 0, max all ones).
+  sh.excl[2 * tid] = e0;
+  sh.excl[2 * tid + 1] = e1;
+  if (tid == MRN_JAG_THREADS - 1) sh.excl[MRN_JAG_TILE] = agg;
+  // Run test: beg - excl equal for every parent with children (a parent
+  // outside the pool fails it: min 0, max all ones).
   unsigned long long kmin = ~0ull, kmax = 0ull;
-  if (bad) {
+  if (b0 == ~0ull || b1 == ~0ull) {
     kmin = 0ull;
     kmax = ~0ull;
-  } else if (len > 0) {
-    kmin = kmax = beg - excl;
+  } else {
+    if (l0 > 0) kmin = min(kmin, b0 - e0), kmax = max(kmax, b0 - e0);
+    if (l1 > 0) kmin = min(kmin, b1 - e1), kmax = max(kmax, b1 - e1);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -474,16 +497,21 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
   const unsigned long long base = sw.base;
 
   // Offsets: offset_base + children before this parent.
-  if (ok) {
-    const unsigned long long o = jp.offset_base + base + excl;
-    write_offset(jp.offsets, jp.off_size, r, o);
-    if (r == P.n - 1) {
-      const unsigned long long end = o + len;
-      write_offset(jp.offsets, jp.off_size, P.n, end);
-      if (jp.total_out) *jp.total_out = base + excl + len;
-      if (jp.off_size == 4 && (end > 0xffffffffull || end < o)) flag_error(MRN_EOVERFLOW);
-    } else if (jp.off_size == 4 && o + len > 0xffffffffull) {
-      flag_error(MRN_EOVERFLOW);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const uint64_t r = t0 + 2 * tid + k;
+    const unsigned long long excl = k ? e1 : e0, len = k ? l1 : l0;
+    if (r < P.n) {
+      const unsigned long long o = jp.offset_base + base + excl;
+      write_offset(jp.offsets, jp.off_size, r, o);
+      if (r == P.n - 1) {
+        const unsigned long long end = o + len;
+        write_offset(jp.offsets, jp.off_size, P.n, end);
+        if (jp.total_out) *jp.total_out = base + excl + len;
+        if (jp.off_size == 4 && (end > 0xffffffffull || end < o)) flag_error(MRN_EOVERFLOW);
+      } else if (jp.off_size == 4 && o + len > 0xffffffffull) {
+        flag_error(MRN_EOVERFLOW);
+      }
     }
   }
 
@@ -502,7 +530,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
 }
 
 template <int VP, int VC>
-__global__ void __launch_bounds__(256) k_jagged_a2s(const __grid_constant__ JagPlan jp) {
+__global__ void __launch_bounds__(MRN_JAG_THREADS, 6) k_jagged_a2s(const __grid_constant__ JagPlan jp) {
   __shared__ uint32_t tw_all[8 * MRN_TW_WORDS_PER_WARP];
   __shared__ JagShared sh;
   __shared__ JagWarp sw;
@@ -1236,7 +1264,7 @@ int launch_jagged_a2s(JagPlan& jp, void* scratch, void* stream) {
   if (e != cudaSuccess) return cuda_status(e);
   void* fn = jag_a2s(jp.parent.vec, jp.child.vec);
   void* args[] = {&jp};
-  e = cudaLaunchKernel(fn, dim3((unsigned)jp.ntiles), dim3(MRN_JAG_TILE), args, 0, s);
+  e = cudaLaunchKernel(fn, dim3((unsigned)jp.ntiles), dim3(MRN_JAG_THREADS), args, 0, s);
   return cuda_status(e);
 }
 

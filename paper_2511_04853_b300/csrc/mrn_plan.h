@@ -80,7 +80,7 @@ struct JagPlan {
   uint64_t pool_n;           // AoS -> SoA: child records in the source pool
   uint64_t capacity;         // AoS -> SoA: child capacity of the destination
   uint64_t m_src;            // SoA -> AoS: child values in the source
-  uint64_t ntiles;           // AoS -> SoA: tiles of 256 parents
+  uint64_t ntiles;           // AoS -> SoA: tiles of MRN_JAG_TILE parents
   unsigned long long* tile_state;  // ntiles words: flag (2 bits) | value
   unsigned int* tile_counter;      // dynamic tile id
   unsigned long long timeout_ns;   // bound of each look-back wait
@@ -100,7 +100,8 @@ struct GapPlan {
   uint32_t len[MRN_MAX_GAPS];
 };
 
-#define MRN_JAG_TILE 256  // parents per tile of the jagged scan
+#define MRN_JAG_TILE 512     // parents per tile of the jagged scan
+#define MRN_JAG_THREADS 256  // threads per jagged tile (two parents each)
 #define MRN_JAG_CHILD_GROUP 128  // child records per warp group of a jagged SoA -> AoS conversion
 
 // One job of a batched launch: a plain conversion (plan in jp.parent), a

@@ -68,7 +68,7 @@ extern "C" int mrn_autotune(const mrn_schema* s, mrn_layout src_l, mrn_layout ds
   if (src_l.kind < MRN_AOS || src_l.kind > MRN_AOSOA || dst_l.kind < MRN_AOS || dst_l.kind > MRN_AOSOA ||
       (src_l.kind == MRN_AOSOA && src_l.block < 1) || (dst_l.kind == MRN_AOSOA && dst_l.block < 1))
     return MRN_EINVAL;
-  if (s->has_jagged) return MRN_EUNSUPPORTED;  // jagged tiles are fixed at 256 parents
+  if (s->has_jagged) return MRN_EUNSUPPORTED;  // jagged tiles are fixed at MRN_JAG_TILE parents
   if (src_l.kind == MRN_AOS && dst_l.kind == MRN_AOS) return MRN_EUNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MRN_ECUDA;

@@ -228,7 +228,7 @@ def test_lookback_wait_is_bounded():
     """Fault injection on the host side: tile 1 never publishes its sum, so
     tile 2's look-back wait must expire (1 ms bound) and report
     MRN_ETIMEOUT; the context stays usable afterwards."""
-    n = 4 * 256
+    n = 4 * 512  # four jagged tiles
     s, o, d = tracks(n, seed=3)
     o_aos = oracle.pack(o, d, "aos")
     try:

@@ -41,7 +41,7 @@ def test_matches_mrn_convert_twice(n, seed):
 
 def test_rejects_sizes_beyond_the_array_and_other_layouts():
     s = mrn.Schema(datagen.TRACKS)
-    big = 8_380_416 + 1
+    big = 16_760_832 + 1
     buf = garbage(1 << 12)
     src = mrn.View(s, "aos", big, base=buf, child_pool=buf, m=1)
     dst = mrn.View(s, "soa", big, base=buf, m=1)
