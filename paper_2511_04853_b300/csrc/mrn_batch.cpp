@@ -28,6 +28,7 @@ struct mrn_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   uint32_t ctas_per_sm = 0;
+  uint32_t max_chunk = 8;  // consecutive tiles a CTA takes at once
 
   ~mrn_batch() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -121,6 +122,23 @@ int plan_job(const mrn_view& src, const mrn_view& dst, std::vector<BatchJob>* ou
   return MRN_OK;
 }
 
+// Approximate bytes read and written by one tile of a job.
+double tile_traffic(const BatchJob& j) {
+  switch (j.kind) {
+    case JOB_CONVERT:
+      return (double)j.tile_records * 2.0 * j.jp.parent.stride;
+    case JOB_JAG_A2S: {
+      const JagPlan& jp = j.jp;
+      const double kids = jp.parent.n ? (double)jp.pool_n / (double)jp.parent.n : 0.0;
+      return MRN_JAG_TILE * (2.0 * jp.parent.stride + jp.off_size + 2.0 * kids * jp.child.stride);
+    }
+    case JOB_JAG_S2A:
+      return 8.0 * 32.0 * 2.0 * j.jp.parent.stride;
+    default:
+      return 256.0 * 16.0;
+  }
+}
+
 int rebuild_tables(mrn_batch* b) {
   b->jobs.clear();
   b->first_entry.clear();
@@ -137,6 +155,12 @@ int rebuild_tables(mrn_batch* b) {
     t += b->jobs[i].ntiles;
   }
   b->total_tiles = t;
+  // Chunks of about 192 KB of traffic: eight staged conversion tiles, one
+  // jagged tile.
+  double bytes = 0;
+  for (const BatchJob& j : b->jobs) bytes += (double)j.ntiles * tile_traffic(j);
+  const double per_tile = t ? bytes / (double)t : 1.0;
+  b->max_chunk = (uint32_t)std::max(1.0, std::min(8.0, 196608.0 / std::max(per_tile, 1.0)));
   return MRN_OK;
 }
 
@@ -163,7 +187,8 @@ int enqueue(mrn_batch* b, cudaStream_t s) {
   if (cudaMemsetAsync(b->d_scratch, 0, b->scratch_bytes, s) != cudaSuccess) return MRN_ECUDA;
   return launch_batch(b->d_jobs, b->d_first, (unsigned)b->jobs.size(), b->total_tiles,
                       reinterpret_cast<unsigned int*>(b->d_scratch),
-                      reinterpret_cast<unsigned long long*>(b->d_scratch + 256), b->ctas_per_sm, s);
+                      reinterpret_cast<unsigned long long*>(b->d_scratch + 256), b->ctas_per_sm,
+                      b->max_chunk, s);
 }
 
 int capture(mrn_batch* b) {

@@ -89,10 +89,11 @@ int launch_jagged_a2s(JagPlan& jp, void* scratch, void* stream);
 int launch_jagged_s2a(const JagPlan& jp, void* stream);
 int launch_jagged_count(const ConvPlan& parent, uint64_t* dev_total, void* stream);
 
-// Persistent launch of a batch (mrn_batch.cpp owns the device tables).
+// Persistent launch of a batch (mrn_batch.cpp owns the device tables);
+// max_chunk caps the consecutive tiles a CTA takes at once.
 int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, unsigned int njobs,
                  unsigned long long total_tiles, unsigned int* counter, unsigned long long* states,
-                 unsigned int ctas_per_sm, void* stream);
+                 unsigned int ctas_per_sm, unsigned int max_chunk, void* stream);
 int batch_occupancy();
 
 // Cached launch shape for a plan (autotuner), or the default.

@@ -1301,12 +1301,12 @@ int batch_occupancy() {
 
 int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, unsigned int njobs,
                  unsigned long long total_tiles, unsigned int* counter, unsigned long long* states,
-                 unsigned int ctas_per_sm, void* stream) {
+                 unsigned int ctas_per_sm, unsigned int max_chunk, void* stream) {
   if (total_tiles == 0) return MRN_OK;
   const int occ = batch_occupancy();
   const int per_sm = ctas_per_sm ? std::min((int)ctas_per_sm, occ) : occ;
   const uint64_t cap = (uint64_t)device_sm_count() * (uint64_t)per_sm;
-  const uint32_t chunk = chunk_for(total_tiles, cap);
+  const uint32_t chunk = std::min<uint32_t>(std::max(1u, max_chunk), chunk_for(total_tiles, cap));
   const uint64_t chunks = (total_tiles + chunk - 1) / chunk;
   const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(cap, chunks));
   k_batch<<<grid, kBThreads, kBatchSmem, static_cast<cudaStream_t>(stream)>>>(jobs, first_tile, njobs,
