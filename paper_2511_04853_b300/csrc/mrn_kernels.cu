@@ -304,6 +304,50 @@ __device__ __forceinline__ void jagged_children(const JagPlan& jp, const JagShar
   }
 }
 
+// The children of a jagged tile that form one run of the pool, for child
+// records of at most 8 bytes: slot j moves pool record key + j to row
+// base + j; each lane holds S records (one 64-bit word each) in flight.
+template <int S>
+__device__ __forceinline__ void jagged_run_small(const JagPlan& jp, unsigned long long agg, unsigned long long base,
+                                                 unsigned long long key, int lane, int warp) {
+  const ConvPlan& C = jp.child;
+  const uint32_t nc = C.naos, stride = C.stride, vec = C.vec;
+  const char* pool = C.src.base;
+  constexpr unsigned long long kPass = 32 * S;
+  for (unsigned long long j0 = (unsigned long long)warp * kPass; j0 < agg; j0 += 8 * kPass) {
+    uint64_t rec[S];
+    uint32_t ok = 0;
+#pragma unroll
+    for (int u = 0; u < S; ++u) {
+      const unsigned long long j = j0 + u * 32 + lane;
+      const bool cok = j < agg;
+      const bool sok = cok && base + j < jp.capacity;
+      if (cok && !sok) flag_error(MRN_ESIZE);
+      ok |= (uint32_t)sok << u;
+      uint64_t hi;
+      rec[u] = 0;
+      if (sok) load_small(pool + (key + j) * stride, stride, vec, &rec[u], &hi);
+    }
+    if (!ok) continue;
+    for (uint32_t ci = 0; ci < nc; ++ci) {
+      const ColPlan cp = C.aos_cols[ci];
+      char* col = C.dst.col[cp.fm];
+#pragma unroll
+      for (int u = 0; u < S; ++u) {
+        if (!((ok >> u) & 1)) continue;
+        const unsigned long long row = base + j0 + u * 32 + lane;
+        const uint64_t v = small_field(rec[u], 0, cp.aos_off, cp.size);
+        switch (cp.size) {
+          case 8: st_col<8>(col, row, v); break;
+          case 4: st_col<4>(col, row, v); break;
+          case 2: st_col<2>(col, row, v); break;
+          default: st_col<1>(col, row, v); break;
+        }
+      }
+    }
+  }
+}
+
 // Children of a jagged SoA -> AoS conversion, records [j0, j0 + 32 *
 // kJagSlots) of one warp: records of at most 16 bytes are assembled in
 // registers from the child columns and stored whole; wider ones go through
@@ -395,7 +439,7 @@ __device__ __forceinline__ unsigned long long jagged_lookback(const JagPlan& jp,
 // already running), or whoever hands out the tiles has published every sum
 // beforehand (Published = true: the tile only publishes its inclusive
 // prefix).
-template <int VP, int VC, class Sync = CtaSync, bool Published = false, int W = MRN_WIN_WORDS, int RS = kJagSlots>
+template <int VP, int VC, class Sync = CtaSync, bool Published = false, int W = MRN_WIN_WORDS, bool SmallRun = true>
 __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile, unsigned long long* st,
                                                 uint32_t* tw_all, JagShared& sh, JagWarp& sw,
                                                 const Sync& sync = Sync()) {
@@ -523,8 +567,10 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
     kmin = min(kmin, sw.kmin[w]);
     kmax = max(kmax, sw.kmax[w]);
   }
-  if (kmin == kmax)
-    jagged_children<true, RS>(jp, sh, agg, base, kmin, lane, warp);
+  if (SmallRun && kmin == kmax && jp.child.stride <= 8)
+    jagged_run_small<kJagSlots>(jp, agg, base, kmin, lane, warp);
+  else if (kmin == kmax)
+    jagged_children<true>(jp, sh, agg, base, kmin, lane, warp);
   else
     jagged_children<false>(jp, sh, agg, base, 0ull, lane, warp);
 }
@@ -1017,8 +1063,8 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
         const uint32_t tr = J.tile_records;
         conv_range<0, kBWin>(J.jp.parent, local * tr, (local + 1) * tr, tw, lane, warp, 8);
       } else if (J.kind == JOB_JAG_A2S) {
-        jagged_a2s_tile<0, 0, ConsumerSync, true, kBWin>(J.jp, local, states + J.tile_begin, scratch, sh, sw,
-                                                         sync);
+        jagged_a2s_tile<0, 0, ConsumerSync, true, kBWin, false>(J.jp, local, states + J.tile_begin, scratch, sh,
+                                                                sw, sync);
         // the tile's arrays lie over the lane words: every warp is done
         // reading them before any warp's next tile writes its lane words
         sync();
