@@ -796,10 +796,25 @@ __device__ __forceinline__ void tma_store_tile_warp(const ConvPlan& p, uint64_t 
   bulk_commit();
 }
 
-// Loader warp: the plan's column descriptors and header into a stage's table
-// (lane c writes column c).
-__device__ __forceinline__ void fill_stage_desc(const ConvPlan& p, StageDesc* sd, unsigned int job, int lane) {
+// Loader warp: the plan's column descriptors and header into stage s's
+// table (lane c writes column c), copied from another stage when one holds
+// the same job's.
+__device__ __forceinline__ void fill_stage_desc(const ConvPlan& p, const BatchSmem& m, uint32_t s,
+                                                unsigned int job, int lane) {
+  StageDesc* sd = m.desc(s);
   if (sd->job == job) return;
+  // another stage may already hold this job's table: copy it in shared memory
+  for (uint32_t q = 0; q < kBNS; ++q) {
+    const StageDesc* o = m.desc(q);
+    if (q == s || o->job != job) continue;
+    for (uint32_t c = lane; c < o->h.ncols; c += 32) sd->d[c] = o->d[c];
+    __syncwarp();
+    if (lane == 0) {
+      sd->h = o->h;
+      sd->job = job;
+    }
+    return;
+  }
   for (uint32_t c = lane; c < p.ncols; c += 32) sd->d[c] = tile_desc(p, c);
   __syncwarp();
   if (lane != 0) return;
@@ -900,7 +915,7 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
           it.pad = 0;
           *m.sq(c_issue % kSQ) = it;
         }
-        fill_stage_desc(P, m.desc(s), cand.job, lane);
+        fill_stage_desc(P, m, s, cand.job, lane);
         __syncwarp();
         tma_load_tile_warp(P, cand.local, m.src(s), m.full(s), lane);
         ++c_issue;
