@@ -293,6 +293,7 @@ void tile_geometry(const mrn_schema* s, ConvPlan* p, uint32_t stage_bytes) {
   }
   if (T == 0) return;
   g.T = T;
+  g.G = (uint32_t)q;
   g.src_bytes = (uint32_t)tile_bytes(s, p->src, T, g.src_off);
   g.dst_bytes = (uint32_t)tile_bytes(s, p->dst, T, g.dst_off);
   uint32_t used = 0, k = 0;

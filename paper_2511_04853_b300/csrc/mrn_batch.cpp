@@ -74,7 +74,7 @@ void convert_tiles(BatchJob* j) {
   j->tile_records = tr;
   const ConvPlan& p = j->jp.parent;
   const uint64_t nrec = p.dir == DIR_FM_AOS ? p.n : p.n_fm_pad;
-  j->ntiles = (nrec + tr - 1) / tr;
+  j->ntiles = p.tg.tma ? staged_tile_count(p.n, nrec, p.tg.T, p.tg.G) : (nrec + tr - 1) / tr;
 }
 
 // Plans one job (everything but tile_begin), followed by a zero-fill job

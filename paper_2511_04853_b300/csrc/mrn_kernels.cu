@@ -56,12 +56,12 @@ __global__ void __launch_bounds__(256) k_convert(const __grid_constant__ ConvPla
 // ------------------------------------------------- staged tile transform
 
 // All threads: source tile -> destination tile in shared memory.
-__device__ __forceinline__ void tma_transform(const TileHdr& h, uint32_t desc, const char* st, char* dt, int lane,
-                                              int warp) {
+__device__ __forceinline__ void tma_transform(const TileHdr& h, uint32_t desc, const char* st, char* dt, uint32_t R,
+                                              int lane, int warp) {
   const uint32_t s = smem_u32(st), d = smem_u32(dt);
   const TileHdr hh = h;
-  for (uint32_t g = (uint32_t)warp * 32; g < hh.T; g += 2 * 8 * 32)
-    tile_convert(hh, desc, s, d, g + lane, g + 8 * 32 < hh.T);
+  for (uint32_t g = (uint32_t)warp * 32; g < R; g += 2 * 8 * 32)
+    tile_convert(hh, desc, s, d, g + lane, g + 8 * 32 < R);
 }
 
 // Entry k of the staged-transform descriptor table: the k-th column in
@@ -677,7 +677,7 @@ struct TileSlot {
   unsigned long long t;  // global tile; >= total_tiles: no more tiles
   unsigned long long local;
   unsigned int job;
-  unsigned int staged;
+  unsigned int staged;  // records of a staged tile; 0: the tile runs directly
 };
 
 struct StageDesc {
@@ -690,7 +690,7 @@ struct StageDesc {
 struct StoreItem {
   unsigned long long local;
   unsigned int job;
-  unsigned int pad;
+  unsigned int records;  // records of the tile (T, or fewer for a job's partial staged tile)
 };
 
 // Consumer scratch: 8 warps' lane words in 32-byte windows (a jagged tile's
@@ -759,39 +759,51 @@ struct ConsumerSync {
   }
 };
 
-// Warp-wide bulk loads of source tile lt: lane 0 sets the transaction
-// count, then lane c copies SoA column c (lane 0 copies an AoS / AoSoA
-// tile, which is one range).
-__device__ __forceinline__ void tma_load_tile_warp(const ConvPlan& p, uint64_t lt, char* stage,
+// Bytes of the first R records (a multiple of the staging granule) of a
+// tile side whose full tile is `full` bytes.
+__device__ __forceinline__ uint32_t side_tile_bytes(const ConvPlan& p, const SidePlan& sp, uint32_t full, uint32_t R) {
+  if (R == p.tg.T) return full;
+  if (sp.kind == K_AOS) return R * p.stride;
+  if (sp.kind == K_AOSOA) return R / sp.block * (uint32_t)sp.block_bytes;
+  return full / p.tg.T * R;  // SoA: T * (sum of column sizes), columns packed
+}
+
+// Warp-wide bulk loads of the first R records of source tile lt: lane 0
+// sets the transaction count, then lane c copies SoA column c (lane 0
+// copies an AoS / AoSoA tile, which is one range).
+__device__ __forceinline__ void tma_load_tile_warp(const ConvPlan& p, uint64_t lt, uint32_t R, char* stage,
                                                    unsigned long long* bar, int lane) {
   const TileGeom& g = p.tg;
   const uint64_t t0 = lt * g.T;
   const SidePlan& sp = p.src;
-  if (lane == 0) mbar_expect_tx(bar, g.src_bytes);
+  const uint32_t bytes = side_tile_bytes(p, sp, g.src_bytes, R);
+  if (lane == 0) mbar_expect_tx(bar, bytes);
   __syncwarp();
   if (sp.kind == K_AOS) {
-    if (lane == 0) bulk_g2s(stage, sp.base + t0 * p.stride, g.src_bytes, bar);
+    if (lane == 0) bulk_g2s(stage, sp.base + t0 * p.stride, bytes, bar);
   } else if (sp.kind == K_AOSOA) {
-    if (lane == 0) bulk_g2s(stage, sp.base + (t0 / sp.block) * sp.block_bytes, g.src_bytes, bar);
+    if (lane == 0) bulk_g2s(stage, sp.base + (t0 / sp.block) * sp.block_bytes, bytes, bar);
   } else {
     for (uint32_t c = lane; c < p.ncols; c += 32)
-      bulk_g2s(stage + g.src_off[c], sp.col[c] + t0 * p.fm_size[c], g.T * p.fm_size[c], bar);
+      bulk_g2s(stage + g.src_off[c], sp.col[c] + t0 * p.fm_size[c], R * p.fm_size[c], bar);
   }
 }
 
-// Warp-wide bulk stores of destination tile lt; every lane commits its own
-// bulk group.
-__device__ __forceinline__ void tma_store_tile_warp(const ConvPlan& p, uint64_t lt, const char* tile, int lane) {
+// Warp-wide bulk stores of the first R records of destination tile lt;
+// every lane commits its own bulk group.
+__device__ __forceinline__ void tma_store_tile_warp(const ConvPlan& p, uint64_t lt, uint32_t R, const char* tile,
+                                                    int lane) {
   const TileGeom& g = p.tg;
   const uint64_t t0 = lt * g.T;
   const SidePlan& sp = p.dst;
+  const uint32_t bytes = side_tile_bytes(p, sp, g.dst_bytes, R);
   if (sp.kind == K_AOS) {
-    if (lane == 0) bulk_s2g(sp.base + t0 * p.stride, tile, g.dst_bytes);
+    if (lane == 0) bulk_s2g(sp.base + t0 * p.stride, tile, bytes);
   } else if (sp.kind == K_AOSOA) {
-    if (lane == 0) bulk_s2g(sp.base + (t0 / sp.block) * sp.block_bytes, tile, g.dst_bytes);
+    if (lane == 0) bulk_s2g(sp.base + (t0 / sp.block) * sp.block_bytes, tile, bytes);
   } else {
     for (uint32_t c = lane; c < p.ncols; c += 32)
-      bulk_s2g(sp.col[c] + t0 * p.fm_size[c], tile + g.dst_off[c], g.T * p.fm_size[c]);
+      bulk_s2g(sp.col[c] + t0 * p.fm_size[c], tile + g.dst_off[c], R * p.fm_size[c]);
   }
   bulk_commit();
 }
@@ -893,7 +905,10 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
         cand.job = cursor;
         cand.local = cand.t - J.tile_begin;
         const ConvPlan& P = J.jp.parent;
-        cand.staged = J.kind == JOB_CONVERT && P.tg.tma && (cand.local + 1) * P.tg.T <= P.n;
+        if (J.kind == JOB_CONVERT && P.tg.tma) {
+          const StagedTiles st = staged_tiles(P.n, 0, P.tg.T, P.tg.G);
+          cand.staged = cand.local < st.nfull ? P.tg.T : (cand.local == st.nfull ? (uint32_t)st.rs : 0u);
+        }
       }
       have = true;
     }
@@ -912,12 +927,12 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
           StoreItem it;
           it.local = cand.local;
           it.job = cand.job;
-          it.pad = 0;
+          it.records = cand.staged;
           *m.sq(c_issue % kSQ) = it;
         }
         fill_stage_desc(P, m, s, cand.job, lane);
         __syncwarp();
-        tma_load_tile_warp(P, cand.local, m.src(s), m.full(s), lane);
+        tma_load_tile_warp(P, cand.local, cand.staged, m.src(s), m.full(s), lane);
         ++c_issue;
       }
       if (lane == 0) {
@@ -969,7 +984,7 @@ __device__ __forceinline__ void batch_storer(const BatchJob* __restrict__ jobs, 
     if (ready) {
       __syncwarp();  // orders lane 0's acquire before the other lanes' stores
       const StoreItem it = *m.sq(c % kSQ);
-      tma_store_tile_warp(jobs[it.job].jp.parent, it.local, m.dst(d), lane);
+      tma_store_tile_warp(jobs[it.job].jp.parent, it.local, it.records, m.dst(d), lane);
       bulk_wait_read<0>();
       __syncwarp();
       if (lane == 0) mbar_arrive(m.dfree(d));
@@ -1062,7 +1077,7 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
         break;
       }
       const StageDesc* sd = m.desc(s);
-      tma_transform(sd->h, smem_u32(sd->d), m.src(s), m.dst(d), lane, warp);
+      tma_transform(sd->h, smem_u32(sd->d), m.src(s), m.dst(d), ts.staged, lane, warp);
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
@@ -1075,8 +1090,16 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
       const BatchJob& J = jobs[ts.job];
       const unsigned long long local = ts.local;
       if (J.kind == JOB_CONVERT) {
-        const uint32_t tr = J.tile_records;
-        conv_range<0, kBWin>(J.jp.parent, local * tr, (local + 1) * tr, tw, lane, warp, 8);
+        const ConvPlan& P = J.jp.parent;
+        uint64_t r0, r1;
+        if (P.tg.tma) {  // the records after a staged job's staged tiles
+          r0 = staged_tiles(P.n, 0, P.tg.T, P.tg.G).d0;
+          r1 = ~0ull;
+        } else {
+          r0 = local * J.tile_records;
+          r1 = r0 + J.tile_records;
+        }
+        conv_range<0, kBWin>(P, r0, r1, tw, lane, warp, 8);
       } else if (J.kind == JOB_JAG_A2S) {
         jagged_a2s_tile<0, 0, ConsumerSync, true, kBWin, false>(J.jp, local, states + J.tile_begin, scratch, sh,
                                                                 sw, sync);
@@ -1222,7 +1245,7 @@ int launch_convert(const ConvPlan& p, void* stream, const LaunchShape* shape) {
     job.kind = JOB_CONVERT;
     job.jp.parent = p;
     job.tile_records = p.tg.T;
-    job.ntiles = (nrec + p.tg.T - 1) / p.tg.T;
+    job.ntiles = staged_tile_count(p.n, nrec, p.tg.T, p.tg.G);
     const void* fn = reinterpret_cast<const void*>(&k_convert_ws);
     allow_batch_smem(fn);
     const int occ = occupancy(fn, kBThreads, kBatchSmem);

@@ -40,7 +40,8 @@ struct ColPlan {
 #define MRN_BATCH_STAGE_BYTES 12288u  // stage of the warp-specialized pipeline
 struct TileGeom {
   uint32_t tma;        // 1: full tiles go through the TMA pipeline
-  uint32_t T;          // records per tile (multiple of 32 and of each AoSoA B)
+  uint32_t T;          // records per tile (multiple of G)
+  uint32_t G;          // staging granule: lcm(32, each AoSoA B)
   uint32_t src_bytes;  // bytes of a source tile
   uint32_t dst_bytes;  // bytes of a destination tile
   uint32_t pad;        // 1: the AoS record has padding bytes (zeroed first)
@@ -99,6 +100,34 @@ struct GapPlan {
   uint64_t off[MRN_MAX_GAPS];
   uint32_t len[MRN_MAX_GAPS];
 };
+
+// Tiles of a staged conversion of n source records (nrec records written:
+// n, or n rounded up to whole AoSoA blocks): the full tiles of T records,
+// then a staged tile of the largest multiple of G inside the partial last
+// tile, then one direct tile of the records left (fewer than G, plus any
+// AoSoA padding slots).
+struct StagedTiles {
+  uint64_t nfull;  // full tiles
+  uint64_t rs;     // records of the partial staged tile (0: none)
+  uint64_t d0;     // first record of the direct tile (== nrec: none)
+};
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline StagedTiles staged_tiles(uint64_t n, uint64_t nrec, uint32_t T, uint32_t G) {
+  StagedTiles s;
+  s.nfull = n / T;
+  s.rs = (n - s.nfull * T) / G * G;
+  s.d0 = s.nfull * T + s.rs;
+  return s;
+}
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline uint64_t staged_tile_count(uint64_t n, uint64_t nrec, uint32_t T, uint32_t G) {
+  const StagedTiles s = staged_tiles(n, nrec, T, G);
+  return s.nfull + (s.rs ? 1 : 0) + (nrec > s.d0 ? 1 : 0);
+}
 
 #define MRN_JAG_TILE 512     // parents per tile of the jagged scan
 #define MRN_JAG_THREADS 256  // threads per jagged tile (two parents each)

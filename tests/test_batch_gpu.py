@@ -176,3 +176,28 @@ def test_batch_lookback_wait_is_bounded():
     assert mrn.sync() == mrn.OK
     want = oracle.convert(o, o_aos, "soa", m=d["m"]).base
     assert np.array_equal(host(dst.tensors[0], want.size), want)
+
+
+def test_partial_tiles_in_one_batch():
+    """Collections whose sizes cut the staged tiles at every kind of place,
+    all in one launch (staged partial tiles and direct remainders side by
+    side with full tiles)."""
+    pairs, checks = [], []
+    kinds = [(("aos", 0), ("soa", 0)), (("soa", 0), ("aosoa", 128)), (("aosoa", 32), ("aos", 0)),
+             (("soa", 0), ("aos", 0))]
+    for j, n in enumerate([1, 31, 32, 33, 511, 513, 544, 545, 1151, 1152, 1153, 4097, 20000]):
+        for name in ("cells", "points"):
+            desc = datagen.WORKLOAD_SCHEMAS[name]
+            s, o = mrn.Schema(desc), oracle.Schema(desc)
+            (sk, sb), (dk, db) = kinds[(j + len(name)) % len(kinds)]
+            d = datagen.workload(name, n, 700 + j)
+            o_src = oracle.pack(o, d, sk, sb)
+            want = oracle.convert(o, o_src, dk, db).base
+            dst = dev_dest(s, dk, n, 0, db)
+            pairs.append((mrn.View(s, sk, n, block=sb, base=dev(o_src.base)), dst))
+            checks.append((dst, want))
+    b = mrn.Batch(pairs, use_graph=True)
+    b.launch()
+    assert mrn.sync() == mrn.OK
+    for k, (dst, want) in enumerate(checks):
+        assert np.array_equal(host(dst.tensors[0], want.size), want), "job %d" % k

@@ -156,10 +156,13 @@ def test_direct_path_parity(direct_path, name, src, dst):
     check_pair(name, 5000, src[0], src[1], dst[0], dst[1])
 
 
-@pytest.mark.parametrize("n", [683, 2048, 100000])
+@pytest.mark.parametrize("n", [31, 32, 33, 383, 511, 512, 513, 543, 544, 545, 683, 1024 + 127, 1024 + 128,
+                               1024 + 129, 2048, 100000])
 def test_staged_tiles_and_tail(n):
-    """Sizes around whole staged tiles: full tiles go through shared memory,
-    the remainder through the direct path."""
+    """Sizes around whole staged tiles (512 cell / 384 point records) and
+    staging granules (32 records; 128 with AoSoA(128)): full tiles and the
+    granule-aligned part of the last tile go through shared memory, the
+    records after them through the direct path."""
     for (sk, sb), (dk, db) in [(("aos", 0), ("soa", 0)), (("soa", 0), ("aosoa", 128)),
                                (("aosoa", 32), ("aos", 0))]:
         check_pair("cells", n, sk, sb, dk, db, seed=7)
