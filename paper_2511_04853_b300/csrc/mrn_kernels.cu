@@ -539,6 +539,24 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
   }
   sync();
   const unsigned long long base = sw.base;
+  // Children in one run of the pool: start pulling their source range into
+  // L2 while the offsets are written.
+  kmin = ~0ull;
+  kmax = 0ull;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    kmin = min(kmin, sw.kmin[w]);
+    kmax = max(kmax, sw.kmax[w]);
+  }
+  const bool run = kmin == kmax;
+  if (run && warp == 0 && agg > 0) {
+    const uint32_t cs = jp.child.stride;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(jp.child.src.base + kmin * cs);
+    const uintptr_t b = reinterpret_cast<uintptr_t>(jp.child.src.base + (kmin + agg) * cs);
+    const uintptr_t lo = a & ~(uintptr_t)15, hi = (b + 15) & ~(uintptr_t)15;
+    for (uintptr_t q = lo + (uintptr_t)lane * 32768; q < hi; q += 32 * 32768)
+      bulk_prefetch_l2(reinterpret_cast<const void*>(q), (uint32_t)min((uintptr_t)32768, hi - q));
+  }
 
   // Offsets: offset_base + children before this parent.
 #pragma unroll
@@ -560,16 +578,9 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
   }
 
   // Children, as one run of the pool when they form one.
-  kmin = ~0ull;
-  kmax = 0ull;
-#pragma unroll
-  for (int w = 0; w < 8; ++w) {
-    kmin = min(kmin, sw.kmin[w]);
-    kmax = max(kmax, sw.kmax[w]);
-  }
-  if (SmallRun && kmin == kmax && jp.child.stride <= 8)
+  if (SmallRun && run && jp.child.stride <= 8)
     jagged_run_small<kJagSlots>(jp, agg, base, kmin, lane, warp);
-  else if (kmin == kmax)
+  else if (run)
     jagged_children<true>(jp, sh, agg, base, kmin, lane, warp);
   else
     jagged_children<false>(jp, sh, agg, base, 0ull, lane, warp);
