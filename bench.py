@@ -574,11 +574,21 @@ def run_e2e(mrn, torch, s, colls, args, world):
                       mrn.View(s, "aosoa", n, block=BLOCK, base=d_blk[i]),
                       mrn.View(s, "aos", n, base=h_out[i], mem="pinned")))
 
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    main = torch.cuda.current_stream()
+
     def step():
-        for hin, soa, blk, hout in views:
-            mrn.transfer_convert(hin, soa, chunk_bytes=1 << 20, n_slots=4)
-            mrn.convert(soa, blk)
-            mrn.transfer_convert(blk, hout, chunk_bytes=1 << 20, n_slots=4)
+        # collection i on stream i % 2: one collection's device -> host copy
+        # overlaps the next one's host -> device copy
+        for st in streams:
+            st.wait_stream(main)
+        for i, (hin, soa, blk, hout) in enumerate(views):
+            st = streams[i % len(streams)]
+            mrn.transfer_convert(hin, soa, stream=st)
+            mrn.convert(soa, blk, stream=st)
+            mrn.transfer_convert(blk, hout, stream=st)
+        for st in streams:
+            main.wait_stream(st)
 
     for _ in range(2):
         step()
@@ -597,7 +607,8 @@ def run_e2e(mrn, torch, s, colls, args, world):
     return {"value": round(world * step_bytes / el / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": len(colls) * n * 24, "d2h_bytes_per_step": len(colls) * n * 24,
             "ms_per_step": round(el * 1e3, 3), "steps": k,
-            "path": "mrn_transfer_convert (1 MiB chunks, 4 slots) + mrn_convert, pinned host buffers"}
+            "path": "mrn_transfer_convert (default 4 MiB chunks, 4 slots) + mrn_convert, pinned host buffers, "
+                    "collection i on stream i % 2"}
 
 
 def secondary(mrn, torch, stream, peak):
@@ -681,8 +692,24 @@ def secondary(mrn, torch, stream, peak):
         b.record(stream)
         b.synchronize()
         best_d2h = min(best_d2h, a.elapsed_time(b))
+    # both directions at once (two streams): the ceiling of a round trip
+    h2 = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
+    dbuf2 = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    best_bi = 1e9
+    for _ in range(5):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s1):
+            dbuf.copy_(h, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h2.copy_(dbuf2, non_blocking=True)
+        torch.cuda.synchronize()
+        best_bi = min(best_bi, time.perf_counter() - t0)
     out["host_link_gbps"] = {"h2d": round((1 << 30) / (best_h2d * 1e-3) / 1e9, 1),
-                             "d2h": round((1 << 30) / (best_d2h * 1e-3) / 1e9, 1)}
+                             "d2h": round((1 << 30) / (best_d2h * 1e-3) / 1e9, 1),
+                             "both_directions_total": round(2 * (1 << 30) / best_bi / 1e9, 1)}
+    del h2, dbuf2
     del h, dbuf
     torch.cuda.empty_cache()
     return out

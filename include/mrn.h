@@ -265,7 +265,10 @@ typedef struct mrn_transfer_opts {
  * (convert into staging, then copy out).  Equal layouts skip staging.
  * Jagged schemas: the whole source is staged, then converted.
  * Ordered after prior work on `stream`; later work on `stream` waits for
- * it.  Pageable host memory works but serialises the copies. */
+ * it.  Each device has one pipeline per direction: calls in the same
+ * direction run one after another, a host->device and a device->host call
+ * issued on different streams overlap (both directions of the host link).
+ * Pageable host memory works but serialises the copies. */
 int mrn_transfer_convert(const mrn_view* src, const mrn_view* dst,
                          const mrn_transfer_opts* opts, void* stream);
 

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <new>
 #include <numeric>
 
 namespace mrn {
@@ -355,8 +356,12 @@ int TransferEngine::run_chunked(const mrn_view& src, const mrn_view& dst, uint64
 }
 
 namespace {
-std::mutex g_engine_mu;
-TransferEngine* g_engine = nullptr;
+// The default pipelines: one per device and direction, so that a
+// host -> device and a device -> host transfer (issued on different
+// streams) use both directions of the host link at once.
+constexpr int kMaxDevices = 64;
+std::mutex g_engine_mu[kMaxDevices][2];
+TransferEngine* g_engine[kMaxDevices][2];
 }  // namespace
 
 }  // namespace mrn
@@ -374,8 +379,12 @@ extern "C" int mrn_transfer_convert(const mrn_view* src, const mrn_view* dst, co
   const bool d2h = src->mem == MRN_MEM_DEVICE && src->device == dev && is_host(*dst);
   if (!h2d && !d2h) return MRN_EINVAL;
   if (jag && dst->layout.kind == MRN_AOS && dst->n_children < src->n_children) return MRN_ESIZE;
-  std::lock_guard<std::mutex> lk(g_engine_mu);
-  if (!g_engine) g_engine = new TransferEngine();
-  return g_engine->run(*src, *dst, opts ? opts->chunk_bytes : 0, opts ? opts->n_slots : 0,
-                       static_cast<cudaStream_t>(stream));
+  if (dev >= kMaxDevices) return MRN_EUNSUPPORTED;
+  const int dir = h2d ? 0 : 1;
+  std::lock_guard<std::mutex> lk(g_engine_mu[dev][dir]);
+  TransferEngine*& e = g_engine[dev][dir];
+  if (!e) e = new (std::nothrow) TransferEngine();
+  if (!e) return MRN_ENOMEM;
+  return e->run(*src, *dst, opts ? opts->chunk_bytes : 0, opts ? opts->n_slots : 0,
+                static_cast<cudaStream_t>(stream));
 }

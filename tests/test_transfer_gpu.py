@@ -128,3 +128,36 @@ def test_host_to_host_rejected():
     st = mrn.lib().mrn_transfer_convert(mrn.View(s, "aos", 10, base=a, mem="host").ref,
                                         mrn.View(s, "soa", 10, base=a, mem="host").ref, None, None)
     assert st == mrn.EINVAL
+
+
+def test_both_directions_on_several_streams():
+    """Host -> device and device -> host transfers issued on four streams
+    (they overlap on the two direction pipelines) give the oracle's bytes,
+    and the round trip host AoS -> device SoA -> AoSoA(32) -> host AoS
+    reproduces every collection."""
+    t = torch()
+    s, o = mrn.Schema(datagen.CELLS), oracle.Schema(datagen.CELLS)
+    streams = [t.cuda.Stream() for _ in range(4)]
+    jobs = []
+    for i in range(8):
+        n = 50000 + 977 * i
+        d = datagen.workload("cells", n, 40 + i)
+        o_aos = oracle.pack(o, d, "aos")
+        jobs.append((n, o_aos, host_side(o_aos.base), garbage(s.required_bytes("soa", n)),
+                     garbage(s.required_bytes("aosoa", n, 0, 32)), pinned(n * 24)))
+    t.cuda.synchronize()
+    for i, (n, o_aos, h_in, d_soa, d_blk, h_out) in enumerate(jobs):
+        st = streams[i % 4]
+        soa = mrn.View(s, "soa", n, base=d_soa)
+        blk = mrn.View(s, "aosoa", n, block=32, base=d_blk)
+        mrn.transfer_convert(mrn.View(s, "aos", n, base=h_in, mem="pinned"), soa, chunk_bytes=256 << 10,
+                             n_slots=4, stream=st)
+        mrn.convert(soa, blk, stream=st)
+        mrn.transfer_convert(blk, mrn.View(s, "aos", n, base=h_out, mem="pinned"), chunk_bytes=256 << 10,
+                             n_slots=4, stream=st)
+    t.cuda.synchronize()
+    assert mrn.sync() == mrn.OK
+    for n, o_aos, h_in, d_soa, d_blk, h_out in jobs:
+        want_soa = oracle.convert(o, o_aos, "soa").base
+        assert np.array_equal(host(d_soa, want_soa.size), want_soa)
+        assert np.array_equal(h_out.numpy()[: n * 24], o_aos.base[: n * 24])
