@@ -676,6 +676,29 @@ def secondary(mrn, torch, stream, peak):
         del recs, pool, soa
     out["single_collection"] = rows
     del flush
+    # transfer-and-convert: chunked staging against zero-copy (the kernel
+    # reads / writes the pinned host buffer itself), source bytes per second
+    s = mrn.Schema(datagen.CELLS)
+    abl = {}
+    for n in (200000, 1 << 24):
+        h_aos = torch.full((n * 24,), 0x3C, dtype=torch.uint8).pin_memory()
+        d_soa = torch.empty(s.required_bytes("soa", n), dtype=torch.uint8, device="cuda")
+        hv = mrn.View(s, "aos", n, base=h_aos, mem="pinned")
+        dv = mrn.View(s, "soa", n, base=d_soa)
+        for name, zc in (("chunked", False), ("zero_copy", True)):
+            for direction, a, b in (("h2d", hv, dv), ("d2h", dv, hv)):
+                reps = 20 if n < 1e6 else 5
+                mrn.transfer_convert(a, b, stream=stream, zero_copy=zc)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    mrn.transfer_convert(a, b, stream=stream, zero_copy=zc)
+                torch.cuda.synchronize()
+                el = (time.perf_counter() - t0) / reps
+                abl["cells_%d_%s_%s_gbps" % (n, direction, name)] = round(n * 24 / el / 1e9, 1)
+        assert mrn.sync() == mrn.OK
+        del h_aos, d_soa
+    out["transfer_chunked_vs_zero_copy"] = abl
     # host link: pinned 1 GiB copies, best of 5
     h = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
     dbuf = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")

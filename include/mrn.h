@@ -252,8 +252,17 @@ typedef struct mrn_transfer_opts {
   size_t chunk_bytes; /* source bytes per chunk (0: 4 MiB); rounded to records
                          (and to whole blocks for AoSoA)                      */
   int32_t n_slots;    /* staging slots in flight (0: 4, max 16)               */
-  int32_t reserved;
+  int32_t flags;      /* MRN_TRANSFER_* bits (0: chunked staging)             */
 } mrn_transfer_opts;
+
+/* Zero-copy: no staging; the conversion kernel reads (host -> device) or
+ * writes (device -> host) the pinned host buffers directly over the host
+ * link, through their mapped device addresses.  Needs MRN_MEM_HOST_PINNED
+ * memory that the driver maps (cudaHostGetDevicePointer; otherwise
+ * MRN_EUNSUPPORTED); jagged schemas return MRN_EUNSUPPORTED.  An
+ * alternative to the chunked pipeline for the paper's memcopy with extra
+ * arguments (Sec. VI-A). */
+#define MRN_TRANSFER_ZERO_COPY 1
 
 /* Converts between a host view (MRN_MEM_HOST or MRN_MEM_HOST_PINNED) and a
  * device view, in either direction (the analogue of a copy between
@@ -268,7 +277,9 @@ typedef struct mrn_transfer_opts {
  * it.  Each device has one pipeline per direction: calls in the same
  * direction run one after another, a host->device and a device->host call
  * issued on different streams overlap (both directions of the host link).
- * Pageable host memory works but serialises the copies. */
+ * Pageable host memory works but serialises the copies.  With
+ * MRN_TRANSFER_ZERO_COPY in opts->flags the kernel moves the data over the
+ * host link itself (see above), on `stream`. */
 int mrn_transfer_convert(const mrn_view* src, const mrn_view* dst,
                          const mrn_transfer_opts* opts, void* stream);
 

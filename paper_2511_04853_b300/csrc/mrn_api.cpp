@@ -373,6 +373,19 @@ int build_jagged_plan(const mrn_view& src, const mrn_view& dst, JagPlan* jp) {
   return MRN_OK;
 }
 
+// A non-jagged conversion on the direct kernel only (plain loads and stores,
+// no bulk copies), for views in mapped host memory.
+int convert_direct(const mrn_view& src, const mrn_view& dst, void* stream) {
+  ConvPlan p;
+  int rc = build_plan(src, dst, &p);
+  if (rc) return rc;
+  LaunchShape sh;
+  sh.generic = 1;
+  if ((rc = launch_convert(p, stream, &sh))) return rc;
+  GapPlan g;
+  gap_plan(src.schema, dst, &g);
+  return g.ngaps ? launch_zero_gaps(g, stream) : MRN_OK;
+}
 }  // namespace mrn
 
 using namespace mrn;

@@ -61,6 +61,9 @@ int build_plan(const mrn_view& src, const mrn_view& dst, ConvPlan* p);
 // Recomputes the shared-memory tile geometry of a plan for stages of
 // `stage_bytes` (tg.tma = 0 when the plan cannot be staged).
 void plan_tiles(const mrn_schema* s, ConvPlan* p, uint32_t stage_bytes);
+// A validated non-jagged pair converted by the direct kernel only (plain
+// loads and stores: mapped host memory on one side).
+int convert_direct(const mrn_view& src, const mrn_view& dst, void* stream);
 // Builds the plan of a validated jagged view pair.
 int build_jagged_plan(const mrn_view& src, const mrn_view& dst, JagPlan* jp);
 // The children of a jagged SoA -> AoS plan as a plain conversion of the

@@ -356,6 +356,36 @@ int TransferEngine::run_chunked(const mrn_view& src, const mrn_view& dst, uint64
 }
 
 namespace {
+// The same view with its host buffers replaced by their mapped device
+// addresses (pinned memory the driver maps into the device's address
+// space); `cols` holds the mapped SoA column pointers.
+int map_host_view(const mrn_view& v, int dev, mrn_view* out, std::vector<void*>* cols) {
+  auto map = [](void* h, void** d) -> int {
+    if (!h) {
+      *d = nullptr;
+      return MRN_OK;
+    }
+    if (cudaHostGetDevicePointer(d, h, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return MRN_EUNSUPPORTED;
+    }
+    return MRN_OK;
+  };
+  *out = v;
+  out->mem = MRN_MEM_DEVICE;
+  out->device = dev;
+  int rc = map(v.base, &out->base);
+  if (rc) return rc;
+  if (v.columns) {
+    const size_t nc = v.schema->cols.size();
+    cols->assign(nc, nullptr);
+    for (size_t c = 0; c < nc; ++c)
+      if ((rc = map(v.columns[c], &(*cols)[c]))) return rc;
+    out->columns = cols->data();
+  }
+  return MRN_OK;
+}
+
 // The default pipelines: one per device and direction, so that a
 // host -> device and a device -> host transfer (issued on different
 // streams) use both directions of the host link at once.
@@ -379,6 +409,18 @@ extern "C" int mrn_transfer_convert(const mrn_view* src, const mrn_view* dst, co
   const bool d2h = src->mem == MRN_MEM_DEVICE && src->device == dev && is_host(*dst);
   if (!h2d && !d2h) return MRN_EINVAL;
   if (jag && dst->layout.kind == MRN_AOS && dst->n_children < src->n_children) return MRN_ESIZE;
+  if (opts && (opts->flags & MRN_TRANSFER_ZERO_COPY)) {
+    if (jag) return MRN_EUNSUPPORTED;
+    const mrn_view& hv = h2d ? *src : *dst;
+    if (hv.mem != MRN_MEM_HOST_PINNED) return MRN_EINVAL;
+    if (same_layout(*src, *dst) || (src->layout.kind == MRN_AOS && dst->layout.kind == MRN_AOS))
+      return MRN_EINVAL;  // nothing to convert: a plain copy
+    std::vector<void*> cols;
+    mrn_view mapped;
+    if ((rc = map_host_view(hv, dev, &mapped, &cols))) return rc;
+    if (!h2d) zero_host_soa_gaps(*dst);
+    return convert_direct(h2d ? mapped : *src, h2d ? *dst : mapped, stream);
+  }
   if (dev >= kMaxDevices) return MRN_EUNSUPPORTED;
   const int dir = h2d ? 0 : 1;
   std::lock_guard<std::mutex> lk(g_engine_mu[dev][dir]);

@@ -47,7 +47,7 @@ class ColumnInfo(ctypes.Structure):
 
 
 class TransferOpts(ctypes.Structure):
-    _fields_ = [("chunk_bytes", sz), ("n_slots", i32), ("reserved", i32)]
+    _fields_ = [("chunk_bytes", sz), ("n_slots", i32), ("flags", i32)]
 
 
 class Job(ctypes.Structure):
@@ -321,8 +321,11 @@ def debug_set(key, value):
     check(lib().mrn_debug_set(key, value))
 
 
-def transfer_convert(src, dst, chunk_bytes=0, n_slots=0, stream=None):
-    opts = TransferOpts(chunk_bytes, n_slots, 0)
+TRANSFER_ZERO_COPY = 1
+
+
+def transfer_convert(src, dst, chunk_bytes=0, n_slots=0, stream=None, zero_copy=False):
+    opts = TransferOpts(chunk_bytes, n_slots, TRANSFER_ZERO_COPY if zero_copy else 0)
     check(lib().mrn_transfer_convert(src.ref, dst.ref, ctypes.byref(opts), _stream(stream)),
           "mrn_transfer_convert")
 

@@ -161,3 +161,54 @@ def test_both_directions_on_several_streams():
         want_soa = oracle.convert(o, o_aos, "soa").base
         assert np.array_equal(host(d_soa, want_soa.size), want_soa)
         assert np.array_equal(h_out.numpy()[: n * 24], o_aos.base[: n * 24])
+
+
+@pytest.mark.parametrize("pair", [(("aos", 0), ("soa", 0)), (("aos", 0), ("aosoa", 32)), (("soa", 0), ("aos", 0)),
+                                  (("aosoa", 128), ("soa", 0))], ids=lambda p: "%s%d-%s%d" % (p[0] + p[1]))
+@pytest.mark.parametrize("name,n", [("cells", 70001), ("points", 10000), ("sensor", 999)])
+def test_zero_copy_both_directions(pair, name, n):
+    """Zero-copy transfer-and-convert: the kernel reads (host -> device) or
+    writes (device -> host) the pinned host buffer directly; bytes equal the
+    oracle's, alignment holes and AoSoA tail slots included."""
+    (sk, sb), (dk, db) = pair
+    desc = datagen.WORKLOAD_SCHEMAS.get(name) or getattr(datagen, name.upper())
+    s, o = mrn.Schema(desc), oracle.Schema(desc)
+    if name in datagen.WORKLOAD_SCHEMAS:
+        d = datagen.workload(name, n, 31)
+    else:
+        d = datagen.random_columns(desc, n, 31)
+    o_src = oracle.pack(o, d, sk, sb)
+    want = oracle.convert(o, o_src, dk, db).base
+    nb = s.required_bytes(dk, n, 0, db)
+    # host -> device
+    dst = garbage(nb)
+    mrn.transfer_convert(mrn.View(s, sk, n, block=sb, base=host_side(o_src.base), mem="pinned"),
+                         mrn.View(s, dk, n, block=db, base=dst), zero_copy=True)
+    assert mrn.sync() == mrn.OK
+    assert np.array_equal(host(dst, want.size), want)
+    # device -> host
+    h = pinned(nb)
+    mrn.transfer_convert(mrn.View(s, sk, n, block=sb, base=dev(o_src.base)),
+                         mrn.View(s, dk, n, block=db, base=h, mem="pinned"), zero_copy=True)
+    torch().cuda.synchronize()
+    assert mrn.sync() == mrn.OK
+    assert np.array_equal(h.numpy()[: want.size], want)
+
+
+def test_zero_copy_rejections():
+    s = mrn.Schema(datagen.TRACKS)
+    buf = garbage(1 << 12)
+    hp = pinned(1 << 12)
+    src = mrn.View(s, "aos", 10, base=hp, child_pool=hp, m=1, mem="pinned")
+    assert lib_status(src, mrn.View(s, "soa", 10, base=buf, m=1)) == mrn.EUNSUPPORTED
+    c = mrn.Schema(datagen.CELLS)
+    pageable = torch().zeros(1 << 12, dtype=torch().uint8)
+    assert lib_status(mrn.View(c, "aos", 10, base=pageable, mem="host"),
+                      mrn.View(c, "soa", 10, base=buf)) == mrn.EINVAL
+
+
+def lib_status(src, dst):
+    import ctypes
+    from paper_2511_04853_b300 import mrn as binding
+    opts = binding.TransferOpts(0, 0, binding.TRANSFER_ZERO_COPY)
+    return binding.lib().mrn_transfer_convert(src.ref, dst.ref, ctypes.byref(opts), None)
