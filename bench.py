@@ -356,6 +356,7 @@ def run_mixed(mrn, torch, stream, peak, args):
             tuned["%s_aos_to_%s%s" % (name, dk, db or "")] = {k: r[k] for k in ("staged", "threads",
                                                                                "tile_records", "ctas_per_sm")}
     tb = mrn.Batch(pairs, use_graph=True)
+    launch_shape = tb.tune()
     for o in outs:
         o.fill_(0xA5)
     ms_tuned = timed(tb.launch, 5)
@@ -372,7 +373,7 @@ def run_mixed(mrn, torch, stream, peak, args):
                 "gbps_autotuned": round(alg / (ms_tuned * 1e-3) / 1e9, 1),
                 "per_call_ms": round(ms_per, 3), "per_call_launches": len(plan),
                 "speedup_vs_per_call": round(ms_per / best, 3),
-                "autotuned_shapes": tuned})
+                "autotuned_shapes": tuned, "autotuned_launch": launch_shape})
     del want, outs, pairs
     torch.cuda.empty_cache()
     return res
@@ -447,6 +448,7 @@ def run_mine(args, rank, world):
     s = mrn.Schema(datagen.CELLS)
     colls = make_inputs(mrn, torch, s, args.batch)
     batch = mrn.Batch(pairs_for(mrn, s, colls), use_graph=True)
+    launch_shape = batch.tune()  # the batch autotuner picks the launch shape (setup, not timed)
     step_bytes = args.batch * bytes_per_collection()
 
     def barrier():
@@ -549,6 +551,7 @@ def run_mine(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic (seeded generator; distributions of the calorimeter-cell workload)",
             "config": workload_config(args.batch),
+            "batch_launch": dict(launch_shape, chosen_by="mrn_batch_tune (chunk x CTAs per SM, timed on the batch)"),
             "e2e": e2e,
             "gpu_launches": args.steps,
             "roofline": roof,

@@ -308,6 +308,19 @@ int mrn_batch_launch_per_job(mrn_batch* b, void* stream);
 int mrn_batch_update(mrn_batch* b, size_t j, const mrn_view* src, const mrn_view* dst);
 void mrn_batch_destroy(mrn_batch* b);
 
+typedef struct mrn_batch_tune_result {
+  uint32_t max_chunk;   /* consecutive tiles a CTA takes at once (1..16)     */
+  uint32_t ctas_per_sm; /* resident CTAs per SM of the grid (0: occupancy)   */
+  double ms;            /* device time of one launch with the winner         */
+  double default_ms;    /* device time of one launch with the defaults       */
+} mrn_batch_tune_result;
+
+/* Autotunes the launch shape of this batch on its own jobs: times launches
+ * on `stream` for every chunk size in {1, 2, 4, 8, 16} and CTAs per SM in
+ * {occupancy, 2}, keeps the fastest (the graph is re-captured) and reports
+ * it.  The jobs' destinations are written by the trial launches. */
+int mrn_batch_tune(mrn_batch* b, void* stream, mrn_batch_tune_result* out);
+
 typedef struct mrn_tune_result {
   uint32_t threads;       /* threads per CTA                                  */
   uint32_t ctas_per_sm;   /* resident CTAs per SM of the grid (0: occupancy)  */

@@ -295,6 +295,70 @@ int mrn_batch_update(mrn_batch* b, size_t j, const mrn_view* src, const mrn_view
   return MRN_OK;
 }
 
+int mrn_batch_tune(mrn_batch* b, void* stream, mrn_batch_tune_result* out) {
+  if (!b || !out) return MRN_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return MRN_ECUDA;
+  }
+  // best of three launches after one untimed
+  auto time_it = [&](float* ms) -> int {
+    int rc = enqueue(b, s);
+    if (rc) return rc;
+    float best = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+      cudaEventRecord(e0, s);
+      if ((rc = enqueue(b, s))) return rc;
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return MRN_ECUDA;
+      float t = 0;
+      cudaEventElapsedTime(&t, e0, e1);
+      best = std::min(best, t);
+    }
+    *ms = best;
+    return MRN_OK;
+  };
+  const uint32_t def_chunk = b->max_chunk, def_cps = b->ctas_per_sm;
+  float def_ms = 0, best_ms = 0;
+  int rc = time_it(&def_ms);
+  uint32_t best_chunk = def_chunk, best_cps = def_cps;
+  best_ms = def_ms;
+  for (uint32_t cps : {0u, 2u})
+    for (uint32_t chunk : {1u, 2u, 4u, 8u, 16u}) {
+      if (rc) break;
+      b->max_chunk = chunk;
+      b->ctas_per_sm = cps;
+      float t = 0;
+      rc = time_it(&t);
+      if (!rc && t < best_ms) {
+        best_ms = t;
+        best_chunk = chunk;
+        best_cps = cps;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->max_chunk = best_chunk;
+  b->ctas_per_sm = best_cps;
+  if (rc) return rc;
+  if (b->exec) {  // the graph holds the launch shape: capture it again
+    cudaGraphExecDestroy(b->exec);
+    cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    if ((rc = capture(b))) return rc;
+  }
+  out->max_chunk = best_chunk;
+  out->ctas_per_sm = best_cps;
+  out->ms = best_ms;
+  out->default_ms = def_ms;
+  return MRN_OK;
+}
+
 void mrn_batch_destroy(mrn_batch* b) {
   if (!b) return;
   cudaDeviceSynchronize();

@@ -681,7 +681,7 @@ constexpr uint32_t kBNS = 3;      // source stages
 constexpr uint32_t kBND = 2;      // destination buffers
 constexpr uint32_t kRing = 8;     // decided tiles in flight
 constexpr uint32_t kSQ = 8;       // staged tiles between loader and storer
-constexpr uint64_t kChunk = 8;    // most consecutive tiles per chunk
+constexpr uint64_t kChunk = 16;   // most consecutive tiles per chunk
 constexpr uint32_t kBThreads = 320;
 
 struct TileSlot {
@@ -1239,10 +1239,10 @@ void allow_batch_smem(const void* fn) {
   done.emplace_back(fn, dev);
 }
 
-// Tiles per chunk: up to kChunk (fewer job switches per CTA), but small
-// enough that every CTA of the grid gets about four chunks.
+// Tiles per chunk by default: up to 8 (fewer job switches per CTA), but
+// small enough that every CTA of the grid gets about four chunks.
 uint32_t chunk_for(uint64_t tiles, uint64_t ctas) {
-  return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(kChunk, tiles / (4 * std::max<uint64_t>(1, ctas))));
+  return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(8, tiles / (4 * std::max<uint64_t>(1, ctas))));
 }
 
 int launch_convert(const ConvPlan& p, void* stream, const LaunchShape* shape) {
@@ -1401,7 +1401,11 @@ int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, uns
   const int occ = batch_occupancy();
   const int per_sm = ctas_per_sm ? std::min((int)ctas_per_sm, occ) : occ;
   const uint64_t cap = (uint64_t)device_sm_count() * (uint64_t)per_sm;
-  const uint32_t chunk = std::min<uint32_t>(std::max(1u, max_chunk), chunk_for(total_tiles, cap));
+  // max_chunk caps the default choice; a tuned value above 8 is taken as is
+  // (up to kChunk) while every CTA still gets a chunk
+  uint32_t chunk = std::min<uint32_t>(std::max(1u, max_chunk), chunk_for(total_tiles, cap));
+  if (max_chunk > 8)
+    chunk = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>({(uint64_t)max_chunk, kChunk, total_tiles / cap}));
   const uint64_t chunks = (total_tiles + chunk - 1) / chunk;
   const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(cap, chunks));
   k_batch<<<grid, kBThreads, kBatchSmem, static_cast<cudaStream_t>(stream)>>>(jobs, first_tile, njobs,

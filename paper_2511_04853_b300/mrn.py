@@ -60,6 +60,11 @@ class TuneResult(ctypes.Structure):
                 ("default_gbps", ctypes.c_double)]
 
 
+class BatchTuneResult(ctypes.Structure):
+    _fields_ = [("max_chunk", u32), ("ctas_per_sm", u32), ("ms", ctypes.c_double),
+                ("default_ms", ctypes.c_double)]
+
+
 class ServerOpts(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", sz), ("max_slots", i32), ("reserved", i32),
                 ("chunk_bytes", sz)]
@@ -106,6 +111,7 @@ SIGNATURES = [
     ("mrn_batch_launch_per_job", ctypes.c_int, [vp, vp]),
     ("mrn_batch_update", ctypes.c_int, [vp, sz, ctypes.POINTER(ViewStruct), ctypes.POINTER(ViewStruct)]),
     ("mrn_batch_destroy", None, [vp]),
+    ("mrn_batch_tune", ctypes.c_int, [vp, vp, ctypes.POINTER(BatchTuneResult)]),
     ("mrn_autotune", ctypes.c_int, [vp, Layout, Layout, u64, ctypes.POINTER(TuneResult)]),
     ("mrn_autotune_clear", ctypes.c_int, []),
     ("mrn_server_create", ctypes.c_int, [ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]),
@@ -349,6 +355,13 @@ class Batch:
 
     def launch_per_job(self, stream=None):
         check(lib().mrn_batch_launch_per_job(self._h, _stream(stream)), "per-job")
+
+    def tune(self, stream=None):
+        """Autotunes this batch's launch shape on its own jobs (the trial
+        launches write the destinations)."""
+        r = BatchTuneResult()
+        check(lib().mrn_batch_tune(self._h, _stream(stream), ctypes.byref(r)), "mrn_batch_tune")
+        return {"max_chunk": r.max_chunk, "ctas_per_sm": r.ctas_per_sm, "ms": r.ms, "default_ms": r.default_ms}
 
     def update(self, j, src, dst):
         self._pairs[j] = (src, dst)

@@ -201,3 +201,21 @@ def test_partial_tiles_in_one_batch():
     assert mrn.sync() == mrn.OK
     for k, (dst, want) in enumerate(checks):
         assert np.array_equal(host(dst.tensors[0], want.size), want), "job %d" % k
+
+
+def test_batch_tune_keeps_results_exact():
+    """The batch autotuner times launch shapes on the batch's own jobs; the
+    tuned batch (re-captured graph) still gives the oracle's bytes."""
+    jobs = make_jobs(11, 24)
+    b = mrn.Batch([(s, d) for s, d, _, _ in jobs], use_graph=True)
+    r = b.tune()
+    assert r["max_chunk"] in (1, 2, 4, 8, 16) and r["ctas_per_sm"] in (0, 2)
+    assert 0 < r["ms"] <= r["default_ms"]
+    for _, d, _, _ in jobs:
+        d.tensors[0].fill_(0xA5)
+        if d.tensors[1] is not None:
+            d.tensors[1].fill_(0xA5)
+    b.launch()
+    assert mrn.sync() == mrn.OK
+    for i, (s, d, want, name) in enumerate(jobs):
+        assert np.array_equal(result(d, want, name), want), "job %d (%s)" % (i, name)
