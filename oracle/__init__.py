@@ -57,6 +57,7 @@ def lib():
                 ("orc_aosoa_col_start", u64, [vp, u32, i32]),
                 ("orc_aosoa_block_bytes", u64, [vp, u32]),
                 ("orc_soa_region_start", u64, [vp, u64, u64, i32]),
+                ("orc_fm_region_start", u64, [vp, i32, u32, u64, u64, i32]),
                 ("orc_soa_bytes", u64, [vp, u64, u64]),
                 ("orc_base_bytes", u64, [vp, i32, u32, u64, u64])]:
             f = getattr(L, name)
@@ -128,6 +129,12 @@ class Schema:
 
     def soa_region_start(self, n, m, r):
         return lib().orc_soa_region_start(self._h, n, m, r)
+
+    def fm_region_start(self, kind, block, n, m, r):
+        """Start of region r of a single-block field-major side (SoA: data
+        columns, offsets, child columns; jagged AoSoA(B): blocks, offsets,
+        child columns)."""
+        return lib().orc_fm_region_start(self._h, KIND.get(kind, kind), block, n, m, r)
 
     def base_bytes(self, kind, block, n, m=0):
         return lib().orc_base_bytes(self._h, KIND.get(kind, kind), block, n, m)
@@ -275,16 +282,19 @@ def shuffle_pool(schema, side, order, gap=0):
 
 
 def region(schema, side, r):
-    """Bytes of region ``r`` (data column, offsets, child column) of a
-    single-block SoA side."""
+    """Bytes of region ``r`` of a single-block field-major side: SoA data
+    column / offsets / child column, or (jagged AoSoA) blocks / offsets /
+    child column."""
     n, m = side.n, side.m
-    start = schema.soa_region_start(n, m, r)
-    if r < schema.ncols:
-        size = n * schema.col_size[r]
-    elif schema.has_jagged and r == schema.ncols:
+    P = 1 if side.kind == AOSOA else schema.ncols
+    start = schema.fm_region_start(side.kind, side.block, n, m, r)
+    if r < P:
+        size = ((n + side.block - 1) // side.block * schema.aosoa_block_bytes(side.block)
+                if side.kind == AOSOA else n * schema.col_size[r])
+    elif schema.has_jagged and r == P:
         size = (n + 1) * schema.off_size
     else:
-        size = m * schema.child.col_size[r - schema.ncols - 1]
+        size = m * schema.child.col_size[r - P - 1]
     return side.base[start:start + size]
 
 

@@ -27,12 +27,15 @@
  *    each) follow.
  *  - AoSoA(B) ("allocating memory in blocks of a given size", Sec. IV):
  *    each block is the C struct { T_0 c0[B]; T_1 c1[B]; ... } of the
- *    flattened columns.
+ *    flattened columns; for a jagged schema the blocks are followed, in the
+ *    same buffer, by the offsets column and the child columns (each region
+ *    128-byte aligned, as in the single-block SoA).
  *  - Every destination byte that no property writes is 0.
  *
  * Parity unpinned: the 128-byte SoA column alignment, the AoSoA in-block
- * arrangement and the AoS jagged descriptor are readings (the paper fixes no
- * bytes for them); they are checked by round trips and special cases only.
+ * arrangement, the regions of a jagged AoSoA side and the AoS jagged
+ * descriptor are readings (the paper fixes no bytes for them); they are
+ * checked by round trips and special cases only.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -218,39 +221,56 @@ uint64_t orc_aosoa_block_bytes(const orc_schema* s, uint32_t B) {
   return align_up(end, al);
 }
 
-/* SoA single block: region r of the block, in order: the data columns
- * 0..ncols-1, then (jagged) the offsets column, then the child columns.
- * Each region starts at a multiple of 128 bytes. */
-static uint64_t soa_region_bytes(const orc_schema* s, uint64_t n, uint64_t m, int r) {
-  if (r < s->ncols) return n * s->col_size[r];
-  if (r == s->ncols) return (n + 1) * s->off_size;
-  return m * s->child->col_size[r - s->ncols - 1];
+/* Single-block field-major sides.  SoA: region r of the block, in order:
+ * the data columns 0..ncols-1, then (jagged) the offsets column, then the
+ * child columns.  AoSoA(B) of a jagged schema: the parent blocks, then the
+ * offsets column, then the child columns.  Each region starts at a
+ * multiple of 128 bytes. */
+static int parent_regions(const orc_schema* s, int kind) { return kind == ORC_AOSOA ? 1 : s->ncols; }
+
+static uint64_t fm_region_bytes(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, int r) {
+  int P = parent_regions(s, kind);
+  if (r < P) {
+    if (kind == ORC_AOSOA) return (B ? (n + B - 1) / B : 0) * orc_aosoa_block_bytes(s, B);
+    return n * s->col_size[r];
+  }
+  if (r == P) return (n + 1) * s->off_size;
+  return m * s->child->col_size[r - P - 1];
 }
 
-static int soa_nregions(const orc_schema* s) {
-  return s->ncols + (s->has_jagged ? 1 + s->child->ncols : 0);
+static int fm_nregions(const orc_schema* s, int kind) {
+  return parent_regions(s, kind) + (s->has_jagged ? 1 + s->child->ncols : 0);
 }
 
-uint64_t orc_soa_region_start(const orc_schema* s, uint64_t n, uint64_t m, int r) {
+uint64_t orc_fm_region_start(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, int r) {
   uint64_t start = 0, end = 0;
   for (int k = 0; k <= r; k++) {
     start = align_up(end, 128);
-    end = start + soa_region_bytes(s, n, m, k);
+    end = start + fm_region_bytes(s, kind, B, n, m, k);
   }
   return start;
 }
 
-uint64_t orc_soa_bytes(const orc_schema* s, uint64_t n, uint64_t m) {
-  int nr = soa_nregions(s);
-  uint64_t end = orc_soa_region_start(s, n, m, nr - 1) + soa_region_bytes(s, n, m, nr - 1);
+uint64_t orc_soa_region_start(const orc_schema* s, uint64_t n, uint64_t m, int r) {
+  return orc_fm_region_start(s, ORC_SOA, 0, n, m, r);
+}
+
+static uint64_t fm_bytes(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m) {
+  int nr = fm_nregions(s, kind);
+  uint64_t end = orc_fm_region_start(s, kind, B, n, m, nr - 1) + fm_region_bytes(s, kind, B, n, m, nr - 1);
   return align_up(end, 128);
 }
+
+uint64_t orc_soa_bytes(const orc_schema* s, uint64_t n, uint64_t m) { return fm_bytes(s, ORC_SOA, 0, n, m); }
 
 /* Bytes of the `base` buffer of a side. */
 uint64_t orc_base_bytes(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m) {
   if (kind == ORC_AOS) return n * s->stride;
   if (kind == ORC_SOA) return orc_soa_bytes(s, n, m);
-  if (kind == ORC_AOSOA) return (B ? (n + B - 1) / B : 0) * orc_aosoa_block_bytes(s, B);
+  if (kind == ORC_AOSOA) {
+    if (s->has_jagged) return fm_bytes(s, ORC_AOSOA, B, n, m);
+    return (B ? (n + B - 1) / B : 0) * orc_aosoa_block_bytes(s, B);
+  }
   return 0;
 }
 
@@ -270,12 +290,12 @@ static uint8_t* col_addr(const orc_schema* s, const orc_side* v, int c, uint64_t
 
 static uint8_t* offsets_ptr(const orc_schema* s, const orc_side* v) {
   if (v->offsets) return v->offsets;
-  return v->base + orc_soa_region_start(s, v->n, v->m, s->ncols);
+  return v->base + orc_fm_region_start(s, v->kind, v->block, v->n, v->m, parent_regions(s, v->kind));
 }
 
 static uint8_t* child_col_ptr(const orc_schema* s, const orc_side* v, int cc) {
   if (v->child_cols) return v->child_cols[cc];
-  return v->base + orc_soa_region_start(s, v->n, v->m, s->ncols + 1 + cc);
+  return v->base + orc_fm_region_start(s, v->kind, v->block, v->n, v->m, parent_regions(s, v->kind) + 1 + cc);
 }
 
 static uint64_t rd(const uint8_t* p, uint32_t size) {
@@ -304,7 +324,7 @@ static void zero_side(const orc_schema* s, const orc_side* d) {
     return;
   }
   memset(d->base, 0, orc_base_bytes(s, d->kind, d->block, d->n, d->m));
-  if (d->kind == ORC_SOA && s->has_jagged) {
+  if (d->kind != ORC_AOS && s->has_jagged) {
     if (d->offsets) memset(d->offsets, 0, (d->n + 1) * s->off_size);
     if (d->child_cols)
       for (int cc = 0; cc < s->child->ncols; cc++)
@@ -315,16 +335,18 @@ static void zero_side(const orc_schema* s, const orc_side* d) {
 }
 
 /* Converts one collection from `src` to `dst` (same schema, same N).
- * For a jagged schema only AoS <-> SoA is defined; *m_out receives the
- * number of child values written. */
+ * For a jagged schema the AoS side is converted to or from a field-major
+ * side (SoA or AoSoA(B)), or one field-major side to another; *m_out
+ * receives the number of child values written. */
 int orc_convert(const orc_schema* s, const orc_side* src, orc_side* dst, uint64_t* m_out) {
   if (!valid_side(src) || !valid_side(dst) || src->n != dst->n) return ORC_EINVAL;
   uint64_t n = src->n;
   if (m_out) *m_out = 0;
   if (s->has_jagged) {
-    int a2s = src->kind == ORC_AOS && dst->kind == ORC_SOA;
-    int s2a = src->kind == ORC_SOA && dst->kind == ORC_AOS;
-    if (!a2s && !s2a) return ORC_EINVAL;
+    int a2s = src->kind == ORC_AOS && dst->kind != ORC_AOS;
+    int s2a = src->kind != ORC_AOS && dst->kind == ORC_AOS;
+    int f2f = src->kind != ORC_AOS && dst->kind != ORC_AOS;
+    if (!a2s && !s2a && !f2f) return ORC_EINVAL;
     if (a2s) {
       /* Prefix sum of the sizes, checked against the offset type (Sec. V,
        * jagged vector property: the prefix type may be narrower than the
@@ -361,6 +383,15 @@ int orc_convert(const orc_schema* s, const orc_side* src, orc_side* dst, uint64_
 
   if (!s->has_jagged) return ORC_OK;
   const orc_schema* ch = s->child;
+  if (src->kind != ORC_AOS && dst->kind != ORC_AOS) {
+    /* Field-major to field-major: the offsets and the child values keep
+     * their order; only the parents change layout. */
+    memcpy(offsets_ptr(s, dst), offsets_ptr(s, src), (n + 1) * s->off_size);
+    for (int cc = 0; cc < ch->ncols; cc++)
+      memcpy(child_col_ptr(s, dst, cc), child_col_ptr(s, src, cc), src->m * ch->col_size[cc]);
+    if (m_out) *m_out = src->m;
+    return ORC_OK;
+  }
   if (src->kind == ORC_AOS) {
     uint8_t* off = offsets_ptr(s, dst);
     uint64_t run = 0;

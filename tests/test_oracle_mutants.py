@@ -26,6 +26,10 @@ MUTANTS = {
     "child_wrong_column": ("src->pool + (beg + k) * ch->stride + ch->col_aos_off[cc]",
                            "src->pool + (beg + k) * ch->stride + ch->col_aos_off[0]"),
     "aosoa_slot_swapped": ("(i % v->block) * sz;", "((v->block - 1 - i % v->block)) * sz;"),
+    "jagged_aosoa_regions_as_soa": ("static int parent_regions(const orc_schema* s, int kind) { return kind == ORC_AOSOA ? 1 : s->ncols; }",
+                                    "static int parent_regions(const orc_schema* s, int kind) { return s->ncols; }"),
+    "f2f_children_dropped": ("memcpy(child_col_ptr(s, dst, cc), child_col_ptr(s, src, cc), src->m * ch->col_size[cc]);",
+                             "(void)cc;"),
 }
 
 

@@ -324,3 +324,64 @@ def test_brute_force_small_schemas(desc):
         # no byte lost or duplicated: the multiset of data bytes is preserved
         got = np.concatenate([oracle.region(s, soa, c) for c in range(s.ncols)]) if n else np.zeros(0, np.uint8)
         assert sorted(got.tolist()) == sorted(raw[raw != 0].tolist())
+
+
+# ------------------------------------------------ jagged parents in AoSoA(B)
+
+@pytest.mark.parametrize("B", [1, 2, 4, 8, 32, 128])
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 7, 8, 9, 300])
+def test_jagged_aosoa_regions_and_round_trips(n, B):
+    """A jagged AoSoA(B) side is the AoSoA(B) blocks of the parent columns,
+    then the offsets and the child columns (each region 128-byte aligned).
+    Pinned by: the blocks equal the AoSoA(B) conversion of a schema of the
+    parent fields alone; the offsets equal the prefix sum of the lengths;
+    the child regions equal the SoA side's; AoS -> AoSoA(B) -> AoS, SoA ->
+    AoSoA(B) -> SoA and AoS -> AoSoA(B) -> SoA reproduce the direct
+    results byte for byte."""
+    s, d = _tracks(n, 12 + B, mean_len=2.0)
+    aos = oracle.pack(s, d, "aos")
+    soa = oracle.convert(s, aos, "soa", m=d["m"])
+    blk = oracle.convert(s, aos, "aosoa", B, m=d["m"])
+    assert blk.written == d["m"]
+    # region placement
+    for r in range(1 + 1 + 2):
+        assert s.fm_region_start("aosoa", B, n, d["m"], r) % 128 == 0
+    # blocks: the parent columns alone, as a non-jagged AoSoA(B)
+    parents = oracle.Schema([("pt", "f32", 1), ("eta", "f32", 1), ("label", "i32", 1)])
+    p_soa = oracle.Side("soa", n, 0, cols=[oracle.region(s, soa, c).copy() for c in range(3)],
+                        base=np.zeros(1, np.uint8))
+    p_blk = oracle.convert(parents, p_soa, "aosoa", B)
+    assert oracle.region(s, blk, 0).tobytes() == p_blk.base[: parents.base_bytes("aosoa", B, n)].tobytes()
+    # offsets and children as on the SoA side
+    for r in range(3):
+        assert oracle.region(s, blk, 1 + r).tobytes() == oracle.region(s, soa, s.ncols + r).tobytes()
+    off = oracle.region(s, blk, 1).view(np.uint32).astype(np.int64)
+    assert off.tolist() == np.concatenate([[0], np.cumsum(d["lengths"].astype(np.int64))]).tolist()
+    # round trips and paths through AoSoA(B)
+    back = oracle.convert(s, blk, "aos", m=d["m"])
+    assert back.base.tobytes() == aos.base.tobytes()
+    assert back.pool[: d["m"] * 8].tobytes() == aos.pool[: d["m"] * 8].tobytes()
+    assert oracle.convert(s, blk, "soa", m=d["m"]).base.tobytes() == soa.base.tobytes()
+    assert oracle.convert(s, soa, "aosoa", B, m=d["m"]).base.tobytes() == blk.base.tobytes()
+    other = 32 if B != 32 else 8
+    assert oracle.convert(s, oracle.convert(s, blk, "aosoa", other, m=d["m"]), "aosoa", B,
+                          m=d["m"]).base.tobytes() == blk.base.tobytes()
+
+
+def test_jagged_aosoa_tail_slots_and_gaps_are_zero():
+    """Every byte of a jagged AoSoA side that holds no value is zero: the
+    unused slots of the last block and the bytes between regions."""
+    n, B = 37, 32
+    s, d = _tracks(n, 5, raw=True)
+    aos = oracle.pack(s, d, "aos")
+    blk = oracle.convert(s, aos, "aosoa", B, m=d["m"])
+    mask = np.zeros(blk.base.size, bool)
+    for r in range(4):
+        st = s.fm_region_start("aosoa", B, n, d["m"], r)
+        mask[st: st + oracle.region(s, blk, r).size] = True
+    assert not blk.base[~mask].any()
+    blocks = oracle.region(s, blk, 0).reshape(2, -1)
+    for c in range(3):  # slots 37 - 32 = 5 .. 31 of the second block
+        start = s.aosoa_col_start(B, c)
+        col = blocks[1, start: start + B * 4].reshape(B, 4)
+        assert not col[n - B:].any()
