@@ -153,8 +153,13 @@ typedef enum mrn_memctx {
  *             offsets / M children.
  *   AoSoA(B): block b at base + b*block_bytes is the C struct
  *             { T_0 c0[B]; T_1 c1[B]; ... } of the flattened columns; record
- *             i is slot i%B of block i/B.  Jagged schemas are not supported
- *             in AoSoA (MRN_EUNSUPPORTED).
+ *             i is slot i%B of block i/B.  For a jagged schema the blocks
+ *             hold the parent columns and are followed, inside view.base,
+ *             by the offsets (N+1) and the child columns (M each), each
+ *             region starting at a multiple of 128 bytes (view.offsets /
+ *             view.child_columns may point elsewhere instead), as the
+ *             paper's size tags and global properties allow for any
+ *             layout (Sec. V, Sec. VI-B).
  * In every destination, bytes no property writes (AoS padding, alignment
  * holes, unused AoSoA slots of the last block) are written as zero. */
 typedef struct mrn_layout {
@@ -188,6 +193,11 @@ int mrn_child_pool_bytes(const mrn_schema* s, uint64_t m, size_t* out);
 /* Start of region r inside a single-block SoA of n records / m children:
  * r < n_columns: data column r; r == n_columns: offsets; then child columns. */
 int mrn_soa_region_offset(const mrn_schema* s, uint64_t n, uint64_t m, uint32_t r, size_t* out);
+/* Start of region r inside view.base for either field-major layout: SoA as
+ * mrn_soa_region_offset; jagged AoSoA(B): r == 0 the blocks, r == 1 the
+ * offsets, r >= 2 child column r - 2.  Other layouts: MRN_EINVAL. */
+int mrn_region_offset(const mrn_schema* s, mrn_layout layout, uint64_t n, uint64_t m, uint32_t r,
+                      size_t* out);
 /* AoSoA(B): bytes per block, and the start of column c inside a block. */
 int mrn_aosoa_block_bytes(const mrn_schema* s, uint32_t B, size_t* out);
 int mrn_aosoa_column_offset(const mrn_schema* s, uint32_t B, uint32_t c, size_t* out);
@@ -195,7 +205,10 @@ int mrn_aosoa_column_offset(const mrn_schema* s, uint32_t B, uint32_t c, size_t*
 /* --------------------------------------------------------------- convert */
 /* Converts src into dst, both MRN_MEM_DEVICE on the current device, same
  * schema and n_records.  Any pair of AoS / SoA / AoSoA(B) layouts for a
- * schema without a jagged property; AoS <-> SoA for a jagged schema:
+ * schema without a jagged property.  For a jagged schema, AoS to or from
+ * either field-major layout (SoA, AoSoA(B); "SoA" below means either), and
+ * one field-major layout to another (the parents change layout; offsets
+ * and child values are copied as they are, dst.n_children >= src's):
  *   AoS -> SoA: offsets = offset_base + exclusive prefix sum of the lengths
  *     (N+1 entries), child values gathered from child_pool[begin + k] in
  *     object order.  dst.n_children is the child capacity; children beyond it

@@ -42,18 +42,20 @@ int fm_side(const mrn_schema* s, const mrn_view& v, bool child, SidePlan* sp) {
   const mrn_schema* t = child ? s->child.get() : s;
   const uint32_t nc = (uint32_t)t->cols.size();
   std::memset(sp, 0, sizeof(*sp));
-  sp->kind = v.layout.kind;
+  sp->kind = child ? K_SOA : v.layout.kind;  // child values are columns in either layout
   sp->block_shift = MRN_NO_SHIFT;
-  if (v.layout.kind == MRN_SOA) {
+  if (v.layout.kind == MRN_SOA || child) {
     void* const* cols = child ? v.child_columns : v.columns;
+    const uint32_t P = parent_regions(s, v.layout.kind);
     for (uint32_t c = 0; c < nc; ++c) {
       char* p;
       if (cols) {
         p = static_cast<char*>(cols[c]);
       } else {
         if (!v.base) return MRN_EINVAL;
-        const uint32_t region = child ? (uint32_t)s->cols.size() + 1 + c : c;
-        p = static_cast<char*>(v.base) + soa_region_start(s, v.n_records, v.n_children, region);
+        const uint32_t region = child ? P + 1 + c : c;
+        p = static_cast<char*>(v.base) +
+            fm_region_start(s, v.layout.kind, v.layout.block, v.n_records, v.n_children, region);
       }
       if (!p && (child ? v.n_children : v.n_records) > 0) return MRN_EINVAL;
       if (reinterpret_cast<uintptr_t>(p) % t->cols[c].size) return MRN_EALIGN;
@@ -136,56 +138,88 @@ int level_plan(const mrn_schema* s, const mrn_view& src, const mrn_view& dst, bo
   return MRN_OK;
 }
 
-// Alignment holes of a single-block SoA or AoSoA destination.
-void gap_plan(const mrn_schema* s, const mrn_view& dst, GapPlan* g) {
-  std::memset(g, 0, sizeof(*g));
-  auto add = [&](uint64_t a, uint64_t b) {
-    if (b > a && g->ngaps < MRN_MAX_GAPS) {
-      g->off[g->ngaps] = a;
-      g->len[g->ngaps] = (uint32_t)(b - a);
-      g->ngaps++;
-    }
-  };
-  g->base = static_cast<char*>(dst.base);
-  if (dst.layout.kind == MRN_SOA) {
-    if (dst.columns || !dst.base) return;
-    const uint64_t n = dst.n_records, m = dst.n_children;
-    const uint32_t nc = (uint32_t)s->cols.size();
-    const uint32_t nr = nc + (s->has_jagged ? 1 + (uint32_t)s->child->cols.size() : 0);
-    if (s->has_jagged && (dst.offsets || dst.child_columns)) return;
-    uint64_t prev_end = 0;
-    for (uint32_t r = 0; r < nr; ++r) {
-      const uint64_t st = soa_region_start(s, n, m, r);
-      add(prev_end, st);
-      uint64_t bytes = r < nc ? n * s->cols[r].size
-                              : (r == nc ? (n + 1) * s->off_size : m * s->child->cols[r - nc - 1].size);
-      prev_end = st + bytes;
-    }
-    add(prev_end, soa_total_bytes(s, n, m));
-    g->nblocks = 1;
-    g->block_bytes = 0;
-  } else if (dst.layout.kind == MRN_AOSOA) {
+// Zero-fill plans of a destination (see gap_plans_of).
+int gap_plans(const mrn_schema* s, const mrn_view& dst, GapPlan g[2]) {
+  int np = 0;
+  if (dst.layout.kind == MRN_AOSOA && dst.base) {  // holes inside every block
+    GapPlan& h = g[np];
+    std::memset(&h, 0, sizeof(h));
     const uint32_t B = dst.layout.block;
     uint64_t prev_end = 0;
+    auto add = [&](uint64_t a, uint64_t b) {
+      if (b > a && h.ngaps < MRN_MAX_GAPS) {
+        h.off[h.ngaps] = a;
+        h.len[h.ngaps] = (uint32_t)(b - a);
+        h.ngaps++;
+      }
+    };
     for (uint32_t c = 0; c < s->cols.size(); ++c) {
       const uint64_t st = aosoa_col_start(s, B, c);
       add(prev_end, st);
       prev_end = st + (uint64_t)B * s->cols[c].size;
     }
     add(prev_end, aosoa_block_bytes(s, B));
-    g->block_bytes = aosoa_block_bytes(s, B);
-    g->nblocks = (dst.n_records + B - 1) / B;
+    h.base = static_cast<char*>(dst.base);
+    h.block_bytes = aosoa_block_bytes(s, B);
+    h.nblocks = (dst.n_records + B - 1) / B;
+    if (h.ngaps && h.nblocks) ++np;
   }
+  const bool fm = dst.layout.kind == MRN_SOA || (dst.layout.kind == MRN_AOSOA && s->has_jagged);
+  if (fm && fm_single_block(dst)) {  // bytes between the regions of one block
+    GapPlan& h = g[np];
+    std::memset(&h, 0, sizeof(h));
+    const int kind = dst.layout.kind;
+    const uint32_t B = dst.layout.block;
+    const uint64_t n = dst.n_records, m = dst.n_children;
+    uint64_t prev_end = 0;
+    auto add = [&](uint64_t a, uint64_t b) {
+      if (b > a && h.ngaps < MRN_MAX_GAPS) {
+        h.off[h.ngaps] = a;
+        h.len[h.ngaps] = (uint32_t)(b - a);
+        h.ngaps++;
+      }
+    };
+    for (uint32_t r = 0; r < fm_region_count(s, kind); ++r) {
+      const uint64_t st = fm_region_start(s, kind, B, n, m, r);
+      add(prev_end, st);
+      prev_end = st + fm_region_bytes(s, kind, B, n, m, r);
+    }
+    add(prev_end, fm_total_bytes(s, kind, B, n, m));
+    h.base = static_cast<char*>(dst.base);
+    h.nblocks = 1;
+    h.block_bytes = 0;
+    if (h.ngaps) ++np;
+  }
+  return np;
 }
 
 }  // namespace
 
-void gap_plan_of(const mrn_view& dst, GapPlan* g) { gap_plan(dst.schema, dst, g); }
+bool fm_single_block(const mrn_view& v) {
+  if (!v.base) return false;
+  if (v.layout.kind == MRN_SOA && v.columns) return false;
+  if (v.schema->has_jagged && (v.offsets || v.child_columns)) return false;
+  return true;
+}
+
+char* fm_offsets(const mrn_view& v) {
+  if (v.offsets) return static_cast<char*>(v.offsets);
+  if (!v.base) return nullptr;
+  const mrn_schema* s = v.schema;
+  return static_cast<char*>(v.base) + fm_region_start(s, v.layout.kind, v.layout.block, v.n_records,
+                                                      v.n_children, parent_regions(s, v.layout.kind));
+}
+
+int gap_plans_of(const mrn_view& dst, GapPlan g[2]) { return gap_plans(dst.schema, dst, g); }
 
 int zero_dst_gaps(const mrn_view& dst, void* stream) {
-  GapPlan g;
-  gap_plan(dst.schema, dst, &g);
-  return g.ngaps ? launch_zero_gaps(g, stream) : MRN_OK;
+  GapPlan g[2];
+  const int np = gap_plans(dst.schema, dst, g);
+  for (int i = 0; i < np; ++i) {
+    const int rc = launch_zero_gaps(g[i], stream);
+    if (rc) return rc;
+  }
+  return MRN_OK;
 }
 
 int validate_pair(const mrn_view* src, const mrn_view* dst, bool need_device, bool* is_jagged) {
@@ -208,8 +242,10 @@ int validate_pair(const mrn_view* src, const mrn_view* dst, bool need_device, bo
   if (s->cols.size() > MRN_MAX_COLS) return MRN_EUNSUPPORTED;
   if (s->has_jagged) {
     if (s->child->cols.size() > MRN_MAX_COLS) return MRN_EUNSUPPORTED;
-    if (src->layout.kind == MRN_AOSOA || dst->layout.kind == MRN_AOSOA) return MRN_EUNSUPPORTED;
-    if (src->layout.kind == dst->layout.kind) return MRN_EUNSUPPORTED;
+    // nothing to convert between equal layouts
+    if (src->layout.kind == dst->layout.kind &&
+        (src->layout.kind != MRN_AOSOA || src->layout.block == dst->layout.block))
+      return MRN_EUNSUPPORTED;
   }
   return MRN_OK;
 }
@@ -350,12 +386,8 @@ int build_jagged_plan(const mrn_view& src, const mrn_view& dst, JagPlan* jp) {
   if (rc) return rc;
   jp->off_size = s->off_size;
   jp->len_off = s->len_off;
-  char* offs = static_cast<char*>(soa.offsets);
-  if (!offs) {
-    if (!soa.base) return MRN_EINVAL;
-    offs = static_cast<char*>(soa.base) + soa_region_start(s, soa.n_records, soa.n_children,
-                                                           (uint32_t)s->cols.size());
-  }
+  char* offs = fm_offsets(soa);
+  if (!offs) return MRN_EINVAL;
   if (reinterpret_cast<uintptr_t>(offs) % s->off_size) return MRN_EALIGN;
   jp->offsets = offs;
   jp->skip_publish_tile = g_skip_publish_tile.load();
@@ -373,6 +405,32 @@ int build_jagged_plan(const mrn_view& src, const mrn_view& dst, JagPlan* jp) {
   return MRN_OK;
 }
 
+// A jagged collection from one field-major layout to another: the parents
+// change layout (a plain conversion of the parent columns); the offsets
+// and the child values keep their order and are copied as they are.
+int convert_jagged_fm(const mrn_view& src, const mrn_view& dst, void* stream) {
+  const mrn_schema* s = src.schema;
+  if (dst.n_children < src.n_children) return MRN_ESIZE;
+  ConvPlan p;
+  int rc = build_plan(src, dst, &p);
+  if (rc) return rc;
+  if ((rc = launch_convert(p, stream, nullptr))) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint64_t n = src.n_records, m = src.n_children;
+  char* so = fm_offsets(src);
+  char* dof = fm_offsets(dst);
+  if (!so || !dof) return MRN_EINVAL;
+  if (cudaMemcpyAsync(dof, so, (n + 1) * s->off_size, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return MRN_ECUDA;
+  SidePlan a, b;
+  if ((rc = fm_side(s, src, true, &a)) || (rc = fm_side(s, dst, true, &b))) return rc;
+  for (uint32_t c = 0; c < s->child->cols.size() && m; ++c)
+    if (cudaMemcpyAsync(b.col[c], a.col[c], m * s->child->cols[c].size, cudaMemcpyDeviceToDevice, st) !=
+        cudaSuccess)
+      return MRN_ECUDA;
+  return zero_dst_gaps(dst, stream);
+}
+
 // A non-jagged conversion on the direct kernel only (plain loads and stores,
 // no bulk copies), for views in mapped host memory.
 int convert_direct(const mrn_view& src, const mrn_view& dst, void* stream) {
@@ -382,9 +440,7 @@ int convert_direct(const mrn_view& src, const mrn_view& dst, void* stream) {
   LaunchShape sh;
   sh.generic = 1;
   if ((rc = launch_convert(p, stream, &sh))) return rc;
-  GapPlan g;
-  gap_plan(src.schema, dst, &g);
-  return g.ngaps ? launch_zero_gaps(g, stream) : MRN_OK;
+  return zero_dst_gaps(dst, stream);
 }
 }  // namespace mrn
 
@@ -416,6 +472,8 @@ int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
   int rc = validate_pair(src, dst, true, &jag);
   if (rc) return rc;
   const mrn_schema* s = src->schema;
+  if (jag && src->layout.kind != MRN_AOS && dst->layout.kind != MRN_AOS)
+    return convert_jagged_fm(*src, *dst, stream);
   if (jag) {
     JagPlan jp;
     if ((rc = build_jagged_plan(*src, *dst, &jp))) return rc;
@@ -423,7 +481,7 @@ int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
       cudaStream_t st = static_cast<cudaStream_t>(stream);
       void* scratch = nullptr;
       if (src->n_records > 0) {
-        if (cudaMallocAsync(&scratch, jagged_scratch_bytes(src->n_records), st) != cudaSuccess)
+        if (cudaMallocAsync(&scratch, jagged_scratch_bytes(jagged_tile_records(jp)), st) != cudaSuccess)
           return MRN_ENOMEM;
       }
       rc = launch_jagged_a2s(jp, scratch, stream);
@@ -439,9 +497,7 @@ int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
       if ((rc = launch_jagged_s2a(jp, stream))) return rc;
       if ((rc = launch_convert(kids, stream, nullptr))) return rc;
     }
-    GapPlan g;
-    gap_plan(s, *dst, &g);
-    return g.ngaps ? launch_zero_gaps(g, stream) : MRN_OK;
+    return zero_dst_gaps(*dst, stream);
   }
   if (src->layout.kind == MRN_AOS && dst->layout.kind == MRN_AOS) {
     const size_t bytes = (size_t)src->n_records * s->stride;
@@ -457,9 +513,7 @@ int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
   LaunchShape sh = tuned_shape(p);
   if (g_force_direct.load()) sh.generic = 1;
   if ((rc = launch_convert(p, stream, &sh))) return rc;
-  GapPlan g;
-  gap_plan(s, *dst, &g);
-  return g.ngaps ? launch_zero_gaps(g, stream) : MRN_OK;
+  return zero_dst_gaps(*dst, stream);
 }
 
 int mrn_sync(void* stream) {

@@ -86,10 +86,12 @@ int plan_job(const mrn_view& src, const mrn_view& dst, std::vector<BatchJob>* ou
   BatchJob j;
   std::memset(&j, 0, sizeof(j));
   if (jag) {
+    // field-major to field-major jagged pairs run through mrn_convert only
+    if (src.layout.kind != MRN_AOS && dst.layout.kind != MRN_AOS) return MRN_EUNSUPPORTED;
     if ((rc = build_jagged_plan(src, dst, &j.jp))) return rc;
     if (src.layout.kind == MRN_AOS) {
       j.kind = JOB_JAG_A2S;
-      j.ntiles = (src.n_records + MRN_JAG_TILE - 1) / MRN_JAG_TILE;
+      j.ntiles = (jagged_tile_records(j.jp) + MRN_JAG_TILE - 1) / MRN_JAG_TILE;
     } else {
       // children: a plain conversion job; this job builds the parents
       BatchJob kids;
@@ -109,14 +111,14 @@ int plan_job(const mrn_view& src, const mrn_view& dst, std::vector<BatchJob>* ou
     convert_tiles(&j);
   }
   out->push_back(j);
-  GapPlan g;
-  gap_plan_of(dst, &g);
-  if (g.ngaps && g.nblocks) {
+  GapPlan g[2];
+  const int np = gap_plans_of(dst, g);
+  for (int i = 0; i < np; ++i) {
     BatchJob z;
     std::memset(&z, 0, sizeof(z));
     z.kind = JOB_ZERO;
-    z.gp = g;
-    z.ntiles = (g.nblocks * g.ngaps + 255) / 256;
+    z.gp = g[i];
+    z.ntiles = (g[i].nblocks * g[i].ngaps + 255) / 256;
     out->push_back(z);
   }
   return MRN_OK;

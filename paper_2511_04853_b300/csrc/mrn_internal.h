@@ -46,6 +46,14 @@ uint32_t dtype_size(int dtype);
 uint64_t aosoa_block_bytes(const mrn_schema* s, uint32_t B);
 uint64_t aosoa_col_start(const mrn_schema* s, uint32_t B, uint32_t c);
 uint64_t soa_region_start(const mrn_schema* s, uint64_t n, uint64_t m, uint32_t r);
+// Regions of a single-block field-major view of either kind (SoA: data
+// columns, offsets, child columns; jagged AoSoA(B): blocks, offsets, child
+// columns), each 128-byte aligned.
+uint32_t parent_regions(const mrn_schema* s, int kind);
+uint32_t fm_region_count(const mrn_schema* s, int kind);
+uint64_t fm_region_bytes(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint32_t r);
+uint64_t fm_region_start(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint32_t r);
+uint64_t fm_total_bytes(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m);
 uint64_t soa_total_bytes(const mrn_schema* s, uint64_t n, uint64_t m);
 uint64_t base_bytes(const mrn_schema* s, const mrn_layout& l, uint64_t n, uint64_t m);
 
@@ -66,13 +74,24 @@ void plan_tiles(const mrn_schema* s, ConvPlan* p, uint32_t stage_bytes);
 int convert_direct(const mrn_view& src, const mrn_view& dst, void* stream);
 // Builds the plan of a validated jagged view pair.
 int build_jagged_plan(const mrn_view& src, const mrn_view& dst, JagPlan* jp);
+// Parents a jagged AoS -> field-major conversion covers: n, or n rounded up
+// to whole AoSoA blocks (the slots after n are written as zero).
+inline uint64_t jagged_tile_records(const JagPlan& jp) {
+  return jp.parent.n_fm_pad > jp.parent.n ? jp.parent.n_fm_pad : jp.parent.n;
+}
 // The children of a jagged SoA -> AoS plan as a plain conversion of the
 // child schema (child row j -> pool record j, j < m_src), with tiles.
 int jagged_children_plan(const mrn_schema* s, const JagPlan& jp, ConvPlan* out);
-// Alignment holes of a single-block SoA or AoSoA destination view.
-void gap_plan_of(const mrn_view& dst, GapPlan* g);
-// Zeroes the alignment holes of a single-block SoA or AoSoA device view.
+// Zero-fill plans of a destination view's bytes that no value fills: the
+// holes inside every AoSoA block, and the bytes between the regions of a
+// single-block field-major view.  Returns how many plans (0..2) it wrote.
+int gap_plans_of(const mrn_view& dst, GapPlan g[2]);
+// Zeroes those bytes of a device view.
 int zero_dst_gaps(const mrn_view& dst, void* stream);
+// True when a field-major view keeps its offsets and child columns inside
+// view.base (single block); its offsets pointer.
+bool fm_single_block(const mrn_view& v);
+char* fm_offsets(const mrn_view& v);
 // Host-side validation of a device view pair; fills *is_jagged.
 int validate_pair(const mrn_view* src, const mrn_view* dst, bool need_device, bool* is_jagged);
 

@@ -462,7 +462,8 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
     const bool ok = r < P.n;
     len[k] = 0;
     beg[k] = 0;
-    aos_to_fm_lane<VP, W>(P, r, ok, ok, P.src.base + r * P.stride, tw, lane, &len[k], &beg[k]);
+    // slots after n of a destination's last AoSoA block are written as zero
+    aos_to_fm_lane<VP, W>(P, r, ok, r < P.n_fm_pad, P.src.base + r * P.stride, tw, lane, &len[k], &beg[k]);
     if (!ok) len[k] = 0;
     if (ok && (beg[k] > jp.pool_n || (uint64_t)len[k] > jp.pool_n - beg[k])) {
       flag_error(MRN_EINVAL);
@@ -1350,12 +1351,13 @@ int launch_jagged_a2s(JagPlan& jp, void* scratch, void* stream) {
     k_write_offset0<<<1, 1, 0, s>>>(jp.offsets, jp.off_size, jp.offset_base);
     return cuda_status(cudaGetLastError());
   }
-  jp.ntiles = (n + MRN_JAG_TILE - 1) / MRN_JAG_TILE;
+  const uint64_t nt = jagged_tile_records(jp);  // AoSoA: whole blocks
+  jp.ntiles = (nt + MRN_JAG_TILE - 1) / MRN_JAG_TILE;
   if (jp.ntiles > 0x7fffffffull) return MRN_EUNSUPPORTED;
   char* sc = static_cast<char*>(scratch);
   jp.tile_counter = reinterpret_cast<unsigned int*>(sc);
   jp.tile_state = reinterpret_cast<unsigned long long*>(sc + 256);
-  cudaError_t e = cudaMemsetAsync(sc, 0, jagged_scratch_bytes(n), s);
+  cudaError_t e = cudaMemsetAsync(sc, 0, jagged_scratch_bytes(nt), s);
   if (e != cudaSuccess) return cuda_status(e);
   void* fn = jag_a2s(jp.parent.vec, jp.child.vec);
   void* args[] = {&jp};

@@ -154,34 +154,47 @@ uint64_t aosoa_block_bytes(const mrn_schema* s, uint32_t B) {
   return align_up(end, al);
 }
 
-namespace {
-uint64_t region_bytes(const mrn_schema* s, uint64_t n, uint64_t m, uint32_t r) {
-  const uint32_t nc = (uint32_t)s->cols.size();
-  if (r < nc) return n * s->cols[r].size;
-  if (r == nc) return (n + 1) * s->off_size;
-  return m * s->child->cols[r - nc - 1].size;
+// Regions of a single-block field-major view: SoA: the data columns, then
+// (jagged) the offsets and the child columns; jagged AoSoA(B): the parent
+// blocks, then the offsets and the child columns.
+uint32_t parent_regions(const mrn_schema* s, int kind) {
+  return kind == MRN_AOSOA ? 1u : (uint32_t)s->cols.size();
 }
-uint32_t region_count(const mrn_schema* s) {
-  return (uint32_t)s->cols.size() + (s->has_jagged ? 1 + (uint32_t)s->child->cols.size() : 0);
+uint64_t fm_region_bytes(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint32_t r) {
+  const uint32_t P = parent_regions(s, kind);
+  if (r < P) return kind == MRN_AOSOA ? (n + B - 1) / B * aosoa_block_bytes(s, B) : n * s->cols[r].size;
+  if (r == P) return (n + 1) * s->off_size;
+  return m * s->child->cols[r - P - 1].size;
 }
-}  // namespace
 
-uint64_t soa_region_start(const mrn_schema* s, uint64_t n, uint64_t m, uint32_t r) {
+uint32_t fm_region_count(const mrn_schema* s, int kind) {
+  return parent_regions(s, kind) + (s->has_jagged ? 1 + (uint32_t)s->child->cols.size() : 0);
+}
+
+uint64_t fm_region_start(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint32_t r) {
   uint64_t pos = 0;
-  for (uint32_t k = 0; k < r; ++k) pos = align_up(pos + region_bytes(s, n, m, k), 128);
+  for (uint32_t k = 0; k < r; ++k) pos = align_up(pos + fm_region_bytes(s, kind, B, n, m, k), 128);
   return pos;
 }
 
-uint64_t soa_total_bytes(const mrn_schema* s, uint64_t n, uint64_t m) {
-  const uint32_t nr = region_count(s);
-  return align_up(soa_region_start(s, n, m, nr - 1) + region_bytes(s, n, m, nr - 1), 128);
+uint64_t soa_region_start(const mrn_schema* s, uint64_t n, uint64_t m, uint32_t r) {
+  return fm_region_start(s, MRN_SOA, 0, n, m, r);
 }
+
+uint64_t fm_total_bytes(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m) {
+  const uint32_t nr = fm_region_count(s, kind);
+  return align_up(fm_region_start(s, kind, B, n, m, nr - 1) + fm_region_bytes(s, kind, B, n, m, nr - 1), 128);
+}
+
+uint64_t soa_total_bytes(const mrn_schema* s, uint64_t n, uint64_t m) { return fm_total_bytes(s, MRN_SOA, 0, n, m); }
 
 uint64_t base_bytes(const mrn_schema* s, const mrn_layout& l, uint64_t n, uint64_t m) {
   switch (l.kind) {
     case MRN_AOS: return n * s->stride;
-    case MRN_SOA: return soa_total_bytes(s, n, m);
-    default: return (n + l.block - 1) / l.block * aosoa_block_bytes(s, l.block);
+    case MRN_SOA: return fm_total_bytes(s, MRN_SOA, 0, n, m);
+    default:
+      if (s->has_jagged) return fm_total_bytes(s, MRN_AOSOA, l.block, n, m);
+      return (n + l.block - 1) / l.block * aosoa_block_bytes(s, l.block);
   }
 }
 
@@ -319,8 +332,17 @@ int mrn_child_pool_bytes(const mrn_schema* s, uint64_t m, size_t* out) {
 }
 
 int mrn_soa_region_offset(const mrn_schema* s, uint64_t n, uint64_t m, uint32_t r, size_t* out) {
-  if (!s || !s->finalized || !out || r >= region_count(s)) return MRN_EINVAL;
+  if (!s || !s->finalized || !out || r >= fm_region_count(s, MRN_SOA)) return MRN_EINVAL;
   *out = (size_t)soa_region_start(s, n, m, r);
+  return MRN_OK;
+}
+
+int mrn_region_offset(const mrn_schema* s, mrn_layout l, uint64_t n, uint64_t m, uint32_t r, size_t* out) {
+  if (!s || !s->finalized || !out) return MRN_EINVAL;
+  if (l.kind == MRN_SOA) return mrn_soa_region_offset(s, n, m, r, out);
+  if (l.kind != MRN_AOSOA || l.block < 1 || !s->has_jagged || r >= fm_region_count(s, MRN_AOSOA))
+    return MRN_EINVAL;
+  *out = (size_t)fm_region_start(s, MRN_AOSOA, l.block, n, m, r);
   return MRN_OK;
 }
 

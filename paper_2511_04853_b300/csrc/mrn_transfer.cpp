@@ -23,9 +23,10 @@ bool same_layout(const mrn_view& a, const mrn_view& b) {
          (a.layout.kind != MRN_AOSOA || a.layout.block == b.layout.block);
 }
 
-char* soa_part(const mrn_view& v, uint32_t region, void* const* cols, uint32_t idx) {
+char* fm_part(const mrn_view& v, uint32_t region, void* const* cols, uint32_t idx) {
   if (cols) return static_cast<char*>(cols[idx]);
-  return static_cast<char*>(v.base) + soa_region_start(v.schema, v.n_records, v.n_children, region);
+  return static_cast<char*>(v.base) +
+         fm_region_start(v.schema, v.layout.kind, v.layout.block, v.n_records, v.n_children, region);
 }
 
 uint64_t gcd64(uint64_t a, uint64_t b) {
@@ -66,13 +67,15 @@ uint64_t staged_view(const mrn_view& like, char* stage, mrn_view* out, std::vect
   if (like.layout.kind == MRN_AOS) {
     out->base = take(n * s->stride);
     if (s->has_jagged) out->child_pool = take(m * s->child->stride);
-  } else if (like.layout.kind == MRN_AOSOA) {
-    out->base = take((n + like.layout.block - 1) / like.layout.block * aosoa_block_bytes(s, like.layout.block));
   } else {
-    cols.assign(s->cols.size(), nullptr);
-    for (size_t c = 0; c < s->cols.size(); ++c) cols[c] = take(n * s->cols[c].size);
-    out->columns = cols.data();
-    out->base = cols.empty() ? nullptr : cols[0];
+    if (like.layout.kind == MRN_AOSOA) {
+      out->base = take((n + like.layout.block - 1) / like.layout.block * aosoa_block_bytes(s, like.layout.block));
+    } else {
+      cols.assign(s->cols.size(), nullptr);
+      for (size_t c = 0; c < s->cols.size(); ++c) cols[c] = take(n * s->cols[c].size);
+      out->columns = cols.data();
+      out->base = cols.empty() ? nullptr : cols[0];
+    }
     if (s->has_jagged) {
       out->offsets = take((n + 1) * s->off_size);
       ccols.assign(s->child->cols.size(), nullptr);
@@ -106,17 +109,21 @@ std::vector<ViewPart> view_parts(const mrn_view& v) {
   if (v.layout.kind == MRN_AOS) {
     out.push_back({static_cast<char*>(v.base), n * s->stride});
     if (s->has_jagged) out.push_back({static_cast<char*>(v.child_pool), m * s->child->stride});
-  } else if (v.layout.kind == MRN_AOSOA) {
-    const uint64_t B = v.layout.block;
-    out.push_back({static_cast<char*>(v.base), (n + B - 1) / B * aosoa_block_bytes(s, (uint32_t)B)});
   } else {
-    const uint32_t nc = (uint32_t)s->cols.size();
-    for (uint32_t c = 0; c < nc; ++c) out.push_back({soa_part(v, c, v.columns, c), n * s->cols[c].size});
+    uint32_t P;
+    if (v.layout.kind == MRN_AOSOA) {
+      const uint64_t B = v.layout.block;
+      out.push_back({static_cast<char*>(v.base), (n + B - 1) / B * aosoa_block_bytes(s, (uint32_t)B)});
+      P = 1;
+    } else {
+      P = (uint32_t)s->cols.size();
+      for (uint32_t c = 0; c < P; ++c) out.push_back({fm_part(v, c, v.columns, c), n * s->cols[c].size});
+    }
     if (s->has_jagged) {
-      char* offs = v.offsets ? static_cast<char*>(v.offsets) : soa_part(v, nc, nullptr, 0);
+      char* offs = v.offsets ? static_cast<char*>(v.offsets) : fm_part(v, P, nullptr, 0);
       out.push_back({offs, (n + 1) * s->off_size});
       for (uint32_t c = 0; c < s->child->cols.size(); ++c)
-        out.push_back({soa_part(v, nc + 1 + c, v.child_columns, c), m * s->child->cols[c].size});
+        out.push_back({fm_part(v, P + 1 + c, v.child_columns, c), m * s->child->cols[c].size});
     }
   }
   return out;
@@ -133,7 +140,7 @@ mrn_view sub_view(const mrn_view& v, uint64_t r0, uint64_t cnt, std::vector<void
   } else {
     cols.assign(s->cols.size(), nullptr);
     for (uint32_t c = 0; c < s->cols.size(); ++c)
-      cols[c] = soa_part(v, c, v.columns, c) + r0 * s->cols[c].size;
+      cols[c] = fm_part(v, c, v.columns, c) + r0 * s->cols[c].size;
     o.columns = cols.data();
     o.base = cols.empty() ? nullptr : cols[0];
   }
@@ -237,11 +244,11 @@ uint64_t TransferEngine::staging_bytes(const mrn_view& src, const mrn_view& dst,
 }
 
 namespace {
-// Zeroes the alignment holes of a host single-block SoA destination (the
-// bytes between and after its regions), on the calling thread.
+// Zeroes the alignment holes of a host single-block field-major destination
+// (the bytes between and after its regions), on the calling thread.
 void zero_host_soa_gaps(const mrn_view& dst) {
-  if (dst.layout.kind != MRN_SOA || dst.columns || !dst.base) return;
-  if (dst.schema->has_jagged && (dst.offsets || dst.child_columns)) return;
+  const bool fm = dst.layout.kind == MRN_SOA || (dst.layout.kind == MRN_AOSOA && dst.schema->has_jagged);
+  if (!fm || !fm_single_block(dst)) return;
   char* base = static_cast<char*>(dst.base);
   uint64_t prev = 0;
   for (const auto& p : view_parts(dst)) {
@@ -249,7 +256,7 @@ void zero_host_soa_gaps(const mrn_view& dst) {
     if (st > prev) std::memset(base + prev, 0, st - prev);
     prev = st + p.bytes;
   }
-  const uint64_t total = soa_total_bytes(dst.schema, dst.n_records, dst.n_children);
+  const uint64_t total = base_bytes(dst.schema, dst.layout, dst.n_records, dst.n_children);
   if (total > prev) std::memset(base + prev, 0, total - prev);
 }
 }  // namespace

@@ -96,6 +96,7 @@ SIGNATURES = [
     ("mrn_required_bytes", ctypes.c_int, [vp, Layout, u64, u64, ctypes.POINTER(sz)]),
     ("mrn_child_pool_bytes", ctypes.c_int, [vp, u64, ctypes.POINTER(sz)]),
     ("mrn_soa_region_offset", ctypes.c_int, [vp, u64, u64, u32, ctypes.POINTER(sz)]),
+    ("mrn_region_offset", ctypes.c_int, [vp, Layout, u64, u64, u32, ctypes.POINTER(sz)]),
     ("mrn_aosoa_block_bytes", ctypes.c_int, [vp, u32, ctypes.POINTER(sz)]),
     ("mrn_aosoa_column_offset", ctypes.c_int, [vp, u32, u32, ctypes.POINTER(sz)]),
     ("mrn_convert", ctypes.c_int, [ctypes.POINTER(ViewStruct), ctypes.POINTER(ViewStruct), vp]),
@@ -244,6 +245,12 @@ class Schema:
     def child_pool_bytes(self, m):
         out = sz()
         check(lib().mrn_child_pool_bytes(self._h, m, ctypes.byref(out)))
+        return out.value
+
+    def region_offset(self, kind, n, m, r, block=0):
+        out = sz()
+        check(lib().mrn_region_offset(self._h, Layout(KIND.get(kind, kind), block), n, m, r,
+                                      ctypes.byref(out)))
         return out.value
 
     def soa_region_offset(self, n, m, r):

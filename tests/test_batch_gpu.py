@@ -219,3 +219,31 @@ def test_batch_tune_keeps_results_exact():
     assert mrn.sync() == mrn.OK
     for i, (s, d, want, name) in enumerate(jobs):
         assert np.array_equal(result(d, want, name), want), "job %d (%s)" % (i, name)
+
+
+def test_jagged_aosoa_jobs_in_a_batch():
+    """Jagged AoS -> AoSoA(B) and AoSoA(B) -> AoS jobs in one launch equal
+    the oracle; a field-major to field-major jagged job is refused."""
+    pairs, checks = [], []
+    for j, (n, B) in enumerate([(777, 32), (5000, 128), (513, 5), (20000, 32)]):
+        s, o = mrn.Schema(datagen.TRACKS), oracle.Schema(datagen.TRACKS)
+        d = datagen.workload("tracks", n, 800 + j)
+        o_aos = oracle.pack(o, d, "aos")
+        o_blk = oracle.convert(o, o_aos, "aosoa", B, m=d["m"])
+        dst = dev_dest(s, "aosoa", n, d["m"], B)
+        pairs.append((mrn.View(s, "aos", n, base=dev(o_aos.base), child_pool=dev(o_aos.pool), m=d["m"]), dst))
+        checks.append((dst.tensors[0], o_blk.base[: o.base_bytes("aosoa", B, n, d["m"])]))
+        back = dev_dest(s, "aos", n, d["m"])
+        pairs.append((mrn.View(s, "aosoa", n, block=B, base=dev(o_blk.base), m=d["m"]), back))
+        checks.append((back.tensors[0], o_aos.base[: n * 24]))
+        checks.append((back.tensors[1], o_aos.pool[: d["m"] * 8]))
+    b = mrn.Batch(pairs, use_graph=True)
+    b.launch()
+    assert mrn.sync() == mrn.OK
+    for k, (t, want) in enumerate(checks):
+        assert np.array_equal(host(t, want.size), want), "check %d" % k
+    s = mrn.Schema(datagen.TRACKS)
+    a = mrn.View(s, "soa", 10, base=garbage(1 << 12), m=1)
+    c = mrn.View(s, "aosoa", 10, block=32, base=garbage(1 << 12), m=1)
+    with pytest.raises(mrn.MrnError):
+        mrn.Batch([(a, c)], use_graph=False)

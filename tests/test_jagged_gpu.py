@@ -243,9 +243,90 @@ def test_lookback_wait_is_bounded():
     a2s_check(s, o, o_aos)  # normal operation afterwards
 
 
-def test_aosoa_with_jagged_is_unsupported():
+def test_equal_jagged_layouts_are_unsupported():
     s = mrn.Schema(datagen.TRACKS)
     buf = garbage(1 << 12)
-    src = mrn.View(s, "aos", 10, base=buf, child_pool=buf, m=1)
-    dst = mrn.View(s, "aosoa", 10, block=32, base=buf)
-    assert mrn.convert_status(src, dst) == mrn.EUNSUPPORTED
+    a = mrn.View(s, "aosoa", 10, block=32, base=buf, m=1)
+    b = mrn.View(s, "aosoa", 10, block=32, base=garbage(1 << 12), m=1)
+    assert mrn.convert_status(a, b) == mrn.EUNSUPPORTED
+
+
+# ---------------------------------------------- jagged parents in AoSoA(B)
+
+def _bytes(view_tensor, n):
+    return host(view_tensor, n)
+
+
+@pytest.mark.parametrize("B", [32, 128, 5])
+@pytest.mark.parametrize("n", [0, 1, 511, 512, 513, 5003])
+def test_aos_to_aosoa_and_back(n, B):
+    """Jagged AoS -> AoSoA(B): the parent blocks (tail slots zero), the
+    offsets and the child columns equal the oracle's, byte for byte, for a
+    canonical and a shuffled pool; AoSoA(B) -> AoS gives the canonical AoS
+    collection back."""
+    s, o, d = tracks(n, seed=40 + B)
+    o_aos = oracle.pack(o, d, "aos")
+    o_blk = oracle.convert(o, o_aos, "aosoa", B, m=d["m"])
+    nb = o.base_bytes("aosoa", B, n, d["m"])
+    for src_side in (o_aos, oracle.shuffle_pool(o, o_aos, np.random.default_rng(B).permutation(n), gap=1)):
+        dst = dev_dest(s, "aosoa", n, d["m"], B)
+        mrn.convert(dev_view(s, src_side, o), dst)
+        assert mrn.sync() == mrn.OK
+        assert np.array_equal(host(dst.tensors[0], nb), o_blk.base[:nb])
+    back = dev_dest(s, "aos", n, d["m"])
+    mrn.convert(dev_view(s, o_blk, o), back)
+    assert mrn.sync() == mrn.OK
+    assert np.array_equal(host(back.tensors[0], n * 24), o_aos.base[: n * 24])
+    assert np.array_equal(host(back.tensors[1], d["m"] * 8), o_aos.pool[: d["m"] * 8])
+
+
+@pytest.mark.parametrize("pair", [("soa", 0, "aosoa", 32), ("aosoa", 32, "soa", 0), ("aosoa", 32, "aosoa", 128),
+                                  ("aosoa", 128, "aosoa", 5)], ids=lambda p: "%s%d-%s%d" % p)
+def test_field_major_to_field_major(pair):
+    """SoA <-> AoSoA(B) and AoSoA(B) -> AoSoA(B') of a jagged collection:
+    parents change layout, offsets and child values are copied."""
+    sk, sb, dk, db = pair
+    n = 3001
+    s, o, d = tracks(n, seed=9, raw=True)
+    o_aos = oracle.pack(o, d, "aos")
+    o_src = oracle.convert(o, o_aos, sk, sb, m=d["m"])
+    want = oracle.convert(o, o_src, dk, db, m=d["m"]).base
+    nb = o.base_bytes(dk, db, n, d["m"])
+    dst = dev_dest(s, dk, n, d["m"], db)
+    mrn.convert(dev_view(s, o_src, o), dst)
+    assert mrn.sync() == mrn.OK
+    assert np.array_equal(host(dst.tensors[0], nb), want[:nb])
+
+
+def test_aosoa_with_separate_offsets_and_child_columns():
+    """A jagged AoSoA view may keep its offsets and child columns outside
+    view.base; results equal the regions of the single-block form."""
+    n, B = 2048 + 77, 32
+    s, o, d = tracks(n, seed=21)
+    m = d["m"]
+    o_aos = oracle.pack(o, d, "aos")
+    o_blk = oracle.convert(o, o_aos, "aosoa", B, m=m)
+    blocks = garbage(s.required_bytes("aosoa", n, 0, B))
+    offs = garbage((n + 1) * 4)
+    kids = [garbage(m * 4) for _ in range(2)]
+    dst = mrn.View(s, "aosoa", n, block=B, base=blocks, offsets=offs, child_columns=kids, m=m)
+    mrn.convert(dev_view(s, o_aos, o), dst)
+    assert mrn.sync() == mrn.OK
+    nblk = oracle.region(o, o_blk, 0).size
+    assert np.array_equal(host(blocks, nblk), oracle.region(o, o_blk, 0))
+    assert np.array_equal(host(offs), oracle.region(o, o_blk, 1))
+    for c in range(2):
+        assert np.array_equal(host(kids[c]), oracle.region(o, o_blk, 2 + c))
+    # and back to AoS from the split form
+    back = dev_dest(s, "aos", n, m)
+    mrn.convert(dst, back)
+    assert mrn.sync() == mrn.OK
+    assert np.array_equal(host(back.tensors[0], n * 24), o_aos.base[: n * 24])
+
+
+def test_region_offsets_match_the_oracle():
+    s, o = mrn.Schema(datagen.TRACKS), oracle.Schema(datagen.TRACKS)
+    for n, m, B in [(0, 0, 32), (1, 3, 5), (1000, 20000, 128), (12345, 6789, 32)]:
+        assert s.required_bytes("aosoa", n, m, B) == o.base_bytes("aosoa", B, n, m)
+        for r in range(4):
+            assert s.region_offset("aosoa", n, m, r, B) == o.fm_region_start("aosoa", B, n, m, r)

@@ -212,3 +212,28 @@ def lib_status(src, dst):
     from paper_2511_04853_b300 import mrn as binding
     opts = binding.TransferOpts(0, 0, binding.TRANSFER_ZERO_COPY)
     return binding.lib().mrn_transfer_convert(src.ref, dst.ref, ctypes.byref(opts), None)
+
+
+@pytest.mark.parametrize("B", [32, 128])
+def test_jagged_aosoa_both_directions(B):
+    """Host AoS -> device jagged AoSoA(B) and device AoSoA(B) -> host AoS
+    through the transfer engine (host single-block holes zeroed)."""
+    s, o = mrn.Schema(datagen.TRACKS), oracle.Schema(datagen.TRACKS)
+    n = 7777
+    d = datagen.workload("tracks", n, 61)
+    m = d["m"]
+    o_aos = oracle.pack(o, d, "aos")
+    o_blk = oracle.convert(o, o_aos, "aosoa", B, m=m)
+    nb = o.base_bytes("aosoa", B, n, m)
+    dst = garbage(nb)
+    src = mrn.View(s, "aos", n, base=host_side(o_aos.base), child_pool=host_side(o_aos.pool), m=m, mem="pinned")
+    mrn.transfer_convert(src, mrn.View(s, "aosoa", n, block=B, base=dst, m=m))
+    assert mrn.sync() == mrn.OK
+    assert np.array_equal(host(dst, nb), o_blk.base[:nb])
+    h_rec, h_pool = pinned(n * 24), pinned(m * 8)
+    mrn.transfer_convert(mrn.View(s, "aosoa", n, block=B, base=dev(o_blk.base), m=m),
+                         mrn.View(s, "aos", n, base=h_rec, child_pool=h_pool, m=m, mem="pinned"))
+    torch().cuda.synchronize()
+    assert mrn.sync() == mrn.OK
+    assert np.array_equal(h_rec.numpy()[: n * 24], o_aos.base[: n * 24])
+    assert np.array_equal(h_pool.numpy()[: m * 8], o_aos.pool[: m * 8])
