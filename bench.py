@@ -221,18 +221,14 @@ MIXED_SCHEMAS = ["points", "cells", "tracks"]
 def mixed_plan(jobs, seed=3, lo=3.0, hi=6.0):
     """Job list of the mixed batch: sizes round(10^U(lo, hi)) records,
     schema uniform over points / cells / tracks, AoS source, target uniform
-    over SoA / AoSoA(32) / AoSoA(128).  Jagged parents have no AoSoA form in
-    this library, so track jobs always target SoA."""
+    over SoA / AoSoA(32) / AoSoA(128) (track parents in AoSoA(B) keep their
+    offsets and child columns after the blocks)."""
     import numpy as np
     rng = np.random.default_rng(seed)
     ns = np.rint(10.0 ** rng.uniform(lo, hi, jobs)).astype(np.int64)
     sch = rng.integers(0, 3, jobs)
     tgt = rng.integers(0, 3, jobs)
-    out = []
-    for i in range(jobs):
-        name = MIXED_SCHEMAS[sch[i]]
-        out.append((name, int(ns[i]), MIXED_TARGETS[0] if name == "tracks" else MIXED_TARGETS[tgt[i]]))
-    return out
+    return [(MIXED_SCHEMAS[sch[i]], int(ns[i]), MIXED_TARGETS[tgt[i]]) for i in range(jobs)]
 
 
 def device_aos(torch, s, name, n, seed):
@@ -327,7 +323,7 @@ def run_mixed(mrn, torch, stream, peak, args):
 
     res = {"workload": "%d collections, records round(10^U(3,6)), schema uniform over points / cells / "
                        "tracks (jagged, Poisson(20) children clipped at 256), AoS source, target uniform over "
-                       "SoA / AoSoA(32) / AoSoA(128) (tracks: SoA)" % len(plan),
+                       "SoA / AoSoA(32) / AoSoA(128)" % len(plan),
            "records": sum(n for _, n, _ in plan), "algorithmic_bytes": alg, "setup_s": round(setup_s, 1)}
     # autotuner off: the library's default shapes
     mrn.autotune_clear()
@@ -776,7 +772,8 @@ def run_served(mrn, torch, args):
     t_cols = [torch.zeros(nt * 4, dtype=torch.uint8, device="cuda") for _ in range(3)]
     t_offs = torch.from_numpy(csum.astype(np.uint32).view(np.uint8)).cuda()
     t_kids = [torch.zeros(mt * 4, dtype=torch.uint8, device="cuda") for _ in range(2)]
-    t_dev_dst = torch.empty(st.required_bytes("soa", nt, mt), dtype=torch.uint8, device="cuda")
+    t_dev_dst = {k: torch.empty(st.required_bytes(k[0], nt, mt, k[1]), dtype=torch.uint8, device="cuda")
+                 for k in (("soa", 0), ("aosoa", 32), ("aosoa", 128))}
 
     def make_request():
         name = ["points", "cells", "tracks"][rng.integers(0, 3)]
@@ -786,8 +783,9 @@ def run_served(mrn, torch, args):
             n = max(1, min(nt - 1, size // 184))  # ~184 source bytes per parent at mean length 20
             m = int(csum[n])
             if h2d:
+                dk, dbk = [("soa", 0), ("aosoa", 32), ("aosoa", 128)][rng.integers(0, 3)]
                 src = mrn.View(st, "aos", n, base=t_host[0], child_pool=t_host[1], m=m, mem="pinned")
-                dst = mrn.View(st, "soa", n, base=t_dev_dst, m=m)
+                dst = mrn.View(st, dk, n, block=dbk, base=t_dev_dst[(dk, dbk)], m=m)
             else:
                 src = mrn.View(st, "soa", n, columns=t_cols, offsets=t_offs, child_columns=t_kids, m=m)
                 dst = mrn.View(st, "aos", n, base=t_host[0], child_pool=t_host[1], m=m, mem="pinned")
