@@ -656,8 +656,9 @@ __global__ void k_write_offset0(char* offs, uint32_t osz, unsigned long long v) 
 //
 // Every job of a batch in one persistent, warp-specialized launch of 320
 // threads per CTA.
-//  - Warp 8 (loader) takes chunks of `chunk` consecutive global tiles from an
-//    atomic counter (chunks are handed out in increasing order), publishes
+//  - Warp 8 (loader) takes chunks of up to `chunk` consecutive global tiles
+//    (fewer as the tiles run out) from an atomic tile counter (chunks are
+//    handed out in increasing order), publishes
 //    the child counts of the chunk's jagged tiles at once (so a jagged
 //    tile's look-back waits only for chunks taken earlier), decides each
 //    tile and issues the TMA loads of staged tiles up to kBNS stages ahead
@@ -887,6 +888,7 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
   uint64_t next_t = 0, chunk_end = 0;
   unsigned int pcursor = 0;
   uint32_t n_chunks = 0;  // static assignment: chunks taken so far
+  uint64_t seen = 0;      // dynamic assignment: end of the last chunk taken
   bool have = false;
   TileSlot cand;
   cand.t = 0;
@@ -898,14 +900,24 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
         if constexpr (kStatic) {
           next_t = ((uint64_t)n_chunks * gridDim.x + blockIdx.x) * chunk;
           ++n_chunks;
+          chunk_end = next_t + chunk;
         } else {
-          unsigned int cidx = 0;
-          if (lane == 0) cidx = atomicAdd(counter, 1u);
-          next_t = (uint64_t)__shfl_sync(0xffffffffu, cidx, 0) * chunk;
-          publish_jagged_sums(jobs, first_tile, njobs, total_tiles, states, next_t, next_t + chunk, &pcursor,
-                              lane);
+          // guided chunks: up to `chunk` tiles, fewer as the tiles run out
+          // (about half the remaining tiles' share per CTA), so the CTAs
+          // finish together; the counter counts tiles, handed out in
+          // increasing order
+          unsigned int start = 0, size = 0;
+          if (lane == 0) {
+            const unsigned long long rem = total_tiles > seen ? total_tiles - seen : 0ull;
+            const unsigned long long share = rem / (2ull * gridDim.x);
+            size = (unsigned int)(share < 1ull ? 1ull : (share > chunk ? (unsigned long long)chunk : share));
+            start = atomicAdd(counter, size);
+          }
+          next_t = __shfl_sync(0xffffffffu, start, 0);
+          chunk_end = next_t + __shfl_sync(0xffffffffu, size, 0);
+          seen = chunk_end;
+          publish_jagged_sums(jobs, first_tile, njobs, total_tiles, states, next_t, chunk_end, &pcursor, lane);
         }
-        chunk_end = next_t + chunk;
       }
       cand.t = next_t++;
       cand.staged = 0;
