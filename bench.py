@@ -547,6 +547,7 @@ def run_mine(args, rank, world):
     extra.update(secondary(mrn, torch, stream, peak))
     if args.mixed_jobs > 0:
         extra["batched_mixed"] = run_mixed(mrn, torch, stream, peak, args)
+    extra["sensor_grid"] = run_sensor_grid(mrn, torch, stream)
     extra["served"] = run_served(mrn, torch, args)
     cpu_val, cpu_reps, cpu_s = cpu_oracle_rate(10.0, N_RECORDS)
     line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
@@ -742,6 +743,83 @@ def secondary(mrn, torch, stream, peak):
     del h, dbuf
     torch.cuda.empty_cache()
     return out
+
+
+def run_sensor_grid(mrn, torch, stream):
+    """The paper's sensor workload (Sec. VII, Listing 1 Sensor records) as a
+    synthetic grid: host AoS sensors -> device SoA (transfer-and-convert), a
+    stand-in per-sensor computation on the SoA columns (energy = counts * A
+    + B, zero for noisy sensors; the real calibration is not in the paper),
+    device SoA -> host AoS.  Reports each stage against a single-threaded
+    numpy pass over the same AoS array."""
+    import numpy as np
+    import datagen
+    s = mrn.Schema(datagen.SENSOR)
+    off = {c["name"]: c["aos_offset"] for c in s.columns}
+    col = {c["name"]: i for i, c in enumerate(s.columns)}
+    rows = {}
+    for g in (100, 1000, 3000, 5000):
+        n = g * g
+        rng = np.random.default_rng(g)
+        rec = np.zeros((n, s.stride), np.uint8)
+        rec[:, off["type"]] = rng.integers(0, 4, n, dtype=np.uint8)
+        rec[:, off["counts"]: off["counts"] + 8] = rng.integers(0, 1 << 16, n, dtype=np.uint64).view(np.uint8).reshape(n, 8)
+        rec[:, off["calibration_data.noisy"]] = (rng.random(n) < 0.01).astype(np.uint8)
+        for k, lo, hi in (("parameter_A", 0.9, 1.1), ("parameter_B", -1.0, 1.0), ("noise_A", 0.0, 0.1),
+                          ("noise_B", 0.0, 0.1)):
+            o = off["calibration_data." + k]
+            rec[:, o: o + 4] = rng.uniform(lo, hi, n).astype(np.float32).view(np.uint8).reshape(n, 4)
+        h_in = torch.from_numpy(rec.reshape(-1)).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        soa = torch.empty(s.required_bytes("soa", n), dtype=torch.uint8, device="cuda")
+
+        def column(name, dtype):
+            o = s.soa_region_offset(n, 0, col[name])
+            size = torch.tensor([], dtype=dtype).element_size()
+            return soa[o: o + n * size].view(dtype)
+
+        hv = mrn.View(s, "aos", n, base=h_in, mem="pinned")
+        dv = mrn.View(s, "soa", n, base=soa)
+        hv_out = mrn.View(s, "aos", n, base=h_out, mem="pinned")
+        counts, energy = column("counts", torch.int64), column("energy", torch.float32)
+        a, b = column("calibration_data.parameter_A", torch.float32), column("calibration_data.parameter_B", torch.float32)
+        noisy = column("calibration_data.noisy", torch.uint8)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        best = None
+        for _ in range(3):
+            ev[0].record(stream)
+            mrn.transfer_convert(hv, dv, stream=stream)
+            ev[1].record(stream)
+            energy.copy_(torch.where(noisy != 0, 0.0, counts.to(torch.float32) * a + b))
+            ev[2].record(stream)
+            mrn.transfer_convert(dv, hv_out, stream=stream)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            t = [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
+            if best is None or sum(t) < sum(best):
+                best = t
+        assert mrn.sync() == mrn.OK
+        # the same computation on the host AoS array, one numpy pass
+        t0 = time.perf_counter()
+        cnt = rec[:, off["counts"]: off["counts"] + 8].copy().view(np.int64).reshape(-1)
+        pa = rec[:, off["calibration_data.parameter_A"]:][:, :4].copy().view(np.float32).reshape(-1)
+        pb = rec[:, off["calibration_data.parameter_B"]:][:, :4].copy().view(np.float32).reshape(-1)
+        nz = rec[:, off["calibration_data.noisy"]]
+        e_cpu = np.where(nz != 0, np.float32(0), cnt.astype(np.float32) * pa + pb).astype(np.float32)
+        cpu_ms = (time.perf_counter() - t0) * 1e3
+        out = h_out.numpy().reshape(n, s.stride)
+        e_gpu = out[:, off["energy"]: off["energy"] + 4].copy().view(np.float32).reshape(-1)
+        assert np.allclose(e_gpu, e_cpu, rtol=1e-6, atol=1e-6), "sensor energies differ"
+        assert np.array_equal(np.delete(out, np.s_[off["energy"]: off["energy"] + 4], axis=1),
+                              np.delete(rec, np.s_[off["energy"]: off["energy"] + 4], axis=1))
+        rows["%dx%d" % (g, g)] = {"sensors": n, "h2d_convert_ms": round(best[0], 3),
+                                  "stand_in_kernel_ms": round(best[1], 3), "d2h_convert_ms": round(best[2], 3),
+                                  "gpu_total_ms": round(sum(best), 3), "cpu_numpy_ms": round(cpu_ms, 3),
+                                  "transfer_convert_share": round((best[0] + best[2]) / sum(best), 3)}
+        del h_in, h_out, soa
+    torch.cuda.empty_cache()
+    return {"what": "Sensor records (40-byte AoS) host -> device SoA -> stand-in energy pass -> host AoS, "
+                    "against one numpy pass on the host AoS array", "grids": rows}
 
 
 def run_served(mrn, torch, args):
