@@ -23,7 +23,8 @@ struct mrn_batch {
   BatchJob* d_jobs = nullptr;
   unsigned long long* d_first = nullptr;
   char* d_scratch = nullptr;  // counter (256 B) + one look-back word per tile
-  size_t scratch_bytes = 0;
+  size_t scratch_bytes = 0;  // the look-back words only with jagged AoS -> SoA jobs
+  bool jag_a2s = false;
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -75,6 +76,7 @@ void convert_tiles(BatchJob* j) {
   const ConvPlan& p = j->jp.parent;
   const uint64_t nrec = p.dir == DIR_FM_AOS ? p.n : p.n_fm_pad;
   j->ntiles = p.tg.tma ? staged_tile_count(p.n, nrec, p.tg.T, p.tg.G) : (nrec + tr - 1) / tr;
+  if (p.tg.tma) fill_stage_rec(p, &j->stage);
 }
 
 // Plans one job (everything but tile_begin), followed by a zero-fill job
@@ -168,8 +170,11 @@ int rebuild_tables(mrn_batch* b) {
 
 int upload(mrn_batch* b) {
   const size_t jb = std::max<size_t>(1, b->jobs.size()) * sizeof(BatchJob);
-  const size_t fb = std::max<size_t>(1, b->first_tile.size()) * sizeof(unsigned long long);
-  b->scratch_bytes = 256 + (size_t)b->total_tiles * sizeof(unsigned long long);
+  // the tile index is read by whole 16-byte pieces (L2 prefetch)
+  const size_t fb = align_up(std::max<size_t>(1, b->first_tile.size()) * sizeof(unsigned long long), 16);
+  b->jag_a2s = false;
+  for (const BatchJob& j : b->jobs) b->jag_a2s |= j.kind == JOB_JAG_A2S;
+  b->scratch_bytes = 256 + (b->jag_a2s ? (size_t)b->total_tiles * sizeof(unsigned long long) : 0);
   if (cudaMalloc(&b->d_jobs, jb) != cudaSuccess || cudaMalloc(&b->d_first, fb) != cudaSuccess ||
       cudaMalloc(&b->d_scratch, b->scratch_bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -189,7 +194,8 @@ int enqueue(mrn_batch* b, cudaStream_t s) {
   if (cudaMemsetAsync(b->d_scratch, 0, b->scratch_bytes, s) != cudaSuccess) return MRN_ECUDA;
   return launch_batch(b->d_jobs, b->d_first, (unsigned)b->jobs.size(), b->total_tiles,
                       reinterpret_cast<unsigned int*>(b->d_scratch),
-                      reinterpret_cast<unsigned long long*>(b->d_scratch + 256), b->ctas_per_sm,
+                      b->jag_a2s ? reinterpret_cast<unsigned long long*>(b->d_scratch + 256) : nullptr,
+                      b->ctas_per_sm,
                       b->max_chunk, s);
 }
 

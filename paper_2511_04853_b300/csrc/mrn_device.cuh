@@ -281,6 +281,13 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// A word other CTAs update atomically, read where they update it (L2).
+__device__ __forceinline__ unsigned int ld_relaxed_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -418,22 +425,10 @@ __device__ __forceinline__ void sts128_zero(uint32_t a) {
   asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(a), "r"(0u) : "memory");
 }
 
-// The fields of a plan the staged transform reads, copied into shared memory
-// next to the column descriptors.  Each side of a tile is described by one
-// row geometry, whatever its layout: record r lies in row block
-// r >> shift (r / block when shift is MRN_NO_SHIFT) at byte bb * row block,
-// slot r - block * row block.  AoS: block 1, shift 0, bb = stride (every
-// record its own row, slot 0); SoA: shift 31 (one row, slot r); AoSoA(B):
-// block B, bb = block bytes.
-struct TileHdr {
-  uint32_t ncols, stride, vec, pad, T, nsize;
-  uint32_t sblock, sshift, sbb;  // source row geometry
-  uint32_t dblock, dshift, dbb;  // destination row geometry
-};
-
 // Row geometry of one side of a plan (see TileHdr).
-__device__ __forceinline__ void tile_side_geometry(uint32_t kind, uint32_t block, uint32_t shift, uint64_t bb,
-                                                   uint32_t stride, uint32_t* gb, uint32_t* gs, uint32_t* gbb) {
+__host__ __device__ __forceinline__ void tile_side_geometry(uint32_t kind, uint32_t block, uint32_t shift, uint64_t bb,
+                                                            uint32_t stride, uint32_t* gb, uint32_t* gs,
+                                                            uint32_t* gbb) {
   if (kind == K_AOS) {
     *gb = 1, *gs = 0, *gbb = stride;
   } else if (kind == K_SOA) {

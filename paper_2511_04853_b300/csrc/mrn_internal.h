@@ -103,6 +103,8 @@ struct LaunchShape {
   uint32_t generic = 0;      // 1: direct kernel even when the plan can be staged
 };
 int launch_convert(const ConvPlan& p, void* stream, const LaunchShape* shape);
+// The stage table of a staged plan (header and column descriptors).
+void fill_stage_rec(const ConvPlan& p, StageRec* out);
 int launch_zero_gaps(const GapPlan& g, void* stream);
 // Jagged conversions.  `scratch` (AoS->SoA only) must hold
 // jagged_scratch_bytes(n) bytes; it is cleared on `stream` first.

@@ -66,14 +66,14 @@ __device__ __forceinline__ void tma_transform(const TileHdr& h, uint32_t desc, c
 
 // Entry k of the staged-transform descriptor table: the k-th column in
 // size-class order (see tile_convert).
-__device__ __forceinline__ uint4 tile_desc(const ConvPlan& p, uint32_t k) {
+__host__ __device__ __forceinline__ uint4 tile_desc(const ConvPlan& p, uint32_t k) {
   const uint32_t c = p.tg.order[k];
   const uint32_t col = p.tg.col[c], aos_off = col & 0xffffffu;
   return make_uint4(col >> 24, p.src.kind == K_AOS ? aos_off : p.tg.src_off[c],
                     p.dst.kind == K_AOS ? aos_off : p.tg.dst_off[c], 0u);
 }
 
-__device__ __forceinline__ TileHdr tile_hdr(const ConvPlan& p) {
+__host__ __device__ __forceinline__ TileHdr tile_hdr(const ConvPlan& p) {
   TileHdr h;
   h.ncols = p.ncols;
   h.stride = p.stride;
@@ -693,12 +693,14 @@ struct TileSlot {
   unsigned int staged;  // records of a staged tile; 0: the tile runs directly
 };
 
+// A stage's table in shared memory: the layout of StageRec, read as uint4.
 struct StageDesc {
   TileHdr h;
-  unsigned int pad;
-  unsigned int job;
+  unsigned int pad[4];
   uint4 d[MRN_MAX_COLS];
 };
+static_assert(sizeof(StageDesc) == sizeof(StageRec), "a stage table is a StageRec");
+static_assert(sizeof(StageDesc) % 16 == 0, "stage tables are whole bulk copies");
 
 struct StoreItem {
   unsigned long long local;
@@ -720,7 +722,8 @@ constexpr size_t kBNumBars = 2 * kBNS + 2 * kBND + 2 * kRing + 1;
 constexpr size_t kBOffRing = kBOffBar + kBNumBars * 8;
 constexpr size_t kBOffSQ = kBOffRing + kRing * sizeof(TileSlot);
 constexpr size_t kBOffFlag = kBOffSQ + kSQ * sizeof(StoreItem);
-constexpr size_t kBatchSmem = kBOffFlag + 16;
+constexpr size_t kBOffSJob = kBOffFlag + 16;
+constexpr size_t kBatchSmem = kBOffSJob + 16;
 
 struct BatchSmem {
   char* base;
@@ -751,6 +754,8 @@ struct BatchSmem {
   // [0] abort, [1] loader finished, [2] staged tiles issued in total,
   // [3] tiles decided so far (the storer's sign that the loader is alive)
   __device__ __forceinline__ volatile int* flags() const { return reinterpret_cast<volatile int*>(base + kBOffFlag); }
+  // the job whose table each stage holds (the loader's own record)
+  __device__ __forceinline__ unsigned int* sjob() const { return reinterpret_cast<unsigned int*>(base + kBOffSJob); }
 };
 
 __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
@@ -783,14 +788,19 @@ __device__ __forceinline__ uint32_t side_tile_bytes(const ConvPlan& p, const Sid
 
 // Warp-wide bulk loads of the first R records of source tile lt: lane 0
 // sets the transaction count, then lane c copies SoA column c (lane 0
-// copies an AoS / AoSoA tile, which is one range).
+// copies an AoS / AoSoA tile, which is one range).  With `rec`, lane 0
+// also copies that stage table into `table` on the same barrier.
 __device__ __forceinline__ void tma_load_tile_warp(const ConvPlan& p, uint64_t lt, uint32_t R, char* stage,
-                                                   unsigned long long* bar, int lane) {
+                                                   unsigned long long* bar, int lane, const StageRec* rec,
+                                                   StageDesc* table) {
   const TileGeom& g = p.tg;
   const uint64_t t0 = lt * g.T;
   const SidePlan& sp = p.src;
   const uint32_t bytes = side_tile_bytes(p, sp, g.src_bytes, R);
-  if (lane == 0) mbar_expect_tx(bar, bytes);
+  if (lane == 0) {
+    mbar_expect_tx(bar, bytes + (rec ? (uint32_t)sizeof(StageRec) : 0u));
+    if (rec) bulk_g2s(table, rec, (uint32_t)sizeof(StageRec), bar);
+  }
   __syncwarp();
   if (sp.kind == K_AOS) {
     if (lane == 0) bulk_g2s(stage, sp.base + t0 * p.stride, bytes, bar);
@@ -821,30 +831,42 @@ __device__ __forceinline__ void tma_store_tile_warp(const ConvPlan& p, uint64_t 
   bulk_commit();
 }
 
-// Loader warp: the plan's column descriptors and header into stage s's
-// table (lane c writes column c), copied from another stage when one holds
-// the same job's.
-__device__ __forceinline__ void fill_stage_desc(const ConvPlan& p, const BatchSmem& m, uint32_t s,
-                                                unsigned int job, int lane) {
+// Loader warp, one conversion per launch: the plan's column descriptors and
+// header into stage s's table (lane c writes column c).
+__device__ __forceinline__ void fill_stage_desc(const ConvPlan& p, const BatchSmem& m, uint32_t s, int lane) {
   StageDesc* sd = m.desc(s);
-  if (sd->job == job) return;
-  // another stage may already hold this job's table: copy it in shared memory
-  for (uint32_t q = 0; q < kBNS; ++q) {
-    const StageDesc* o = m.desc(q);
-    if (q == s || o->job != job) continue;
-    for (uint32_t c = lane; c < o->h.ncols; c += 32) sd->d[c] = o->d[c];
-    __syncwarp();
-    if (lane == 0) {
-      sd->h = o->h;
-      sd->job = job;
-    }
-    return;
-  }
   for (uint32_t c = lane; c < p.ncols; c += 32) sd->d[c] = tile_desc(p, c);
-  __syncwarp();
-  if (lane != 0) return;
-  sd->h = tile_hdr(p);
-  sd->job = job;
+  if (lane == 0) sd->h = tile_hdr(p);
+}
+
+static_assert(sizeof(BatchJob) % 16 == 0, "a job descriptor is one whole L2 prefetch");
+
+// The job of tile t: the last job j >= cur with first_tile[j] <= t, given
+// first_tile[cur] <= t (jobs without tiles are passed over).  Gallops from
+// cur, then bisects, so that the next tile's job costs one or two loads and
+// a jump over many jobs a logarithmic number.
+__device__ __forceinline__ unsigned int advance_job(const unsigned long long* __restrict__ first_tile,
+                                                    unsigned int njobs, unsigned int cur, uint64_t t) {
+  if (cur + 1 >= njobs || __ldg(first_tile + cur + 1) > t) return cur;
+  unsigned int lo = cur + 1, hi = njobs, step = 1;  // first_tile[lo] <= t < first_tile[hi]
+  for (;;) {
+    const unsigned int nx = lo + step;
+    if (nx >= njobs) break;
+    if (__ldg(first_tile + nx) > t) {
+      hi = nx;
+      break;
+    }
+    lo = nx;
+    step <<= 1;
+  }
+  while (hi - lo > 1) {
+    const unsigned int mid = lo + (hi - lo) / 2;
+    if (__ldg(first_tile + mid) <= t)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
 }
 
 // Loader warp, on taking tiles [t0, t1): publishes the child count of each
@@ -857,9 +879,12 @@ __device__ __forceinline__ void publish_jagged_sums(const BatchJob* __restrict__
                                                     unsigned long long* states, uint64_t t0, uint64_t t1,
                                                     unsigned int* cursor, int lane) {
   for (uint64_t t = t0; t < t1 && t < total_tiles; ++t) {
-    while (*cursor + 1 < njobs && __ldg(first_tile + *cursor + 1) <= t) ++*cursor;
+    *cursor = advance_job(first_tile, njobs, *cursor, t);
     const BatchJob& J = jobs[*cursor];
-    if (J.kind != JOB_JAG_A2S) continue;
+    if (J.kind != JOB_JAG_A2S) {
+      t = J.tile_begin + J.ntiles - 1;  // the job's other tiles publish nothing either
+      continue;
+    }
     const JagPlan& jp = J.jp;
     const uint64_t local = t - J.tile_begin;
     const uint64_t r0 = local * MRN_JAG_TILE, n = jp.parent.n;
@@ -889,6 +914,7 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
   unsigned int pcursor = 0;
   uint32_t n_chunks = 0;  // static assignment: chunks taken so far
   uint64_t seen = 0;      // dynamic assignment: end of the last chunk taken
+  uint64_t snap = 0;      // the counter, read while deciding a chunk's last tile
   bool have = false;
   TileSlot cand;
   cand.t = 0;
@@ -903,28 +929,36 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
           chunk_end = next_t + chunk;
         } else {
           // guided chunks: up to `chunk` tiles, fewer as the tiles run out
-          // (about half the remaining tiles' share per CTA), so the CTAs
-          // finish together; the counter counts tiles, handed out in
-          // increasing order
+          // (the remaining tiles' share per CTA), so the CTAs finish
+          // together; the counter counts tiles, handed out in increasing
+          // order.  The remaining tiles are judged by the counter as it
+          // stood when the last chunk's last tile was decided: this CTA's
+          // own last chunk says little about the others'.
           unsigned int start = 0, size = 0;
           if (lane == 0) {
+            seen = max(seen, snap);
             const unsigned long long rem = total_tiles > seen ? total_tiles - seen : 0ull;
-            const unsigned long long share = rem / (2ull * gridDim.x);
+            const unsigned long long share = rem / (1ull * gridDim.x);
             size = (unsigned int)(share < 1ull ? 1ull : (share > chunk ? (unsigned long long)chunk : share));
             start = atomicAdd(counter, size);
           }
           next_t = __shfl_sync(0xffffffffu, start, 0);
           chunk_end = next_t + __shfl_sync(0xffffffffu, size, 0);
           seen = chunk_end;
-          publish_jagged_sums(jobs, first_tile, njobs, total_tiles, states, next_t, chunk_end, &pcursor, lane);
+          if (states)  // a batch without jagged AoS -> SoA jobs publishes nothing
+            publish_jagged_sums(jobs, first_tile, njobs, total_tiles, states, next_t, chunk_end, &pcursor, lane);
         }
       }
+      // read early, so that the load's latency hides behind this tile's
+      // stage wait
+      if constexpr (!kStatic)
+        if (lane == 0 && next_t + 1 == chunk_end) snap = ld_relaxed_u32(counter);
       cand.t = next_t++;
       cand.staged = 0;
       cand.job = 0;
       cand.local = 0;
       if (cand.t < total_tiles) {
-        while (cursor + 1 < njobs && __ldg(first_tile + cursor + 1) <= cand.t) ++cursor;
+        if constexpr (!kStatic) cursor = advance_job(first_tile, njobs, cursor, cand.t);
         const BatchJob& J = jobs[cursor];
         cand.job = cursor;
         cand.local = cand.t - J.tile_begin;
@@ -954,9 +988,20 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
           it.records = cand.staged;
           *m.sq(c_issue % kSQ) = it;
         }
-        fill_stage_desc(P, m, s, cand.job, lane);
+        // the stage's table changes with the job: one conversion's is
+        // written in place (first use of each stage), a batch job's comes
+        // from its record with the tile's data
+        const StageRec* rec = nullptr;
+        if (m.sjob()[s] != cand.job) {
+          if constexpr (kStatic)
+            fill_stage_desc(P, m, s, lane);
+          else
+            rec = &jobs[cand.job].stage;
+          __syncwarp();
+          if (lane == 0) m.sjob()[s] = cand.job;
+        }
         __syncwarp();
-        tma_load_tile_warp(P, cand.local, cand.staged, m.src(s), m.full(s), lane);
+        tma_load_tile_warp(P, cand.local, cand.staged, m.src(s), m.full(s), lane, rec, m.desc(s));
         ++c_issue;
       }
       if (lane == 0) {
@@ -1047,11 +1092,22 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
                                            unsigned long long* states, uint32_t chunk, char* batch_smem) {
   BatchSmem m{batch_smem};
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if constexpr (!kStatic) {
+    // the first tiles' job descriptors and the job index are read in a
+    // chain of dependent loads: bring them into L2 while the CTA starts
+    // (CTA b fetches job b; CTA 0 the tile index of the jobs)
+    if (warp == 9 && lane == 0) {
+      if (blockIdx.x < njobs) bulk_prefetch_l2(jobs + blockIdx.x, (uint32_t)sizeof(BatchJob));
+      if (blockIdx.x == 0)
+        for (uint32_t q = 0; q < njobs; q += 2048)
+          bulk_prefetch_l2(first_tile + q, (min(njobs - q, 2048u) * 8 + 15) & ~15u);
+    }
+  }
   if (tid == 0) {
     for (uint32_t s = 0; s < kBNS; ++s) {
       mbar_init(m.full(s), 1);
       mbar_init(m.empty(s), 8);
-      m.desc(s)->job = 0xffffffffu;
+      m.sjob()[s] = 0xffffffffu;
     }
     for (uint32_t d = 0; d < kBND; ++d) {
       mbar_init(m.done(d), 8);
@@ -1304,6 +1360,18 @@ int launch_zero_gaps(const GapPlan& g, void* stream) {
   const unsigned grid = (unsigned)std::min<uint64_t>((total + 255) / 256, 4096);
   k_zero_gaps<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(g);
   return cuda_status(cudaGetLastError());
+}
+
+void fill_stage_rec(const ConvPlan& p, StageRec* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->h = tile_hdr(p);
+  for (uint32_t c = 0; c < p.ncols; ++c) {
+    const uint4 d = tile_desc(p, c);
+    out->d[c][0] = d.x;
+    out->d[c][1] = d.y;
+    out->d[c][2] = d.z;
+    out->d[c][3] = d.w;
+  }
 }
 
 uint64_t jagged_scratch_bytes(uint64_t n) {

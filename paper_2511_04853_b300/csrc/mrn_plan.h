@@ -52,6 +52,29 @@ struct TileGeom {
   uint8_t order[MRN_MAX_COLS];     // data columns by decreasing size (stable)
 };
 
+// The fields of a plan the staged transform reads, copied into shared memory
+// next to the column descriptors.  Each side of a tile is described by one
+// row geometry, whatever its layout: record r lies in row block
+// r >> shift (r / block when shift is MRN_NO_SHIFT) at byte bb * row block,
+// slot r - block * row block.  AoS: block 1, shift 0, bb = stride (every
+// record its own row, slot 0); SoA: shift 31 (one row, slot r); AoSoA(B):
+// block B, bb = block bytes.
+struct TileHdr {
+  uint32_t ncols, stride, vec, pad, T, nsize;
+  uint32_t sblock, sshift, sbb;  // source row geometry
+  uint32_t dblock, dshift, dbb;  // destination row geometry
+};
+
+// What the consumers of a staged tile read: the header and one descriptor
+// per column in size-class order {size, source offset, destination offset,
+// 0}.  A batch job carries its own, built on the host, and the loader brings
+// it into a stage's table with one bulk copy beside the tile's data.
+struct alignas(16) StageRec {
+  TileHdr h;
+  uint32_t pad[4];
+  uint32_t d[MRN_MAX_COLS][4];
+};
+
 struct ConvPlan {
   uint64_t n;          // records
   uint64_t n_fm_pad;   // records written on the destination (AoSoA: N rounded up to B)
@@ -147,4 +170,5 @@ struct BatchJob {
     JagPlan jp;                 // JOB_CONVERT uses jp.parent
     GapPlan gp;                 // JOB_ZERO
   };
+  StageRec stage;               // JOB_CONVERT with staged tiles: jp.parent's stage table
 };
