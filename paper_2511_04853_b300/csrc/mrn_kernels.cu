@@ -842,29 +842,23 @@ __device__ __forceinline__ void fill_stage_desc(const ConvPlan& p, const BatchSm
 static_assert(sizeof(BatchJob) % 16 == 0, "a job descriptor is one whole L2 prefetch");
 
 // The job of tile t: the last job j >= cur with first_tile[j] <= t, given
-// first_tile[cur] <= t (jobs without tiles are passed over).  Gallops from
-// cur, then bisects, so that the next tile's job costs one or two loads and
-// a jump over many jobs a logarithmic number.
+// first_tile[cur] <= t (jobs without tiles are passed over).  Called by a
+// whole warp: the next job is one load; a jump over many jobs is a 32-way
+// search, each round one coalesced load of 32 tile starts, so a CTA's first
+// chunk finds its job in one or two round trips instead of a chain.
 __device__ __forceinline__ unsigned int advance_job(const unsigned long long* __restrict__ first_tile,
-                                                    unsigned int njobs, unsigned int cur, uint64_t t) {
+                                                    unsigned int njobs, unsigned int cur, uint64_t t,
+                                                    int lane) {
   if (cur + 1 >= njobs || __ldg(first_tile + cur + 1) > t) return cur;
-  unsigned int lo = cur + 1, hi = njobs, step = 1;  // first_tile[lo] <= t < first_tile[hi]
-  for (;;) {
-    const unsigned int nx = lo + step;
-    if (nx >= njobs) break;
-    if (__ldg(first_tile + nx) > t) {
-      hi = nx;
-      break;
-    }
-    lo = nx;
-    step <<= 1;
-  }
+  unsigned int lo = cur + 1, hi = njobs;  // first_tile[lo] <= t < first_tile[hi]
   while (hi - lo > 1) {
-    const unsigned int mid = lo + (hi - lo) / 2;
-    if (__ldg(first_tile + mid) <= t)
-      lo = mid;
-    else
-      hi = mid;
+    const unsigned int step = (hi - lo + 31) / 32;
+    const unsigned int j = lo + (unsigned int)lane * step;
+    const bool le = j < hi && __ldg(first_tile + j) <= t;
+    const unsigned int mask = __ballot_sync(0xffffffffu, le);  // lane 0 (j = lo) is set
+    const unsigned int k = 31u - (unsigned int)__clz(mask);
+    lo += k * step;
+    hi = min(hi, lo + step);
   }
   return lo;
 }
@@ -879,7 +873,7 @@ __device__ __forceinline__ void publish_jagged_sums(const BatchJob* __restrict__
                                                     unsigned long long* states, uint64_t t0, uint64_t t1,
                                                     unsigned int* cursor, int lane) {
   for (uint64_t t = t0; t < t1 && t < total_tiles; ++t) {
-    *cursor = advance_job(first_tile, njobs, *cursor, t);
+    *cursor = advance_job(first_tile, njobs, *cursor, t, lane);
     const BatchJob& J = jobs[*cursor];
     if (J.kind != JOB_JAG_A2S) {
       t = J.tile_begin + J.ntiles - 1;  // the job's other tiles publish nothing either
@@ -906,7 +900,8 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
                                              const unsigned long long* __restrict__ first_tile,
                                              unsigned int njobs, unsigned long long total_tiles,
                                              unsigned int* counter, unsigned long long* states,
-                                             uint32_t chunk, const BatchSmem& m, int lane) {
+                                             uint32_t chunk, unsigned int first_start, unsigned int first_size,
+                                             const BatchSmem& m, int lane) {
   uint64_t k_issue = 0;  // tiles decided
   uint32_t c_issue = 0;  // staged tiles loaded
   unsigned int cursor = 0;
@@ -923,7 +918,7 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
     if (m.flags()[0]) break;
     if (!have) {
       if (next_t == chunk_end) {
-        if constexpr (kStatic) {
+        if (kStatic && !counter) {
           next_t = ((uint64_t)n_chunks * gridDim.x + blockIdx.x) * chunk;
           ++n_chunks;
           chunk_end = next_t + chunk;
@@ -935,7 +930,11 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
           // stood when the last chunk's last tile was decided: this CTA's
           // own last chunk says little about the others'.
           unsigned int start = 0, size = 0;
-          if (lane == 0) {
+          if (lane == 0 && first_size) {  // taken at entry (lane 0's values)
+            start = first_start;
+            size = first_size;
+            first_size = 0;
+          } else if (lane == 0) {
             seen = max(seen, snap);
             const unsigned long long rem = total_tiles > seen ? total_tiles - seen : 0ull;
             const unsigned long long share = rem / (1ull * gridDim.x);
@@ -951,14 +950,13 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
       }
       // read early, so that the load's latency hides behind this tile's
       // stage wait
-      if constexpr (!kStatic)
-        if (lane == 0 && next_t + 1 == chunk_end) snap = ld_relaxed_u32(counter);
+      if (counter && lane == 0 && next_t + 1 == chunk_end) snap = ld_relaxed_u32(counter);
       cand.t = next_t++;
       cand.staged = 0;
       cand.job = 0;
       cand.local = 0;
       if (cand.t < total_tiles) {
-        if constexpr (!kStatic) cursor = advance_job(first_tile, njobs, cursor, cand.t);
+        if constexpr (!kStatic) cursor = advance_job(first_tile, njobs, cursor, cand.t, lane);
         const BatchJob& J = jobs[cursor];
         cand.job = cursor;
         cand.local = cand.t - J.tile_begin;
@@ -1103,30 +1101,37 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
           bulk_prefetch_l2(first_tile + q, (min(njobs - q, 2048u) * 8 + 15) & ~15u);
     }
   }
-  if (tid == 0) {
-    for (uint32_t s = 0; s < kBNS; ++s) {
-      mbar_init(m.full(s), 1);
-      mbar_init(m.empty(s), 8);
-      m.sjob()[s] = 0xffffffffu;
+  // warp 0 initializes the barriers, one per lane
+  if (warp == 0) {
+    constexpr uint32_t kBars = 2 * kBNS + 2 * kBND + 2 * kRing + 1;
+    static_assert(kBars <= 32, "one barrier per lane");
+    if ((uint32_t)lane < kBars) {
+      const uint32_t i = lane;
+      uint32_t count;
+      if (i < kBNS) count = 1;                                  // full
+      else if (i < 2 * kBNS) count = 8;                         // empty
+      else if (i < 2 * kBNS + kBND) count = 8;                  // done
+      else if (i < 2 * kBNS + 2 * kBND) count = 1;              // dfree
+      else if (i < 2 * kBNS + 2 * kBND + kRing) count = 1;      // ready
+      else count = 8;                                           // rel, cbar
+      mbar_init(m.bar(i), count);
+      fence_mbar_init();
     }
-    for (uint32_t d = 0; d < kBND; ++d) {
-      mbar_init(m.done(d), 8);
-      mbar_init(m.dfree(d), 1);
-    }
-    for (uint32_t i = 0; i < kRing; ++i) {
-      mbar_init(m.ready(i), 1);
-      mbar_init(m.rel(i), 8);
-    }
-    mbar_init(m.cbar(), 8);
-    m.flags()[0] = 0;
-    m.flags()[1] = 0;
-    m.flags()[2] = 0;
-    m.flags()[3] = 0;
-    fence_mbar_init();
+    if ((uint32_t)lane < kBNS) m.sjob()[lane] = 0xffffffffu;
+    if (lane < 4) m.flags()[lane] = 0;
+  }
+  // the loader takes its first chunk now, so that the atomic's round trip
+  // overlaps the barrier set-up
+  unsigned int first_start = 0, first_size = 0;
+  if (warp == 8 && lane == 0 && counter) {
+    const unsigned long long share = total_tiles / gridDim.x;
+    first_size = (unsigned int)(share < 1ull ? 1ull : (share > chunk ? (unsigned long long)chunk : share));
+    first_start = atomicAdd(counter, first_size);
   }
   __syncthreads();
   if (warp == 8) {
-    batch_loader<kStatic>(jobs, first_tile, njobs, total_tiles, counter, states, chunk, m, lane);
+    batch_loader<kStatic>(jobs, first_tile, njobs, total_tiles, counter, states, chunk, first_start, first_size, m,
+                          lane);
     return;
   }
   if (warp == 9) {
@@ -1212,12 +1217,14 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
 }
 
 // One staged conversion through the same warp-specialized pipeline: the
-// job travels as a kernel parameter and chunk c of tiles belongs to CTA
-// c % gridDim.x (no scratch, no counter; the job has no jagged tiles).
+// job travels as a kernel parameter (it has no jagged tiles).  Without a
+// counter, chunk c of tiles belongs to CTA c % gridDim.x; with one (a
+// zeroed word), chunks are guided as in a batch, so that CTAs that run
+// faster take more of them.
 __global__ void __launch_bounds__(kBThreads, 3) k_convert_ws(const __grid_constant__ BatchJob job,
-                                                             uint32_t chunk) {
+                                                             uint32_t chunk, unsigned int* counter) {
   extern __shared__ __align__(128) char batch_smem[];
-  batch_main<true>(&job, nullptr, 1u, job.ntiles, nullptr, nullptr, chunk, batch_smem);
+  batch_main<true>(&job, nullptr, 1u, job.ntiles, counter, nullptr, chunk, batch_smem);
 }
 
 // ================================================================== host
@@ -1308,6 +1315,9 @@ void allow_batch_smem(const void* fn) {
   done.emplace_back(fn, dev);
 }
 
+// Tiles per CTA from which a single staged conversion takes guided chunks.
+constexpr uint64_t kDynamicTilesPerCta = 32;
+
 // Tiles per chunk by default: up to 8 (fewer job switches per CTA), but
 // small enough that every CTA of the grid gets about four chunks.
 uint32_t chunk_for(uint64_t tiles, uint64_t ctas) {
@@ -1331,12 +1341,31 @@ int launch_convert(const ConvPlan& p, void* stream, const LaunchShape* shape) {
     const int occ = occupancy(fn, kBThreads, kBatchSmem);
     const int per_sm = sh.ctas_per_sm ? std::min((int)sh.ctas_per_sm, occ) : occ;
     const uint64_t cap = (uint64_t)device_sm_count() * (uint64_t)per_sm;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint32_t chunk = chunk_for(job.ntiles, cap);
+    unsigned int* counter = nullptr;
+    // Large conversions take guided chunks from a counter: CTAs do not all
+    // run at the same speed, and a static split leaves the fast ones idle
+    // at the end.  The counter costs an allocation and a memset, which
+    // conversions of fewer than kDynamicTilesPerCta tiles per CTA do not
+    // earn back.
+    if (job.ntiles >= kDynamicTilesPerCta * cap) {
+      if (cudaMallocAsync(reinterpret_cast<void**>(&counter), 256, st) != cudaSuccess) {
+        cudaGetLastError();
+        counter = nullptr;
+      } else if (cudaMemsetAsync(counter, 0, sizeof(unsigned int), st) != cudaSuccess) {
+        cudaFreeAsync(counter, st);
+        return MRN_ECUDA;
+      } else {
+        chunk = (uint32_t)kChunk;
+      }
+    }
     const uint64_t chunks = (job.ntiles + chunk - 1) / chunk;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(chunks, cap));
-    void* args[] = {&job, &chunk};
-    return cuda_status(cudaLaunchKernel(fn, dim3(grid), dim3(kBThreads), args, kBatchSmem,
-                                        static_cast<cudaStream_t>(stream)));
+    void* args[] = {&job, &chunk, &counter};
+    const int rc = cuda_status(cudaLaunchKernel(fn, dim3(grid), dim3(kBThreads), args, kBatchSmem, st));
+    if (counter) cudaFreeAsync(counter, st);
+    return rc;
   }
   if (sh.threads != 64 && sh.threads != 128 && sh.threads != 256) sh.threads = 256;
   if (sh.tile_records == 0 || sh.tile_records % 32) sh.tile_records = sh.threads * 2;

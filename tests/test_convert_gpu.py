@@ -167,3 +167,14 @@ def test_staged_tiles_and_tail(n):
                                (("aosoa", 32), ("aos", 0))]:
         check_pair("cells", n, sk, sb, dk, db, seed=7)
         check_pair("points", n, sk, sb, dk, db, seed=7)
+
+
+@pytest.mark.parametrize("name,n", [("cells", 7_300_033), ("points", 5_500_017)])
+def test_large_staged_conversions(name, n):
+    """Conversions of at least 32 staged tiles per resident CTA (on a
+    148-SM GPU: 7,274,496 cell or 5,455,872 point records) take guided
+    chunks from a counter instead of a static split; a ragged size also
+    ends in a partial tile."""
+    for (sk, sb), (dk, db) in [(("aos", 0), ("soa", 0)), (("soa", 0), ("aosoa", 128)),
+                               (("aosoa", 32), ("aos", 0))]:
+        check_pair(name, n, sk, sb, dk, db, seed=11)
