@@ -392,6 +392,80 @@ int mrn_server_stats_get(mrn_server* sv, mrn_server_stats* out);
 /* Drains outstanding requests, stops the thread, frees device memory. */
 void mrn_server_destroy(mrn_server* sv);
 
+/* ---------------------------------------------------- overlapping moves */
+/* Moves `bytes` bytes from src to dst inside one memory context, where the
+ * two ranges may overlap (the partially overlapping memcopy of Sec. VI-A,
+ * used to open or close a gap for insertion and deletion): afterwards dst
+ * holds what src held before.  MRN_MEM_DEVICE: both ranges on the current
+ * device, asynchronous on `stream`, one kernel that reads each chunk before
+ * any chunk overlapping it is written (each wait bounded; MRN_ETIMEOUT is
+ * recorded if one expires).  MRN_MEM_HOST / MRN_MEM_HOST_PINNED: a host
+ * memmove once `stream` is idle. */
+int mrn_memmove(void* dst, const void* src, uint64_t bytes, int mem, void* stream);
+
+/* ------------------------------------------------------------ collections */
+/* A library-owned collection (Sec. VI-A memory contexts, Sec. VI-B layout
+ * holders): one schema, one layout and one memory context, storage for
+ * `capacity` objects (and, for a jagged schema, `child_capacity` child
+ * values), and the current sizes n <= capacity and m <= child_capacity.
+ * Storage per layout:
+ *   AoS: capacity records (jagged: plus a child pool of child_capacity child
+ *        records; the parents' {length, begin} index into it);
+ *   SoA: one block laid out as the single-block SoA for (capacity,
+ *        child_capacity) -- data columns, offsets, child columns;
+ *   AoSoA(B): ceil(capacity / B) blocks (jagged: then offsets and child
+ *        columns, as the single-block jagged AoSoA for the capacities).
+ * Every field-major jagged collection keeps offsets[0] == 0 and
+ * m == offsets[n].  Objects a resize adds are all-zero (jagged: no
+ * children).  Unused AoSoA slots of the last block stay zero.
+ * Memory contexts: MRN_MEM_DEVICE (device `device`; moves and fills run
+ * in kernels on `stream`), MRN_MEM_HOST_PINNED and MRN_MEM_HOST (moves and
+ * fills on the host once `stream` is idle; conversions into them go
+ * through mrn_transfer_convert, which needs MRN_MEM_HOST_PINNED).
+ * A collection is not internally synchronised. */
+typedef struct mrn_collection mrn_collection; /* opaque */
+
+int mrn_collection_create(const mrn_schema* s, mrn_layout layout, int mem, int device, uint64_t capacity,
+                          uint64_t child_capacity, mrn_collection** out);
+void mrn_collection_destroy(mrn_collection* c);
+/* A view of the current contents (n objects, m children).  Its pointer
+ * arrays belong to the collection and stay valid until the next call that
+ * reallocates (reserve, a growing resize / insert / assign, shrink_to_fit,
+ * set_context) or destroy. */
+int mrn_collection_view(const mrn_collection* c, mrn_view* out);
+int mrn_collection_sizes(const mrn_collection* c, uint64_t* n, uint64_t* m, uint64_t* capacity,
+                         uint64_t* child_capacity);
+/* Grows the capacities (never shrinks them): new storage in the same
+ * context, the contents copied over, the old storage freed. */
+int mrn_collection_reserve(mrn_collection* c, uint64_t capacity, uint64_t child_capacity, void* stream);
+/* Sets n.  Growing appends all-zero objects (capacity doubled as needed);
+ * shrinking drops the last objects (jagged: and their children). */
+int mrn_collection_resize(mrn_collection* c, uint64_t n, void* stream);
+int mrn_collection_clear(mrn_collection* c, void* stream);
+/* Reallocates to capacity n and child capacity m. */
+int mrn_collection_shrink_to_fit(mrn_collection* c, void* stream);
+/* Removes objects [first, first + count) (jagged: with their children; the
+ * later offsets drop by the children removed).  AoS and SoA collections,
+ * and jagged AoS (the children stay in the pool, unreferenced); AoSoA:
+ * MRN_EUNSUPPORTED.  A field-major jagged erase waits for `stream` to read
+ * two offsets. */
+int mrn_collection_erase(mrn_collection* c, uint64_t first, uint64_t count, void* stream);
+/* Inserts the objects of `src` (same schema; any layout, any context
+ * mrn_convert or mrn_transfer_convert accepts against this collection's)
+ * before object `pos`: the tail moves up, then src is converted into the
+ * gap.  AoS and SoA collections, and jagged SoA; other layouts:
+ * MRN_EUNSUPPORTED.  A jagged insert waits for `stream` (offsets, and the
+ * child count of an AoS source). */
+int mrn_collection_insert(mrn_collection* c, uint64_t pos, const mrn_view* src, void* stream);
+/* Replaces the contents with those of `src` (same schema, any layout),
+ * converted into this collection's layout (copy assignment between
+ * layouts, Sec. VI-B). */
+int mrn_collection_assign(mrn_collection* c, const mrn_view* src, void* stream);
+/* Moves the collection to another memory context (update of the memory
+ * context information, Sec. VI-A): new storage there with the same
+ * capacities and layout, the contents copied, the old storage freed. */
+int mrn_collection_set_context(mrn_collection* c, int mem, int device, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

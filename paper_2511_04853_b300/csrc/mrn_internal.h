@@ -113,6 +113,21 @@ int launch_jagged_a2s(JagPlan& jp, void* scratch, void* stream);
 int launch_jagged_s2a(const JagPlan& jp, void* stream);
 int launch_jagged_count(const ConvPlan& parent, uint64_t* dev_total, void* stream);
 
+// Moves of byte ranges inside device memory whose source and destination
+// may overlap (disjoint ones become plain copies); with elem (4 or 8) the
+// range holds unsigned integers and delta is added to each.  Ranges must not
+// overlap one another.
+struct MoveRange {
+  const char* src;
+  char* dst;
+  uint64_t bytes;
+  uint32_t elem;
+  long long delta;
+};
+int launch_moves(const MoveRange* r, size_t n, void* stream);
+// count unsigned integers of elem bytes at dst = the one at `from`.
+int launch_fill_from(char* dst, const char* from, uint64_t count, uint32_t elem, void* stream);
+
 // Persistent launch of a batch (mrn_batch.cpp owns the device tables);
 // max_chunk caps the consecutive tiles a CTA takes at once.
 int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, unsigned int njobs,

@@ -1525,3 +1525,247 @@ int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, uns
 }
 
 }  // namespace mrn
+
+// ------------------------------------------------ overlapping moves
+
+
+// One range of an overlapping move: `bytes` bytes from src to dst, read and
+// written `w` bytes at a time.  With elem (4 or 8) the range holds unsigned
+// integers of that size and `delta` is added to each as it moves (jagged
+// offsets after an insertion or deletion).
+struct MoveSeg {
+  const char* src;
+  char* dst;
+  uint64_t bytes;
+  uint64_t chunk_begin;  // first chunk of this range among the launch's chunks
+  uint64_t nchunks;
+  long long delta;
+  uint32_t w;
+  uint32_t elem;
+  uint32_t up;  // 1: dst above src; chunks are taken from the top down
+  uint32_t pad;
+};
+
+constexpr uint32_t kMoveSegs = 136;     // a schema's 64 columns, offsets, 64 child columns
+constexpr uint32_t kMoveThreads = 256;
+constexpr uint32_t kMoveVec = 4;        // accesses per thread per chunk
+
+struct MovePlan {
+  MoveSeg seg[kMoveSegs];
+  uint32_t nseg;
+  uint32_t pad;
+  uint64_t total_chunks;
+  unsigned int* counter;  // chunk tickets
+  unsigned int* flags;    // per chunk: 1 once its source has been read
+  unsigned long long timeout_ns;
+};
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const unsigned int* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned int* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <int W>
+struct MoveWord;
+template <> struct MoveWord<1> { using T = uint8_t; };
+template <> struct MoveWord<2> { using T = uint16_t; };
+template <> struct MoveWord<4> { using T = uint32_t; };
+template <> struct MoveWord<8> { using T = unsigned long long; };
+template <> struct MoveWord<16> { using T = uint4; };
+
+// Read phase: the chunk's source words into shared memory (the stores there
+// consume the loads, so the reads are complete at the barrier that follows).
+template <int W>
+__device__ __forceinline__ void move_read(const MoveSeg& S, uint64_t lo, uint64_t hi, unsigned char* buf) {
+  using T = typename MoveWord<W>::T;
+  const T* src = reinterpret_cast<const T*>(S.src + lo);
+  T* b = reinterpret_cast<T*>(buf);
+  const uint64_t nw = (hi - lo) / W;
+#pragma unroll
+  for (uint32_t i = 0; i < kMoveVec; ++i) {
+    const uint64_t k = threadIdx.x + (uint64_t)i * kMoveThreads;
+    if (k < nw) b[k] = src[k];
+  }
+}
+
+template <int W>
+__device__ __forceinline__ void move_write(const MoveSeg& S, uint64_t lo, uint64_t hi, const unsigned char* buf) {
+  using T = typename MoveWord<W>::T;
+  T* dst = reinterpret_cast<T*>(S.dst + lo);
+  const T* b = reinterpret_cast<const T*>(buf);
+  const uint64_t nw = (hi - lo) / W;
+#pragma unroll
+  for (uint32_t i = 0; i < kMoveVec; ++i) {
+    const uint64_t k = threadIdx.x + (uint64_t)i * kMoveThreads;
+    if (k < nw) {
+      T v = b[k];
+      if constexpr (W == 4 || W == 8)
+        if (S.elem) v = (T)(v + (T)S.delta);
+      dst[k] = v;
+    }
+  }
+}
+
+// Waits until every chunk of S whose source overlaps [a, b) (the
+// destination of chunk p) has been read; those chunks hold earlier tickets.
+__device__ bool move_wait_sources(const MovePlan& P, const MoveSeg& S, uint64_t p, uint64_t CB, uintptr_t a,
+                                  uintptr_t b) {
+  const uintptr_t s0 = reinterpret_cast<uintptr_t>(S.src), s1 = s0 + S.bytes;
+  if (b <= s0 || a >= s1) return true;
+  const uint64_t q0 = (uint64_t)((a > s0 ? a : s0) - s0) / CB;
+  const uint64_t q1 = (uint64_t)((b < s1 ? b : s1) - 1 - s0) / CB;
+  const unsigned long long deadline = global_ns() + P.timeout_ns;
+  for (uint64_t q = q0; q <= q1; ++q) {
+    if (q == p) continue;
+    const uint64_t c = S.chunk_begin + (S.up ? S.nchunks - 1 - q : q);
+    for (uint32_t i = 0; ld_acquire_u32(P.flags + c) == 0; ++i) {
+      if ((i & 63) == 63 && global_ns() > deadline) return false;
+      __nanosleep(64);
+    }
+  }
+  return true;
+}
+
+// Persistent grid: each CTA takes chunks by ticket (chunks of a range in
+// the order that makes every overlap point back to an earlier ticket), reads
+// one into shared memory, marks it read, waits for the chunks its
+// destination overlaps to have been read, then writes it.  A chunk's read
+// never waits, so the chunks a CTA waits for always finish their reads.
+__global__ void __launch_bounds__(kMoveThreads) k_move(const __grid_constant__ MovePlan P) {
+  __shared__ __align__(16) unsigned char buf[kMoveThreads * kMoveVec * 16];
+  __shared__ unsigned long long s_chunk;
+  __shared__ int s_ok;
+  for (;;) {
+    if (threadIdx.x == 0) s_chunk = atomicAdd(P.counter, 1u);
+    __syncthreads();
+    const uint64_t c = s_chunk;
+    if (c >= P.total_chunks) return;
+    uint32_t si = 0;
+    while (si + 1 < P.nseg && P.seg[si + 1].chunk_begin <= c) ++si;
+    const MoveSeg& S = P.seg[si];
+    const uint64_t k = c - S.chunk_begin;
+    const uint64_t p = S.up ? S.nchunks - 1 - k : k;
+    const uint64_t CB = (uint64_t)kMoveThreads * kMoveVec * S.w;
+    const uint64_t lo = p * CB, hi = min(lo + CB, S.bytes);
+    switch (S.w) {
+      case 16: move_read<16>(S, lo, hi, buf); break;
+      case 8: move_read<8>(S, lo, hi, buf); break;
+      case 4: move_read<4>(S, lo, hi, buf); break;
+      case 2: move_read<2>(S, lo, hi, buf); break;
+      default: move_read<1>(S, lo, hi, buf); break;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      st_release_u32(P.flags + c, 1u);
+      const uintptr_t a = reinterpret_cast<uintptr_t>(S.dst) + lo, b = reinterpret_cast<uintptr_t>(S.dst) + hi;
+      s_ok = move_wait_sources(P, S, p, CB, a, b);
+      if (!s_ok) flag_error(MRN_ETIMEOUT);
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    switch (S.w) {
+      case 16: move_write<16>(S, lo, hi, buf); break;
+      case 8: move_write<8>(S, lo, hi, buf); break;
+      case 4: move_write<4>(S, lo, hi, buf); break;
+      case 2: move_write<2>(S, lo, hi, buf); break;
+      default: move_write<1>(S, lo, hi, buf); break;
+    }
+    __syncthreads();  // the buffer and s_chunk are reused
+  }
+}
+
+// Fills count unsigned integers of `elem` bytes at dst with the value at
+// `from` (read on the device: the new objects' offsets after a resize).
+__global__ void k_fill_from(char* dst, const char* from, uint64_t count, uint32_t elem) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  if (elem == 8)
+    reinterpret_cast<unsigned long long*>(dst)[i] = *reinterpret_cast<const unsigned long long*>(from);
+  else
+    reinterpret_cast<unsigned int*>(dst)[i] = *reinterpret_cast<const unsigned int*>(from);
+}
+
+
+namespace mrn {
+
+int launch_moves(const MoveRange* r, size_t nr, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  MovePlan* P = new (std::nothrow) MovePlan;
+  if (!P) return MRN_ENOMEM;
+  std::memset(P, 0, sizeof(*P));
+  uint64_t chunks = 0;
+  int rc = MRN_OK;
+  for (size_t i = 0; i < nr && rc == MRN_OK; ++i) {
+    const MoveRange& m = r[i];
+    if (m.bytes == 0 || (m.src == m.dst && !m.elem)) continue;
+    const uintptr_t s0 = reinterpret_cast<uintptr_t>(m.src), d0 = reinterpret_cast<uintptr_t>(m.dst);
+    const bool overlap = s0 < d0 + m.bytes && d0 < s0 + m.bytes;
+    if (!overlap && !m.elem) {
+      rc = cuda_status(cudaMemcpyAsync(m.dst, m.src, m.bytes, cudaMemcpyDeviceToDevice, st));
+      continue;
+    }
+    if (P->nseg == kMoveSegs) {
+      rc = MRN_EINVAL;
+      break;
+    }
+    // widest access that divides both addresses and the length
+    uint32_t w = m.elem ? m.elem : 16;
+    const uintptr_t x = s0 | d0 | (uintptr_t)m.bytes;
+    while (w > 1 && (x & (w - 1))) w >>= 1;
+    if (m.elem && w != m.elem) {
+      rc = MRN_EALIGN;
+      break;
+    }
+    MoveSeg& S = P->seg[P->nseg++];
+    S.src = m.src;
+    S.dst = m.dst;
+    S.bytes = m.bytes;
+    S.w = w;
+    S.elem = m.elem;
+    S.delta = m.delta;
+    S.up = d0 > s0;
+    const uint64_t CB = (uint64_t)kMoveThreads * kMoveVec * w;
+    S.chunk_begin = chunks;
+    S.nchunks = (m.bytes + CB - 1) / CB;
+    chunks += S.nchunks;
+  }
+  if (rc == MRN_OK && P->nseg) {
+    void* scratch = nullptr;
+    const size_t sb = 256 + chunks * sizeof(unsigned int);
+    rc = cuda_status(cudaMallocAsync(&scratch, sb, st));
+    if (rc == MRN_OK) {
+      rc = cuda_status(cudaMemsetAsync(scratch, 0, sb, st));
+      P->counter = static_cast<unsigned int*>(scratch);
+      P->flags = reinterpret_cast<unsigned int*>(static_cast<char*>(scratch) + 256);
+      P->total_chunks = chunks;
+      P->timeout_ns = 2000000000ull;
+      const int per_sm = occupancy(reinterpret_cast<const void*>(&k_move), kMoveThreads, 0);
+      const uint64_t cap = (uint64_t)device_sm_count() * (uint64_t)per_sm;
+      const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(cap, chunks));
+      if (rc == MRN_OK) {
+        void* args[] = {P};
+        rc = cuda_status(cudaLaunchKernel(reinterpret_cast<const void*>(&k_move), dim3(grid), dim3(kMoveThreads),
+                                          args, 0, st));
+      }
+      cudaFreeAsync(scratch, st);
+    } else {
+      cudaGetLastError();
+    }
+  }
+  delete P;
+  return rc;
+}
+
+int launch_fill_from(char* dst, const char* from, uint64_t count, uint32_t elem, void* stream) {
+  if (count == 0) return MRN_OK;
+  const unsigned grid = (unsigned)((count + 255) / 256);
+  k_fill_from<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(dst, from, count, elem);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace mrn

@@ -122,6 +122,21 @@ SIGNATURES = [
     ("mrn_server_wait", ctypes.c_int, [vp, u64, u64, ctypes.POINTER(ctypes.c_int)]),
     ("mrn_server_stats_get", ctypes.c_int, [vp, ctypes.POINTER(ServerStats)]),
     ("mrn_server_destroy", None, [vp]),
+    ("mrn_memmove", ctypes.c_int, [vp, vp, u64, ctypes.c_int, vp]),
+    ("mrn_collection_create", ctypes.c_int, [vp, Layout, ctypes.c_int, ctypes.c_int, u64, u64,
+                                             ctypes.POINTER(vp)]),
+    ("mrn_collection_destroy", None, [vp]),
+    ("mrn_collection_view", ctypes.c_int, [vp, ctypes.POINTER(ViewStruct)]),
+    ("mrn_collection_sizes", ctypes.c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
+                                            ctypes.POINTER(u64), ctypes.POINTER(u64)]),
+    ("mrn_collection_reserve", ctypes.c_int, [vp, u64, u64, vp]),
+    ("mrn_collection_resize", ctypes.c_int, [vp, u64, vp]),
+    ("mrn_collection_clear", ctypes.c_int, [vp, vp]),
+    ("mrn_collection_shrink_to_fit", ctypes.c_int, [vp, vp]),
+    ("mrn_collection_erase", ctypes.c_int, [vp, u64, u64, vp]),
+    ("mrn_collection_insert", ctypes.c_int, [vp, u64, ctypes.POINTER(ViewStruct), vp]),
+    ("mrn_collection_assign", ctypes.c_int, [vp, ctypes.POINTER(ViewStruct), vp]),
+    ("mrn_collection_set_context", ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp]),
 ]
 
 _lib = None
@@ -439,3 +454,84 @@ class Server:
 
     def __del__(self):
         self.close()
+
+
+def memmove(dst, src, nbytes, mem="device", stream=None):
+    """Moves nbytes from src to dst (addresses, tensors or arrays) inside one
+    memory context; the ranges may overlap."""
+    check(lib().mrn_memmove(_ptr(dst), _ptr(src), nbytes, MEM.get(mem, mem), _stream(stream)),
+          "mrn_memmove")
+
+
+class _CollectionView:
+    """The ``mrn_view`` of a collection's current contents (pointer arrays
+    owned by the collection: valid until it reallocates)."""
+
+    def __init__(self, schema, s):
+        self.schema = schema
+        self.s = s
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.s)
+
+
+class Collection:
+    """A library-owned collection (``mrn_collection``): a schema, a layout
+    and a memory context ("device", "pinned" or "host")."""
+
+    def __init__(self, schema, kind, capacity=0, child_capacity=0, block=0, mem="device", device=0):
+        self.schema = schema
+        h = vp()
+        check(lib().mrn_collection_create(schema._h, Layout(KIND.get(kind, kind), block), MEM.get(mem, mem),
+                                          device, capacity, child_capacity, ctypes.byref(h)),
+              "mrn_collection_create")
+        self._h = h
+
+    def view(self):
+        v = ViewStruct()
+        check(lib().mrn_collection_view(self._h, ctypes.byref(v)), "mrn_collection_view")
+        return _CollectionView(self.schema, v)
+
+    def sizes(self):
+        """(n, m, capacity, child_capacity)"""
+        out = [u64(), u64(), u64(), u64()]
+        check(lib().mrn_collection_sizes(self._h, *[ctypes.byref(x) for x in out]), "mrn_collection_sizes")
+        return tuple(int(x.value) for x in out)
+
+    def reserve(self, capacity, child_capacity=0, stream=None):
+        check(lib().mrn_collection_reserve(self._h, capacity, child_capacity, _stream(stream)),
+              "mrn_collection_reserve")
+
+    def resize(self, n, stream=None):
+        check(lib().mrn_collection_resize(self._h, n, _stream(stream)), "mrn_collection_resize")
+
+    def clear(self, stream=None):
+        check(lib().mrn_collection_clear(self._h, _stream(stream)), "mrn_collection_clear")
+
+    def shrink_to_fit(self, stream=None):
+        check(lib().mrn_collection_shrink_to_fit(self._h, _stream(stream)), "mrn_collection_shrink_to_fit")
+
+    def erase(self, first, count, stream=None):
+        check(lib().mrn_collection_erase(self._h, first, count, _stream(stream)), "mrn_collection_erase")
+
+    def insert(self, pos, src, stream=None):
+        check(lib().mrn_collection_insert(self._h, pos, src.ref, _stream(stream)), "mrn_collection_insert")
+
+    def assign(self, src, stream=None):
+        check(lib().mrn_collection_assign(self._h, src.ref, _stream(stream)), "mrn_collection_assign")
+
+    def set_context(self, mem, device=0, stream=None):
+        check(lib().mrn_collection_set_context(self._h, MEM.get(mem, mem), device, _stream(stream)),
+              "mrn_collection_set_context")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mrn_collection_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -385,3 +385,79 @@ def test_jagged_aosoa_tail_slots_and_gaps_are_zero():
         start = s.aosoa_col_start(B, c)
         col = blocks[1, start: start + B * 4].reshape(B, 4)
         assert not col[n - B:].any()
+
+
+# ------------------------------------------- size-changing operations (Sec. VI-B)
+
+from oracle import collection as oc  # noqa: E402
+
+ONE = [("v", "u32", 1)]
+JAG = [("p", "u16", 1), ("k", "jagged", "u32", [("x", "u8", 1)])]
+
+
+def _one(vals):
+    return {"n": len(vals), "columns": [np.array(vals, np.uint32)]}
+
+
+def _jag(p, lengths, kids):
+    return {"n": len(p), "columns": [np.array(p, np.uint16)], "lengths": np.array(lengths, np.uint32),
+            "children": [np.array(kids, np.uint8)], "m": len(kids)}
+
+
+def test_collection_ops_worked_examples():
+    """Hand-written results of the vector-like operations."""
+    d = _one([10, 20, 30])
+    assert oc.erase(d, 1, 1)["columns"][0].tolist() == [10, 30]
+    assert oc.insert(d, 1, _one([99]))["columns"][0].tolist() == [10, 99, 20, 30]
+    assert oc.insert(d, 3, _one([7, 8]))["columns"][0].tolist() == [10, 20, 30, 7, 8]
+    assert oc.resize(d, 5)["columns"][0].tolist() == [10, 20, 30, 0, 0]
+    assert oc.resize(d, 1)["columns"][0].tolist() == [10]
+    assert oc.take(d, 1, 2)["columns"][0].tolist() == [20, 30]
+    j = _jag([1, 2, 3], [2, 0, 1], [5, 6, 7])
+    e = oc.erase(j, 0, 1)
+    assert (e["n"], e["m"], e["lengths"].tolist(), e["children"][0].tolist()) == (2, 1, [0, 1], [7])
+    e = oc.erase(j, 1, 1)   # an object without children
+    assert (e["m"], e["lengths"].tolist(), e["children"][0].tolist()) == (3, [2, 1], [5, 6, 7])
+    i = oc.insert(j, 1, _jag([9], [2], [8, 9]))
+    assert i["columns"][0].tolist() == [1, 9, 2, 3]
+    assert (i["m"], i["lengths"].tolist(), i["children"][0].tolist()) == (5, [2, 2, 0, 1], [5, 6, 8, 9, 7])
+    r = oc.resize(j, 4)
+    assert (r["lengths"].tolist(), r["children"][0].tolist(), r["columns"][0].tolist()) == \
+        ([2, 0, 1, 0], [5, 6, 7], [1, 2, 3, 0])
+
+
+@pytest.mark.parametrize("name,n", [("cells", 0), ("cells", 57), ("tracks", 41)])
+def test_collection_ops_identities(name, n):
+    """Erase and re-insert, grow and shrink, split and rejoin give back the
+    original, and the laid-out SoA of an erased collection is the SoA with
+    the erased rows (and children) cut out of every region."""
+    s = oracle.Schema(datagen.WORKLOAD_SCHEMAS[name])
+    d = datagen.workload(name, n, 5)
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        f = int(rng.integers(0, n + 1))
+        c = int(rng.integers(0, n - f + 1))
+        back = oc.insert(oc.erase(d, f, c), f, oc.take(d, f, c))
+        assert oracle.pack(s, back, "soa").base.tobytes() == oracle.pack(s, d, "soa").base.tobytes()
+        assert oracle.pack(s, oc.resize(oc.resize(d, n + 9), n), "aos").base.tobytes() == \
+            oracle.pack(s, d, "aos").base.tobytes()
+        # laid out: each region is the concatenation of the kept rows
+        full, cut = oracle.pack(s, d, "soa"), oracle.pack(s, oc.erase(d, f, c), "soa")
+        for r in range(s.ncols):
+            col = oracle.region(s, full, r)
+            sz = col.size // max(n, 1) if n else 0
+            want = np.concatenate([col[: f * sz], col[(f + c) * sz:]]) if n else col
+            assert oracle.region(s, cut, r).tobytes() == want.tobytes()
+        if s.has_jagged:
+            off = oracle.region(s, full, s.ncols).view(np.uint32).astype(np.int64)
+            a, b = int(off[f]), int(off[f + c])
+            for r in range(s.ncols + 1, s.ncols + 1 + len(d["children"])):
+                kid = oracle.region(s, full, r)
+                ksz = kid.size // max(d["m"], 1)
+                want = np.concatenate([kid[: a * ksz], kid[b * ksz:]])
+                assert oracle.region(s, cut, r).tobytes() == want.tobytes()
+            coff = oracle.region(s, cut, s.ncols).view(np.uint32).astype(np.int64)
+            want = np.concatenate([off[:f], off[f + c:] - (b - a)])
+            assert coff.tolist() == want.tolist()
+    empty = oc.erase(d, 0, n)
+    assert empty["n"] == 0 and (not s.has_jagged or empty["m"] == 0)
