@@ -548,6 +548,7 @@ def run_mine(args, rank, world):
     if args.mixed_jobs > 0:
         extra["batched_mixed"] = run_mixed(mrn, torch, stream, peak, args)
     extra["sensor_grid"] = run_sensor_grid(mrn, torch, stream)
+    extra["collection_ops"] = run_collection_ops(mrn, torch, stream, peak)
     extra["served"] = run_served(mrn, torch, args)
     cpu_val, cpu_reps, cpu_s = cpu_oracle_rate(10.0, N_RECORDS)
     line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
@@ -741,6 +742,86 @@ def secondary(mrn, torch, stream, peak):
                              "both_directions_total": round(2 * (1 << 30) / best_bi / 1e9, 1)}
     del h2, dbuf2
     del h, dbuf
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_collection_ops(mrn, torch, stream, peak):
+    """Size-changing operations on device collections (the overlapping move
+    k_move underneath), against the HBM roofline: algorithmic bytes are the
+    bytes moved read once and written once (plus a conversion's own bytes
+    for an insert), timed with CUDA events around each call."""
+    import datagen
+    out = {}
+
+    def timed(fn, reps=5):
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        assert mrn.sync() == mrn.OK
+        return statistics.median(ts)
+
+    def row(alg, ms):
+        return {"ms": round(ms, 4), "gbps": round(alg / (ms * 1e-3) / 1e9, 1),
+                "frac_of_hbm": round(alg / (ms * 1e-3) / 1e9 / peak, 3)}
+
+    # the overlapping move alone: 1 GiB shifted by a little and by a lot
+    nb = 1 << 30
+    buf = torch.empty(nb + (64 << 20), dtype=torch.uint8, device="cuda")
+    p0 = buf.data_ptr() + (32 << 20)
+    mv = {}
+    for name, shift in (("up_64B", 64), ("down_64B", -64), ("up_8MiB", 8 << 20), ("down_8MiB", -(8 << 20))):
+        ms = timed(lambda: mrn.memmove(p0 + shift, p0, nb, stream=stream))
+        mv[name] = row(2 * nb, ms)
+    out["memmove_1GiB"] = mv
+    del buf
+    # a calorimeter-cell SoA collection of 2^26 objects: erase 1% at the
+    # front, insert 1% (from device AoS) at the front
+    s = mrn.Schema(datagen.CELLS)
+    n, k = 1 << 26, (1 << 26) // 100
+    coll = mrn.Collection(s, "soa", capacity=n + k)
+    coll.resize(n)
+    src = torch.full((k * 24,), 0x3C, dtype=torch.uint8, device="cuda")
+    sv = mrn.View(s, "aos", k, base=src)
+    cells = {}
+    ms_e, ms_i = [], []
+    for _ in range(4):
+        ms_e.append(timed(lambda: coll.erase(0, k), 1))
+        ms_i.append(timed(lambda: coll.insert(0, sv), 1))
+    cells["erase_front_1pct"] = row(2 * (n - k) * 24, statistics.median(ms_e))
+    cells["insert_front_1pct"] = row(2 * (n - k) * 24 + 2 * k * 24, statistics.median(ms_i))
+    out["cells_soa_2^26"] = cells
+    del coll, src
+    # jagged tracks, SoA collection of 4,194,304 parents (~84 M children)
+    s = mrn.Schema(datagen.TRACKS)
+    n = 1 << 22
+    m, recs, pool = jagged_aos(torch, s, n)
+    coll = mrn.Collection(s, "soa", capacity=n + n // 50, child_capacity=m + m // 20)
+    coll.assign(mrn.View(s, "aos", n, base=recs, child_pool=pool, m=m))
+    k = n // 100
+    kv = mrn.View(s, "aos", k, base=recs, child_pool=pool, m=m)
+    tr = {}
+    ms_e, ms_i, moved = [], [], []
+    for _ in range(3):
+        n0, m0 = coll.sizes()[:2]
+        ms_e.append(timed(lambda: coll.erase(0, k), 1))
+        n1, m1 = coll.sizes()[:2]
+        moved.append((n1 * 12 + (n1 + 1) * 4 + m1 * 8, m0 - m1))
+        ms_i.append(timed(lambda: coll.insert(0, kv), 1))
+    b_move, kids = moved[0]
+    tr["erase_front_1pct"] = dict(row(2 * b_move, statistics.median(ms_e)), children_removed=int(kids))
+    tr["insert_front_1pct"] = dict(row(2 * b_move + k * 24 + kids * 8 + k * 16 + kids * 8,
+                                       statistics.median(ms_i)))
+    tr["note"] = ("field-major jagged erase / insert wait for the stream to read offsets (and an AoS "
+                  "source's child count); those host round trips are inside the timed call")
+    out["tracks_soa_4M"] = tr
+    del coll, recs, pool
     torch.cuda.empty_cache()
     return out
 

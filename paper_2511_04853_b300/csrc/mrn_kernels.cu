@@ -1548,14 +1548,14 @@ struct MoveSeg {
 
 constexpr uint32_t kMoveSegs = 136;     // a schema's 64 columns, offsets, 64 child columns
 constexpr uint32_t kMoveThreads = 256;
-constexpr uint32_t kMoveVec = 4;        // accesses per thread per chunk
+constexpr uint32_t kMoveBytes = 64;     // bytes per thread per chunk, whatever the access width
 
 struct MovePlan {
   MoveSeg seg[kMoveSegs];
   uint32_t nseg;
   uint32_t pad;
   uint64_t total_chunks;
-  unsigned int* counter;  // chunk tickets
+  unsigned int* counter;  // [0] chunk tickets, [1] set once a wait has expired
   unsigned int* flags;    // per chunk: 1 once its source has been read
   unsigned long long timeout_ns;
 };
@@ -1587,7 +1587,7 @@ __device__ __forceinline__ void move_read(const MoveSeg& S, uint64_t lo, uint64_
   T* b = reinterpret_cast<T*>(buf);
   const uint64_t nw = (hi - lo) / W;
 #pragma unroll
-  for (uint32_t i = 0; i < kMoveVec; ++i) {
+  for (uint32_t i = 0; i < kMoveBytes / W; ++i) {
     const uint64_t k = threadIdx.x + (uint64_t)i * kMoveThreads;
     if (k < nw) b[k] = src[k];
   }
@@ -1600,7 +1600,7 @@ __device__ __forceinline__ void move_write(const MoveSeg& S, uint64_t lo, uint64
   const T* b = reinterpret_cast<const T*>(buf);
   const uint64_t nw = (hi - lo) / W;
 #pragma unroll
-  for (uint32_t i = 0; i < kMoveVec; ++i) {
+  for (uint32_t i = 0; i < kMoveBytes / W; ++i) {
     const uint64_t k = threadIdx.x + (uint64_t)i * kMoveThreads;
     if (k < nw) {
       T v = b[k];
@@ -1624,7 +1624,8 @@ __device__ bool move_wait_sources(const MovePlan& P, const MoveSeg& S, uint64_t 
     if (q == p) continue;
     const uint64_t c = S.chunk_begin + (S.up ? S.nchunks - 1 - q : q);
     for (uint32_t i = 0; ld_acquire_u32(P.flags + c) == 0; ++i) {
-      if ((i & 63) == 63 && global_ns() > deadline) return false;
+      // after another chunk gave up, this wait may never end: give up too
+      if ((i & 63) == 63 && (global_ns() > deadline || ld_acquire_u32(P.counter + 1))) return false;
       __nanosleep(64);
     }
   }
@@ -1637,7 +1638,7 @@ __device__ bool move_wait_sources(const MovePlan& P, const MoveSeg& S, uint64_t 
 // destination overlaps to have been read, then writes it.  A chunk's read
 // never waits, so the chunks a CTA waits for always finish their reads.
 __global__ void __launch_bounds__(kMoveThreads) k_move(const __grid_constant__ MovePlan P) {
-  __shared__ __align__(16) unsigned char buf[kMoveThreads * kMoveVec * 16];
+  __shared__ __align__(16) unsigned char buf[kMoveThreads * kMoveBytes];
   __shared__ unsigned long long s_chunk;
   __shared__ int s_ok;
   for (;;) {
@@ -1650,7 +1651,7 @@ __global__ void __launch_bounds__(kMoveThreads) k_move(const __grid_constant__ M
     const MoveSeg& S = P.seg[si];
     const uint64_t k = c - S.chunk_begin;
     const uint64_t p = S.up ? S.nchunks - 1 - k : k;
-    const uint64_t CB = (uint64_t)kMoveThreads * kMoveVec * S.w;
+    const uint64_t CB = (uint64_t)kMoveThreads * kMoveBytes;
     const uint64_t lo = p * CB, hi = min(lo + CB, S.bytes);
     switch (S.w) {
       case 16: move_read<16>(S, lo, hi, buf); break;
@@ -1664,7 +1665,10 @@ __global__ void __launch_bounds__(kMoveThreads) k_move(const __grid_constant__ M
       st_release_u32(P.flags + c, 1u);
       const uintptr_t a = reinterpret_cast<uintptr_t>(S.dst) + lo, b = reinterpret_cast<uintptr_t>(S.dst) + hi;
       s_ok = move_wait_sources(P, S, p, CB, a, b);
-      if (!s_ok) flag_error(MRN_ETIMEOUT);
+      if (!s_ok) {
+        flag_error(MRN_ETIMEOUT);
+        st_release_u32(P.counter + 1, 1u);
+      }
     }
     __syncthreads();
     if (!s_ok) return;
@@ -1729,7 +1733,7 @@ int launch_moves(const MoveRange* r, size_t nr, void* stream) {
     S.elem = m.elem;
     S.delta = m.delta;
     S.up = d0 > s0;
-    const uint64_t CB = (uint64_t)kMoveThreads * kMoveVec * w;
+    const uint64_t CB = (uint64_t)kMoveThreads * kMoveBytes;
     S.chunk_begin = chunks;
     S.nchunks = (m.bytes + CB - 1) / CB;
     chunks += S.nchunks;
