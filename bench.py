@@ -568,7 +568,7 @@ def run_mine(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_e2e(mrn, torch, s, colls, args, world):
+def run_e2e(mrn, torch, s, colls, args, world, n_streams=2):
     """Host pinned AoS -> device SoA, SoA -> AoSoA(32), device AoSoA(32) ->
     host pinned AoS for every collection of the batch, per step."""
     n = N_RECORDS
@@ -582,12 +582,14 @@ def run_e2e(mrn, torch, s, colls, args, world):
                       mrn.View(s, "aosoa", n, block=BLOCK, base=d_blk[i]),
                       mrn.View(s, "aos", n, base=h_out[i], mem="pinned")))
 
-    streams = [torch.cuda.Stream() for _ in range(2)]
+    streams = [torch.cuda.Stream() for _ in range(n_streams)]
     main = torch.cuda.current_stream()
 
     def step():
-        # collection i on stream i % 2: one collection's device -> host copy
-        # overlaps the next one's host -> device copy
+        # collection i on stream i % n_streams: collections' device -> host
+        # copies overlap later ones' host -> device copies (each direction
+        # has its own copy pipeline; a stream only orders its own
+        # collections)
         for st in streams:
             st.wait_stream(main)
         for i, (hin, soa, blk, hout) in enumerate(views):
@@ -616,7 +618,7 @@ def run_e2e(mrn, torch, s, colls, args, world):
             "h2d_bytes_per_step": len(colls) * n * 24, "d2h_bytes_per_step": len(colls) * n * 24,
             "ms_per_step": round(el * 1e3, 3), "steps": k,
             "path": "mrn_transfer_convert (default 4 MiB chunks, 4 slots) + mrn_convert, pinned host buffers, "
-                    "collection i on stream i % 2"}
+                    "collection i on stream i %% %d" % n_streams}
 
 
 def secondary(mrn, torch, stream, peak):
