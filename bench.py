@@ -185,6 +185,49 @@ def cpu_oracle_rate(seconds, n_records):
     return reps * bytes_per_collection(24, n_records) / el / 1e9, reps, el
 
 
+def _oracle_worker(job):
+    """One host process of the all-cores oracle measurement: its own seeded
+    collection, the three conversions repeated for `seconds` from a common
+    start time."""
+    seconds, n_records, seed, start_at = job
+    step = oracle_step_setup(n_records, seed)
+    step()
+    while time.time() < start_at:
+        time.sleep(0.01)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        step()
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            return reps, el
+
+
+def cpu_oracle_rate_all_cores(seconds, n_records):
+    """The same oracle, unchanged, in one process per host core (spawned:
+    the parent already holds a CUDA context), each on its own collection,
+    all started together; aggregate GB/s."""
+    import multiprocessing as mp
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    lead = 5.0 + 0.05 * cores
+    start_at = time.time() + lead
+    pool = ctx.Pool(cores)
+    try:
+        job = pool.map_async(_oracle_worker, [(seconds, n_records, 1 + i, start_at) for i in range(cores)])
+        res = job.get(timeout=lead + seconds + 120.0)  # a worker that died must not hang the bench
+    except Exception as e:
+        pool.terminate()
+        return None, "not measured: %s" % type(e).__name__
+    pool.close()
+    pool.join()
+    per = bytes_per_collection(24, n_records)
+    return sum(r * per / el for r, el in res) / 1e9, cores
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -551,6 +594,7 @@ def run_mine(args, rank, world):
     extra["collection_ops"] = run_collection_ops(mrn, torch, stream, peak)
     extra["served"] = run_served(mrn, torch, args)
     cpu_val, cpu_reps, cpu_s = cpu_oracle_rate(10.0, N_RECORDS)
+    cpu_all, cpu_cores = cpu_oracle_rate_all_cores(10.0, N_RECORDS)
     line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
@@ -562,7 +606,12 @@ def run_mine(args, rank, world):
             "roofline": roof,
             "cpu_baseline": {"value": round(cpu_val, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
                              "sample": "3 conversions of one 200,000-record collection x %d (%.1f s)"
-                                       % (cpu_reps, cpu_s)},
+                                       % (cpu_reps, cpu_s),
+                             "all_cores": {"value": round(cpu_all, 3) if cpu_all else None, "unit": "GB/s",
+                                           "cores": cpu_cores,
+                                           "sample": "one process per core, each the same 3 conversions of "
+                                                     "its own 200,000-record collection for 10 s, started "
+                                                     "together; aggregate"}},
             "clocks": clocks}
     line.update(extra)
     print(json.dumps(line), flush=True)
