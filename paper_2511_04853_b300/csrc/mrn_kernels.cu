@@ -1549,6 +1549,8 @@ struct MoveSeg {
 constexpr uint32_t kMoveSegs = 136;     // a schema's 64 columns, offsets, 64 child columns
 constexpr uint32_t kMoveThreads = 256;
 constexpr uint32_t kMoveBytes = 64;     // bytes per thread per chunk, whatever the access width
+// k_move runs 8 CTAs per SM (32 registers): measured 25-40% faster than the
+// 64-register build at 4 CTAs per SM, and than double-buffered chunks
 
 struct MovePlan {
   MoveSeg seg[kMoveSegs];
@@ -1586,7 +1588,7 @@ __device__ __forceinline__ void move_read(const MoveSeg& S, uint64_t lo, uint64_
   const T* src = reinterpret_cast<const T*>(S.src + lo);
   T* b = reinterpret_cast<T*>(buf);
   const uint64_t nw = (hi - lo) / W;
-#pragma unroll
+#pragma unroll 4
   for (uint32_t i = 0; i < kMoveBytes / W; ++i) {
     const uint64_t k = threadIdx.x + (uint64_t)i * kMoveThreads;
     if (k < nw) b[k] = src[k];
@@ -1599,7 +1601,7 @@ __device__ __forceinline__ void move_write(const MoveSeg& S, uint64_t lo, uint64
   T* dst = reinterpret_cast<T*>(S.dst + lo);
   const T* b = reinterpret_cast<const T*>(buf);
   const uint64_t nw = (hi - lo) / W;
-#pragma unroll
+#pragma unroll 4
   for (uint32_t i = 0; i < kMoveBytes / W; ++i) {
     const uint64_t k = threadIdx.x + (uint64_t)i * kMoveThreads;
     if (k < nw) {
@@ -1637,7 +1639,7 @@ __device__ bool move_wait_sources(const MovePlan& P, const MoveSeg& S, uint64_t 
 // one into shared memory, marks it read, waits for the chunks its
 // destination overlaps to have been read, then writes it.  A chunk's read
 // never waits, so the chunks a CTA waits for always finish their reads.
-__global__ void __launch_bounds__(kMoveThreads) k_move(const __grid_constant__ MovePlan P) {
+__global__ void __launch_bounds__(kMoveThreads, 8) k_move(const __grid_constant__ MovePlan P) {
   __shared__ __align__(16) unsigned char buf[kMoveThreads * kMoveBytes];
   __shared__ unsigned long long s_chunk;
   __shared__ int s_ok;
