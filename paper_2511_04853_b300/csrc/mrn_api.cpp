@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <mutex>
 
 #include "mrn_internal.h"
 
@@ -446,6 +447,23 @@ int convert_direct(const mrn_view& src, const mrn_view& dst, void* stream) {
 
 using namespace mrn;
 
+namespace {
+// One non-blocking side stream per device, for work that runs beside the
+// caller's stream inside one call (joined back before the call returns).
+cudaStream_t side_stream() {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    streams[dev] = nullptr;
+  }
+  return streams[dev];
+}
+}  // namespace
+
 extern "C" {
 
 const char* mrn_status_str(int st) {
@@ -491,11 +509,25 @@ int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
       // The children are stored contiguously on both sides (Sec. V, jagged
       // vector property): child row j -> pool record j is a plain SoA -> AoS
       // conversion of the child schema; the kernel builds only the parents.
+      // The parents (a latency-bound kernel over few bytes) run on a side
+      // stream beside the children's bandwidth-bound conversion.
       ConvPlan kids;
       if ((rc = jagged_children_plan(s, jp, &kids))) return rc;
       jp.m_src = 0;
-      if ((rc = launch_jagged_s2a(jp, stream))) return rc;
-      if ((rc = launch_convert(kids, stream, nullptr))) return rc;
+      cudaStream_t st = static_cast<cudaStream_t>(stream);
+      cudaStream_t side = side_stream();
+      cudaEvent_t fork = nullptr, join = nullptr;
+      const bool split = side && cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
+                         cudaEventCreateWithFlags(&join, cudaEventDisableTiming) == cudaSuccess &&
+                         cudaEventRecord(fork, st) == cudaSuccess && cudaStreamWaitEvent(side, fork, 0) == cudaSuccess;
+      if (!split) cudaGetLastError();
+      rc = launch_jagged_s2a(jp, split ? side : st);
+      if (split && cudaEventRecord(join, side) != cudaSuccess && !rc) rc = MRN_ECUDA;
+      if (!rc) rc = launch_convert(kids, stream, nullptr);
+      if (split && cudaStreamWaitEvent(st, join, 0) != cudaSuccess && !rc) rc = MRN_ECUDA;
+      if (fork) cudaEventDestroy(fork);
+      if (join) cudaEventDestroy(join);
+      if (rc) return rc;
     }
     return zero_dst_gaps(*dst, stream);
   }
