@@ -17,14 +17,23 @@ struct mrn_batch {
   std::vector<mrn_view> src, dst;
   std::vector<std::vector<void*>> cols;  // 4 per job
   std::vector<size_t> first_entry;       // job -> index of its first table entry
-  std::vector<BatchJob> jobs;
-  std::vector<unsigned long long> first_tile;
-  unsigned long long total_tiles = 0;
+  std::vector<BatchJob> jobs;  // every planned job, in order
+  // The jobs split over the two launches: jagged AoS -> field-major jobs
+  // (k_batch_jag, one CTA per tile) and all others (k_batch, persistent);
+  // each launch numbers its own tiles.
+  std::vector<BatchJob> plain, jag;
+  std::vector<std::pair<int, size_t>> where;  // jobs[i] -> (0: plain / 1: jag, index)
+  std::vector<unsigned long long> first_tile;  // plain jobs
+  std::vector<unsigned int> tile_job;          // jagged tile -> index in jag
+  unsigned long long total_tiles = 0, jag_tiles = 0;
   BatchJob* d_jobs = nullptr;
   unsigned long long* d_first = nullptr;
-  char* d_scratch = nullptr;  // counter (256 B) + one look-back word per tile
-  size_t scratch_bytes = 0;  // the look-back words only with jagged AoS -> SoA jobs
-  bool jag_a2s = false;
+  BatchJob* d_jag = nullptr;
+  unsigned int* d_tile_job = nullptr;
+  // counters (k_batch at 0, k_batch_jag at 64), then one look-back word per
+  // jagged tile
+  char* d_scratch = nullptr;
+  size_t scratch_bytes = 0;
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -37,6 +46,8 @@ struct mrn_batch {
     if (cap) cudaStreamDestroy(cap);
     cudaFree(d_jobs);
     cudaFree(d_first);
+    cudaFree(d_jag);
+    cudaFree(d_tile_job);
     cudaFree(d_scratch);
   }
 };
@@ -151,52 +162,73 @@ int rebuild_tables(mrn_batch* b) {
     int rc = plan_job(b->src[i], b->dst[i], &b->jobs);
     if (rc) return rc;
   }
-  b->first_tile.assign(b->jobs.size(), 0);
-  unsigned long long t = 0;
-  for (size_t i = 0; i < b->jobs.size(); ++i) {
-    b->jobs[i].tile_begin = t;
-    b->first_tile[i] = t;
-    t += b->jobs[i].ntiles;
+  b->plain.clear();
+  b->jag.clear();
+  b->where.clear();
+  b->first_tile.clear();
+  b->tile_job.clear();
+  unsigned long long t = 0, tj = 0;
+  for (BatchJob& j : b->jobs) {
+    if (j.kind == JOB_JAG_A2S) {
+      j.tile_begin = tj;
+      b->where.push_back({1, b->jag.size()});
+      if (tj + j.ntiles > 0x7fffffffull) return MRN_EUNSUPPORTED;
+      b->tile_job.insert(b->tile_job.end(), j.ntiles, (unsigned int)b->jag.size());
+      b->jag.push_back(j);
+      tj += j.ntiles;
+    } else {
+      j.tile_begin = t;
+      b->where.push_back({0, b->plain.size()});
+      b->first_tile.push_back(t);
+      b->plain.push_back(j);
+      t += j.ntiles;
+    }
   }
   b->total_tiles = t;
-  // Chunks of about 192 KB of traffic: eight staged conversion tiles, one
-  // jagged tile.
+  b->jag_tiles = tj;
+  // Chunks of about 192 KB of traffic: eight staged conversion tiles.
   double bytes = 0;
-  for (const BatchJob& j : b->jobs) bytes += (double)j.ntiles * tile_traffic(j);
+  for (const BatchJob& j : b->plain) bytes += (double)j.ntiles * tile_traffic(j);
   const double per_tile = t ? bytes / (double)t : 1.0;
   b->max_chunk = (uint32_t)std::max(1.0, std::min(8.0, 196608.0 / std::max(per_tile, 1.0)));
   return MRN_OK;
 }
 
 int upload(mrn_batch* b) {
-  const size_t jb = std::max<size_t>(1, b->jobs.size()) * sizeof(BatchJob);
+  const size_t jb = std::max<size_t>(1, b->plain.size()) * sizeof(BatchJob);
+  const size_t gb = std::max<size_t>(1, b->jag.size()) * sizeof(BatchJob);
   // the tile index is read by whole 16-byte pieces (L2 prefetch)
   const size_t fb = align_up(std::max<size_t>(1, b->first_tile.size()) * sizeof(unsigned long long), 16);
-  b->jag_a2s = false;
-  for (const BatchJob& j : b->jobs) b->jag_a2s |= j.kind == JOB_JAG_A2S;
-  b->scratch_bytes = 256 + (b->jag_a2s ? (size_t)b->total_tiles * sizeof(unsigned long long) : 0);
+  const size_t tb = std::max<size_t>(1, b->tile_job.size()) * sizeof(unsigned int);
+  b->scratch_bytes = 256 + (size_t)b->jag_tiles * sizeof(unsigned long long);
   if (cudaMalloc(&b->d_jobs, jb) != cudaSuccess || cudaMalloc(&b->d_first, fb) != cudaSuccess ||
+      cudaMalloc(&b->d_jag, gb) != cudaSuccess || cudaMalloc(&b->d_tile_job, tb) != cudaSuccess ||
       cudaMalloc(&b->d_scratch, b->scratch_bytes) != cudaSuccess) {
     cudaGetLastError();
     return MRN_ENOMEM;
   }
-  if (b->jobs.empty()) return MRN_OK;
-  if (cudaMemcpy(b->d_jobs, b->jobs.data(), b->jobs.size() * sizeof(BatchJob), cudaMemcpyHostToDevice) !=
-          cudaSuccess ||
-      cudaMemcpy(b->d_first, b->first_tile.data(), b->first_tile.size() * sizeof(unsigned long long),
-                 cudaMemcpyHostToDevice) != cudaSuccess)
+  auto put = [](void* d, const void* h, size_t n) {
+    return n == 0 || cudaMemcpy(d, h, n, cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  if (!put(b->d_jobs, b->plain.data(), b->plain.size() * sizeof(BatchJob)) ||
+      !put(b->d_first, b->first_tile.data(), b->first_tile.size() * sizeof(unsigned long long)) ||
+      !put(b->d_jag, b->jag.data(), b->jag.size() * sizeof(BatchJob)) ||
+      !put(b->d_tile_job, b->tile_job.data(), b->tile_job.size() * sizeof(unsigned int)))
     return MRN_ECUDA;
   return MRN_OK;
 }
 
 int enqueue(mrn_batch* b, cudaStream_t s) {
-  if (b->total_tiles == 0) return MRN_OK;
+  if (b->total_tiles == 0 && b->jag_tiles == 0) return MRN_OK;
   if (cudaMemsetAsync(b->d_scratch, 0, b->scratch_bytes, s) != cudaSuccess) return MRN_ECUDA;
-  return launch_batch(b->d_jobs, b->d_first, (unsigned)b->jobs.size(), b->total_tiles,
-                      reinterpret_cast<unsigned int*>(b->d_scratch),
-                      b->jag_a2s ? reinterpret_cast<unsigned long long*>(b->d_scratch + 256) : nullptr,
-                      b->ctas_per_sm,
-                      b->max_chunk, s);
+  int rc = MRN_OK;
+  if (b->total_tiles)
+    rc = launch_batch(b->d_jobs, b->d_first, (unsigned)b->plain.size(), b->total_tiles,
+                      reinterpret_cast<unsigned int*>(b->d_scratch), nullptr, b->ctas_per_sm, b->max_chunk, s);
+  if (!rc && b->jag_tiles)
+    rc = launch_batch_jag(b->d_jag, b->d_tile_job, b->jag_tiles, reinterpret_cast<unsigned int*>(b->d_scratch + 64),
+                          reinterpret_cast<unsigned long long*>(b->d_scratch + 256), s);
+  return rc;
 }
 
 int capture(mrn_batch* b) {
@@ -289,7 +321,9 @@ int mrn_batch_update(mrn_batch* b, size_t j, const mrn_view* src, const mrn_view
   const size_t next = j + 1 < b->first_entry.size() ? b->first_entry[j + 1] : b->jobs.size();
   if (fresh.size() != next - k) return MRN_EINVAL;
   for (size_t i = 0; i < fresh.size(); ++i) {
-    if (fresh[i].ntiles != b->jobs[k + i].ntiles) return MRN_EINVAL;
+    if (fresh[i].ntiles != b->jobs[k + i].ntiles ||
+        (fresh[i].kind == JOB_JAG_A2S) != (b->jobs[k + i].kind == JOB_JAG_A2S))
+      return MRN_EINVAL;
     fresh[i].tile_begin = b->jobs[k + i].tile_begin;
   }
   for (int q = 0; q < 4; ++q) b->cols[4 * j + q] = std::move(c[q]);
@@ -297,8 +331,10 @@ int mrn_batch_update(mrn_batch* b, size_t j, const mrn_view* src, const mrn_view
   own_view(*dst, &b->cols[4 * j + 2], &b->cols[4 * j + 3], &b->dst[j]);
   for (size_t i = 0; i < fresh.size(); ++i) {
     b->jobs[k + i] = fresh[i];
-    if (cudaMemcpy(b->d_jobs + k + i, &fresh[i], sizeof(BatchJob), cudaMemcpyHostToDevice) != cudaSuccess)
-      return MRN_ECUDA;
+    const auto w = b->where[k + i];
+    (w.first ? b->jag : b->plain)[w.second] = fresh[i];
+    BatchJob* d = (w.first ? b->d_jag : b->d_jobs) + w.second;
+    if (cudaMemcpy(d, &fresh[i], sizeof(BatchJob), cudaMemcpyHostToDevice) != cudaSuccess) return MRN_ECUDA;
   }
   return MRN_OK;
 }

@@ -133,6 +133,10 @@ int launch_fill_from(char* dst, const char* from, uint64_t count, uint32_t elem,
 int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, unsigned int njobs,
                  unsigned long long total_tiles, unsigned int* counter, unsigned long long* states,
                  unsigned int ctas_per_sm, unsigned int max_chunk, void* stream);
+// The jagged AoS -> field-major jobs of a batch (their own tile numbering,
+// tile_job[t] = job of tile t), one CTA per tile.
+int launch_batch_jag(const BatchJob* jobs, const unsigned int* tile_job, unsigned long long total,
+                     unsigned int* counter, unsigned long long* states, void* stream);
 int batch_occupancy();
 
 // Cached launch shape for a plan (autotuner), or the default.

@@ -598,6 +598,27 @@ __global__ void __launch_bounds__(MRN_JAG_THREADS, 6) k_jagged_a2s(const __grid_
   jagged_a2s_tile<VP, VC>(jp, s_tile, jp.tile_state, tw_all, sh, sw);
 }
 
+// The jagged AoS -> field-major jobs of a batch: one CTA per tile as in
+// k_jagged_a2s (6 CTAs per SM: the scan and the gather are latency-bound
+// and want many warps), tiles taken in increasing order over all the jobs,
+// each tile's job read from a host-built map.  A tile's look-back only
+// visits its own job's earlier tiles, which hold earlier tickets.
+__global__ void __launch_bounds__(MRN_JAG_THREADS, 6) k_batch_jag(const BatchJob* __restrict__ jobs,
+                                                                 const unsigned int* __restrict__ tile_job,
+                                                                 unsigned long long total, unsigned int* counter,
+                                                                 unsigned long long* states) {
+  __shared__ uint32_t tw_all[8 * MRN_TW_WORDS_PER_WARP];
+  __shared__ JagShared sh;
+  __shared__ JagWarp sw;
+  __shared__ unsigned int s_tile;
+  if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
+  __syncthreads();
+  const uint64_t t = s_tile;
+  if (t >= total) return;
+  const BatchJob& J = jobs[__ldg(tile_job + t)];
+  jagged_a2s_tile<0, 0>(J.jp, t - J.tile_begin, states + J.tile_begin, tw_all, sh, sw);
+}
+
 // One warp group of a jagged SoA -> AoS conversion: groups [0,
 // parent_groups) build 32 parent records each (length and begin from the
 // offsets), the following groups convert MRN_JAG_CHILD_GROUP of the m_src
@@ -1503,6 +1524,14 @@ int batch_occupancy() {
   const void* fn = reinterpret_cast<const void*>(&k_batch);
   allow_batch_smem(fn);
   return occupancy(fn, kBThreads, kBatchSmem);
+}
+
+int launch_batch_jag(const BatchJob* jobs, const unsigned int* tile_job, unsigned long long total,
+                     unsigned int* counter, unsigned long long* states, void* stream) {
+  if (total == 0) return MRN_OK;
+  k_batch_jag<<<(unsigned)total, MRN_JAG_THREADS, 0, static_cast<cudaStream_t>(stream)>>>(jobs, tile_job, total,
+                                                                                       counter, states);
+  return cuda_status(cudaGetLastError());
 }
 
 int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, unsigned int njobs,

@@ -209,7 +209,8 @@ def test_batch_tune_keeps_results_exact():
     jobs = make_jobs(11, 24)
     b = mrn.Batch([(s, d) for s, d, _, _ in jobs], use_graph=True)
     r = b.tune()
-    assert r["max_chunk"] in (1, 2, 4, 8, 16) and r["ctas_per_sm"] in (0, 2)
+    # the tuned shape is one of the candidates, or the default when that was fastest
+    assert 1 <= r["max_chunk"] <= 16 and r["ctas_per_sm"] in (0, 2)
     assert 0 < r["ms"] <= r["default_ms"]
     for _, d, _, _ in jobs:
         d.tensors[0].fill_(0xA5)
