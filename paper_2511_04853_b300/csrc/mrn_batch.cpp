@@ -224,7 +224,7 @@ int enqueue(mrn_batch* b, cudaStream_t s) {
   int rc = MRN_OK;
   if (b->total_tiles)
     rc = launch_batch(b->d_jobs, b->d_first, (unsigned)b->plain.size(), b->total_tiles,
-                      reinterpret_cast<unsigned int*>(b->d_scratch), nullptr, b->ctas_per_sm, b->max_chunk, s);
+                      reinterpret_cast<unsigned int*>(b->d_scratch), b->ctas_per_sm, b->max_chunk, s);
   if (!rc && b->jag_tiles)
     rc = launch_batch_jag(b->d_jag, b->d_tile_job, b->jag_tiles, reinterpret_cast<unsigned int*>(b->d_scratch + 64),
                           reinterpret_cast<unsigned long long*>(b->d_scratch + 256), s);

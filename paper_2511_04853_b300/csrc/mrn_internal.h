@@ -131,7 +131,7 @@ int launch_fill_from(char* dst, const char* from, uint64_t count, uint32_t elem,
 // Persistent launch of a batch (mrn_batch.cpp owns the device tables);
 // max_chunk caps the consecutive tiles a CTA takes at once.
 int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, unsigned int njobs,
-                 unsigned long long total_tiles, unsigned int* counter, unsigned long long* states,
+                 unsigned long long total_tiles, unsigned int* counter,
                  unsigned int ctas_per_sm, unsigned int max_chunk, void* stream);
 // The jagged AoS -> field-major jobs of a batch (their own tile numbering,
 // tile_job[t] = job of tile t), one CTA per tile.

@@ -116,17 +116,9 @@ __device__ __forceinline__ uint64_t read_offset(const char* offs, uint32_t osz, 
   return __ldg(reinterpret_cast<const unsigned long long*>(offs) + i);
 }
 
-// Barrier of the 256 threads running a jagged tile: __syncthreads() in the
-// per-call kernel; a bounded mbarrier barrier among the consumer warps in the
-// batch kernel (see ConsumerSync).
-struct CtaSync {
-  __device__ __forceinline__ void operator()() const { __syncthreads(); }
-};
-
-// Shared state of a jagged tile.  The per-parent arrays (JagShared) are
-// written only after every warp has finished its parent conversion, so the
-// batch kernel lays them over its lane-word scratch; the small per-warp
-// values (JagWarp) are written earlier and need their own space.
+// Shared state of a jagged tile: per-parent arrays (JagShared), written only
+// after every warp has finished its parent conversion, and small per-warp
+// values (JagWarp).
 struct JagShared {
   unsigned long long excl[MRN_JAG_TILE + 1];
   unsigned long long beg[MRN_JAG_TILE];
@@ -432,17 +424,14 @@ __device__ __forceinline__ unsigned long long jagged_lookback(const JagPlan& jp,
 // (256 threads, two parents each): converts the parents, scans their
 // lengths, obtains the tile's child base by a decoupled look-back over the
 // predecessors' published sums in `st`, writes the offsets and gathers the
-// tile's children, load-balanced over the tile's threads.  Every
-// predecessor's word must be published independently of this tile's
-// progress: either each tile publishes its own sum first (Published =
-// false; tiles handed out in increasing order, so every predecessor is
-// already running), or whoever hands out the tiles has published every sum
-// beforehand (Published = true: the tile only publishes its inclusive
-// prefix).
-template <int VP, int VC, class Sync = CtaSync, bool Published = false, int W = MRN_WIN_WORDS, bool SmallRun = true>
+// tile's children, load-balanced over the tile's threads.  Each tile
+// publishes its own sum before its look-back, and tiles are handed out in
+// increasing order, so every predecessor a look-back waits for is already
+// running.
+template <int VP, int VC>
 __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile, unsigned long long* st,
-                                                uint32_t* tw_all, JagShared& sh, JagWarp& sw,
-                                                const Sync& sync = Sync()) {
+                                                uint32_t* tw_all, JagShared& sh, JagWarp& sw) {
+  constexpr int W = MRN_WIN_WORDS;
   static_assert(MRN_JAG_TILE == 2 * MRN_JAG_THREADS, "two parents per thread");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t* tw = tw_all + warp * MRN_TW_WORDS(W);
@@ -451,9 +440,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
 
   // Parents q = tid and q = 256 + tid of the tile (consecutive records per
   // warp); then their lengths go to excl[] for the scan and their begins
-  // (all ones for a parent whose children lie outside the pool) to beg[],
-  // once every warp is done with its lane words (the batch kernel lays
-  // these arrays over them).
+  // (all ones for a parent whose children lie outside the pool) to beg[].
   uint32_t len[2];
   uint64_t beg[2];
 #pragma unroll
@@ -470,13 +457,13 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
       beg[k] = ~0ull;
     }
   }
-  sync();
+  __syncthreads();
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     sh.excl[k * MRN_JAG_THREADS + tid] = len[k];
     sh.beg[k * MRN_JAG_THREADS + tid] = beg[k];
   }
-  sync();
+  __syncthreads();
 
   // CTA-wide exclusive scan in parent order: thread t owns parents 2t and
   // 2t + 1 (64-bit sums).
@@ -489,7 +476,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
     if (lane >= o) x += y;
   }
   if (lane == 31) sw.warp[warp] = x;
-  sync();
+  __syncthreads();
   if (warp == 0) {
     unsigned long long t = lane < 8 ? sw.warp[lane] : 0ull;
 #pragma unroll
@@ -499,7 +486,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
     }
     if (lane < 8) sw.warp[lane] = t;
   }
-  sync();
+  __syncthreads();
   const unsigned long long e0 = x - (l0 + l1) + (warp > 0 ? sw.warp[warp - 1] : 0ull), e1 = e0 + l0;
   const unsigned long long agg = sw.warp[7];
   sh.excl[2 * tid] = e0;
@@ -530,15 +517,15 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
     const bool publish = (long long)tile != jp.skip_publish_tile;
     unsigned long long prefix = 0;
     if (tile == 0) {
-      if (!Published && publish && lane == 0) st_release_u64(&st[0], MRN_TS_PREFIX | (agg & MRN_TS_VALUE));
+      if (publish && lane == 0) st_release_u64(&st[0], MRN_TS_PREFIX | (agg & MRN_TS_VALUE));
     } else {
-      if (!Published && publish && lane == 0) st_release_u64(&st[tile], MRN_TS_AGG | (agg & MRN_TS_VALUE));
+      if (publish && lane == 0) st_release_u64(&st[tile], MRN_TS_AGG | (agg & MRN_TS_VALUE));
       prefix = jagged_lookback(jp, tile, st, lane);
       if (publish && lane == 0) st_release_u64(&st[tile], MRN_TS_PREFIX | ((prefix + agg) & MRN_TS_VALUE));
     }
     if (lane == 0) sw.base = prefix;
   }
-  sync();
+  __syncthreads();
   const unsigned long long base = sw.base;
   // Children in one run of the pool: start pulling their source range into
   // L2 while the offsets are written.
@@ -579,7 +566,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
   }
 
   // Children, as one run of the pool when they form one.
-  if (SmallRun && run && jp.child.stride <= 8)
+  if (run && jp.child.stride <= 8)
     jagged_run_small<kJagSlots>(jp, agg, base, kmin, lane, warp);
   else if (run)
     jagged_children<true>(jp, sh, agg, base, kmin, lane, warp);
@@ -695,7 +682,6 @@ __global__ void k_write_offset0(char* offs, uint32_t osz, unsigned long long v) 
 //   ready[i] / rel[i]   ring slot i written / read by all consumer warps
 //   full[s] / empty[s]  source stage s loaded / read by all consumer warps
 //   done[d] / dfree[d]  destination buffer d written / read by its stores
-//   cbar                barrier of the consumer warps (jagged tiles only)
 // Each stage carries its job's column descriptors, written by the loader
 // before the stage's loads.  Every wait is bounded; on expiry the warp that
 // saw it records MRN_ETIMEOUT and stops, and the others follow.
@@ -729,17 +715,15 @@ struct StoreItem {
   unsigned int records;  // records of the tile (T, or fewer for a job's partial staged tile)
 };
 
-// Consumer scratch: 8 warps' lane words in 32-byte windows (a jagged tile's
-// JagShared lies over them), then a jagged tile's JagWarp.
+// Consumer scratch: 8 warps' lane words in 32-byte windows.
 constexpr uint32_t kBWin = 8;
 constexpr size_t kBTw = 8 * MRN_TW_WORDS(kBWin) * sizeof(uint32_t);
-static_assert(sizeof(JagShared) <= kBTw, "jagged tile arrays fit the lane-word scratch");
-constexpr size_t kBScratch = (kBTw + sizeof(JagWarp) + 15) / 16 * 16;
+constexpr size_t kBScratch = (kBTw + 15) / 16 * 16;
 constexpr size_t kBOffDst = (size_t)kBNS * kBStage;
 constexpr size_t kBOffScratch = kBOffDst + (size_t)kBND * kBStage;
 constexpr size_t kBOffDesc = kBOffScratch + kBScratch;
 constexpr size_t kBOffBar = kBOffDesc + kBNS * sizeof(StageDesc);
-constexpr size_t kBNumBars = 2 * kBNS + 2 * kBND + 2 * kRing + 1;
+constexpr size_t kBNumBars = 2 * kBNS + 2 * kBND + 2 * kRing;
 constexpr size_t kBOffRing = kBOffBar + kBNumBars * 8;
 constexpr size_t kBOffSQ = kBOffRing + kRing * sizeof(TileSlot);
 constexpr size_t kBOffFlag = kBOffSQ + kSQ * sizeof(StoreItem);
@@ -765,7 +749,6 @@ struct BatchSmem {
   __device__ __forceinline__ unsigned long long* rel(uint32_t i) const {
     return bar(2 * kBNS + 2 * kBND + kRing + i);
   }
-  __device__ __forceinline__ unsigned long long* cbar() const { return bar(2 * kBNS + 2 * kBND + 2 * kRing); }
   __device__ __forceinline__ TileSlot* ring(uint32_t i) const {
     return reinterpret_cast<TileSlot*>(base + kBOffRing) + i;
   }
@@ -782,21 +765,6 @@ struct BatchSmem {
 __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-
-// Barrier of the 8 consumer warps on an mbarrier (one arrival per warp,
-// bounded wait).  Every consumer thread passes the same sequence of these
-// barriers and counts them in `phase`; a failed wait clears `ok`.
-struct ConsumerSync {
-  unsigned long long* bar;
-  uint32_t* phase;
-  bool* ok;
-  __device__ __forceinline__ void operator()() const {
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
-    if (!mbar_wait_bounded(bar, *phase & 1)) *ok = false;
-    ++*phase;
-  }
-};
 
 // Bytes of the first R records (a multiple of the staging granule) of a
 // tile side whose full tile is `full` bytes.
@@ -884,35 +852,6 @@ __device__ __forceinline__ unsigned int advance_job(const unsigned long long* __
   return lo;
 }
 
-// Loader warp, on taking tiles [t0, t1): publishes the child count of each
-// jagged AoS -> SoA tile among them (the inclusive prefix for a job's first
-// tile), before any of them is decided.  A tile's look-back then waits only
-// for chunks taken before its own, never for another CTA's consumers.
-__device__ __forceinline__ void publish_jagged_sums(const BatchJob* __restrict__ jobs,
-                                                    const unsigned long long* __restrict__ first_tile,
-                                                    unsigned int njobs, unsigned long long total_tiles,
-                                                    unsigned long long* states, uint64_t t0, uint64_t t1,
-                                                    unsigned int* cursor, int lane) {
-  for (uint64_t t = t0; t < t1 && t < total_tiles; ++t) {
-    *cursor = advance_job(first_tile, njobs, *cursor, t, lane);
-    const BatchJob& J = jobs[*cursor];
-    if (J.kind != JOB_JAG_A2S) {
-      t = J.tile_begin + J.ntiles - 1;  // the job's other tiles publish nothing either
-      continue;
-    }
-    const JagPlan& jp = J.jp;
-    const uint64_t local = t - J.tile_begin;
-    const uint64_t r0 = local * MRN_JAG_TILE, n = jp.parent.n;
-    unsigned long long sum = 0;
-    for (uint64_t r = r0 + lane; r < r0 + MRN_JAG_TILE && r < n; r += 32)
-      sum += __ldg(reinterpret_cast<const unsigned int*>(jp.parent.src.base + r * jp.parent.stride + jp.len_off));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0 && (long long)local != jp.skip_publish_tile)
-      st_release_u64(&states[J.tile_begin + local], (local == 0 ? MRN_TS_PREFIX : MRN_TS_AGG) | (sum & MRN_TS_VALUE));
-  }
-}
-
 // Loader warp: decides tiles in order (lane 0 decides, the warp follows)
 // and issues the loads of staged ones; returns after publishing the
 // end-of-work slot, or on abort once its loads in flight have landed.
@@ -920,14 +859,13 @@ template <bool kStatic>
 __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
                                              const unsigned long long* __restrict__ first_tile,
                                              unsigned int njobs, unsigned long long total_tiles,
-                                             unsigned int* counter, unsigned long long* states,
+                                             unsigned int* counter,
                                              uint32_t chunk, unsigned int first_start, unsigned int first_size,
                                              const BatchSmem& m, int lane) {
   uint64_t k_issue = 0;  // tiles decided
   uint32_t c_issue = 0;  // staged tiles loaded
   unsigned int cursor = 0;
   uint64_t next_t = 0, chunk_end = 0;
-  unsigned int pcursor = 0;
   uint32_t n_chunks = 0;  // static assignment: chunks taken so far
   uint64_t seen = 0;      // dynamic assignment: end of the last chunk taken
   uint64_t snap = 0;      // the counter, read while deciding a chunk's last tile
@@ -965,8 +903,6 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
           next_t = __shfl_sync(0xffffffffu, start, 0);
           chunk_end = next_t + __shfl_sync(0xffffffffu, size, 0);
           seen = chunk_end;
-          if (states)  // a batch without jagged AoS -> SoA jobs publishes nothing
-            publish_jagged_sums(jobs, first_tile, njobs, total_tiles, states, next_t, chunk_end, &pcursor, lane);
         }
       }
       // read early, so that the load's latency hides behind this tile's
@@ -1108,7 +1044,7 @@ template <bool kStatic>
 __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
                                            const unsigned long long* __restrict__ first_tile, unsigned int njobs,
                                            unsigned long long total_tiles, unsigned int* counter,
-                                           unsigned long long* states, uint32_t chunk, char* batch_smem) {
+                                           uint32_t chunk, char* batch_smem) {
   BatchSmem m{batch_smem};
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if constexpr (!kStatic) {
@@ -1124,7 +1060,7 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
   }
   // warp 0 initializes the barriers, one per lane
   if (warp == 0) {
-    constexpr uint32_t kBars = 2 * kBNS + 2 * kBND + 2 * kRing + 1;
+    constexpr uint32_t kBars = (uint32_t)kBNumBars;
     static_assert(kBars <= 32, "one barrier per lane");
     if ((uint32_t)lane < kBars) {
       const uint32_t i = lane;
@@ -1134,7 +1070,7 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
       else if (i < 2 * kBNS + kBND) count = 8;                  // done
       else if (i < 2 * kBNS + 2 * kBND) count = 1;              // dfree
       else if (i < 2 * kBNS + 2 * kBND + kRing) count = 1;      // ready
-      else count = 8;                                           // rel, cbar
+      else count = 8;                                           // rel
       mbar_init(m.bar(i), count);
       fence_mbar_init();
     }
@@ -1151,7 +1087,7 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
   }
   __syncthreads();
   if (warp == 8) {
-    batch_loader<kStatic>(jobs, first_tile, njobs, total_tiles, counter, states, chunk, first_start, first_size, m,
+    batch_loader<kStatic>(jobs, first_tile, njobs, total_tiles, counter, chunk, first_start, first_size, m,
                           lane);
     return;
   }
@@ -1162,11 +1098,7 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
   // consumers
   uint32_t* scratch = m.scratch();
   uint32_t* tw = scratch + warp * MRN_TW_WORDS(kBWin);
-  JagShared& sh = *reinterpret_cast<JagShared*>(scratch);
-  JagWarp& sw = *reinterpret_cast<JagWarp*>(reinterpret_cast<char*>(scratch) + kBTw);
-  uint32_t cphase = 0;
   bool ok = true;
-  const ConsumerSync sync{m.cbar(), &cphase, &ok};
   uint32_t c = 0;  // staged tiles consumed
   for (uint64_t k = 0;; ++k) {
     const uint32_t slot = k % kRing;
@@ -1206,13 +1138,6 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
           r1 = r0 + J.tile_records;
         }
         conv_range<0, kBWin>(P, r0, r1, tw, lane, warp, 8);
-      } else if (J.kind == JOB_JAG_A2S) {
-        jagged_a2s_tile<0, 0, ConsumerSync, true, kBWin, false>(J.jp, local, states + J.tile_begin, scratch, sh,
-                                                                sw, sync);
-        // the tile's arrays lie over the lane words: every warp is done
-        // reading them before any warp's next tile writes its lane words
-        sync();
-        if (!ok) break;
       } else if (J.kind == JOB_JAG_S2A) {
         jagged_s2a_group<0, 0, kBWin>(J.jp, local * 8 + warp, J.parent_groups, tw, lane);
       } else {
@@ -1231,10 +1156,9 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
 __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restrict__ jobs,
                                                         const unsigned long long* __restrict__ first_tile,
                                                         unsigned int njobs, unsigned long long total_tiles,
-                                                        unsigned int* counter, unsigned long long* states,
-                                                        uint32_t chunk) {
+                                                        unsigned int* counter, uint32_t chunk) {
   extern __shared__ __align__(128) char batch_smem[];
-  batch_main<false>(jobs, first_tile, njobs, total_tiles, counter, states, chunk, batch_smem);
+  batch_main<false>(jobs, first_tile, njobs, total_tiles, counter, chunk, batch_smem);
 }
 
 // One staged conversion through the same warp-specialized pipeline: the
@@ -1245,7 +1169,7 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
 __global__ void __launch_bounds__(kBThreads, 3) k_convert_ws(const __grid_constant__ BatchJob job,
                                                              uint32_t chunk, unsigned int* counter) {
   extern __shared__ __align__(128) char batch_smem[];
-  batch_main<true>(&job, nullptr, 1u, job.ntiles, counter, nullptr, chunk, batch_smem);
+  batch_main<true>(&job, nullptr, 1u, job.ntiles, counter, chunk, batch_smem);
 }
 
 // ================================================================== host
@@ -1535,7 +1459,7 @@ int launch_batch_jag(const BatchJob* jobs, const unsigned int* tile_job, unsigne
 }
 
 int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, unsigned int njobs,
-                 unsigned long long total_tiles, unsigned int* counter, unsigned long long* states,
+                 unsigned long long total_tiles, unsigned int* counter,
                  unsigned int ctas_per_sm, unsigned int max_chunk, void* stream) {
   if (total_tiles == 0) return MRN_OK;
   const int occ = batch_occupancy();
@@ -1549,7 +1473,7 @@ int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, uns
   const uint64_t chunks = (total_tiles + chunk - 1) / chunk;
   const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(cap, chunks));
   k_batch<<<grid, kBThreads, kBatchSmem, static_cast<cudaStream_t>(stream)>>>(jobs, first_tile, njobs,
-                                                                                total_tiles, counter, states, chunk);
+                                                                                total_tiles, counter, chunk);
   return cuda_status(cudaGetLastError());
 }
 
