@@ -589,7 +589,10 @@ __global__ void __launch_bounds__(MRN_JAG_THREADS, 6) k_jagged_a2s(const __grid_
 // k_jagged_a2s (6 CTAs per SM: the scan and the gather are latency-bound
 // and want many warps), tiles taken in increasing order over all the jobs,
 // each tile's job read from a host-built map.  A tile's look-back only
-// visits its own job's earlier tiles, which hold earlier tickets.
+// visits its own job's earlier tiles, which hold earlier tickets.  The
+// job's plan is copied into shared memory first: the tile reads its fields
+// all along, and from global memory (not the constant bank, where a single
+// conversion's plan sits) those reads cost the batch a quarter of its speed.
 __global__ void __launch_bounds__(MRN_JAG_THREADS, 6) k_batch_jag(const BatchJob* __restrict__ jobs,
                                                                  const unsigned int* __restrict__ tile_job,
                                                                  unsigned long long total, unsigned int* counter,
@@ -598,12 +601,17 @@ __global__ void __launch_bounds__(MRN_JAG_THREADS, 6) k_batch_jag(const BatchJob
   __shared__ JagShared sh;
   __shared__ JagWarp sw;
   __shared__ unsigned int s_tile;
+  __shared__ __align__(16) unsigned long long jps[(sizeof(JagPlan) + 7) / 8];
   if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
   __syncthreads();
   const uint64_t t = s_tile;
   if (t >= total) return;
   const BatchJob& J = jobs[__ldg(tile_job + t)];
-  jagged_a2s_tile<0, 0>(J.jp, t - J.tile_begin, states + J.tile_begin, tw_all, sh, sw);
+  const unsigned long long* g = reinterpret_cast<const unsigned long long*>(&J.jp);
+  for (uint32_t i = threadIdx.x; i < sizeof(JagPlan) / 8; i += blockDim.x) jps[i] = __ldg(g + i);
+  const uint64_t tb = J.tile_begin;
+  __syncthreads();
+  jagged_a2s_tile<0, 0>(*reinterpret_cast<const JagPlan*>(jps), t - tb, states + tb, tw_all, sh, sw);
 }
 
 // One warp group of a jagged SoA -> AoS conversion: groups [0,
