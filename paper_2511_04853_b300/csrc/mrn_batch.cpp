@@ -104,7 +104,8 @@ int plan_job(const mrn_view& src, const mrn_view& dst, std::vector<BatchJob>* ou
     if ((rc = build_jagged_plan(src, dst, &j.jp))) return rc;
     if (src.layout.kind == MRN_AOS) {
       j.kind = JOB_JAG_A2S;
-      j.ntiles = (jagged_tile_records(j.jp) + MRN_JAG_TILE - 1) / MRN_JAG_TILE;
+      // an empty collection still has one tile: it writes offsets[0]
+      j.ntiles = std::max<uint64_t>(1, (jagged_tile_records(j.jp) + MRN_JAG_TILE - 1) / MRN_JAG_TILE);
     } else {
       // children: a plain conversion job; this job builds the parents
       BatchJob kids;

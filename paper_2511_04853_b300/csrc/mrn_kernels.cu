@@ -546,7 +546,9 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
       bulk_prefetch_l2(reinterpret_cast<const void*>(q), (uint32_t)min((uintptr_t)32768, hi - q));
   }
 
-  // Offsets: offset_base + children before this parent.
+  // Offsets: offset_base + children before this parent (a collection of
+  // no objects, given one tile, has the single offset offset_base).
+  if (P.n == 0 && tid == 0) write_offset(jp.offsets, jp.off_size, 0, jp.offset_base);
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const uint64_t r = t0 + 2 * tid + k;

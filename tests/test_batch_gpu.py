@@ -248,3 +248,30 @@ def test_jagged_aosoa_jobs_in_a_batch():
     c = mrn.View(s, "aosoa", 10, block=32, base=garbage(1 << 12), m=1)
     with pytest.raises(mrn.MrnError):
         mrn.Batch([(a, c)], use_graph=False)
+
+
+def test_empty_jobs_in_a_batch():
+    """Collections of zero objects in a batch: a jagged AoS -> SoA job still
+    writes its single offset (0), the others write nothing, and the jobs
+    around them are unaffected."""
+    jobs = make_jobs(31, 6)
+    for name in ("tracks", "cells", "points"):
+        desc = datagen.WORKLOAD_SCHEMAS[name]
+        s, o = mrn.Schema(desc), oracle.Schema(desc)
+        d = datagen.workload(name, 0, 5)
+        o_src = oracle.pack(o, d, "aos")
+        dk = "soa" if name != "points" else "aosoa"
+        o_dst = oracle.convert(o, o_src, dk, 32 if dk == "aosoa" else 0, m=0)
+        src = mrn.View(s, "aos", 0, base=dev(o_src.base), child_pool=dev(o_src.pool) if name == "tracks" else None)
+        dst = dev_dest(s, dk, 0, 0, 32 if dk == "aosoa" else 0)
+        # only the layout's own bytes (none for a plain empty collection)
+        jobs.append((src, dst, o_dst.base[: s.required_bytes(dk, 0, 0, 32 if dk == "aosoa" else 0)], name))
+    jobs += make_jobs(32, 6)
+    for use_graph in (True, False):
+        for _, d, _, _ in jobs:
+            d.tensors[0].fill_(0xA5)
+        b = mrn.Batch([(s, d) for s, d, _, _ in jobs], use_graph=use_graph)
+        b.launch()
+        assert mrn.sync() == mrn.OK
+        for i, (s, d, want, name) in enumerate(jobs):
+            assert np.array_equal(result(d, want, name), want), "job %d (%s)" % (i, name)
