@@ -617,7 +617,7 @@ def run_mine(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_e2e(mrn, torch, s, colls, args, world, n_streams=2):
+def run_e2e(mrn, torch, s, colls, args, world, n_streams=2, chunk_bytes=0):
     """Host pinned AoS -> device SoA, SoA -> AoSoA(32), device AoSoA(32) ->
     host pinned AoS for every collection of the batch, per step."""
     n = N_RECORDS
@@ -643,9 +643,9 @@ def run_e2e(mrn, torch, s, colls, args, world, n_streams=2):
             st.wait_stream(main)
         for i, (hin, soa, blk, hout) in enumerate(views):
             st = streams[i % len(streams)]
-            mrn.transfer_convert(hin, soa, stream=st)
+            mrn.transfer_convert(hin, soa, chunk_bytes=chunk_bytes, stream=st)
             mrn.convert(soa, blk, stream=st)
-            mrn.transfer_convert(blk, hout, stream=st)
+            mrn.transfer_convert(blk, hout, chunk_bytes=chunk_bytes, stream=st)
         for st in streams:
             main.wait_stream(st)
 
