@@ -334,7 +334,7 @@ def run_mixed(mrn, torch, stream, peak, args):
     import datagen
     plan = mixed_plan(args.mixed_jobs)
     schemas = {k: mrn.Schema(datagen.WORKLOAD_SCHEMAS[k]) for k in MIXED_SCHEMAS}
-    pairs, outs, alg = [], [], 0
+    pairs, outs, alg, alg_jag = [], [], 0, 0
     t_setup = time.perf_counter()
     for i, (name, n, (dk, db)) in enumerate(plan):
         s = schemas[name]
@@ -346,6 +346,7 @@ def run_mixed(mrn, torch, stream, peak, args):
         outs.append(out)
         if name == "tracks":
             alg += 24 * n + 8 * m + 12 * n + 4 * (n + 1) + 8 * m
+            alg_jag += 24 * n + 8 * m + 12 * n + 4 * (n + 1) + 8 * m
         else:
             alg += n * (s.stride + sum(c["size"] for c in s.columns))
     torch.cuda.synchronize()
@@ -367,7 +368,8 @@ def run_mixed(mrn, torch, stream, peak, args):
     res = {"workload": "%d collections, records round(10^U(3,6)), schema uniform over points / cells / "
                        "tracks (jagged, Poisson(20) children clipped at 256), AoS source, target uniform over "
                        "SoA / AoSoA(32) / AoSoA(128)" % len(plan),
-           "records": sum(n for _, n, _ in plan), "algorithmic_bytes": alg, "setup_s": round(setup_s, 1)}
+           "records": sum(n for _, n, _ in plan), "algorithmic_bytes": alg,
+           "algorithmic_bytes_jagged_jobs": alg_jag, "setup_s": round(setup_s, 1)}
     # autotuner off: the library's default shapes
     mrn.autotune_clear()
     plain = mrn.Batch(pairs, use_graph=True)
