@@ -138,16 +138,11 @@ int plan_job(const mrn_view& src, const mrn_view& dst, std::vector<BatchJob>* ou
   return MRN_OK;
 }
 
-// Approximate bytes read and written by one tile of a job.
+// Approximate bytes read and written by one tile of a job of k_batch.
 double tile_traffic(const BatchJob& j) {
   switch (j.kind) {
     case JOB_CONVERT:
       return (double)j.tile_records * 2.0 * j.jp.parent.stride;
-    case JOB_JAG_A2S: {
-      const JagPlan& jp = j.jp;
-      const double kids = jp.parent.n ? (double)jp.pool_n / (double)jp.parent.n : 0.0;
-      return MRN_JAG_TILE * (2.0 * jp.parent.stride + jp.off_size + 2.0 * kids * jp.child.stride);
-    }
     case JOB_JAG_S2A:
       return 8.0 * 32.0 * 2.0 * j.jp.parent.stride;
     default:
