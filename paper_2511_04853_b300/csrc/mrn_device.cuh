@@ -421,6 +421,10 @@ __device__ __forceinline__ void sts32(uint32_t a, uint32_t v) {
 __device__ __forceinline__ void sts64(uint32_t a, uint2 v) {
   asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(a), "r"(v.x), "r"(v.y) : "memory");
 }
+__device__ __forceinline__ void sts128(uint32_t a, uint4 v) {
+  asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
 __device__ __forceinline__ void sts128_zero(uint32_t a) {
   asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(a), "r"(0u) : "memory");
 }
@@ -527,8 +531,51 @@ __device__ __forceinline__ void tile_class(uint32_t desc, uint32_t c0, uint32_t 
 // serves every pair of layouts, so tiles of different layout pairs running
 // side by side share their instructions; each size class is a loop of its
 // own, so no element access branches on its size.
+// An AoS <-> SoA tile whose AoS record is W (2 or 4) 4-byte words, the
+// columns in order (h.packed): the record moves as one 8- or 16-byte vector
+// on the AoS side, and word k to or from its SoA column.  Narrow records
+// are bound by the per-column work of the general body.
+template <int W>
+__device__ __forceinline__ void tile_convert_packed(const TileHdr& h, uint32_t desc, uint32_t st, uint32_t dt,
+                                                    uint32_t r0, bool two) {
+  const bool a2s = h.sshift == 0;  // AoS source (a row per record)
+  uint32_t off[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    const uint4 d = lds128(desc + k * 16);
+    off[k] = a2s ? d.z : d.y;  // the SoA side's column offset in the tile
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    if (q == 1 && !two) break;
+    const uint32_t r = r0 + 256 * q;
+    if (a2s) {
+      if constexpr (W == 2) {
+        const uint2 v = lds64(st + r * 8);
+        sts32(dt + off[0] + r * 4, v.x);
+        sts32(dt + off[1] + r * 4, v.y);
+      } else {
+        const uint4 v = lds128(st + r * 16);
+        sts32(dt + off[0] + r * 4, v.x);
+        sts32(dt + off[1] + r * 4, v.y);
+        sts32(dt + off[2] + r * 4, v.z);
+        sts32(dt + off[3] + r * 4, v.w);
+      }
+    } else {
+      if constexpr (W == 2) {
+        sts64(dt + r * 8, make_uint2(lds32(st + off[0] + r * 4), lds32(st + off[1] + r * 4)));
+      } else {
+        sts128(dt + r * 16, make_uint4(lds32(st + off[0] + r * 4), lds32(st + off[1] + r * 4),
+                                       lds32(st + off[2] + r * 4), lds32(st + off[3] + r * 4)));
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ void tile_convert(const TileHdr& h, uint32_t desc, uint32_t st, uint32_t dt,
                                              uint32_t r0, bool two) {
+  if (h.packed == 2) return tile_convert_packed<2>(h, desc, st, dt, r0, two);
+  if (h.packed == 4) return tile_convert_packed<4>(h, desc, st, dt, r0, two);
   const uint32_t r1 = two ? r0 + 256 : r0;
   uint32_t sb0, si0, db0, di0, sb1, si1, db1, di1;
   tile_row(h.sblock, h.sshift, h.sbb, st, r0, &sb0, &si0);

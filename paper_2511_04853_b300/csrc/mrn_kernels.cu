@@ -81,6 +81,14 @@ __host__ __device__ __forceinline__ TileHdr tile_hdr(const ConvPlan& p) {
   h.pad = p.dst.kind == K_AOS ? p.tg.pad : 0u;
   h.T = p.tg.T;
   h.nsize = p.tg.nsize;
+  h.packed = 0;
+  const uint32_t n4 = (p.tg.nsize >> 8) & 0xff;
+  if (((p.src.kind == K_AOS && p.dst.kind == K_SOA) || (p.src.kind == K_SOA && p.dst.kind == K_AOS)) &&
+      p.tg.nsize == (n4 << 8) && (n4 == 2 || n4 == 4) && p.ncols == n4 && p.stride == 4 * n4) {
+    bool in_order = true;
+    for (uint32_t k = 0; k < n4; ++k) in_order = in_order && (p.tg.col[p.tg.order[k]] & 0xffffffu) == 4 * k;
+    if (in_order) h.packed = n4;
+  }
   tile_side_geometry(p.src.kind, p.src.block, p.src.block_shift, p.src.block_bytes, p.stride, &h.sblock, &h.sshift,
                      &h.sbb);
   tile_side_geometry(p.dst.kind, p.dst.block, p.dst.block_shift, p.dst.block_bytes, p.stride, &h.dblock, &h.dshift,
@@ -713,7 +721,7 @@ struct TileSlot {
 // A stage's table in shared memory: the layout of StageRec, read as uint4.
 struct StageDesc {
   TileHdr h;
-  unsigned int pad[4];
+  unsigned int pad[3];
   uint4 d[MRN_MAX_COLS];
 };
 static_assert(sizeof(StageDesc) == sizeof(StageRec), "a stage table is a StageRec");

@@ -63,6 +63,10 @@ struct TileHdr {
   uint32_t ncols, stride, vec, pad, T, nsize;
   uint32_t sblock, sshift, sbb;  // source row geometry
   uint32_t dblock, dshift, dbb;  // destination row geometry
+  // 2 or 4: an AoS <-> SoA pair of that many 4-byte columns, the AoS
+  // record being exactly those words in column order (records move as one
+  // vector); 0 otherwise
+  uint32_t packed;
 };
 
 // What the consumers of a staged tile read: the header and one descriptor
@@ -71,7 +75,7 @@ struct TileHdr {
 // it into a stage's table with one bulk copy beside the tile's data.
 struct alignas(16) StageRec {
   TileHdr h;
-  uint32_t pad[4];
+  uint32_t pad[3];
   uint32_t d[MRN_MAX_COLS][4];
 };
 

@@ -22,11 +22,13 @@ NESTED = [("a", "u8", 1),
 ODD = [("a", "u8", 1), ("b", "u16", 1)]                 # 4-byte record, 2-byte fields
 TINY = [("a", "u8", 3)]                                 # 3-byte record: byte accesses
 WIDE = [("v%d" % i, "f64" if i % 3 == 0 else "u16", 1) for i in range(40)]  # > 64-byte record
+PACK2 = [("index", "u32", 1), ("weight", "f32", 1)]       # records of two 4-byte words
+PACK4 = [("a", "i32", 1), ("v", "f32", 3)]                 # four 4-byte words (an array of 3)
 
 
 def schemas():
     return {"points": datagen.POINTS, "cells": datagen.CELLS, "sensor": datagen.SENSOR,
-            "nested": NESTED, "odd": ODD, "tiny": TINY, "wide": WIDE}
+            "nested": NESTED, "odd": ODD, "tiny": TINY, "wide": WIDE, "pack2": PACK2, "pack4": PACK4}
 
 
 def data_for(name, n, seed=0, raw=False):
@@ -178,3 +180,14 @@ def test_large_staged_conversions(name, n):
     for (sk, sb), (dk, db) in [(("aos", 0), ("soa", 0)), (("soa", 0), ("aosoa", 128)),
                                (("aosoa", 32), ("aos", 0))]:
         check_pair(name, n, sk, sb, dk, db, seed=11)
+
+
+@pytest.mark.parametrize("name", ["pack2", "pack4"])
+@pytest.mark.parametrize("n", [31, 32, 1000, 1536 * 3 + 64, 100003, 9_000_001])
+def test_packed_records_aos_soa(name, n):
+    """Records that are exactly two or four 4-byte words, in column order,
+    move between AoS and SoA as one vector per record in the staged
+    transform; full tiles, partial tiles and the large-conversion path."""
+    check_pair(name, n, "aos", 0, "soa", 0, seed=3)
+    check_pair(name, n, "soa", 0, "aos", 0, seed=4)
+    check_pair(name, n, "aos", 0, "aosoa", 32, seed=5)
