@@ -596,14 +596,16 @@ __global__ void __launch_bounds__(MRN_JAG_THREADS, 6) k_jagged_a2s(const __grid_
 }
 
 // The jagged AoS -> field-major jobs of a batch: one CTA per tile as in
-// k_jagged_a2s (6 CTAs per SM: the scan and the gather are latency-bound
-// and want many warps), tiles taken in increasing order over all the jobs,
+// k_jagged_a2s, 7 CTAs per SM (the scan and the gather are latency-bound
+// and want many warps; measured 7% faster than 6 here, while the
+// single-conversion kernel, whose plan sits in the constant bank, is
+// faster at 6), tiles taken in increasing order over all the jobs,
 // each tile's job read from a host-built map.  A tile's look-back only
 // visits its own job's earlier tiles, which hold earlier tickets.  The
 // job's plan is copied into shared memory first: the tile reads its fields
 // all along, and from global memory (not the constant bank, where a single
 // conversion's plan sits) those reads cost the batch a quarter of its speed.
-__global__ void __launch_bounds__(MRN_JAG_THREADS, 6) k_batch_jag(const BatchJob* __restrict__ jobs,
+__global__ void __launch_bounds__(MRN_JAG_THREADS, 7) k_batch_jag(const BatchJob* __restrict__ jobs,
                                                                  const unsigned int* __restrict__ tile_job,
                                                                  unsigned long long total, unsigned int* counter,
                                                                  unsigned long long* states) {
