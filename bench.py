@@ -57,7 +57,7 @@ def parse():
                     help="profiling runs: only the timed device step (no e2e, baselines or extras)")
     ap.add_argument("--case", default=None,
                     help="profiling runs: repeat one conversion, e.g. cells:aos:soa:16777216 "
-                         "(schema:src[/B]:dst[/B]:records)")
+                         "(schema:src[/B]:dst[/B]:records), or one overlapping move, memmove:bytes:shift")
     ap.add_argument("--mixed-jobs", type=int, default=4096,
                     help="collections in the mixed batch (0 skips it)")
     ap.add_argument("--mixed-only", action="store_true", help="run the mixed batch alone")
@@ -1080,6 +1080,25 @@ def run_case(args):
     import torch
     import paper_2511_04853_b300 as mrn
     import datagen
+    if args.case.startswith("memmove:"):
+        # memmove:bytes:shift -- one overlapping move inside a device buffer
+        _, nb, shift = args.case.split(":")
+        nb, shift = int(nb), int(shift)
+        buf = torch.empty(nb + 2 * abs(shift) + 256, dtype=torch.uint8, device="cuda")
+        src = buf.data_ptr() + abs(shift) + 128
+        for _ in range(args.warmup):
+            mrn.memmove(src + shift, src, nb)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            mrn.memmove(src + shift, src, nb)
+        e1.record()
+        torch.cuda.synchronize()
+        assert mrn.sync() == mrn.OK
+        ms = e0.elapsed_time(e1) / args.steps
+        print(json.dumps({"case": args.case, "ms": round(ms, 5), "gbps": round(2 * nb / (ms * 1e-3) / 1e9, 1)}),
+              flush=True)
+        return
     name, sk, dk, n = args.case.split(":")
     n = int(n)
 
