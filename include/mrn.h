@@ -305,14 +305,16 @@ typedef struct mrn_job {
 typedef struct mrn_batch mrn_batch; /* opaque */
 
 /* Prepares many independent conversions (any schemas, any supported layout
- * pairs, jagged AoS<->SoA included) to run in ONE persistent kernel launch:
- * a device job table, a prefix over the jobs' tiles, per-job tile sizes from
- * the autotuner cache.  With use_graph = 1 the launch sequence (scratch
- * reset + persistent kernel) is captured once into a CUDA graph and each
- * mrn_batch_launch replays it.  The views' buffers must stay valid while the
- * batch is used.  Copies the job descriptions; `jobs` may be freed. */
+ * pairs, jagged AoS<->SoA included) to run in one persistent kernel launch,
+ * plus one launch for all the jagged AoS -> field-major jobs (one CTA per
+ * tile of 512 parents, which their scan and gather need): a device job
+ * table, a prefix over the jobs' tiles, per-job tile sizes from the
+ * autotuner cache.  With use_graph = 1 the launch sequence (scratch reset +
+ * the launches) is captured once into a CUDA graph and each mrn_batch_launch
+ * replays it.  The views' buffers must stay valid while the batch is used.
+ * Copies the job descriptions; `jobs` may be freed. */
 int mrn_batch_create(const mrn_job* jobs, size_t n_jobs, int use_graph, mrn_batch** out);
-/* Runs every job of the batch on `stream` (one persistent launch). */
+/* Runs every job of the batch on `stream`. */
 int mrn_batch_launch(mrn_batch* b, void* stream);
 /* Baseline: runs the same jobs with one mrn_convert launch per job. */
 int mrn_batch_launch_per_job(mrn_batch* b, void* stream);
