@@ -795,32 +795,6 @@ __device__ __forceinline__ uint32_t side_tile_bytes(const ConvPlan& p, const Sid
   return full / p.tg.T * R;  // SoA: T * (sum of column sizes), columns packed
 }
 
-// Warp-wide bulk loads of the first R records of source tile lt: lane 0
-// sets the transaction count, then lane c copies SoA column c (lane 0
-// copies an AoS / AoSoA tile, which is one range).  With `rec`, lane 0
-// also copies that stage table into `table` on the same barrier.
-__device__ __forceinline__ void tma_load_tile_warp(const ConvPlan& p, uint64_t lt, uint32_t R, char* stage,
-                                                   unsigned long long* bar, int lane, const StageRec* rec,
-                                                   StageDesc* table) {
-  const TileGeom& g = p.tg;
-  const uint64_t t0 = lt * g.T;
-  const SidePlan& sp = p.src;
-  const uint32_t bytes = side_tile_bytes(p, sp, g.src_bytes, R);
-  if (lane == 0) {
-    mbar_expect_tx(bar, bytes + (rec ? (uint32_t)sizeof(StageRec) : 0u));
-    if (rec) bulk_g2s(table, rec, (uint32_t)sizeof(StageRec), bar);
-  }
-  __syncwarp();
-  if (sp.kind == K_AOS) {
-    if (lane == 0) bulk_g2s(stage, sp.base + t0 * p.stride, bytes, bar);
-  } else if (sp.kind == K_AOSOA) {
-    if (lane == 0) bulk_g2s(stage, sp.base + (t0 / sp.block) * sp.block_bytes, bytes, bar);
-  } else {
-    for (uint32_t c = lane; c < p.ncols; c += 32)
-      bulk_g2s(stage + g.src_off[c], sp.col[c] + t0 * p.fm_size[c], R * p.fm_size[c], bar);
-  }
-}
-
 // Warp-wide bulk stores of the first R records of destination tile lt;
 // every lane commits its own bulk group.
 __device__ __forceinline__ void tma_store_tile_warp(const ConvPlan& p, uint64_t lt, uint32_t R, const char* tile,
@@ -872,6 +846,77 @@ __device__ __forceinline__ unsigned int advance_job(const unsigned long long* __
   return lo;
 }
 
+// What the loader warp reads of its current job for every tile, kept in
+// registers from one job switch to the next (a batch's job table is in
+// global memory, and the plan fields of one tile are a chain of loads on
+// the way to its bulk copies): the tile numbering and the source side, with
+// lane c holding columns c and c + 32.
+struct LoadCache {
+  unsigned int job;
+  bool staged_job;
+  uint32_t T, rs, kind, ncols, stride, src_bytes, block;
+  uint64_t tile_begin, nfull, block_bytes;
+  const char* base;
+  const char* col[2];
+  uint32_t size[2], off[2];
+};
+
+__device__ __forceinline__ void load_cache(const BatchJob& J, unsigned int job, int lane, LoadCache* c) {
+  const ConvPlan& P = J.jp.parent;
+  c->job = job;
+  c->tile_begin = J.tile_begin;
+  c->staged_job = J.kind == JOB_CONVERT && P.tg.tma;
+  c->T = P.tg.T;
+  const StagedTiles st = staged_tiles(P.n, 0, P.tg.T, P.tg.G);
+  c->nfull = st.nfull;
+  c->rs = (uint32_t)st.rs;
+  c->kind = P.src.kind;
+  c->ncols = P.ncols;
+  c->stride = P.stride;
+  c->src_bytes = P.tg.src_bytes;
+  c->block = (uint32_t)P.src.block;
+  c->block_bytes = P.src.block_bytes;
+  c->base = P.src.base;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const uint32_t col = (uint32_t)lane + 32u * k;
+    const bool have = col < P.ncols && P.src.kind == K_SOA;
+    c->col[k] = have ? P.src.col[col] : nullptr;
+    c->size[k] = have ? P.fm_size[col] : 0u;
+    c->off[k] = have ? P.tg.src_off[col] : 0u;
+  }
+}
+
+// Warp-wide bulk loads of the first R records of source tile lt, from the
+// cached fields: lane 0 sets the transaction count, then lane c copies SoA
+// columns c and c + 32 (lane 0 copies an AoS / AoSoA tile, which is one
+// range).  With `rec`, lane 0 also copies that stage table into `table` on
+// the same barrier.
+__device__ __forceinline__ void tma_load_tile_cached(const LoadCache& c, uint64_t lt, uint32_t R, char* stage,
+                                                     unsigned long long* bar, int lane, const StageRec* rec,
+                                                     StageDesc* table) {
+  const uint64_t t0 = lt * c.T;
+  uint32_t bytes;
+  if (R == c.T) bytes = c.src_bytes;
+  else if (c.kind == K_AOS) bytes = R * c.stride;
+  else if (c.kind == K_AOSOA) bytes = R / c.block * (uint32_t)c.block_bytes;
+  else bytes = c.src_bytes / c.T * R;
+  if (lane == 0) {
+    mbar_expect_tx(bar, bytes + (rec ? (uint32_t)sizeof(StageRec) : 0u));
+    if (rec) bulk_g2s(table, rec, (uint32_t)sizeof(StageRec), bar);
+  }
+  __syncwarp();
+  if (c.kind == K_AOS) {
+    if (lane == 0) bulk_g2s(stage, c.base + t0 * c.stride, bytes, bar);
+  } else if (c.kind == K_AOSOA) {
+    if (lane == 0) bulk_g2s(stage, c.base + (t0 / c.block) * c.block_bytes, bytes, bar);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      if (c.col[k]) bulk_g2s(stage + c.off[k], c.col[k] + t0 * c.size[k], R * c.size[k], bar);
+  }
+}
+
 // Loader warp: decides tiles in order (lane 0 decides, the warp follows)
 // and issues the loads of staged ones; returns after publishing the
 // end-of-work slot, or on abort once its loads in flight have landed.
@@ -889,6 +934,8 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
   uint32_t n_chunks = 0;  // static assignment: chunks taken so far
   uint64_t seen = 0;      // dynamic assignment: end of the last chunk taken
   uint64_t snap = 0;      // the counter, read while deciding a chunk's last tile
+  LoadCache lc;           // the fields of job lc.job the loader reads per tile
+  lc.job = 0xffffffffu;
   bool have = false;
   TileSlot cand;
   cand.t = 0;
@@ -934,14 +981,11 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
       cand.local = 0;
       if (cand.t < total_tiles) {
         if constexpr (!kStatic) cursor = advance_job(first_tile, njobs, cursor, cand.t, lane);
-        const BatchJob& J = jobs[cursor];
+        if (cursor != lc.job) load_cache(jobs[cursor], cursor, lane, &lc);
         cand.job = cursor;
-        cand.local = cand.t - J.tile_begin;
-        const ConvPlan& P = J.jp.parent;
-        if (J.kind == JOB_CONVERT && P.tg.tma) {
-          const StagedTiles st = staged_tiles(P.n, 0, P.tg.T, P.tg.G);
-          cand.staged = cand.local < st.nfull ? P.tg.T : (cand.local == st.nfull ? (uint32_t)st.rs : 0u);
-        }
+        cand.local = cand.t - lc.tile_begin;
+        if (lc.staged_job)
+          cand.staged = cand.local < lc.nfull ? lc.T : (cand.local == lc.nfull ? lc.rs : 0u);
       }
       have = true;
     }
@@ -976,7 +1020,7 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
           if (lane == 0) m.sjob()[s] = cand.job;
         }
         __syncwarp();
-        tma_load_tile_warp(P, cand.local, cand.staged, m.src(s), m.full(s), lane, rec, m.desc(s));
+        tma_load_tile_cached(lc, cand.local, cand.staged, m.src(s), m.full(s), lane, rec, m.desc(s));
         ++c_issue;
       }
       if (lane == 0) {
