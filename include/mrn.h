@@ -238,7 +238,7 @@ int mrn_sync_bits(void* stream, uint32_t* bits);
  * AoS source and a SoA destination; any other pair returns MRN_EINVAL.
  * The scan's scratch is a fixed 256 KiB array inside the library, present on
  * every device that loads the library until the process exits; it holds at
- * most 16,760,832 parents per call, larger n_records returns MRN_ESIZE before
+ * most 33,521,664 parents per call, larger n_records returns MRN_ESIZE before
  * anything is launched.  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make that
  * first call before any stream capture.  All calls share the array and each
@@ -307,7 +307,7 @@ typedef struct mrn_batch mrn_batch; /* opaque */
 /* Prepares many independent conversions (any schemas, any supported layout
  * pairs, jagged AoS<->SoA included) to run in one persistent kernel launch,
  * plus one launch for all the jagged AoS -> field-major jobs (one CTA per
- * tile of 512 parents, which their scan and gather need): a device job
+ * tile of 1,024 parents, which their scan and gather need): a device job
  * table, a prefix over the jobs' tiles, per-job tile sizes from the
  * autotuner cache.  With use_graph = 1 the launch sequence (scratch reset +
  * the launches) is captured once into a CUDA graph and each mrn_batch_launch

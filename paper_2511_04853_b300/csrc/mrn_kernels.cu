@@ -132,8 +132,8 @@ struct JagShared {
   unsigned long long beg[MRN_JAG_TILE];
 };
 struct JagWarp {
-  unsigned long long warp[8];
-  unsigned long long kmin[8], kmax[8];  // per warp: min / max of begin - exclusive offset
+  unsigned long long warp[MRN_JAG_WARPS];
+  unsigned long long kmin[MRN_JAG_WARPS], kmax[MRN_JAG_WARPS];  // per warp: min / max of begin - exclusive offset
   unsigned long long base;
 };
 
@@ -240,7 +240,7 @@ __device__ __forceinline__ void jagged_children(const JagPlan& jp, const JagShar
   const uint32_t nc = C.naos, stride = C.stride, vec = C.vec;
   const char* pool = C.src.base;
   constexpr unsigned long long kPass = 32 * S;
-  for (unsigned long long j0 = (unsigned long long)warp * kPass; j0 < agg; j0 += 8 * kPass) {
+  for (unsigned long long j0 = (unsigned long long)warp * kPass; j0 < agg; j0 += MRN_JAG_WARPS * kPass) {
     uint64_t si[S], di[S];
     uint32_t ld_ok = 0, st_ok = 0;
 #pragma unroll
@@ -314,7 +314,7 @@ __device__ __forceinline__ void jagged_run_small(const JagPlan& jp, unsigned lon
   const uint32_t nc = C.naos, stride = C.stride, vec = C.vec;
   const char* pool = C.src.base;
   constexpr unsigned long long kPass = 32 * S;
-  for (unsigned long long j0 = (unsigned long long)warp * kPass; j0 < agg; j0 += 8 * kPass) {
+  for (unsigned long long j0 = (unsigned long long)warp * kPass; j0 < agg; j0 += MRN_JAG_WARPS * kPass) {
     uint64_t rec[S];
     uint32_t ok = 0;
 #pragma unroll
@@ -428,8 +428,8 @@ __device__ __forceinline__ unsigned long long jagged_lookback(const JagPlan& jp,
   return prefix;
 }
 
-// One tile of MRN_JAG_TILE (512) parents of a jagged AoS -> SoA conversion
-// (256 threads, two parents each): converts the parents, scans their
+// One tile of MRN_JAG_TILE (1,024) parents of a jagged AoS -> SoA conversion
+// (512 threads, two parents each): converts the parents, scans their
 // lengths, obtains the tile's child base by a decoupled look-back over the
 // predecessors' published sums in `st`, writes the offsets and gathers the
 // tile's children, load-balanced over the tile's threads.  Each tile
@@ -446,7 +446,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
   const ConvPlan& P = jp.parent;
   const uint64_t t0 = tile * MRN_JAG_TILE;
 
-  // Parents q = tid and q = 256 + tid of the tile (consecutive records per
+  // Parents q = tid and q = MRN_JAG_THREADS + tid of the tile (consecutive records per
   // warp); then their lengths go to excl[] for the scan and their begins
   // (all ones for a parent whose children lie outside the pool) to beg[].
   uint32_t len[2];
@@ -486,17 +486,17 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
   if (lane == 31) sw.warp[warp] = x;
   __syncthreads();
   if (warp == 0) {
-    unsigned long long t = lane < 8 ? sw.warp[lane] : 0ull;
+    unsigned long long t = lane < MRN_JAG_WARPS ? sw.warp[lane] : 0ull;
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
+    for (int o = 1; o < MRN_JAG_WARPS; o <<= 1) {
       const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
       if (lane >= o) t += y;
     }
-    if (lane < 8) sw.warp[lane] = t;
+    if (lane < MRN_JAG_WARPS) sw.warp[lane] = t;
   }
   __syncthreads();
   const unsigned long long e0 = x - (l0 + l1) + (warp > 0 ? sw.warp[warp - 1] : 0ull), e1 = e0 + l0;
-  const unsigned long long agg = sw.warp[7];
+  const unsigned long long agg = sw.warp[MRN_JAG_WARPS - 1];
   sh.excl[2 * tid] = e0;
   sh.excl[2 * tid + 1] = e1;
   if (tid == MRN_JAG_THREADS - 1) sh.excl[MRN_JAG_TILE] = agg;
@@ -540,7 +540,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
   kmin = ~0ull;
   kmax = 0ull;
 #pragma unroll
-  for (int w = 0; w < 8; ++w) {
+  for (int w = 0; w < MRN_JAG_WARPS; ++w) {
     kmin = min(kmin, sw.kmin[w]);
     kmax = max(kmax, sw.kmax[w]);
   }
@@ -585,9 +585,13 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
 }
 
 template <int VP, int VC>
-__global__ void __launch_bounds__(MRN_JAG_THREADS, 6) k_jagged_a2s(const __grid_constant__ JagPlan jp) {
-  __shared__ uint32_t tw_all[8 * MRN_TW_WORDS_PER_WARP];
-  __shared__ JagShared sh;
+__global__ void __launch_bounds__(MRN_JAG_THREADS, 3) k_jagged_a2s(const __grid_constant__ JagPlan jp) {
+  // The tile windows serve the parent conversion only; the per-parent
+  // arrays are written after every warp has finished it.
+  constexpr size_t kTw = MRN_JAG_WARPS * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t);
+  __shared__ __align__(16) unsigned char jag_raw[kTw > sizeof(JagShared) ? kTw : sizeof(JagShared)];
+  uint32_t* tw_all = reinterpret_cast<uint32_t*>(jag_raw);
+  JagShared& sh = *reinterpret_cast<JagShared*>(jag_raw);
   __shared__ JagWarp sw;
   __shared__ unsigned int s_tile;
   if (threadIdx.x == 0) s_tile = atomicAdd(jp.tile_counter, 1u);
@@ -596,21 +600,23 @@ __global__ void __launch_bounds__(MRN_JAG_THREADS, 6) k_jagged_a2s(const __grid_
 }
 
 // The jagged AoS -> field-major jobs of a batch: one CTA per tile as in
-// k_jagged_a2s, 7 CTAs per SM (the scan and the gather are latency-bound
-// and want many warps; measured 7% faster than 6 here, while the
-// single-conversion kernel, whose plan sits in the constant bank, is
-// faster at 6), tiles taken in increasing order over all the jobs,
+// k_jagged_a2s, 3 CTAs (48 warps) per SM, tiles taken in increasing order
+// over all the jobs,
 // each tile's job read from a host-built map.  A tile's look-back only
 // visits its own job's earlier tiles, which hold earlier tickets.  The
 // job's plan is copied into shared memory first: the tile reads its fields
 // all along, and from global memory (not the constant bank, where a single
 // conversion's plan sits) those reads cost the batch a quarter of its speed.
-__global__ void __launch_bounds__(MRN_JAG_THREADS, 7) k_batch_jag(const BatchJob* __restrict__ jobs,
+__global__ void __launch_bounds__(MRN_JAG_THREADS, 3) k_batch_jag(const BatchJob* __restrict__ jobs,
                                                                  const unsigned int* __restrict__ tile_job,
                                                                  unsigned long long total, unsigned int* counter,
                                                                  unsigned long long* states) {
-  __shared__ uint32_t tw_all[8 * MRN_TW_WORDS_PER_WARP];
-  __shared__ JagShared sh;
+  // The tile windows serve the parent conversion only; the per-parent
+  // arrays are written after every warp has finished it.
+  constexpr size_t kTw = MRN_JAG_WARPS * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t);
+  __shared__ __align__(16) unsigned char jag_raw[kTw > sizeof(JagShared) ? kTw : sizeof(JagShared)];
+  uint32_t* tw_all = reinterpret_cast<uint32_t*>(jag_raw);
+  JagShared& sh = *reinterpret_cast<JagShared*>(jag_raw);
   __shared__ JagWarp sw;
   __shared__ unsigned int s_tile;
   __shared__ __align__(16) unsigned long long jps[(sizeof(JagPlan) + 7) / 8];

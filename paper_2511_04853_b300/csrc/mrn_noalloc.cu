@@ -1,7 +1,7 @@
 // Allocation-free variant of the jagged AoS -> SoA conversion.
 //
 // mrn_convert() takes the look-back scratch of the jagged scan (a tile
-// counter and one word per tile of 512 parents) from the stream-ordered
+// counter and one word per tile of 1,024 parents) from the stream-ordered
 // allocator.  Some callers cannot let a library allocate device memory: a
 // host application that owns every byte of the GPU through its own pool and
 // rejects outside allocations, a process that already holds nearly all of
@@ -15,8 +15,8 @@
 
 #include "mrn_internal.h"
 
-// 256 KiB: a 256-byte counter block plus one 8-byte word per tile of 512
-// parents, i.e. at most 32,736 tiles = 16,760,832 parents per call.
+// 256 KiB: a 256-byte counter block plus one 8-byte word per tile of 1,024
+// parents, i.e. at most 32,736 tiles = 33,521,664 parents per call.
 #define MRN_NOALLOC_SCRATCH_BYTES (256u * 1024u)
 #define MRN_NOALLOC_MAX_DEVICES 64
 

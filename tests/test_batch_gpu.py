@@ -156,7 +156,7 @@ def test_batch_lookback_wait_is_bounded():
     """Host-side fault injection: jagged tile 1 of a batched job never
     publishes its sum, so tile 2's look-back must expire (1 ms bound) and
     report MRN_ETIMEOUT; batches built afterwards run normally."""
-    n = 4 * 512  # four jagged tiles
+    n = 8 * 1024  # at least four jagged tiles for tiles of up to 2,048 parents
     s, o = mrn.Schema(datagen.TRACKS), oracle.Schema(datagen.TRACKS)
     d = datagen.workload("tracks", n, 3)
     o_aos = oracle.pack(o, d, "aos")

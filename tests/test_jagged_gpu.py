@@ -63,13 +63,13 @@ def test_stray_empty_begins_and_one_tile_out_of_order():
     parent lookup; empty parents may carry any begin within the pool without
     breaking the run, and a tile whose runs are out of order (tile 1 here)
     takes the general path.  Both must equal the oracle."""
-    n = 4 * 256 + 17
+    n = 4 * 1024 + 17  # four jagged tiles of 1,024 parents and a ragged one
     s, o, d = tracks(n, seed=11, mean_len=2.0)
     o_aos = oracle.pack(o, d, "aos")
     lens = d["lengths"]
     assert (lens == 0).sum() > 50
     order = np.arange(n)
-    cand = [i for i in range(256, 512) if lens[i] > 0]
+    cand = [i for i in range(1024, 2048) if lens[i] > 0]
     i, j = cand[3], cand[10]
     order[i], order[j] = j, i
     sh = oracle.shuffle_pool(o, o_aos, order, gap=0)
@@ -80,7 +80,7 @@ def test_stray_empty_begins_and_one_tile_out_of_order():
     a2s_check(s, o, sh, m_cap=d["m"])
 
 
-@pytest.mark.parametrize("n", [0, 1, 255, 256, 257, 1000, 5003])
+@pytest.mark.parametrize("n", [0, 1, 255, 256, 257, 1000, 1023, 1024, 1025, 3073, 5003])
 @pytest.mark.parametrize("osz", ["u32", "u64"])
 def test_sizes_and_offset_types(n, osz):
     desc = [("a", "u8", 1), ("b", "f64", 1),
@@ -228,7 +228,7 @@ def test_lookback_wait_is_bounded():
     """Fault injection on the host side: tile 1 never publishes its sum, so
     tile 2's look-back wait must expire (1 ms bound) and report
     MRN_ETIMEOUT; the context stays usable afterwards."""
-    n = 4 * 512  # four jagged tiles
+    n = 8 * 1024  # at least four jagged tiles for tiles of up to 2,048 parents
     s, o, d = tracks(n, seed=3)
     o_aos = oracle.pack(o, d, "aos")
     try:
@@ -258,7 +258,7 @@ def _bytes(view_tensor, n):
 
 
 @pytest.mark.parametrize("B", [32, 128, 5])
-@pytest.mark.parametrize("n", [0, 1, 511, 512, 513, 5003])
+@pytest.mark.parametrize("n", [0, 1, 511, 512, 513, 1023, 1024, 1025, 2049, 5003])
 def test_aos_to_aosoa_and_back(n, B):
     """Jagged AoS -> AoSoA(B): the parent blocks (tail slots zero), the
     offsets and the child columns equal the oracle's, byte for byte, for a

@@ -14,7 +14,7 @@ import pytest
 import datagen
 import oracle
 import paper_2511_04853_b300 as mrn
-from gpu_util import dev, garbage, host
+from gpu_util import dev, garbage, host, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -40,11 +40,21 @@ def test_matches_mrn_convert_twice(n, seed):
 
 
 def test_rejects_sizes_beyond_the_array_and_other_layouts():
+    """One parent more than the scratch array holds is refused before
+    anything runs.  The views are backed by buffers of the size they
+    describe (all lengths 0), so a check that let the call through would
+    fail this test, never access memory outside its buffers."""
+    t = torch()
     s = mrn.Schema(datagen.TRACKS)
-    big = 16_760_832 + 1
+    big = 33_521_664 + 1
     buf = garbage(1 << 12)
-    src = mrn.View(s, "aos", big, base=buf, child_pool=buf, m=1)
-    dst = mrn.View(s, "soa", big, base=buf, m=1)
+    aos = t.zeros(s.required_bytes("aos", big, 1), dtype=t.uint8, device="cuda")
+    pool = t.zeros(s.child_pool_bytes(1), dtype=t.uint8, device="cuda")
+    soa = t.zeros(s.required_bytes("soa", big, 1), dtype=t.uint8, device="cuda")
+    src = mrn.View(s, "aos", big, base=aos, child_pool=pool, m=1)
+    dst = mrn.View(s, "soa", big, base=soa, m=1)
     assert _call(src, dst) == mrn.ESIZE  # checked before anything runs
+    assert mrn.sync() == mrn.OK
+    del aos, pool, soa
     c = mrn.Schema(datagen.CELLS)
     assert _call(mrn.View(c, "aos", 10, base=buf), mrn.View(c, "soa", 10, base=buf)) == mrn.EINVAL
