@@ -309,6 +309,55 @@ bool side_stageable(const mrn_schema* s, const SidePlan& sp, bool is_dst) {
   return true;
 }
 
+// An AoS destination record with padding is zeroed before its fields are
+// written.  Where every padding byte lies within the widest store a field
+// preceding it can make (aligned within the record, at most 8 bytes and
+// the record's own alignment in a tile row), the field is stored that wide
+// instead, its value zero-extended, and the zeroing pass is dropped.  The
+// widened fields go to the end of a second descriptor order, outside the
+// size classes.  Leaves nwide = 0 when some padding byte is not covered.
+void widen_into_padding(const mrn_schema* s, TileGeom* g) {
+  const uint32_t S = s->stride, nc = (uint32_t)s->cols.size();
+  if (S > 256) return;
+  bool field[256] = {}, covered[256] = {};
+  for (uint32_t c = 0; c < nc; ++c)
+    for (uint32_t b = 0; b < s->cols[c].size; ++b) field[s->cols[c].aos_off + b] = covered[s->cols[c].aos_off + b] = true;
+  const uint32_t amax = std::min<uint32_t>(8, lowbit(S));
+  uint32_t wide[MRN_MAX_COLS] = {};
+  for (uint32_t c = 0; c < nc; ++c) {
+    const uint32_t off = s->cols[c].aos_off, sz = s->cols[c].size;
+    for (uint32_t w = amax; w > sz; w >>= 1) {
+      if (off % w || off + w > S) continue;
+      bool pad_only = true;
+      for (uint32_t b = off + sz; b < off + w; ++b) pad_only = pad_only && !field[b];
+      if (!pad_only) continue;
+      wide[c] = w == 8 ? 3 : w == 4 ? 2 : 1;
+      for (uint32_t b = off + sz; b < off + w; ++b) covered[b] = true;
+      break;
+    }
+  }
+  for (uint32_t b = 0; b < S; ++b)
+    if (!covered[b]) return;
+  uint8_t order[MRN_MAX_COLS];
+  uint32_t k = 0, nwide = 0, nsize = 0;
+  for (uint32_t i = 0; i < nc; ++i) {
+    const uint32_t c = g->order[i];
+    if (wide[c]) continue;
+    order[k++] = (uint8_t)c;
+    nsize += 1u << (8 * (3 - ((g->col[c] >> 24) & 3u)));
+  }
+  for (uint32_t i = 0; i < nc; ++i) {
+    const uint32_t c = g->order[i];
+    if (!wide[c]) continue;
+    order[k++] = (uint8_t)c;
+    g->col[c] |= wide[c] << 28;
+    ++nwide;
+  }
+  std::memcpy(g->worder, order, nc);
+  g->wnsize = nsize;
+  g->nwide = nwide;
+}
+
 // Chooses the shared-memory tile of a plan: the largest T, a multiple of 32
 // and of every AoSoA block size, whose source and destination tiles each fit
 // one stage buffer.  Leaves tg.tma = 0 when the plan cannot be staged (an
@@ -351,6 +400,7 @@ void tile_geometry(const mrn_schema* s, ConvPlan* p, uint32_t stage_bytes) {
     g.nsize |= cnt << (8 * (3 - lsz));
   }
   g.pad = used != s->stride;
+  if (g.pad && p->dst.kind == K_AOS && !s->has_jagged) widen_into_padding(s, &g);
   g.tma = 1;
 }
 

@@ -521,6 +521,34 @@ __device__ __forceinline__ void tile_class(uint32_t desc, uint32_t c0, uint32_t 
   }
 }
 
+// The widened columns [c0, c1) of an AoS destination (see tile_convert):
+// a field of 2^x bytes (x < 3, descriptor word x) is loaded as usual and
+// stored, zero-extended, with 2^w bytes (word w), which also writes the
+// padding that follows it in the record.
+__device__ __forceinline__ uint2 lds_any(uint32_t a, uint32_t L) {
+  if (L == 2) return make_uint2(lds32(a), 0u);
+  if (L == 1) return make_uint2(lds16(a), 0u);
+  return make_uint2(lds8(a), 0u);
+}
+
+__device__ __forceinline__ void sts_wide(uint32_t a, uint2 v, uint32_t w) {
+  if (w == 3) sts64(a, v);
+  else if (w == 2) sts32(a, v.x);
+  else sts16(a, v.x);
+}
+
+__device__ __forceinline__ void tile_wide(uint32_t desc, uint32_t c0, uint32_t c1, uint32_t sb0, uint32_t si0,
+                                          uint32_t sb1, uint32_t si1, uint32_t db0, uint32_t db1, bool two) {
+  for (uint32_t c = c0; c < c1; ++c) {
+    const uint4 d = lds128(desc + c * 16);
+    const uint2 v0 = lds_any(sb0 + d.y + (si0 << d.x), d.x);
+    uint2 v1 = v0;
+    if (two) v1 = lds_any(sb1 + d.y + (si1 << d.x), d.x);
+    sts_wide(db0 + d.z, v0, d.w);
+    if (two) sts_wide(db1 + d.z, v1, d.w);
+  }
+}
+
 // Staged tile transform: each lane converts records r0 and r1 (= r0 + 256,
 // when `two`) of the tile.  Per column one shared load and one shared store
 // per record, addressed from the column descriptor table `desc` (uint4
@@ -530,7 +558,9 @@ __device__ __forceinline__ void tile_class(uint32_t desc, uint32_t c0, uint32_t 
 // the record) as row + column offset + (slot << log2(size)).  One body
 // serves every pair of layouts, so tiles of different layout pairs running
 // side by side share their instructions; each size class is a loop of its
-// own, so no element access branches on its size.
+// own, so no element access branches on its size.  With Wide, the last
+// h.nwide descriptors are fields of an AoS destination stored wider than
+// they are, over the padding after them; such records are not zeroed first.
 // An AoS <-> SoA tile whose AoS record is W (2 or 4) 4-byte words, the
 // columns in order (h.packed): the record moves as one 8- or 16-byte vector
 // on the AoS side, and word k to or from its SoA column.  Narrow records
@@ -572,6 +602,7 @@ __device__ __forceinline__ void tile_convert_packed(const TileHdr& h, uint32_t d
   }
 }
 
+template <bool Wide>
 __device__ __forceinline__ void tile_convert(const TileHdr& h, uint32_t desc, uint32_t st, uint32_t dt,
                                              uint32_t r0, bool two) {
   if (h.packed == 2) return tile_convert_packed<2>(h, desc, st, dt, r0, two);
@@ -585,8 +616,10 @@ __device__ __forceinline__ void tile_convert(const TileHdr& h, uint32_t desc, ui
   zero_record(h, db0);
   if (two) zero_record(h, db1);
   const uint32_t e8 = h.nsize & 0xff, e4 = e8 + ((h.nsize >> 8) & 0xff), e2 = e4 + ((h.nsize >> 16) & 0xff);
+  const uint32_t ew = Wide ? h.ncols - h.nwide : h.ncols;
   tile_class<3>(desc, 0, e8, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
   tile_class<2>(desc, e8, e4, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
   tile_class<1>(desc, e4, e2, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
-  tile_class<0>(desc, e2, h.ncols, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
+  tile_class<0>(desc, e2, ew, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
+  if (Wide && ew < h.ncols) tile_wide(desc, ew, h.ncols, sb0, si0, sb1, si1, db0, db1, two);
 }

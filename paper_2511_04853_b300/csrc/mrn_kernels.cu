@@ -55,32 +55,39 @@ __global__ void __launch_bounds__(256) k_convert(const __grid_constant__ ConvPla
 
 // ------------------------------------------------- staged tile transform
 
-// All threads: source tile -> destination tile in shared memory.
+// All threads: source tile -> destination tile in shared memory.  Wide:
+// the tables may hold widened fields (single conversions; a batch's tables
+// never do, and its transform has no branch for them).
+template <bool Wide>
 __device__ __forceinline__ void tma_transform(const TileHdr& h, uint32_t desc, const char* st, char* dt, uint32_t R,
                                               int lane, int warp) {
   const uint32_t s = smem_u32(st), d = smem_u32(dt);
   const TileHdr hh = h;
   for (uint32_t g = (uint32_t)warp * 32; g < R; g += 2 * 8 * 32)
-    tile_convert(hh, desc, s, d, g + lane, g + 8 * 32 < R);
+    tile_convert<Wide>(hh, desc, s, d, g + lane, g + 8 * 32 < R);
 }
 
 // Entry k of the staged-transform descriptor table: the k-th column in
-// size-class order (see tile_convert).
-__host__ __device__ __forceinline__ uint4 tile_desc(const ConvPlan& p, uint32_t k) {
-  const uint32_t c = p.tg.order[k];
+// size-class order (see tile_convert); with `wide`, the order with the
+// fields widened over an AoS destination's padding last.
+__host__ __device__ __forceinline__ uint4 tile_desc(const ConvPlan& p, uint32_t k, bool wide = false) {
+  const bool w = wide && p.dst.kind == K_AOS && p.tg.nwide;
+  const uint32_t c = w ? p.tg.worder[k] : p.tg.order[k];
   const uint32_t col = p.tg.col[c], aos_off = col & 0xffffffu;
-  return make_uint4(col >> 24, p.src.kind == K_AOS ? aos_off : p.tg.src_off[c],
-                    p.dst.kind == K_AOS ? aos_off : p.tg.dst_off[c], 0u);
+  return make_uint4((col >> 24) & 3u, p.src.kind == K_AOS ? aos_off : p.tg.src_off[c],
+                    p.dst.kind == K_AOS ? aos_off : p.tg.dst_off[c], (col >> 28) & 3u);
 }
 
-__host__ __device__ __forceinline__ TileHdr tile_hdr(const ConvPlan& p) {
+__host__ __device__ __forceinline__ TileHdr tile_hdr(const ConvPlan& p, bool wide = false) {
+  const bool w = wide && p.dst.kind == K_AOS && p.tg.nwide;
   TileHdr h;
   h.ncols = p.ncols;
   h.stride = p.stride;
   h.vec = p.vec;
-  h.pad = p.dst.kind == K_AOS ? p.tg.pad : 0u;
+  h.pad = p.dst.kind == K_AOS && !w ? p.tg.pad : 0u;
   h.T = p.tg.T;
-  h.nsize = p.tg.nsize;
+  h.nsize = w ? p.tg.wnsize : p.tg.nsize;
+  h.nwide = w ? p.tg.nwide : 0u;
   h.packed = 0;
   const uint32_t n4 = (p.tg.nsize >> 8) & 0xff;
   if (((p.src.kind == K_AOS && p.dst.kind == K_SOA) || (p.src.kind == K_SOA && p.dst.kind == K_AOS)) &&
@@ -729,7 +736,7 @@ struct TileSlot {
 // A stage's table in shared memory: the layout of StageRec, read as uint4.
 struct StageDesc {
   TileHdr h;
-  unsigned int pad[3];
+  unsigned int pad[2];
   uint4 d[MRN_MAX_COLS];
 };
 static_assert(sizeof(StageDesc) == sizeof(StageRec), "a stage table is a StageRec");
@@ -821,11 +828,12 @@ __device__ __forceinline__ void tma_store_tile_warp(const ConvPlan& p, uint64_t 
 }
 
 // Loader warp, one conversion per launch: the plan's column descriptors and
-// header into stage s's table (lane c writes column c).
+// header into stage s's table (lane c writes column c), padding absorbed in
+// widened field stores where the plan has them.
 __device__ __forceinline__ void fill_stage_desc(const ConvPlan& p, const BatchSmem& m, uint32_t s, int lane) {
   StageDesc* sd = m.desc(s);
-  for (uint32_t c = lane; c < p.ncols; c += 32) sd->d[c] = tile_desc(p, c);
-  if (lane == 0) sd->h = tile_hdr(p);
+  for (uint32_t c = lane; c < p.ncols; c += 32) sd->d[c] = tile_desc(p, c, true);
+  if (lane == 0) sd->h = tile_hdr(p, true);
 }
 
 static_assert(sizeof(BatchJob) % 16 == 0, "a job descriptor is one whole L2 prefetch");
@@ -1185,7 +1193,7 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
         break;
       }
       const StageDesc* sd = m.desc(s);
-      tma_transform(sd->h, smem_u32(sd->d), m.src(s), m.dst(d), ts.staged, lane, warp);
+      tma_transform<kStatic>(sd->h, smem_u32(sd->d), m.src(s), m.dst(d), ts.staged, lane, warp);
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {

@@ -46,10 +46,18 @@ struct TileGeom {
   uint32_t dst_bytes;  // bytes of a destination tile
   uint32_t pad;        // 1: the AoS record has padding bytes (zeroed first)
   uint32_t nsize;      // columns of 8, 4, 2 and 1 bytes: n8 | n4 << 8 | n2 << 16 | n1 << 24
+  // AoS destination each of whose padding bytes some field can be stored
+  // wide enough to cover: nwide > 0 such fields, stored 2^w bytes wide (w
+  // in col bits 28-29), zero-extended, come last in `worder`, after the
+  // others in size-class order (counts in wnsize); with that table the
+  // record needs no zeroing pass.  Single conversions use it; a batch's
+  // stage tables keep `order`.
+  uint32_t nwide, wnsize;
   uint32_t src_off[MRN_MAX_COLS];  // SoA: column offset in the tile; AoSoA: column start in a block
   uint32_t dst_off[MRN_MAX_COLS];
-  uint32_t col[MRN_MAX_COLS];      // per data column: AoS offset | log2(size) << 24
+  uint32_t col[MRN_MAX_COLS];      // per data column: AoS offset | log2(size) << 24 | w << 28
   uint8_t order[MRN_MAX_COLS];     // data columns by decreasing size (stable)
+  uint8_t worder[MRN_MAX_COLS];
 };
 
 // The fields of a plan the staged transform reads, copied into shared memory
@@ -67,15 +75,19 @@ struct TileHdr {
   // record being exactly those words in column order (records move as one
   // vector); 0 otherwise
   uint32_t packed;
+  // AoS destination: the last nwide descriptors are fields stored wider
+  // than they are, over the padding that follows them (see TileGeom)
+  uint32_t nwide;
 };
 
 // What the consumers of a staged tile read: the header and one descriptor
-// per column in size-class order {size, source offset, destination offset,
-// 0}.  A batch job carries its own, built on the host, and the loader brings
+// per column in size-class order {log2 size, source offset, destination
+// offset, log2 store size of a widened field (else unused)}.  A batch job
+// carries its own, built on the host, and the loader brings
 // it into a stage's table with one bulk copy beside the tile's data.
 struct alignas(16) StageRec {
   TileHdr h;
-  uint32_t pad[3];
+  uint32_t pad[2];
   uint32_t d[MRN_MAX_COLS][4];
 };
 
