@@ -259,6 +259,66 @@ __device__ __forceinline__ void fm_to_aos_lane(const ConvPlan& p, uint64_t r, bo
   }
 }
 
+// fm_to_aos_lane with the loads of up to 8 consecutive columns of a window
+// issued before any of them is used, so that a record costs one memory
+// round trip per 8 columns instead of one per column (for kernels with
+// registers to spare; the columns are in AoS order).
+template <int V, int W = MRN_WIN_WORDS>
+__device__ __forceinline__ void fm_to_aos_lane_ilp(const ConvPlan& p, uint64_t r, bool ok, char* rec,
+                                                   uint32_t* tw, int lane, uint32_t jlen, uint64_t jbeg) {
+  constexpr int NB = 8;
+  uint32_t ci = 0;
+  const uint32_t naos = p.naos, stride = p.stride, aw = p.aos_words;
+  for (uint32_t win = 0; win < aw; win += W) {
+    const uint32_t nw = min((uint32_t)W, aw - win);
+#pragma unroll
+    for (int k = 0; k < W; ++k)
+      if (k < (int)nw) tw[k * MRN_TW_PITCH + lane] = 0;
+    const uint32_t wend = (win + W) * 4;
+    while (ci < naos && p.aos_cols[ci].aos_off < wend) {
+      uint64_t v[NB];
+      uint32_t cnt = 0;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        v[k] = 0;
+        const uint32_t c = ci + k;
+        if (c < naos && c == ci + cnt) {
+          const ColPlan cp = p.aos_cols[c];
+          if (cp.aos_off < wend) {
+            if (cp.fm >= 0) {
+              if (ok) v[k] = ld_elem(fm_addr(p.src, cp.fm, cp.size, r), cp.size);
+            } else {
+              v[k] = cp.fm == FM_JLEN ? (uint64_t)jlen : jbeg;
+            }
+            ++cnt;
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        if (k >= (int)cnt) break;
+        const ColPlan cp = p.aos_cols[ci + k];
+        uint32_t* t = tw + (cp.aos_off / 4 - win) * MRN_TW_PITCH + lane;
+        if (cp.size == 8) {
+          t[0] = (uint32_t)v[k];
+          t[MRN_TW_PITCH] = (uint32_t)(v[k] >> 32);
+        } else if (cp.size == 4) {
+          t[0] = (uint32_t)v[k];
+        } else {
+          t[0] |= ((uint32_t)v[k] & lowbits_mask(cp.size)) << ((cp.aos_off & 3) * 8);
+        }
+      }
+      ci += cnt;
+    }
+    if (ok) {
+      uint32_t w[W];
+#pragma unroll
+      for (int k = 0; k < W; ++k) w[k] = k < (int)nw ? tw[k * MRN_TW_PITCH + lane] : 0u;
+      store_any<V, W>(rec + win * 4, min(4u * W, stride - win * 4), w, p.vec);
+    }
+  }
+}
+
 // Field-major -> field-major (SoA <-> AoSoA(B), AoSoA(B) -> AoSoA(B')),
 // one record per lane, column by column.
 __device__ __forceinline__ void fm_to_fm_lane(const ConvPlan& p, uint64_t r, bool ld_ok, bool st_ok) {

@@ -643,7 +643,7 @@ __global__ void __launch_bounds__(MRN_JAG_THREADS, 3) k_batch_jag(const BatchJob
 // parent_groups) build 32 parent records each (length and begin from the
 // offsets), the following groups convert MRN_JAG_CHILD_GROUP of the m_src
 // children each into the pool.
-template <int VP, int VC, int W = MRN_WIN_WORDS>
+template <int VP, int VC, int W = MRN_WIN_WORDS, bool Ilp = false>
 __device__ __forceinline__ void jagged_s2a_group(const JagPlan& jp, uint64_t w, uint64_t parent_groups,
                                                  uint32_t* tw, int lane) {
   if (w < parent_groups) {
@@ -654,9 +654,14 @@ __device__ __forceinline__ void jagged_s2a_group(const JagPlan& jp, uint64_t w, 
     if (ok) {
       a = read_offset(jp.offsets, jp.off_size, r);
       b = read_offset(jp.offsets, jp.off_size, r + 1);
-      if (b < a || b - a > 0xffffffffull) flag_error(MRN_EINVAL);
     }
-    fm_to_aos_lane<VP, W>(P, r, ok, P.dst.base + r * P.stride, tw, lane, (uint32_t)(b - a), a);
+    // Ilp: the offsets and the parent columns are all loaded before any is
+    // used (the offsets are checked after the record is written).
+    if constexpr (Ilp)
+      fm_to_aos_lane_ilp<VP, W>(P, r, ok, P.dst.base + r * P.stride, tw, lane, (uint32_t)(b - a), a);
+    else
+      fm_to_aos_lane<VP, W>(P, r, ok, P.dst.base + r * P.stride, tw, lane, (uint32_t)(b - a), a);
+    if (ok && (b < a || b - a > 0xffffffffull)) flag_error(MRN_EINVAL);
   } else {
     jagged_s2a_children<VC, W>(jp, (w - parent_groups) * MRN_JAG_CHILD_GROUP, tw, lane);
   }
@@ -672,7 +677,7 @@ __global__ void __launch_bounds__(256) k_jagged_s2a(const __grid_constant__ JagP
   const uint64_t all = parent_groups + (jp.m_src + MRN_JAG_CHILD_GROUP - 1) / MRN_JAG_CHILD_GROUP;
   const uint64_t total_warps = (uint64_t)gridDim.x * wpb;
   for (uint64_t w = (uint64_t)blockIdx.x * wpb + warp; w < all; w += total_warps)
-    jagged_s2a_group<VP, VC>(jp, w, parent_groups, tw, lane);
+    jagged_s2a_group<VP, VC, MRN_WIN_WORDS, true>(jp, w, parent_groups, tw, lane);
 }
 
 // Sum of the jagged lengths of AoS parents.
