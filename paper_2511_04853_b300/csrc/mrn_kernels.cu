@@ -56,8 +56,8 @@ __global__ void __launch_bounds__(256) k_convert(const __grid_constant__ ConvPla
 // ------------------------------------------------- staged tile transform
 
 // All threads: source tile -> destination tile in shared memory.  Wide:
-// the tables may hold widened fields (single conversions; a batch's tables
-// never do, and its transform has no branch for them).
+// the tables may hold widened fields (k_convert_ws<true>, for single
+// conversions that have them; no other instance carries the branch).
 template <bool Wide>
 __device__ __forceinline__ void tma_transform(const TileHdr& h, uint32_t desc, const char* st, char* dt, uint32_t R,
                                               int lane, int warp) {
@@ -835,10 +835,11 @@ __device__ __forceinline__ void tma_store_tile_warp(const ConvPlan& p, uint64_t 
 // Loader warp, one conversion per launch: the plan's column descriptors and
 // header into stage s's table (lane c writes column c), padding absorbed in
 // widened field stores where the plan has them.
-__device__ __forceinline__ void fill_stage_desc(const ConvPlan& p, const BatchSmem& m, uint32_t s, int lane) {
+__device__ __forceinline__ void fill_stage_desc(const ConvPlan& p, const BatchSmem& m, uint32_t s, int lane,
+                                                bool wide) {
   StageDesc* sd = m.desc(s);
-  for (uint32_t c = lane; c < p.ncols; c += 32) sd->d[c] = tile_desc(p, c, true);
-  if (lane == 0) sd->h = tile_hdr(p, true);
+  for (uint32_t c = lane; c < p.ncols; c += 32) sd->d[c] = tile_desc(p, c, wide);
+  if (lane == 0) sd->h = tile_hdr(p, wide);
 }
 
 static_assert(sizeof(BatchJob) % 16 == 0, "a job descriptor is one whole L2 prefetch");
@@ -939,7 +940,7 @@ __device__ __forceinline__ void tma_load_tile_cached(const LoadCache& c, uint64_
 // Loader warp: decides tiles in order (lane 0 decides, the warp follows)
 // and issues the loads of staged ones; returns after publishing the
 // end-of-work slot, or on abort once its loads in flight have landed.
-template <bool kStatic>
+template <bool kStatic, bool kWide>
 __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
                                              const unsigned long long* __restrict__ first_tile,
                                              unsigned int njobs, unsigned long long total_tiles,
@@ -1032,7 +1033,7 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
         const StageRec* rec = nullptr;
         if (m.sjob()[s] != cand.job) {
           if constexpr (kStatic)
-            fill_stage_desc(P, m, s, lane);
+            fill_stage_desc(P, m, s, lane, kWide);
           else
             rec = &jobs[cand.job].stage;
           __syncwarp();
@@ -1123,7 +1124,7 @@ __device__ __forceinline__ void batch_storer(const BatchJob* __restrict__ jobs, 
   bulk_wait_all();
 }
 
-template <bool kStatic>
+template <bool kStatic, bool kWide>
 __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
                                            const unsigned long long* __restrict__ first_tile, unsigned int njobs,
                                            unsigned long long total_tiles, unsigned int* counter,
@@ -1170,7 +1171,7 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
   }
   __syncthreads();
   if (warp == 8) {
-    batch_loader<kStatic>(jobs, first_tile, njobs, total_tiles, counter, chunk, first_start, first_size, m,
+    batch_loader<kStatic, kWide>(jobs, first_tile, njobs, total_tiles, counter, chunk, first_start, first_size, m,
                           lane);
     return;
   }
@@ -1198,7 +1199,7 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
         break;
       }
       const StageDesc* sd = m.desc(s);
-      tma_transform<kStatic>(sd->h, smem_u32(sd->d), m.src(s), m.dst(d), ts.staged, lane, warp);
+      tma_transform<kWide>(sd->h, smem_u32(sd->d), m.src(s), m.dst(d), ts.staged, lane, warp);
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
@@ -1241,18 +1242,20 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
                                                         unsigned int njobs, unsigned long long total_tiles,
                                                         unsigned int* counter, uint32_t chunk) {
   extern __shared__ __align__(128) char batch_smem[];
-  batch_main<false>(jobs, first_tile, njobs, total_tiles, counter, chunk, batch_smem);
+  batch_main<false, false>(jobs, first_tile, njobs, total_tiles, counter, chunk, batch_smem);
 }
 
 // One staged conversion through the same warp-specialized pipeline: the
 // job travels as a kernel parameter (it has no jagged tiles).  Without a
 // counter, chunk c of tiles belongs to CTA c % gridDim.x; with one (a
 // zeroed word), chunks are guided as in a batch, so that CTAs that run
-// faster take more of them.
+// faster take more of them.  kWide: the instance for conversions whose
+// plan stores fields wider over an AoS destination's padding.
+template <bool kWide>
 __global__ void __launch_bounds__(kBThreads, 3) k_convert_ws(const __grid_constant__ BatchJob job,
                                                              uint32_t chunk, unsigned int* counter) {
   extern __shared__ __align__(128) char batch_smem[];
-  batch_main<true>(&job, nullptr, 1u, job.ntiles, counter, chunk, batch_smem);
+  batch_main<true, kWide>(&job, nullptr, 1u, job.ntiles, counter, chunk, batch_smem);
 }
 
 // ================================================================== host
@@ -1364,7 +1367,10 @@ int launch_convert(const ConvPlan& p, void* stream, const LaunchShape* shape) {
     job.jp.parent = p;
     job.tile_records = p.tg.T;
     job.ntiles = staged_tile_count(p.n, nrec, p.tg.T, p.tg.G);
-    const void* fn = reinterpret_cast<const void*>(&k_convert_ws);
+    // the instance with the widened-field transform only for plans that
+    // have widened fields: the branch costs the others a few percent
+    const void* fn = p.dst.kind == K_AOS && p.tg.nwide ? reinterpret_cast<const void*>(&k_convert_ws<true>)
+                                                       : reinterpret_cast<const void*>(&k_convert_ws<false>);
     allow_batch_smem(fn);
     const int occ = occupancy(fn, kBThreads, kBatchSmem);
     const int per_sm = sh.ctas_per_sm ? std::min((int)sh.ctas_per_sm, occ) : occ;
