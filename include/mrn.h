@@ -241,7 +241,8 @@ int mrn_sync_bits(void* stream, uint32_t* bits);
  * most 33,521,664 parents per call, larger n_records returns MRN_ESIZE before
  * anything is launched.  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  All calls share the array and each
+ * first call before any stream capture.  `stream` must belong to the
+ * current device (else MRN_EINVAL), since the address is that device's.  All calls share the array and each
  * clears it on its stream before use, so calls that overlap on the GPU
  * (different streams, no ordering between them) race and must not be
  * issued. */
@@ -316,6 +317,16 @@ typedef struct mrn_batch mrn_batch; /* opaque */
 int mrn_batch_create(const mrn_job* jobs, size_t n_jobs, int use_graph, mrn_batch** out);
 /* Runs every job of the batch on `stream`. */
 int mrn_batch_launch(mrn_batch* b, void* stream);
+/* As mrn_batch_launch, and records three caller-created CUDA events
+ * (cudaEvent_t, passed as void*) on `stream`: ev_begin before the batch's
+ * work, ev_mid after the persistent launch of the non-jagged jobs (and the
+ * scratch reset before it), ev_end after the launch of the jagged AoS jobs.
+ * With use_graph = 1 the events are record nodes of a second graph of the
+ * same work, captured at the first call and pointed at the given events at
+ * each call; a batch without jobs of one kind records two events back to
+ * back.  For measuring each kernel of a replay; no counterpart in the
+ * paper (the batched form is not the paper's). */
+int mrn_batch_launch_timed(mrn_batch* b, void* stream, void* ev_begin, void* ev_mid, void* ev_end);
 /* Baseline: runs the same jobs with one mrn_convert launch per job. */
 int mrn_batch_launch_per_job(mrn_batch* b, void* stream);
 /* Points job j at new buffers of the same schemas, layouts and sizes (the

@@ -37,18 +37,35 @@ struct mrn_batch {
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // The timed form of the graph: the same nodes plus three event-record
+  // nodes (before the scratch reset, between the two kernels, after the
+  // jagged launch), captured with the batch's own placeholder events and
+  // pointed at the caller's events at each replay.
+  cudaGraph_t tgraph = nullptr;
+  cudaGraphExec_t texec = nullptr;
+  cudaGraphNode_t tnode[3] = {};
+  cudaEvent_t tev[3] = {};
   uint32_t ctas_per_sm = 0;
   uint32_t max_chunk = 8;  // consecutive tiles a CTA takes at once
 
   ~mrn_batch() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    drop_timed();
+    for (cudaEvent_t e : tev)
+      if (e) cudaEventDestroy(e);
     if (cap) cudaStreamDestroy(cap);
     cudaFree(d_jobs);
     cudaFree(d_first);
     cudaFree(d_jag);
     cudaFree(d_tile_job);
     cudaFree(d_scratch);
+  }
+  void drop_timed() {
+    if (texec) cudaGraphExecDestroy(texec);
+    if (tgraph) cudaGraphDestroy(tgraph);
+    texec = nullptr;
+    tgraph = nullptr;
   }
 };
 
@@ -214,23 +231,35 @@ int upload(mrn_batch* b) {
   return MRN_OK;
 }
 
-int enqueue(mrn_batch* b, cudaStream_t s) {
-  if (b->total_tiles == 0 && b->jag_tiles == 0) return MRN_OK;
-  if (cudaMemsetAsync(b->d_scratch, 0, b->scratch_bytes, s) != cudaSuccess) return MRN_ECUDA;
+// The batch's work on `s`: scratch reset, the persistent launch of the plain
+// jobs, the launch of the jagged jobs.  With `ev`, ev[0] is recorded first,
+// ev[1] between the two kernels and ev[2] last (`evflags` as for
+// cudaEventRecordWithFlags; cudaEventRecordExternal makes them graph nodes
+// during capture).
+int enqueue(mrn_batch* b, cudaStream_t s, const cudaEvent_t* ev = nullptr, unsigned evflags = 0) {
+  auto mark = [&](int i) { return !ev || cudaEventRecordWithFlags(ev[i], s, evflags) == cudaSuccess; };
+  if (!mark(0)) return MRN_ECUDA;
   int rc = MRN_OK;
-  if (b->total_tiles)
-    rc = launch_batch(b->d_jobs, b->d_first, (unsigned)b->plain.size(), b->total_tiles,
-                      reinterpret_cast<unsigned int*>(b->d_scratch), b->ctas_per_sm, b->max_chunk, s);
+  if (b->total_tiles || b->jag_tiles) {
+    if (cudaMemsetAsync(b->d_scratch, 0, b->scratch_bytes, s) != cudaSuccess) return MRN_ECUDA;
+    if (b->total_tiles)
+      rc = launch_batch(b->d_jobs, b->d_first, (unsigned)b->plain.size(), b->total_tiles,
+                        reinterpret_cast<unsigned int*>(b->d_scratch), b->ctas_per_sm, b->max_chunk, s);
+  }
+  if (!rc && !mark(1)) rc = MRN_ECUDA;
   if (!rc && b->jag_tiles)
     rc = launch_batch_jag(b->d_jag, b->d_tile_job, b->jag_tiles, reinterpret_cast<unsigned int*>(b->d_scratch + 64),
                           reinterpret_cast<unsigned long long*>(b->d_scratch + 256), s);
+  if (!rc && !mark(2)) rc = MRN_ECUDA;
   return rc;
 }
 
-int capture(mrn_batch* b) {
+// Captures the batch's work into *graph / *exec (timed: with the
+// placeholder events as record nodes, whose nodes go to b->tnode).
+int capture_into(mrn_batch* b, bool timed, cudaGraph_t* graph, cudaGraphExec_t* exec) {
   if (!b->cap && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return MRN_ECUDA;
   if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MRN_ECUDA;
-  const int rc = enqueue(b, b->cap);
+  const int rc = timed ? enqueue(b, b->cap, b->tev, cudaEventRecordExternal) : enqueue(b, b->cap);
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
   if (rc || e != cudaSuccess) {
@@ -238,10 +267,44 @@ int capture(mrn_batch* b) {
     cudaGetLastError();
     return rc ? rc : MRN_ECUDA;
   }
-  b->graph = g;
-  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) return MRN_ECUDA;
+  if (timed) {
+    size_t nn = 0;
+    if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return MRN_ECUDA;
+    }
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn && cudaGraphGetNodes(g, nodes.data(), &nn) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return MRN_ECUDA;
+    }
+    int found = 0;
+    for (cudaGraphNode_t nd : nodes) {
+      cudaGraphNodeType ty;
+      cudaEvent_t ev = nullptr;
+      if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeEventRecord) continue;
+      if (cudaGraphEventRecordNodeGetEvent(nd, &ev) != cudaSuccess) continue;
+      for (int i = 0; i < 3; ++i)
+        if (ev == b->tev[i]) {
+          b->tnode[i] = nd;
+          ++found;
+        }
+    }
+    if (found != 3) {
+      cudaGraphDestroy(g);
+      cudaGetLastError();
+      return MRN_ECUDA;
+    }
+  }
+  *graph = g;
+  if (cudaGraphInstantiate(exec, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return MRN_ECUDA;
+  }
   return MRN_OK;
 }
+
+int capture(mrn_batch* b) { return capture_into(b, false, &b->graph, &b->exec); }
 
 }  // namespace
 }  // namespace mrn
@@ -285,6 +348,32 @@ int mrn_batch_launch(mrn_batch* b, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (b->exec) return cudaGraphLaunch(b->exec, s) == cudaSuccess ? MRN_OK : MRN_ECUDA;
   return enqueue(b, s);
+}
+
+int mrn_batch_launch_timed(mrn_batch* b, void* stream, void* ev_begin, void* ev_mid, void* ev_end) {
+  if (!b || !ev_begin || !ev_mid || !ev_end) return MRN_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t ev[3] = {static_cast<cudaEvent_t>(ev_begin), static_cast<cudaEvent_t>(ev_mid),
+                       static_cast<cudaEvent_t>(ev_end)};
+  if (!b->use_graph) return enqueue(b, s, ev, cudaEventRecordDefault);
+  if (!b->texec) {
+    for (cudaEvent_t& e : b->tev)
+      if (!e && cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return MRN_ECUDA;
+      }
+    const int rc = capture_into(b, true, &b->tgraph, &b->texec);
+    if (rc) {
+      b->drop_timed();
+      return rc;
+    }
+  }
+  for (int i = 0; i < 3; ++i)
+    if (cudaGraphExecEventRecordNodeSetEvent(b->texec, b->tnode[i], ev[i]) != cudaSuccess) {
+      cudaGetLastError();
+      return MRN_ECUDA;
+    }
+  return cudaGraphLaunch(b->texec, s) == cudaSuccess ? MRN_OK : MRN_ECUDA;
 }
 
 int mrn_batch_launch_per_job(mrn_batch* b, void* stream) {
@@ -392,6 +481,7 @@ int mrn_batch_tune(mrn_batch* b, void* stream, mrn_batch_tune_result* out) {
     b->graph = nullptr;
     if ((rc = capture(b))) return rc;
   }
+  b->drop_timed();  // captured again, with the new shape, at its next use
   out->max_chunk = best_chunk;
   out->ctas_per_sm = best_cps;
   out->ms = best_ms;

@@ -56,6 +56,15 @@ extern "C" int mrn_convert_jagged_noalloc(const mrn_view* src, const mrn_view* d
   int rc = validate_pair(src, dst, true, &jag);
   if (rc) return rc;
   if (!jag || src->layout.kind != MRN_AOS || dst->layout.kind != MRN_SOA) return MRN_EINVAL;
+  // The array is looked up for the current device: a stream of another
+  // device would run the kernel there against this device's address.
+  int cur = -1, sdev = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess ||
+      cudaStreamGetDevice(static_cast<cudaStream_t>(stream), &sdev) != cudaSuccess) {
+    cudaGetLastError();
+    return MRN_ECUDA;
+  }
+  if (sdev != cur) return MRN_EINVAL;
   if (jagged_scratch_bytes(src->n_records) > MRN_NOALLOC_SCRATCH_BYTES) return MRN_ESIZE;
   JagPlan jp;
   if ((rc = build_jagged_plan(*src, *dst, &jp))) return rc;

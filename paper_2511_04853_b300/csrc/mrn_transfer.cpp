@@ -267,6 +267,14 @@ int TransferEngine::run(const mrn_view& src, const mrn_view& dst, uint64_t chunk
   if (rc) return rc;
   if (!chunk_bytes) chunk_bytes = 4ull << 20;
   n_slots = std::max(1, std::min(16, n_slots ? n_slots : 4));
+  // The staging memory and both internal streams are shared by every call
+  // of this engine, whatever stream it came from: this call's copies and
+  // conversions start only after the previous call's have all finished
+  // (ev_done_ is recorded once both streams have joined), and after the
+  // caller's earlier work.  A call's own chunks still overlap each other.
+  if (cudaStreamWaitEvent(s_copy_, ev_done_, 0) != cudaSuccess ||
+      cudaStreamWaitEvent(s_conv_, ev_done_, 0) != cudaSuccess)
+    return MRN_ECUDA;
   if (cudaEventRecord(ev_start_, user) != cudaSuccess) return MRN_ECUDA;
   cudaStreamWaitEvent(s_copy_, ev_start_, 0);
   cudaStreamWaitEvent(s_conv_, ev_start_, 0);
@@ -284,19 +292,25 @@ int TransferEngine::run(const mrn_view& src, const mrn_view& dst, uint64_t chunk
     const uint64_t need = staging_bytes(src, dst, chunk_bytes, n_slots);
     char* stage = arena;
     if (!stage) {
-      if ((rc = ensure_staging(need))) return rc;
+      rc = ensure_staging(need);
       stage = staging_;
     } else if (arena_bytes < need) {
-      return MRN_ENOMEM;
+      rc = MRN_ENOMEM;
     }
-    rc = src.schema->has_jagged ? run_whole(src, dst, user, stage, need)
-                                : run_chunked(src, dst, chunk_bytes, n_slots, user, stage, need);
+    if (!rc)
+      rc = src.schema->has_jagged ? run_whole(src, dst, user, stage, need)
+                                  : run_chunked(src, dst, chunk_bytes, n_slots, user, stage, need);
   }
-  if (cudaEventRecord(ev_copy_done_, s_copy_) != cudaSuccess) return MRN_ECUDA;
-  cudaStreamWaitEvent(s_conv_, ev_copy_done_, 0);
-  if (cudaEventRecord(ev_done_, s_conv_) != cudaSuccess) return MRN_ECUDA;
-  if (cudaStreamWaitEvent(user, ev_done_, 0) != cudaSuccess) return MRN_ECUDA;
-  return rc;
+  // Every return path after ev_start_ joins the two streams and orders the
+  // caller's stream after them, so that work already queued by a call that
+  // fails part way is finished before the caller's next work (and before a
+  // caller that syncs its own stream frees the buffers).
+  int jrc = MRN_OK;
+  if (cudaEventRecord(ev_copy_done_, s_copy_) != cudaSuccess ||
+      cudaStreamWaitEvent(s_conv_, ev_copy_done_, 0) != cudaSuccess ||
+      cudaEventRecord(ev_done_, s_conv_) != cudaSuccess || cudaStreamWaitEvent(user, ev_done_, 0) != cudaSuccess)
+    jrc = MRN_ECUDA;
+  return rc ? rc : jrc;
 }
 
 int TransferEngine::run_whole(const mrn_view& src, const mrn_view& dst, cudaStream_t, char* stage,

@@ -109,6 +109,7 @@ SIGNATURES = [
                                             ctypes.POINTER(TransferOpts), vp]),
     ("mrn_batch_create", ctypes.c_int, [ctypes.POINTER(Job), sz, ctypes.c_int, ctypes.POINTER(vp)]),
     ("mrn_batch_launch", ctypes.c_int, [vp, vp]),
+    ("mrn_batch_launch_timed", ctypes.c_int, [vp, vp, vp, vp, vp]),
     ("mrn_batch_launch_per_job", ctypes.c_int, [vp, vp]),
     ("mrn_batch_update", ctypes.c_int, [vp, sz, ctypes.POINTER(ViewStruct), ctypes.POINTER(ViewStruct)]),
     ("mrn_batch_destroy", None, [vp]),
@@ -374,6 +375,17 @@ class Batch:
 
     def launch(self, stream=None):
         check(lib().mrn_batch_launch(self._h, _stream(stream)), "mrn_batch_launch")
+
+    def launch_timed(self, ev_begin, ev_mid, ev_end, stream=None):
+        """``mrn_batch_launch_timed``: the events (torch.cuda.Event with
+        timing) are recorded before the batch, between its two kernels and
+        after them."""
+        evs = []
+        for e in (ev_begin, ev_mid, ev_end):
+            if not e.cuda_event:  # torch creates an event at its first record
+                e.record()
+            evs.append(vp(e.cuda_event))
+        check(lib().mrn_batch_launch_timed(self._h, _stream(stream), *evs), "mrn_batch_launch_timed")
 
     def launch_per_job(self, stream=None):
         check(lib().mrn_batch_launch_per_job(self._h, _stream(stream)), "per-job")

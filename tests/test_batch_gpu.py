@@ -275,3 +275,54 @@ def test_empty_jobs_in_a_batch():
         assert mrn.sync() == mrn.OK
         for i, (s, d, want, name) in enumerate(jobs):
             assert np.array_equal(result(d, want, name), want), "job %d (%s)" % (i, name)
+
+
+def test_cfg4_size_law_batch_matches_oracle_with_timed_launch():
+    """320 collections drawn as in the 4,096-collection mixed batch (seed 3:
+    records round(10^U(3, 6)), schema uniform over points / cells / tracks,
+    AoS source, target uniform over SoA / AoSoA(32) / AoSoA(128)), each
+    size capped at 10,000 records so the oracle runs in seconds.  The plain
+    replay and the timed replay (events recorded between the two kernels)
+    both give the oracle's bytes, and the events measure the two kernels."""
+    t = torch_mod()
+    rng = np.random.default_rng(3)
+    count = 320
+    ns = np.rint(10.0 ** rng.uniform(3.0, 6.0, count)).astype(np.int64)
+    sch = rng.integers(0, 3, count)
+    tgt = rng.integers(0, 3, count)
+    targets = [("soa", 0), ("aosoa", 32), ("aosoa", 128)]
+    pairs, checks = [], []
+    schemas = {k: (mrn.Schema(datagen.WORKLOAD_SCHEMAS[k]), oracle.Schema(datagen.WORKLOAD_SCHEMAS[k]))
+               for k in NAMES}
+    for j in range(count):
+        name, n = NAMES[sch[j]], int(min(ns[j], 10000))
+        dk, db = targets[tgt[j]]
+        s, o = schemas[name]
+        d = datagen.workload(name, n, 3000 + j)
+        o_aos = oracle.pack(o, d, "aos")
+        m = d["m"] if name == "tracks" else 0
+        want = oracle.convert(o, o_aos, dk, db, m=m).base[: o.base_bytes(dk, db, n, m)]
+        pool = dev(o_aos.pool) if name == "tracks" else None
+        src = mrn.View(s, "aos", n, base=dev(o_aos.base), child_pool=pool, m=m)
+        dst = dev_dest(s, dk, n, m, db)
+        pairs.append((src, dst))
+        checks.append((dst, want))
+    b = mrn.Batch(pairs, use_graph=True)
+    ev = [t.cuda.Event(enable_timing=True) for _ in range(3)]
+    for timed in (False, True, True):
+        for dst, _ in checks:
+            dst.tensors[0].fill_(0xA5)
+        if timed:
+            b.launch_timed(*ev)
+        else:
+            b.launch()
+        assert mrn.sync() == mrn.OK
+        for k, (dst, want) in enumerate(checks):
+            assert np.array_equal(host(dst.tensors[0], want.size), want), "job %d (timed %s)" % (k, timed)
+    t.cuda.synchronize()
+    assert ev[0].elapsed_time(ev[1]) > 0 and ev[1].elapsed_time(ev[2]) > 0
+
+
+def torch_mod():
+    import torch
+    return torch

@@ -237,3 +237,38 @@ def test_jagged_aosoa_both_directions(B):
     assert mrn.sync() == mrn.OK
     assert np.array_equal(h_rec.numpy()[: n * 24], o_aos.base[: n * 24])
     assert np.array_equal(h_pool.numpy()[: m * 8], o_aos.pool[: m * 8])
+
+
+def test_back_to_back_calls_on_different_streams_share_staging_safely():
+    """Host -> device calls issued on two streams with no synchronisation
+    between them use the same staging memory: a chunked call on stream A
+    followed by a jagged (whole-source) call on stream B, then a chunked
+    call with another chunk size on stream A.  Each result equals the
+    oracle's."""
+    t = torch()
+    a, b = t.cuda.Stream(), t.cuda.Stream()
+    n = 200000
+    s, o, d = cells(n, seed=11)
+    o_aos = oracle.pack(o, d, "aos")
+    o_soa = oracle.convert(o, o_aos, "soa")
+    st, ot = mrn.Schema(datagen.TRACKS), oracle.Schema(datagen.TRACKS)
+    nt = 30000
+    dt = datagen.workload("tracks", nt, 12)
+    ot_aos = oracle.pack(ot, dt, "aos")
+    ot_soa = oracle.convert(ot, ot_aos, "soa")
+    h_cells = host_side(o_aos.base)
+    h_rec, h_pool = host_side(ot_aos.base), host_side(ot_aos.pool)
+    d1, d3 = garbage(s.required_bytes("soa", n)), garbage(s.required_bytes("soa", n))
+    d2 = garbage(st.required_bytes("soa", nt, dt["m"]))
+    t.cuda.synchronize()
+    mrn.transfer_convert(mrn.View(s, "aos", n, base=h_cells, mem="pinned"), mrn.View(s, "soa", n, base=d1),
+                         chunk_bytes=256 << 10, n_slots=2, stream=a)
+    mrn.transfer_convert(mrn.View(st, "aos", nt, base=h_rec, child_pool=h_pool, m=dt["m"], mem="pinned"),
+                         mrn.View(st, "soa", nt, base=d2, m=dt["m"]), stream=b)
+    mrn.transfer_convert(mrn.View(s, "aos", n, base=h_cells, mem="pinned"), mrn.View(s, "soa", n, base=d3),
+                         chunk_bytes=1 << 20, n_slots=3, stream=a)
+    t.cuda.synchronize()
+    assert mrn.sync() == mrn.OK
+    assert np.array_equal(host(d1, o_soa.base.size), o_soa.base)
+    assert np.array_equal(host(d2, ot_soa.base.size), ot_soa.base)
+    assert np.array_equal(host(d3, o_soa.base.size), o_soa.base)
