@@ -1,23 +1,30 @@
 """Benchmark of the layout-conversion hot path on one B300 (or N replicas).
 
-Step: one pass over a batch of R calorimeter-cell collections (200,000
-records of {f32 energy, time, eta, phi; u32 cell_id; u16 gain, quality},
-24-byte AoS records), each converted AoS -> SoA, SoA -> AoSoA(32) and
-AoSoA(32) -> AoS (three independent conversions per collection, each
-reading its own resident input), all 3R conversions in ONE persistent kernel
-launch replayed from a CUDA graph.  Inputs are resident in HBM; the batch
-(R * 6 buffers of 4.8 MB) is larger than the 126 MB L2, so every step
-streams from HBM.
+Step: one replay of the CUDA graph of the mixed batch -- 4,096 collections
+(records round(10^U(3, 6)), seed 3; schema uniform over points / cells /
+tracks, the tracks jagged with Poisson(20) children clipped at 256; AoS
+source; target uniform over SoA / AoSoA(32) / AoSoA(128)) converted in two
+launches: the persistent k_batch (points and cells) and k_batch_jag (the
+jagged tracks, one CTA per 1,024-parent tile).  About 92 GB of algorithmic
+bytes per step, inputs resident in HBM (far larger than the 126 MB L2).
 
-value         algorithmic bytes (read + write of every conversion) / step time
-e2e           the same bytes through the C ABI with pinned HOST buffers: per
-              collection host AoS -> device SoA (transfer-and-convert),
-              SoA -> AoSoA(32) on the device, device AoSoA(32) -> host AoS
-roofline      the persistent kernel against the measured HBM copy bandwidth
-cpu_baseline  the CPU oracle (plain C, one thread) on a bounded sample
-batched_vs_per_call  the same step with one launch per conversion
-served        Poisson arrivals of transfer-and-convert requests at fractions
-              of the measured saturation rate: p50/p99 latency, throughput
+value         algorithmic bytes (read + write of every conversion) / step
+              time (CUDA events around all timed steps)
+roofline      the dominant kernel (k_batch_jag) against the measured HBM copy
+              bandwidth, from events recorded inside every timed replay
+              between the two kernels; per_kernel gives both
+e2e           the same collections through the C ABI from pinned HOST
+              buffers: mrn_transfer_convert host AoS -> device target for
+              every collection, then the status word read back
+cpu_baseline  the CPU oracle (plain C) on a bounded sample of the same jobs
+batched_vs_per_call  the same jobs with one mrn_convert launch each
+extras        single conversions (configs 1-3 and 2^26 scale-ups), the
+              transfer chunk sweep against the host link, the 16-collection
+              cell batch, the sensor grid, collections, the served sweep
+
+Before timing, a seeded sample of the batch (every tracks job of at most
+200,000 parents and every 64th job) is compared byte for byte with the
+oracle, and the timed outputs are compared with the checked ones.
 
 --impl reference runs the CPU oracle as the reference arm on the same
 workload and metric.  Under torchrun (N > 1) every rank runs an independent
@@ -42,6 +49,7 @@ BATCH = 16
 BLOCK = 32
 FALLBACK_HBM_GBS = 6400.0
 METRIC = "layout-convert HBM GB/s"
+MIXED_SEED = 3
 KERNEL_SOURCES = ["paper_2511_04853_b300/csrc/mrn_kernels.cu", "paper_2511_04853_b300/csrc/mrn_device.cuh",
                   "paper_2511_04853_b300/csrc/mrn_plan.h"]
 
@@ -49,20 +57,25 @@ KERNEL_SOURCES = ["paper_2511_04853_b300/csrc/mrn_kernels.cu", "paper_2511_04853
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--batch", type=int, default=BATCH, help="collections of the cell batch extra")
     ap.add_argument("--device-only", action="store_true",
                     help="profiling runs: only the timed device step (no e2e, baselines or extras)")
     ap.add_argument("--case", default=None,
                     help="profiling runs: repeat one conversion, e.g. cells:aos:soa:16777216 "
                          "(schema:src[/B]:dst[/B]:records), or one overlapping move, memmove:bytes:shift")
-    ap.add_argument("--mixed-jobs", type=int, default=4096,
-                    help="collections in the mixed batch (0 skips it)")
-    ap.add_argument("--mixed-only", action="store_true", help="run the mixed batch alone")
-    ap.add_argument("--serve-rates", default="0.25,0.5,0.9,1.2",
+    ap.add_argument("--mixed-jobs", type=int, default=4096, help="collections in the mixed batch")
+    ap.add_argument("--mixed-only", action="store_true",
+                    help="profiling runs: the mixed batch's check and timed steps only")
+    ap.add_argument("--serve-rates", default="0.1,0.25,0.5,0.75,0.9,1.0,1.2",
                     help="served arrival rates as fractions of the measured saturation rate")
+    ap.add_argument("--serve-requests", type=int, default=10000, help="requests per served rate")
+    ap.add_argument("--serve-seconds", type=float, default=30.0, help="offered time per served rate")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extras (single conversions, sweeps, cell batch, sensor grid, "
+                         "collections, serving)")
     return ap.parse_args()
 
 
@@ -88,21 +101,32 @@ def bytes_per_collection(stride=24, n=N_RECORDS):
     return 3 * 2 * n * stride
 
 
-def workload_config(batch):
-    return {"workload": "calorimeter cells: %d collections x 200,000 records (24-byte AoS: f32 energy, "
-                        "time, eta, phi; u32 cell_id; u16 gain, quality); per collection AoS->SoA, "
-                        "SoA->AoSoA(32), AoSoA(32)->AoS" % batch,
-            "records_per_collection": N_RECORDS, "collections_per_step": batch,
-            "launch": "one persistent kernel per step (CUDA graph replay)",
-            "l2": "inputs larger than L2 (%d MB touched per step, L2 126 MB)"
-                  % (batch * bytes_per_collection() // 10**6),
-            "parallelism": "replicas"}
+def cells_workload(batch):
+    return ("calorimeter cells: %d collections x 200,000 records (24-byte AoS); per collection AoS->SoA, "
+            "SoA->AoSoA(32), AoSoA(32)->AoS" % batch)
+
+
+def workload_config(jobs, alg_bytes=None, records=None):
+    """The step's workload: the mixed batch (the short name first)."""
+    c = {"workload": "mixed batch: %d collections, one CUDA graph (k_batch + k_batch_jag)" % jobs,
+         "collections": jobs,
+         "sizes": "records round(10^U(3,6)), seed %d" % MIXED_SEED,
+         "schemas": "uniform over points (32 B AoS), cells (24 B), tracks (24 B + jagged 8 B children, "
+                    "lengths min(Poisson(20), 256))",
+         "layouts": "AoS source; target uniform over SoA / AoSoA(32) / AoSoA(128)",
+         "l2": "inputs larger than L2 (every step streams the whole batch from HBM; L2 126 MB)",
+         "parallelism": "replicas"}
+    if alg_bytes is not None:
+        c["algorithmic_bytes_per_step"] = alg_bytes
+    if records is not None:
+        c["records"] = records
+    return c
 
 
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
-    """nvidia-smi samples (200 ms) while the timed region runs."""
+    """nvidia-smi samples (every 50 ms) while the timed region runs."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -114,16 +138,24 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             threading.Thread(target=self._read, daemon=True).start()
         except OSError:
             self.proc = None
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
-    def stop(self):
+    def wait_first(self, timeout=3.0):
+        """Waits until nvidia-smi has printed its first sample."""
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.01)
+
+    def stop(self, window=None):
+        """Median SM clock and the throttle reasons of the samples taken in
+        `window` (host times (t0, t1); all samples when None)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -133,7 +165,9 @@ class ClockSampler:
             self.proc.kill()
         sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for t, ln in self.lines:
+            if window and not (window[0] <= t <= window[1]):
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -153,28 +187,50 @@ class ClockSampler:
 
 # --------------------------------------------------------------- reference
 
-def oracle_step_setup(n_records, seed=1):
+PACKED = {"points": 25, "cells": 24}
+
+
+def mixed_alg_bytes(name, n, m=0):
+    """Algorithmic bytes of one job of the mixed batch: each record read
+    once and written once (the packed field bytes on the field-major side);
+    tracks: 24 B parent + 8 B per child read, 12 B parent columns + 4 B
+    offset + 8 B per child written, plus the last offset."""
+    if name == "tracks":
+        return 24 * n + 8 * m + 12 * n + 4 * (n + 1) + 8 * m
+    return n * ({"points": 32, "cells": 24}[name] + PACKED[name])
+
+
+def oracle_mixed_sample(stride, jobs=4096, offset=0):
+    """Jobs offset, offset + stride, ... of the mixed batch's plan, generated
+    on the host by the seeded generator and laid out as AoS by the oracle;
+    returns a step that converts every sampled job with the oracle, its
+    algorithmic bytes and a description."""
     import datagen
     import oracle
-    o = oracle.Schema(datagen.CELLS)
-    d = datagen.workload("cells", n_records, seed)
-    aos = oracle.pack(o, d, "aos")
-    soa = oracle.convert(o, aos, "soa")
-    blk = oracle.convert(o, soa, "aosoa", BLOCK)
-    outs = [oracle.alloc(o, "soa", n_records), oracle.alloc(o, "aosoa", n_records, 0, BLOCK),
-            oracle.alloc(o, "aos", n_records)]
+    plan = mixed_plan(jobs)
+    schemas = {k: oracle.Schema(datagen.WORKLOAD_SCHEMAS[k]) for k in MIXED_SCHEMAS}
+    work, alg = [], 0
+    for i in range(offset, len(plan), stride):
+        name, n, (dk, db) = plan[i]
+        o = schemas[name]
+        d = datagen.workload(name, n, 1000 + i)
+        src = oracle.pack(o, d, "aos")
+        m = d["m"] if name == "tracks" else 0
+        work.append((o, src, oracle.alloc(o, dk, n, m, db)))
+        alg += mixed_alg_bytes(name, n, m)
 
     def step():
-        for src, dst in zip([aos, soa, blk], outs):
+        for o, src, dst in work:
             st, _ = oracle.convert_into(o, src, dst)
             assert st == 0
-    return step
+    return step, alg, "%d of the %d mixed-batch collections (every %d-th from %d), %.2f GB algorithmic" % (
+        len(work), jobs, stride, offset, alg / 1e9)
 
 
-def cpu_oracle_rate(seconds, n_records):
-    """The oracle (plain C, one thread) on the step's three conversions of
-    one collection of n_records, repeated for about `seconds`; GB/s."""
-    step = oracle_step_setup(n_records)
+def cpu_oracle_rate(seconds, stride=64):
+    """The oracle (plain C, one thread) on a sample of the mixed batch,
+    repeated for about `seconds`; GB/s."""
+    step, alg, what = oracle_mixed_sample(stride)
     reps, t0 = 0, time.perf_counter()
     while True:
         step()
@@ -182,15 +238,15 @@ def cpu_oracle_rate(seconds, n_records):
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    return reps * bytes_per_collection(24, n_records) / el / 1e9, reps, el
+    return alg * reps / el / 1e9, reps, el, what
 
 
 def _oracle_worker(job):
-    """One host process of the all-cores oracle measurement: its own seeded
-    collection, the three conversions repeated for `seconds` from a common
+    """One host process of the all-cores oracle measurement: its own slice
+    of the sample, the conversions repeated for `seconds` from a common
     start time."""
-    seconds, n_records, seed, start_at = job
-    step = oracle_step_setup(n_records, seed)
+    seconds, stride, offset, start_at = job
+    step, alg, _ = oracle_mixed_sample(stride, offset=offset)
     step()
     while time.time() < start_at:
         time.sleep(0.01)
@@ -200,57 +256,62 @@ def _oracle_worker(job):
         reps += 1
         el = time.perf_counter() - t0
         if el >= seconds:
-            return reps, el
+            return reps * alg, el
 
 
-def cpu_oracle_rate_all_cores(seconds, n_records):
+def cpu_oracle_rate_all_cores(seconds):
     """The same oracle, unchanged, in one process per host core (spawned:
-    the parent already holds a CUDA context), each on its own collection,
-    all started together; aggregate GB/s."""
+    the parent already holds a CUDA context), each on its own slice of the
+    mixed batch (every 256th job from a per-core offset), all started
+    together; aggregate GB/s."""
     import multiprocessing as mp
     try:
         cores = len(os.sched_getaffinity(0))
     except AttributeError:
         cores = os.cpu_count() or 1
     ctx = mp.get_context("spawn")
-    lead = 5.0 + 0.05 * cores
+    lead = 10.0 + 0.1 * cores
     start_at = time.time() + lead
     pool = ctx.Pool(cores)
     try:
-        job = pool.map_async(_oracle_worker, [(seconds, n_records, 1 + i, start_at) for i in range(cores)])
-        res = job.get(timeout=lead + seconds + 120.0)  # a worker that died must not hang the bench
+        job = pool.map_async(_oracle_worker, [(seconds, 256, (7 * i) % 256, start_at) for i in range(cores)])
+        res = job.get(timeout=lead + seconds + 180.0)  # a worker that died must not hang the bench
     except Exception as e:
         pool.terminate()
         return None, "not measured: %s" % type(e).__name__
     pool.close()
     pool.join()
-    per = bytes_per_collection(24, n_records)
-    return sum(r * per / el for r, el in res) / 1e9, cores
+    return sum(b / el for b, el in res) / 1e9, cores
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle on the step's workload (the mixed
+    batch), each step a bounded sample of its collections sized so the
+    whole run takes about a minute."""
     if rank != 0:
         return
-    # size each step so the whole --steps/--warmup run stays near a minute
-    probe, _, _ = cpu_oracle_rate(0.5, 20000)
+    probe_step, probe_alg, _ = oracle_mixed_sample(256, args.mixed_jobs)
+    t0 = time.perf_counter()
+    probe_step()
+    rate = probe_alg / max(1e-6, time.perf_counter() - t0)
     per_step_s = 60.0 / max(1, args.steps + args.warmup)
-    n_rec = int(max(1000, min(N_RECORDS, per_step_s * probe * 1e9 / bytes_per_collection(24, 1))))
-    step = oracle_step_setup(n_rec)
+    full = sum(mixed_alg_bytes(nm, n, 20 * n if nm == "tracks" else 0) for nm, n, _ in mixed_plan(args.mixed_jobs))
+    stride = int(min(args.mixed_jobs, max(1, full / max(1.0, per_step_s * rate))))
+    step, alg, what = oracle_mixed_sample(stride, args.mixed_jobs)
     for _ in range(args.warmup):
         step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         step()
     el = time.perf_counter() - t0
-    val = args.steps * bytes_per_collection(24, n_rec) / el / 1e9
-    sample = "%d-record cells collection x 3 conversions per step" % n_rec
+    val = args.steps * alg / el / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": round(val, 3), "unit": "GB/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(el / args.steps * 1e3, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": workload_config(args.batch),
+            "config": workload_config(args.mixed_jobs),
             "cpu_baseline": {"value": round(val, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": "per step: " + what},
             "e2e": {"value": round(val, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -327,97 +388,78 @@ def device_aos(torch, s, name, n, seed):
     return rec, pool, m
 
 
-def run_mixed(mrn, torch, stream, peak, args):
-    """The mixed batch (4,096 collections by default) in one persistent
-    launch per step under a CUDA graph, with the autotuner's shapes and
-    without them, against one launch per collection on the same stream."""
+def build_mixed(mrn, torch, jobs):
+    """The mixed batch's collections on the device: AoS sources generated
+    with the workload distributions, garbage-filled destinations, and the
+    job list (schema name, records, children, target, buffers)."""
     import datagen
-    plan = mixed_plan(args.mixed_jobs)
+    plan = mixed_plan(jobs)
     schemas = {k: mrn.Schema(datagen.WORKLOAD_SCHEMAS[k]) for k in MIXED_SCHEMAS}
-    pairs, outs, alg, alg_jag = [], [], 0, 0
-    t_setup = time.perf_counter()
+    items, alg, alg_jag = [], 0, 0
+    t0 = time.perf_counter()
     for i, (name, n, (dk, db)) in enumerate(plan):
         s = schemas[name]
         rec, pool, m = device_aos(torch, s, name, n, 1000 + i)
-        out = torch.empty(s.required_bytes(dk, n, m, db), dtype=torch.uint8, device="cuda")
+        out = torch.full((s.required_bytes(dk, n, m, db),), 0xA5, dtype=torch.uint8, device="cuda")
         src = mrn.View(s, "aos", n, base=rec, child_pool=pool, m=m)
         dst = mrn.View(s, dk, n, block=db, base=out, m=m)
-        pairs.append((src, dst))
-        outs.append(out)
+        items.append({"name": name, "n": n, "m": m, "dk": dk, "db": db, "rec": rec, "pool": pool,
+                      "out": out, "src": src, "dst": dst, "s": s})
+        a = mixed_alg_bytes(name, n, m)
+        alg += a
         if name == "tracks":
-            alg += 24 * n + 8 * m + 12 * n + 4 * (n + 1) + 8 * m
-            alg_jag += 24 * n + 8 * m + 12 * n + 4 * (n + 1) + 8 * m
-        else:
-            alg += n * (s.stride + sum(c["size"] for c in s.columns))
+            alg_jag += a
     torch.cuda.synchronize()
-    setup_s = time.perf_counter() - t_setup
+    return {"items": items, "alg": alg, "alg_jag": alg_jag, "alg_plain": alg - alg_jag,
+            "records": sum(n for _, n, _ in plan), "setup_s": round(time.perf_counter() - t0, 1),
+            "pairs": [(it["src"], it["dst"]) for it in items]}
 
-    def timed(fn, reps):
-        for _ in range(2):
-            fn()
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(reps):
-            fn()
-        b.record(stream)
-        torch.cuda.synchronize()
-        assert mrn.sync() == mrn.OK
-        return a.elapsed_time(b) / reps
 
-    res = {"workload": "%d collections, records round(10^U(3,6)), schema uniform over points / cells / "
-                       "tracks (jagged, Poisson(20) children clipped at 256), AoS source, target uniform over "
-                       "SoA / AoSoA(32) / AoSoA(128)" % len(plan),
-           "records": sum(n for _, n, _ in plan), "algorithmic_bytes": alg,
-           "algorithmic_bytes_jagged_jobs": alg_jag, "setup_s": round(setup_s, 1)}
-    # autotuner off: the library's default shapes
-    mrn.autotune_clear()
-    plain = mrn.Batch(pairs, use_graph=True)
-    plain.launch()
-    torch.cuda.synchronize()
-    assert mrn.sync() == mrn.OK
-    want = [o.clone() for o in outs]
-    for o in outs:
-        o.fill_(0xA5)
-    ms_plain = timed(plain.launch, 5)
-    del plain
-    # one launch per collection, same kernels, same stream
-    per = mrn.Batch(pairs, use_graph=False)
-    for o in outs:
-        o.fill_(0xA5)
-    ms_per = timed(per.launch_per_job, 3)
-    for o, w in zip(outs, want):
-        assert torch.equal(o, w), "per-call output differs from the batched output"
-    del per
-    # autotuned shapes for every non-jagged (schema, target) pair
-    tuned = {}
-    for name in ("points", "cells"):
-        for dk, db in MIXED_TARGETS:
-            r = mrn.autotune(schemas[name], "aos", dk, 1 << 22, 0, db)
-            tuned["%s_aos_to_%s%s" % (name, dk, db or "")] = {k: r[k] for k in ("staged", "threads",
-                                                                               "tile_records", "ctas_per_sm")}
-    tb = mrn.Batch(pairs, use_graph=True)
-    launch_shape = tb.tune()
-    for o in outs:
-        o.fill_(0xA5)
-    ms_tuned = timed(tb.launch, 5)
-    for o, w in zip(outs, want):
-        assert torch.equal(o, w), "autotuned batch output differs"
-    del tb
-    mrn.autotune_clear()
-    best = min(ms_plain, ms_tuned)
-    res.update({"ms_per_launch_default_shapes": round(ms_plain, 3),
-                "ms_per_launch_autotuned": round(ms_tuned, 3),
-                "gbps": round(alg / (best * 1e-3) / 1e9, 1),
-                "frac_of_hbm": round(alg / (best * 1e-3) / 1e9 / peak, 3),
-                "gbps_default_shapes": round(alg / (ms_plain * 1e-3) / 1e9, 1),
-                "gbps_autotuned": round(alg / (ms_tuned * 1e-3) / 1e9, 1),
-                "per_call_ms": round(ms_per, 3), "per_call_launches": len(plan),
-                "speedup_vs_per_call": round(ms_per / best, 3),
-                "autotuned_shapes": tuned, "autotuned_launch": launch_shape})
-    del want, outs, pairs
-    torch.cuda.empty_cache()
-    return res
+def oracle_check_mixed(torch, M, max_tracks=200_000, every=64):
+    """Compares a seeded sample of the batch's outputs byte for byte with
+    the oracle run on the same input bytes: every tracks job of at most
+    max_tracks parents and every `every`-th job.  The oracle (a C library
+    called through ctypes, which releases the GIL) runs on one thread per
+    host core."""
+    import numpy as np
+    import datagen
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    schemas = {k: oracle.Schema(datagen.WORKLOAD_SCHEMAS[k]) for k in MIXED_SCHEMAS}
+    pick = [i for i, it in enumerate(M["items"])
+            if (it["name"] == "tracks" and it["n"] <= max_tracks) or i % every == 0]
+
+    def one(i):
+        it = M["items"][i]
+        o, n, m = schemas[it["name"]], it["n"], it["m"]
+        rec = it["rec"][: n * o.stride].cpu().numpy()
+        pool = it["pool"][: m * 8].cpu().numpy() if it["pool"] is not None else None
+        src = oracle.Side(oracle.AOS, n, m, base=rec, pool=pool)
+        dst = oracle.alloc(o, it["dk"], n, m, it["db"])
+        st, _ = oracle.convert_into(o, src, dst)
+        nb = o.base_bytes(it["dk"], it["db"], n, m)
+        got = it["out"][:nb].cpu().numpy()
+        return st == 0 and np.array_equal(got, dst.base[:nb]), nb
+    t0 = time.perf_counter()
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    with ThreadPoolExecutor(max(1, cores)) as ex:
+        res = list(ex.map(one, pick))
+    bad = [pick[k] for k, (ok, _) in enumerate(res) if not ok]
+    assert not bad, "mixed-batch jobs differ from the oracle: %s" % bad[:10]
+    return {"jobs_checked": len(pick), "tracks_jobs_checked": sum(1 for i in pick if M["items"][i]["name"] == "tracks"),
+            "output_bytes_compared": int(sum(nb for _, nb in res)), "seconds": round(time.perf_counter() - t0, 1),
+            "rule": "every tracks job of <= %d parents and every %d-th job, oracle on the same input bytes, "
+                    "bit-exact" % (max_tracks, every)}
+
+
+def outputs_equal(torch, M, want):
+    for k, (it, w) in enumerate(zip(M["items"], want)):
+        if not torch.equal(it["out"], w):
+            return k
+    return -1
 
 
 # -------------------------------------------------------------------- mine
@@ -466,7 +508,9 @@ def check_outputs(torch, colls):
         assert torch.equal(c["out"][2], c["aos"]), "AoSoA->AoS output differs from the AoS input"
 
 
-def traffic_record():
+def traffic_record(kernel):
+    """DRAM bytes per algorithmic byte of `kernel` from the committed ncu
+    summary, while the kernel sources are the ones it was taken on."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
@@ -474,7 +518,60 @@ def traffic_record():
         j = json.load(f)
     if j.get("kernel_source_hash") != kernel_hash():
         return None
-    return j
+    return j.get("kernels", {}).get(kernel)
+
+
+def roof(alg, ms, peak, peak_src, kernel, ratio_rec, **kw):
+    achieved = alg / (ms * 1e-3) / 1e9
+    r = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+         "frac": round(achieved / peak, 4),
+         "traffic": int(ratio_rec["traffic_per_algorithmic_byte"] * alg) if ratio_rec else None,
+         "kernel": kernel, "algorithmic_bytes_per_launch": alg, "launch_ms_mean": round(ms, 5),
+         "peak_source": ("of measured (MEASURED_PEAKS.json hbm_gbs, copy read+write)" if peak_src == "measured"
+                         else "of fallback 6.4 TB/s")}
+    if ratio_rec:
+        r["traffic_source"] = "ncu dram__bytes read+write per algorithmic byte on %s, scaled to this launch" % (
+            ratio_rec["workload"])
+    r.update(kw)
+    return r
+
+
+def timed_steps(mrn, torch, stream, batch, steps, warmup, world, local):
+    """Warm-up replays, then `steps` timed replays of the batch's graph with
+    events between its kernels in every replay; clocks sampled meanwhile."""
+    import torch.distributed as dist
+    clk = ClockSampler(local)
+    clk.start()
+    clk.wait_first()
+    for _ in range(warmup):
+        batch.launch()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for e in ev:  # create the events before the timed region
+        for x in e:
+            x.record(stream)
+    torch.cuda.synchronize()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0 = time.time()
+    t_start.record(stream)
+    for k in range(steps):
+        batch.launch_timed(*ev[k], stream=stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    h1 = time.time()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    time.sleep(0.06)
+    clocks = clk.stop(window=(h0, h1))
+    clocks["window_s"] = round(h1 - h0, 3)
+    total = t_start.elapsed_time(t_end)
+    return {"ms_per_step": total / steps, "k_batch": [a.elapsed_time(b) for a, b, _ in ev],
+            "k_batch_jag": [b.elapsed_time(c) for _, b, c in ev], "launch": [a.elapsed_time(c) for a, _, c in ev],
+            "clocks": clocks}
 
 
 def run_mine(args, rank, world):
@@ -486,197 +583,191 @@ def run_mine(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    s = mrn.Schema(datagen.CELLS)
-    colls = make_inputs(mrn, torch, s, args.batch)
-    batch = mrn.Batch(pairs_for(mrn, s, colls), use_graph=True)
-    launch_shape = batch.tune()  # the batch autotuner picks the launch shape (setup, not timed)
-    step_bytes = args.batch * bytes_per_collection()
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    # the measured path is checked before it is timed
+    peak, peak_src = peaks()
+    M = build_mixed(mrn, torch, args.mixed_jobs)
+    # autotuner: per-pair tile shapes, then the batch's launch shape
+    tuned = {}
+    profiling = args.device_only or args.mixed_only
+    for name in () if profiling else ("points", "cells"):
+        s = mrn.Schema(datagen.WORKLOAD_SCHEMAS[name])
+        for dk, db in MIXED_TARGETS:
+            r = mrn.autotune(s, "aos", dk, 1 << 22, 0, db)
+            tuned["%s_aos_to_%s%s" % (name, dk, db or "")] = {k: r[k] for k in ("staged", "threads",
+                                                                               "tile_records", "ctas_per_sm")}
+    batch = mrn.Batch(M["pairs"], use_graph=True)
+    launch_shape = {} if profiling else batch.tune()
+    # the measured path is checked before it is timed: a sample against the
+    # oracle, then the whole output kept for the checks after timing
+    for it in M["items"]:
+        it["out"].fill_(0xA5)
     batch.launch()
     assert mrn.sync() == mrn.OK
-    check_outputs(torch, colls)
-
-    # ---- device step: one persistent launch (graph replay) per step
-    for _ in range(args.warmup):
-        batch.launch()
-    torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-    clk = ClockSampler(local)
-    clk.start()
-    # per-launch events bracket every 16th launch (the kernel's launch
-    # duration for the roofline); the others run back to back
-    sampled = list(range(0, args.steps, 16))
-    ev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in sampled}
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    for k in range(args.steps):
-        if k in ev:
-            ev[k][0].record(stream)
-            batch.launch()
-            ev[k][1].record(stream)
-        else:
-            batch.launch()
-    t_end.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-    clocks = clk.stop()
-    total_ms = t_start.elapsed_time(t_end)
-    launch_ms = [a.elapsed_time(b) for a, b in ev.values()]
-    ms_step = total_ms / args.steps
+    parity = oracle_check_mixed(torch, M) if rank == 0 else None
+    want = [it["out"].clone() for it in M["items"]]
+    T = timed_steps(mrn, torch, stream, batch, args.steps, args.warmup, world, local)
+    ms_step = T["ms_per_step"]
     if world > 1:
         t = torch.tensor([ms_step], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
-    value = world * step_bytes / (ms_step * 1e-3) / 1e9
+    value = world * M["alg"] / (ms_step * 1e-3) / 1e9
     assert mrn.sync() == mrn.OK
-    check_outputs(torch, colls)
-
-    if args.device_only:
+    bad = outputs_equal(torch, M, want)
+    assert bad < 0, "timed output of job %d differs from the checked output" % bad
+    lm, lj, lb = (statistics.mean(T[k]) for k in ("launch", "k_batch_jag", "k_batch"))
+    roofline = roof(M["alg_jag"], lj, peak, peak_src, "k_batch_jag (the %d jagged tracks jobs; one CTA per "
+                    "1,024-parent tile)" % sum(1 for it in M["items"] if it["name"] == "tracks"),
+                    traffic_record("k_batch_jag"),
+                    launch_samples="every timed replay (%d), events recorded inside the graph" % args.steps,
+                    step={"launch_ms_mean": round(lm, 5), "ms_per_step": round(ms_step, 5),
+                          "gbps": round(M["alg"] / (lm * 1e-3) / 1e9, 1),
+                          "frac": round(M["alg"] / (lm * 1e-3) / 1e9 / peak, 4)},
+                    per_kernel={"k_batch_jag": {"ms_mean": round(lj, 4), "algorithmic_bytes": M["alg_jag"],
+                                                "gbps": round(M["alg_jag"] / (lj * 1e-3) / 1e9, 1),
+                                                "frac": round(M["alg_jag"] / (lj * 1e-3) / 1e9 / peak, 4)},
+                                "k_batch": {"ms_mean": round(lb, 4), "algorithmic_bytes": M["alg_plain"],
+                                            "gbps": round(M["alg_plain"] / (lb * 1e-3) / 1e9, 1),
+                                            "frac": round(M["alg_plain"] / (lb * 1e-3) / 1e9 / peak, 4),
+                                            "note": "includes the scratch-reset memset node before it",
+                                            "traffic": (int(traffic_record("k_batch")["traffic_per_algorithmic_byte"]
+                                                            * M["alg_plain"]) if traffic_record("k_batch") else None)}})
+    if profiling:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
-                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
-                              "mode": "device-only (profiling)", "config": workload_config(args.batch)}),
-                  flush=True)
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+                              "mode": "device-only (profiling)", "roofline": roofline,
+                              "config": workload_config(args.mixed_jobs, M["alg"], M["records"])}), flush=True)
         return
+    finish_mine(mrn, torch, stream, args, rank, world, M, batch, want, T, ms_step, value, roofline, parity,
+                launch_shape, tuned, peak)
 
+
+def finish_mine(mrn, torch, stream, args, rank, world, M, batch, want, T, ms_step, value, roofline, parity,
+                launch_shape, tuned, peak):
+    """Everything after the timed step: the per-call baseline and the
+    default-shape batch, e2e, the extras, the CPU baseline, the JSON line."""
     extra = {}
+    alg_step, records = M["alg"], M["records"]
     if rank == 0:
-        # ---- per-call baseline: the same 3R conversions, one launch each
-        for _ in range(3):
-            batch.launch_per_job()
-        torch.cuda.synchronize()
-        reps = max(3, min(50, args.steps // 10))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(reps):
-            batch.launch_per_job()
-        b.record(stream)
-        torch.cuda.synchronize()
-        per_call_ms = a.elapsed_time(b) / reps
-        assert mrn.sync() == mrn.OK
-        check_outputs(torch, colls)
-        extra["batched_vs_per_call"] = {"per_call_ms_per_step": round(per_call_ms, 4),
-                                        "batched_ms_per_step": round(ms_step, 4),
-                                        "speedup": round(per_call_ms / ms_step, 3),
-                                        "per_call_launches_per_step": 3 * args.batch}
-
-    # ---- end to end through pinned host buffers
-    e2e = run_e2e(mrn, torch, s, colls, args, world)
-    del batch
+        def timed(fn, reps):
+            fn()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            assert mrn.sync() == mrn.OK
+            return a.elapsed_time(b) / reps
+        # one mrn_convert launch per collection, same kernels, same stream
+        for it in M["items"]:
+            it["out"].fill_(0xA5)
+        per_ms = timed(batch.launch_per_job, 3)
+        bad = outputs_equal(torch, M, want)
+        assert bad < 0, "per-call output of job %d differs" % bad
+        extra["batched_vs_per_call"] = {"per_call_ms_per_step": round(per_ms, 3), "batched_ms_per_step":
+                                        round(ms_step, 3), "speedup": round(per_ms / ms_step, 3),
+                                        "per_call_launches_per_step": len(M["items"]),
+                                        "per_call_gbps": round(M["alg"] / (per_ms * 1e-3) / 1e9, 1)}
+        # the autotuner off: default tile shapes and launch shape
+        mrn.autotune_clear()
+        plain = mrn.Batch(M["pairs"], use_graph=True)
+        for it in M["items"]:
+            it["out"].fill_(0xA5)
+        def_ms = timed(plain.launch, 5)
+        bad = outputs_equal(torch, M, want)
+        assert bad < 0, "default-shape output of job %d differs" % bad
+        del plain
+        extra["autotuner"] = {"default_shapes_ms_per_step": round(def_ms, 3), "autotuned_ms_per_step":
+                              round(ms_step, 3), "gain": round(def_ms / ms_step, 4),
+                              "launch_shape": dict(launch_shape, chosen_by="mrn_batch_tune"),
+                              "pair_shapes": tuned}
+    link = host_link(torch, stream) if rank == 0 else None
+    e2e = run_e2e_mixed(mrn, torch, M, world, link, want)
+    del batch, want
+    for it in M["items"]:
+        it["out"] = None
+    M.clear()
+    torch.cuda.empty_cache()
     if rank != 0:
         return
-    for c in colls:
-        c["out"] = None
-    peak, peak_src = peaks()
-    lm = statistics.mean(launch_ms)
-    achieved = step_bytes / (lm * 1e-3) / 1e9
-    tr = traffic_record()
-    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": tr["bytes_per_launch"] if tr else None,
-            "kernel": "k_batch (persistent; %d conversions per launch)" % (3 * args.batch),
-            "algorithmic_bytes_per_launch": step_bytes, "launch_ms_mean": round(lm, 5),
-            "launch_ms_median": round(statistics.median(launch_ms), 5),
-            "launch_samples": "%d of %d timed launches bracketed by events" % (len(launch_ms), args.steps),
-            "peak_source": ("of measured (MEASURED_PEAKS.json hbm_gbs, copy read+write)" if peak_src == "measured"
-                            else "of fallback 6.4 TB/s")}
-    del colls
-    torch.cuda.empty_cache()
-    extra.update(secondary(mrn, torch, stream, peak))
-    if args.mixed_jobs > 0:
-        extra["batched_mixed"] = run_mixed(mrn, torch, stream, peak, args)
-    extra["sensor_grid"] = run_sensor_grid(mrn, torch, stream)
-    extra["collection_ops"] = run_collection_ops(mrn, torch, stream, peak)
-    extra["served"] = run_served(mrn, torch, args)
-    cpu_val, cpu_reps, cpu_s = cpu_oracle_rate(10.0, N_RECORDS)
-    cpu_all, cpu_cores = cpu_oracle_rate_all_cores(10.0, N_RECORDS)
+    if not args.no_extras:
+        extra["host_link_gbps"] = link
+        extra.update(secondary(mrn, torch, stream, peak, link))
+        extra["cells_batch_16x3"] = run_cells_batch(mrn, torch, stream, peak, args)
+        extra["sensor_grid"] = run_sensor_grid(mrn, torch, stream)
+        extra["collection_ops"] = run_collection_ops(mrn, torch, stream, peak)
+        extra["served"] = run_served(mrn, torch, args)
+    cpu_val, cpu_reps, cpu_s, cpu_what = cpu_oracle_rate(10.0)
+    cpu_all, cpu_cores = cpu_oracle_rate_all_cores(10.0)
     line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-            "data": "synthetic (seeded generator; distributions of the calorimeter-cell workload)",
-            "config": workload_config(args.batch),
-            "batch_launch": dict(launch_shape, chosen_by="mrn_batch_tune (chunk x CTAs per SM, timed on the batch)"),
-            "e2e": e2e,
-            "gpu_launches": args.steps,
-            "roofline": roof,
+            "data": "synthetic (seeded generators; distributions of the points / cells / tracks workloads)",
+            "config": workload_config(args.mixed_jobs, alg_step, records),
+            "e2e": e2e, "gpu_launches": 2 * args.steps, "roofline": roofline,
             "cpu_baseline": {"value": round(cpu_val, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": "3 conversions of one 200,000-record collection x %d (%.1f s)"
-                                       % (cpu_reps, cpu_s),
+                             "sample": "%s, converted %d times (%.1f s)" % (cpu_what, cpu_reps, cpu_s),
                              "all_cores": {"value": round(cpu_all, 3) if cpu_all else None, "unit": "GB/s",
                                            "cores": cpu_cores,
-                                           "sample": "one process per core, each the same 3 conversions of "
-                                                     "its own 200,000-record collection for 10 s, started "
-                                                     "together; aggregate"}},
-            "clocks": clocks}
+                                           "sample": "one process per core, each every 256th collection from "
+                                                     "its own offset, 10 s, started together; aggregate"}},
+            "clocks": T["clocks"]}
+    # the large extras first, the headline's own evidence last (the tail of
+    # a long line is what survives truncation)
+    for k in ("served", "collection_ops", "sensor_grid", "single_collection", "cells_batch_16x3"):
+        if k in extra:
+            line[k] = extra.pop(k)
     line.update(extra)
+    line["parity_sample"] = parity
     print(json.dumps(line), flush=True)
 
 
-def run_e2e(mrn, torch, s, colls, args, world, n_streams=2, chunk_bytes=0):
-    """Host pinned AoS -> device SoA, SoA -> AoSoA(32), device AoSoA(32) ->
-    host pinned AoS for every collection of the batch, per step."""
-    n = N_RECORDS
-    h_in = [c["aos"].cpu().pin_memory() for c in colls]
-    h_out = [torch.empty_like(h).pin_memory() for h in h_in]
-    d_soa = [torch.empty_like(c["soa"]) for c in colls]
-    d_blk = [torch.empty_like(c["blk"]) for c in colls]
-    views = []
-    for i in range(len(colls)):
-        views.append((mrn.View(s, "aos", n, base=h_in[i], mem="pinned"), mrn.View(s, "soa", n, base=d_soa[i]),
-                      mrn.View(s, "aosoa", n, block=BLOCK, base=d_blk[i]),
-                      mrn.View(s, "aos", n, base=h_out[i], mem="pinned")))
-
-    streams = [torch.cuda.Stream() for _ in range(n_streams)]
-    main = torch.cuda.current_stream()
-
-    def step():
-        # collection i on stream i % n_streams: collections' device -> host
-        # copies overlap later ones' host -> device copies (each direction
-        # has its own copy pipeline; a stream only orders its own
-        # collections)
-        for st in streams:
-            st.wait_stream(main)
-        for i, (hin, soa, blk, hout) in enumerate(views):
-            st = streams[i % len(streams)]
-            mrn.transfer_convert(hin, soa, chunk_bytes=chunk_bytes, stream=st)
-            mrn.convert(soa, blk, stream=st)
-            mrn.transfer_convert(blk, hout, chunk_bytes=chunk_bytes, stream=st)
-        for st in streams:
-            main.wait_stream(st)
-
-    for _ in range(2):
-        step()
-    torch.cuda.synchronize()
-    for i in range(len(colls)):
-        assert torch.equal(h_out[i], h_in[i]), "end-to-end round trip differs"
-    k = max(3, min(20, args.steps // 100))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(k):
-        step()
-    torch.cuda.synchronize()
-    el = (time.perf_counter() - t0) / k
-    assert mrn.sync() == mrn.OK
-    step_bytes = len(colls) * bytes_per_collection()
-    return {"value": round(world * step_bytes / el / 1e9, 2), "unit": "GB/s",
-            "h2d_bytes_per_step": len(colls) * n * 24, "d2h_bytes_per_step": len(colls) * n * 24,
-            "ms_per_step": round(el * 1e3, 3), "steps": k,
-            "path": "mrn_transfer_convert (default 4 MiB chunks, 4 slots) + mrn_convert, pinned host buffers, "
-                    "collection i on stream i %% %d" % n_streams}
+def host_link(torch, stream):
+    """Pinned host <-> device copies of 1 GiB (best of 5) and both
+    directions at once: the bound of every transfer path."""
+    h = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
+    dbuf = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    best_h2d = best_d2h = 1e9
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dbuf.copy_(h, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        best_h2d = min(best_h2d, a.elapsed_time(b))
+        a.record(stream)
+        h.copy_(dbuf, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        best_d2h = min(best_d2h, a.elapsed_time(b))
+    h2 = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
+    dbuf2 = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    best_bi = 1e9
+    for _ in range(5):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s1):
+            dbuf.copy_(h, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h2.copy_(dbuf2, non_blocking=True)
+        torch.cuda.synchronize()
+        best_bi = min(best_bi, time.perf_counter() - t0)
+    out = {"h2d": round((1 << 30) / (best_h2d * 1e-3) / 1e9, 1),
+           "d2h": round((1 << 30) / (best_d2h * 1e-3) / 1e9, 1),
+           "both_directions_total": round(2 * (1 << 30) / best_bi / 1e9, 1)}
+    del h, h2, dbuf, dbuf2
+    torch.cuda.empty_cache()
+    return out
 
 
-def secondary(mrn, torch, stream, peak):
+def secondary(mrn, torch, stream, peak, link):
     """Single-collection launches at the workload sizes and scale-up
     collections (2^26 records), L2 flushed before each launch, against the
-    HBM roofline; the host link bandwidth."""
-    import numpy as np
+    HBM roofline (small collections also back to back); the transfer chunk
+    sweep and the zero-copy ablation against the host link."""
     import datagen
     out = {}
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
@@ -694,18 +785,35 @@ def secondary(mrn, torch, stream, peak):
                 ts.append(a.elapsed_time(b))
         return statistics.median(ts), sorted(ts)[:max(1, len(ts) // 5)]
 
-    def row(alg, med, fastest):
-        return {"us_median": round(med * 1e3, 2), "gbps": round(alg / (med * 1e-3) / 1e9, 1),
-                "frac_of_hbm": round(alg / (med * 1e-3) / 1e9 / peak, 3),
-                "gbps_mean_fastest_fifth": round(alg / (statistics.mean(fastest) * 1e-3) / 1e9, 1)}
+    def back_to_back(src, dst, reps=50):
+        mrn.convert(src, dst)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            mrn.convert(src, dst)
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / reps
 
+    def row(alg, med, fastest, b2b=None):
+        r = {"us_median": round(med * 1e3, 2), "gbps": round(alg / (med * 1e-3) / 1e9, 1),
+             "frac_of_hbm": round(alg / (med * 1e-3) / 1e9 / peak, 3),
+             "gbps_mean_fastest_fifth": round(alg / (statistics.mean(fastest) * 1e-3) / 1e9, 1),
+             "algorithmic_bytes": alg}
+        if b2b is not None:
+            r["us_back_to_back"] = round(b2b * 1e3, 2)
+        return r
+
+    packed = {"points": 25, "cells": 24}
     rows = {}
     for name, n, pairs in [("points", 10000, [("aos", 0, "soa", 0), ("soa", 0, "aos", 0)]),
                            ("cells", 200000, [("aos", 0, "soa", 0), ("soa", 0, "aosoa", 32),
                                               ("aosoa", 32, "aos", 0)]),
                            ("cells", 1 << 26, [("aos", 0, "soa", 0), ("soa", 0, "aos", 0),
                                                ("soa", 0, "aosoa", 32), ("aosoa", 32, "aos", 0)]),
-                           ("points", 1 << 26, [("aos", 0, "soa", 0), ("soa", 0, "aos", 0)])]:
+                           ("points", 1 << 26, [("aos", 0, "soa", 0), ("soa", 0, "aos", 0),
+                                                ("aosoa", 32, "aos", 0)])]:
         s = mrn.Schema(datagen.WORKLOAD_SCHEMAS[name])
         bufs = {}
         for sk, sb, dk, db in pairs:
@@ -717,8 +825,9 @@ def secondary(mrn, torch, stream, peak):
             src = mrn.View(s, sk, n, block=sb, base=bufs[(sk, sb)])
             dst = mrn.View(s, dk, n, block=db, base=bufs[(dk, db)])
             med, fastest = time_conv(src, dst, 10 if n > 1e6 else 30)
+            b2b = back_to_back(src, dst) if n < 1e6 else None
             key = "%s_%d_%s%s_to_%s%s" % (name, n, sk, sb or "", dk, db or "")
-            rows[key] = row(2 * n * s.stride, med, fastest)
+            rows[key] = row(n * (s.stride + packed[name]), med, fastest, b2b)
         del bufs
     # jagged tracks, AoS -> SoA and back (canonical child pool)
     s = mrn.Schema(datagen.TRACKS)
@@ -727,16 +836,21 @@ def secondary(mrn, torch, stream, peak):
         soa = torch.empty(s.required_bytes("soa", n, m), dtype=torch.uint8, device="cuda")
         src = mrn.View(s, "aos", n, base=recs, child_pool=pool, m=m)
         dst = mrn.View(s, "soa", n, base=soa, m=m)
-        alg = n * 24 + m * 8 + n * 12 + (n + 1) * 4 + m * 8
+        alg = mixed_alg_bytes("tracks", n, m)
         med, fastest = time_conv(src, dst, 10)
-        rows["tracks_%d_aos_to_soa" % n] = dict(row(alg, med, fastest), children=m)
+        b2b = back_to_back(src, dst) if n < 1e6 else None
+        rows["tracks_%d_aos_to_soa" % n] = dict(row(alg, med, fastest, b2b), children=m)
         back = mrn.View(s, "aos", n, base=recs, child_pool=pool, m=m)
         med, fastest = time_conv(dst, back, 10)
-        rows["tracks_%d_soa_to_aos" % n] = row(alg, med, fastest)
+        b2b = back_to_back(dst, back) if n < 1e6 else None
+        rows["tracks_%d_soa_to_aos" % n] = row(alg, med, fastest, b2b)
         assert mrn.sync() == mrn.OK
         del recs, pool, soa
+    rows["bytes_rule"] = ("algorithmic bytes: points 32 + 25 B/record, cells 24 + 24 B/record, tracks "
+                          "40 + 16 x length B/parent (+4 B for the last offset)")
     out["single_collection"] = rows
     del flush
+    out["transfer_chunk_sweep"] = chunk_sweep(mrn, torch, stream, link)
     # transfer-and-convert: chunked staging against zero-copy (the kernel
     # reads / writes the pinned host buffer itself), source bytes per second
     s = mrn.Schema(datagen.CELLS)
@@ -760,43 +874,175 @@ def secondary(mrn, torch, stream, peak):
         assert mrn.sync() == mrn.OK
         del h_aos, d_soa
     out["transfer_chunked_vs_zero_copy"] = abl
-    # host link: pinned 1 GiB copies, best of 5
-    h = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
-    dbuf = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
-    best_h2d = best_d2h = 1e9
-    for _ in range(5):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        dbuf.copy_(h, non_blocking=True)
-        b.record(stream)
-        b.synchronize()
-        best_h2d = min(best_h2d, a.elapsed_time(b))
-        a.record(stream)
-        h.copy_(dbuf, non_blocking=True)
-        b.record(stream)
-        b.synchronize()
-        best_d2h = min(best_d2h, a.elapsed_time(b))
-    # both directions at once (two streams): the ceiling of a round trip
-    h2 = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
-    dbuf2 = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
-    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
-    best_bi = 1e9
-    for _ in range(5):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        with torch.cuda.stream(s1):
-            dbuf.copy_(h, non_blocking=True)
-        with torch.cuda.stream(s2):
-            h2.copy_(dbuf2, non_blocking=True)
-        torch.cuda.synchronize()
-        best_bi = min(best_bi, time.perf_counter() - t0)
-    out["host_link_gbps"] = {"h2d": round((1 << 30) / (best_h2d * 1e-3) / 1e9, 1),
-                             "d2h": round((1 << 30) / (best_d2h * 1e-3) / 1e9, 1),
-                             "both_directions_total": round(2 * (1 << 30) / best_bi / 1e9, 1)}
-    del h2, dbuf2
-    del h, dbuf
     torch.cuda.empty_cache()
     return out
+
+
+def chunk_sweep(mrn, torch, stream, link):
+    """Host pinned AoS <-> device SoA for the 200,000-record cell collection
+    (4.8 MB of source) at chunk sizes 64 KiB ... 16 MiB, against a plain
+    pinned copy of the same bytes timed the same way (the control) and the
+    1 GiB host link; source bytes per second, mean over 30 calls."""
+    import datagen
+    n = 200000
+    s = mrn.Schema(datagen.CELLS)
+    h_aos = torch.full((n * 24,), 0x3C, dtype=torch.uint8).pin_memory()
+    d_soa = torch.empty(s.required_bytes("soa", n), dtype=torch.uint8, device="cuda")
+    d_raw = torch.empty(n * 24, dtype=torch.uint8, device="cuda")
+    hv = mrn.View(s, "aos", n, base=h_aos, mem="pinned")
+    dv = mrn.View(s, "soa", n, base=d_soa)
+    reps = 30
+
+    def rate(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        return n * 24 / (a.elapsed_time(b) / reps * 1e-3) / 1e9
+
+    out = {"collection": "cells, 200,000 records, 4.8 MB AoS source", "unit": "GB/s of source bytes",
+           "control_pinned_copy": {"h2d": round(rate(lambda: d_raw.copy_(h_aos, non_blocking=True)), 1),
+                                   "d2h": round(rate(lambda: h_aos.copy_(d_raw, non_blocking=True)), 1)},
+           "points": []}
+    for k in range(9):
+        chunk = (64 << 10) << k
+        h2d = rate(lambda: mrn.transfer_convert(hv, dv, chunk_bytes=chunk, stream=stream))
+        d2h = rate(lambda: mrn.transfer_convert(dv, hv, chunk_bytes=chunk, stream=stream))
+        p = {"chunk_bytes": chunk, "h2d": round(h2d, 1), "d2h": round(d2h, 1),
+             "h2d_frac_of_control": round(h2d / out["control_pinned_copy"]["h2d"], 3),
+             "d2h_frac_of_control": round(d2h / out["control_pinned_copy"]["d2h"], 3)}
+        if link:
+            p["h2d_frac_of_link"] = round(h2d / link["h2d"], 3)
+            p["d2h_frac_of_link"] = round(d2h / link["d2h"], 3)
+        out["points"].append(p)
+    assert mrn.sync() == mrn.OK
+    del h_aos, d_soa, d_raw
+    return out
+
+
+def mem_available():
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    return int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def run_e2e_mixed(mrn, torch, M, world, link, want=None, steps=3, n_streams=2):
+    """The mixed batch end to end through the public API from pinned host
+    memory: per step, every collection host AoS -> device target with
+    mrn_transfer_convert (collection i on stream i % n_streams; each
+    direction has one copy pipeline per device), then mrn_sync reads the
+    device status word back.  All collections when three times their
+    source bytes fit in the host's available memory, else every k-th."""
+    items = M["items"]
+    need = [it["n"] * it["s"].stride + it["m"] * 8 for it in items]
+    avail = mem_available()
+    k = 1
+    while k < len(items) and 3 * sum(need[::k]) > avail:
+        k *= 2
+    pick = list(range(0, len(items), k))
+    total = sum(((need[i] + 255) // 256) * 256 for i in pick)
+    hbuf = torch.empty(max(1, total), dtype=torch.uint8, pin_memory=True)
+    views, pos = [], 0
+    for i in pick:
+        it = items[i]
+        nb = it["n"] * it["s"].stride
+        hb = hbuf[pos: pos + nb]
+        hb.copy_(it["rec"][:nb])
+        pos += (nb + 255) // 256 * 256
+        hp = None
+        if it["name"] == "tracks":
+            pb = hbuf[pos: pos + it["m"] * 8]
+            pb.copy_(it["pool"][: it["m"] * 8])
+            hp = pb
+            pos = (pos + it["m"] * 8 + 255) // 256 * 256
+        views.append((mrn.View(it["s"], "aos", it["n"], base=hb, child_pool=hp, m=it["m"], mem="pinned"),
+                      it["dst"]))
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream() for _ in range(n_streams)]
+    main = torch.cuda.current_stream()
+
+    def step():
+        for st in streams:
+            st.wait_stream(main)
+        for j, (hv, dv) in enumerate(views):
+            mrn.transfer_convert(hv, dv, stream=streams[j % n_streams])
+        for st in streams:
+            main.wait_stream(st)
+        return mrn.sync(main)
+
+    for i in pick:
+        items[i]["out"].fill_(0xA5)
+    assert step() == mrn.OK
+    if want is not None:
+        for i in pick:
+            assert torch.equal(items[i]["out"], want[i]), "end-to-end output of job %d differs" % i
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        assert step() == mrn.OK
+    el = (time.perf_counter() - t0) / steps
+    alg = sum(mixed_alg_bytes(items[i]["name"], items[i]["n"], items[i]["m"]) for i in pick)
+    bi = sum(need[i] for i in pick)
+    out = {"value": round(world * alg / el / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": bi,
+           "d2h_bytes_per_step": 4, "ms_per_step": round(el * 1e3, 2), "steps": steps,
+           "collections": len(pick), "collections_rule": "all" if k == 1 else "every %d-th (host memory)" % k,
+           "path": "mrn_transfer_convert host pinned AoS -> device target (4 MiB chunks, 4 slots; jagged: "
+                   "whole source staged), collection i on stream i %% %d, then mrn_sync (4-byte status read)"
+                   % n_streams,
+           "host_link_gbps": round(bi / el / 1e9, 2)}
+    if link:
+        out["host_link_frac"] = round(bi / el / 1e9 / link["h2d"], 3)
+        out["host_link_measured_h2d_gbps"] = link["h2d"]
+    del hbuf, views
+    return out
+
+
+def run_cells_batch(mrn, torch, stream, peak, args):
+    """The cell batch: 16 collections of 200,000 cells, each converted
+    AoS -> SoA, SoA -> AoSoA(32) and AoSoA(32) -> AoS, 48 conversions in one
+    graph replay, against one launch per conversion."""
+    import datagen
+    s = mrn.Schema(datagen.CELLS)
+    colls = make_inputs(mrn, torch, s, args.batch)
+    batch = mrn.Batch(pairs_for(mrn, s, colls), use_graph=True)
+    shape = batch.tune()
+    batch.launch()
+    assert mrn.sync() == mrn.OK
+    check_outputs(torch, colls)
+    step_bytes = args.batch * bytes_per_collection()
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        assert mrn.sync() == mrn.OK
+        return a.elapsed_time(b) / reps
+    ms = timed(batch.launch, 200)
+    check_outputs(torch, colls)
+    per = timed(batch.launch_per_job, 20)
+    check_outputs(torch, colls)
+    del batch, colls
+    torch.cuda.empty_cache()
+    return {"workload": cells_workload(args.batch), "algorithmic_bytes_per_launch": step_bytes,
+            "ms_per_launch_back_to_back": round(ms, 4), "gbps": round(step_bytes / (ms * 1e-3) / 1e9, 1),
+            "frac_of_hbm": round(step_bytes / (ms * 1e-3) / 1e9 / peak, 3),
+            "per_call_ms": round(per, 4), "speedup_vs_per_call": round(per / ms, 3),
+            "launch_shape": shape}
 
 
 def run_collection_ops(mrn, torch, stream, peak):
@@ -961,7 +1207,9 @@ def run_served(mrn, torch, args):
     log-uniform 10 KB - 256 MB, schemas points / cells / tracks, random
     source and target layouts, host->device or device->host, 64 GB budget.
     The saturation rate is measured first (a closed burst), then each
-    fraction of it is offered for up to 3 s / 1500 requests."""
+    fraction of it is offered for --serve-requests requests or
+    --serve-seconds seconds, whichever ends first.  Latency (submission ->
+    completion) is reported overall and per decade of request size."""
     import numpy as np
     import datagen
     rng = np.random.default_rng(4)
@@ -1038,15 +1286,20 @@ def run_served(mrn, torch, args):
     out["saturation"] = {"req_per_s": round(sat, 1), "source_gbps": round(total / el / 1e9, 2)}
     sv.close()
     rates = []
+
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, max(0, int(np.ceil(q * len(v))) - 1))] if v else None
+
     for frac in [float(x) for x in args.serve_rates.split(",") if x]:
         lam = frac * sat
         sv = mrn.Server(budget, max_slots=8, chunk_bytes=4 << 20)
-        nreq = int(min(1500, max(50, lam * 3.0)))
+        nreq = int(min(args.serve_requests, max(50, lam * args.serve_seconds)))
         arrivals = np.cumsum(rng.exponential(1.0 / lam, nreq))
         batch = [make_request() for _ in range(nreq)]
         tickets, late = [], 0.0
         t0 = time.perf_counter()
-        for (src, dst, _), ta in zip(batch, arrivals):
+        for (src, dst, nbytes), ta in zip(batch, arrivals):
             now = time.perf_counter() - t0
             if ta > now:
                 time.sleep(ta - now)
@@ -1054,19 +1307,27 @@ def run_served(mrn, torch, args):
                 late = max(late, now - ta)
             rc, t = sv.submit(src, dst)
             if rc == mrn.OK:
-                tickets.append(t)
-        for t in tickets:
-            assert sv.wait(t, 600.0) == mrn.OK
+                tickets.append((t, nbytes))
+        lat_by = {}
+        for t, nbytes in tickets:
+            st_, lat = sv.wait_latency(t, 600.0)
+            assert st_ == mrn.OK
+            dec = int(np.floor(np.log10(max(1, nbytes))))
+            lat_by.setdefault(dec, []).append(lat)
         el = time.perf_counter() - t0
         stt = sv.stats()
         sv.close()
+        decades = {"1e%d-1e%d B" % (d, d + 1): {"requests": len(v), "p50_ms": round(pct(v, 0.5), 3),
+                                               "p99_ms": round(pct(v, 0.99), 3)}
+                   for d, v in sorted(lat_by.items())}
         rates.append({"frac_of_saturation": frac, "offered_req_per_s": round(lam, 1), "requests": nreq,
+                      "offered_s": round(float(arrivals[-1]), 2),
                       "p50_ms": round(stt["p50_ms"], 3), "p99_ms": round(stt["p99_ms"], 3),
                       "max_ms": round(stt["max_ms"], 3),
                       "throughput_source_gbps": round(stt["bytes_in"] / el / 1e9, 2),
                       "completed": stt["completed"], "rejected": stt["rejected"],
                       "peak_device_bytes": stt["peak_device_bytes"],
-                      "client_max_lateness_ms": round(late * 1e3, 3)})
+                      "client_max_lateness_ms": round(late * 1e3, 3), "by_source_size": decades})
     out["rates"] = rates
     del pools, t_host, t_cols, t_offs, t_kids, t_dev_dst
     torch.cuda.empty_cache()
@@ -1162,11 +1423,6 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
-        return
-    if args.mixed_only:
-        import torch
-        import paper_2511_04853_b300 as mrn
-        print(json.dumps(run_mixed(mrn, torch, torch.cuda.current_stream(), peaks()[0], args)), flush=True)
         return
     if world > 1:
         import torch

@@ -401,6 +401,11 @@ int mrn_server_submit(mrn_server* sv, const mrn_view* src, const mrn_view* dst, 
 int mrn_server_poll(mrn_server* sv, uint64_t ticket, int* done, int* status);
 /* Blocks until the request finished or timeout_ns passed (MRN_ETIMEOUT). */
 int mrn_server_wait(mrn_server* sv, uint64_t ticket, uint64_t timeout_ns, int* status);
+/* As mrn_server_wait, and *latency_ms receives this request's latency
+ * (submission -> completion of its work, as the statistics count it), so
+ * that callers can split latency by request size or kind. */
+int mrn_server_wait_latency(mrn_server* sv, uint64_t ticket, uint64_t timeout_ns, int* status,
+                            double* latency_ms);
 int mrn_server_stats_get(mrn_server* sv, mrn_server_stats* out);
 /* Drains outstanding requests, stops the thread, frees device memory. */
 void mrn_server_destroy(mrn_server* sv);

@@ -98,6 +98,7 @@ struct Request {
   Clock::time_point arrival;
   int status = MRN_EBUSY;
   bool done = false;
+  double latency_ms = 0;  // arrival -> completion, set when done
   uint64_t arena_off = ~0ull;
 };
 
@@ -207,7 +208,8 @@ struct mrn_server {
     } else {
       failed++;
     }
-    lat_ms.push_back(std::chrono::duration<double, std::milli>(now - r->arrival).count());
+    r->latency_ms = std::chrono::duration<double, std::milli>(now - r->arrival).count();
+    lat_ms.push_back(r->latency_ms);
   }
 
   void loop() {
@@ -356,6 +358,21 @@ int mrn_server_wait(mrn_server* sv, uint64_t ticket, uint64_t timeout_ns, int* s
   if (!sv->cv_done.wait_for(lk, std::chrono::nanoseconds(timeout_ns), [r] { return r->done; }))
     return MRN_ETIMEOUT;
   *status = r->status;
+  sv->requests.erase(ticket);
+  return MRN_OK;
+}
+
+int mrn_server_wait_latency(mrn_server* sv, uint64_t ticket, uint64_t timeout_ns, int* status,
+                            double* latency_ms) {
+  if (!sv || !status || !latency_ms) return MRN_EINVAL;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->requests.find(ticket);
+  if (it == sv->requests.end()) return MRN_ENOTFOUND;
+  Request* r = it->second.get();
+  if (!sv->cv_done.wait_for(lk, std::chrono::nanoseconds(timeout_ns), [r] { return r->done; }))
+    return MRN_ETIMEOUT;
+  *status = r->status;
+  *latency_ms = r->latency_ms;
   sv->requests.erase(ticket);
   return MRN_OK;
 }

@@ -121,6 +121,8 @@ SIGNATURES = [
                                          ctypes.POINTER(u64)]),
     ("mrn_server_poll", ctypes.c_int, [vp, u64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("mrn_server_wait", ctypes.c_int, [vp, u64, u64, ctypes.POINTER(ctypes.c_int)]),
+    ("mrn_server_wait_latency", ctypes.c_int, [vp, u64, u64, ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(ctypes.c_double)]),
     ("mrn_server_stats_get", ctypes.c_int, [vp, ctypes.POINTER(ServerStats)]),
     ("mrn_server_destroy", None, [vp]),
     ("mrn_memmove", ctypes.c_int, [vp, vp, u64, ctypes.c_int, vp]),
@@ -452,6 +454,16 @@ class Server:
             self._live.pop(ticket, None)
             return st.value
         return rc
+
+    def wait_latency(self, ticket, timeout_s=60.0):
+        """Waits for the request; returns (status, latency in ms)."""
+        st, lat = ctypes.c_int(), ctypes.c_double()
+        rc = lib().mrn_server_wait_latency(self._h, ticket, int(timeout_s * 1e9), ctypes.byref(st),
+                                           ctypes.byref(lat))
+        if rc == OK:
+            self._live.pop(ticket, None)
+            return st.value, lat.value
+        return rc, None
 
     def stats(self):
         s = ServerStats()

@@ -199,3 +199,37 @@ def test_destroy_drains_outstanding_requests():
     want = oracle.convert(o, o_aos, "aosoa", 32).base
     for out in outs:
         assert np.array_equal(host(out, want.size), want)
+
+
+def test_wait_latency_reports_each_request():
+    """mrn_server_wait_latency returns the request's status and its latency
+    (positive, no larger than the largest latency in the statistics), and
+    the result equals the oracle."""
+    n = 20000
+    s, o = mrn.Schema(datagen.CELLS), oracle.Schema(datagen.CELLS)
+    d = datagen.workload("cells", n, 8)
+    o_aos = oracle.pack(o, d, "aos")
+    want = oracle.convert(o, o_aos, "aosoa", 32).base
+    src = pinned_from(o_aos.base)
+    sv = mrn.Server(256 << 20, max_slots=4)
+    try:
+        dsts, tickets = [], []
+        for _ in range(6):
+            dst = garbage(s.required_bytes("aosoa", n, 0, 32))
+            rc, t = sv.submit(mrn.View(s, "aos", n, base=src, mem="pinned"),
+                              mrn.View(s, "aosoa", n, block=32, base=dst))
+            assert rc == mrn.OK
+            dsts.append(dst)
+            tickets.append(t)
+        lats = []
+        for t in tickets:
+            st, lat = sv.wait_latency(t, 60.0)
+            assert st == mrn.OK and lat is not None and lat > 0
+            lats.append(lat)
+        stt = sv.stats()
+        assert max(lats) <= stt["max_ms"] + 1e-9
+        torch().cuda.synchronize()
+        for dst in dsts:
+            assert np.array_equal(host(dst, want.size), want)
+    finally:
+        sv.close()
