@@ -631,6 +631,9 @@ def run_mine(args, rank, world):
                                             "note": "includes the scratch-reset memset node before it",
                                             "traffic": (int(traffic_record("k_batch")["traffic_per_algorithmic_byte"]
                                                             * M["alg_plain"]) if traffic_record("k_batch") else None)}})
+    if rank == 0:
+        print("step: %.3f ms, %.1f GB/s; k_batch %.3f ms, k_batch_jag %.3f ms; parity %s" % (
+            ms_step, value, lb, lj, parity), file=sys.stderr, flush=True)
     if profiling:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
@@ -949,7 +952,10 @@ def run_e2e_mixed(mrn, torch, M, world, link, want=None, steps=3, n_streams=2):
     while k < len(items) and 3 * sum(need[::k]) > avail:
         k *= 2
     pick = list(range(0, len(items), k))
-    total = sum(((need[i] + 255) // 256) * 256 for i in pick)
+
+    def up(x):
+        return (x + 255) // 256 * 256
+    total = sum(up(items[i]["n"] * items[i]["s"].stride) + up(items[i]["m"] * 8) for i in pick)
     hbuf = torch.empty(max(1, total), dtype=torch.uint8, pin_memory=True)
     views, pos = [], 0
     for i in pick:
@@ -957,13 +963,13 @@ def run_e2e_mixed(mrn, torch, M, world, link, want=None, steps=3, n_streams=2):
         nb = it["n"] * it["s"].stride
         hb = hbuf[pos: pos + nb]
         hb.copy_(it["rec"][:nb])
-        pos += (nb + 255) // 256 * 256
+        pos += up(nb)
         hp = None
         if it["name"] == "tracks":
             pb = hbuf[pos: pos + it["m"] * 8]
             pb.copy_(it["pool"][: it["m"] * 8])
             hp = pb
-            pos = (pos + it["m"] * 8 + 255) // 256 * 256
+            pos += up(it["m"] * 8)
         views.append((mrn.View(it["s"], "aos", it["n"], base=hb, child_pool=hp, m=it["m"], mem="pinned"),
                       it["dst"]))
     torch.cuda.synchronize()
