@@ -4,7 +4,12 @@ A schema is a list of members. Each member is one of
 
 * ``(name, dtype, extent)``            a per-item property (extent 1) or a
                                        fixed-extent array property (Sec. V,
-                                       "per-item property", "array property")
+                                       "per-item property", "array property"),
+                                       stored field-major as E separate columns
+* ``(name, dtype, extent, "interleaved")``
+                                       an array property stored field-major as
+                                       one N x E array (the property's other
+                                       interface in Sec. V)
 * ``(name, "group", [members])``       a sub-group property (Sec. V)
 * ``(name, "jagged", offset_dtype, [members])``
                                        a jagged vector property (Sec. V); the

@@ -59,7 +59,9 @@ def lib():
                 ("orc_soa_region_start", u64, [vp, u64, u64, i32]),
                 ("orc_fm_region_start", u64, [vp, i32, u32, u64, u64, i32]),
                 ("orc_soa_bytes", u64, [vp, u64, u64]),
-                ("orc_base_bytes", u64, [vp, i32, u32, u64, u64])]:
+                ("orc_base_bytes", u64, [vp, i32, u32, u64, u64]),
+                ("orc_col_es", i32, [vp, i32]), ("orc_col_sub", i32, [vp, i32]),
+                ("orc_col_store", i32, [vp, i32]), ("orc_nstore", i32, [vp])]:
             f = getattr(L, name)
             f.restype, f.argtypes = rt, at
         L.orc_convert.restype = i32
@@ -80,6 +82,8 @@ def tokens(desc):
         elif m[1] == "jagged":
             ch = tokens(m[3])
             out += [4, _SIZES[m[2]], len(ch)] + ch
+        elif len(m) > 3 and m[3] == "interleaved":
+            out += [5, _SIZES[m[1]], int(m[2])]
         else:
             out += [1, _SIZES[m[1]], int(m[2])]
     return out
@@ -105,6 +109,10 @@ class Schema:
         self.ncols = L.orc_ncols(self._h)
         self.col_size = [L.orc_col_size(self._h, c) for c in range(self.ncols)]
         self.col_aos_off = [L.orc_col_aos_off(self._h, c) for c in range(self.ncols)]
+        self.col_es = [L.orc_col_es(self._h, c) for c in range(self.ncols)]
+        self.col_sub = [L.orc_col_sub(self._h, c) for c in range(self.ncols)]
+        self.col_store = [L.orc_col_store(self._h, c) for c in range(self.ncols)]
+        self.nstore = L.orc_nstore(self._h)
         self.stride = L.orc_stride(self._h)
         self.has_jagged = bool(L.orc_has_jagged(self._h))
         self.child = None
@@ -215,24 +223,44 @@ def convert(schema, src, kind, block=0, m=None):
     return dst
 
 
-def flat_columns(values):
-    """Per-flattened-column contiguous arrays from generator leaves
-    (an ``(n, E)`` array property becomes E columns)."""
+def flat_columns(values, interleaved=None):
+    """Per-flattened-column arrays from generator leaves (an ``(n, E)`` array
+    property becomes E columns).  A leaf marked interleaved stays one
+    row-major ``(n, E)`` array; its E column entries are byte views of it
+    starting at element k (so that column k's pointer is the array's plus
+    k * size), returned with the array that owns them."""
     cols = []
-    for v in values:
+    for i, v in enumerate(values):
         v = np.asarray(v)
         if v.ndim == 1:
             cols.append(np.ascontiguousarray(v).view(np.uint8))
+        elif interleaved and interleaved[i]:
+            whole = np.ascontiguousarray(v).view(np.uint8).reshape(-1)
+            z = v.dtype.itemsize
+            for k in range(v.shape[1]):
+                cols.append(whole[k * z:])
         else:
             for k in range(v.shape[1]):
                 cols.append(np.ascontiguousarray(v[:, k]).view(np.uint8))
     return cols
 
 
+def _interleaved_flags(desc):
+    out = []
+    for m in desc:
+        if m[1] == "group":
+            out += _interleaved_flags(m[2])
+        elif m[1] == "jagged":
+            continue
+        else:
+            out.append(len(m) > 3 and m[3] == "interleaved")
+    return out
+
+
 def values_side(schema, data):
     """The generator's values as a per-column SoA side."""
     n = data["n"]
-    cols = flat_columns(data["columns"])
+    cols = flat_columns(data["columns"], _interleaved_flags(schema.desc))
     if not cols:
         cols = None
     if not schema.has_jagged:
@@ -240,7 +268,8 @@ def values_side(schema, data):
     lengths = np.asarray(data["lengths"], dtype=np.uint64)
     offs = np.concatenate([[0], np.cumsum(lengths)]).astype(
         np.uint32 if schema.off_size == 4 else np.uint64)
-    kids = flat_columns(data["children"])
+    jm = [m for m in _flat_members(schema.desc) if m[1] == "jagged"][0]
+    kids = flat_columns(data["children"], _interleaved_flags(jm[3]))
     return Side(SOA, n, data["m"], cols=cols, offsets=offs.view(np.uint8),
                 child_cols=kids, base=np.zeros(1, np.uint8))
 

@@ -13,7 +13,10 @@
  *
  *  - Schema lowering.  Sub-group members are stored as if declared at the
  *    top level (Sec. V, sub-group property); an array property of extent E
- *    is E separate per-index columns (Sec. V, array property); a jagged
+ *    is E separate per-index columns (Sec. V, array property: "stored in
+ *    separate arrays"), or, declared interleaved, one field-major column of
+ *    E-element rows (the property's other interface, a single N x E array:
+ *    record i's element k at row i, position k); a jagged
  *    vector property keeps a prefix sum of the sizes as a global property
  *    and all values as one contiguous vector (Sec. V, jagged vector
  *    property).
@@ -27,10 +30,18 @@
  *    each) follow.
  *  - AoSoA(B) ("allocating memory in blocks of a given size", Sec. IV):
  *    each block is the C struct { T_0 c0[B]; T_1 c1[B]; ... } of the
- *    flattened columns; for a jagged schema the blocks are followed, in the
+ *    flattened columns (an interleaved array of extent E: T a[B][E]); for
+ *    a jagged schema the blocks are followed, in the
  *    same buffer, by the offsets column and the child columns (each region
  *    128-byte aligned, as in the single-block SoA).
  *  - Every destination byte that no property writes is 0.
+ *
+ * Field-major storage: every flattened column is stored on its own (its
+ * own SoA region, its own B-element array in an AoSoA block) except the
+ * columns of one interleaved array, which share one storage column whose
+ * element is the whole E-element row; column k of the array is then at
+ * byte k * size of each row, and consecutive records' elements are E * size
+ * bytes apart.
  *
  * Parity unpinned: the 128-byte SoA column alignment, the AoSoA in-block
  * arrangement, the regions of a jagged AoSoA side and the AoS jagged
@@ -54,6 +65,7 @@
 #define TK_GROUP 2
 #define TK_END 3
 #define TK_JAGGED 4
+#define TK_IFIELD 5 /* interleaved array property: size, extent */
 
 #define ORC_MAXCOLS 1024
 
@@ -61,6 +73,15 @@ typedef struct orc_schema {
   int ncols;
   uint32_t col_size[ORC_MAXCOLS];
   uint64_t col_aos_off[ORC_MAXCOLS];
+  /* field-major storage of each column: its storage column, its byte offset
+   * inside a storage element, and the bytes between consecutive records'
+   * elements (the storage element's size) */
+  int col_store[ORC_MAXCOLS];
+  uint32_t col_sub[ORC_MAXCOLS];
+  uint32_t col_es[ORC_MAXCOLS];
+  int nstore;
+  uint32_t store_es[ORC_MAXCOLS];   /* storage element bytes */
+  uint32_t store_align[ORC_MAXCOLS]; /* alignment of a storage element */
   uint64_t stride;
   uint64_t align;
   int has_jagged;
@@ -104,18 +125,27 @@ static int layout_members(orc_schema* s, const int32_t* tk, int ntk, int* pos,
       (*pos)++;
       closed = 1;
       break;
-    } else if (op == TK_FIELD) {
+    } else if (op == TK_FIELD || op == TK_IFIELD) {
       if (*pos + 2 >= ntk) return ORC_EINVAL;
       uint32_t size = (uint32_t)tk[*pos + 1];
       int32_t extent = tk[*pos + 2];
+      int inter = op == TK_IFIELD;
       *pos += 3;
       if (!(size == 1 || size == 2 || size == 4 || size == 8) || extent < 1)
         return ORC_EINVAL;
       uint64_t off = align_up(cur, size);
       for (int k = 0; k < extent; k++) {
-        if (s->ncols >= ORC_MAXCOLS) return ORC_EINVAL;
+        if (s->ncols >= ORC_MAXCOLS || s->nstore >= ORC_MAXCOLS) return ORC_EINVAL;
         s->col_size[s->ncols] = size;
         s->col_aos_off[s->ncols] = off + (uint64_t)k * size;
+        if (!inter || k == 0) {
+          s->store_es[s->nstore] = inter ? size * (uint32_t)extent : size;
+          s->store_align[s->nstore] = size;
+          s->nstore++;
+        }
+        s->col_store[s->ncols] = s->nstore - 1;
+        s->col_sub[s->ncols] = inter ? (uint32_t)k * size : 0;
+        s->col_es[s->ncols] = s->store_es[s->nstore - 1];
         s->ncols++;
       }
       cur = off + (uint64_t)extent * size;
@@ -202,53 +232,76 @@ const orc_schema* orc_child(const orc_schema* s) { return s->child; }
 
 /* ---- layout address rules ---- */
 
-/* AoSoA(B): start of column c inside a block (C struct of B-element arrays). */
-uint64_t orc_aosoa_col_start(const orc_schema* s, uint32_t B, int c) {
+/* AoSoA(B): start of storage column q inside a block (C struct of
+ * B-element arrays of storage elements). */
+static uint64_t aosoa_store_start(const orc_schema* s, uint32_t B, int q) {
   uint64_t end = 0, start = 0;
-  for (int k = 0; k <= c; k++) {
-    start = align_up(end, s->col_size[k]);
-    end = start + (uint64_t)B * s->col_size[k];
+  for (int k = 0; k <= q; k++) {
+    start = align_up(end, s->store_align[k]);
+    end = start + (uint64_t)B * s->store_es[k];
   }
   return start;
+}
+
+/* Start of column c's first element inside a block. */
+uint64_t orc_aosoa_col_start(const orc_schema* s, uint32_t B, int c) {
+  return aosoa_store_start(s, B, s->col_store[c]) + s->col_sub[c];
 }
 
 uint64_t orc_aosoa_block_bytes(const orc_schema* s, uint32_t B) {
   uint64_t end = 0, al = 1;
-  for (int k = 0; k < s->ncols; k++) {
-    end = align_up(end, s->col_size[k]) + (uint64_t)B * s->col_size[k];
-    if (s->col_size[k] > al) al = s->col_size[k];
+  for (int k = 0; k < s->nstore; k++) {
+    end = align_up(end, s->store_align[k]) + (uint64_t)B * s->store_es[k];
+    if (s->store_align[k] > al) al = s->store_align[k];
   }
   return align_up(end, al);
 }
 
-/* Single-block field-major sides.  SoA: region r of the block, in order:
- * the data columns 0..ncols-1, then (jagged) the offsets column, then the
- * child columns.  AoSoA(B) of a jagged schema: the parent blocks, then the
- * offsets column, then the child columns.  Each region starts at a
- * multiple of 128 bytes. */
-static int parent_regions(const orc_schema* s, int kind) { return kind == ORC_AOSOA ? 1 : s->ncols; }
+/* Single-block field-major sides.  SoA: region q of the block, in order:
+ * the data storage columns 0..nstore-1, then (jagged) the offsets column,
+ * then the child storage columns.  AoSoA(B) of a jagged schema: the parent
+ * blocks, then the offsets column, then the child storage columns.  Each
+ * region starts at a multiple of 128 bytes. */
+static int parent_regions(const orc_schema* s, int kind) { return kind == ORC_AOSOA ? 1 : s->nstore; }
 
-static uint64_t fm_region_bytes(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, int r) {
+static uint64_t fm_region_bytes(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, int q) {
   int P = parent_regions(s, kind);
-  if (r < P) {
+  if (q < P) {
     if (kind == ORC_AOSOA) return (B ? (n + B - 1) / B : 0) * orc_aosoa_block_bytes(s, B);
-    return n * s->col_size[r];
+    return n * s->store_es[q];
   }
-  if (r == P) return (n + 1) * s->off_size;
-  return m * s->child->col_size[r - P - 1];
+  if (q == P) return (n + 1) * s->off_size;
+  return m * s->child->store_es[q - P - 1];
 }
 
 static int fm_nregions(const orc_schema* s, int kind) {
-  return parent_regions(s, kind) + (s->has_jagged ? 1 + s->child->ncols : 0);
+  return parent_regions(s, kind) + (s->has_jagged ? 1 + s->child->nstore : 0);
 }
 
-uint64_t orc_fm_region_start(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, int r) {
+static uint64_t region_start(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, int q) {
   uint64_t start = 0, end = 0;
-  for (int k = 0; k <= r; k++) {
+  for (int k = 0; k <= q; k++) {
     start = align_up(end, 128);
     end = start + fm_region_bytes(s, kind, B, n, m, k);
   }
   return start;
+}
+
+/* Where item r of a single-block field-major side starts, r counted by
+ * columns: SoA: data column r (r < ncols), the offsets (r == ncols), child
+ * column r - ncols - 1; jagged AoSoA(B): the blocks (r == 0), the offsets
+ * (r == 1), child column r - 2.  A column of an interleaved array starts at
+ * its element inside the array's first row. */
+uint64_t orc_fm_region_start(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, int r) {
+  int P = parent_regions(s, kind);
+  int Pc = kind == ORC_AOSOA ? 1 : s->ncols; /* items before the offsets */
+  if (r < Pc) {
+    if (kind == ORC_AOSOA) return region_start(s, kind, B, n, m, 0);
+    return region_start(s, kind, B, n, m, s->col_store[r]) + s->col_sub[r];
+  }
+  if (r == Pc) return region_start(s, kind, B, n, m, P);
+  int cc = r - Pc - 1;
+  return region_start(s, kind, B, n, m, P + 1 + s->child->col_store[cc]) + s->child->col_sub[cc];
 }
 
 uint64_t orc_soa_region_start(const orc_schema* s, uint64_t n, uint64_t m, int r) {
@@ -257,7 +310,7 @@ uint64_t orc_soa_region_start(const orc_schema* s, uint64_t n, uint64_t m, int r
 
 static uint64_t fm_bytes(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m) {
   int nr = fm_nregions(s, kind);
-  uint64_t end = orc_fm_region_start(s, kind, B, n, m, nr - 1) + fm_region_bytes(s, kind, B, n, m, nr - 1);
+  uint64_t end = region_start(s, kind, B, n, m, nr - 1) + fm_region_bytes(s, kind, B, n, m, nr - 1);
   return align_up(end, 128);
 }
 
@@ -274,17 +327,25 @@ uint64_t orc_base_bytes(const orc_schema* s, int kind, uint32_t B, uint64_t n, u
   return 0;
 }
 
+int orc_col_es(const orc_schema* s, int c) { return (int)s->col_es[c]; }
+int orc_col_sub(const orc_schema* s, int c) { return (int)s->col_sub[c]; }
+int orc_col_store(const orc_schema* s, int c) { return s->col_store[c]; }
+int orc_nstore(const orc_schema* s) { return s->nstore; }
+
+/* Address of record i's element of column c (SoA per-column pointers: the
+ * pointer of each column, an interleaved array's columns pointing at their
+ * element of the first row). */
 static uint8_t* col_addr(const orc_schema* s, const orc_side* v, int c, uint64_t i) {
-  uint64_t sz = s->col_size[c];
+  uint64_t es = s->col_es[c];
   switch (v->kind) {
     case ORC_AOS:
       return v->base + i * s->stride + s->col_aos_off[c];
     case ORC_SOA:
-      if (v->cols) return v->cols[c] + i * sz;
-      return v->base + orc_soa_region_start(s, v->n, v->m, c) + i * sz;
+      if (v->cols) return v->cols[c] + i * es;
+      return v->base + orc_soa_region_start(s, v->n, v->m, c) + i * es;
     default:
       return v->base + (i / v->block) * orc_aosoa_block_bytes(s, v->block) +
-             orc_aosoa_col_start(s, v->block, c) + (i % v->block) * sz;
+             orc_aosoa_col_start(s, v->block, c) + (i % v->block) * es;
   }
 }
 
@@ -293,6 +354,7 @@ static uint8_t* offsets_ptr(const orc_schema* s, const orc_side* v) {
   return v->base + orc_fm_region_start(s, v->kind, v->block, v->n, v->m, parent_regions(s, v->kind));
 }
 
+/* Child column cc of a field-major side (element j at + j * es). */
 static uint8_t* child_col_ptr(const orc_schema* s, const orc_side* v, int cc) {
   if (v->child_cols) return v->child_cols[cc];
   return v->base + orc_fm_region_start(s, v->kind, v->block, v->n, v->m, parent_regions(s, v->kind) + 1 + cc);
@@ -315,11 +377,12 @@ static int valid_side(const orc_side* v) {
  * bytes"; data bytes are overwritten afterwards). */
 static void zero_side(const orc_schema* s, const orc_side* d) {
   if (d->kind == ORC_SOA && d->cols) {
-    for (int c = 0; c < s->ncols; c++) memset(d->cols[c], 0, d->n * s->col_size[c]);
+    for (int c = 0; c < s->ncols; c++)
+      if (s->col_sub[c] == 0) memset(d->cols[c], 0, d->n * s->col_es[c]);
     if (s->has_jagged) {
       memset(offsets_ptr(s, d), 0, (d->n + 1) * s->off_size);
       for (int cc = 0; cc < s->child->ncols; cc++)
-        memset(child_col_ptr(s, d, cc), 0, d->m * s->child->col_size[cc]);
+        if (s->child->col_sub[cc] == 0) memset(child_col_ptr(s, d, cc), 0, d->m * s->child->col_es[cc]);
     }
     return;
   }
@@ -328,7 +391,7 @@ static void zero_side(const orc_schema* s, const orc_side* d) {
     if (d->offsets) memset(d->offsets, 0, (d->n + 1) * s->off_size);
     if (d->child_cols)
       for (int cc = 0; cc < s->child->ncols; cc++)
-        memset(d->child_cols[cc], 0, d->m * s->child->col_size[cc]);
+        if (s->child->col_sub[cc] == 0) memset(d->child_cols[cc], 0, d->m * s->child->col_es[cc]);
   }
   if (d->kind == ORC_AOS && s->has_jagged && d->pool)
     memset(d->pool, 0, d->m * s->child->stride);
@@ -388,7 +451,8 @@ int orc_convert(const orc_schema* s, const orc_side* src, orc_side* dst, uint64_
      * their order; only the parents change layout. */
     memcpy(offsets_ptr(s, dst), offsets_ptr(s, src), (n + 1) * s->off_size);
     for (int cc = 0; cc < ch->ncols; cc++)
-      memcpy(child_col_ptr(s, dst, cc), child_col_ptr(s, src, cc), src->m * ch->col_size[cc]);
+      if (ch->col_sub[cc] == 0)
+        memcpy(child_col_ptr(s, dst, cc), child_col_ptr(s, src, cc), src->m * ch->col_es[cc]);
     if (m_out) *m_out = src->m;
     return ORC_OK;
   }
@@ -402,7 +466,7 @@ int orc_convert(const orc_schema* s, const orc_side* src, orc_side* dst, uint64_
       uint64_t beg = rd(rec + s->begin_off, 8);
       for (uint64_t k = 0; k < len; k++)
         for (int cc = 0; cc < ch->ncols; cc++)
-          memcpy(child_col_ptr(s, dst, cc) + (run + k) * ch->col_size[cc],
+          memcpy(child_col_ptr(s, dst, cc) + (run + k) * ch->col_es[cc],
                  src->pool + (beg + k) * ch->stride + ch->col_aos_off[cc], ch->col_size[cc]);
       run += len;
       wr(off + (i + 1) * s->off_size, run, s->off_size);
@@ -421,7 +485,7 @@ int orc_convert(const orc_schema* s, const orc_side* src, orc_side* dst, uint64_
     for (uint64_t j = 0; j < src->m; j++)
       for (int cc = 0; cc < ch->ncols; cc++)
         memcpy(dst->pool + j * ch->stride + ch->col_aos_off[cc],
-               child_col_ptr(s, src, cc) + j * ch->col_size[cc], ch->col_size[cc]);
+               child_col_ptr(s, src, cc) + j * ch->col_es[cc], ch->col_size[cc]);
     if (m_out) *m_out = src->m;
   }
   return ORC_OK;

@@ -93,3 +93,45 @@ def fill_block_column(blocks, c, col, n):
     full = np.zeros(fld.size, fld.dtype)
     full[:n] = np.asarray(col).view(fld.dtype)
     fld[...] = full.reshape(fld.shape)
+
+
+def leaf_kinds(desc):
+    """(dtype, extent, interleaved) of every data leaf, depth first."""
+    out = []
+    for m in desc:
+        if m[1] == "group":
+            out += leaf_kinds(m[2])
+        elif m[1] == "jagged":
+            continue
+        else:
+            out.append((m[1], m[2], len(m) > 3 and m[3] == "interleaved"))
+    return out
+
+
+def storage_block_dtype(desc, B):
+    """AoSoA block as a C struct with one member per field-major storage
+    column: a B-element array per separately stored column, and a B x E
+    array for an interleaved array property (record r's row r)."""
+    fields, k = [], 0
+    for dt, e, inter in leaf_kinds(desc):
+        if inter:
+            fields.append(("s%d" % k, NUMPY_TYPES[dt], (B, e)))
+            k += 1
+        else:
+            for _ in range(e):
+                fields.append(("s%d" % k, NUMPY_TYPES[dt], (B,)))
+                k += 1
+    return np.dtype(fields, align=True)
+
+
+def storage_values(desc, values):
+    """Each storage column's values as a C-contiguous array: one per
+    separately stored column, the (n, E) rows of an interleaved array."""
+    out = []
+    for (dt, e, inter), v in zip(leaf_kinds(desc), values):
+        v = np.asarray(v)
+        if inter or v.ndim == 1:
+            out.append(np.ascontiguousarray(v))
+        else:
+            out += [np.ascontiguousarray(v[:, k]) for k in range(e)]
+    return out

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "mrn_oracle.c")
 
 MUTANTS = {
-    "aosoa_no_align": ("start = align_up(end, s->col_size[k]);", "start = end;"),
+    "aosoa_no_align": ("start = align_up(end, s->store_align[k]);", "start = end;"),
     "begin_align_4": ("s->begin_off = align_up(cur, 8);", "s->begin_off = align_up(cur, 4);"),
     "group_not_aligned": ("uint64_t goff = align_up(cur, galign);", "uint64_t goff = cur;"),
     "no_tail_padding": ("*size_out = align_up(cur, al);", "*size_out = cur;"),
@@ -25,11 +25,17 @@ MUTANTS = {
     "soa_align_64": ("start = align_up(end, 128);", "start = align_up(end, 64);"),
     "child_wrong_column": ("src->pool + (beg + k) * ch->stride + ch->col_aos_off[cc]",
                            "src->pool + (beg + k) * ch->stride + ch->col_aos_off[0]"),
-    "aosoa_slot_swapped": ("(i % v->block) * sz;", "((v->block - 1 - i % v->block)) * sz;"),
-    "jagged_aosoa_regions_as_soa": ("static int parent_regions(const orc_schema* s, int kind) { return kind == ORC_AOSOA ? 1 : s->ncols; }",
-                                    "static int parent_regions(const orc_schema* s, int kind) { return s->ncols; }"),
-    "f2f_children_dropped": ("memcpy(child_col_ptr(s, dst, cc), child_col_ptr(s, src, cc), src->m * ch->col_size[cc]);",
+    "aosoa_slot_swapped": ("(i % v->block) * es;", "((v->block - 1 - i % v->block)) * es;"),
+    "jagged_aosoa_regions_as_soa": ("static int parent_regions(const orc_schema* s, int kind) { return kind == ORC_AOSOA ? 1 : s->nstore; }",
+                                    "static int parent_regions(const orc_schema* s, int kind) { return s->nstore; }"),
+    "f2f_children_dropped": ("memcpy(child_col_ptr(s, dst, cc), child_col_ptr(s, src, cc), src->m * ch->col_es[cc]);",
                              "(void)cc;"),
+    "interleaved_stride_as_size": ("s->col_es[s->ncols] = s->store_es[s->nstore - 1];",
+                                   "s->col_es[s->ncols] = size;"),
+    "interleaved_element_offset_dropped": ("s->col_sub[s->ncols] = inter ? (uint32_t)k * size : 0;",
+                                           "s->col_sub[s->ncols] = 0;"),
+    "interleaved_block_row_as_element": ("end = start + (uint64_t)B * s->store_es[k];",
+                                         "end = start + (uint64_t)B * s->store_align[k];"),
 }
 
 

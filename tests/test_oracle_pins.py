@@ -461,3 +461,178 @@ def test_collection_ops_identities(name, n):
             assert coff.tolist() == want.tolist()
     empty = oc.erase(d, 0, n)
     assert empty["n"] == 0 and (not s.has_jagged or empty["m"] == 0)
+
+
+# ------------------------------------------- interleaved array properties
+# An array property declared interleaved is stored field-major as ONE N x E
+# array (Sec. V, array property, its single-array interface): record i's
+# element k at row i, position k.  numpy's row-major subarray fields are
+# that array, and numpy's aligned structs with (B, E) members are the AoSoA
+# block; AoS is unchanged (the C array inside the record).
+
+from np_layout import leaf_kinds, storage_block_dtype, storage_values  # noqa: E402
+
+INTERLEAVED = [("id", "u32", 1), ("pos", "f32", 3, "interleaved"), ("flag", "u8", 1),
+               ("w", "u16", 4, "interleaved"), ("k", "u64", 2, "interleaved"),
+               ("c", "u8", 3, "interleaved"), ("plain", "u16", 2)]
+IL_SCHEMAS = {"mixed": INTERLEAVED,
+              "only": [("v", "f64", 3, "interleaved")],
+              "grouped": [("a", "u8", 1), ("g", "group", [("x", "u32", 3, "interleaved"), ("y", "u8", 1)]),
+                          ("b", "u16", 4, "interleaved")]}
+
+
+def _storage_first_cols(desc):
+    """Flattened index of the first column of every storage column."""
+    out, c = [], 0
+    for dt, e, inter in leaf_kinds(desc):
+        if inter:
+            out.append(c)
+            c += e
+        else:
+            for _ in range(e):
+                out.append(c)
+                c += 1
+    return out
+
+
+@pytest.mark.parametrize("name", list(IL_SCHEMAS))
+def test_interleaved_aos_is_the_c_array(name):
+    desc = IL_SCHEMAS[name]
+    s = oracle.Schema(desc)
+    dt = struct_dtype(desc)
+    assert s.stride == dt.itemsize
+    for n in (0, 1, 9, 300):
+        d = values_for(desc, n, 31)
+        aos = oracle.pack(s, d, "aos")
+        assert aos.base[: n * s.stride].tobytes() == aos_from_values(desc, d["columns"], n).tobytes()
+
+
+@pytest.mark.parametrize("name", list(IL_SCHEMAS))
+@pytest.mark.parametrize("n", [0, 1, 5, 129, 1000])
+def test_interleaved_soa_is_the_row_major_array(name, n):
+    desc = IL_SCHEMAS[name]
+    s = oracle.Schema(desc)
+    ref = aos_from_values(desc, values_for(desc, n, 7)["columns"], n)
+    raw = np.frombuffer(ref.tobytes(), np.uint8).copy() if n else np.zeros(1, np.uint8)
+    soa = oracle.convert(s, oracle.Side("aos", n, base=raw), "soa")
+    arrs = storage_values(desc, [get for get in _numpy_leaves(desc, ref)])
+    firsts = _storage_first_cols(desc)
+    assert s.nstore == len(arrs)
+    mask = np.ones(soa.base.size, bool)
+    for q, (c, a) in enumerate(zip(firsts, arrs)):
+        st = s.soa_region_start(n, 0, c)
+        nb = a.nbytes
+        assert st % 128 == 0
+        assert soa.base[st:st + nb].tobytes() == a.tobytes(), "storage column %d" % q
+        mask[st:st + nb] = False
+    assert not soa.base[mask].any()
+    # the other columns of an interleaved array start at their element
+    for c in range(s.ncols):
+        assert s.soa_region_start(n, 0, c) == s.soa_region_start(n, 0, firsts[s.col_store[c]]) + s.col_sub[c]
+
+
+def _numpy_leaves(desc, arr):
+    from np_layout import leaf_paths, get_leaf
+    return [np.asarray(get_leaf(arr, p)) for p, _, _ in leaf_paths(desc)]
+
+
+@pytest.mark.parametrize("name", list(IL_SCHEMAS))
+@pytest.mark.parametrize("B", [1, 3, 8, 32])
+@pytest.mark.parametrize("n", [0, 1, 31, 33, 300])
+def test_interleaved_aosoa_matches_numpy_block_struct(name, B, n):
+    desc = IL_SCHEMAS[name]
+    s = oracle.Schema(desc)
+    d = values_for(desc, n, 13)
+    bd = storage_block_dtype(desc, B)
+    assert s.aosoa_block_bytes(B) == bd.itemsize
+    out = oracle.pack(s, d, "aosoa", B)
+    nb = (n + B - 1) // B
+    ref = np.zeros(nb, bd)
+    for q, v in enumerate(storage_values(desc, d["columns"])):
+        fld = ref["s%d" % q]
+        full = np.zeros((nb * B,) + v.shape[1:], fld.dtype)
+        full[:n] = v.view(fld.dtype) if v.dtype != fld.dtype else v
+        fld[...] = full.reshape(fld.shape)
+    assert out.base[: ref.nbytes].tobytes() == ref.tobytes()
+
+
+@pytest.mark.parametrize("name", list(IL_SCHEMAS))
+@pytest.mark.parametrize("n", [0, 1, 100, 4097])
+def test_interleaved_round_trips(name, n):
+    desc = IL_SCHEMAS[name]
+    s = oracle.Schema(desc)
+    aos = oracle.pack(s, values_for(desc, n, 17), "aos")
+    soa = oracle.convert(s, aos, "soa")
+    assert oracle.convert(s, soa, "aos").base.tobytes() == aos.base.tobytes()
+    b = oracle.convert(s, oracle.convert(s, oracle.convert(s, aos, "aosoa", 32), "soa"), "aos")
+    assert b.base.tobytes() == aos.base.tobytes()
+    c = oracle.convert(s, oracle.convert(s, oracle.convert(s, soa, "aosoa", 32), "aosoa", 128), "soa")
+    assert c.base.tobytes() == soa.base.tobytes()
+
+
+def test_interleaved_special_cases():
+    # extent 1: interleaving changes nothing, in any layout
+    n = 50
+    a, b = [("v", "u32", 1), ("t", "u8", 1)], [("v", "u32", 1, "interleaved"), ("t", "u8", 1)]
+    sa, sb = oracle.Schema(a), oracle.Schema(b)
+    d = values_for(a, n, 3)
+    for kind, B in [("aos", 0), ("soa", 0), ("aosoa", 8)]:
+        assert oracle.pack(sa, d, kind, B).base.tobytes() == oracle.pack(sb, d, kind, B).base.tobytes()
+    # a single interleaved array of a record without padding: the SoA array
+    # is the AoS buffer itself
+    one = [("v", "u16", 5, "interleaved")]
+    so = oracle.Schema(one)
+    d = values_for(one, n, 4)
+    aos = oracle.pack(so, d, "aos")
+    soa = oracle.convert(so, aos, "soa")
+    assert soa.base[: n * 10].tobytes() == aos.base[: n * 10].tobytes()
+    # one block holding every record equals the single-block SoA of B records
+    B = 64
+    blk = oracle.convert(so, aos, "aosoa", B)
+    soa_b = oracle.convert(so, oracle.pack(so, values_for(one, B, 4), "aos"), "soa")
+    assert blk.base[: n * 10].tobytes() == soa_b.base[: n * 10].tobytes()
+    assert not blk.base[n * 10: B * 10].any()
+
+
+IL_FIELD_TYPES = [(dt, e, "interleaved") for dt in DTS for e in (2, 3)]
+
+
+def _small_interleaved_schemas():
+    rng = np.random.default_rng(5)
+    out = [[("f0",) + t] for t in IL_FIELD_TYPES]
+    pool = FIELD_TYPES + IL_FIELD_TYPES
+    for _ in range(60):
+        idx = rng.integers(0, len(pool), 3)
+        out.append([("f%d" % i,) + tuple(pool[j]) for i, j in enumerate(idx)])
+    return out
+
+
+@pytest.mark.parametrize("desc", _small_interleaved_schemas(), ids=lambda d: "-".join("%s%d%s" % (
+    m[1], m[2], "i" if len(m) > 3 else "") for m in d))
+def test_brute_force_interleaved_schemas(desc):
+    """Unique field bytes through SoA and AoSoA(B) and back: every storage
+    column equals numpy's (row-major rows for interleaved arrays), no byte
+    is lost, duplicated or misplaced, and the padding is zero."""
+    s = oracle.Schema(desc)
+    dt = struct_dtype(desc)
+    assert s.stride == dt.itemsize
+    for n in (0, 1, 2, 3, 7, 8, 9):
+        raw = _unique_bytes(s, n)
+        arr = np.frombuffer(raw[: n * s.stride].tobytes(), dt, count=n)
+        arrs = storage_values(desc, _numpy_leaves(desc, arr))
+        src = oracle.Side("aos", n, base=raw)
+        soa = oracle.convert(s, src, "soa")
+        for c, a in zip(_storage_first_cols(desc), arrs):
+            st = s.soa_region_start(n, 0, c)
+            assert soa.base[st:st + a.nbytes].tobytes() == a.tobytes()
+        assert oracle.convert(s, soa, "aos").base[: n * s.stride].tobytes() == raw[: n * s.stride].tobytes()
+        for B in (1, 2, 4, 8):
+            blk = oracle.convert(s, src, "aosoa", B)
+            bd = storage_block_dtype(desc, B)
+            nb = (n + B - 1) // B
+            blocks = np.frombuffer(blk.base[: nb * bd.itemsize].tobytes(), bd, count=nb)
+            for q, a in enumerate(arrs):
+                got = blocks["s%d" % q].reshape((nb * B,) + a.shape[1:])
+                assert got[:n].tobytes() == a.tobytes()
+                assert not got[n:].view(np.uint8).any()
+            assert oracle.convert(s, blk, "aos").base[: n * s.stride].tobytes() == raw[: n * s.stride].tobytes()
