@@ -76,6 +76,19 @@ int mrn_schema_create(mrn_schema** out);
  * array inside the AoS record.  `name` is copied (max 63 bytes). */
 int mrn_schema_add_field(mrn_schema* s, const char* name, int dtype, uint32_t extent);
 
+/* Appends an array property of `extent` elements stored interleaved: in
+ * SoA its E elements per record form ONE column of N rows of E elements
+ * (record i's element k at byte (i * extent + k) * size of the column), the
+ * array property's single-array interface (Sec. V); in an AoSoA(B) block
+ * the array is a B x extent member; the AoS record is the same as for
+ * mrn_schema_add_field.  The array still flattens to `extent` columns
+ * (mrn_schema_column reports fm_stride = extent * size); a per-column SoA
+ * view passes, for column k of the array, the address of element k of the
+ * first row.  extent * size <= 65535.  Conversions between any layouts run
+ * on the device (mrn_convert, batches); transfers, servers, collections and
+ * jagged child schemas with such a property return MRN_EUNSUPPORTED. */
+int mrn_schema_add_field_interleaved(mrn_schema* s, const char* name, int dtype, uint32_t extent);
+
 /* Opens / closes a sub-group property (Sec. V, "sub-group property"): its
  * members are stored as separate columns, as if declared at the top level;
  * in the AoS record the group is a nested struct (aligned to its widest
@@ -123,7 +136,9 @@ typedef struct mrn_column_info {
   uint32_t size;        /* element bytes: 1, 2, 4 or 8                       */
   uint32_t aos_offset;  /* byte offset inside the AoS record                 */
   int32_t dtype;        /* mrn_dtype                                         */
-  uint32_t reserved;
+  uint32_t fm_stride;   /* bytes between consecutive records' elements in
+                           SoA / AoSoA: size, or extent * size for a column
+                           of an interleaved array property                 */
   char name[128];       /* dotted path, "[k]" suffix for array elements      */
 } mrn_column_info;
 
@@ -191,7 +206,10 @@ int mrn_required_bytes(const mrn_schema* s, mrn_layout layout, uint64_t n, uint6
 /* Bytes of an AoS child pool of m child records. */
 int mrn_child_pool_bytes(const mrn_schema* s, uint64_t m, size_t* out);
 /* Start of region r inside a single-block SoA of n records / m children:
- * r < n_columns: data column r; r == n_columns: offsets; then child columns. */
+ * r < n_columns: data column r; r == n_columns: offsets; then child columns.
+ * Each stored column starts at a multiple of 128 bytes; the columns of an
+ * interleaved array share one stored N x extent array and column k of it
+ * starts at element k of its first row. */
 int mrn_soa_region_offset(const mrn_schema* s, uint64_t n, uint64_t m, uint32_t r, size_t* out);
 /* Start of region r inside view.base for either field-major layout: SoA as
  * mrn_soa_region_offset; jagged AoSoA(B): r == 0 the blocks, r == 1 the

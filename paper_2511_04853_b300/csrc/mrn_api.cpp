@@ -47,16 +47,16 @@ int fm_side(const mrn_schema* s, const mrn_view& v, bool child, SidePlan* sp) {
   sp->block_shift = MRN_NO_SHIFT;
   if (v.layout.kind == MRN_SOA || child) {
     void* const* cols = child ? v.child_columns : v.columns;
-    const uint32_t P = parent_regions(s, v.layout.kind);
     for (uint32_t c = 0; c < nc; ++c) {
       char* p;
       if (cols) {
         p = static_cast<char*>(cols[c]);
+        // the columns of an interleaved array are elements of one row
+        if (t->cols[c].sub && p != sp->col[c - 1] + t->cols[c - 1].size) return MRN_EINVAL;
       } else {
         if (!v.base) return MRN_EINVAL;
-        const uint32_t region = child ? P + 1 + c : c;
         p = static_cast<char*>(v.base) +
-            fm_region_start(s, v.layout.kind, v.layout.block, v.n_records, v.n_children, region);
+            fm_col_start(s, v.layout.kind, v.layout.block, v.n_records, v.n_children, child, c);
       }
       if (!p && (child ? v.n_children : v.n_records) > 0) return MRN_EINVAL;
       if (reinterpret_cast<uintptr_t>(p) % t->cols[c].size) return MRN_EALIGN;
@@ -90,7 +90,10 @@ void aos_entries(const mrn_schema* t, bool with_jag, ConvPlan* p) {
                    [](const ColPlan& a, const ColPlan& b) { return a.aos_off < b.aos_off; });
   p->naos = k;
   p->ncols = (uint32_t)t->cols.size();
-  for (uint32_t c = 0; c < t->cols.size(); ++c) p->fm_size[c] = (uint8_t)t->cols[c].size;
+  for (uint32_t c = 0; c < t->cols.size(); ++c) {
+    p->fm_size[c] = (uint8_t)t->cols[c].size;
+    p->fm_es[c] = (uint16_t)t->cols[c].es;
+  }
   p->stride = t->stride;
   p->aos_words = (t->stride + 3) / 4;
 }
@@ -155,9 +158,10 @@ int gap_plans(const mrn_schema* s, const mrn_view& dst, GapPlan g[2]) {
       }
     };
     for (uint32_t c = 0; c < s->cols.size(); ++c) {
+      if (s->cols[c].sub) continue;  // inside its interleaved array's rows
       const uint64_t st = aosoa_col_start(s, B, c);
       add(prev_end, st);
-      prev_end = st + (uint64_t)B * s->cols[c].size;
+      prev_end = st + (uint64_t)B * s->cols[c].es;
     }
     add(prev_end, aosoa_block_bytes(s, B));
     h.base = static_cast<char*>(dst.base);
@@ -365,6 +369,9 @@ void widen_into_padding(const mrn_schema* s, TileGeom* g) {
 void tile_geometry(const mrn_schema* s, ConvPlan* p, uint32_t stage_bytes) {
   TileGeom& g = p->tg;
   std::memset(&g, 0, sizeof(g));
+  // The staged tile keeps each field-major column contiguous; interleaved
+  // arrays go through the direct kernel.
+  if (s->interleaved) return;
   if (!side_stageable(s, p->src, false) || !side_stageable(s, p->dst, true)) return;
   if (s->stride >= (1u << 24)) return;
   uint64_t q = 32;

@@ -40,10 +40,12 @@ __device__ __forceinline__ T ldx(const T* p) {
   if constexpr (G) return __ldg(p); else return *p;
 }
 
-// Address of element i of field-major column c.
-__device__ __forceinline__ char* fm_addr(const SidePlan& sp, int c, uint32_t size, uint64_t i) {
+// Address of element i of field-major column c, whose consecutive
+// elements are `es` bytes apart (the element size, or E * size for a
+// column of an interleaved array).
+__device__ __forceinline__ char* fm_addr(const SidePlan& sp, int c, uint32_t es, uint64_t i) {
   char* col = sp.col[c];
-  if (sp.kind == K_SOA) return col + i * size;
+  if (sp.kind == K_SOA) return col + i * es;
   uint64_t blk, slot;
   if (sp.block_shift != MRN_NO_SHIFT) {
     blk = i >> sp.block_shift;
@@ -52,7 +54,7 @@ __device__ __forceinline__ char* fm_addr(const SidePlan& sp, int c, uint32_t siz
     blk = i / sp.block;
     slot = i - blk * sp.block;
   }
-  return col + blk * sp.block_bytes + slot * size;
+  return col + blk * sp.block_bytes + slot * es;
 }
 
 template <bool G = true>
@@ -198,7 +200,7 @@ __device__ __forceinline__ void aos_to_fm_lane(const ConvPlan& p, uint64_t r, bo
       const uint32_t lo = tw[wi * MRN_TW_PITCH + lane];
       if (cp.fm >= 0) {
         if (st_ok) {
-          char* d = fm_addr(p.dst, cp.fm, cp.size, r);
+          char* d = fm_addr(p.dst, cp.fm, p.fm_es[cp.fm], r);
           const uint32_t sh = (cp.aos_off & 3) * 8;
           switch (cp.size) {
             case 1: *reinterpret_cast<unsigned char*>(d) = (unsigned char)(lo >> sh); break;
@@ -237,7 +239,7 @@ __device__ __forceinline__ void fm_to_aos_lane(const ConvPlan& p, uint64_t r, bo
       const uint32_t wi = cp.aos_off / 4 - win;
       uint64_t v;
       if (cp.fm >= 0)
-        v = ok ? ld_elem(fm_addr(p.src, cp.fm, cp.size, r), cp.size) : 0;
+        v = ok ? ld_elem(fm_addr(p.src, cp.fm, p.fm_es[cp.fm], r), cp.size) : 0;
       else
         v = cp.fm == FM_JLEN ? (uint64_t)jlen : jbeg;
       uint32_t* t = tw + wi * MRN_TW_PITCH + lane;
@@ -286,7 +288,7 @@ __device__ __forceinline__ void fm_to_aos_lane_ilp(const ConvPlan& p, uint64_t r
           const ColPlan cp = p.aos_cols[c];
           if (cp.aos_off < wend) {
             if (cp.fm >= 0) {
-              if (ok) v[k] = ld_elem(fm_addr(p.src, cp.fm, cp.size, r), cp.size);
+              if (ok) v[k] = ld_elem(fm_addr(p.src, cp.fm, p.fm_es[cp.fm], r), cp.size);
             } else {
               v[k] = cp.fm == FM_JLEN ? (uint64_t)jlen : jbeg;
             }
@@ -324,9 +326,9 @@ __device__ __forceinline__ void fm_to_aos_lane_ilp(const ConvPlan& p, uint64_t r
 __device__ __forceinline__ void fm_to_fm_lane(const ConvPlan& p, uint64_t r, bool ld_ok, bool st_ok) {
   if (!st_ok) return;
   for (uint32_t c = 0; c < p.ncols; ++c) {
-    const uint32_t sz = p.fm_size[c];
-    const uint64_t v = ld_ok ? ld_elem(fm_addr(p.src, c, sz, r), sz) : 0;
-    st_elem(fm_addr(p.dst, c, sz, r), sz, v);
+    const uint32_t sz = p.fm_size[c], es = p.fm_es[c];
+    const uint64_t v = ld_ok ? ld_elem(fm_addr(p.src, c, es, r), sz) : 0;
+    st_elem(fm_addr(p.dst, c, es, r), sz, v);
   }
 }
 

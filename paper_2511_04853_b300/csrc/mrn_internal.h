@@ -13,12 +13,25 @@
 
 struct mrn_schema_node;
 
-// One flattened column of a compiled schema.
+// One flattened column of a compiled schema.  In field-major layouts a
+// column lives in a storage column: its own, or, for the columns of an
+// interleaved array property, the array's one storage column of E-element
+// rows (`sub` = byte offset of the column's element in a row, `es` = bytes
+// between consecutive records' elements, E * size).
 struct MrnColumn {
   uint32_t size;
   uint32_t aos_off;
   int32_t dtype;
   std::string name;
+  uint32_t es = 0;
+  uint32_t sub = 0;
+  uint32_t store = 0;
+};
+
+// One field-major storage column: element bytes and alignment.
+struct MrnStore {
+  uint32_t es;
+  uint32_t align;
 };
 
 struct mrn_schema {
@@ -28,6 +41,8 @@ struct mrn_schema {
   std::vector<mrn_schema_node*> open_groups;
   // ---- compiled state (valid once finalized)
   std::vector<MrnColumn> cols;
+  std::vector<MrnStore> stores;  // field-major storage columns
+  bool interleaved = false;      // some array property is stored interleaved
   uint32_t stride = 0;
   uint32_t align = 1;
   bool has_jagged = false;
@@ -45,6 +60,9 @@ uint32_t dtype_size(int dtype);
 // ---- layout rules (the library's own implementation)
 uint64_t aosoa_block_bytes(const mrn_schema* s, uint32_t B);
 uint64_t aosoa_col_start(const mrn_schema* s, uint32_t B, uint32_t c);
+// Start of column c (child: the jagged child's column c) inside a
+// single-block field-major view: its storage region plus its element offset.
+uint64_t fm_col_start(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, bool child, uint32_t c);
 uint64_t soa_region_start(const mrn_schema* s, uint64_t n, uint64_t m, uint32_t r);
 // Regions of a single-block field-major view of either kind (SoA: data
 // columns, offsets, child columns; jagged AoSoA(B): blocks, offsets, child

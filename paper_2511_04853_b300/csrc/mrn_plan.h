@@ -103,6 +103,7 @@ struct ConvPlan {
   uint64_t tune_key;   // (schema, layout pair) key of the launch-shape cache
   ColPlan aos_cols[MRN_MAX_COLS + 2];
   uint8_t fm_size[MRN_MAX_COLS];
+  uint16_t fm_es[MRN_MAX_COLS];  // field-major bytes between records' elements (size, or E * size interleaved)
   SidePlan src, dst;
   TileGeom tg;
 };

@@ -11,6 +11,7 @@ struct mrn_schema_node {
   std::string name;
   int dtype = 0;
   uint32_t extent = 1;
+  bool interleaved = false;  // FIELD: one field-major N x extent array
   int offset_dtype = 0;
   std::vector<std::unique_ptr<mrn_schema_node>> members;  // GROUP
   std::unique_ptr<mrn_schema> child;                      // JAGGED (finalized copy)
@@ -55,8 +56,13 @@ bool lay_out(const std::vector<std::unique_ptr<mrn_schema_node>>& members, const
         c.dtype = m->dtype;
         c.name = prefix + m->name;
         if (m->extent > 1) c.name += "[" + std::to_string(k) + "]";
+        if (!m->interleaved || k == 0) s->stores.push_back(MrnStore{m->interleaved ? sz * m->extent : sz, sz});
+        c.store = (uint32_t)s->stores.size() - 1;
+        c.es = s->stores.back().es;
+        c.sub = m->interleaved ? k * sz : 0;
         s->cols.push_back(c);
       }
+      if (m->interleaved && m->extent > 1) s->interleaved = true;
       cur = off + (uint64_t)m->extent * sz;
       al = std::max<uint64_t>(al, sz);
     } else if (m->kind == mrn_schema_node::GROUP) {
@@ -105,6 +111,8 @@ std::unique_ptr<mrn_schema> clone_schema(const mrn_schema& s) {
   for (const auto& r : s.roots) c->roots.push_back(clone_node(*r));
   c->finalized = s.finalized;
   c->cols = s.cols;
+  c->stores = s.stores;
+  c->interleaved = s.interleaved;
   c->stride = s.stride;
   c->align = s.align;
   c->has_jagged = s.has_jagged;
@@ -122,6 +130,7 @@ std::unique_ptr<mrn_schema_node> clone_node(const mrn_schema_node& n) {
   c->name = n.name;
   c->dtype = n.dtype;
   c->extent = n.extent;
+  c->interleaved = n.interleaved;
   c->offset_dtype = n.offset_dtype;
   for (const auto& m : n.members) c->members.push_back(clone_node(*m));
   if (n.child) c->child = clone_schema(*n.child);
@@ -136,39 +145,48 @@ bool valid_name(const char* name) { return name && std::strlen(name) < 64; }
 
 }  // namespace
 
-uint64_t aosoa_col_start(const mrn_schema* s, uint32_t B, uint32_t c) {
+namespace {
+// Start of storage column q inside an AoSoA(B) block: the C struct of the
+// storage columns' B-element arrays (an interleaved array: B rows of E).
+uint64_t aosoa_store_start(const mrn_schema* s, uint32_t B, uint32_t q) {
   uint64_t end = 0, start = 0;
-  for (uint32_t k = 0; k <= c; ++k) {
-    start = align_up(end, s->cols[k].size);
-    end = start + (uint64_t)B * s->cols[k].size;
+  for (uint32_t k = 0; k <= q; ++k) {
+    start = align_up(end, s->stores[k].align);
+    end = start + (uint64_t)B * s->stores[k].es;
   }
   return start;
+}
+}  // namespace
+
+uint64_t aosoa_col_start(const mrn_schema* s, uint32_t B, uint32_t c) {
+  return aosoa_store_start(s, B, s->cols[c].store) + s->cols[c].sub;
 }
 
 uint64_t aosoa_block_bytes(const mrn_schema* s, uint32_t B) {
   uint64_t end = 0, al = 1;
-  for (const auto& c : s->cols) {
-    end = align_up(end, c.size) + (uint64_t)B * c.size;
-    al = std::max<uint64_t>(al, c.size);
+  for (const auto& q : s->stores) {
+    end = align_up(end, q.align) + (uint64_t)B * q.es;
+    al = std::max<uint64_t>(al, q.align);
   }
   return align_up(end, al);
 }
 
-// Regions of a single-block field-major view: SoA: the data columns, then
-// (jagged) the offsets and the child columns; jagged AoSoA(B): the parent
-// blocks, then the offsets and the child columns.
+// Regions of a single-block field-major view: SoA: the data storage
+// columns, then (jagged) the offsets and the child storage columns; jagged
+// AoSoA(B): the parent blocks, then the offsets and the child storage
+// columns.
 uint32_t parent_regions(const mrn_schema* s, int kind) {
-  return kind == MRN_AOSOA ? 1u : (uint32_t)s->cols.size();
+  return kind == MRN_AOSOA ? 1u : (uint32_t)s->stores.size();
 }
 uint64_t fm_region_bytes(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint32_t r) {
   const uint32_t P = parent_regions(s, kind);
-  if (r < P) return kind == MRN_AOSOA ? (n + B - 1) / B * aosoa_block_bytes(s, B) : n * s->cols[r].size;
+  if (r < P) return kind == MRN_AOSOA ? (n + B - 1) / B * aosoa_block_bytes(s, B) : n * s->stores[r].es;
   if (r == P) return (n + 1) * s->off_size;
-  return m * s->child->cols[r - P - 1].size;
+  return m * s->child->stores[r - P - 1].es;
 }
 
 uint32_t fm_region_count(const mrn_schema* s, int kind) {
-  return parent_regions(s, kind) + (s->has_jagged ? 1 + (uint32_t)s->child->cols.size() : 0);
+  return parent_regions(s, kind) + (s->has_jagged ? 1 + (uint32_t)s->child->stores.size() : 0);
 }
 
 uint64_t fm_region_start(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint32_t r) {
@@ -179,6 +197,12 @@ uint64_t fm_region_start(const mrn_schema* s, int kind, uint32_t B, uint64_t n, 
 
 uint64_t soa_region_start(const mrn_schema* s, uint64_t n, uint64_t m, uint32_t r) {
   return fm_region_start(s, MRN_SOA, 0, n, m, r);
+}
+
+uint64_t fm_col_start(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, bool child, uint32_t c) {
+  if (!child) return fm_region_start(s, kind, B, n, m, s->cols[c].store) + s->cols[c].sub;
+  const MrnColumn& cc = s->child->cols[c];
+  return fm_region_start(s, kind, B, n, m, parent_regions(s, kind) + 1 + cc.store) + cc.sub;
 }
 
 uint64_t fm_total_bytes(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m) {
@@ -225,6 +249,20 @@ int mrn_schema_add_field(mrn_schema* s, const char* name, int dtype, uint32_t ex
   return MRN_OK;
 }
 
+int mrn_schema_add_field_interleaved(mrn_schema* s, const char* name, int dtype, uint32_t extent) {
+  if (!s || s->finalized || !valid_name(name) || dtype_size(dtype) == 0 || extent < 1 ||
+      (uint64_t)extent * dtype_size(dtype) > 65535)
+    return MRN_EINVAL;
+  auto n = std::make_unique<mrn_schema_node>();
+  n->kind = mrn_schema_node::FIELD;
+  n->name = name;
+  n->dtype = dtype;
+  n->extent = extent;
+  n->interleaved = true;
+  current_list(s)->push_back(std::move(n));
+  return MRN_OK;
+}
+
 int mrn_schema_begin_group(mrn_schema* s, const char* name) {
   if (!s || s->finalized || !valid_name(name) || s->open_groups.size() >= 32) return MRN_EINVAL;
   auto n = std::make_unique<mrn_schema_node>();
@@ -247,6 +285,7 @@ int mrn_schema_add_jagged(mrn_schema* s, const char* name, int offset_dtype, con
       child->cols.empty() || (offset_dtype != MRN_U32 && offset_dtype != MRN_U64) ||
       find_jagged(s->roots))
     return MRN_EINVAL;
+  if (child->interleaved) return MRN_EUNSUPPORTED;  // child columns are stored one by one
   auto n = std::make_unique<mrn_schema_node>();
   n->kind = mrn_schema_node::JAGGED;
   n->name = name;
@@ -259,6 +298,8 @@ int mrn_schema_add_jagged(mrn_schema* s, const char* name, int offset_dtype, con
 int mrn_schema_finalize(mrn_schema* s) {
   if (!s || s->finalized || !s->open_groups.empty()) return MRN_EINVAL;
   s->cols.clear();
+  s->stores.clear();
+  s->interleaved = false;
   s->has_jagged = false;
   uint64_t size = 0, al = 1;
   if (!lay_out(s->roots, "", s, &size, &al)) return MRN_EINVAL;
@@ -269,7 +310,7 @@ int mrn_schema_finalize(mrn_schema* s) {
   uint64_t h = 1469598103934665603ull;
   h = fnv(h, s->stride);
   h = fnv(h, s->cols.size());
-  for (const auto& c : s->cols) h = fnv(fnv(h, c.size), c.aos_off);
+  for (const auto& c : s->cols) h = fnv(fnv(fnv(fnv(h, c.size), c.aos_off), c.es), c.sub);
   if (s->has_jagged) {
     h = fnv(fnv(fnv(h, s->len_off), s->begin_off), s->off_size);
     h = fnv(h, s->child->hash);
@@ -304,6 +345,7 @@ int mrn_schema_column(const mrn_schema* s, int child, uint32_t c, mrn_column_inf
   std::memset(out, 0, sizeof(*out));
   out->size = t->cols[c].size;
   out->aos_offset = t->cols[c].aos_off;
+  out->fm_stride = t->cols[c].es;
   out->dtype = t->cols[c].dtype;
   std::strncpy(out->name, t->cols[c].name.c_str(), sizeof(out->name) - 1);
   return MRN_OK;
@@ -332,17 +374,27 @@ int mrn_child_pool_bytes(const mrn_schema* s, uint64_t m, size_t* out) {
 }
 
 int mrn_soa_region_offset(const mrn_schema* s, uint64_t n, uint64_t m, uint32_t r, size_t* out) {
-  if (!s || !s->finalized || !out || r >= fm_region_count(s, MRN_SOA)) return MRN_EINVAL;
-  *out = (size_t)soa_region_start(s, n, m, r);
+  if (!s || !s->finalized || !out) return MRN_EINVAL;
+  const uint32_t nc = (uint32_t)s->cols.size();
+  const uint32_t nk = s->has_jagged ? (uint32_t)s->child->cols.size() : 0;
+  if (r < nc)
+    *out = (size_t)fm_col_start(s, MRN_SOA, 0, n, m, false, r);
+  else if (s->has_jagged && r == nc)
+    *out = (size_t)fm_region_start(s, MRN_SOA, 0, n, m, parent_regions(s, MRN_SOA));
+  else if (s->has_jagged && r <= nc + nk)
+    *out = (size_t)fm_col_start(s, MRN_SOA, 0, n, m, true, r - nc - 1);
+  else
+    return MRN_EINVAL;
   return MRN_OK;
 }
 
 int mrn_region_offset(const mrn_schema* s, mrn_layout l, uint64_t n, uint64_t m, uint32_t r, size_t* out) {
   if (!s || !s->finalized || !out) return MRN_EINVAL;
   if (l.kind == MRN_SOA) return mrn_soa_region_offset(s, n, m, r, out);
-  if (l.kind != MRN_AOSOA || l.block < 1 || !s->has_jagged || r >= fm_region_count(s, MRN_AOSOA))
+  if (l.kind != MRN_AOSOA || l.block < 1 || !s->has_jagged || r >= 2 + s->child->cols.size())
     return MRN_EINVAL;
-  *out = (size_t)fm_region_start(s, MRN_AOSOA, l.block, n, m, r);
+  *out = (size_t)(r < 2 ? fm_region_start(s, MRN_AOSOA, l.block, n, m, r)
+                        : fm_col_start(s, MRN_AOSOA, l.block, n, m, true, r - 2));
   return MRN_OK;
 }
 

@@ -43,7 +43,7 @@ class SchemaInfo(ctypes.Structure):
 
 class ColumnInfo(ctypes.Structure):
     _fields_ = [("size", u32), ("aos_offset", u32), ("dtype", i32),
-                ("reserved", u32), ("name", ctypes.c_char * 128)]
+                ("fm_stride", u32), ("name", ctypes.c_char * 128)]
 
 
 class TransferOpts(ctypes.Structure):
@@ -85,6 +85,7 @@ SIGNATURES = [
     ("mrn_version", ctypes.c_int, []),
     ("mrn_schema_create", ctypes.c_int, [ctypes.POINTER(vp)]),
     ("mrn_schema_add_field", ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_int, u32]),
+    ("mrn_schema_add_field_interleaved", ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_int, u32]),
     ("mrn_schema_begin_group", ctypes.c_int, [vp, ctypes.c_char_p]),
     ("mrn_schema_end_group", ctypes.c_int, [vp]),
     ("mrn_schema_add_jagged", ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_int, vp]),
@@ -245,6 +246,8 @@ class Schema:
                 child = Schema(m[3])
                 self._children.append(child)
                 check(L.mrn_schema_add_jagged(self._h, name, DTYPES[m[2]], child._h))
+            elif len(m) > 3 and m[3] == "interleaved":
+                check(L.mrn_schema_add_field_interleaved(self._h, name, DTYPES[m[1]], int(m[2])), m[0])
             else:
                 check(L.mrn_schema_add_field(self._h, name, DTYPES[m[1]], int(m[2])), m[0])
 
@@ -252,7 +255,7 @@ class Schema:
         ci = ColumnInfo()
         check(lib().mrn_schema_column(self._h, 1 if child else 0, c, ctypes.byref(ci)))
         return {"size": ci.size, "aos_offset": ci.aos_offset, "dtype": ci.dtype,
-                "name": ci.name.decode()}
+                "fm_stride": ci.fm_stride, "name": ci.name.decode()}
 
     def required_bytes(self, kind, n, m=0, block=0):
         out = sz()

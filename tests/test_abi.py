@@ -48,8 +48,14 @@ def test_status_strings():
 NESTED = [("a", "u8", 1),
           ("g", "group", [("x", "f64", 1), ("y", "u8", 1), ("h", "group", [("p", "u16", 3)])]),
           ("b", "u8", 1), ("c", "u32", 2)]
+INTERLEAVED = [("id", "u32", 1), ("pos", "f32", 3, "interleaved"), ("flag", "u8", 1),
+               ("g", "group", [("w", "u16", 4, "interleaved"), ("k", "u64", 2, "interleaved")]),
+               ("c", "u8", 3, "interleaved"), ("plain", "u16", 2)]
+INTERLEAVED_JAGGED = [("pt", "f32", 1), ("cov", "f32", 3, "interleaved"),
+                      ("hits", "jagged", "u32", [("index", "u32", 1), ("weight", "f32", 1)])]
 ALL = {"points": datagen.POINTS, "cells": datagen.CELLS, "tracks": datagen.TRACKS,
-       "sensor": datagen.SENSOR, "particle": datagen.PARTICLE, "nested": NESTED}
+       "sensor": datagen.SENSOR, "particle": datagen.PARTICLE, "nested": NESTED,
+       "interleaved": INTERLEAVED, "interleaved_jagged": INTERLEAVED_JAGGED}
 
 
 @pytest.mark.parametrize("name", sorted(ALL))
@@ -59,6 +65,7 @@ def test_schema_compiler_matches_oracle(name):
     assert s.stride == o.stride
     assert [c["aos_offset"] for c in s.columns] == o.col_aos_off
     assert [c["size"] for c in s.columns] == o.col_size
+    assert [c["fm_stride"] for c in s.columns] == o.col_es
     assert s.has_jagged == o.has_jagged
     if s.has_jagged:
         assert s.info.jag_length_offset == o.len_off
@@ -72,12 +79,26 @@ def test_schema_compiler_matches_oracle(name):
         nreg = s.ncols + (1 + len(s.child_columns) if s.has_jagged else 0)
         for r in range(nreg):
             assert s.soa_region_offset(n, m, r) == o.soa_region_start(n, m, r)
-        if not s.has_jagged:
-            for B in (1, 3, 32, 128):
-                assert s.required_bytes("aosoa", n, m, B) == o.base_bytes("aosoa", B, n, m)
-                assert s.aosoa_block_bytes(B) == o.aosoa_block_bytes(B)
-                for c in range(s.ncols):
-                    assert s.aosoa_column_offset(B, c) == o.aosoa_col_start(B, c)
+        for B in (1, 3, 32, 128):
+            assert s.required_bytes("aosoa", n, m, B) == o.base_bytes("aosoa", B, n, m)
+            assert s.aosoa_block_bytes(B) == o.aosoa_block_bytes(B)
+            for c in range(s.ncols):
+                assert s.aosoa_column_offset(B, c) == o.aosoa_col_start(B, c)
+
+
+def test_interleaved_child_schema_is_refused():
+    child = mrn.Schema([("x", "f32", 3, "interleaved")])
+    L = mrn.lib()
+    h = ctypes.c_void_p()
+    assert L.mrn_schema_create(ctypes.byref(h)) == 0
+    assert L.mrn_schema_add_jagged(h, b"v", 4, child._h) == mrn.EUNSUPPORTED
+    L.mrn_schema_destroy(h)
+
+
+def test_interleaved_hash_differs_from_separate_columns():
+    a = mrn.Schema([("v", "u16", 4)])
+    b = mrn.Schema([("v", "u16", 4, "interleaved")])
+    assert a.hash != b.hash and a.stride == b.stride
 
 
 def test_column_names_follow_the_description():
