@@ -80,15 +80,24 @@ def workload(name, n, seed, raw=False, mean_len=20.0, max_len=256):
         cols, lengths, kids = _tracks(n, rng, mean_len, max_len)
         out = {"columns": cols, "n": n, "lengths": lengths,
                "children": kids, "m": int(lengths.sum(dtype=np.uint64))}
+    elif name == "tracks_nested":
+        cols, lengths, kids = _tracks(n, rng, mean_len, max_len)
+        m = int(lengths.sum(dtype=np.uint64))
+        l1 = np.minimum(rng.poisson(3.0, m), 32).astype(np.uint32)
+        m2 = int(l1.sum(dtype=np.uint64))
+        t = rng.integers(0, 65536, m2, dtype=np.uint16)
+        adc = rng.integers(0, 4096, m2, dtype=np.uint16)
+        out = {"columns": cols, "n": n, "lengths": lengths, "children": kids, "m": m,
+               "child_lengths": l1, "grandchildren": [t, adc], "m2": m2}
     else:
         raise ValueError(name)
     if raw:
         rr = np.random.default_rng(seed + 1_000_003)
         out["columns"] = [raw_bits(rr, _np_to_name(c.dtype), c.shape)
                           for c in out["columns"]]
-        if "children" in out:
-            out["children"] = [raw_bits(rr, _np_to_name(c.dtype), c.shape)
-                               for c in out["children"]]
+        for key in ("children", "grandchildren"):
+            if key in out:
+                out[key] = [raw_bits(rr, _np_to_name(c.dtype), c.shape) for c in out[key]]
     return out
 
 
@@ -101,8 +110,15 @@ def jagged_random(schema, n, seed, mean_len=3.0, max_len=16):
     lengths = np.minimum(rng.poisson(mean_len, n), max_len).astype(np.uint32)
     m = int(lengths.sum(dtype=np.uint64))
     kids = [raw_bits(rng, dt, _leaf_shape(m, e)) for _, dt, e in leaves(child)]
-    return {"columns": cols, "n": n, "lengths": lengths, "children": kids,
-            "m": m}
+    out = {"columns": cols, "n": n, "lengths": lengths, "children": kids, "m": m}
+    if jagged_member(child) is not None:
+        # a nested jagged member: lengths per child, then the grandchildren
+        _, _, grand = jagged_member(child)
+        l1 = np.minimum(rng.poisson(mean_len, m), max_len).astype(np.uint32)
+        m2 = int(l1.sum(dtype=np.uint64))
+        out.update(child_lengths=l1, m2=m2,
+                   grandchildren=[raw_bits(rng, dt, _leaf_shape(m2, e)) for _, dt, e in leaves(grand)])
+    return out
 
 
 def pool_permutation(m, seed):

@@ -56,6 +56,15 @@ TRACKS = [
     ("hits", "jagged", "u32", [("index", "u32", 1), ("weight", "f32", 1)]),
 ]
 
+# Jagged with a nested jagged member: every hit of a track holds a list of
+# {time, adc} samples (Poisson(3) per hit, clipped at 32), uint32 prefix
+# sums at both levels.
+TRACKS_NESTED = [
+    ("pt", "f32", 1), ("eta", "f32", 1), ("label", "i32", 1),
+    ("hits", "jagged", "u32", [("index", "u32", 1), ("weight", "f32", 1),
+                                ("samples", "jagged", "u32", [("t", "u16", 1), ("adc", "u16", 1)])]),
+]
+
 # The motivating example's Sensor (Listing 1 / Listing 3): an enum stored in
 # one byte, a sub-group of calibration constants.
 SENSOR = [
@@ -82,6 +91,7 @@ PARTICLE = [
 ]
 
 WORKLOAD_SCHEMAS = {"points": POINTS, "cells": CELLS, "tracks": TRACKS}
+NESTED_SCHEMAS = {"tracks_nested": TRACKS_NESTED}
 
 
 def leaves(schema, prefix=""):

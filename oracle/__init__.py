@@ -32,7 +32,9 @@ class _Side(ctypes.Structure):
                 ("base", ctypes.c_void_p), ("cols", ctypes.c_void_p),
                 ("offsets", ctypes.c_void_p), ("child_cols", ctypes.c_void_p),
                 ("pool", ctypes.c_void_p), ("n", ctypes.c_uint64),
-                ("m", ctypes.c_uint64)]
+                ("m", ctypes.c_uint64), ("gpool", ctypes.c_void_p),
+                ("m2", ctypes.c_uint64), ("child_offsets", ctypes.c_void_p),
+                ("gchild_cols", ctypes.c_void_p)]
 
 
 def lib():
@@ -56,10 +58,10 @@ def lib():
                 ("orc_child", vp, [vp]),
                 ("orc_aosoa_col_start", u64, [vp, u32, i32]),
                 ("orc_aosoa_block_bytes", u64, [vp, u32]),
-                ("orc_soa_region_start", u64, [vp, u64, u64, i32]),
-                ("orc_fm_region_start", u64, [vp, i32, u32, u64, u64, i32]),
-                ("orc_soa_bytes", u64, [vp, u64, u64]),
-                ("orc_base_bytes", u64, [vp, i32, u32, u64, u64]),
+                ("orc_soa_region_start", u64, [vp, u64, u64, u64, i32]),
+                ("orc_fm_region_start", u64, [vp, i32, u32, u64, u64, u64, i32]),
+                ("orc_soa_bytes", u64, [vp, u64, u64, u64]),
+                ("orc_base_bytes", u64, [vp, i32, u32, u64, u64, u64]),
                 ("orc_col_es", i32, [vp, i32]), ("orc_col_sub", i32, [vp, i32]),
                 ("orc_col_store", i32, [vp, i32]), ("orc_nstore", i32, [vp])]:
             f = getattr(L, name)
@@ -135,17 +137,17 @@ class Schema:
     def aosoa_block_bytes(self, B):
         return lib().orc_aosoa_block_bytes(self._h, B)
 
-    def soa_region_start(self, n, m, r):
-        return lib().orc_soa_region_start(self._h, n, m, r)
+    def soa_region_start(self, n, m, r, m2=0):
+        return lib().orc_soa_region_start(self._h, n, m, m2, r)
 
-    def fm_region_start(self, kind, block, n, m, r):
-        """Start of region r of a single-block field-major side (SoA: data
-        columns, offsets, child columns; jagged AoSoA(B): blocks, offsets,
-        child columns)."""
-        return lib().orc_fm_region_start(self._h, KIND.get(kind, kind), block, n, m, r)
+    def fm_region_start(self, kind, block, n, m, r, m2=0):
+        """Start of item r of a single-block field-major side (SoA: data
+        columns, offsets, then the child level's items; jagged AoSoA(B):
+        blocks, offsets, then the child level's items)."""
+        return lib().orc_fm_region_start(self._h, KIND.get(kind, kind), block, n, m, m2, r)
 
-    def base_bytes(self, kind, block, n, m=0):
-        return lib().orc_base_bytes(self._h, KIND.get(kind, kind), block, n, m)
+    def base_bytes(self, kind, block, n, m=0, m2=0):
+        return lib().orc_base_bytes(self._h, KIND.get(kind, kind), block, n, m, m2)
 
 
 def _flat_members(desc):
@@ -172,30 +174,36 @@ class Side:
     """One side of a conversion: numpy buffers in a layout."""
 
     def __init__(self, kind, n, m=0, block=0, base=None, cols=None,
-                 offsets=None, child_cols=None, pool=None):
+                 offsets=None, child_cols=None, pool=None, gpool=None, m2=0,
+                 child_offsets=None, gchild_cols=None):
         self.kind = KIND.get(kind, kind)
-        self.block, self.n, self.m = block, n, m
+        self.block, self.n, self.m, self.m2 = block, n, m, m2
         self.base, self.cols, self.offsets = base, cols, offsets
-        self.child_cols, self.pool = child_cols, pool
+        self.child_cols, self.pool, self.gpool = child_cols, pool, gpool
+        self.child_offsets, self.gchild_cols = child_offsets, gchild_cols
 
     def _c(self):
         keep = []
         cols, k1 = _ptr_array(self.cols)
         ccols, k2 = _ptr_array(self.child_cols)
-        keep += [k1, k2]
+        gcols, k3 = _ptr_array(self.gchild_cols)
+        keep += [k1, k2, k3]
         s = _Side(self.kind, self.block, _ptr(self.base), cols,
-                  _ptr(self.offsets), ccols, _ptr(self.pool), self.n, self.m)
+                  _ptr(self.offsets), ccols, _ptr(self.pool), self.n, self.m,
+                  _ptr(self.gpool), self.m2, _ptr(self.child_offsets), gcols)
         return s, keep
 
 
-def alloc(schema, kind, n, m=0, block=0):
+def alloc(schema, kind, n, m=0, block=0, m2=0):
     """A zero-filled destination side in single-buffer form."""
     kind = KIND.get(kind, kind)
-    base = np.zeros(max(1, schema.base_bytes(kind, block, n, m)), np.uint8)
-    pool = None
+    base = np.zeros(max(1, schema.base_bytes(kind, block, n, m, m2)), np.uint8)
+    pool = gpool = None
     if kind == AOS and schema.has_jagged:
         pool = np.zeros(max(1, m * schema.child.stride), np.uint8)
-    return Side(kind, n, m, block, base=base, pool=pool)
+        if schema.child.has_jagged:
+            gpool = np.zeros(max(1, m2 * schema.child.child.stride), np.uint8)
+    return Side(kind, n, m, block, base=base, pool=pool, gpool=gpool, m2=m2)
 
 
 def convert_into(schema, src, dst):
@@ -209,13 +217,16 @@ def convert_into(schema, src, dst):
     return st, mo.value
 
 
-def convert(schema, src, kind, block=0, m=None):
+def convert(schema, src, kind, block=0, m=None, m2=None):
     """Converts ``src`` into a freshly allocated side of ``kind``.  For a
     jagged schema ``m`` is the destination's child capacity (default: the
-    source's child count); the number written is left in ``.written``."""
+    source's child count), ``m2`` its grandchild capacity for a nested
+    member; the number of children written is left in ``.written``."""
     if m is None:
         m = src.m
-    dst = alloc(schema, kind, src.n, m, block)
+    if m2 is None:
+        m2 = src.m2
+    dst = alloc(schema, kind, src.n, m, block, m2)
     st, mo = convert_into(schema, src, dst)
     if st != OK:
         raise ValueError("oracle conversion failed with status %d" % st)
@@ -270,8 +281,18 @@ def values_side(schema, data):
         np.uint32 if schema.off_size == 4 else np.uint64)
     jm = [m for m in _flat_members(schema.desc) if m[1] == "jagged"][0]
     kids = flat_columns(data["children"], _interleaved_flags(jm[3]))
+    if not schema.child.has_jagged:
+        return Side(SOA, n, data["m"], cols=cols, offsets=offs.view(np.uint8),
+                    child_cols=kids, base=np.zeros(1, np.uint8))
+    # nested: the children's own lengths and the grandchild values
+    l1 = np.asarray(data["child_lengths"], dtype=np.uint64)
+    offs1 = np.concatenate([[0], np.cumsum(l1)]).astype(
+        np.uint32 if schema.child.off_size == 4 else np.uint64)
+    gm = [m for m in _flat_members(jm[3]) if m[1] == "jagged"][0]
+    grand = flat_columns(data["grandchildren"], _interleaved_flags(gm[3]))
     return Side(SOA, n, data["m"], cols=cols, offsets=offs.view(np.uint8),
-                child_cols=kids, base=np.zeros(1, np.uint8))
+                child_cols=kids, base=np.zeros(1, np.uint8), m2=data["m2"],
+                child_offsets=offs1.view(np.uint8), gchild_cols=grand)
 
 
 def pack(schema, data, kind, block=0, pool_perm=None):
@@ -280,7 +301,7 @@ def pack(schema, data, kind, block=0, pool_perm=None):
     reorders the parents' runs in the child pool and rewrites each
     parent's ``begin``."""
     src = values_side(schema, data)
-    out = convert(schema, src, kind, block, m=src.m)
+    out = convert(schema, src, kind, block, m=src.m, m2=src.m2)
     if pool_perm is not None and schema.has_jagged and out.kind == AOS:
         out = shuffle_pool(schema, out, pool_perm)
     return out

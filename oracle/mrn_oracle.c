@@ -34,6 +34,13 @@
  *    a jagged schema the blocks are followed, in the
  *    same buffer, by the offsets column and the child columns (each region
  *    128-byte aligned, as in the single-block SoA).
+ *  - A jagged member may nest once: its child records may hold a jagged
+ *    member of their own (Sec. V: the children are themselves a collection
+ *    described by properties).  AoS: the children's {length, begin} index a
+ *    second pool of grandchild records.  Field-major: the child level is
+ *    laid out as a single-block SoA of the child schema (child columns, the
+ *    children's offsets, m + 1 entries, the grandchild columns), after the
+ *    parents' offsets.
  *  - Every destination byte that no property writes is 0.
  *
  * Field-major storage: every flattened column is stored on its own (its
@@ -101,6 +108,10 @@ typedef struct orc_side {
   uint8_t* pool;        /* AoS child-record pool */
   uint64_t n;           /* records */
   uint64_t m;           /* children (capacity when destination) */
+  uint8_t* gpool;       /* nested jagged, AoS: the children's own child pool */
+  uint64_t m2;          /* nested jagged: grandchildren (capacity when destination) */
+  uint8_t* child_offsets; /* nested jagged, SoA: the children's offsets, or NULL (inside base) */
+  uint8_t** gchild_cols;  /* nested jagged, SoA: grandchild columns, or NULL (inside base) */
 } orc_side;
 
 static uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
@@ -113,8 +124,11 @@ static void free_schema(orc_schema* s) {
 
 /* Lays out members until TK_END (nested) or the end of the tokens.
  * Column offsets are written relative to the start of this (sub)struct. */
+/* `level` is 0 for the collection's own records, 1 for a jagged member's
+ * children, 2 for the children's children (a jagged member nests at most
+ * once). */
 static int layout_members(orc_schema* s, const int32_t* tk, int ntk, int* pos,
-                          int nested, int in_child, uint64_t* size_out,
+                          int nested, int level, uint64_t* size_out,
                           uint64_t* align_out) {
   uint64_t cur = 0, al = 1;
   int closed = 0;
@@ -155,7 +169,7 @@ static int layout_members(orc_schema* s, const int32_t* tk, int ntk, int* pos,
       int first = s->ncols;
       int had_jag = s->has_jagged;
       uint64_t gsize, galign;
-      int rc = layout_members(s, tk, ntk, pos, 1, in_child, &gsize, &galign);
+      int rc = layout_members(s, tk, ntk, pos, 1, level, &gsize, &galign);
       if (rc) return rc;
       uint64_t goff = align_up(cur, galign);
       for (int c = first; c < s->ncols; c++) s->col_aos_off[c] += goff;
@@ -166,7 +180,7 @@ static int layout_members(orc_schema* s, const int32_t* tk, int ntk, int* pos,
       cur = goff + gsize;
       if (galign > al) al = galign;
     } else if (op == TK_JAGGED) {
-      if (*pos + 2 >= ntk || s->has_jagged || in_child) return ORC_EINVAL;
+      if (*pos + 2 >= ntk || s->has_jagged || level >= 2) return ORC_EINVAL;
       uint32_t osz = (uint32_t)tk[*pos + 1];
       int nchild = tk[*pos + 2];
       *pos += 3;
@@ -176,7 +190,7 @@ static int layout_members(orc_schema* s, const int32_t* tk, int ntk, int* pos,
       if (!ch) return ORC_EINVAL;
       int cpos = 0;
       uint64_t csize, calign;
-      int rc = layout_members(ch, tk + *pos, nchild, &cpos, 0, 1, &csize, &calign);
+      int rc = layout_members(ch, tk + *pos, nchild, &cpos, 0, level + 1, &csize, &calign);
       if (rc || ch->ncols == 0) {
         free_schema(ch);
         return ORC_EINVAL;
@@ -259,69 +273,87 @@ uint64_t orc_aosoa_block_bytes(const orc_schema* s, uint32_t B) {
 
 /* Single-block field-major sides.  SoA: region q of the block, in order:
  * the data storage columns 0..nstore-1, then (jagged) the offsets column,
- * then the child storage columns.  AoSoA(B) of a jagged schema: the parent
- * blocks, then the offsets column, then the child storage columns.  Each
- * region starts at a multiple of 128 bytes. */
+ * then the child level as a single-block SoA of the child schema (its data
+ * storage columns, and for a nested jagged member its own offsets and the
+ * grandchildren's storage columns).  AoSoA(B) of a jagged schema: the
+ * parent blocks, then the offsets column, then the child level.  Each
+ * region starts at a multiple of 128 bytes.  Counts: n records, m
+ * children, m2 grandchildren. */
 static int parent_regions(const orc_schema* s, int kind) { return kind == ORC_AOSOA ? 1 : s->nstore; }
 
-static uint64_t fm_region_bytes(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, int q) {
+static uint64_t fm_region_bytes(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint64_t m2,
+                                int q) {
   int P = parent_regions(s, kind);
   if (q < P) {
     if (kind == ORC_AOSOA) return (B ? (n + B - 1) / B : 0) * orc_aosoa_block_bytes(s, B);
     return n * s->store_es[q];
   }
   if (q == P) return (n + 1) * s->off_size;
-  return m * s->child->store_es[q - P - 1];
+  return fm_region_bytes(s->child, ORC_SOA, 0, m, m2, 0, q - P - 1);
 }
 
 static int fm_nregions(const orc_schema* s, int kind) {
-  return parent_regions(s, kind) + (s->has_jagged ? 1 + s->child->nstore : 0);
+  return parent_regions(s, kind) + (s->has_jagged ? 1 + fm_nregions(s->child, ORC_SOA) : 0);
 }
 
-static uint64_t region_start(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, int q) {
+static uint64_t region_start(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint64_t m2,
+                             int q) {
   uint64_t start = 0, end = 0;
   for (int k = 0; k <= q; k++) {
     start = align_up(end, 128);
-    end = start + fm_region_bytes(s, kind, B, n, m, k);
+    end = start + fm_region_bytes(s, kind, B, n, m, m2, k);
   }
   return start;
 }
 
-/* Where item r of a single-block field-major side starts, r counted by
- * columns: SoA: data column r (r < ncols), the offsets (r == ncols), child
- * column r - ncols - 1; jagged AoSoA(B): the blocks (r == 0), the offsets
- * (r == 1), child column r - 2.  A column of an interleaved array starts at
- * its element inside the array's first row. */
-uint64_t orc_fm_region_start(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, int r) {
+/* Region and byte offset of item r of a single-block field-major side, r
+ * counted by columns: SoA: data column r (r < ncols), the offsets (r ==
+ * ncols), then item r - ncols - 1 of the child level counted the same way
+ * (child columns, its offsets, grandchild columns); jagged AoSoA(B): the
+ * blocks (r == 0), the offsets (r == 1), child-level item r - 2.  A column
+ * of an interleaved array starts at its element inside the first row. */
+static void item_region(const orc_schema* s, int kind, int r, int* q, uint64_t* sub) {
   int P = parent_regions(s, kind);
-  int Pc = kind == ORC_AOSOA ? 1 : s->ncols; /* items before the offsets */
+  int Pc = kind == ORC_AOSOA ? 1 : s->ncols;
   if (r < Pc) {
-    if (kind == ORC_AOSOA) return region_start(s, kind, B, n, m, 0);
-    return region_start(s, kind, B, n, m, s->col_store[r]) + s->col_sub[r];
+    *q = kind == ORC_AOSOA ? 0 : s->col_store[r];
+    *sub = kind == ORC_AOSOA ? 0 : s->col_sub[r];
+  } else if (r == Pc) {
+    *q = P;
+    *sub = 0;
+  } else {
+    item_region(s->child, ORC_SOA, r - Pc - 1, q, sub);
+    *q += P + 1;
   }
-  if (r == Pc) return region_start(s, kind, B, n, m, P);
-  int cc = r - Pc - 1;
-  return region_start(s, kind, B, n, m, P + 1 + s->child->col_store[cc]) + s->child->col_sub[cc];
 }
 
-uint64_t orc_soa_region_start(const orc_schema* s, uint64_t n, uint64_t m, int r) {
-  return orc_fm_region_start(s, ORC_SOA, 0, n, m, r);
+uint64_t orc_fm_region_start(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint64_t m2, int r) {
+  int q;
+  uint64_t sub;
+  item_region(s, kind, r, &q, &sub);
+  return region_start(s, kind, B, n, m, m2, q) + sub;
 }
 
-static uint64_t fm_bytes(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m) {
+uint64_t orc_soa_region_start(const orc_schema* s, uint64_t n, uint64_t m, uint64_t m2, int r) {
+  return orc_fm_region_start(s, ORC_SOA, 0, n, m, m2, r);
+}
+
+static uint64_t fm_bytes(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint64_t m2) {
   int nr = fm_nregions(s, kind);
-  uint64_t end = region_start(s, kind, B, n, m, nr - 1) + fm_region_bytes(s, kind, B, n, m, nr - 1);
+  uint64_t end = region_start(s, kind, B, n, m, m2, nr - 1) + fm_region_bytes(s, kind, B, n, m, m2, nr - 1);
   return align_up(end, 128);
 }
 
-uint64_t orc_soa_bytes(const orc_schema* s, uint64_t n, uint64_t m) { return fm_bytes(s, ORC_SOA, 0, n, m); }
+uint64_t orc_soa_bytes(const orc_schema* s, uint64_t n, uint64_t m, uint64_t m2) {
+  return fm_bytes(s, ORC_SOA, 0, n, m, m2);
+}
 
 /* Bytes of the `base` buffer of a side. */
-uint64_t orc_base_bytes(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m) {
+uint64_t orc_base_bytes(const orc_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint64_t m2) {
   if (kind == ORC_AOS) return n * s->stride;
-  if (kind == ORC_SOA) return orc_soa_bytes(s, n, m);
+  if (kind == ORC_SOA) return orc_soa_bytes(s, n, m, m2);
   if (kind == ORC_AOSOA) {
-    if (s->has_jagged) return fm_bytes(s, ORC_AOSOA, B, n, m);
+    if (s->has_jagged) return fm_bytes(s, ORC_AOSOA, B, n, m, m2);
     return (B ? (n + B - 1) / B : 0) * orc_aosoa_block_bytes(s, B);
   }
   return 0;
@@ -342,22 +374,39 @@ static uint8_t* col_addr(const orc_schema* s, const orc_side* v, int c, uint64_t
       return v->base + i * s->stride + s->col_aos_off[c];
     case ORC_SOA:
       if (v->cols) return v->cols[c] + i * es;
-      return v->base + orc_soa_region_start(s, v->n, v->m, c) + i * es;
+      return v->base + orc_soa_region_start(s, v->n, v->m, v->m2, c) + i * es;
     default:
       return v->base + (i / v->block) * orc_aosoa_block_bytes(s, v->block) +
              orc_aosoa_col_start(s, v->block, c) + (i % v->block) * es;
   }
 }
 
+/* Item index of the offsets of a field-major side (see item_region). */
+static int offsets_item(const orc_schema* s, int kind) { return kind == ORC_AOSOA ? 1 : s->ncols; }
+
 static uint8_t* offsets_ptr(const orc_schema* s, const orc_side* v) {
   if (v->offsets) return v->offsets;
-  return v->base + orc_fm_region_start(s, v->kind, v->block, v->n, v->m, parent_regions(s, v->kind));
+  return v->base + orc_fm_region_start(s, v->kind, v->block, v->n, v->m, v->m2, offsets_item(s, v->kind));
 }
 
 /* Child column cc of a field-major side (element j at + j * es). */
 static uint8_t* child_col_ptr(const orc_schema* s, const orc_side* v, int cc) {
   if (v->child_cols) return v->child_cols[cc];
-  return v->base + orc_fm_region_start(s, v->kind, v->block, v->n, v->m, parent_regions(s, v->kind) + 1 + cc);
+  return v->base + orc_fm_region_start(s, v->kind, v->block, v->n, v->m, v->m2, offsets_item(s, v->kind) + 1 + cc);
+}
+
+/* Nested jagged member of a field-major side (single block): the
+ * children's offsets (m + 1 entries) and grandchild column g. */
+static uint8_t* child_offsets_ptr(const orc_schema* s, const orc_side* v) {
+  if (v->child_offsets) return v->child_offsets;
+  return v->base + orc_fm_region_start(s, v->kind, v->block, v->n, v->m, v->m2,
+                                       offsets_item(s, v->kind) + 1 + s->child->ncols);
+}
+
+static uint8_t* gchild_col_ptr(const orc_schema* s, const orc_side* v, int g) {
+  if (v->gchild_cols) return v->gchild_cols[g];
+  return v->base + orc_fm_region_start(s, v->kind, v->block, v->n, v->m, v->m2,
+                                       offsets_item(s, v->kind) + 2 + s->child->ncols + g);
 }
 
 static uint64_t rd(const uint8_t* p, uint32_t size) {
@@ -383,18 +432,40 @@ static void zero_side(const orc_schema* s, const orc_side* d) {
       memset(offsets_ptr(s, d), 0, (d->n + 1) * s->off_size);
       for (int cc = 0; cc < s->child->ncols; cc++)
         if (s->child->col_sub[cc] == 0) memset(child_col_ptr(s, d, cc), 0, d->m * s->child->col_es[cc]);
+      if (s->child->has_jagged) {
+        const orc_schema* gc = s->child->child;
+        memset(child_offsets_ptr(s, d), 0, (d->m + 1) * s->child->off_size);
+        for (int g = 0; g < gc->ncols; g++)
+          if (gc->col_sub[g] == 0) memset(gchild_col_ptr(s, d, g), 0, d->m2 * gc->col_es[g]);
+      }
     }
     return;
   }
-  memset(d->base, 0, orc_base_bytes(s, d->kind, d->block, d->n, d->m));
+  memset(d->base, 0, orc_base_bytes(s, d->kind, d->block, d->n, d->m, d->m2));
   if (d->kind != ORC_AOS && s->has_jagged) {
     if (d->offsets) memset(d->offsets, 0, (d->n + 1) * s->off_size);
     if (d->child_cols)
       for (int cc = 0; cc < s->child->ncols; cc++)
         if (s->child->col_sub[cc] == 0) memset(d->child_cols[cc], 0, d->m * s->child->col_es[cc]);
+    if (s->child->has_jagged) {
+      const orc_schema* gc = s->child->child;
+      if (d->child_offsets) memset(d->child_offsets, 0, (d->m + 1) * s->child->off_size);
+      if (d->gchild_cols)
+        for (int g = 0; g < gc->ncols; g++)
+          if (gc->col_sub[g] == 0) memset(d->gchild_cols[g], 0, d->m2 * gc->col_es[g]);
+    }
   }
   if (d->kind == ORC_AOS && s->has_jagged && d->pool)
     memset(d->pool, 0, d->m * s->child->stride);
+  if (d->kind == ORC_AOS && s->has_jagged && s->child->has_jagged && d->gpool)
+    memset(d->gpool, 0, d->m2 * s->child->child->stride);
+}
+
+/* A nested jagged member (the children have a jagged member of their
+ * own): an AoS side needs the second pool when it has children. */
+static int nested_ok(const orc_schema* s, const orc_side* v) {
+  if (!s->has_jagged || !s->child->has_jagged || v->kind != ORC_AOS) return 1;
+  return v->m == 0 || (v->pool != NULL && (v->m2 == 0 || v->gpool != NULL));
 }
 
 /* Converts one collection from `src` to `dst` (same schema, same N).
@@ -403,6 +474,8 @@ static void zero_side(const orc_schema* s, const orc_side* d) {
  * receives the number of child values written. */
 int orc_convert(const orc_schema* s, const orc_side* src, orc_side* dst, uint64_t* m_out) {
   if (!valid_side(src) || !valid_side(dst) || src->n != dst->n) return ORC_EINVAL;
+  if (!nested_ok(s, src) || !nested_ok(s, dst)) return ORC_EINVAL;
+  const int nest = s->has_jagged && s->child->has_jagged;
   uint64_t n = src->n;
   if (m_out) *m_out = 0;
   if (s->has_jagged) {
@@ -425,6 +498,23 @@ int orc_convert(const orc_schema* s, const orc_side* src, orc_side* dst, uint64_
         total += len;
       }
       if (total > dst->m) return ORC_ESIZE;
+      if (nest) {
+        /* the same checks one level down, over the children reached */
+        const orc_schema* ch = s->child;
+        uint64_t total1 = 0, lim1 = ch->off_size == 4 ? 0xffffffffull : ~0ull;
+        for (uint64_t i = 0; i < n; i++) {
+          const uint8_t* rec = src->base + i * s->stride;
+          uint64_t len = rd(rec + s->len_off, 4), beg = rd(rec + s->begin_off, 8);
+          for (uint64_t k = 0; k < len; k++) {
+            const uint8_t* c = src->pool + (beg + k) * ch->stride;
+            uint64_t len1 = rd(c + ch->len_off, 4), beg1 = rd(c + ch->begin_off, 8);
+            if (beg1 > src->m2 || len1 > src->m2 - beg1) return ORC_EINVAL;
+            if (len1 > lim1 - total1) return ORC_EOVERFLOW;
+            total1 += len1;
+          }
+        }
+        if (total1 > dst->m2) return ORC_ESIZE;
+      }
     } else {
       const uint8_t* off = offsets_ptr(s, src);
       for (uint64_t i = 0; i < n; i++) {
@@ -434,6 +524,17 @@ int orc_convert(const orc_schema* s, const orc_side* src, orc_side* dst, uint64_
       }
       if (n > 0 && rd(off + n * s->off_size, s->off_size) > src->m) return ORC_EINVAL;
       if (dst->m < src->m) return ORC_ESIZE;
+      if (nest) {
+        const orc_schema* ch = s->child;
+        const uint8_t* off1 = child_offsets_ptr(s, src);
+        for (uint64_t j = 0; j < src->m; j++) {
+          uint64_t a = rd(off1 + j * ch->off_size, ch->off_size);
+          uint64_t b = rd(off1 + (j + 1) * ch->off_size, ch->off_size);
+          if (b < a || b - a > 0xffffffffull) return ORC_EINVAL;
+        }
+        if (src->m > 0 && rd(off1 + src->m * ch->off_size, ch->off_size) > src->m2) return ORC_EINVAL;
+        if (dst->m2 < src->m2) return ORC_ESIZE;
+      }
     }
   }
 
@@ -453,6 +554,12 @@ int orc_convert(const orc_schema* s, const orc_side* src, orc_side* dst, uint64_
     for (int cc = 0; cc < ch->ncols; cc++)
       if (ch->col_sub[cc] == 0)
         memcpy(child_col_ptr(s, dst, cc), child_col_ptr(s, src, cc), src->m * ch->col_es[cc]);
+    if (nest) {
+      const orc_schema* gc = ch->child;
+      memcpy(child_offsets_ptr(s, dst), child_offsets_ptr(s, src), (src->m + 1) * ch->off_size);
+      for (int g = 0; g < gc->ncols; g++)
+        if (gc->col_sub[g] == 0) memcpy(gchild_col_ptr(s, dst, g), gchild_col_ptr(s, src, g), src->m2 * gc->col_es[g]);
+    }
     if (m_out) *m_out = src->m;
     return ORC_OK;
   }
@@ -472,6 +579,31 @@ int orc_convert(const orc_schema* s, const orc_side* src, orc_side* dst, uint64_
       wr(off + (i + 1) * s->off_size, run, s->off_size);
     }
     if (m_out) *m_out = run;
+    if (nest) {
+      /* The children's own jagged member, one level down: child j (in
+       * parent order) gets offsets1[j+1] = offsets1[j] + its length, and its
+       * grandchildren are copied, property by property, after the previous
+       * child's. */
+      const orc_schema* gc = ch->child;
+      uint8_t* off1 = child_offsets_ptr(s, dst);
+      uint64_t j = 0, run1 = 0;
+      wr(off1, 0, ch->off_size);
+      for (uint64_t i = 0; i < n; i++) {
+        const uint8_t* rec = src->base + i * s->stride;
+        uint64_t len = rd(rec + s->len_off, 4), beg = rd(rec + s->begin_off, 8);
+        for (uint64_t k = 0; k < len; k++) {
+          const uint8_t* c = src->pool + (beg + k) * ch->stride;
+          uint64_t len1 = rd(c + ch->len_off, 4), beg1 = rd(c + ch->begin_off, 8);
+          for (uint64_t q = 0; q < len1; q++)
+            for (int g = 0; g < gc->ncols; g++)
+              memcpy(gchild_col_ptr(s, dst, g) + (run1 + q) * gc->col_es[g],
+                     src->gpool + (beg1 + q) * gc->stride + gc->col_aos_off[g], gc->col_size[g]);
+          run1 += len1;
+          j++;
+          wr(off1 + j * ch->off_size, run1, ch->off_size);
+        }
+      }
+    }
   } else {
     const uint8_t* off = offsets_ptr(s, src);
     for (uint64_t i = 0; i < n; i++) {
@@ -486,6 +618,23 @@ int orc_convert(const orc_schema* s, const orc_side* src, orc_side* dst, uint64_
       for (int cc = 0; cc < ch->ncols; cc++)
         memcpy(dst->pool + j * ch->stride + ch->col_aos_off[cc],
                child_col_ptr(s, src, cc) + j * ch->col_es[cc], ch->col_size[cc]);
+    if (nest) {
+      /* one level down: child j's {length, begin} from the children's
+       * offsets, the grandchildren contiguously into the second pool */
+      const orc_schema* gc = ch->child;
+      const uint8_t* off1 = child_offsets_ptr(s, src);
+      for (uint64_t j = 0; j < src->m; j++) {
+        uint8_t* c = dst->pool + j * ch->stride;
+        uint64_t a = rd(off1 + j * ch->off_size, ch->off_size);
+        uint64_t b = rd(off1 + (j + 1) * ch->off_size, ch->off_size);
+        wr(c + ch->len_off, b - a, 4);
+        wr(c + ch->begin_off, a, 8);
+      }
+      for (uint64_t k = 0; k < src->m2; k++)
+        for (int g = 0; g < gc->ncols; g++)
+          memcpy(dst->gpool + k * gc->stride + gc->col_aos_off[g],
+                 gchild_col_ptr(s, src, g) + k * gc->col_es[g], gc->col_size[g]);
+    }
     if (m_out) *m_out = src->m;
   }
   return ORC_OK;

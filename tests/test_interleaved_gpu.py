@@ -29,7 +29,7 @@ def check_pair(desc, n, sk, sb, dk, db, seed=1):
     s, o = mrn.Schema(desc), oracle.Schema(desc)
     d = datagen.random_columns(desc, n, seed)
     o_src = oracle.pack(o, d, sk, sb)
-    want = oracle.convert(o, o_src, dk, db).base
+    want = oracle.convert(o, o_src, dk, db).base[: s.required_bytes(dk, n, 0, db)]
     dst = dev_dest(s, dk, n, 0, db)
     mrn.convert(mrn.View(s, sk, n, block=sb, base=dev(o_src.base)), dst)
     assert mrn.sync() == mrn.OK

@@ -34,6 +34,14 @@ MUTANTS = {
                                    "s->col_es[s->ncols] = size;"),
     "interleaved_element_offset_dropped": ("s->col_sub[s->ncols] = inter ? (uint32_t)k * size : 0;",
                                            "s->col_sub[s->ncols] = 0;"),
+    "nested_offsets_not_summed": ("          run1 += len1;\n", "\n"),
+    "nested_grandchild_from_run_start": ("src->gpool + (beg1 + q) * gc->stride + gc->col_aos_off[g]",
+                                         "src->gpool + q * gc->stride + gc->col_aos_off[g]"),
+    "nested_grandchild_regions_dropped": ("return fm_region_bytes(s->child, ORC_SOA, 0, m, m2, 0, q - P - 1);",
+                                          "return fm_region_bytes(s->child, ORC_SOA, 0, m, 0, 0, q - P - 1);"),
+    "nested_begin_from_next_offset": ("        wr(c + ch->begin_off, a, 8);", "        wr(c + ch->begin_off, b, 8);"),
+    "jagged_offsets_item_as_storage_index": ("static int offsets_item(const orc_schema* s, int kind) { return kind == ORC_AOSOA ? 1 : s->ncols; }",
+                                             "static int offsets_item(const orc_schema* s, int kind) { return kind == ORC_AOSOA ? 1 : s->nstore; }"),
     "interleaved_block_row_as_element": ("end = start + (uint64_t)B * s->store_es[k];",
                                          "end = start + (uint64_t)B * s->store_align[k];"),
 }

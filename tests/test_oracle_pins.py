@@ -352,6 +352,9 @@ def test_jagged_aosoa_regions_and_round_trips(n, B):
                         base=np.zeros(1, np.uint8))
     p_blk = oracle.convert(parents, p_soa, "aosoa", B)
     assert oracle.region(s, blk, 0).tobytes() == p_blk.base[: parents.base_bytes("aosoa", B, n)].tobytes()
+    # the offsets follow the parents' blocks directly (the next multiple of
+    # 128 after the blocks of the parent-only schema)
+    assert s.fm_region_start("aosoa", B, n, d["m"], 1) == (parents.base_bytes("aosoa", B, n) + 127) // 128 * 128
     # offsets and children as on the SoA side
     for r in range(3):
         assert oracle.region(s, blk, 1 + r).tobytes() == oracle.region(s, soa, s.ncols + r).tobytes()
@@ -636,3 +639,236 @@ def test_brute_force_interleaved_schemas(desc):
                 assert got[:n].tobytes() == a.tobytes()
                 assert not got[n:].view(np.uint8).any()
             assert oracle.convert(s, blk, "aos").base[: n * s.stride].tobytes() == raw[: n * s.stride].tobytes()
+
+
+# --------------------------------------------------- nested jagged members
+# A jagged member may nest once (the children are a collection described by
+# properties, Sec. V): every hit of a track holds its own list of samples.
+# The pins: numpy's C structs for both record levels, the offsets invariants
+# at both levels, round trips, a zero-length special case, and a brute-force
+# walk over shuffled pools at both levels on tiny inputs.
+
+def _nested(n, seed, raw=False):
+    s = oracle.Schema(datagen.TRACKS_NESTED)
+    return s, datagen.workload("tracks_nested", n, seed, raw=raw)
+
+
+def test_nested_strides_match_numpy():
+    s = oracle.Schema(datagen.TRACKS_NESTED)
+    child_desc = datagen.jagged_member(datagen.TRACKS_NESTED)[2]
+    grand_desc = datagen.jagged_member(child_desc)[2]
+    assert s.stride == struct_dtype(datagen.TRACKS_NESTED).itemsize
+    assert s.child.stride == struct_dtype(child_desc).itemsize == 24
+    assert (s.child.len_off, s.child.begin_off) == (8, 16)
+    assert s.child.child.stride == struct_dtype(grand_desc).itemsize == 4
+
+
+@pytest.mark.parametrize("n", [0, 1, 17, 1000])
+def test_nested_soa_columns_and_offsets_invariants(n):
+    s, d = _nested(n, 3)
+    aos = oracle.pack(s, d, "aos")
+    soa = oracle.convert(s, aos, "soa")
+    m, m2 = d["m"], d["m2"]
+    base = soa.base
+    # parents
+    for c, v in enumerate(d["columns"]):
+        st = s.soa_region_start(n, m, c, m2)
+        assert base[st: st + v.nbytes].tobytes() == v.tobytes()
+    # offsets at both levels: exclusive scans ending at the totals
+    st = s.soa_region_start(n, m, s.ncols, m2)
+    off0 = base[st: st + 4 * (n + 1)].view("<u4")
+    assert off0.tolist() == np.concatenate([[0], np.cumsum(d["lengths"].astype(np.uint64))]).tolist()
+    assert int(off0[-1]) == m
+    r = s.ncols + 1
+    for c, v in enumerate(d["children"]):
+        st = s.soa_region_start(n, m, r + c, m2)
+        assert base[st: st + v.nbytes].tobytes() == v.tobytes()
+    st = s.soa_region_start(n, m, r + s.child.ncols, m2)
+    off1 = base[st: st + 4 * (m + 1)].view("<u4")
+    assert off1.tolist() == np.concatenate([[0], np.cumsum(d["child_lengths"].astype(np.uint64))]).tolist()
+    assert int(off1[-1]) == m2
+    for g, v in enumerate(d["grandchildren"]):
+        st = s.soa_region_start(n, m, r + s.child.ncols + 1 + g, m2)
+        assert st % 128 == 0
+        assert base[st: st + v.nbytes].tobytes() == v.tobytes()
+
+
+@pytest.mark.parametrize("n", [0, 1, 300])
+def test_nested_round_trips(n):
+    s, d = _nested(n, 5, raw=True)
+    aos = oracle.pack(s, d, "aos")
+    soa = oracle.convert(s, aos, "soa")
+    back = oracle.convert(s, soa, "aos")
+    assert back.base.tobytes() == aos.base.tobytes()
+    assert back.pool.tobytes() == aos.pool.tobytes()
+    assert back.gpool.tobytes() == aos.gpool.tobytes()
+    for B in (1, 3, 32):
+        blk = oracle.convert(s, aos, "aosoa", B)
+        again = oracle.convert(s, blk, "aos")
+        assert again.base.tobytes() == aos.base.tobytes() and again.gpool.tobytes() == aos.gpool.tobytes()
+        assert oracle.convert(s, blk, "soa").base.tobytes() == soa.base.tobytes()
+        assert oracle.convert(s, soa, "aosoa", B).base.tobytes() == blk.base.tobytes()
+
+
+def test_nested_with_no_grandchildren_is_the_flat_layout_plus_zero_offsets():
+    n = 200
+    s, d = _nested(n, 9)
+    d["child_lengths"] = np.zeros(d["m"], np.uint32)
+    d["grandchildren"] = [g[:0] for g in d["grandchildren"]]
+    d["m2"] = 0
+    flat = oracle.Schema([m if m[1] != "jagged" else (m[0], m[1], m[2], m[3][:2]) for m in datagen.TRACKS_NESTED])
+    soa = oracle.convert(s, oracle.pack(s, d, "aos"), "soa")
+    ref = oracle.pack(flat, d, "soa")
+    head = flat.base_bytes("soa", 0, n, d["m"])
+    assert soa.base[:head].tobytes() == ref.base[:head].tobytes()
+    st = s.soa_region_start(n, d["m"], s.ncols + 1 + s.child.ncols, 0)
+    assert st == head and not soa.base[st:].any()
+
+
+def _jagged_path(desc):
+    """Group names leading to the jagged member, then its name."""
+    for m in desc:
+        if m[1] == "jagged":
+            return [m[0]]
+        if m[1] == "group":
+            p = _jagged_path(m[2])
+            if p:
+                return [m[0]] + p
+    return None
+
+
+def _at(rec, path, suffix):
+    for g in path[:-1]:
+        rec = rec[g]
+    return rec[path[-1] + suffix]
+
+
+def _walk_nested(desc, n, recs, pool, gpool):
+    """Brute force: the canonical child and grandchild sequences, walking
+    numpy records parent by parent, child by child."""
+    jn, _, cdesc = datagen.jagged_member(desc)
+    gn, _, gdesc = datagen.jagged_member(cdesc)
+    jp, gp = _jagged_path(desc), _jagged_path(cdesc)
+    pd, cd, gd = struct_dtype(desc), struct_dtype(cdesc), struct_dtype(gdesc)
+    P = np.frombuffer(recs[: n * pd.itemsize].tobytes(), pd, count=n)
+    C = np.frombuffer(pool.tobytes(), cd, count=pool.size // cd.itemsize)
+    G = np.frombuffer(gpool.tobytes(), gd, count=gpool.size // gd.itemsize)
+    kids, grand, off0, off1 = [], [], [0], [0]
+    for i in range(n):
+        b, L = int(_at(P[i], jp, "_begin")), int(_at(P[i], jp, "_length"))
+        for k in range(L):
+            c = C[b + k]
+            kids.append(c)
+            b1, L1 = int(_at(c, gp, "_begin")), int(_at(c, gp, "_length"))
+            grand += [G[b1 + q] for q in range(L1)]
+            off1.append(off1[-1] + L1)
+        off0.append(off0[-1] + L)
+    return kids, grand, off0, off1
+
+
+NESTED_SMALL = [
+    [("a", "u8", 1), ("v", "jagged", "u32", [("x", "u16", 1), ("w", "jagged", "u32", [("y", "u8", 1)])])],
+    [("v", "jagged", "u64", [("w", "jagged", "u32", [("y", "u64", 1), ("z", "u8", 3)]), ("x", "f32", 1)]),
+     ("b", "u32", 2)],
+    [("g", "group", [("p", "f64", 1), ("v", "jagged", "u32", [("x", "u8", 2, "interleaved"),
+                                                            ("w", "jagged", "u64", [("y", "u16", 1)])])])],
+]
+
+
+def _shuffle_runs(recs, count, stride, len_off, begin_off, pool, rsize, order, gap):
+    """Re-lays the runs that `count` records (stride bytes each, with a
+    {u32 length @len_off, u64 begin @begin_off} descriptor) own in `pool`
+    (rsize-byte records): record order[k]'s run goes k-th, `gap` empty slots
+    before each; the begins are rewritten.  Returns the new pool."""
+    lens = [int(recs[i * stride + len_off: i * stride + len_off + 4].view("<u4")[0]) for i in range(count)]
+    begs = [int(recs[i * stride + begin_off: i * stride + begin_off + 8].view("<u8")[0]) for i in range(count)]
+    out = np.zeros(max(1, (sum(lens) + gap * count) * rsize), np.uint8)
+    cur = 0
+    for i in order:
+        i = int(i)
+        cur += gap
+        out[cur * rsize:(cur + lens[i]) * rsize] = pool[begs[i] * rsize:(begs[i] + lens[i]) * rsize]
+        recs[i * stride + begin_off: i * stride + begin_off + 8] = np.array([cur], "<u8").view(np.uint8)
+        cur += lens[i]
+    return out
+
+
+@pytest.mark.parametrize("k", range(len(NESTED_SMALL)))
+def test_brute_force_nested_shuffled_pools(k):
+    """Tiny nested collections whose pools are shuffled at both levels (runs
+    in random order, a free slot before each): the SoA output equals a
+    walk over the numpy records, parent by parent and child by child, and
+    converts back to the same values."""
+    from np_layout import leaf_paths, get_leaf
+    desc = NESTED_SMALL[k]
+    cdesc = datagen.jagged_member(desc)[2]
+    gdesc = datagen.jagged_member(cdesc)[2]
+    s = oracle.Schema(desc)
+    cs, gs = s.child.stride, s.child.child.stride
+    for n in (0, 1, 2, 5, 9):
+        d = datagen.jagged_random(desc, n, 100 + n, mean_len=2.0, max_len=4)
+        aos = oracle.pack(s, d, "aos")
+        m, m2 = d["m"], d["m2"]
+        rng = np.random.default_rng(7 * n + k)
+        kids = aos.pool[: max(1, m * cs)].copy()
+        gpool = _shuffle_runs(kids, m, cs, s.child.len_off, s.child.begin_off, aos.gpool, gs, rng.permutation(m), 1)
+        recs = aos.base.copy()
+        pool = _shuffle_runs(recs, n, s.stride, s.len_off, s.begin_off, kids, cs, rng.permutation(n), 1)
+        src = oracle.Side("aos", n, (pool.size // cs) if m else 0, base=recs, pool=pool, gpool=gpool,
+                          m2=(gpool.size // gs) if m2 else 0)
+        soa = oracle.convert(s, src, "soa", m=m, m2=m2)
+        assert soa.written == m
+        kid_recs, grand, off0, off1 = _walk_nested(desc, n, recs, pool, gpool)
+        base = soa.base
+        st = s.soa_region_start(n, m, s.ncols, m2)
+        assert base[st: st + s.off_size * (n + 1)].view("<u%d" % s.off_size).tolist() == off0
+        st = s.soa_region_start(n, m, s.ncols + 1 + s.child.ncols, m2)
+        o1 = s.child.off_size
+        assert base[st: st + o1 * (m + 1)].view("<u%d" % o1).tolist() == off1
+        for level, (recs_l, ldesc, first, lsch) in enumerate(
+                [(kid_recs, cdesc, s.ncols + 1, s.child),
+                 (grand, gdesc, s.ncols + 2 + s.child.ncols, s.child.child)]):
+            col = 0
+            for path, _, e in leaf_paths(ldesc):
+                for kk in range(e):
+                    st = s.soa_region_start(n, m, first + col, m2)
+                    es = lsch.col_es[col]
+                    for j, rec in enumerate(recs_l):
+                        v = np.asarray(get_leaf(rec, path))
+                        want = (v if e == 1 else v[kk]).tobytes()
+                        assert base[st + j * es: st + j * es + len(want)].tobytes() == want, (level, col, j)
+                    col += 1
+        # and back: the canonical pools hold the same values in walk order
+        back = oracle.convert(s, soa, "aos")
+        k2, g2, _, _ = _walk_nested(desc, n, back.base, back.pool, back.gpool)
+        strip = lambda r, dd: [np.asarray(get_leaf(r, p)).tobytes() for p, _, _ in leaf_paths(dd)]  # noqa: E731
+        assert [strip(r, cdesc) for r in k2] == [strip(r, cdesc) for r in kid_recs]
+        assert [strip(r, gdesc) for r in g2] == [strip(r, gdesc) for r in grand]
+
+
+def test_interleaved_parent_array_with_a_jagged_member():
+    """A jagged schema whose parents hold an interleaved array: the parent
+    storage columns, then the offsets and the child columns, each where the
+    column-counted item index says; numpy rows for the array, cumsum for
+    the offsets, round trips through SoA and AoSoA(B)."""
+    desc = [("pt", "f32", 1), ("cov", "f32", 3, "interleaved"),
+            ("hits", "jagged", "u32", [("index", "u32", 1), ("weight", "f32", 1)])]
+    s = oracle.Schema(desc)
+    n = 257
+    d = datagen.random_columns(desc, n, 6)
+    dj = datagen.workload("tracks", n, 7)
+    d.update(lengths=dj["lengths"], children=dj["children"], m=dj["m"])
+    aos = oracle.pack(s, d, "aos")
+    soa = oracle.convert(s, aos, "soa")
+    m = d["m"]
+    st = s.soa_region_start(n, m, 1)
+    assert soa.base[st: st + 12 * n].tobytes() == np.ascontiguousarray(d["columns"][1]).tobytes()
+    st = s.soa_region_start(n, m, s.ncols)
+    assert soa.base[st: st + 4 * (n + 1)].view("<u4").tolist() == \
+        np.concatenate([[0], np.cumsum(d["lengths"].astype(np.uint64))]).tolist()
+    for c, v in enumerate(d["children"]):
+        st = s.soa_region_start(n, m, s.ncols + 1 + c)
+        assert soa.base[st: st + v.nbytes].tobytes() == v.tobytes()
+    assert oracle.convert(s, soa, "aos").base.tobytes() == aos.base.tobytes()
+    for B in (3, 32):
+        assert oracle.convert(s, oracle.convert(s, aos, "aosoa", B), "soa").base.tobytes() == soa.base.tobytes()
