@@ -106,8 +106,21 @@ int mrn_schema_end_group(mrn_schema* s);
  *   SoA side: an offsets column of N+1 entries (offsets[0] = 0 unless an
  *     offset base is given, offsets[N] = number of children) and one column
  *     per flattened child property, holding all children contiguously.
- * At most one jagged property per schema; the child may not be jagged.
- * Returns MRN_EINVAL otherwise. */
+ * At most one jagged property per schema.  The child may itself have one
+ * jagged property (nesting once, Sec. V: the children are a collection
+ * described by properties) whose own child is not jagged:
+ *   AoS side: the children's {length, begin} index a second pool
+ *     (view.grandchild_pool, view.n_grandchildren records);
+ *   field-major side (single block only, view.base): after the parents'
+ *     offsets, the child level is laid out as the child schema's
+ *     single-block SoA for (n_children, n_grandchildren): child columns,
+ *     the children's offsets (n_children + 1), the grandchild columns.
+ *   Nested members convert between AoS and SoA / AoSoA(B) with
+ *   mrn_convert; the AoS -> field-major direction reads the children's
+ *   count back to the host between its two levels (it waits for `stream`
+ *   once).  Other calls return MRN_EUNSUPPORTED for them.
+ * Returns MRN_EINVAL for deeper nesting or two jagged properties;
+ * MRN_EUNSUPPORTED for a child with an interleaved array property. */
 int mrn_schema_add_jagged(mrn_schema* s, const char* name, int offset_dtype,
                           const mrn_schema* child);
 
@@ -198,6 +211,11 @@ typedef struct mrn_view {
   void* child_pool;       /* AoS jagged: child records (child AoS layout)     */
   uint64_t offset_base;   /* SoA jagged destination: added to every offset
                              (shards of one collection); 0 otherwise          */
+  /* Nested jagged member (the children have a jagged member of their own):
+   * the second level's size tag and, on the AoS side, the pool of the
+   * children's child records that their {length, begin} index. */
+  uint64_t n_grandchildren; /* M2: grandchildren (source) / capacity (dst)  */
+  void* grandchild_pool;    /* AoS side: grandchild records                  */
 } mrn_view;
 
 /* Bytes needed for view.base of a collection of n records / m children in
@@ -205,6 +223,17 @@ typedef struct mrn_view {
 int mrn_required_bytes(const mrn_schema* s, mrn_layout layout, uint64_t n, uint64_t m, size_t* out);
 /* Bytes of an AoS child pool of m child records. */
 int mrn_child_pool_bytes(const mrn_schema* s, uint64_t m, size_t* out);
+/* For a nested jagged member: view.base bytes with m2 grandchildren, the
+ * bytes of an AoS pool of m2 grandchild records, and the start of item r
+ * of a single-block field-major view (SoA: data column r < n_columns, the
+ * offsets at n_columns, then the child level's items counted the same way:
+ * child columns, the children's offsets, grandchild columns; AoSoA(B):
+ * blocks at 0, offsets at 1, then the child level's items). */
+int mrn_required_bytes_nested(const mrn_schema* s, mrn_layout layout, uint64_t n, uint64_t m, uint64_t m2,
+                              size_t* out);
+int mrn_grandchild_pool_bytes(const mrn_schema* s, uint64_t m2, size_t* out);
+int mrn_region_offset_nested(const mrn_schema* s, mrn_layout layout, uint64_t n, uint64_t m, uint64_t m2,
+                             uint32_t r, size_t* out);
 /* Start of region r inside a single-block SoA of n records / m children:
  * r < n_columns: data column r; r == n_columns: offsets; then child columns.
  * Each stored column starts at a multiple of 128 bytes; the columns of an

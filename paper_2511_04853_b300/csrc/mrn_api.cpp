@@ -56,7 +56,7 @@ int fm_side(const mrn_schema* s, const mrn_view& v, bool child, SidePlan* sp) {
       } else {
         if (!v.base) return MRN_EINVAL;
         p = static_cast<char*>(v.base) +
-            fm_col_start(s, v.layout.kind, v.layout.block, v.n_records, v.n_children, child, c);
+            fm_col_start(s, v.layout.kind, v.layout.block, v.n_records, v.n_children, child, c, v.n_grandchildren);
       }
       if (!p && (child ? v.n_children : v.n_records) > 0) return MRN_EINVAL;
       if (reinterpret_cast<uintptr_t>(p) % t->cols[c].size) return MRN_EALIGN;
@@ -175,7 +175,7 @@ int gap_plans(const mrn_schema* s, const mrn_view& dst, GapPlan g[2]) {
     std::memset(&h, 0, sizeof(h));
     const int kind = dst.layout.kind;
     const uint32_t B = dst.layout.block;
-    const uint64_t n = dst.n_records, m = dst.n_children;
+    const uint64_t n = dst.n_records, m = dst.n_children, m2 = dst.n_grandchildren;
     uint64_t prev_end = 0;
     auto add = [&](uint64_t a, uint64_t b) {
       if (b > a && h.ngaps < MRN_MAX_GAPS) {
@@ -185,11 +185,11 @@ int gap_plans(const mrn_schema* s, const mrn_view& dst, GapPlan g[2]) {
       }
     };
     for (uint32_t r = 0; r < fm_region_count(s, kind); ++r) {
-      const uint64_t st = fm_region_start(s, kind, B, n, m, r);
+      const uint64_t st = fm_region_start(s, kind, B, n, m, r, m2);
       add(prev_end, st);
-      prev_end = st + fm_region_bytes(s, kind, B, n, m, r);
+      prev_end = st + fm_region_bytes(s, kind, B, n, m, r, m2);
     }
-    add(prev_end, fm_total_bytes(s, kind, B, n, m));
+    add(prev_end, fm_total_bytes(s, kind, B, n, m, m2));
     h.base = static_cast<char*>(dst.base);
     h.nblocks = 1;
     h.block_bytes = 0;
@@ -547,6 +547,7 @@ int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
   int rc = validate_pair(src, dst, true, &jag);
   if (rc) return rc;
   const mrn_schema* s = src->schema;
+  if (is_nested(s)) return convert_nested(*src, *dst, stream);
   if (jag && src->layout.kind != MRN_AOS && dst->layout.kind != MRN_AOS)
     return convert_jagged_fm(*src, *dst, stream);
   if (jag) {

@@ -113,6 +113,7 @@ int plan_job(const mrn_view& src, const mrn_view& dst, std::vector<BatchJob>* ou
   bool jag = false;
   int rc = validate_pair(&src, &dst, true, &jag);
   if (rc) return rc;
+  if (is_nested(src.schema)) return MRN_EUNSUPPORTED;  // converted level by level by mrn_convert
   BatchJob j;
   std::memset(&j, 0, sizeof(j));
   if (jag) {

@@ -468,7 +468,7 @@ int mrn_collection_create(const mrn_schema* s, mrn_layout layout, int mem, int d
   if (!s || !s->finalized || check_mem(mem)) return MRN_EINVAL;
   if (layout.kind != MRN_AOS && layout.kind != MRN_SOA && layout.kind != MRN_AOSOA) return MRN_EINVAL;
   if (layout.kind == MRN_AOSOA && layout.block == 0) return MRN_EINVAL;
-  if (s->interleaved) return MRN_EUNSUPPORTED;  // storage moves are per stored column
+  if (s->interleaved || is_nested(s)) return MRN_EUNSUPPORTED;  // storage moves are per stored column
   mrn_collection* c = new (std::nothrow) mrn_collection;
   if (!c) return MRN_ENOMEM;
   c->s = s;

@@ -62,18 +62,30 @@ uint64_t aosoa_block_bytes(const mrn_schema* s, uint32_t B);
 uint64_t aosoa_col_start(const mrn_schema* s, uint32_t B, uint32_t c);
 // Start of column c (child: the jagged child's column c) inside a
 // single-block field-major view: its storage region plus its element offset.
-uint64_t fm_col_start(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, bool child, uint32_t c);
-uint64_t soa_region_start(const mrn_schema* s, uint64_t n, uint64_t m, uint32_t r);
+uint64_t fm_col_start(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, bool child, uint32_t c,
+                      uint64_t m2 = 0);
 // Regions of a single-block field-major view of either kind (SoA: data
-// columns, offsets, child columns; jagged AoSoA(B): blocks, offsets, child
-// columns), each 128-byte aligned.
+// storage columns, offsets, then the child level; jagged AoSoA(B): blocks,
+// offsets, then the child level), each 128-byte aligned.  The child level
+// is the child schema's single-block SoA for (m, m2): child storage columns
+// and, for a nested jagged member, the children's offsets and the
+// grandchild storage columns.  m2 counts grandchildren (0 unless nested).
 uint32_t parent_regions(const mrn_schema* s, int kind);
 uint32_t fm_region_count(const mrn_schema* s, int kind);
-uint64_t fm_region_bytes(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint32_t r);
-uint64_t fm_region_start(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint32_t r);
-uint64_t fm_total_bytes(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m);
+uint64_t fm_region_bytes(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint32_t r,
+                         uint64_t m2 = 0);
+uint64_t fm_region_start(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint32_t r,
+                         uint64_t m2 = 0);
+uint64_t fm_total_bytes(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint64_t m2 = 0);
 uint64_t soa_total_bytes(const mrn_schema* s, uint64_t n, uint64_t m);
-uint64_t base_bytes(const mrn_schema* s, const mrn_layout& l, uint64_t n, uint64_t m);
+uint64_t base_bytes(const mrn_schema* s, const mrn_layout& l, uint64_t n, uint64_t m, uint64_t m2 = 0);
+// A schema whose jagged member's children have a jagged member of their own.
+inline bool is_nested(const mrn_schema* s) { return s->has_jagged && s->child->has_jagged; }
+// Nested member of a single-block field-major view: the children's offsets
+// (m + 1 entries) and grandchild column g.
+uint64_t fm_child_offsets_start(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint64_t m2);
+uint64_t fm_gchild_col_start(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint64_t m2,
+                             uint32_t g);
 
 // ---- device status word and scratch helpers (mrn_kernels.cu)
 int device_sm_count();
@@ -110,6 +122,9 @@ int zero_dst_gaps(const mrn_view& dst, void* stream);
 // view.base (single block); its offsets pointer.
 bool fm_single_block(const mrn_view& v);
 char* fm_offsets(const mrn_view& v);
+// A nested jagged member between AoS and a single-block field-major side,
+// level by level (mrn_nested.cpp).
+int convert_nested(const mrn_view& src, const mrn_view& dst, void* stream);
 // Host-side validation of a device view pair; fills *is_jagged.
 int validate_pair(const mrn_view* src, const mrn_view* dst, bool need_device, bool* is_jagged);
 

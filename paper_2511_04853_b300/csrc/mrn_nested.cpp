@@ -1,0 +1,163 @@
+// Nested jagged members: a jagged member whose child records hold a jagged
+// member of their own (Sec. V: the children are themselves a collection
+// described by properties; one nesting level).  The conversion runs level by
+// level with the library's own jagged kernels:
+//
+//   field-major -> AoS: the child level is an ordinary jagged SoA -> AoS
+//     conversion of the child schema (child columns + the children's
+//     offsets + grandchild columns -> child records with their {length,
+//     begin} + the grandchild pool), then the parents' records are built
+//     from their offsets;
+//   AoS -> field-major: the parents' tile scan gathers each child's data
+//     columns into the child level and its {length, begin} into two scratch
+//     columns; the children's count is read back; the descriptors are packed
+//     into 16-byte records {u32 length, u64 begin}, which an ordinary jagged
+//     AoS -> SoA conversion of a descriptor-only schema turns into the
+//     children's offsets and the gathered grandchild columns.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "mrn_internal.h"
+
+namespace mrn {
+
+namespace {
+
+// A finalized schema built through the C API, destroyed with the object.
+struct OwnedSchema {
+  mrn_schema* s = nullptr;
+  ~OwnedSchema() { mrn_schema_destroy(s); }
+};
+
+mrn_view device_view(const mrn_schema* s, int kind, int device, uint64_t n, uint64_t m) {
+  mrn_view v;
+  std::memset(&v, 0, sizeof(v));
+  v.schema = s;
+  v.layout.kind = kind;
+  v.layout.block = 0;
+  v.mem = MRN_MEM_DEVICE;
+  v.device = device;
+  v.n_records = n;
+  v.n_children = m;
+  return v;
+}
+
+}  // namespace
+
+int convert_nested(const mrn_view& src, const mrn_view& dst, void* stream) {
+  const mrn_schema* s = src.schema;
+  const mrn_schema* ch = s->child.get();
+  const bool a2s = src.layout.kind == MRN_AOS, s2a = dst.layout.kind == MRN_AOS;
+  if (a2s == s2a) return MRN_EUNSUPPORTED;  // field-major to field-major
+  const mrn_view& fm = a2s ? dst : src;
+  const mrn_view& aos = a2s ? src : dst;
+  if (!fm.base || !fm_single_block(fm)) return MRN_EUNSUPPORTED;  // single-block field-major side
+  if (aos.n_children > 0 && !aos.child_pool) return MRN_EINVAL;
+  if (aos.n_grandchildren > 0 && !aos.grandchild_pool) return MRN_EINVAL;
+  const int kind = fm.layout.kind;
+  const uint32_t B = fm.layout.block;
+  const uint64_t n = fm.n_records, m = fm.n_children, m2 = fm.n_grandchildren;
+  char* base = static_cast<char*>(fm.base);
+  // The field-major side's child level, as per-column pointers.
+  std::vector<void*> kcols(ch->cols.size()), gcols(ch->child->cols.size());
+  for (uint32_t c = 0; c < kcols.size(); ++c) kcols[c] = base + fm_col_start(s, kind, B, n, m, true, c, m2);
+  for (uint32_t g = 0; g < gcols.size(); ++g) gcols[g] = base + fm_gchild_col_start(s, kind, B, n, m, m2, g);
+  char* off1 = base + fm_child_offsets_start(s, kind, B, n, m, m2);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc;
+
+  if (s2a) {
+    if (dst.n_children < src.n_children || dst.n_grandchildren < src.n_grandchildren) return MRN_ESIZE;
+    // child level: child columns + offsets + grandchild columns -> child
+    // records (with their descriptors) + grandchild pool
+    mrn_view ks = device_view(ch, MRN_SOA, src.device, src.n_children, src.n_grandchildren);
+    ks.base = off1;
+    ks.columns = kcols.data();
+    ks.offsets = off1;
+    ks.child_columns = gcols.data();
+    mrn_view kd = device_view(ch, MRN_AOS, dst.device, src.n_children, dst.n_grandchildren);
+    kd.base = dst.child_pool;
+    kd.child_pool = dst.grandchild_pool;
+    if ((rc = mrn_convert(&ks, &kd, stream))) return rc;
+    // parents: records with {length, begin} from their offsets
+    JagPlan jp;
+    if ((rc = build_jagged_plan(src, dst, &jp))) return rc;
+    jp.m_src = 0;
+    return launch_jagged_s2a(jp, stream);
+  }
+
+  // AoS -> field-major.  Level 0 gathers the children's descriptors into
+  // scratch columns beside their data columns.
+  JagPlan jp;
+  if ((rc = build_jagged_plan(src, dst, &jp))) return rc;
+  ConvPlan& C = jp.child;
+  const uint32_t nc = (uint32_t)ch->cols.size();
+  if (nc + 2 > MRN_MAX_COLS) return MRN_EUNSUPPORTED;
+  const uint64_t mcap = dst.n_children;
+  const uint64_t lb_bytes = align_up(jagged_scratch_bytes(std::max<uint64_t>(1, jagged_tile_records(jp))), 256);
+  const uint64_t len_at = lb_bytes, beg_at = align_up(len_at + 4 * mcap, 256),
+                 rec_at = align_up(beg_at + 8 * mcap, 256), tot_at = align_up(rec_at + 16 * mcap, 256);
+  char* scratch = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&scratch), tot_at + 256, st) != cudaSuccess) {
+    cudaGetLastError();
+    return MRN_ENOMEM;
+  }
+  auto done = [&](int r) {
+    cudaFreeAsync(scratch, st);
+    return r;
+  };
+  C.aos_cols[C.naos++] = ColPlan{4, (int16_t)nc, ch->len_off};
+  C.aos_cols[C.naos++] = ColPlan{8, (int16_t)(nc + 1), ch->begin_off};
+  std::stable_sort(C.aos_cols, C.aos_cols + C.naos,
+                   [](const ColPlan& a, const ColPlan& b) { return a.aos_off < b.aos_off; });
+  C.dst.col[nc] = scratch + len_at;
+  C.dst.col[nc + 1] = scratch + beg_at;
+  C.fm_size[nc] = 4;
+  C.fm_es[nc] = 4;
+  C.fm_size[nc + 1] = 8;
+  C.fm_es[nc + 1] = 8;
+  unsigned long long* d_total = reinterpret_cast<unsigned long long*>(scratch + tot_at);
+  jp.total_out = d_total;
+  if (cudaMemsetAsync(d_total, 0, sizeof(unsigned long long), st) != cudaSuccess) return done(MRN_ECUDA);
+  if ((rc = launch_jagged_a2s(jp, scratch, stream))) return done(rc);
+  unsigned long long m1 = 0;
+  if (cudaMemcpyAsync(&m1, d_total, sizeof(m1), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return done(MRN_ECUDA);
+  if (m1 > mcap) return done(MRN_ESIZE);  // recorded by the kernel as well
+
+  // The descriptors as 16-byte records {u32 length, u64 begin}.
+  OwnedSchema plain, desc;
+  if (mrn_schema_create(&plain.s) || mrn_schema_add_field(plain.s, "length", MRN_U32, 1) ||
+      mrn_schema_add_field(plain.s, "begin", MRN_U64, 1) || mrn_schema_finalize(plain.s) ||
+      mrn_schema_create(&desc.s) ||
+      mrn_schema_add_jagged(desc.s, "v", ch->off_size == 4 ? MRN_U32 : MRN_U64, ch->child.get()) ||
+      mrn_schema_finalize(desc.s))
+    return done(MRN_ENOMEM);
+  if (plain.s->stride != 16 || desc.s->stride != 16 || desc.s->len_off != 0 || desc.s->begin_off != 8)
+    return done(MRN_EINVAL);
+  void* pcols[2] = {scratch + len_at, scratch + beg_at};
+  mrn_view ps = device_view(plain.s, MRN_SOA, dst.device, m1, 0);
+  ps.base = scratch + len_at;
+  ps.columns = pcols;
+  mrn_view pd = device_view(plain.s, MRN_AOS, dst.device, m1, 0);
+  pd.base = scratch + rec_at;
+  if (m1 && (rc = mrn_convert(&ps, &pd, stream))) return done(rc);
+
+  // Level 1: the children's offsets and the grandchild columns.
+  mrn_view ds = device_view(desc.s, MRN_AOS, src.device, m1, src.n_grandchildren);
+  ds.base = scratch + rec_at;
+  ds.child_pool = src.grandchild_pool;
+  mrn_view dd = device_view(desc.s, MRN_SOA, dst.device, m1, dst.n_grandchildren);
+  dd.base = off1;
+  dd.offsets = off1;
+  dd.child_columns = gcols.data();
+  if ((rc = mrn_convert(&ds, &dd, stream))) return done(rc);
+  if ((rc = zero_dst_gaps(dst, stream))) return done(rc);
+  return done(MRN_OK);
+}
+
+}  // namespace mrn

@@ -55,7 +55,8 @@ extern "C" int mrn_convert_jagged_noalloc(const mrn_view* src, const mrn_view* d
   bool jag = false;
   int rc = validate_pair(src, dst, true, &jag);
   if (rc) return rc;
-  if (!jag || src->layout.kind != MRN_AOS || dst->layout.kind != MRN_SOA) return MRN_EINVAL;
+  if (!jag || is_nested(src->schema) || src->layout.kind != MRN_AOS || dst->layout.kind != MRN_SOA)
+    return MRN_EINVAL;
   // The array is looked up for the current device: a stream of another
   // device would run the kernel there against this device's address.
   int cur = -1, sdev = -1;

@@ -178,46 +178,61 @@ uint64_t aosoa_block_bytes(const mrn_schema* s, uint32_t B) {
 uint32_t parent_regions(const mrn_schema* s, int kind) {
   return kind == MRN_AOSOA ? 1u : (uint32_t)s->stores.size();
 }
-uint64_t fm_region_bytes(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint32_t r) {
+uint64_t fm_region_bytes(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint32_t r,
+                         uint64_t m2) {
   const uint32_t P = parent_regions(s, kind);
   if (r < P) return kind == MRN_AOSOA ? (n + B - 1) / B * aosoa_block_bytes(s, B) : n * s->stores[r].es;
   if (r == P) return (n + 1) * s->off_size;
-  return m * s->child->stores[r - P - 1].es;
+  return fm_region_bytes(s->child.get(), MRN_SOA, 0, m, m2, r - P - 1, 0);
 }
 
 uint32_t fm_region_count(const mrn_schema* s, int kind) {
-  return parent_regions(s, kind) + (s->has_jagged ? 1 + (uint32_t)s->child->stores.size() : 0);
+  return parent_regions(s, kind) + (s->has_jagged ? 1 + fm_region_count(s->child.get(), MRN_SOA) : 0);
 }
 
-uint64_t fm_region_start(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint32_t r) {
+uint64_t fm_region_start(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint32_t r,
+                         uint64_t m2) {
   uint64_t pos = 0;
-  for (uint32_t k = 0; k < r; ++k) pos = align_up(pos + fm_region_bytes(s, kind, B, n, m, k), 128);
+  for (uint32_t k = 0; k < r; ++k) pos = align_up(pos + fm_region_bytes(s, kind, B, n, m, k, m2), 128);
   return pos;
+}
+
+uint64_t fm_child_offsets_start(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint64_t m2) {
+  return fm_region_start(s, kind, B, n, m, parent_regions(s, kind) + 1 + (uint32_t)s->child->stores.size(), m2);
+}
+
+uint64_t fm_gchild_col_start(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint64_t m2,
+                             uint32_t g) {
+  const MrnColumn& gc = s->child->child->cols[g];
+  return fm_region_start(s, kind, B, n, m, parent_regions(s, kind) + 2 + (uint32_t)s->child->stores.size() + gc.store,
+                         m2) + gc.sub;
 }
 
 uint64_t soa_region_start(const mrn_schema* s, uint64_t n, uint64_t m, uint32_t r) {
   return fm_region_start(s, MRN_SOA, 0, n, m, r);
 }
 
-uint64_t fm_col_start(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, bool child, uint32_t c) {
-  if (!child) return fm_region_start(s, kind, B, n, m, s->cols[c].store) + s->cols[c].sub;
+uint64_t fm_col_start(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, bool child, uint32_t c,
+                      uint64_t m2) {
+  if (!child) return fm_region_start(s, kind, B, n, m, s->cols[c].store, m2) + s->cols[c].sub;
   const MrnColumn& cc = s->child->cols[c];
-  return fm_region_start(s, kind, B, n, m, parent_regions(s, kind) + 1 + cc.store) + cc.sub;
+  return fm_region_start(s, kind, B, n, m, parent_regions(s, kind) + 1 + cc.store, m2) + cc.sub;
 }
 
-uint64_t fm_total_bytes(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m) {
+uint64_t fm_total_bytes(const mrn_schema* s, int kind, uint32_t B, uint64_t n, uint64_t m, uint64_t m2) {
   const uint32_t nr = fm_region_count(s, kind);
-  return align_up(fm_region_start(s, kind, B, n, m, nr - 1) + fm_region_bytes(s, kind, B, n, m, nr - 1), 128);
+  return align_up(fm_region_start(s, kind, B, n, m, nr - 1, m2) + fm_region_bytes(s, kind, B, n, m, nr - 1, m2),
+                  128);
 }
 
 uint64_t soa_total_bytes(const mrn_schema* s, uint64_t n, uint64_t m) { return fm_total_bytes(s, MRN_SOA, 0, n, m); }
 
-uint64_t base_bytes(const mrn_schema* s, const mrn_layout& l, uint64_t n, uint64_t m) {
+uint64_t base_bytes(const mrn_schema* s, const mrn_layout& l, uint64_t n, uint64_t m, uint64_t m2) {
   switch (l.kind) {
     case MRN_AOS: return n * s->stride;
-    case MRN_SOA: return fm_total_bytes(s, MRN_SOA, 0, n, m);
+    case MRN_SOA: return fm_total_bytes(s, MRN_SOA, 0, n, m, m2);
     default:
-      if (s->has_jagged) return fm_total_bytes(s, MRN_AOSOA, l.block, n, m);
+      if (s->has_jagged) return fm_total_bytes(s, MRN_AOSOA, l.block, n, m, m2);
       return (n + l.block - 1) / l.block * aosoa_block_bytes(s, l.block);
   }
 }
@@ -281,7 +296,7 @@ int mrn_schema_end_group(mrn_schema* s) {
 }
 
 int mrn_schema_add_jagged(mrn_schema* s, const char* name, int offset_dtype, const mrn_schema* child) {
-  if (!s || s->finalized || !valid_name(name) || !child || !child->finalized || child->has_jagged ||
+  if (!s || s->finalized || !valid_name(name) || !child || !child->finalized || is_nested(child) ||
       child->cols.empty() || (offset_dtype != MRN_U32 && offset_dtype != MRN_U64) ||
       find_jagged(s->roots))
     return MRN_EINVAL;
@@ -364,6 +379,46 @@ int mrn_required_bytes(const mrn_schema* s, mrn_layout l, uint64_t n, uint64_t m
       (l.kind == MRN_AOSOA && l.block < 1))
     return MRN_EINVAL;
   *out = (size_t)base_bytes(s, l, n, m);
+  return MRN_OK;
+}
+
+int mrn_required_bytes_nested(const mrn_schema* s, mrn_layout l, uint64_t n, uint64_t m, uint64_t m2,
+                              size_t* out) {
+  if (!s || !s->finalized || !out || l.kind < MRN_AOS || l.kind > MRN_AOSOA ||
+      (l.kind == MRN_AOSOA && l.block < 1))
+    return MRN_EINVAL;
+  *out = (size_t)base_bytes(s, l, n, m, m2);
+  return MRN_OK;
+}
+
+int mrn_grandchild_pool_bytes(const mrn_schema* s, uint64_t m2, size_t* out) {
+  if (!s || !s->finalized || !is_nested(s) || !out) return MRN_EINVAL;
+  *out = (size_t)(m2 * s->child->child->stride);
+  return MRN_OK;
+}
+
+int mrn_region_offset_nested(const mrn_schema* s, mrn_layout l, uint64_t n, uint64_t m, uint64_t m2, uint32_t r,
+                             size_t* out) {
+  if (!s || !s->finalized || !out || !s->has_jagged || (l.kind != MRN_SOA && l.kind != MRN_AOSOA) ||
+      (l.kind == MRN_AOSOA && l.block < 1))
+    return MRN_EINVAL;
+  const int kind = l.kind;
+  const uint32_t B = l.kind == MRN_AOSOA ? l.block : 0;
+  const uint32_t pc = kind == MRN_AOSOA ? 1u : (uint32_t)s->cols.size();  // items before the offsets
+  const mrn_schema* ch = s->child.get();
+  const uint32_t kc = (uint32_t)ch->cols.size();
+  if (r < pc)
+    *out = (size_t)(kind == MRN_AOSOA ? 0 : fm_col_start(s, kind, B, n, m, false, r, m2));
+  else if (r == pc)
+    *out = (size_t)fm_region_start(s, kind, B, n, m, parent_regions(s, kind), m2);
+  else if (r - pc - 1 < kc)
+    *out = (size_t)fm_col_start(s, kind, B, n, m, true, r - pc - 1, m2);
+  else if (is_nested(s) && r - pc - 1 == kc)
+    *out = (size_t)fm_child_offsets_start(s, kind, B, n, m, m2);
+  else if (is_nested(s) && r - pc - 2 - kc < ch->child->cols.size())
+    *out = (size_t)fm_gchild_col_start(s, kind, B, n, m, m2, r - pc - 2 - kc);
+  else
+    return MRN_EINVAL;
   return MRN_OK;
 }
 

@@ -310,7 +310,7 @@ int mrn_server_submit(mrn_server* sv, const mrn_view* src, const mrn_view* dst, 
   int rc = validate_pair(src, dst, false, &jag);
   if (rc) return rc;
   if (!is_host(*src) && !is_host(*dst)) return MRN_EINVAL;
-  if (src->schema->interleaved) return MRN_EUNSUPPORTED;  // served through the transfer engine
+  if (src->schema->interleaved || is_nested(src->schema)) return MRN_EUNSUPPORTED;  // via the transfer engine
   for (const mrn_view* v : {src, dst})
     if (v->mem == MRN_MEM_DEVICE && v->device != sv->device) return MRN_EINVAL;
   if (jag && dst->layout.kind == MRN_AOS && dst->n_children < src->n_children) return MRN_ESIZE;

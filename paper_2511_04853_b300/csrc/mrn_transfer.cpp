@@ -425,7 +425,7 @@ extern "C" int mrn_transfer_convert(const mrn_view* src, const mrn_view* dst, co
   int rc = validate_pair(src, dst, false, &jag);
   if (rc) return rc;
   // staging and the chunk views keep each field-major column separate
-  if (src->schema->interleaved) return MRN_EUNSUPPORTED;
+  if (src->schema->interleaved || is_nested(src->schema)) return MRN_EUNSUPPORTED;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return MRN_ECUDA;
   const bool h2d = is_host(*src) && dst->mem == MRN_MEM_DEVICE && dst->device == dev;

@@ -30,7 +30,8 @@ class ViewStruct(ctypes.Structure):
     _fields_ = [("schema", vp), ("layout", Layout), ("mem", i32), ("device", i32),
                 ("n_records", u64), ("n_children", u64), ("base", vp),
                 ("columns", vp), ("offsets", vp), ("child_columns", vp),
-                ("child_pool", vp), ("offset_base", u64)]
+                ("child_pool", vp), ("offset_base", u64), ("n_grandchildren", u64),
+                ("grandchild_pool", vp)]
 
 
 class SchemaInfo(ctypes.Structure):
@@ -86,6 +87,9 @@ SIGNATURES = [
     ("mrn_schema_create", ctypes.c_int, [ctypes.POINTER(vp)]),
     ("mrn_schema_add_field", ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_int, u32]),
     ("mrn_schema_add_field_interleaved", ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_int, u32]),
+    ("mrn_required_bytes_nested", ctypes.c_int, [vp, Layout, u64, u64, u64, ctypes.POINTER(sz)]),
+    ("mrn_grandchild_pool_bytes", ctypes.c_int, [vp, u64, ctypes.POINTER(sz)]),
+    ("mrn_region_offset_nested", ctypes.c_int, [vp, Layout, u64, u64, u64, u32, ctypes.POINTER(sz)]),
     ("mrn_schema_begin_group", ctypes.c_int, [vp, ctypes.c_char_p]),
     ("mrn_schema_end_group", ctypes.c_int, [vp]),
     ("mrn_schema_add_jagged", ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_int, vp]),
@@ -268,6 +272,23 @@ class Schema:
         check(lib().mrn_child_pool_bytes(self._h, m, ctypes.byref(out)))
         return out.value
 
+    def required_bytes_nested(self, kind, n, m, m2, block=0):
+        out = sz()
+        check(lib().mrn_required_bytes_nested(self._h, Layout(KIND.get(kind, kind), block), n, m, m2,
+                                              ctypes.byref(out)))
+        return out.value
+
+    def grandchild_pool_bytes(self, m2):
+        out = sz()
+        check(lib().mrn_grandchild_pool_bytes(self._h, m2, ctypes.byref(out)))
+        return out.value
+
+    def region_offset_nested(self, kind, n, m, m2, r, block=0):
+        out = sz()
+        check(lib().mrn_region_offset_nested(self._h, Layout(KIND.get(kind, kind), block), n, m, m2, r,
+                                             ctypes.byref(out)))
+        return out.value
+
     def region_offset(self, kind, n, m, r, block=0):
         out = sz()
         check(lib().mrn_region_offset(self._h, Layout(KIND.get(kind, kind), block), n, m, r,
@@ -301,9 +322,9 @@ class View:
 
     def __init__(self, schema, kind, n, block=0, base=None, columns=None, offsets=None,
                  child_columns=None, child_pool=None, m=0, mem="device", device=None,
-                 offset_base=0):
+                 offset_base=0, m2=0, grandchild_pool=None):
         self.schema = schema
-        self._keep = [base, columns, offsets, child_columns, child_pool]
+        self._keep = [base, columns, offsets, child_columns, child_pool, grandchild_pool]
         if device is None:
             device = 0
             if hasattr(base, "data_ptr") and getattr(base, "is_cuda", False):
@@ -319,7 +340,7 @@ class View:
             schema._h, Layout(KIND.get(kind, kind), block), MEM.get(mem, mem), device, n, m,
             _ptr(base), ctypes.cast(cols_arr, vp) if cols_arr is not None else None,
             _ptr(offsets), ctypes.cast(ccols_arr, vp) if ccols_arr is not None else None,
-            _ptr(child_pool), offset_base)
+            _ptr(child_pool), offset_base, m2, _ptr(grandchild_pool))
 
     @property
     def ref(self):

@@ -115,7 +115,7 @@ def test_column_names_follow_the_description():
     [("x", "u8", 0)],
     [("v", "jagged", "u16", [("x", "u8", 1)])],
     [("v", "jagged", "u32", [("x", "u8", 1)]), ("w", "jagged", "u32", [("x", "u8", 1)])],
-    [("v", "jagged", "u32", [("c", "jagged", "u32", [("x", "u8", 1)])])],
+    [("v", "jagged", "u32", [("c", "jagged", "u32", [("d", "jagged", "u32", [("x", "u8", 1)])])])],
 ])
 def test_invalid_schemas_are_rejected(bad):
     with pytest.raises(mrn.MrnError) as e:
@@ -152,3 +152,36 @@ def test_convert_rejects_bad_views_without_a_device():
     assert mrn.convert_status(src, dst, stream=0) == mrn.EINVAL
     dst2 = mrn.View(s, "aosoa", 10, block=0, base=buf, mem="host")
     assert mrn.convert_status(src, dst2, stream=0) == mrn.EINVAL
+
+
+@pytest.mark.parametrize("desc", [datagen.TRACKS_NESTED,
+                                  [("g", "group", [("p", "f64", 1),
+                                                   ("v", "jagged", "u32", [("x", "u8", 2),
+                                                                           ("w", "jagged", "u64",
+                                                                            [("y", "u16", 1)])])])]])
+def test_nested_layout_matches_oracle(desc):
+    s, o = mrn.Schema(desc), oracle.Schema(desc)
+    assert s.stride == o.stride and s.info.child_stride == o.child.stride
+    items = s.ncols + 1 + len(s.child_columns) + 1 + len(o.child.child.col_size)
+    for n, m, m2 in [(0, 0, 0), (1, 3, 7), (1000, 20011, 60001)]:
+        for kind, B in (("soa", 0), ("aosoa", 1), ("aosoa", 32)):
+            assert s.required_bytes_nested(kind, n, m, m2, B) == o.base_bytes(kind, B, n, m, m2)
+            nit = items if kind == "soa" else 2 + len(s.child_columns) + 1 + len(o.child.child.col_size)
+            for r in range(nit):
+                assert s.region_offset_nested(kind, n, m, m2, r, B) == o.fm_region_start(kind, B, n, m, r, m2), \
+                    (kind, B, n, m, m2, r)
+        assert s.grandchild_pool_bytes(m2) == m2 * o.child.child.stride
+
+
+def test_nesting_deeper_than_once_is_refused():
+    inner = mrn.Schema([("x", "u8", 1), ("w", "jagged", "u32", [("y", "u8", 1)])])
+    mid = mrn.Schema([("z", "u8", 1), ("v", "jagged", "u32", [("x", "u8", 1), ("w", "jagged", "u32",
+                                                                                 [("y", "u8", 1)])])])
+    L = mrn.lib()
+    h = ctypes.c_void_p()
+    assert L.mrn_schema_create(ctypes.byref(h)) == 0
+    assert L.mrn_schema_add_jagged(h, b"ok", 4, inner._h) == 0
+    L.mrn_schema_destroy(h)
+    assert L.mrn_schema_create(ctypes.byref(h)) == 0
+    assert L.mrn_schema_add_jagged(h, b"deep", 4, mid._h) == mrn.EINVAL
+    L.mrn_schema_destroy(h)

@@ -1,0 +1,126 @@
+"""GPU parity of nested jagged members (children with a jagged member of
+their own): AoS <-> single-block SoA and AoS <-> AoSoA(B) on canonical and
+shuffled pools at both levels, sizes across many tiles, u32 and u64
+offsets, and the errors each level reports, each equal to the oracle."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+import paper_2511_04853_b300 as mrn
+from gpu_util import dev, garbage, host
+from nested_util import shuffled_nested
+
+pytestmark = pytest.mark.gpu
+
+SMALL = [
+    [("a", "u8", 1), ("v", "jagged", "u32", [("x", "u16", 1), ("w", "jagged", "u32", [("y", "u8", 1)])])],
+    [("v", "jagged", "u64", [("w", "jagged", "u32", [("y", "u64", 1), ("z", "u8", 3)]), ("x", "f32", 1)]),
+     ("b", "u32", 2)],
+    [("g", "group", [("p", "f64", 1), ("v", "jagged", "u32", [("x", "u8", 2),
+                                                            ("w", "jagged", "u64", [("y", "u16", 1)])])])],
+]
+
+
+def fm_dest(s, kind, n, m, m2, block=0):
+    return garbage(s.required_bytes_nested(kind, n, m, m2, block))
+
+
+def to_fm(s, o, o_src, n, m, m2, kind, block):
+    """Device AoS (from the oracle side) -> field-major; returns the bytes
+    and the oracle's bytes of the same conversion."""
+    want = oracle.convert(o, o_src, kind, block, m=m, m2=m2).base[: s.required_bytes_nested(kind, n, m, m2, block)]
+    dst = fm_dest(s, kind, n, m, m2, block)
+    src = mrn.View(s, "aos", n, base=dev(o_src.base), child_pool=dev(o_src.pool), m=o_src.m,
+                   m2=o_src.m2, grandchild_pool=dev(o_src.gpool))
+    mrn.convert(src, mrn.View(s, kind, n, block=block, base=dst, m=m, m2=m2))
+    assert mrn.sync() == mrn.OK
+    return host(dst, want.size), want, dst
+
+
+def back_to_aos(s, o, dst, n, m, m2, kind, block):
+    recs, pool, gpool = garbage(n * o.stride), garbage(m * o.child.stride), garbage(m2 * o.child.child.stride)
+    mrn.convert(mrn.View(s, kind, n, block=block, base=dst, m=m, m2=m2),
+                mrn.View(s, "aos", n, base=recs, child_pool=pool, m=m, m2=m2, grandchild_pool=gpool))
+    assert mrn.sync() == mrn.OK
+    return host(recs, n * o.stride), host(pool, m * o.child.stride), host(gpool, m2 * o.child.child.stride)
+
+
+@pytest.mark.parametrize("n", [0, 1, 1000, 70001])
+@pytest.mark.parametrize("kind,block", [("soa", 0), ("aosoa", 32), ("aosoa", 5)])
+def test_tracks_nested_round_trip(n, kind, block):
+    s, o = mrn.Schema(datagen.TRACKS_NESTED), oracle.Schema(datagen.TRACKS_NESTED)
+    d = datagen.workload("tracks_nested", n, 3 + n % 7)
+    aos = oracle.pack(o, d, "aos")
+    m, m2 = d["m"], d["m2"]
+    got, want, dst = to_fm(s, o, aos, n, m, m2, kind, block)
+    assert np.array_equal(got, want)
+    recs, pool, gpool = back_to_aos(s, o, dst, n, m, m2, kind, block)
+    assert np.array_equal(recs, aos.base[: n * o.stride])
+    assert np.array_equal(pool, aos.pool[: m * o.child.stride])
+    assert np.array_equal(gpool, aos.gpool[: m2 * o.child.child.stride])
+
+
+@pytest.mark.parametrize("k", range(len(SMALL)))
+@pytest.mark.parametrize("n", [1, 7, 3001])
+def test_shuffled_pools_raw_bits(k, n):
+    desc = SMALL[k]
+    s, o = mrn.Schema(desc), oracle.Schema(desc)
+    d = datagen.jagged_random(desc, n, 50 + n + k, mean_len=3.0, max_len=8)
+    aos = oracle.pack(o, d, "aos")
+    recs, pool, gpool, mp, m2p = shuffled_nested(o, aos, seed=k * 100 + n)
+    src_o = oracle.Side("aos", n, mp, base=recs, pool=pool, gpool=gpool, m2=m2p)
+    m, m2 = d["m"], d["m2"]
+    for kind, block in (("soa", 0), ("aosoa", 32)):
+        got, want, _ = to_fm(s, o, src_o, n, m, m2, kind, block)
+        assert np.array_equal(got, want), (kind, block)
+
+
+def test_capacity_and_bad_indices_are_reported():
+    s, o = mrn.Schema(datagen.TRACKS_NESTED), oracle.Schema(datagen.TRACKS_NESTED)
+    n = 5000
+    d = datagen.workload("tracks_nested", n, 11)
+    aos = oracle.pack(o, d, "aos")
+    m, m2 = d["m"], d["m2"]
+    src = mrn.View(s, "aos", n, base=dev(aos.base), child_pool=dev(aos.pool), m=m, m2=m2,
+                   grandchild_pool=dev(aos.gpool))
+    # too few children slots: refused once the children's count is known
+    small = fm_dest(s, "soa", n, m - 1, m2)
+    st = mrn.convert_status(src, mrn.View(s, "soa", n, base=small, m=m - 1, m2=m2))
+    assert st == mrn.ESIZE
+    mrn.sync()  # the kernel recorded it too
+    # too few grandchild slots: recorded by the second level
+    dst = fm_dest(s, "soa", n, m, m2 - 1)
+    assert mrn.convert_status(src, mrn.View(s, "soa", n, base=dst, m=m, m2=m2 - 1)) == mrn.OK
+    assert mrn.sync() == mrn.ESIZE
+    # a child whose samples run past the grandchild pool
+    pool = aos.pool.copy()
+    pool[o.child.begin_off: o.child.begin_off + 8] = np.array([m2], "<u8").view(np.uint8)
+    pool[o.child.len_off: o.child.len_off + 4] = np.array([1], "<u4").view(np.uint8)
+    bad = mrn.View(s, "aos", n, base=dev(aos.base), child_pool=dev(pool), m=m, m2=m2,
+                   grandchild_pool=dev(aos.gpool))
+    dst = fm_dest(s, "soa", n, m, m2 + 1)
+    assert mrn.convert_status(bad, mrn.View(s, "soa", n, base=dst, m=m, m2=m2 + 1)) == mrn.OK
+    assert mrn.sync() == mrn.EINVAL
+    # afterwards a good conversion runs normally
+    got, want, _ = to_fm(s, o, aos, n, m, m2, "soa", 0)
+    assert np.array_equal(got, want)
+
+
+def test_other_paths_refuse_nested_members():
+    import torch
+    s = mrn.Schema(datagen.TRACKS_NESTED)
+    n, m, m2 = 10, 20, 30
+    a = fm_dest(s, "soa", n, m, m2)
+    b = fm_dest(s, "aosoa", n, m, m2, 32)
+    src = mrn.View(s, "soa", n, base=a, m=m, m2=m2)
+    assert mrn.convert_status(src, mrn.View(s, "aosoa", n, block=32, base=b, m=m, m2=m2)) == mrn.EUNSUPPORTED
+    recs, pool, gpool = garbage(n * s.stride), garbage(m * 24), garbage(m2 * 4)
+    aos = mrn.View(s, "aos", n, base=recs, child_pool=pool, m=m, m2=m2, grandchild_pool=gpool)
+    with pytest.raises(mrn.MrnError):
+        mrn.Batch([(aos, mrn.View(s, "soa", n, base=a, m=m, m2=m2))], use_graph=False)
+    h = torch.zeros(n * s.stride, dtype=torch.uint8).pin_memory()
+    hv = mrn.View(s, "aos", n, base=h, child_pool=h, m=m, m2=m2, grandchild_pool=h, mem="pinned")
+    st = mrn.lib().mrn_transfer_convert(hv.ref, mrn.View(s, "soa", n, base=a, m=m, m2=m2).ref, None,
+                                        mrn.mrn._stream(None))
+    assert st == mrn.EUNSUPPORTED

@@ -775,22 +775,7 @@ NESTED_SMALL = [
 ]
 
 
-def _shuffle_runs(recs, count, stride, len_off, begin_off, pool, rsize, order, gap):
-    """Re-lays the runs that `count` records (stride bytes each, with a
-    {u32 length @len_off, u64 begin @begin_off} descriptor) own in `pool`
-    (rsize-byte records): record order[k]'s run goes k-th, `gap` empty slots
-    before each; the begins are rewritten.  Returns the new pool."""
-    lens = [int(recs[i * stride + len_off: i * stride + len_off + 4].view("<u4")[0]) for i in range(count)]
-    begs = [int(recs[i * stride + begin_off: i * stride + begin_off + 8].view("<u8")[0]) for i in range(count)]
-    out = np.zeros(max(1, (sum(lens) + gap * count) * rsize), np.uint8)
-    cur = 0
-    for i in order:
-        i = int(i)
-        cur += gap
-        out[cur * rsize:(cur + lens[i]) * rsize] = pool[begs[i] * rsize:(begs[i] + lens[i]) * rsize]
-        recs[i * stride + begin_off: i * stride + begin_off + 8] = np.array([cur], "<u8").view(np.uint8)
-        cur += lens[i]
-    return out
+from nested_util import shuffle_runs as _shuffle_runs  # noqa: E402
 
 
 @pytest.mark.parametrize("k", range(len(NESTED_SMALL)))
