@@ -142,6 +142,7 @@ struct JagWarp {
   unsigned long long warp[MRN_JAG_WARPS];
   unsigned long long kmin[MRN_JAG_WARPS], kmax[MRN_JAG_WARPS];  // per warp: min / max of begin - exclusive offset
   unsigned long long base;
+  unsigned long long lsum[MRN_JAG_WARPS];  // per warp: sum of its lengths (early aggregate)
 };
 
 // Loads and stores of one column element of S bytes.
@@ -447,19 +448,56 @@ template <int VP, int VC>
 __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile, unsigned long long* st,
                                                 uint32_t* tw_all, JagShared& sh, JagWarp& sw) {
   constexpr int W = MRN_WIN_WORDS;
-  static_assert(MRN_JAG_TILE == 2 * MRN_JAG_THREADS, "two parents per thread");
+  constexpr int K = MRN_JAG_TILE / MRN_JAG_THREADS;  // parents per thread
+  static_assert(MRN_JAG_TILE == K * MRN_JAG_THREADS, "whole parents per thread");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t* tw = tw_all + warp * MRN_TW_WORDS(W);
   const ConvPlan& P = jp.parent;
   const uint64_t t0 = tile * MRN_JAG_TILE;
 
-  // Parents q = tid and q = MRN_JAG_THREADS + tid of the tile (consecutive records per
-  // warp); then their lengths go to excl[] for the scan and their begins
-  // (all ones for a parent whose children lie outside the pool) to beg[].
-  uint32_t len[2];
-  uint64_t beg[2];
+  // The tile's aggregate first, from the lengths alone, published at once:
+  // the tiles after this one sum it in their look-back, which otherwise
+  // waits for this tile's whole parent conversion.  (The records' lines
+  // stay in cache for the conversion below.)
+  const bool publish = (long long)tile != jp.skip_publish_tile;
+  {
+    unsigned long long own = 0;
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < K; ++k) {
+      const uint64_t r = t0 + k * MRN_JAG_THREADS + tid;
+      if (r < P.n) {
+        const char* q = P.src.base + r * P.stride + jp.len_off;
+        if (P.vec >= 4) {
+          own += __ldg(reinterpret_cast<const unsigned int*>(q));
+        } else {  // a base aligned to less than 4 bytes: byte by byte
+          uint32_t v = 0;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) v |= (uint32_t)__ldg(reinterpret_cast<const unsigned char*>(q + b)) << (8 * b);
+          own += v;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) own += __shfl_xor_sync(0xffffffffu, own, o);
+    if (lane == 0) sw.lsum[warp] = own;
+    __syncthreads();
+    if (tid == 0) {
+      unsigned long long a = 0;
+#pragma unroll
+      for (int w = 0; w < MRN_JAG_WARPS; ++w) a += sw.lsum[w];
+      if (publish)
+        st_release_u64(&st[tile], (tile == 0 ? MRN_TS_PREFIX : MRN_TS_AGG) | (a & MRN_TS_VALUE));
+    }
+  }
+
+  // Parents q = k * MRN_JAG_THREADS + tid of the tile (consecutive records
+  // per warp); then their lengths go to excl[] for the scan and their
+  // begins (all ones for a parent whose children lie outside the pool) to
+  // beg[].
+  uint32_t len[K];
+  uint64_t beg[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
     const uint64_t r = t0 + k * MRN_JAG_THREADS + tid;
     const bool ok = r < P.n;
     len[k] = 0;
@@ -474,17 +512,18 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
   }
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < K; ++k) {
     sh.excl[k * MRN_JAG_THREADS + tid] = len[k];
     sh.beg[k * MRN_JAG_THREADS + tid] = beg[k];
   }
   __syncthreads();
 
-  // CTA-wide exclusive scan in parent order: thread t owns parents 2t and
-  // 2t + 1 (64-bit sums).
-  const unsigned long long l0 = sh.excl[2 * tid], l1 = sh.excl[2 * tid + 1];
-  const unsigned long long b0 = sh.beg[2 * tid], b1 = sh.beg[2 * tid + 1];
-  unsigned long long x = l0 + l1;
+  // CTA-wide exclusive scan in parent order: thread t owns parents K t ..
+  // K t + K - 1 (64-bit sums).
+  unsigned long long own = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) own += sh.excl[K * tid + k];
+  unsigned long long x = own;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
@@ -502,21 +541,28 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
     if (lane < MRN_JAG_WARPS) sw.warp[lane] = t;
   }
   __syncthreads();
-  const unsigned long long e0 = x - (l0 + l1) + (warp > 0 ? sw.warp[warp - 1] : 0ull), e1 = e0 + l0;
   const unsigned long long agg = sw.warp[MRN_JAG_WARPS - 1];
-  sh.excl[2 * tid] = e0;
-  sh.excl[2 * tid + 1] = e1;
-  if (tid == MRN_JAG_THREADS - 1) sh.excl[MRN_JAG_TILE] = agg;
-  // Run test: beg - excl equal for every parent with children (a parent
-  // outside the pool fails it: min 0, max all ones).
+  // Exclusive offsets of the thread's parents written back in place; the
+  // run test on the way: beg - excl equal for every parent with children
+  // (a parent outside the pool fails it: min 0, max all ones).
   unsigned long long kmin = ~0ull, kmax = 0ull;
-  if (b0 == ~0ull || b1 == ~0ull) {
-    kmin = 0ull;
-    kmax = ~0ull;
-  } else {
-    if (l0 > 0) kmin = min(kmin, b0 - e0), kmax = max(kmax, b0 - e0);
-    if (l1 > 0) kmin = min(kmin, b1 - e1), kmax = max(kmax, b1 - e1);
+  {
+    unsigned long long e = x - own + (warp > 0 ? sw.warp[warp - 1] : 0ull);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const unsigned long long l = sh.excl[K * tid + k], b = sh.beg[K * tid + k];
+      if (b == ~0ull) {
+        kmin = 0ull;
+        kmax = ~0ull;
+      } else if (l > 0) {
+        kmin = min(kmin, b - e);
+        kmax = max(kmax, b - e);
+      }
+      sh.excl[K * tid + k] = e;
+      e += l;
+    }
   }
+  if (tid == MRN_JAG_THREADS - 1) sh.excl[MRN_JAG_TILE] = agg;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
@@ -527,14 +573,11 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
     sw.kmax[warp] = kmax;
   }
 
-  // Decoupled look-back for the number of children of all earlier tiles.
+  // Decoupled look-back for the number of children of all earlier tiles
+  // (the tile's aggregate was published as soon as its lengths were in).
   if (warp == 0) {
-    const bool publish = (long long)tile != jp.skip_publish_tile;
     unsigned long long prefix = 0;
-    if (tile == 0) {
-      if (publish && lane == 0) st_release_u64(&st[0], MRN_TS_PREFIX | (agg & MRN_TS_VALUE));
-    } else {
-      if (publish && lane == 0) st_release_u64(&st[tile], MRN_TS_AGG | (agg & MRN_TS_VALUE));
+    if (tile > 0) {
       prefix = jagged_lookback(jp, tile, st, lane);
       if (publish && lane == 0) st_release_u64(&st[tile], MRN_TS_PREFIX | ((prefix + agg) & MRN_TS_VALUE));
     }
@@ -562,12 +605,14 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
   }
 
   // Offsets: offset_base + children before this parent (a collection of
-  // no objects, given one tile, has the single offset offset_base).
+  // no objects, given one tile, has the single offset offset_base).  Every
+  // parent's exclusive offset and the next one are in excl[] (excl[TILE] =
+  // the tile's sum), written before the look-back's barrier.
   if (P.n == 0 && tid == 0) write_offset(jp.offsets, jp.off_size, 0, jp.offset_base);
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const uint64_t r = t0 + 2 * tid + k;
-    const unsigned long long excl = k ? e1 : e0, len = k ? l1 : l0;
+  for (int k = 0; k < K; ++k) {
+    const uint64_t r = t0 + K * tid + k;
+    const unsigned long long excl = sh.excl[K * tid + k], len = sh.excl[K * tid + k + 1] - excl;
     if (r < P.n) {
       const unsigned long long o = jp.offset_base + base + excl;
       write_offset(jp.offsets, jp.off_size, r, o);

@@ -169,8 +169,10 @@ inline uint64_t staged_tile_count(uint64_t n, uint64_t nrec, uint32_t T, uint32_
   return s.nfull + (s.rs ? 1 : 0) + (nrec > s.d0 ? 1 : 0);
 }
 
+#ifndef MRN_JAG_TILE
 #define MRN_JAG_TILE 1024    // parents per tile of the jagged scan
-#define MRN_JAG_THREADS 512  // threads per jagged tile (two parents each)
+#endif
+#define MRN_JAG_THREADS 512  // threads per jagged tile (MRN_JAG_TILE / 512 parents each)
 #define MRN_JAG_WARPS (MRN_JAG_THREADS / 32)
 #define MRN_JAG_CHILD_GROUP 128  // child records per warp group of a jagged SoA -> AoS conversion
 
