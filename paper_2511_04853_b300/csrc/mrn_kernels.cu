@@ -637,7 +637,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
 }
 
 template <int VP, int VC>
-__global__ void __launch_bounds__(MRN_JAG_THREADS, 3) k_jagged_a2s(const __grid_constant__ JagPlan jp) {
+__global__ void __launch_bounds__(MRN_JAG_THREADS, MRN_JAG_CTAS) k_jagged_a2s(const __grid_constant__ JagPlan jp) {
   // The tile windows serve the parent conversion only; the per-parent
   // arrays are written after every warp has finished it.
   constexpr size_t kTw = MRN_JAG_WARPS * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t);
@@ -659,7 +659,7 @@ __global__ void __launch_bounds__(MRN_JAG_THREADS, 3) k_jagged_a2s(const __grid_
 // job's plan is copied into shared memory first: the tile reads its fields
 // all along, and from global memory (not the constant bank, where a single
 // conversion's plan sits) those reads cost the batch a quarter of its speed.
-__global__ void __launch_bounds__(MRN_JAG_THREADS, 3) k_batch_jag(const BatchJob* __restrict__ jobs,
+__global__ void __launch_bounds__(MRN_JAG_THREADS, MRN_JAG_CTAS) k_batch_jag(const BatchJob* __restrict__ jobs,
                                                                  const unsigned int* __restrict__ tile_job,
                                                                  unsigned long long total, unsigned int* counter,
                                                                  unsigned long long* states) {

@@ -172,7 +172,12 @@ inline uint64_t staged_tile_count(uint64_t n, uint64_t nrec, uint32_t T, uint32_
 #ifndef MRN_JAG_TILE
 #define MRN_JAG_TILE 1024    // parents per tile of the jagged scan
 #endif
-#define MRN_JAG_THREADS 512  // threads per jagged tile (MRN_JAG_TILE / 512 parents each)
+#ifndef MRN_JAG_THREADS
+#define MRN_JAG_THREADS 512  // threads per jagged tile (MRN_JAG_TILE / MRN_JAG_THREADS parents each)
+#endif
+#ifndef MRN_JAG_CTAS
+#define MRN_JAG_CTAS 3       // resident jagged CTAs per SM the kernels are compiled for
+#endif
 #define MRN_JAG_WARPS (MRN_JAG_THREADS / 32)
 #define MRN_JAG_CHILD_GROUP 128  // child records per warp group of a jagged SoA -> AoS conversion
 
