@@ -521,6 +521,54 @@ cudaStream_t side_stream() {
 }
 }  // namespace
 
+namespace {
+// Plans of recent plain conversions, so that a conversion repeated on the
+// same views (a loop over the same buffers) skips planning.  The key is
+// every byte the plan depends on: both views, their column pointers, the
+// schemas' structure, the tuned-shape generation and the debug switch.
+struct PlanKey {
+  mrn_view src, dst;
+  void* scols[MRN_MAX_COLS];
+  void* dcols[MRN_MAX_COLS];
+  uint64_t src_hash, dst_hash, tune_gen;
+  int force_direct;
+};
+struct PlanEntry {
+  bool valid = false;
+  PlanKey key;
+  ConvPlan plan;
+  LaunchShape shape;
+  int np = 0;
+  GapPlan g[2];
+};
+constexpr int kPlanSlots = 16;
+std::mutex g_plan_mu;
+PlanEntry g_plans[kPlanSlots];
+
+void plan_key(const mrn_view& src, const mrn_view& dst, PlanKey* k) {
+  std::memset(k, 0, sizeof(*k));
+  k->src = src;
+  k->dst = dst;
+  k->src.columns = k->dst.columns = nullptr;
+  const size_t nc = src.schema->cols.size();
+  for (size_t c = 0; c < nc; ++c) {
+    if (src.columns) k->scols[c] = src.columns[c];
+    if (dst.columns) k->dcols[c] = dst.columns[c];
+  }
+  k->src_hash = src.schema->hash;
+  k->dst_hash = dst.schema->hash;
+  k->tune_gen = tune_generation();
+  k->force_direct = g_force_direct.load();
+}
+
+int plan_slot(const PlanKey& k) {
+  uint64_t h = reinterpret_cast<uintptr_t>(k.src.base) ^ (reinterpret_cast<uintptr_t>(k.dst.base) << 1) ^
+               (k.src.n_records * 0x9e3779b97f4a7c15ull) ^ ((uint64_t)k.dst.layout.kind << 7) ^ k.dst.layout.block;
+  h ^= h >> 29;
+  return (int)(h % kPlanSlots);
+}
+}  // namespace
+
 extern "C" {
 
 const char* mrn_status_str(int st) {
@@ -556,6 +604,19 @@ int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
     if (src->layout.kind == MRN_AOS) {
       cudaStream_t st = static_cast<cudaStream_t>(stream);
       void* scratch = nullptr;
+      // a single-block destination's few gaps are zeroed by the kernel's
+      // tile 0 instead of a launch of their own
+      GapPlan g[2];
+      const int np = src->n_records > 0 ? gap_plans_of(*dst, g) : -1;
+      const bool fold = np == 0 || (np == 1 && g[0].nblocks == 1 && g[0].ngaps <= MRN_JAG_GAPS);
+      if (fold && np == 1) {
+        jp.gap_base = g[0].base;
+        jp.ngaps = g[0].ngaps;
+        for (uint32_t k = 0; k < g[0].ngaps; ++k) {
+          jp.gap_off[k] = g[0].off[k];
+          jp.gap_len[k] = g[0].len[k];
+        }
+      }
       if (src->n_records > 0) {
         if (cudaMallocAsync(&scratch, jagged_scratch_bytes(jagged_tile_records(jp)), st) != cudaSuccess)
           return MRN_ENOMEM;
@@ -563,6 +624,7 @@ int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
       rc = launch_jagged_a2s(jp, scratch, stream);
       if (scratch) cudaFreeAsync(scratch, st);
       if (rc) return rc;
+      if (fold) return MRN_OK;
     } else {
       // The children are stored contiguously on both sides (Sec. V, jagged
       // vector property): child row j -> pool record j is a plain SoA -> AoS
@@ -598,12 +660,32 @@ int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
                ? MRN_OK
                : MRN_ECUDA;
   }
-  ConvPlan p;
-  if ((rc = build_plan(*src, *dst, &p))) return rc;
-  LaunchShape sh = tuned_shape(p);
-  if (g_force_direct.load()) sh.generic = 1;
-  if ((rc = launch_convert(p, stream, &sh))) return rc;
-  return zero_dst_gaps(*dst, stream);
+  PlanKey key;
+  plan_key(*src, *dst, &key);
+  const int slot = plan_slot(key);
+  PlanEntry e;
+  bool hit = false;
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    if (g_plans[slot].valid && std::memcmp(&g_plans[slot].key, &key, sizeof(key)) == 0) {
+      e = g_plans[slot];
+      hit = true;
+    }
+  }
+  if (!hit) {
+    if ((rc = build_plan(*src, *dst, &e.plan))) return rc;
+    e.shape = tuned_shape(e.plan);
+    if (g_force_direct.load()) e.shape.generic = 1;
+    e.np = gap_plans_of(*dst, e.g);
+    e.key = key;
+    e.valid = true;
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plans[slot] = e;
+  }
+  if ((rc = launch_convert(e.plan, stream, &e.shape))) return rc;
+  for (int i = 0; i < e.np; ++i)
+    if ((rc = launch_zero_gaps(e.g[i], stream))) return rc;
+  return MRN_OK;
 }
 
 int mrn_sync(void* stream) {

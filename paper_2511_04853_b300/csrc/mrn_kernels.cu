@@ -604,6 +604,11 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
       bulk_prefetch_l2(reinterpret_cast<const void*>(q), (uint32_t)min((uintptr_t)32768, hi - q));
   }
 
+  // Tile 0 of a single conversion zeroes the destination's gap bytes.
+  if (tile == 0 && jp.ngaps)
+    for (uint32_t k = 0; k < jp.ngaps; ++k)
+      for (uint32_t b = tid; b < jp.gap_len[k]; b += MRN_JAG_THREADS) jp.gap_base[jp.gap_off[k] + b] = 0;
+
   // Offsets: offset_base + children before this parent (a collection of
   // no objects, given one tile, has the single offset offset_base).  Every
   // parent's exclusive offset and the next one are in excl[] (excl[TILE] =

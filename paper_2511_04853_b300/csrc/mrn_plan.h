@@ -7,6 +7,7 @@
 
 #define MRN_MAX_COLS 64   // flattened data columns per schema (and per child)
 #define MRN_MAX_GAPS 160  // zero-fill ranges of one destination
+#define MRN_JAG_GAPS 8    // zero-fill ranges a jagged tile 0 takes over
 #define MRN_NO_SHIFT 0xffffffffu
 
 enum MrnKind : int32_t { K_AOS = 0, K_SOA = 1, K_AOSOA = 2 };
@@ -127,6 +128,12 @@ struct JagPlan {
   unsigned long long timeout_ns;   // bound of each look-back wait
   long long skip_publish_tile;     // fault injection: tile that never publishes (-1: none)
   unsigned long long* total_out;   // optional: receives the number of children
+  // Single conversions: the few bytes between the regions of a single-block
+  // destination, zeroed by tile 0 of the AoS -> SoA kernel (no extra launch)
+  char* gap_base;
+  uint32_t ngaps;
+  uint32_t gap_len[MRN_JAG_GAPS];
+  uint64_t gap_off[MRN_JAG_GAPS];
 };
 
 // Zero-fill of the alignment holes of a destination: for each of `nblocks`

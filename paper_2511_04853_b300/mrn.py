@@ -183,11 +183,17 @@ def check(code, what=""):
     return code
 
 
+_CURRENT_STREAM = []  # torch.cuda.current_stream once CUDA is known to be available
+
+
 def _stream(stream):
     if stream is None:
+        if _CURRENT_STREAM:
+            return _CURRENT_STREAM[0]().cuda_stream
         try:
             import torch
             if torch.cuda.is_available():
+                _CURRENT_STREAM.append(torch.cuda.current_stream)
                 return torch.cuda.current_stream().cuda_stream
         except ImportError:
             pass
@@ -348,7 +354,17 @@ class View:
 
 
 def convert(src, dst, stream=None):
-    check(lib().mrn_convert(src.ref, dst.ref, _stream(stream)), "mrn_convert")
+    rc = _LIB_CONVERT[0](src.ref, dst.ref, _stream(stream)) if _LIB_CONVERT else _first_convert(src, dst, stream)
+    if rc != OK:
+        raise MrnError(rc, "mrn_convert")
+
+
+_LIB_CONVERT = []
+
+
+def _first_convert(src, dst, stream):
+    _LIB_CONVERT.append(lib().mrn_convert)
+    return _LIB_CONVERT[0](src.ref, dst.ref, _stream(stream))
 
 
 def convert_status(src, dst, stream=None):
