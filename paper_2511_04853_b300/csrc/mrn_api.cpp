@@ -521,54 +521,6 @@ cudaStream_t side_stream() {
 }
 }  // namespace
 
-namespace {
-// Plans of recent plain conversions, so that a conversion repeated on the
-// same views (a loop over the same buffers) skips planning.  The key is
-// every byte the plan depends on: both views, their column pointers, the
-// schemas' structure, the tuned-shape generation and the debug switch.
-struct PlanKey {
-  mrn_view src, dst;
-  void* scols[MRN_MAX_COLS];
-  void* dcols[MRN_MAX_COLS];
-  uint64_t src_hash, dst_hash, tune_gen;
-  int force_direct;
-};
-struct PlanEntry {
-  bool valid = false;
-  PlanKey key;
-  ConvPlan plan;
-  LaunchShape shape;
-  int np = 0;
-  GapPlan g[2];
-};
-constexpr int kPlanSlots = 16;
-std::mutex g_plan_mu;
-PlanEntry g_plans[kPlanSlots];
-
-void plan_key(const mrn_view& src, const mrn_view& dst, PlanKey* k) {
-  std::memset(k, 0, sizeof(*k));
-  k->src = src;
-  k->dst = dst;
-  k->src.columns = k->dst.columns = nullptr;
-  const size_t nc = src.schema->cols.size();
-  for (size_t c = 0; c < nc; ++c) {
-    if (src.columns) k->scols[c] = src.columns[c];
-    if (dst.columns) k->dcols[c] = dst.columns[c];
-  }
-  k->src_hash = src.schema->hash;
-  k->dst_hash = dst.schema->hash;
-  k->tune_gen = tune_generation();
-  k->force_direct = g_force_direct.load();
-}
-
-int plan_slot(const PlanKey& k) {
-  uint64_t h = reinterpret_cast<uintptr_t>(k.src.base) ^ (reinterpret_cast<uintptr_t>(k.dst.base) << 1) ^
-               (k.src.n_records * 0x9e3779b97f4a7c15ull) ^ ((uint64_t)k.dst.layout.kind << 7) ^ k.dst.layout.block;
-  h ^= h >> 29;
-  return (int)(h % kPlanSlots);
-}
-}  // namespace
-
 extern "C" {
 
 const char* mrn_status_str(int st) {
@@ -660,32 +612,12 @@ int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
                ? MRN_OK
                : MRN_ECUDA;
   }
-  PlanKey key;
-  plan_key(*src, *dst, &key);
-  const int slot = plan_slot(key);
-  PlanEntry e;
-  bool hit = false;
-  {
-    std::lock_guard<std::mutex> lk(g_plan_mu);
-    if (g_plans[slot].valid && std::memcmp(&g_plans[slot].key, &key, sizeof(key)) == 0) {
-      e = g_plans[slot];
-      hit = true;
-    }
-  }
-  if (!hit) {
-    if ((rc = build_plan(*src, *dst, &e.plan))) return rc;
-    e.shape = tuned_shape(e.plan);
-    if (g_force_direct.load()) e.shape.generic = 1;
-    e.np = gap_plans_of(*dst, e.g);
-    e.key = key;
-    e.valid = true;
-    std::lock_guard<std::mutex> lk(g_plan_mu);
-    g_plans[slot] = e;
-  }
-  if ((rc = launch_convert(e.plan, stream, &e.shape))) return rc;
-  for (int i = 0; i < e.np; ++i)
-    if ((rc = launch_zero_gaps(e.g[i], stream))) return rc;
-  return MRN_OK;
+  ConvPlan p;
+  if ((rc = build_plan(*src, *dst, &p))) return rc;
+  LaunchShape sh = tuned_shape(p);
+  if (g_force_direct.load()) sh.generic = 1;
+  if ((rc = launch_convert(p, stream, &sh))) return rc;
+  return zero_dst_gaps(*dst, stream);
 }
 
 int mrn_sync(void* stream) {

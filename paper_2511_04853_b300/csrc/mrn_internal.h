@@ -180,6 +180,4 @@ LaunchShape tuned_shape(const ConvPlan& p);
 namespace mrn {
 void store_tuned_shape(uint64_t key, const LaunchShape& s);
 void clear_tuned_shapes();
-// Changes whenever a tuned shape is stored or the tuning cache is cleared.
-uint64_t tune_generation();
 }  // namespace mrn

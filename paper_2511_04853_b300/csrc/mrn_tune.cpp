@@ -1,5 +1,4 @@
 // Launch-shape cache consulted by every conversion (filled by mrn_autotune).
-#include <atomic>
 #include <mutex>
 #include <unordered_map>
 
@@ -10,7 +9,6 @@ namespace mrn {
 namespace {
 std::mutex g_tune_mu;
 std::unordered_map<uint64_t, LaunchShape> g_tune_cache;
-std::atomic<uint64_t> g_tune_generation{0};
 }  // namespace
 
 LaunchShape tuned_shape(const ConvPlan& p) {
@@ -22,15 +20,11 @@ LaunchShape tuned_shape(const ConvPlan& p) {
 void store_tuned_shape(uint64_t key, const LaunchShape& s) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache[key] = s;
-  g_tune_generation.fetch_add(1);
 }
-
-uint64_t tune_generation() { return g_tune_generation.load(); }
 
 void clear_tuned_shapes() {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache.clear();
-  g_tune_generation.fetch_add(1);
 }
 
 }  // namespace mrn
