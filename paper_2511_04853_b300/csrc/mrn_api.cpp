@@ -587,6 +587,38 @@ int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
       if ((rc = jagged_children_plan(s, jp, &kids))) return rc;
       jp.m_src = 0;
       cudaStream_t st = static_cast<cudaStream_t>(stream);
+      // Large SoA parents whose record a plain schema reproduces: their
+      // {length, begin} become two scratch columns, and the parents one
+      // plain staged SoA -> AoS conversion of that schema, then the
+      // children's (small collections keep the two launches below).
+      const FlatParent* fp =
+          src->layout.kind == MRN_SOA && src->n_records >= (1u << 18) ? flat_parent_schema(s) : nullptr;
+      if (fp) {
+        const uint64_t n = src->n_records;
+        char* scratch = nullptr;
+        const uint64_t beg_at = align_up(4 * n, 256);
+        if (cudaMallocAsync(reinterpret_cast<void**>(&scratch), beg_at + 8 * n, st) != cudaSuccess) {
+          cudaGetLastError();
+          return MRN_ENOMEM;
+        }
+        rc = launch_len_begin(jp.offsets, jp.off_size, n, reinterpret_cast<unsigned int*>(scratch),
+                              reinterpret_cast<unsigned long long*>(scratch + beg_at), stream);
+        std::vector<void*> cols(fp->src.size());
+        for (size_t k = 0; k < cols.size(); ++k)
+          cols[k] = fp->src[k] >= 0 ? jp.parent.src.col[fp->src[k]] : fp->src[k] == -1 ? scratch : scratch + beg_at;
+        mrn_view ps = *src, pd = *dst;
+        ps.schema = pd.schema = fp->schema.get();
+        ps.columns = cols.data();
+        ps.offsets = nullptr;
+        ps.child_columns = nullptr;
+        ps.n_children = pd.n_children = ps.n_grandchildren = pd.n_grandchildren = 0;
+        pd.child_pool = pd.grandchild_pool = nullptr;
+        if (!rc) rc = mrn_convert(&ps, &pd, stream);
+        if (!rc) rc = launch_convert(kids, stream, nullptr);
+        cudaFreeAsync(scratch, st);
+        if (rc) return rc;
+        return zero_dst_gaps(*dst, stream);
+      }
       cudaStream_t side = side_stream();
       cudaEvent_t fork = nullptr, join = nullptr;
       const bool split = side && cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&

@@ -145,6 +145,19 @@ uint64_t jagged_scratch_bytes(uint64_t n);
 int launch_jagged_a2s(JagPlan& jp, void* scratch, void* stream);
 int launch_jagged_s2a(const JagPlan& jp, void* stream);
 int launch_jagged_count(const ConvPlan& parent, uint64_t* dev_total, void* stream);
+// Parents' {length, begin} columns from a field-major side's offsets.
+int launch_len_begin(const char* offsets, uint32_t off_size, uint64_t n, unsigned int* len,
+                     unsigned long long* beg, void* stream);
+// A plain schema whose AoS record is byte for byte the parent record of the
+// jagged schema s (its data fields and the "length" u32 and "begin" u64 of
+// the jagged member, in offset order); field k of it is data column src[k]
+// of s, or the length (-1) or the begin (-2).  nullptr when natural
+// alignment cannot reproduce the record.  Cached per schema structure.
+struct FlatParent {
+  std::unique_ptr<mrn_schema> schema;
+  std::vector<int> src;
+};
+const FlatParent* flat_parent_schema(const mrn_schema* s);
 
 // Moves of byte ranges inside device memory whose source and destination
 // may overlap (disjoint ones become plain copies); with elem (4 or 8) the

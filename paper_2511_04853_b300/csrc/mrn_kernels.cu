@@ -742,6 +742,20 @@ __global__ void k_jagged_count(const char* base, uint64_t n, uint32_t stride, ui
   if ((threadIdx.x & 31) == 0 && s) atomicAdd(total, s);
 }
 
+// The {length, begin} of every parent of a field-major jagged side, from
+// its offsets (length = offsets[i+1] - offsets[i], begin = offsets[i]), as
+// two columns: uint32 lengths and uint64 begins.  Decreasing offsets or a
+// length beyond uint32 record MRN_EINVAL.
+__global__ void k_len_begin(const char* offs, uint32_t osz, uint64_t n, unsigned int* len,
+                            unsigned long long* beg) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = read_offset(offs, osz, i), b = read_offset(offs, osz, i + 1);
+    if (b < a || b - a > 0xffffffffull) flag_error(MRN_EINVAL);
+    len[i] = (unsigned int)(b - a);
+    beg[i] = a;
+  }
+}
+
 __global__ void k_write_offset0(char* offs, uint32_t osz, unsigned long long v) {
   write_offset(offs, osz, 0, v);
 }
@@ -1570,6 +1584,14 @@ int launch_jagged_s2a(const JagPlan& jp, void* stream) {
   void* args[] = {const_cast<JagPlan*>(&jp), &pgroups};
   return cuda_status(cudaLaunchKernel(fn, dim3(grid), dim3(256), args, kConvSmem,
                                       static_cast<cudaStream_t>(stream)));
+}
+
+int launch_len_begin(const char* offsets, uint32_t off_size, uint64_t n, unsigned int* len,
+                     unsigned long long* beg, void* stream) {
+  if (n == 0) return MRN_OK;
+  const unsigned grid = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)device_sm_count() * 8);
+  k_len_begin<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(offsets, off_size, n, len, beg);
+  return cuda_status(cudaGetLastError());
 }
 
 int launch_jagged_count(const ConvPlan& parent, uint64_t* dev_total, void* stream) {

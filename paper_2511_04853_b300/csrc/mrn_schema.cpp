@@ -1,6 +1,9 @@
 // Schema builder and compiler: lowers a property description (Sec. V) to
 // flattened columns with AoS offsets, and implements the layout rules.
 #include <algorithm>
+#include <cstdio>
+#include <mutex>
+#include <map>
 #include <cstring>
 #include <new>
 
@@ -235,6 +238,46 @@ uint64_t base_bytes(const mrn_schema* s, const mrn_layout& l, uint64_t n, uint64
       if (s->has_jagged) return fm_total_bytes(s, MRN_AOSOA, l.block, n, m, m2);
       return (n + l.block - 1) / l.block * aosoa_block_bytes(s, l.block);
   }
+}
+
+const FlatParent* flat_parent_schema(const mrn_schema* s) {
+  static std::mutex mu;
+  static std::map<uint64_t, std::unique_ptr<FlatParent>> cache;  // nullptr: not reproducible
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(s->hash);
+  if (it != cache.end()) return it->second.get();
+  std::unique_ptr<FlatParent> f;
+  if (s->has_jagged && !s->interleaved && s->cols.size() + 2 <= MRN_MAX_COLS) {
+    // every field of the record in offset order, the descriptor included
+    struct Item {
+      uint32_t off;
+      int dtype;
+      int src;
+    };
+    std::vector<Item> items;
+    for (size_t c = 0; c < s->cols.size(); ++c) items.push_back({s->cols[c].aos_off, s->cols[c].dtype, (int)c});
+    items.push_back({s->len_off, MRN_U32, -1});
+    items.push_back({s->begin_off, MRN_U64, -2});
+    std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.off < b.off; });
+    f = std::make_unique<FlatParent>();
+    mrn_schema* raw = nullptr;
+    bool ok = mrn_schema_create(&raw) == MRN_OK;
+    f->schema.reset(raw);
+    for (size_t i = 0; ok && i < items.size(); ++i) {
+      char nm[16];
+      std::snprintf(nm, sizeof(nm), "f%zu", i);
+      ok = mrn_schema_add_field(raw, nm, items[i].dtype, 1) == MRN_OK;
+      f->src.push_back(items[i].src);
+    }
+    ok = ok && mrn_schema_finalize(raw) == MRN_OK;
+    // usable only when the flat record is the parent record, byte for byte
+    ok = ok && raw->stride == s->stride && raw->cols.size() == items.size();
+    for (size_t i = 0; ok && i < items.size(); ++i) ok = raw->cols[i].aos_off == items[i].off;
+    if (!ok) f.reset();
+  }
+  const FlatParent* r = f.get();
+  cache.emplace(s->hash, std::move(f));
+  return r;
 }
 
 }  // namespace mrn

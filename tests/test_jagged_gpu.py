@@ -330,3 +330,29 @@ def test_region_offsets_match_the_oracle():
         assert s.required_bytes("aosoa", n, m, B) == o.base_bytes("aosoa", B, n, m)
         for r in range(4):
             assert s.region_offset("aosoa", n, m, r, B) == o.fm_region_start("aosoa", B, n, m, r)
+
+
+@pytest.mark.parametrize("n,osz,raw", [(300001, "u32", False), (262144, "u64", True)])
+def test_large_soa_to_aos_parents_as_a_plain_conversion(n, osz, raw):
+    """From 262,144 parents a SoA -> AoS conversion builds the parents as a
+    plain conversion (their {length, begin} first as two columns): records
+    and child pool equal the oracle's, u32 and u64 offsets, raw bits."""
+    desc = [m if m[1] != "jagged" else (m[0], m[1], osz, m[3]) for m in datagen.TRACKS]
+    s, o = mrn.Schema(desc), oracle.Schema(desc)
+    d = datagen.workload("tracks", n, 17, raw=raw)
+    o_aos = oracle.pack(o, d, "aos")
+    o_soa = oracle.convert(o, o_aos, "soa", m=d["m"])
+    src = mrn.View(s, "soa", n, base=dev(o_soa.base), m=d["m"])
+    back = dev_dest(s, "aos", n, d["m"])
+    mrn.convert(src, back)
+    assert mrn.sync() == mrn.OK
+    assert np.array_equal(host(back.tensors[0], n * o.stride), o_aos.base[: n * o.stride])
+    assert np.array_equal(host(back.tensors[1], d["m"] * 8), o_aos.pool[: d["m"] * 8])
+    # decreasing offsets are reported, not read past
+    bad = o_soa.base.copy()
+    st = o.soa_region_start(n, d["m"], s.ncols)
+    osize = 4 if osz == "u32" else 8
+    bad[st + 5 * osize: st + 6 * osize] = np.full(osize, 0xFF, np.uint8)[:osize] if False else \
+        np.frombuffer(np.array([d["m"] + 10], "<u%d" % osize).tobytes(), np.uint8)
+    mrn.convert(mrn.View(s, "soa", n, base=dev(bad), m=d["m"]), dev_dest(s, "aos", n, d["m"]))
+    assert mrn.sync() == mrn.EINVAL
