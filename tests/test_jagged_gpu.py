@@ -352,7 +352,6 @@ def test_large_soa_to_aos_parents_as_a_plain_conversion(n, osz, raw):
     bad = o_soa.base.copy()
     st = o.soa_region_start(n, d["m"], s.ncols)
     osize = 4 if osz == "u32" else 8
-    bad[st + 5 * osize: st + 6 * osize] = np.full(osize, 0xFF, np.uint8)[:osize] if False else \
-        np.frombuffer(np.array([d["m"] + 10], "<u%d" % osize).tobytes(), np.uint8)
+    bad[st + 5 * osize: st + 6 * osize] = np.frombuffer(np.array([d["m"] + 10], "<u%d" % osize).tobytes(), np.uint8)
     mrn.convert(mrn.View(s, "soa", n, base=dev(bad), m=d["m"]), dev_dest(s, "aos", n, d["m"]))
     assert mrn.sync() == mrn.EINVAL
