@@ -685,6 +685,14 @@ def finish_mine(mrn, torch, stream, args, rank, world, M, batch, want, T, ms_ste
         extra["autotuner"] = {"default_shapes_ms_per_step": round(def_ms, 3), "autotuned_ms_per_step":
                               round(ms_step, 3), "gain": round(def_ms / ms_step, 4),
                               "launch_shape": dict(launch_shape, chosen_by="mrn_batch_tune"),
+                              "launch_shape_spread": {
+                                  "candidates": launch_shape.get("candidates"),
+                                  "best_ms": round(launch_shape.get("ms", 0.0), 3),
+                                  "worst_ms": round(launch_shape.get("worst_ms", 0.0), 3),
+                                  "worst_over_best": round(launch_shape.get("worst_ms", 0.0)
+                                                           / max(1e-9, launch_shape.get("ms", 1.0)), 4),
+                                  "space": "chunk {1,2,4,8,16} x CTAs per SM {occupancy, 2} for k_batch; "
+                                           "k_batch_jag has one CTA per 1,024-parent tile (no launch shape)"},
                               "pair_shapes": tuned}
     link = host_link(torch, stream) if rank == 0 else None
     e2e = run_e2e_mixed(mrn, torch, M, world, link, want)

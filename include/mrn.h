@@ -386,6 +386,9 @@ typedef struct mrn_batch_tune_result {
   uint32_t ctas_per_sm; /* resident CTAs per SM of the grid (0: occupancy)   */
   double ms;            /* device time of one launch with the winner         */
   double default_ms;    /* device time of one launch with the defaults       */
+  double worst_ms;      /* device time of the slowest shape tried            */
+  uint32_t candidates;  /* shapes timed                                      */
+  uint32_t reserved;
 } mrn_batch_tune_result;
 
 /* Autotunes the launch shape of this batch on its own jobs: times launches

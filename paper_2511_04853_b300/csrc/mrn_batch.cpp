@@ -455,8 +455,9 @@ int mrn_batch_tune(mrn_batch* b, void* stream, mrn_batch_tune_result* out) {
   const uint32_t def_chunk = b->max_chunk, def_cps = b->ctas_per_sm;
   float def_ms = 0, best_ms = 0;
   int rc = time_it(&def_ms);
-  uint32_t best_chunk = def_chunk, best_cps = def_cps;
+  uint32_t best_chunk = def_chunk, best_cps = def_cps, tried = 1;
   best_ms = def_ms;
+  float worst_ms = def_ms;
   for (uint32_t cps : {0u, 2u})
     for (uint32_t chunk : {1u, 2u, 4u, 8u, 16u}) {
       if (rc) break;
@@ -464,7 +465,10 @@ int mrn_batch_tune(mrn_batch* b, void* stream, mrn_batch_tune_result* out) {
       b->ctas_per_sm = cps;
       float t = 0;
       rc = time_it(&t);
-      if (!rc && t < best_ms) {
+      if (rc) break;
+      ++tried;
+      worst_ms = std::max(worst_ms, t);
+      if (t < best_ms) {
         best_ms = t;
         best_chunk = chunk;
         best_cps = cps;
@@ -487,6 +491,8 @@ int mrn_batch_tune(mrn_batch* b, void* stream, mrn_batch_tune_result* out) {
   out->ctas_per_sm = best_cps;
   out->ms = best_ms;
   out->default_ms = def_ms;
+  out->worst_ms = worst_ms;
+  out->candidates = tried;
   return MRN_OK;
 }
 

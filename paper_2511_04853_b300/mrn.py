@@ -63,7 +63,8 @@ class TuneResult(ctypes.Structure):
 
 class BatchTuneResult(ctypes.Structure):
     _fields_ = [("max_chunk", u32), ("ctas_per_sm", u32), ("ms", ctypes.c_double),
-                ("default_ms", ctypes.c_double)]
+                ("default_ms", ctypes.c_double), ("worst_ms", ctypes.c_double), ("candidates", u32),
+                ("reserved", u32)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -437,7 +438,8 @@ class Batch:
         launches write the destinations)."""
         r = BatchTuneResult()
         check(lib().mrn_batch_tune(self._h, _stream(stream), ctypes.byref(r)), "mrn_batch_tune")
-        return {"max_chunk": r.max_chunk, "ctas_per_sm": r.ctas_per_sm, "ms": r.ms, "default_ms": r.default_ms}
+        return {"max_chunk": r.max_chunk, "ctas_per_sm": r.ctas_per_sm, "ms": r.ms, "default_ms": r.default_ms,
+                "worst_ms": r.worst_ms, "candidates": r.candidates}
 
     def update(self, j, src, dst):
         self._pairs[j] = (src, dst)
