@@ -6,15 +6,15 @@
  * shares no code, header or table with the CUDA library.
  *
  * What it computes is the plain definition of the paper's default transfer
- * between layouts: "copy the arrays corresponding to each property one by
- * one" (Sec. VI-B, Defining Layouts), i.e. for every object and every
- * property, copy the property's bytes from its source address to its
- * destination address.  Layout rules:
+ * between layouts (Sec. VI-B, Defining Layouts), which moves the data of
+ * each property in turn: for every object and every property, copy the
+ * property's bytes from its source address to its destination address.
+ * Layout rules:
  *
  *  - Schema lowering.  Sub-group members are stored as if declared at the
  *    top level (Sec. V, sub-group property); an array property of extent E
- *    is E separate per-index columns (Sec. V, array property: "stored in
- *    separate arrays"), or, declared interleaved, one field-major column of
+ *    is E separate per-index columns (Sec. V, array property: one array
+ *    per element index), or, declared interleaved, one field-major column of
  *    E-element rows (the property's other interface, a single N x E array:
  *    record i's element k at row i, position k); a jagged
  *    vector property keeps a prefix sum of the sizes as a global property
@@ -28,7 +28,7 @@
  *    order, each starting at a multiple of 128 bytes; for a jagged schema
  *    the offsets column (N+1 entries) and the child columns (M entries
  *    each) follow.
- *  - AoSoA(B) ("allocating memory in blocks of a given size", Sec. IV):
+ *  - AoSoA(B) (Sec. IV: memory allocated in fixed-size blocks of records):
  *    each block is the C struct { T_0 c0[B]; T_1 c1[B]; ... } of the
  *    flattened columns (an interleaved array of extent E: T a[B][E]); for
  *    a jagged schema the blocks are followed, in the
@@ -51,9 +51,10 @@
  * bytes apart.
  *
  * Parity unpinned: the 128-byte SoA column alignment, the AoSoA in-block
- * arrangement, the regions of a jagged AoSoA side and the AoS jagged
- * descriptor are readings (the paper fixes no bytes for them); they are
- * checked by round trips and special cases only.
+ * arrangement, the regions of a jagged AoSoA side, the placement of a
+ * nested member's child level and the AoS jagged descriptor are readings
+ * (the paper fixes no bytes for them); they are checked by round trips and
+ * special cases only.
  */
 #include <stdint.h>
 #include <stdlib.h>

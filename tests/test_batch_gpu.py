@@ -277,7 +277,7 @@ def test_empty_jobs_in_a_batch():
             assert np.array_equal(result(d, want, name), want), "job %d (%s)" % (i, name)
 
 
-def test_cfg4_size_law_batch_matches_oracle_with_timed_launch():
+def test_mixed_size_law_batch_matches_oracle_with_timed_launch():
     """320 collections drawn as in the 4,096-collection mixed batch (seed 3:
     records round(10^U(3, 6)), schema uniform over points / cells / tracks,
     AoS source, target uniform over SoA / AoSoA(32) / AoSoA(128)), each
