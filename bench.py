@@ -857,8 +857,42 @@ def secondary(mrn, torch, stream, peak, link):
         rows["tracks_%d_soa_to_aos" % n] = row(alg, med, fastest, b2b)
         assert mrn.sync() == mrn.OK
         del recs, pool, soa
-    rows["bytes_rule"] = ("algorithmic bytes: points 32 + 25 B/record, cells 24 + 24 B/record, tracks "
-                          "40 + 16 x length B/parent (+4 B for the last offset)")
+    # the points record with its position as one interleaved f32[3] array
+    s = mrn.Schema(datagen.POINTS_INTERLEAVED)
+    n = 1 << 26
+    bufs = {}
+    for k, bk in (("aos", 0), ("soa", 0), ("aosoa", 32)):
+        bufs[(k, bk)] = torch.full((s.required_bytes(k, n, 0, bk),), 0x3C, dtype=torch.uint8, device="cuda")
+    for sk, sb, dk, db in (("aos", 0, "soa", 0), ("soa", 0, "aos", 0), ("aos", 0, "aosoa", 32),
+                           ("aosoa", 32, "aos", 0)):
+        src = mrn.View(s, sk, n, block=sb, base=bufs[(sk, sb)])
+        dst = mrn.View(s, dk, n, block=db, base=bufs[(dk, db)])
+        med, fastest = time_conv(src, dst, 10)
+        rows["points_interleaved_%d_%s%s_to_%s%s" % (n, sk, sb or "", dk, db or "")] = row(n * (32 + 25), med,
+                                                                                          fastest)
+    assert mrn.sync() == mrn.OK
+    del bufs
+    # nested jagged tracks (hits with samples), canonical pools
+    s = mrn.Schema(datagen.TRACKS_NESTED)
+    n = 1 << 21
+    m, m2, recs, pool, gpool = nested_aos(torch, s, n)
+    alg = nested_alg_bytes(n, m, m2)
+    a_view = mrn.View(s, "aos", n, base=recs, child_pool=pool, m=m, m2=m2, grandchild_pool=gpool)
+    for kind, blk in (("soa", 0), ("aosoa", 32)):
+        fm = torch.empty(s.required_bytes_nested(kind, n, m, m2, blk), dtype=torch.uint8, device="cuda")
+        f_view = mrn.View(s, kind, n, block=blk, base=fm, m=m, m2=m2)
+        med, fastest = time_conv(a_view, f_view, 10)
+        rows["tracks_nested_%d_aos_to_%s%s" % (n, kind, blk or "")] = dict(row(alg, med, fastest), children=m,
+                                                                            grandchildren=m2)
+        back = mrn.View(s, "aos", n, base=recs, child_pool=pool, m=m, m2=m2, grandchild_pool=gpool)
+        med, fastest = time_conv(f_view, back, 10)
+        rows["tracks_nested_%d_%s%s_to_aos" % (n, kind, blk or "")] = row(alg, med, fastest)
+        assert mrn.sync() == mrn.OK
+        del fm
+    del recs, pool, gpool
+    rows["bytes_rule"] = ("algorithmic bytes: points 32 + 25 B/record (interleaved too), cells 24 + 24 B/record, "
+                          "tracks 40 + 16 x length B/parent (+4 B for the last offset), nested tracks "
+                          "40 B/parent + 36 B/hit + 8 B/sample (+8 B for the last offsets)")
     out["single_collection"] = rows
     del flush
     out["transfer_chunk_sweep"] = chunk_sweep(mrn, torch, stream, link)
@@ -1381,8 +1415,19 @@ def run_case(args):
         k, _, b = x.partition("/")
         return k, int(b or 0)
     (sk, sb), (dk, db) = lay(sk), lay(dk)
-    s = mrn.Schema(datagen.WORKLOAD_SCHEMAS[name])
-    if s.has_jagged:
+    schemas = dict(datagen.WORKLOAD_SCHEMAS, **datagen.INTERLEAVED_SCHEMAS, **datagen.NESTED_SCHEMAS)
+    s = mrn.Schema(schemas[name])
+    if name in datagen.NESTED_SCHEMAS:
+        m, m2, aos, pool, gpool = nested_aos(torch, s, n)
+        fm = torch.empty(s.required_bytes_nested(dk if sk == "aos" else sk, n, m, m2, db if sk == "aos" else sb),
+                         dtype=torch.uint8, device="cuda")
+        a_view = mrn.View(s, "aos", n, base=aos, child_pool=pool, m=m, m2=m2, grandchild_pool=gpool)
+        f_view = mrn.View(s, dk if sk == "aos" else sk, n, block=db if sk == "aos" else sb, base=fm, m=m, m2=m2)
+        src, dst = (a_view, f_view) if sk == "aos" else (f_view, a_view)
+        if sk != "aos":
+            mrn.convert(a_view, f_view)
+        nbytes = nested_alg_bytes(n, m, m2)
+    elif s.has_jagged:
         m, aos, pool = jagged_aos(torch, s, n)
         soa = torch.empty(s.required_bytes("soa", n, m), dtype=torch.uint8, device="cuda")
         a_view = mrn.View(s, "aos", n, base=aos, child_pool=pool, m=m)
@@ -1395,7 +1440,7 @@ def run_case(args):
         a = torch.full((s.required_bytes(sk, n, 0, sb),), 0x3C, dtype=torch.uint8, device="cuda")
         b = torch.empty(s.required_bytes(dk, n, 0, db), dtype=torch.uint8, device="cuda")
         src, dst = mrn.View(s, sk, n, block=sb, base=a), mrn.View(s, dk, n, block=db, base=b)
-        nbytes = 2 * n * s.stride
+        nbytes = n * (s.stride + sum(c["size"] for c in s.columns))  # AoS record + packed fields
     for _ in range(args.warmup):
         mrn.convert(src, dst)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1426,6 +1471,47 @@ def jagged_aos(torch, s, n, seed=2):
     rv[:, 16:24].copy_(begs.view(torch.uint8).view(n, 8))
     pool = torch.full((max(1, m * 8),), 7, dtype=torch.uint8, device="cuda")
     return m, recs, pool
+
+
+def nested_aos(torch, s, n, seed=5):
+    """Nested jagged AoS (tracks with hits with samples) with canonical
+    pools: parent lengths min(Poisson(20), 256) from the seeded generator,
+    per-hit sample counts min(Poisson(3), 32) drawn on the device; returns
+    (children, grandchildren, records, child pool, grandchild pool)."""
+    import numpy as np
+    import datagen
+    import paper_2511_04853_b300 as mrn
+    ch = mrn.Schema(datagen.TRACKS_NESTED[3][3])  # the hit record, with its own jagged member
+    assert s.stride == 24 and s.info.jag_length_offset == 12 and s.info.jag_begin_offset == 16
+    assert ch.stride == 24 and ch.info.jag_length_offset == 8 and ch.info.jag_begin_offset == 16
+    d = datagen.workload("tracks", n, seed)
+    m = d["m"]
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+
+    def records(count, stride, lens, len_off, beg_off):
+        r = torch.randint(0, 256, (max(1, count * stride),), dtype=torch.uint8, device="cuda", generator=g)
+        rv = r[: count * stride].view(count, stride)
+        begs = torch.cumsum(lens.to(torch.int64), 0) - lens.to(torch.int64)
+        rv[:, len_off:len_off + 4].copy_(lens.to(torch.int32).view(torch.uint8).view(count, 4))
+        rv[:, len_off + 4:beg_off].zero_()  # the padding before the begin
+        rv[:, beg_off:beg_off + 8].copy_(begs.view(torch.uint8).view(count, 8))
+        return r
+    lens = torch.from_numpy(d["lengths"].astype(np.int32)).cuda()
+    recs = records(n, 24, lens, 12, 16)
+    l1 = torch.poisson(torch.full((max(1, m),), 3.0, device="cuda"), generator=g).clamp_(max=32)[:m].to(torch.int32)
+    m2 = int(l1.sum().item())
+    pool = records(m, 24, l1, 8, 16)
+    gpool = torch.randint(0, 256, (max(1, m2 * 4),), dtype=torch.uint8, device="cuda", generator=g)
+    return m, m2, recs, pool, gpool
+
+
+def nested_alg_bytes(n, m, m2):
+    """AoS <-> field-major of the nested tracks: records 24 B per parent and
+    per hit and 4 B per sample read; 12 B of parent columns, 8 B of hit
+    columns, 4 B of sample columns and one 4-byte offset per parent and per
+    hit (plus the last of each level) written."""
+    return 24 * n + 24 * m + 4 * m2 + 12 * n + 4 * (n + 1) + 8 * m + 4 * (m + 1) + 4 * m2
 
 
 def main():

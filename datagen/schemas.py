@@ -90,8 +90,16 @@ PARTICLE = [
     ("noisy_count", "u8", SENSOR_TYPES),
 ]
 
+# The points collection with its position as one interleaved f32[3] array
+# property (one N x 3 array field-major): the same AoS record as POINTS.
+POINTS_INTERLEAVED = [
+    ("pos", "f32", 3, "interleaved"),
+    ("id", "i32", 1), ("key", "u64", 1), ("flag", "u8", 1),
+]
+
 WORKLOAD_SCHEMAS = {"points": POINTS, "cells": CELLS, "tracks": TRACKS}
 NESTED_SCHEMAS = {"tracks_nested": TRACKS_NESTED}
+INTERLEAVED_SCHEMAS = {"points_interleaved": POINTS_INTERLEAVED}
 
 
 def leaves(schema, prefix=""):

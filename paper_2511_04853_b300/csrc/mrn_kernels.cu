@@ -409,7 +409,11 @@ __device__ __forceinline__ unsigned long long jagged_lookback(const JagPlan& jp,
                                                               const unsigned long long* st, int lane) {
   unsigned long long prefix = 0;
   long long j = (long long)tile - 1;  // highest tile not yet accumulated
-  const unsigned long long deadline = global_ns() + jp.timeout_ns;
+  // One deadline for the whole warp (lanes may arrive at different times,
+  // e.g. after lane 0 alone stored to shared memory), and one decision when
+  // it expires: a lane that left the loop alone would leave the others in
+  // a warp-wide ballot it never reaches.
+  const unsigned long long deadline = __shfl_sync(0xffffffffu, global_ns() + jp.timeout_ns, 0);
   unsigned int spins = 0;
   while (j >= 0) {
     const long long jj = j - lane;
@@ -419,7 +423,7 @@ __device__ __forceinline__ unsigned long long jagged_lookback(const JagPlan& jp,
     const unsigned int zero = __ballot_sync(0xffffffffu, fl == 0);
     const unsigned int upto = pref ? ((pref & (0u - pref)) << 1) - 1u : 0xffffffffu;  // lanes to sum
     if (zero & upto) {
-      if (global_ns() > deadline || ++spins > (1u << 24)) {
+      if (__any_sync(0xffffffffu, global_ns() > deadline || ++spins > (1u << 24))) {
         if (lane == 0) flag_error(MRN_ETIMEOUT);
         break;
       }
