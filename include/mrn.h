@@ -301,11 +301,23 @@ int mrn_jagged_count(const mrn_view* src, uint64_t* m, void* stream);
 
 /* Test and fault-injection settings (host side; they take effect for
  * conversions planned afterwards):
- *   key 1: index of a tile that never publishes its sum (-1: none), so that
+ *   key 1: index of a jagged tile (in a split run: a scan chunk of 8,192
+ *          parents) that never publishes its sum (-1: none), so that
  *          its successors' bounded waits expire and record MRN_ETIMEOUT;
  *   key 2: bound of each look-back wait in nanoseconds (default 2e9);
  *   key 3: 1 = single conversions use the direct kernel (vector loads and
- *          stores per lane) even where the TMA-staged kernel applies. */
+ *          stores per lane) even where the TMA-staged kernel applies;
+ *   key 4: parents from which a single jagged AoS -> SoA / AoSoA conversion
+ *          runs split (default: never, the fused kernel is faster for one
+ *          collection at every size measured): a scan of the lengths in chunks
+ *          (offsets' bases, and a check that the pool is canonical: its
+ *          records are exactly the children, in parent order), the parents
+ *          as one staged conversion that also writes the offsets, the pool
+ *          as one staged conversion of the child schema when it is
+ *          canonical, and a pass that gathers the children when it is not.
+ *          Batches split every jagged AoS job whose pool fits the
+ *          destination's child capacity.  A negative value turns split runs
+ *          off (single conversions and batches). */
 int mrn_debug_set(int key, long long value);
 
 /* ------------------------------------------------------- transfer+convert */
@@ -353,11 +365,18 @@ typedef struct mrn_job {
 typedef struct mrn_batch mrn_batch; /* opaque */
 
 /* Prepares many independent conversions (any schemas, any supported layout
- * pairs, jagged AoS<->SoA included) to run in one persistent kernel launch,
- * plus one launch for all the jagged AoS -> field-major jobs (one CTA per
- * tile of 1,024 parents, which their scan and gather need): a device job
- * table, a prefix over the jobs' tiles, per-job tile sizes from the
- * autotuner cache.  With use_graph = 1 the launch sequence (scratch reset +
+ * pairs, jagged AoS<->SoA included) to run in one persistent kernel launch:
+ * a device job table, a prefix over the jobs' tiles, per-job tile sizes
+ * from the autotuner cache.  A jagged AoS -> field-major job runs split
+ * where it can (see mrn_debug_set, key 4): one launch before the persistent
+ * one scans the lengths of all such jobs (chunks of 8,192 parents), and the
+ * persistent launch converts their parents (writing the offsets) and their
+ * child pools (each a plain conversion, run when the scan found the pool
+ * canonical); a last launch gathers the children of any pool that was not
+ * (it returns at once when every pool was).  Jagged jobs that cannot run
+ * split (a pool larger than the destination's child capacity) run in one
+ * more launch before the persistent one, one CTA per tile of 1,024 parents
+ * that scans, converts and gathers.  With use_graph = 1 the launch sequence (scratch reset +
  * the launches) is captured once into a CUDA graph and each mrn_batch_launch
  * replays it.  The views' buffers must stay valid while the batch is used.
  * Copies the job descriptions; `jobs` may be freed. */
@@ -366,8 +385,9 @@ int mrn_batch_create(const mrn_job* jobs, size_t n_jobs, int use_graph, mrn_batc
 int mrn_batch_launch(mrn_batch* b, void* stream);
 /* As mrn_batch_launch, and records three caller-created CUDA events
  * (cudaEvent_t, passed as void*) on `stream`: ev_begin before the batch's
- * work, ev_mid after the persistent launch of the non-jagged jobs (and the
- * scratch reset before it), ev_end after the launch of the jagged AoS jobs.
+ * work, ev_mid after the scratch reset, the split jobs' scan and the fused
+ * jagged launch, ev_end after the persistent launch and the fall-back
+ * gather.
  * With use_graph = 1 the events are record nodes of a second graph of the
  * same work, captured at the first call and pointed at the given events at
  * each call; a batch without jobs of one kind records two events back to

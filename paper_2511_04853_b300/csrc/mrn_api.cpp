@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <climits>
 #include <cstring>
 #include <mutex>
 
@@ -17,6 +18,13 @@ std::atomic<long long> g_skip_publish_tile{-1};
 std::atomic<unsigned long long> g_timeout_ns{2000000000ull};
 // When set, conversions use the direct kernel even when they could be staged.
 std::atomic<int> g_force_direct{0};
+// Parents from which a single jagged AoS -> field-major conversion runs
+// split (scan, parents, pool conversion, fall-back pass); by default never:
+// measured at 100,000 to 4,194,304 parents, its four launches lose to the
+// fused kernel (4,194,304: 308 against 267 us).  Batches split their
+// jagged jobs (in one persistent launch the pools stream at the copy
+// rate) unless the value is negative.
+std::atomic<long long> g_split_parents{LLONG_MAX};
 
 namespace {
 
@@ -432,6 +440,22 @@ int jagged_children_plan(const mrn_schema* s, const JagPlan& jp, ConvPlan* out) 
   return MRN_OK;
 }
 
+int jagged_pool_plan(const mrn_schema* s, const JagPlan& jp, ConvPlan* out) {
+  *out = jp.child;
+  out->n = out->n_fm_pad = jp.pool_n;
+  tile_geometry(s->child.get(), out, MRN_BATCH_STAGE_BYTES);
+  return MRN_OK;
+}
+
+bool jagged_split_ok(const mrn_schema* s, JagPlan* jp, ConvPlan* pool) {
+  if (g_split_parents.load() < 0 || jp->parent.n == 0 || jp->pool_n == 0 || jp->pool_n > jp->capacity) return false;
+  if (jagged_pool_plan(s, *jp, pool) != MRN_OK || !pool->tg.tma) return false;
+  tile_geometry(s, &jp->parent, MRN_BATCH_STAGE_BYTES);
+  // a staged tile's groups: at most three per consumer warp
+  if (jp->parent.tg.tma && jp->parent.tg.T > 768) jp->parent.tg.tma = 0;
+  return true;
+}
+
 int build_jagged_plan(const mrn_view& src, const mrn_view& dst, JagPlan* jp) {
   const mrn_schema* s = src.schema;
   std::memset(jp, 0, sizeof(*jp));
@@ -444,6 +468,7 @@ int build_jagged_plan(const mrn_view& src, const mrn_view& dst, JagPlan* jp) {
   if (rc) return rc;
   jp->off_size = s->off_size;
   jp->len_off = s->len_off;
+  jp->begin_off = s->begin_off;
   char* offs = fm_offsets(soa);
   if (!offs) return MRN_EINVAL;
   if (reinterpret_cast<uintptr_t>(offs) % s->off_size) return MRN_EALIGN;
@@ -569,11 +594,18 @@ int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
           jp.gap_len[k] = g[0].len[k];
         }
       }
+      // Large collections run split: their children become one staged
+      // conversion of the pool when the pool turns out canonical.
+      ConvPlan pool;
+      const long long lim = g_split_parents.load();
+      const bool split = lim >= 0 && src->n_records >= (uint64_t)lim && jagged_split_ok(s, &jp, &pool) &&
+                         jp.parent.tg.tma;
       if (src->n_records > 0) {
-        if (cudaMallocAsync(&scratch, jagged_scratch_bytes(jagged_tile_records(jp)), st) != cudaSuccess)
-          return MRN_ENOMEM;
+        const uint64_t sb = split ? jagged_split_scratch_bytes(src->n_records)
+                                  : jagged_scratch_bytes(jagged_tile_records(jp));
+        if (cudaMallocAsync(&scratch, sb, st) != cudaSuccess) return MRN_ENOMEM;
       }
-      rc = launch_jagged_a2s(jp, scratch, stream);
+      rc = split ? launch_jagged_a2s_split(jp, pool, scratch, stream) : launch_jagged_a2s(jp, scratch, stream);
       if (scratch) cudaFreeAsync(scratch, st);
       if (rc) return rc;
       if (fold) return MRN_OK;
@@ -699,6 +731,7 @@ int mrn_debug_set(int key, long long value) {
       g_timeout_ns.store((unsigned long long)value);
       return MRN_OK;
     case 3: g_force_direct.store(value ? 1 : 0); return MRN_OK;
+    case 4: g_split_parents.store(value < 0 ? -1 : value); return MRN_OK;
     default: return MRN_EINVAL;
   }
 }

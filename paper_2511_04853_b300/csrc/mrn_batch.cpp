@@ -30,10 +30,21 @@ struct mrn_batch {
   unsigned long long* d_first = nullptr;
   BatchJob* d_jag = nullptr;
   unsigned int* d_tile_job = nullptr;
-  // counters (k_batch at 0, k_batch_jag at 64), then one look-back word per
-  // jagged tile
+  // counters (k_batch at 0, k_batch_jag at 64, k_jag_scan at 192), the
+  // word "some split jagged job's pool is not canonical" at 128, one
+  // look-back word per fused jagged tile from 256, one per scan chunk of
+  // the split jagged jobs, one "pool not canonical" word per jagged job
+  // (d_flags); these are cleared before each launch (clear_bytes).  Then
+  // the split jobs' group bases, which the scan overwrites.
   char* d_scratch = nullptr;
-  size_t scratch_bytes = 0;
+  size_t scratch_bytes = 0, clear_bytes = 0;
+  unsigned int* d_flags = nullptr;
+  // split jagged jobs: the scan's chunks (chunk -> index in jag), and the
+  // most fall-back tiles of one of them
+  std::vector<unsigned int> chunk_job;
+  unsigned int* d_chunk_job = nullptr;
+  unsigned long long total_chunks = 0, max_rest_tiles = 0;
+  size_t n_split = 0;
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -59,6 +70,7 @@ struct mrn_batch {
     cudaFree(d_first);
     cudaFree(d_jag);
     cudaFree(d_tile_job);
+    cudaFree(d_chunk_job);
     cudaFree(d_scratch);
   }
   void drop_timed() {
@@ -107,6 +119,36 @@ void convert_tiles(BatchJob* j) {
   if (p.tg.tma) fill_stage_rec(p, &j->stage);
 }
 
+// Tiles of the parents job of a split jagged job: the staged tiles of its
+// parent plan, or direct tiles of 1,024 records.
+void parent_tiles(BatchJob* j) {
+  const ConvPlan& p = j->jp.parent;
+  const uint64_t nrec = p.n_fm_pad > p.n ? p.n_fm_pad : p.n;
+  if (p.tg.tma) {
+    j->tile_records = p.tg.T;
+    j->ntiles = staged_tile_count(p.n, nrec, p.tg.T, p.tg.G);
+    fill_stage_rec(p, &j->stage);
+  } else {
+    j->tile_records = 1024;
+    j->ntiles = (nrec + 1023) / 1024;
+  }
+}
+
+// Zero-fill jobs of a destination's alignment holes.
+int push_gap_jobs(const mrn_view& dst, std::vector<BatchJob>* out) {
+  GapPlan g[2];
+  const int np = gap_plans_of(dst, g);
+  for (int i = 0; i < np; ++i) {
+    BatchJob z;
+    std::memset(&z, 0, sizeof(z));
+    z.kind = JOB_ZERO;
+    z.gp = g[i];
+    z.ntiles = (g[i].nblocks * g[i].ngaps + 255) / 256;
+    out->push_back(z);
+  }
+  return MRN_OK;
+}
+
 // Plans one job (everything but tile_begin), followed by a zero-fill job
 // when the destination has alignment holes.
 int plan_job(const mrn_view& src, const mrn_view& dst, std::vector<BatchJob>* out) {
@@ -124,6 +166,28 @@ int plan_job(const mrn_view& src, const mrn_view& dst, std::vector<BatchJob>* ou
       j.kind = JOB_JAG_A2S;
       // an empty collection still has one tile: it writes offsets[0]
       j.ntiles = std::max<uint64_t>(1, (jagged_tile_records(j.jp) + MRN_JAG_TILE - 1) / MRN_JAG_TILE);
+      // Split: the scan (this job's chunks in k_jag_scan), the parents'
+      // data columns and offsets, and the pool (skipped unless canonical)
+      // as jobs of k_batch, and this job's tiles as the fall-back pass.
+      BatchJob kids;
+      std::memset(&kids, 0, sizeof(kids));
+      if (jagged_split_ok(src.schema, &j.jp, &kids.jp.parent)) {
+        j.jp.mode = JAG_SPLIT;
+        j.jp.nchunks = (src.n_records + MRN_SCAN_CHUNK - 1) / MRN_SCAN_CHUNK;
+        j.jp.ntiles = j.ntiles;  // the fall-back pass's tiles
+        out->push_back(j);
+        BatchJob par;
+        std::memset(&par, 0, sizeof(par));
+        par.kind = JOB_JAG_PARENTS;
+        par.jp = j.jp;
+        parent_tiles(&par);
+        par.jag_link = ~0u;  // the jagged job just before it (resolved with the tables)
+        out->push_back(par);
+        convert_tiles(&kids);
+        kids.cond = kids.jag_link = ~0u;
+        out->push_back(kids);
+        return push_gap_jobs(dst, out);
+      }
     } else {
       // children: a plain conversion job; this job builds the parents
       BatchJob kids;
@@ -143,23 +207,14 @@ int plan_job(const mrn_view& src, const mrn_view& dst, std::vector<BatchJob>* ou
     convert_tiles(&j);
   }
   out->push_back(j);
-  GapPlan g[2];
-  const int np = gap_plans_of(dst, g);
-  for (int i = 0; i < np; ++i) {
-    BatchJob z;
-    std::memset(&z, 0, sizeof(z));
-    z.kind = JOB_ZERO;
-    z.gp = g[i];
-    z.ntiles = (g[i].nblocks * g[i].ngaps + 255) / 256;
-    out->push_back(z);
-  }
-  return MRN_OK;
+  return push_gap_jobs(dst, out);
 }
 
 // Approximate bytes read and written by one tile of a job of k_batch.
 double tile_traffic(const BatchJob& j) {
   switch (j.kind) {
     case JOB_CONVERT:
+    case JOB_JAG_PARENTS:
       return (double)j.tile_records * 2.0 * j.jp.parent.stride;
     case JOB_JAG_S2A:
       return 8.0 * 32.0 * 2.0 * j.jp.parent.stride;
@@ -182,8 +237,23 @@ int rebuild_tables(mrn_batch* b) {
   b->first_tile.clear();
   b->tile_job.clear();
   unsigned long long t = 0, tj = 0;
+  b->n_split = 0;
+  b->chunk_job.clear();
+  b->total_chunks = b->max_rest_tiles = 0;
   for (BatchJob& j : b->jobs) {
-    if (j.kind == JOB_JAG_A2S) {
+    // 1 + the last jagged job (a split job's parents and pool follow it)
+    if (j.cond == ~0u) j.cond = (uint32_t)b->jag.size();
+    if (j.jag_link == ~0u) j.jag_link = (uint32_t)b->jag.size();
+    if (j.kind == JOB_JAG_A2S && j.jp.mode == JAG_SPLIT) {
+      ++b->n_split;
+      j.jp.chunk_begin = b->total_chunks;
+      if (b->total_chunks + j.jp.nchunks > 0x7fffffffull) return MRN_EUNSUPPORTED;
+      b->chunk_job.insert(b->chunk_job.end(), j.jp.nchunks, (unsigned int)b->jag.size());
+      b->total_chunks += j.jp.nchunks;
+      b->max_rest_tiles = std::max<unsigned long long>(b->max_rest_tiles, j.ntiles);
+      b->where.push_back({1, b->jag.size()});
+      b->jag.push_back(j);
+    } else if (j.kind == JOB_JAG_A2S) {
       j.tile_begin = tj;
       b->where.push_back({1, b->jag.size()});
       if (tj + j.ntiles > 0x7fffffffull) return MRN_EUNSUPPORTED;
@@ -214,12 +284,42 @@ int upload(mrn_batch* b) {
   // the tile index is read by whole 16-byte pieces (L2 prefetch)
   const size_t fb = align_up(std::max<size_t>(1, b->first_tile.size()) * sizeof(unsigned long long), 16);
   const size_t tb = std::max<size_t>(1, b->tile_job.size()) * sizeof(unsigned int);
-  b->scratch_bytes = 256 + (size_t)b->jag_tiles * sizeof(unsigned long long);
+  const size_t cb = std::max<size_t>(1, b->chunk_job.size()) * sizeof(unsigned int);
+  const size_t chunks_at = 256 + (size_t)b->jag_tiles * sizeof(unsigned long long);
+  const size_t flags_at = chunks_at + (size_t)b->total_chunks * sizeof(unsigned long long);
+  b->clear_bytes = flags_at + std::max<size_t>(1, b->jag.size()) * sizeof(unsigned int);
+  const size_t groups_at = align_up(b->clear_bytes, 256);
+  size_t ngroups = 0;
+  for (const BatchJob& j : b->jag)
+    if (j.jp.mode == JAG_SPLIT) ngroups += (size_t)(j.jp.parent.n + 31) / 32;
+  b->scratch_bytes = groups_at + ngroups * sizeof(unsigned long long);
   if (cudaMalloc(&b->d_jobs, jb) != cudaSuccess || cudaMalloc(&b->d_first, fb) != cudaSuccess ||
       cudaMalloc(&b->d_jag, gb) != cudaSuccess || cudaMalloc(&b->d_tile_job, tb) != cudaSuccess ||
-      cudaMalloc(&b->d_scratch, b->scratch_bytes) != cudaSuccess) {
+      cudaMalloc(&b->d_chunk_job, cb) != cudaSuccess || cudaMalloc(&b->d_scratch, b->scratch_bytes) != cudaSuccess) {
     cudaGetLastError();
     return MRN_ENOMEM;
+  }
+  b->d_flags = reinterpret_cast<unsigned int*>(b->d_scratch + flags_at);
+  // split jagged jobs: their pool word, chunk words and group bases in the
+  // scratch; their parents jobs write the offsets from the same bases
+  unsigned long long* chunks = reinterpret_cast<unsigned long long*>(b->d_scratch + chunks_at);
+  unsigned long long* groups = reinterpret_cast<unsigned long long*>(b->d_scratch + groups_at);
+  size_t g = 0;
+  for (size_t k = 0; k < b->jobs.size(); ++k) {
+    BatchJob& j = b->jobs[k];
+    if (j.kind != JOB_JAG_A2S || j.jp.mode != JAG_SPLIT) continue;
+    j.jp.noncanon = b->d_flags + b->where[k].second;
+    j.jp.any_noncanon = reinterpret_cast<unsigned int*>(b->d_scratch + 128);
+    j.jp.chunk_state = chunks + j.jp.chunk_begin;
+    j.jp.group_base = groups + g;
+    g += (size_t)(j.jp.parent.n + 31) / 32;
+    b->jag[b->where[k].second] = j;
+  }
+  for (size_t k = 0; k < b->jobs.size(); ++k) {
+    BatchJob& j = b->jobs[k];
+    if (j.kind != JOB_JAG_PARENTS) continue;
+    j.jp.group_base = b->jag[j.jag_link - 1].jp.group_base;
+    b->plain[b->where[k].second] = j;
   }
   auto put = [](void* d, const void* h, size_t n) {
     return n == 0 || cudaMemcpy(d, h, n, cudaMemcpyHostToDevice) == cudaSuccess;
@@ -227,30 +327,42 @@ int upload(mrn_batch* b) {
   if (!put(b->d_jobs, b->plain.data(), b->plain.size() * sizeof(BatchJob)) ||
       !put(b->d_first, b->first_tile.data(), b->first_tile.size() * sizeof(unsigned long long)) ||
       !put(b->d_jag, b->jag.data(), b->jag.size() * sizeof(BatchJob)) ||
-      !put(b->d_tile_job, b->tile_job.data(), b->tile_job.size() * sizeof(unsigned int)))
+      !put(b->d_tile_job, b->tile_job.data(), b->tile_job.size() * sizeof(unsigned int)) ||
+      !put(b->d_chunk_job, b->chunk_job.data(), b->chunk_job.size() * sizeof(unsigned int)))
     return MRN_ECUDA;
   return MRN_OK;
 }
 
-// The batch's work on `s`: scratch reset, the persistent launch of the plain
-// jobs, the launch of the jagged jobs.  With `ev`, ev[0] is recorded first,
-// ev[1] between the two kernels and ev[2] last (`evflags` as for
-// cudaEventRecordWithFlags; cudaEventRecordExternal makes them graph nodes
-// during capture).
+// The batch's work on `s`: scratch reset, the scan of the split jagged AoS
+// jobs (k_jag_scan) and the launch of the fused ones (k_batch_jag), the
+// persistent launch of all other jobs (k_batch: plain conversions, the
+// split jobs' parents and pools), and the split jobs' fall-back pass
+// (k_batch_jag_rest).  With `ev`, ev[0] is recorded first, ev[1] before
+// k_batch and ev[2] last (`evflags` as for cudaEventRecordWithFlags;
+// cudaEventRecordExternal makes them graph nodes during capture).
 int enqueue(mrn_batch* b, cudaStream_t s, const cudaEvent_t* ev = nullptr, unsigned evflags = 0) {
   auto mark = [&](int i) { return !ev || cudaEventRecordWithFlags(ev[i], s, evflags) == cudaSuccess; };
   if (!mark(0)) return MRN_ECUDA;
   int rc = MRN_OK;
-  if (b->total_tiles || b->jag_tiles) {
-    if (cudaMemsetAsync(b->d_scratch, 0, b->scratch_bytes, s) != cudaSuccess) return MRN_ECUDA;
-    if (b->total_tiles)
-      rc = launch_batch(b->d_jobs, b->d_first, (unsigned)b->plain.size(), b->total_tiles,
-                        reinterpret_cast<unsigned int*>(b->d_scratch), b->ctas_per_sm, b->max_chunk, s);
+  if (b->total_tiles || b->jag_tiles || b->total_chunks) {
+    if (cudaMemsetAsync(b->d_scratch, 0, b->clear_bytes, s) != cudaSuccess) return MRN_ECUDA;
   }
-  if (!rc && !mark(1)) rc = MRN_ECUDA;
+  // the scan of the split jagged jobs and the fused jagged tiles first: the
+  // split jobs' parents and pools (jobs of k_batch) need the scan's bases
+  // and pool checks
+  if (b->total_chunks)
+    rc = launch_jag_scan(b->d_jag, b->d_chunk_job, b->total_chunks,
+                         reinterpret_cast<unsigned int*>(b->d_scratch + 192), s);
   if (!rc && b->jag_tiles)
     rc = launch_batch_jag(b->d_jag, b->d_tile_job, b->jag_tiles, reinterpret_cast<unsigned int*>(b->d_scratch + 64),
                           reinterpret_cast<unsigned long long*>(b->d_scratch + 256), s);
+  if (!rc && !mark(1)) rc = MRN_ECUDA;
+  if (!rc && b->total_tiles)
+    rc = launch_batch(b->d_jobs, b->d_first, (unsigned)b->plain.size(), b->total_tiles,
+                      reinterpret_cast<unsigned int*>(b->d_scratch), b->ctas_per_sm, b->max_chunk, s, b->d_flags);
+  if (!rc && b->n_split)
+    rc = launch_batch_jag_rest(b->d_jag, (unsigned)b->jag.size(), b->max_rest_tiles, b->d_flags,
+                               reinterpret_cast<unsigned int*>(b->d_scratch + 128), s);
   if (!rc && !mark(2)) rc = MRN_ECUDA;
   return rc;
 }
@@ -407,10 +519,20 @@ int mrn_batch_update(mrn_batch* b, size_t j, const mrn_view* src, const mrn_view
   const size_t next = j + 1 < b->first_entry.size() ? b->first_entry[j + 1] : b->jobs.size();
   if (fresh.size() != next - k) return MRN_EINVAL;
   for (size_t i = 0; i < fresh.size(); ++i) {
-    if (fresh[i].ntiles != b->jobs[k + i].ntiles ||
-        (fresh[i].kind == JOB_JAG_A2S) != (b->jobs[k + i].kind == JOB_JAG_A2S))
+    const BatchJob& old = b->jobs[k + i];
+    if (fresh[i].ntiles != old.ntiles || fresh[i].kind != old.kind || (fresh[i].cond != 0) != (old.cond != 0) ||
+        (fresh[i].kind == JOB_JAG_A2S && fresh[i].jp.mode != old.jp.mode))
       return MRN_EINVAL;
-    fresh[i].tile_begin = b->jobs[k + i].tile_begin;
+    fresh[i].tile_begin = old.tile_begin;
+    fresh[i].cond = old.cond;
+    fresh[i].jag_link = old.jag_link;
+    if (fresh[i].kind == JOB_JAG_A2S || fresh[i].kind == JOB_JAG_PARENTS) {
+      fresh[i].jp.noncanon = old.jp.noncanon;
+      fresh[i].jp.any_noncanon = old.jp.any_noncanon;
+      fresh[i].jp.chunk_state = old.jp.chunk_state;
+      fresh[i].jp.group_base = old.jp.group_base;
+      fresh[i].jp.chunk_begin = old.jp.chunk_begin;
+    }
   }
   for (int q = 0; q < 4; ++q) b->cols[4 * j + q] = std::move(c[q]);
   own_view(*src, &b->cols[4 * j], &b->cols[4 * j + 1], &b->src[j]);

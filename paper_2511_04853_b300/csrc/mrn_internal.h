@@ -135,7 +135,8 @@ struct LaunchShape {
   uint32_t tile_records = 0; // direct kernel: records per tile (0: default)
   uint32_t generic = 0;      // 1: direct kernel even when the plan can be staged
 };
-int launch_convert(const ConvPlan& p, void* stream, const LaunchShape* shape);
+// With `cond` (staged plans only) the launch does nothing when *cond != 0.
+int launch_convert(const ConvPlan& p, void* stream, const LaunchShape* shape, const unsigned int* cond = nullptr);
 // The stage table of a staged plan (header and column descriptors).
 void fill_stage_rec(const ConvPlan& p, StageRec* out);
 int launch_zero_gaps(const GapPlan& g, void* stream);
@@ -143,7 +144,24 @@ int launch_zero_gaps(const GapPlan& g, void* stream);
 // jagged_scratch_bytes(n) bytes; it is cleared on `stream` first.
 uint64_t jagged_scratch_bytes(uint64_t n);
 int launch_jagged_a2s(JagPlan& jp, void* scratch, void* stream);
+// The same conversion split (JAG_SPLIT): the scan (group bases, offsets[n],
+// the check that the pool is canonical), the parents' data columns and
+// offsets as one staged conversion, the pool's records as one staged
+// conversion `pool` of the child schema into the child rows when it is
+// canonical, and a pass in which the tiles gather their children when it is
+// not.  jp.parent and `pool` must be staged; n > 0; `scratch` holds
+// jagged_split_scratch_bytes(n) bytes.
+uint64_t jagged_split_scratch_bytes(uint64_t n, size_t* group_at = nullptr);
+int launch_jagged_a2s_split(JagPlan& jp, const ConvPlan& pool, void* scratch, void* stream);
 int launch_jagged_s2a(const JagPlan& jp, void* stream);
+// The child pool of a jagged AoS -> field-major plan as a plain conversion of
+// the child schema (pool record j -> child row j, j < pool_n), with tiles.
+int jagged_pool_plan(const mrn_schema* s, const JagPlan& jp, ConvPlan* out);
+// True when a jagged AoS -> field-major plan can run split (split runs are
+// enabled, the pool fits the destination's child capacity and its
+// conversion can be staged); fills *pool and gives jp->parent its staged
+// tiles where it can have them.
+bool jagged_split_ok(const mrn_schema* s, JagPlan* jp, ConvPlan* pool);
 int launch_jagged_count(const ConvPlan& parent, uint64_t* dev_total, void* stream);
 // Parents' {length, begin} columns from a field-major side's offsets.
 int launch_len_begin(const char* offsets, uint32_t off_size, uint64_t n, unsigned int* len,
@@ -178,11 +196,21 @@ int launch_fill_from(char* dst, const char* from, uint64_t count, uint32_t elem,
 // max_chunk caps the consecutive tiles a CTA takes at once.
 int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, unsigned int njobs,
                  unsigned long long total_tiles, unsigned int* counter,
-                 unsigned int ctas_per_sm, unsigned int max_chunk, void* stream);
+                 unsigned int ctas_per_sm, unsigned int max_chunk, void* stream,
+                 const unsigned int* conds = nullptr);
 // The jagged AoS -> field-major jobs of a batch (their own tile numbering,
 // tile_job[t] = job of tile t), one CTA per tile.
 int launch_batch_jag(const BatchJob* jobs, const unsigned int* tile_job, unsigned long long total,
                      unsigned int* counter, unsigned long long* states, void* stream);
+// The fall-back pass of the batch's split jagged jobs (flags[j] != 0: job j
+// of `jobs` gathers its own children; nothing runs unless *any != 0);
+// max_tiles: the most fall-back tiles of one job.
+int launch_batch_jag_rest(const BatchJob* jobs, unsigned int njobs, unsigned long long max_tiles,
+                          const unsigned int* flags, const unsigned int* any, void* stream);
+// The split scan of the batch's split jagged jobs (chunk_job[c] = the job
+// of chunk c, dynamic chunk ids from *counter).
+int launch_jag_scan(const BatchJob* jobs, const unsigned int* chunk_job, unsigned long long total,
+                    unsigned int* counter, void* stream);
 int batch_occupancy();
 
 // Cached launch shape for a plan (autotuner), or the default.

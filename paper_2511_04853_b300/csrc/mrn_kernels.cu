@@ -405,7 +405,7 @@ __device__ __forceinline__ void jagged_s2a_children(const JagPlan& jp, uint64_t 
 // published tile words st[] (warp-wide: 32 predecessors per step; each wait
 // bounded by jp.timeout_ns and an iteration count).  Run by one whole warp;
 // every lane returns the sum.
-__device__ __forceinline__ unsigned long long jagged_lookback(const JagPlan& jp, uint64_t tile,
+__device__ __forceinline__ unsigned long long jagged_lookback(unsigned long long timeout_ns, uint64_t tile,
                                                               const unsigned long long* st, int lane) {
   unsigned long long prefix = 0;
   long long j = (long long)tile - 1;  // highest tile not yet accumulated
@@ -413,7 +413,7 @@ __device__ __forceinline__ unsigned long long jagged_lookback(const JagPlan& jp,
   // e.g. after lane 0 alone stored to shared memory), and one decision when
   // it expires: a lane that left the loop alone would leave the others in
   // a warp-wide ballot it never reaches.
-  const unsigned long long deadline = __shfl_sync(0xffffffffu, global_ns() + jp.timeout_ns, 0);
+  const unsigned long long deadline = __shfl_sync(0xffffffffu, global_ns() + timeout_ns, 0);
   unsigned int spins = 0;
   while (j >= 0) {
     const long long jj = j - lane;
@@ -463,8 +463,11 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
   // the tiles after this one sum it in their look-back, which otherwise
   // waits for this tile's whole parent conversion.  (The records' lines
   // stay in cache for the conversion below.)
-  const bool publish = (long long)tile != jp.skip_publish_tile;
-  {
+  // (The fall-back pass of a split conversion reads each base from the
+  // finished offsets and publishes nothing.)
+  const uint32_t mode = jp.mode;
+  const bool publish = mode != JAG_CHILDREN && (long long)tile != jp.skip_publish_tile;
+  if (mode != JAG_CHILDREN) {
     unsigned long long own = 0;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -581,8 +584,10 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
   // (the tile's aggregate was published as soon as its lengths were in).
   if (warp == 0) {
     unsigned long long prefix = 0;
-    if (tile > 0) {
-      prefix = jagged_lookback(jp, tile, st, lane);
+    if (mode == JAG_CHILDREN) {  // the finished offset of the tile's first parent
+      if (t0 < P.n) prefix = read_offset(jp.offsets, jp.off_size, t0) - jp.offset_base;
+    } else if (tile > 0) {
+      prefix = jagged_lookback(jp.timeout_ns, tile, st, lane);
       if (publish && lane == 0) st_release_u64(&st[tile], MRN_TS_PREFIX | ((prefix + agg) & MRN_TS_VALUE));
     }
     if (lane == 0) sw.base = prefix;
@@ -609,7 +614,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
   }
 
   // Tile 0 of a single conversion zeroes the destination's gap bytes.
-  if (tile == 0 && jp.ngaps)
+  if (tile == 0 && jp.ngaps && mode != JAG_CHILDREN)
     for (uint32_t k = 0; k < jp.ngaps; ++k)
       for (uint32_t b = tid; b < jp.gap_len[k]; b += MRN_JAG_THREADS) jp.gap_base[jp.gap_off[k] + b] = 0;
 
@@ -660,6 +665,23 @@ __global__ void __launch_bounds__(MRN_JAG_THREADS, MRN_JAG_CTAS) k_jagged_a2s(co
   jagged_a2s_tile<VP, VC>(jp, s_tile, jp.tile_state, tw_all, sh, sw);
 }
 
+// Fall-back pass of a split jagged AoS -> field-major conversion (plan mode
+// JAG_CHILDREN): nothing to do unless the scan pass found the pool not
+// canonical; then the CTAs take the tiles in turn and gather their
+// children (no look-back: every base is in the tile words).
+__global__ void __launch_bounds__(MRN_JAG_THREADS, MRN_JAG_CTAS) k_jagged_a2s_rest(const __grid_constant__ JagPlan jp) {
+  if (ld_relaxed_u32(jp.noncanon) == 0) return;
+  constexpr size_t kTw = MRN_JAG_WARPS * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t);
+  __shared__ __align__(16) unsigned char jag_raw[kTw > sizeof(JagShared) ? kTw : sizeof(JagShared)];
+  uint32_t* tw_all = reinterpret_cast<uint32_t*>(jag_raw);
+  JagShared& sh = *reinterpret_cast<JagShared*>(jag_raw);
+  __shared__ JagWarp sw;
+  for (uint64_t t = blockIdx.x; t < jp.ntiles; t += gridDim.x) {
+    jagged_a2s_tile<0, 0>(jp, t, nullptr, tw_all, sh, sw);
+    __syncthreads();  // the next tile's parent windows overlay this tile's arrays
+  }
+}
+
 // The jagged AoS -> field-major jobs of a batch: one CTA per tile as in
 // k_jagged_a2s, 3 CTAs (48 warps) per SM, tiles taken in increasing order
 // over all the jobs,
@@ -691,6 +713,253 @@ __global__ void __launch_bounds__(MRN_JAG_THREADS, MRN_JAG_CTAS) k_batch_jag(con
   const uint64_t tb = J.tile_begin;
   __syncthreads();
   jagged_a2s_tile<0, 0>(*reinterpret_cast<const JagPlan*>(jps), t - tb, states + tb, tw_all, sh, sw);
+}
+
+// Fall-back pass of a batch's split jagged jobs: nothing to do unless the
+// scan pass (k_batch_jag) found some job's pool not canonical (*any);
+// then every CTA walks the jobs, 32 flags at a time, and takes its share of
+// each flagged job's tiles (plan mode JAG_CHILDREN in the shared copy).
+__global__ void __launch_bounds__(MRN_JAG_THREADS, MRN_JAG_CTAS) k_batch_jag_rest(const BatchJob* __restrict__ jobs,
+                                                                      unsigned int njobs,
+                                                                      const unsigned int* flags,
+                                                                      const unsigned int* any) {
+  if (ld_relaxed_u32(any) == 0) return;
+  constexpr size_t kTw = MRN_JAG_WARPS * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t);
+  __shared__ __align__(16) unsigned char jag_raw[kTw > sizeof(JagShared) ? kTw : sizeof(JagShared)];
+  uint32_t* tw_all = reinterpret_cast<uint32_t*>(jag_raw);
+  JagShared& sh = *reinterpret_cast<JagShared*>(jag_raw);
+  __shared__ JagWarp sw;
+  __shared__ unsigned int s_mask;
+  __shared__ __align__(16) unsigned long long jps[(sizeof(JagPlan) + 7) / 8];
+  JagPlan& jp = *reinterpret_cast<JagPlan*>(jps);
+  for (unsigned int j0 = 0; j0 < njobs; j0 += 32) {
+    if (threadIdx.x < 32) {
+      const unsigned int j = j0 + threadIdx.x;
+      const unsigned int m = __ballot_sync(0xffffffffu, j < njobs && ld_relaxed_u32(flags + j) != 0);
+      if (threadIdx.x == 0) s_mask = m;
+    }
+    __syncthreads();
+    unsigned int mask = s_mask;
+    __syncthreads();  // s_mask is written again in the next round
+    while (mask) {
+      const unsigned int j = j0 + (unsigned int)__ffs(mask) - 1u;
+      mask &= mask - 1u;
+      const BatchJob& J = jobs[j];
+      const uint64_t nt = J.ntiles;
+      if (blockIdx.x >= nt) continue;
+      const unsigned long long* g = reinterpret_cast<const unsigned long long*>(&J.jp);
+      for (uint32_t i = threadIdx.x; i < sizeof(JagPlan) / 8; i += blockDim.x) jps[i] = __ldg(g + i);
+      __syncthreads();
+      if (threadIdx.x == 0) jp.mode = JAG_CHILDREN;
+      __syncthreads();
+      for (uint64_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        jagged_a2s_tile<0, 0>(jp, t, nullptr, tw_all, sh, sw);
+        __syncthreads();  // the next tile's windows (or plan) overlay this tile's state
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------- split jagged scan
+
+// A u32 / u64 field of an AoS record whose base is aligned to `vec` bytes.
+__device__ __forceinline__ uint32_t ld_u32_rec(const char* p, uint32_t vec) {
+  if (vec >= 4) return __ldg(reinterpret_cast<const unsigned int*>(p));
+  uint32_t v = 0;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) v |= (uint32_t)__ldg(reinterpret_cast<const unsigned char*>(p + b)) << (8 * b);
+  return v;
+}
+__device__ __forceinline__ uint64_t ld_u64_rec(const char* p, uint32_t vec) {
+  if (vec >= 8) return __ldg(reinterpret_cast<const unsigned long long*>(p));
+  return (uint64_t)ld_u32_rec(p, vec) | ((uint64_t)ld_u32_rec(p + 4, vec) << 32);
+}
+
+__device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long long x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+constexpr uint32_t kScanThreads = 256;
+constexpr uint32_t kScanGroups = MRN_SCAN_CHUNK / 32;                    // groups of 32 parents per chunk
+constexpr uint32_t kScanWarpGroups = kScanGroups / (kScanThreads / 32);  // groups per warp
+static_assert(kScanWarpGroups == 32, "a warp's groups are one per lane");
+
+struct ScanShared {
+  unsigned long long wsum[kScanThreads / 32];
+  unsigned long long base;
+};
+
+// Chunk c (of MRN_SCAN_CHUNK parents) of a split jagged AoS -> field-major
+// conversion: warp w sums the lengths of groups 32 w .. 32 w + 31 of the
+// chunk (lane l of a pass holds parent 32 g + l; lane i ends up holding group
+// i's sum and the spread of begin - exclusive offset over its parents with
+// children), the chunk's aggregate is published and the children before the
+// chunk come from a decoupled look-back over st[]; then every group's base
+// (children before it) goes to group_base.  The pool is canonical where each
+// group with children has begin - exclusive offset equal to its base for all
+// those parents; the group of the last parent writes offsets[n] and checks
+// that the children are exactly the pool's records.
+__device__ __forceinline__ void jag_scan_chunk(const JagPlan& jp, uint64_t c, unsigned long long* st, ScanShared& sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t n = jp.parent.n, pool_n = jp.pool_n;
+  const char* base = jp.parent.src.base;
+  const uint32_t stride = jp.parent.stride, vec = jp.parent.vec, len_off = jp.len_off, begin_off = jp.begin_off;
+  const uint64_t g0 = c * kScanGroups + (uint64_t)warp * kScanWarpGroups;
+  unsigned long long gsum = 0, gmin = ~0ull, gmax = 0ull;  // lane i: group g0 + i
+#pragma unroll 1
+  for (uint32_t i0 = 0; i0 < kScanWarpGroups; i0 += 4) {
+    uint32_t len[4];
+    uint64_t beg[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint64_t r = (g0 + i0 + u) * 32 + lane;
+      len[u] = 0;
+      beg[u] = 0;
+      if (r < n) {
+        const char* q = base + r * stride;
+        len[u] = ld_u32_rec(q + len_off, vec);
+        beg[u] = ld_u64_rec(q + begin_off, vec);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint64_t r = (g0 + i0 + u) * 32 + lane;
+      const bool bad = r < n && (beg[u] > pool_n || (uint64_t)len[u] > pool_n - beg[u]);
+      if (bad) flag_error(MRN_EINVAL);
+      const unsigned long long x = warp_incl_scan_u64(len[u], lane);
+      const unsigned long long excl = x - len[u];
+      const unsigned long long tot = __shfl_sync(0xffffffffu, x, 31);
+      unsigned long long dmin = ~0ull, dmax = 0ull;
+      if (bad) {
+        dmin = 0ull;
+        dmax = ~0ull;
+      } else if (len[u] > 0) {
+        dmin = dmax = beg[u] - excl;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        dmin = min(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+        dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      }
+      if ((uint32_t)lane == i0 + u) {
+        gsum = tot;
+        gmin = dmin;
+        gmax = dmax;
+      }
+    }
+  }
+  const unsigned long long x = warp_incl_scan_u64(gsum, lane);
+  if (lane == 31) sh.wsum[warp] = x;
+  __syncthreads();
+  unsigned long long agg = 0, wbase = 0;
+#pragma unroll
+  for (int w = 0; w < (int)(kScanThreads / 32); ++w) {
+    const unsigned long long v = sh.wsum[w];
+    if (w < warp) wbase += v;
+    agg += v;
+  }
+  const bool publish = (long long)c != jp.skip_publish_tile;
+  if (tid == 0 && publish) st_release_u64(&st[c], (c == 0 ? MRN_TS_PREFIX : MRN_TS_AGG) | (agg & MRN_TS_VALUE));
+  if (warp == 0) {
+    unsigned long long prefix = 0;
+    if (c > 0) {
+      prefix = jagged_lookback(jp.timeout_ns, c, st, lane);
+      if (publish && lane == 0) st_release_u64(&st[c], MRN_TS_PREFIX | ((prefix + agg) & MRN_TS_VALUE));
+    }
+    if (lane == 0) sh.base = prefix;
+  }
+  // chunk 0 of a single conversion zeroes the destination's gap bytes
+  if (c == 0 && jp.ngaps)
+    for (uint32_t k = 0; k < jp.ngaps; ++k)
+      for (uint32_t b = tid; b < jp.gap_len[k]; b += kScanThreads) jp.gap_base[jp.gap_off[k] + b] = 0;
+  __syncthreads();
+  const uint64_t g = g0 + lane;
+  const bool have = g * 32 < n;
+  const unsigned long long gb = sh.base + wbase + (x - gsum);
+  bool bad = have && gsum > 0 && !(gmin == gmax && gmin == gb);
+  if (have) jp.group_base[g] = gb;
+  if (have && (n - 1) / 32 == g) {
+    const unsigned long long total = gb + gsum, end = jp.offset_base + total;
+    write_offset(jp.offsets, jp.off_size, n, end);
+    if (jp.total_out) *jp.total_out = total;
+    if (jp.off_size == 4 && (end > 0xffffffffull || end < total)) flag_error(MRN_EOVERFLOW);
+    if (total != pool_n) bad = true;
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) {
+    atomicExch(jp.noncanon, 1u);
+    if (jp.any_noncanon) atomicExch(jp.any_noncanon, 1u);
+  }
+}
+
+// The split scan of one conversion: chunks handed out in increasing order,
+// so that every chunk a look-back waits for is already running.
+__global__ void __launch_bounds__(kScanThreads) k_jag_scan_one(const __grid_constant__ JagPlan jp) {
+  __shared__ ScanShared sh;
+  __shared__ unsigned int s_chunk;
+  if (threadIdx.x == 0) s_chunk = atomicAdd(jp.tile_counter, 1u);
+  __syncthreads();
+  jag_scan_chunk(jp, s_chunk, jp.chunk_state, sh);
+}
+
+// The split scan of a batch's jagged jobs: the chunks of all of them in one
+// numbering (chunk_job[c] = the job of chunk c), handed out in increasing
+// order; a chunk's look-back visits only its own job's earlier chunks.
+__global__ void __launch_bounds__(kScanThreads) k_jag_scan(const BatchJob* __restrict__ jobs,
+                                                           const unsigned int* __restrict__ chunk_job,
+                                                           unsigned long long total, unsigned int* counter) {
+  __shared__ ScanShared sh;
+  __shared__ unsigned int s_chunk;
+  if (threadIdx.x == 0) s_chunk = atomicAdd(counter, 1u);
+  __syncthreads();
+  const uint64_t c = s_chunk;
+  if (c >= total) return;
+  const JagPlan& jp = jobs[__ldg(chunk_job + c)].jp;
+  const uint64_t cb = jp.chunk_begin;
+  jag_scan_chunk(jp, c - cb, jp.chunk_state, sh);
+}
+
+// Offsets of the parents of a split jagged job, group by group (32
+// parents, starting at a multiple of 32): offset_base + the group's base +
+// the exclusive prefix of the lengths inside the group.  From staged tile
+// `local` of R records (`stage`: the tile's AoS records; consumer warp w
+// takes groups w, w + 8, w + 16 of it, their bases loaded together first),
+// or from global memory.
+constexpr int kJagTileGroups = 3;  // groups per consumer warp of a staged tile (T <= 768)
+__device__ __forceinline__ void jag_offsets_staged(const JagPlan& jp, uint64_t local, uint32_t R, const char* stage,
+                                                   const TileHdr& h, int lane, int warp) {
+  const uint64_t r0 = local * h.T;
+  unsigned long long gb[kJagTileGroups];
+#pragma unroll
+  for (int k = 0; k < kJagTileGroups; ++k) {
+    const uint32_t q = (uint32_t)(warp + 8 * k) * 32;
+    gb[k] = q < R ? __ldg(jp.group_base + (r0 + q) / 32) : 0ull;
+  }
+#pragma unroll
+  for (int k = 0; k < kJagTileGroups; ++k) {
+    const uint32_t q = (uint32_t)(warp + 8 * k) * 32;
+    if (q >= R) break;
+    const uint32_t len = *reinterpret_cast<const unsigned int*>(stage + (size_t)(q + lane) * h.stride + jp.len_off);
+    const unsigned long long x = warp_incl_scan_u64(len, lane);
+    write_offset(jp.offsets, jp.off_size, r0 + q + lane, jp.offset_base + gb[k] + x - len);
+  }
+}
+
+__device__ __forceinline__ void jag_offsets_direct(const JagPlan& jp, uint64_t r0, uint64_t r1, int lane, int warp,
+                                                   int nwarps) {
+  const ConvPlan& P = jp.parent;
+  if (r1 > P.n) r1 = P.n;
+  for (uint64_t q = r0 + (uint64_t)warp * 32; q < r1; q += (uint64_t)nwarps * 32) {
+    const uint64_t r = q + lane;
+    const uint32_t len = r < r1 ? ld_u32_rec(P.src.base + r * P.stride + jp.len_off, P.vec) : 0u;
+    const unsigned long long x = warp_incl_scan_u64(len, lane);
+    const unsigned long long gbase = __ldg(jp.group_base + q / 32);
+    if (r < r1) write_offset(jp.offsets, jp.off_size, r, jp.offset_base + gbase + x - len);
+  }
 }
 
 // One warp group of a jagged SoA -> AoS conversion: groups [0,
@@ -798,12 +1067,15 @@ constexpr uint32_t kRing = 8;     // decided tiles in flight
 constexpr uint32_t kSQ = 8;       // staged tiles between loader and storer
 constexpr uint64_t kChunk = 16;   // most consecutive tiles per chunk
 constexpr uint32_t kBThreads = 320;
+constexpr unsigned long long kSkipTile = ~0ull;
 
 struct TileSlot {
   unsigned long long t;  // global tile; >= total_tiles: no more tiles
-  unsigned long long local;
+  unsigned long long local;  // kSkipTile: a tile of a job whose condition failed
   unsigned int job;
   unsigned int staged;  // records of a staged tile; 0: the tile runs directly
+  unsigned int jag;     // 1: a tile of the parents of a split jagged job (offsets too)
+  unsigned int pad;
 };
 
 // A stage's table in shared memory: the layout of StageRec, read as uint4.
@@ -942,6 +1214,8 @@ __device__ __forceinline__ unsigned int advance_job(const unsigned long long* __
 struct LoadCache {
   unsigned int job;
   bool staged_job;
+  bool skip;  // the job converts a jagged pool that the scan found not canonical
+  bool jag_parents;
   uint32_t T, rs, kind, ncols, stride, src_bytes, block;
   uint64_t tile_begin, nfull, block_bytes;
   const char* base;
@@ -949,11 +1223,14 @@ struct LoadCache {
   uint32_t size[2], off[2];
 };
 
-__device__ __forceinline__ void load_cache(const BatchJob& J, unsigned int job, int lane, LoadCache* c) {
+__device__ __forceinline__ void load_cache(const BatchJob& J, unsigned int job, int lane, LoadCache* c,
+                                           const unsigned int* conds) {
   const ConvPlan& P = J.jp.parent;
   c->job = job;
+  c->skip = J.cond && conds && ld_relaxed_u32(conds + J.cond - 1) != 0;
   c->tile_begin = J.tile_begin;
-  c->staged_job = J.kind == JOB_CONVERT && P.tg.tma;
+  c->staged_job = (J.kind == JOB_CONVERT || J.kind == JOB_JAG_PARENTS) && P.tg.tma;
+  c->jag_parents = J.kind == JOB_JAG_PARENTS;
   c->T = P.tg.T;
   const StagedTiles st = staged_tiles(P.n, 0, P.tg.T, P.tg.G);
   c->nfull = st.nfull;
@@ -1014,7 +1291,7 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
                                              unsigned int njobs, unsigned long long total_tiles,
                                              unsigned int* counter,
                                              uint32_t chunk, unsigned int first_start, unsigned int first_size,
-                                             const BatchSmem& m, int lane) {
+                                             const BatchSmem& m, int lane, const unsigned int* conds) {
   uint64_t k_issue = 0;  // tiles decided
   uint32_t c_issue = 0;  // staged tiles loaded
   unsigned int cursor = 0;
@@ -1067,12 +1344,16 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
       cand.staged = 0;
       cand.job = 0;
       cand.local = 0;
+      cand.jag = 0;
       if (cand.t < total_tiles) {
         if constexpr (!kStatic) cursor = advance_job(first_tile, njobs, cursor, cand.t, lane);
-        if (cursor != lc.job) load_cache(jobs[cursor], cursor, lane, &lc);
+        if (cursor != lc.job) load_cache(jobs[cursor], cursor, lane, &lc, conds);
         cand.job = cursor;
         cand.local = cand.t - lc.tile_begin;
-        if (lc.staged_job)
+        cand.jag = lc.jag_parents ? 1u : 0u;
+        if (lc.skip)
+          cand.local = kSkipTile;
+        else if (lc.staged_job)
           cand.staged = cand.local < lc.nfull ? lc.T : (cand.local == lc.nfull ? lc.rs : 0u);
       }
       have = true;
@@ -1196,7 +1477,7 @@ template <bool kStatic, bool kWide>
 __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
                                            const unsigned long long* __restrict__ first_tile, unsigned int njobs,
                                            unsigned long long total_tiles, unsigned int* counter,
-                                           uint32_t chunk, char* batch_smem) {
+                                           uint32_t chunk, char* batch_smem, const unsigned int* conds) {
   BatchSmem m{batch_smem};
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if constexpr (!kStatic) {
@@ -1240,7 +1521,7 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
   __syncthreads();
   if (warp == 8) {
     batch_loader<kStatic, kWide>(jobs, first_tile, njobs, total_tiles, counter, chunk, first_start, first_size, m,
-                          lane);
+                                 lane, conds);
     return;
   }
   if (warp == 9) {
@@ -1268,6 +1549,9 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
       }
       const StageDesc* sd = m.desc(s);
       tma_transform<kWide>(sd->h, smem_u32(sd->d), m.src(s), m.dst(d), ts.staged, lane, warp);
+      // parents of a split jagged job: the offsets, from the staged lengths
+      // (before the source stage is released)
+      if (ts.jag) jag_offsets_staged(jobs[ts.job].jp, ts.local, ts.staged, m.src(s), sd->h, lane, warp);
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
@@ -1277,9 +1561,10 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
       ++c;
     } else {
       if (ts.t >= total_tiles) break;
+      if (ts.local == kSkipTile) continue;
       const BatchJob& J = jobs[ts.job];
       const unsigned long long local = ts.local;
-      if (J.kind == JOB_CONVERT) {
+      if (J.kind == JOB_CONVERT || J.kind == JOB_JAG_PARENTS) {
         const ConvPlan& P = J.jp.parent;
         uint64_t r0, r1;
         if (P.tg.tma) {  // the records after a staged job's staged tiles
@@ -1290,6 +1575,7 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
           r1 = r0 + J.tile_records;
         }
         conv_range<0, kBWin>(P, r0, r1, tw, lane, warp, 8);
+        if (J.kind == JOB_JAG_PARENTS) jag_offsets_direct(J.jp, r0, r1, lane, warp, 8);
       } else if (J.kind == JOB_JAG_S2A) {
         jagged_s2a_group<0, 0, kBWin>(J.jp, local * 8 + warp, J.parent_groups, tw, lane);
       } else {
@@ -1305,12 +1591,14 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
 }
 
 // Batched conversions: tiles handed out dynamically in increasing order.
+// A job with a condition (cond > 0) is skipped when conds[cond - 1] != 0.
 __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restrict__ jobs,
                                                         const unsigned long long* __restrict__ first_tile,
                                                         unsigned int njobs, unsigned long long total_tiles,
-                                                        unsigned int* counter, uint32_t chunk) {
+                                                        unsigned int* counter, uint32_t chunk,
+                                                        const unsigned int* conds) {
   extern __shared__ __align__(128) char batch_smem[];
-  batch_main<false, false>(jobs, first_tile, njobs, total_tiles, counter, chunk, batch_smem);
+  batch_main<false, false>(jobs, first_tile, njobs, total_tiles, counter, chunk, batch_smem, conds);
 }
 
 // One staged conversion through the same warp-specialized pipeline: the
@@ -1319,11 +1607,15 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
 // zeroed word), chunks are guided as in a batch, so that CTAs that run
 // faster take more of them.  kWide: the instance for conversions whose
 // plan stores fields wider over an AoS destination's padding.
+// With `cond`, the launch does nothing when *cond != 0 (the child pool of a
+// split jagged conversion that the scan found not canonical).
 template <bool kWide>
 __global__ void __launch_bounds__(kBThreads, 3) k_convert_ws(const __grid_constant__ BatchJob job,
-                                                             uint32_t chunk, unsigned int* counter) {
+                                                             uint32_t chunk, unsigned int* counter,
+                                                             const unsigned int* cond) {
+  if (cond && ld_relaxed_u32(cond) != 0) return;
   extern __shared__ __align__(128) char batch_smem[];
-  batch_main<true, kWide>(&job, nullptr, 1u, job.ntiles, counter, chunk, batch_smem);
+  batch_main<true, kWide>(&job, nullptr, 1u, job.ntiles, counter, chunk, batch_smem, nullptr);
 }
 
 // ================================================================== host
@@ -1423,16 +1715,12 @@ uint32_t chunk_for(uint64_t tiles, uint64_t ctas) {
   return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(8, tiles / (4 * std::max<uint64_t>(1, ctas))));
 }
 
-int launch_convert(const ConvPlan& p, void* stream, const LaunchShape* shape) {
+// One staged job (JOB_CONVERT or JOB_JAG_PARENTS, plan in job.jp.parent)
+// through the warp-specialized pipeline of the batch kernel.
+int launch_staged_job(BatchJob& job, void* stream, const LaunchShape& sh, const unsigned int* cond) {
+  const ConvPlan& p = job.jp.parent;
   const uint64_t nrec = p.dir == DIR_FM_AOS ? p.n : p.n_fm_pad;
-  if (nrec == 0) return MRN_OK;
-  LaunchShape sh = shape ? *shape : LaunchShape{};
-  if (p.tg.tma && !sh.generic) {
-    // the warp-specialized pipeline of the batch kernel, one job
-    BatchJob job;
-    std::memset(&job, 0, sizeof(job));
-    job.kind = JOB_CONVERT;
-    job.jp.parent = p;
+  {
     job.tile_records = p.tg.T;
     job.ntiles = staged_tile_count(p.n, nrec, p.tg.T, p.tg.G);
     // the instance with the widened-field transform only for plans that
@@ -1464,11 +1752,25 @@ int launch_convert(const ConvPlan& p, void* stream, const LaunchShape* shape) {
     }
     const uint64_t chunks = (job.ntiles + chunk - 1) / chunk;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(chunks, cap));
-    void* args[] = {&job, &chunk, &counter};
+    void* args[] = {&job, &chunk, &counter, &cond};
     const int rc = cuda_status(cudaLaunchKernel(fn, dim3(grid), dim3(kBThreads), args, kBatchSmem, st));
     if (counter) cudaFreeAsync(counter, st);
     return rc;
   }
+}
+
+int launch_convert(const ConvPlan& p, void* stream, const LaunchShape* shape, const unsigned int* cond) {
+  const uint64_t nrec = p.dir == DIR_FM_AOS ? p.n : p.n_fm_pad;
+  if (nrec == 0) return MRN_OK;
+  LaunchShape sh = shape ? *shape : LaunchShape{};
+  if (p.tg.tma && !sh.generic) {
+    BatchJob job;
+    std::memset(&job, 0, sizeof(job));
+    job.kind = JOB_CONVERT;
+    job.jp.parent = p;
+    return launch_staged_job(job, stream, sh, cond);
+  }
+  if (cond) return MRN_EINVAL;  // only staged launches take a condition
   if (sh.threads != 64 && sh.threads != 128 && sh.threads != 256) sh.threads = 256;
   if (sh.tile_records == 0 || sh.tile_records % 32) sh.tile_records = sh.threads * 2;
   void* fn = conv_kernel(p.dir == DIR_FM_FM ? 1 : p.vec);
@@ -1576,6 +1878,51 @@ int launch_jagged_a2s(JagPlan& jp, void* scratch, void* stream) {
   return cuda_status(e);
 }
 
+uint64_t jagged_split_scratch_bytes(uint64_t n, size_t* group_at) {
+  const uint64_t nchunks = (n + MRN_SCAN_CHUNK - 1) / MRN_SCAN_CHUNK;
+  const uint64_t at = align_up(256 + nchunks * sizeof(unsigned long long), 256);
+  if (group_at) *group_at = (size_t)at;
+  return at + (n + 31) / 32 * sizeof(unsigned long long);
+}
+
+int launch_jagged_a2s_split(JagPlan& jp, const ConvPlan& pool, void* scratch, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint64_t n = jp.parent.n;
+  if (n == 0 || !pool.tg.tma || !jp.parent.tg.tma) return MRN_EINVAL;
+  jp.nchunks = (n + MRN_SCAN_CHUNK - 1) / MRN_SCAN_CHUNK;
+  jp.ntiles = (jagged_tile_records(jp) + MRN_JAG_TILE - 1) / MRN_JAG_TILE;  // tiles of the fall-back pass
+  if (jp.nchunks > 0x7fffffffull || jp.ntiles > 0x7fffffffull) return MRN_EUNSUPPORTED;
+  size_t group_at = 0;
+  jagged_split_scratch_bytes(n, &group_at);
+  char* sc = static_cast<char*>(scratch);
+  jp.mode = JAG_SPLIT;
+  jp.tile_counter = reinterpret_cast<unsigned int*>(sc);
+  jp.noncanon = reinterpret_cast<unsigned int*>(sc + 128);
+  jp.any_noncanon = nullptr;
+  jp.chunk_state = reinterpret_cast<unsigned long long*>(sc + 256);
+  jp.group_base = reinterpret_cast<unsigned long long*>(sc + group_at);
+  cudaError_t e = cudaMemsetAsync(sc, 0, group_at, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  // 1. the scan: group bases, offsets[n], the pool check
+  k_jag_scan_one<<<(unsigned)jp.nchunks, kScanThreads, 0, s>>>(jp);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+  // 2. the parents' data columns and offsets, one staged conversion
+  BatchJob job;
+  std::memset(&job, 0, sizeof(job));
+  job.kind = JOB_JAG_PARENTS;
+  job.jp = jp;
+  int rc = launch_staged_job(job, stream, LaunchShape{}, nullptr);
+  if (rc) return rc;
+  // 3. a canonical pool: its records -> the child rows, one staged conversion
+  if ((rc = launch_convert(pool, stream, nullptr, jp.noncanon))) return rc;
+  // 4. otherwise the tiles gather their children
+  jp.mode = JAG_CHILDREN;
+  const int per_sm = occupancy(reinterpret_cast<const void*>(&k_jagged_a2s_rest), MRN_JAG_THREADS, 0);
+  const uint64_t grid = std::min<uint64_t>(jp.ntiles, (uint64_t)device_sm_count() * (uint64_t)per_sm);
+  k_jagged_a2s_rest<<<(unsigned)grid, MRN_JAG_THREADS, 0, s>>>(jp);
+  return cuda_status(cudaGetLastError());
+}
+
 int launch_jagged_s2a(const JagPlan& jp, void* stream) {
   const uint64_t pw = (jp.parent.n + 31) / 32;
   const uint64_t cw = (jp.m_src + MRN_JAG_CHILD_GROUP - 1) / MRN_JAG_CHILD_GROUP;
@@ -1623,9 +1970,27 @@ int launch_batch_jag(const BatchJob* jobs, const unsigned int* tile_job, unsigne
   return cuda_status(cudaGetLastError());
 }
 
+int launch_batch_jag_rest(const BatchJob* jobs, unsigned int njobs, unsigned long long max_tiles,
+                          const unsigned int* flags, const unsigned int* any, void* stream) {
+  if (max_tiles == 0 || njobs == 0) return MRN_OK;
+  const int per_sm = occupancy(reinterpret_cast<const void*>(&k_batch_jag_rest), MRN_JAG_THREADS, 0);
+  const uint64_t grid = std::min<uint64_t>(max_tiles, (uint64_t)device_sm_count() * (uint64_t)per_sm);
+  k_batch_jag_rest<<<(unsigned)grid, MRN_JAG_THREADS, 0, static_cast<cudaStream_t>(stream)>>>(jobs, njobs, flags,
+                                                                                           any);
+  return cuda_status(cudaGetLastError());
+}
+
+int launch_jag_scan(const BatchJob* jobs, const unsigned int* chunk_job, unsigned long long total,
+                    unsigned int* counter, void* stream) {
+  if (total == 0) return MRN_OK;
+  k_jag_scan<<<(unsigned)total, kScanThreads, 0, static_cast<cudaStream_t>(stream)>>>(jobs, chunk_job, total,
+                                                                                    counter);
+  return cuda_status(cudaGetLastError());
+}
+
 int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, unsigned int njobs,
                  unsigned long long total_tiles, unsigned int* counter,
-                 unsigned int ctas_per_sm, unsigned int max_chunk, void* stream) {
+                 unsigned int ctas_per_sm, unsigned int max_chunk, void* stream, const unsigned int* conds) {
   if (total_tiles == 0) return MRN_OK;
   const int occ = batch_occupancy();
   const int per_sm = ctas_per_sm ? std::min((int)ctas_per_sm, occ) : occ;
@@ -1638,7 +2003,7 @@ int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, uns
   const uint64_t chunks = (total_tiles + chunk - 1) / chunk;
   const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(cap, chunks));
   k_batch<<<grid, kBThreads, kBatchSmem, static_cast<cudaStream_t>(stream)>>>(jobs, first_tile, njobs,
-                                                                                total_tiles, counter, chunk);
+                                                                                total_tiles, counter, chunk, conds);
   return cuda_status(cudaGetLastError());
 }
 

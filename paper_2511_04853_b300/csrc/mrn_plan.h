@@ -134,7 +134,31 @@ struct JagPlan {
   uint32_t ngaps;
   uint32_t gap_len[MRN_JAG_GAPS];
   uint64_t gap_off[MRN_JAG_GAPS];
+  // AoS -> field-major runs fused (JAG_FUSED: the tiles above scan, convert
+  // the parents and gather their own children) or split (JAG_SPLIT):
+  //  - k_jag_scan sums the lengths in chunks of MRN_SCAN_CHUNK parents
+  //    (decoupled look-back over chunk_state), writes the children before
+  //    each 32-parent group to group_base, offsets[n], and sets *noncanon
+  //    (and *any_noncanon) unless the pool is canonical: every parent's
+  //    children at its own offset, and no other records in the pool;
+  //  - the parents' data columns and offsets are a staged conversion job
+  //    (JOB_JAG_PARENTS), and a canonical pool is one more (pool record j
+  //    -> child row j);
+  //  - otherwise the fall-back pass gathers the children (tiles in mode
+  //    JAG_CHILDREN, their bases read from the finished offsets).
+  uint32_t mode;
+  uint32_t begin_off;               // byte offset of the begin in a parent record
+  unsigned int* noncanon;
+  unsigned int* any_noncanon;
+  unsigned long long* group_base;   // ceil(n / 32) words
+  unsigned long long* chunk_state;  // the scan's look-back words, one per chunk
+  uint64_t chunk_begin;             // batches: the job's first chunk in the scan's numbering
+  uint64_t nchunks;
 };
+#define JAG_FUSED 0u
+#define JAG_SPLIT 1u
+#define JAG_CHILDREN 2u
+#define MRN_SCAN_CHUNK 8192u  // parents per chunk of the split scan (256 groups of 32)
 
 // Zero-fill of the alignment holes of a destination: for each of `nblocks`
 // blocks of `block_bytes`, the byte ranges [off[k], off[k] + len[k]).
@@ -189,15 +213,23 @@ inline uint64_t staged_tile_count(uint64_t n, uint64_t nrec, uint32_t T, uint32_
 #define MRN_JAG_CHILD_GROUP 128  // child records per warp group of a jagged SoA -> AoS conversion
 
 // One job of a batched launch: a plain conversion (plan in jp.parent), a
-// jagged conversion, or the zero-fill of a destination's alignment holes,
-// and its slice of the batch's global tile sequence.
-enum MrnJobKind : uint32_t { JOB_CONVERT = 0, JOB_JAG_A2S = 1, JOB_JAG_S2A = 2, JOB_ZERO = 3 };
+// jagged conversion, the parents of a split jagged conversion (a conversion
+// of jp.parent that also writes the offsets from jp.group_base), or the
+// zero-fill of a destination's alignment holes, and its slice of the
+// batch's global tile sequence.
+enum MrnJobKind : uint32_t { JOB_CONVERT = 0, JOB_JAG_A2S = 1, JOB_JAG_S2A = 2, JOB_ZERO = 3, JOB_JAG_PARENTS = 4 };
 struct BatchJob {
   uint32_t kind;
   uint32_t tile_records;        // JOB_CONVERT: records per tile (multiple of 256)
   uint64_t tile_begin;          // first tile of this job in the batch
   uint64_t ntiles;
   uint64_t parent_groups;       // JOB_JAG_S2A: 32-record groups of parents
+  // JOB_CONVERT: 0, or 1 + the index of the jagged job whose pool this job
+  // converts; its tiles are skipped when that job's pool is not canonical
+  uint32_t cond;
+  // host side: 1 + the index of the split jagged job this job belongs to
+  // (its pool or its parents), else 0
+  uint32_t jag_link;
   union {
     JagPlan jp;                 // JOB_CONVERT uses jp.parent
     GapPlan gp;                 // JOB_ZERO

@@ -120,9 +120,21 @@ def test_autotune_then_convert_still_exact():
     mrn.autotune_clear()
 
 
-def test_jagged_jobs_shuffled_pools_many_tiles():
+@pytest.fixture(params=["split", "fused"])
+def jagged_path(request):
+    """Batches split their jagged AoS jobs by default (scan tiles, pool
+    conversions as jobs of the persistent kernel, a fall-back pass); debug
+    key 4 < 0 keeps them fused."""
+    if request.param == "fused":
+        mrn.debug_set(4, -1)
+    yield request.param
+    mrn.debug_set(4, 2**63 - 1)
+
+
+def test_jagged_jobs_shuffled_pools_many_tiles(jagged_path):
     """Jagged jobs of many tiles (look-back across CTAs), canonical and
-    shuffled child pools, between plain conversions, in one launch."""
+    shuffled child pools (with and without records beyond the children),
+    between plain conversions, in one launch."""
     pairs, checks = [], []
     for j, n in enumerate([3000, 41000, 257, 25000, 60000]):
         s, o = mrn.Schema(datagen.TRACKS), oracle.Schema(datagen.TRACKS)
@@ -130,7 +142,7 @@ def test_jagged_jobs_shuffled_pools_many_tiles():
         o_aos = oracle.pack(o, d, "aos")
         if j % 2:
             order = np.random.default_rng(j).permutation(n)
-            o_aos = oracle.shuffle_pool(o, o_aos, order, gap=1)
+            o_aos = oracle.shuffle_pool(o, o_aos, order, gap=1 if j == 1 else 0)
         want = oracle.convert(o, o_aos, "soa", m=d["m"]).base
         src = mrn.View(s, "aos", n, base=dev(o_aos.base), child_pool=dev(o_aos.pool), m=o_aos.m)
         dst = dev_dest(s, "soa", n, d["m"])
@@ -152,11 +164,12 @@ def test_jagged_jobs_shuffled_pools_many_tiles():
             assert np.array_equal(host(dst.tensors[0], want.size), want), "job %d" % k
 
 
-def test_batch_lookback_wait_is_bounded():
-    """Host-side fault injection: jagged tile 1 of a batched job never
-    publishes its sum, so tile 2's look-back must expire (1 ms bound) and
-    report MRN_ETIMEOUT; batches built afterwards run normally."""
-    n = 8 * 1024  # at least four jagged tiles for tiles of up to 2,048 parents
+def test_batch_lookback_wait_is_bounded(jagged_path):
+    """Host-side fault injection: jagged tile 1 of a batched job (the split
+    scan's chunk 1) never publishes its sum, so the later look-backs must
+    expire (1 ms bound) and report MRN_ETIMEOUT; batches built afterwards
+    run normally."""
+    n = 4 * 8192  # at least four tiles / scan chunks, at up to 8,192 parents each
     s, o = mrn.Schema(datagen.TRACKS), oracle.Schema(datagen.TRACKS)
     d = datagen.workload("tracks", n, 3)
     o_aos = oracle.pack(o, d, "aos")
@@ -277,13 +290,14 @@ def test_empty_jobs_in_a_batch():
             assert np.array_equal(result(d, want, name), want), "job %d (%s)" % (i, name)
 
 
+@pytest.mark.usefixtures("jagged_path")
 def test_mixed_size_law_batch_matches_oracle_with_timed_launch():
     """320 collections drawn as in the 4,096-collection mixed batch (seed 3:
     records round(10^U(3, 6)), schema uniform over points / cells / tracks,
     AoS source, target uniform over SoA / AoSoA(32) / AoSoA(128)), each
     size capped at 10,000 records so the oracle runs in seconds.  The plain
-    replay and the timed replay (events recorded between the two kernels)
-    both give the oracle's bytes, and the events measure the two kernels."""
+    replay and the timed replay (events recorded after the jagged tiles)
+    both give the oracle's bytes, and the events measure both parts."""
     t = torch_mod()
     rng = np.random.default_rng(3)
     count = 320

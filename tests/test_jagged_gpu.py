@@ -13,6 +13,18 @@ from gpu_util import dev, dev_dest, dev_view, garbage, host, torch
 
 pytestmark = pytest.mark.gpu
 
+SPLIT_DEFAULT = 2**63 - 1  # parents from which single conversions run split (debug key 4): never
+
+
+@pytest.fixture(autouse=True, params=["fused", "split"])
+def jagged_path(request):
+    """Every test of this module runs twice: with jagged AoS -> field-major
+    conversions fused (the tiles gather their own children) and split (scan
+    pass, pool conversion when the pool is canonical, fall-back pass)."""
+    mrn.debug_set(4, -1 if request.param == "fused" else 0)
+    yield request.param
+    mrn.debug_set(4, SPLIT_DEFAULT)
+
 
 def tracks(n, seed=2, **kw):
     return mrn.Schema(datagen.TRACKS), oracle.Schema(datagen.TRACKS), datagen.workload("tracks", n, seed, **kw)
@@ -225,10 +237,11 @@ def test_decreasing_offsets_reported():
 
 
 def test_lookback_wait_is_bounded():
-    """Fault injection on the host side: tile 1 never publishes its sum, so
-    tile 2's look-back wait must expire (1 ms bound) and report
-    MRN_ETIMEOUT; the context stays usable afterwards."""
-    n = 8 * 1024  # at least four jagged tiles for tiles of up to 2,048 parents
+    """Fault injection on the host side: tile 1 (the split scan's chunk 1)
+    never publishes its sum, so the look-back waits of the later ones must
+    expire (1 ms bound) and report MRN_ETIMEOUT; the context stays usable
+    afterwards."""
+    n = 4 * 8192  # at least four tiles / scan chunks, at up to 8,192 parents each
     s, o, d = tracks(n, seed=3)
     o_aos = oracle.pack(o, d, "aos")
     try:
@@ -355,3 +368,43 @@ def test_large_soa_to_aos_parents_as_a_plain_conversion(n, osz, raw):
     bad[st + 5 * osize: st + 6 * osize] = np.frombuffer(np.array([d["m"] + 10], "<u%d" % osize).tobytes(), np.uint8)
     mrn.convert(mrn.View(s, "soa", n, base=dev(bad), m=d["m"]), dev_dest(s, "aos", n, d["m"]))
     assert mrn.sync() == mrn.EINVAL
+
+
+@pytest.mark.parametrize("case", ["canonical", "swapped_runs", "extra_records", "shuffled"])
+def test_split_pool_checks(case, jagged_path):
+    """The scan pass decides whether the pool can be converted as one plain
+    conversion (pool record j -> child row j): only for a canonical pool that
+    holds no other records.  Swapped runs, records beyond the children and a
+    shuffled pool must take the gathering pass; either way the offsets and
+    child rows equal the oracle's, and child rows past the written count
+    (capacity above the pool) keep their bytes."""
+    n = 5 * 1024 + 333
+    s, o, d = tracks(n, seed=61)
+    o_aos = oracle.pack(o, d, "aos")
+    m, lens = d["m"], d["lengths"]
+    if case == "swapped_runs":
+        order = np.arange(n)
+        nz = [i for i in range(2048, 3072) if lens[i] > 0]
+        order[nz[1]], order[nz[7]] = nz[7], nz[1]
+        o_aos = oracle.shuffle_pool(o, o_aos, order, gap=0)
+    elif case == "extra_records":  # canonical runs, then 50 records no parent owns
+        pool = np.concatenate([o_aos.pool[: m * 8], np.full(50 * 8, 7, np.uint8)])
+        o_aos = oracle.Side("aos", n, m + 50, base=o_aos.base, pool=pool)
+    elif case == "shuffled":
+        o_aos = oracle.shuffle_pool(o, o_aos, np.random.default_rng(5).permutation(n), gap=0)
+    pool_n = o_aos.m
+    cap = pool_n + 100
+    o_soa = oracle.convert(o, o_aos, "soa", m=m)
+    cols = [garbage(n * 4) for _ in range(3)]
+    offs = garbage((n + 1) * 4)
+    kids = [garbage(cap * 4) for _ in range(2)]
+    dst = mrn.View(s, "soa", n, columns=cols, offsets=offs, child_columns=kids, m=cap)
+    mrn.convert(dev_view(s, o_aos, o), dst)
+    assert mrn.sync() == mrn.OK
+    for c in range(3):
+        assert np.array_equal(host(cols[c]), oracle.region(o, o_soa, c))
+    assert np.array_equal(host(offs), oracle.region(o, o_soa, 3))
+    for c in range(2):
+        got = host(kids[c])
+        assert np.array_equal(got[: m * 4], oracle.region(o, o_soa, 4 + c)), "child column %d" % c
+        assert (got[m * 4:] == 0xA5).all(), "child rows past the count were written"
