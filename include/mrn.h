@@ -413,8 +413,10 @@ typedef struct mrn_batch_tune_result {
 
 /* Autotunes the launch shape of this batch on its own jobs: times launches
  * on `stream` for every chunk size in {1, 2, 4, 8, 16} and CTAs per SM in
- * {occupancy, 2}, keeps the fastest (the graph is re-captured) and reports
- * it.  The jobs' destinations are written by the trial launches. */
+ * {occupancy, 2}, times the fastest against the default twice more
+ * (alternately), keeps it only when it is at least 1% faster (the graph is
+ * re-captured) and reports the shape kept.  The jobs' destinations are
+ * written by the trial launches. */
 int mrn_batch_tune(mrn_batch* b, void* stream, mrn_batch_tune_result* out);
 
 typedef struct mrn_tune_result {
@@ -430,9 +432,11 @@ typedef struct mrn_tune_result {
 /* Times candidate launch shapes for converting n_hint records of `s` from
  * `src` to `dst` layouts on scratch device buffers: the TMA-staged kernel
  * (when buffers and tile fit) at two grid sizes, and the direct kernel over
- * threads per CTA, CTAs per SM and records per tile.  Caches the fastest for
- * this (schema hash, layout pair); later conversions and batches use it.
- * Synchronous.  `out` may be NULL. */
+ * threads per CTA, CTAs per SM and records per tile.  The fastest is timed
+ * against the default three more times (alternately) and kept only when it
+ * is at least 3% faster.  Caches the shape kept for this (schema hash,
+ * layout pair); later conversions and batches use it.  Synchronous.  `out`
+ * may be NULL. */
 int mrn_autotune(const mrn_schema* s, mrn_layout src, mrn_layout dst, uint64_t n_hint,
                  mrn_tune_result* out);
 /* Forgets every cached tuning result. */

@@ -596,6 +596,25 @@ int mrn_batch_tune(mrn_batch* b, void* stream, mrn_batch_tune_result* out) {
         best_cps = cps;
       }
     }
+  // the winner against the default, timed again alternately: kept only
+  // when at least 1% faster (one timing each can crown noise)
+  if (!rc && (best_chunk != def_chunk || best_cps != def_cps)) {
+    float td = 0, tw = 0;
+    for (int r = 0; r < 2 && !rc; ++r) {
+      float t = 0;
+      b->max_chunk = def_chunk;
+      b->ctas_per_sm = def_cps;
+      if (!(rc = time_it(&t))) td += t;
+      b->max_chunk = best_chunk;
+      b->ctas_per_sm = best_cps;
+      if (!rc && !(rc = time_it(&t))) tw += t;
+    }
+    if (!rc && !(tw < 0.99f * td)) {
+      best_chunk = def_chunk;
+      best_cps = def_cps;
+      best_ms = def_ms;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->max_chunk = best_chunk;

@@ -797,8 +797,8 @@ struct ScanShared {
 // Chunk c (of MRN_SCAN_CHUNK parents) of a split jagged AoS -> field-major
 // conversion: warp w sums the lengths of groups 32 w .. 32 w + 31 of the
 // chunk (lane l of a pass holds parent 32 g + l; lane i ends up holding group
-// i's sum and the spread of begin - exclusive offset over its parents with
-// children), the chunk's aggregate is published and the children before the
+// i's sum and the begin - exclusive offset its parents with children
+// share, if they do), the chunk's aggregate is published and the children before the
 // chunk come from a decoupled look-back over st[]; then every group's base
 // (children before it) goes to group_base.  The pool is canonical where each
 // group with children has begin - exclusive offset equal to its base for all
@@ -810,13 +810,17 @@ __device__ __forceinline__ void jag_scan_chunk(const JagPlan& jp, uint64_t c, un
   const char* base = jp.parent.src.base;
   const uint32_t stride = jp.parent.stride, vec = jp.parent.vec, len_off = jp.len_off, begin_off = jp.begin_off;
   const uint64_t g0 = c * kScanGroups + (uint64_t)warp * kScanWarpGroups;
-  unsigned long long gsum = 0, gmin = ~0ull, gmax = 0ull;  // lane i: group g0 + i
+  // lane i: group g0 + i's sum, the common begin - exclusive offset of its
+  // parents with children (gd), and whether they all share it (guni)
+  unsigned long long gsum = 0, gd = 0;
+  bool guni = true;
+  constexpr int U = 8;  // groups per pass (loads in flight per lane: 2 U)
 #pragma unroll 1
-  for (uint32_t i0 = 0; i0 < kScanWarpGroups; i0 += 4) {
-    uint32_t len[4];
-    uint64_t beg[4];
+  for (uint32_t i0 = 0; i0 < kScanWarpGroups; i0 += U) {
+    uint32_t len[U];
+    uint64_t beg[U];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < U; ++u) {
       const uint64_t r = (g0 + i0 + u) * 32 + lane;
       len[u] = 0;
       beg[u] = 0;
@@ -827,29 +831,37 @@ __device__ __forceinline__ void jag_scan_chunk(const JagPlan& jp, uint64_t c, un
       }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < U; ++u) {
       const uint64_t r = (g0 + i0 + u) * 32 + lane;
       const bool bad = r < n && (beg[u] > pool_n || (uint64_t)len[u] > pool_n - beg[u]);
       if (bad) flag_error(MRN_EINVAL);
-      const unsigned long long x = warp_incl_scan_u64(len[u], lane);
-      const unsigned long long excl = x - len[u];
-      const unsigned long long tot = __shfl_sync(0xffffffffu, x, 31);
-      unsigned long long dmin = ~0ull, dmax = 0ull;
-      if (bad) {
-        dmin = 0ull;
-        dmax = ~0ull;
-      } else if (len[u] > 0) {
-        dmin = dmax = beg[u] - excl;
-      }
+      // the exclusive prefix inside the group: 32-bit unless some length
+      // could carry past 32 bits (32 lengths below 2^26 cannot)
+      unsigned long long excl, tot;
+      if (__any_sync(0xffffffffu, len[u] >= (1u << 26))) {
+        const unsigned long long x = warp_incl_scan_u64(len[u], lane);
+        excl = x - len[u];
+        tot = __shfl_sync(0xffffffffu, x, 31);
+      } else {
+        uint32_t x = len[u];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        dmin = min(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
-        dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        excl = x - len[u];
+        tot = __reduce_add_sync(0xffffffffu, len[u]);
       }
+      // canonical here: every parent valid, and begin - exclusive offset
+      // the same for all parents with children
+      const unsigned long long d = beg[u] - excl;
+      const unsigned int has = __ballot_sync(0xffffffffu, len[u] > 0);
+      const unsigned long long d0 = __shfl_sync(0xffffffffu, d, has ? __ffs(has) - 1 : 0);
+      const bool uni = __all_sync(0xffffffffu, !bad && (len[u] == 0 || d == d0));
       if ((uint32_t)lane == i0 + u) {
         gsum = tot;
-        gmin = dmin;
-        gmax = dmax;
+        gd = d0;
+        guni = uni;
       }
     }
   }
@@ -881,7 +893,7 @@ __device__ __forceinline__ void jag_scan_chunk(const JagPlan& jp, uint64_t c, un
   const uint64_t g = g0 + lane;
   const bool have = g * 32 < n;
   const unsigned long long gb = sh.base + wbase + (x - gsum);
-  bool bad = have && gsum > 0 && !(gmin == gmax && gmin == gb);
+  bool bad = have && (!guni || (gsum > 0 && gd != gb));
   if (have) jp.group_base[g] = gb;
   if (have && (n - 1) / 32 == g) {
     const unsigned long long total = gb + gsum, end = jp.offset_base + total;
