@@ -317,7 +317,10 @@ int mrn_jagged_count(const mrn_view* src, uint64_t* m, void* stream);
  *          canonical, and a pass that gathers the children when it is not.
  *          Batches split every jagged AoS job whose pool fits the
  *          destination's child capacity.  A negative value turns split runs
- *          off (single conversions and batches). */
+ *          off (single conversions and batches);
+ *   key 5: parents up to which a single fused jagged AoS -> SoA / AoSoA
+ *          conversion uses tiles of 256 parents instead of 1,024 (default
+ *          250,000; -1: never). */
 int mrn_debug_set(int key, long long value);
 
 /* ------------------------------------------------------- transfer+convert */

@@ -25,6 +25,9 @@ std::atomic<int> g_force_direct{0};
 // jagged jobs (in one persistent launch the pools stream at the copy
 // rate) unless the value is negative.
 std::atomic<long long> g_split_parents{LLONG_MAX};
+// Parents up to which a single fused jagged AoS -> field-major conversion
+// takes tiles of MRN_JAG_SMALL_TILE parents (more CTAs for few parents).
+std::atomic<long long> g_small_tile_parents{250000};
 
 namespace {
 
@@ -600,13 +603,15 @@ int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
       const long long lim = g_split_parents.load();
       const bool split = lim >= 0 && src->n_records >= (uint64_t)lim && jagged_split_ok(s, &jp, &pool) &&
                          jp.parent.tg.tma;
+      const bool small = !split && (long long)src->n_records <= g_small_tile_parents.load();
       if (src->n_records > 0) {
-        const uint64_t sb = split ? jagged_split_scratch_bytes(src->n_records)
-                                  : jagged_scratch_bytes(jagged_tile_records(jp));
-        if (cudaMallocAsync(&scratch, sb, st) != cudaSuccess) return MRN_ENOMEM;
+        const uint64_t sb =
+            split ? jagged_split_scratch_bytes(src->n_records)
+                  : jagged_scratch_bytes(jagged_tile_records(jp), small ? MRN_JAG_SMALL_TILE : MRN_JAG_TILE);
+        if (scratch_alloc(&scratch, sb, st) != MRN_OK) return MRN_ENOMEM;
       }
-      rc = split ? launch_jagged_a2s_split(jp, pool, scratch, stream) : launch_jagged_a2s(jp, scratch, stream);
-      if (scratch) cudaFreeAsync(scratch, st);
+      rc = split ? launch_jagged_a2s_split(jp, pool, scratch, stream) : launch_jagged_a2s(jp, scratch, stream, small);
+      scratch_free(scratch, st);
       if (rc) return rc;
       if (fold) return MRN_OK;
     } else {
@@ -629,10 +634,7 @@ int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
         const uint64_t n = src->n_records;
         char* scratch = nullptr;
         const uint64_t beg_at = align_up(4 * n, 256);
-        if (cudaMallocAsync(reinterpret_cast<void**>(&scratch), beg_at + 8 * n, st) != cudaSuccess) {
-          cudaGetLastError();
-          return MRN_ENOMEM;
-        }
+        if (scratch_alloc(reinterpret_cast<void**>(&scratch), beg_at + 8 * n, st) != MRN_OK) return MRN_ENOMEM;
         rc = launch_len_begin(jp.offsets, jp.off_size, n, reinterpret_cast<unsigned int*>(scratch),
                               reinterpret_cast<unsigned long long*>(scratch + beg_at), stream);
         std::vector<void*> cols(fp->src.size());
@@ -647,7 +649,7 @@ int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
         pd.child_pool = pd.grandchild_pool = nullptr;
         if (!rc) rc = mrn_convert(&ps, &pd, stream);
         if (!rc) rc = launch_convert(kids, stream, nullptr);
-        cudaFreeAsync(scratch, st);
+        scratch_free(scratch, st);
         if (rc) return rc;
         return zero_dst_gaps(*dst, stream);
       }
@@ -711,13 +713,13 @@ int mrn_jagged_count(const mrn_view* src, uint64_t* m, void* stream) {
   p.n = src->n_records;
   p.src.base = static_cast<char*>(src->base);
   uint64_t* d = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&d), sizeof(uint64_t), st) != cudaSuccess) return MRN_ENOMEM;
+  if (scratch_alloc(reinterpret_cast<void**>(&d), sizeof(uint64_t), st) != MRN_OK) return MRN_ENOMEM;
   int rc = MRN_OK;
   if (cudaMemsetAsync(d, 0, sizeof(uint64_t), st) != cudaSuccess) rc = MRN_ECUDA;
   if (!rc) rc = launch_jagged_count(p, d, stream);
   uint64_t h = 0;
   if (!rc && cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = MRN_ECUDA;
-  cudaFreeAsync(d, st);
+  scratch_free(d, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) rc = MRN_ECUDA;
   if (!rc) *m = h;
   return rc;
@@ -732,6 +734,7 @@ int mrn_debug_set(int key, long long value) {
       return MRN_OK;
     case 3: g_force_direct.store(value ? 1 : 0); return MRN_OK;
     case 4: g_split_parents.store(value < 0 ? -1 : value); return MRN_OK;
+    case 5: g_small_tile_parents.store(value); return MRN_OK;
     default: return MRN_EINVAL;
   }
 }

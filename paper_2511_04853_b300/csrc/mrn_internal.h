@@ -88,6 +88,11 @@ uint64_t fm_gchild_col_start(const mrn_schema* s, int kind, uint32_t B, uint64_t
                              uint32_t g);
 
 // ---- device status word and scratch helpers (mrn_kernels.cu)
+// Stream-ordered scratch for one call, from the library's own pool on the
+// stream's device (it keeps up to 256 MiB reserved between calls); freed
+// in stream order with scratch_free.  MRN_ENOMEM on failure.
+int scratch_alloc(void** p, size_t bytes, void* stream);
+void scratch_free(void* p, void* stream);
 int device_sm_count();
 int read_and_clear_status(void* stream, uint32_t* bits);
 int status_from_bits(uint32_t bits);
@@ -141,9 +146,11 @@ int launch_convert(const ConvPlan& p, void* stream, const LaunchShape* shape, co
 void fill_stage_rec(const ConvPlan& p, StageRec* out);
 int launch_zero_gaps(const GapPlan& g, void* stream);
 // Jagged conversions.  `scratch` (AoS->SoA only) must hold
-// jagged_scratch_bytes(n) bytes; it is cleared on `stream` first.
-uint64_t jagged_scratch_bytes(uint64_t n);
-int launch_jagged_a2s(JagPlan& jp, void* scratch, void* stream);
+// jagged_scratch_bytes(n, tile) bytes for the launch's tile size; it is
+// cleared on `stream` first.  `small`: tiles of MRN_JAG_SMALL_TILE parents
+// (single conversions of few tiles) instead of MRN_JAG_TILE.
+uint64_t jagged_scratch_bytes(uint64_t n, uint32_t tile = MRN_JAG_TILE);
+int launch_jagged_a2s(JagPlan& jp, void* scratch, void* stream, bool small = false);
 // The same conversion split (JAG_SPLIT): the scan (group bases, offsets[n],
 // the check that the pool is canonical), the parents' data columns and
 // offsets as one staged conversion, the pool's records as one staged

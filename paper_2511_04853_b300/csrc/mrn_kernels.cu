@@ -131,19 +131,36 @@ __device__ __forceinline__ uint64_t read_offset(const char* offs, uint32_t osz, 
   return __ldg(reinterpret_cast<const unsigned long long*>(offs) + i);
 }
 
+// The shapes of a fused jagged tile: parents per tile and threads per CTA.
+// JagBig (1,024 parents, 512 threads) serves every launch but the small
+// single conversions, which take JagSmall (256 parents, 256 threads): a
+// collection of 100,000 parents then has 391 tiles to spread over the
+// SMs instead of 98.
+template <int TILE, int THREADS>
+struct JagCfg {
+  static constexpr int kTile = TILE, kThreads = THREADS, kWarps = THREADS / 32;
+  static_assert(TILE % THREADS == 0, "whole parents per thread");
+};
+using JagBig = JagCfg<MRN_JAG_TILE, MRN_JAG_THREADS>;
+using JagSmall = JagCfg<MRN_JAG_SMALL_TILE, MRN_JAG_SMALL_THREADS>;
+
 // Shared state of a jagged tile: per-parent arrays (JagShared), written only
 // after every warp has finished its parent conversion, and small per-warp
 // values (JagWarp).
-struct JagShared {
-  unsigned long long excl[MRN_JAG_TILE + 1];
-  unsigned long long beg[MRN_JAG_TILE];
+template <class Cfg>
+struct JagSharedT {
+  unsigned long long excl[Cfg::kTile + 1];
+  unsigned long long beg[Cfg::kTile];
 };
-struct JagWarp {
-  unsigned long long warp[MRN_JAG_WARPS];
-  unsigned long long kmin[MRN_JAG_WARPS], kmax[MRN_JAG_WARPS];  // per warp: min / max of begin - exclusive offset
+template <class Cfg>
+struct JagWarpT {
+  unsigned long long warp[Cfg::kWarps];
+  unsigned long long kmin[Cfg::kWarps], kmax[Cfg::kWarps];  // per warp: min / max of begin - exclusive offset
   unsigned long long base;
-  unsigned long long lsum[MRN_JAG_WARPS];  // per warp: sum of its lengths (early aggregate)
+  unsigned long long lsum[Cfg::kWarps];  // per warp: sum of its lengths (early aggregate)
 };
+using JagShared = JagSharedT<JagBig>;
+using JagWarp = JagWarpT<JagBig>;
 
 // Loads and stores of one column element of S bytes.
 template <int S>
@@ -240,15 +257,15 @@ __device__ __forceinline__ void child_column(const char* src, uint32_t stride, c
 // and split in registers, wider ones column by column.  When the tile's
 // children form one run of the pool (Run: beg[p] - excl[p] is the same `key`
 // for every parent with children), the parent lookup is skipped.
-template <bool Run, int S = kJagSlots>
-__device__ __forceinline__ void jagged_children(const JagPlan& jp, const JagShared& sh, unsigned long long agg,
+template <bool Run, class Cfg, int S = kJagSlots>
+__device__ __forceinline__ void jagged_children(const JagPlan& jp, const JagSharedT<Cfg>& sh, unsigned long long agg,
                                                 unsigned long long base, unsigned long long key, int lane,
                                                 int warp) {
   const ConvPlan& C = jp.child;
   const uint32_t nc = C.naos, stride = C.stride, vec = C.vec;
   const char* pool = C.src.base;
   constexpr unsigned long long kPass = 32 * S;
-  for (unsigned long long j0 = (unsigned long long)warp * kPass; j0 < agg; j0 += MRN_JAG_WARPS * kPass) {
+  for (unsigned long long j0 = (unsigned long long)warp * kPass; j0 < agg; j0 += Cfg::kWarps * kPass) {
     uint64_t si[S], di[S];
     uint32_t ld_ok = 0, st_ok = 0;
 #pragma unroll
@@ -258,7 +275,7 @@ __device__ __forceinline__ void jagged_children(const JagPlan& jp, const JagShar
       bool good = cok;
       si[u] = key + j;
       if (!Run && cok) {
-        int lo = 0, hi = MRN_JAG_TILE;
+        int lo = 0, hi = Cfg::kTile;
         while (hi - lo > 1) {
           const int mid = (lo + hi) >> 1;
           if (sh.excl[mid] <= j) lo = mid; else hi = mid;
@@ -315,14 +332,14 @@ __device__ __forceinline__ void jagged_children(const JagPlan& jp, const JagShar
 // The children of a jagged tile that form one run of the pool, for child
 // records of at most 8 bytes: slot j moves pool record key + j to row
 // base + j; each lane holds S records (one 64-bit word each) in flight.
-template <int S>
+template <int S, class Cfg>
 __device__ __forceinline__ void jagged_run_small(const JagPlan& jp, unsigned long long agg, unsigned long long base,
                                                  unsigned long long key, int lane, int warp) {
   const ConvPlan& C = jp.child;
   const uint32_t nc = C.naos, stride = C.stride, vec = C.vec;
   const char* pool = C.src.base;
   constexpr unsigned long long kPass = 32 * S;
-  for (unsigned long long j0 = (unsigned long long)warp * kPass; j0 < agg; j0 += MRN_JAG_WARPS * kPass) {
+  for (unsigned long long j0 = (unsigned long long)warp * kPass; j0 < agg; j0 += Cfg::kWarps * kPass) {
     uint64_t rec[S];
     uint32_t ok = 0;
 #pragma unroll
@@ -448,16 +465,15 @@ __device__ __forceinline__ unsigned long long jagged_lookback(unsigned long long
 // publishes its own sum before its look-back, and tiles are handed out in
 // increasing order, so every predecessor a look-back waits for is already
 // running.
-template <int VP, int VC>
+template <int VP, int VC, class Cfg = JagBig>
 __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile, unsigned long long* st,
-                                                uint32_t* tw_all, JagShared& sh, JagWarp& sw) {
+                                                uint32_t* tw_all, JagSharedT<Cfg>& sh, JagWarpT<Cfg>& sw) {
   constexpr int W = MRN_WIN_WORDS;
-  constexpr int K = MRN_JAG_TILE / MRN_JAG_THREADS;  // parents per thread
-  static_assert(MRN_JAG_TILE == K * MRN_JAG_THREADS, "whole parents per thread");
+  constexpr int K = Cfg::kTile / Cfg::kThreads;  // parents per thread
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t* tw = tw_all + warp * MRN_TW_WORDS(W);
   const ConvPlan& P = jp.parent;
-  const uint64_t t0 = tile * MRN_JAG_TILE;
+  const uint64_t t0 = tile * Cfg::kTile;
 
   // The tile's aggregate first, from the lengths alone, published at once:
   // the tiles after this one sum it in their look-back, which otherwise
@@ -471,7 +487,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
     unsigned long long own = 0;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const uint64_t r = t0 + k * MRN_JAG_THREADS + tid;
+      const uint64_t r = t0 + k * Cfg::kThreads + tid;
       if (r < P.n) {
         const char* q = P.src.base + r * P.stride + jp.len_off;
         if (P.vec >= 4) {
@@ -491,13 +507,13 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
     if (tid == 0) {
       unsigned long long a = 0;
 #pragma unroll
-      for (int w = 0; w < MRN_JAG_WARPS; ++w) a += sw.lsum[w];
+      for (int w = 0; w < Cfg::kWarps; ++w) a += sw.lsum[w];
       if (publish)
         st_release_u64(&st[tile], (tile == 0 ? MRN_TS_PREFIX : MRN_TS_AGG) | (a & MRN_TS_VALUE));
     }
   }
 
-  // Parents q = k * MRN_JAG_THREADS + tid of the tile (consecutive records
+  // Parents q = k * Cfg::kThreads + tid of the tile (consecutive records
   // per warp); then their lengths go to excl[] for the scan and their
   // begins (all ones for a parent whose children lie outside the pool) to
   // beg[].
@@ -505,7 +521,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
   uint64_t beg[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const uint64_t r = t0 + k * MRN_JAG_THREADS + tid;
+    const uint64_t r = t0 + k * Cfg::kThreads + tid;
     const bool ok = r < P.n;
     len[k] = 0;
     beg[k] = 0;
@@ -520,8 +536,8 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    sh.excl[k * MRN_JAG_THREADS + tid] = len[k];
-    sh.beg[k * MRN_JAG_THREADS + tid] = beg[k];
+    sh.excl[k * Cfg::kThreads + tid] = len[k];
+    sh.beg[k * Cfg::kThreads + tid] = beg[k];
   }
   __syncthreads();
 
@@ -539,16 +555,16 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
   if (lane == 31) sw.warp[warp] = x;
   __syncthreads();
   if (warp == 0) {
-    unsigned long long t = lane < MRN_JAG_WARPS ? sw.warp[lane] : 0ull;
+    unsigned long long t = lane < Cfg::kWarps ? sw.warp[lane] : 0ull;
 #pragma unroll
-    for (int o = 1; o < MRN_JAG_WARPS; o <<= 1) {
+    for (int o = 1; o < Cfg::kWarps; o <<= 1) {
       const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
       if (lane >= o) t += y;
     }
-    if (lane < MRN_JAG_WARPS) sw.warp[lane] = t;
+    if (lane < Cfg::kWarps) sw.warp[lane] = t;
   }
   __syncthreads();
-  const unsigned long long agg = sw.warp[MRN_JAG_WARPS - 1];
+  const unsigned long long agg = sw.warp[Cfg::kWarps - 1];
   // Exclusive offsets of the thread's parents written back in place; the
   // run test on the way: beg - excl equal for every parent with children
   // (a parent outside the pool fails it: min 0, max all ones).
@@ -569,7 +585,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
       e += l;
     }
   }
-  if (tid == MRN_JAG_THREADS - 1) sh.excl[MRN_JAG_TILE] = agg;
+  if (tid == Cfg::kThreads - 1) sh.excl[Cfg::kTile] = agg;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
@@ -599,7 +615,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
   kmin = ~0ull;
   kmax = 0ull;
 #pragma unroll
-  for (int w = 0; w < MRN_JAG_WARPS; ++w) {
+  for (int w = 0; w < Cfg::kWarps; ++w) {
     kmin = min(kmin, sw.kmin[w]);
     kmax = max(kmax, sw.kmax[w]);
   }
@@ -616,7 +632,7 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
   // Tile 0 of a single conversion zeroes the destination's gap bytes.
   if (tile == 0 && jp.ngaps && mode != JAG_CHILDREN)
     for (uint32_t k = 0; k < jp.ngaps; ++k)
-      for (uint32_t b = tid; b < jp.gap_len[k]; b += MRN_JAG_THREADS) jp.gap_base[jp.gap_off[k] + b] = 0;
+      for (uint32_t b = tid; b < jp.gap_len[k]; b += Cfg::kThreads) jp.gap_base[jp.gap_off[k] + b] = 0;
 
   // Offsets: offset_base + children before this parent (a collection of
   // no objects, given one tile, has the single offset offset_base).  Every
@@ -643,11 +659,11 @@ __device__ __forceinline__ void jagged_a2s_tile(const JagPlan& jp, uint64_t tile
 
   // Children, as one run of the pool when they form one.
   if (run && jp.child.stride <= 8)
-    jagged_run_small<kJagSlots>(jp, agg, base, kmin, lane, warp);
+    jagged_run_small<kJagSlots, Cfg>(jp, agg, base, kmin, lane, warp);
   else if (run)
-    jagged_children<true>(jp, sh, agg, base, kmin, lane, warp);
+    jagged_children<true, Cfg>(jp, sh, agg, base, kmin, lane, warp);
   else
-    jagged_children<false>(jp, sh, agg, base, 0ull, lane, warp);
+    jagged_children<false, Cfg>(jp, sh, agg, base, 0ull, lane, warp);
 }
 
 template <int VP, int VC>
@@ -663,6 +679,20 @@ __global__ void __launch_bounds__(MRN_JAG_THREADS, MRN_JAG_CTAS) k_jagged_a2s(co
   if (threadIdx.x == 0) s_tile = atomicAdd(jp.tile_counter, 1u);
   __syncthreads();
   jagged_a2s_tile<VP, VC>(jp, s_tile, jp.tile_state, tw_all, sh, sw);
+}
+
+// The same conversion in tiles of JagSmall (256 parents, one per thread),
+// for single conversions of few tiles (generic access widths).
+__global__ void __launch_bounds__(MRN_JAG_SMALL_THREADS, 6) k_jagged_a2s_small(const __grid_constant__ JagPlan jp) {
+  constexpr size_t kTw = JagSmall::kWarps * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t);
+  __shared__ __align__(16) unsigned char jag_raw[kTw > sizeof(JagSharedT<JagSmall>) ? kTw : sizeof(JagSharedT<JagSmall>)];
+  uint32_t* tw_all = reinterpret_cast<uint32_t*>(jag_raw);
+  JagSharedT<JagSmall>& sh = *reinterpret_cast<JagSharedT<JagSmall>*>(jag_raw);
+  __shared__ JagWarpT<JagSmall> sw;
+  __shared__ unsigned int s_tile;
+  if (threadIdx.x == 0) s_tile = atomicAdd(jp.tile_counter, 1u);
+  __syncthreads();
+  jagged_a2s_tile<0, 0, JagSmall>(jp, s_tile, jp.tile_state, tw_all, sh, sw);
 }
 
 // Fall-back pass of a split jagged AoS -> field-major conversion (plan mode
@@ -1672,6 +1702,62 @@ int occupancy(const void* fn, int threads, size_t smem) {
 
 }  // namespace
 
+// Scratch of the library's calls: stream-ordered allocations from a memory
+// pool the library owns, one per device, that keeps up to
+// kScratchKeepBytes reserved between calls.  (The device's default pool
+// returns its free memory at every synchronisation; a call whose scratch
+// must be mapped again then costs more than its kernel at small sizes.)
+// Under stream capture the allocation is an ordinary cudaMallocAsync.
+namespace {
+constexpr uint64_t kScratchKeepBytes = 256ull << 20;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {};
+
+cudaMemPool_t scratch_pool(int dev) {
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = kScratchKeepBytes;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = pool;
+  }
+  return g_pools[dev];
+}
+}  // namespace
+
+int scratch_alloc(void** p, size_t bytes, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  *p = nullptr;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  int dev = -1;
+  cudaMemPool_t pool = nullptr;
+  if (cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone &&
+      cudaStreamGetDevice(s, &dev) == cudaSuccess)
+    pool = scratch_pool(dev);
+  cudaGetLastError();
+  const cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return MRN_ENOMEM;
+  }
+  return MRN_OK;
+}
+
+void scratch_free(void* p, void* stream) {
+  if (p) cudaFreeAsync(p, static_cast<cudaStream_t>(stream));
+}
+
 int device_sm_count() {
   std::lock_guard<std::mutex> lk(g_mu);
   if (g_sm_count == 0) {
@@ -1752,11 +1838,10 @@ int launch_staged_job(BatchJob& job, void* stream, const LaunchShape& sh, const 
     // conversions of fewer than kDynamicTilesPerCta tiles per CTA do not
     // earn back.
     if (job.ntiles >= kDynamicTilesPerCta * cap) {
-      if (cudaMallocAsync(reinterpret_cast<void**>(&counter), 256, st) != cudaSuccess) {
-        cudaGetLastError();
+      if (scratch_alloc(reinterpret_cast<void**>(&counter), 256, st) != MRN_OK) {
         counter = nullptr;
       } else if (cudaMemsetAsync(counter, 0, sizeof(unsigned int), st) != cudaSuccess) {
-        cudaFreeAsync(counter, st);
+        scratch_free(counter, st);
         return MRN_ECUDA;
       } else {
         chunk = (uint32_t)kChunk;
@@ -1766,7 +1851,7 @@ int launch_staged_job(BatchJob& job, void* stream, const LaunchShape& sh, const 
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(chunks, cap));
     void* args[] = {&job, &chunk, &counter, &cond};
     const int rc = cuda_status(cudaLaunchKernel(fn, dim3(grid), dim3(kBThreads), args, kBatchSmem, st));
-    if (counter) cudaFreeAsync(counter, st);
+    if (counter) scratch_free(counter, st);
     return rc;
   }
 }
@@ -1819,8 +1904,8 @@ void fill_stage_rec(const ConvPlan& p, StageRec* out) {
   }
 }
 
-uint64_t jagged_scratch_bytes(uint64_t n) {
-  const uint64_t ntiles = (n + MRN_JAG_TILE - 1) / MRN_JAG_TILE;
+uint64_t jagged_scratch_bytes(uint64_t n, uint32_t tile) {
+  const uint64_t ntiles = (n + tile - 1) / tile;
   return 256 + ntiles * sizeof(unsigned long long);
 }
 
@@ -1869,7 +1954,7 @@ void* jag_s2a(uint32_t vp, uint32_t vc) {
 }
 }  // namespace
 
-int launch_jagged_a2s(JagPlan& jp, void* scratch, void* stream) {
+int launch_jagged_a2s(JagPlan& jp, void* scratch, void* stream, bool small) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const uint64_t n = jp.parent.n;
   if (n == 0) {
@@ -1877,16 +1962,18 @@ int launch_jagged_a2s(JagPlan& jp, void* scratch, void* stream) {
     return cuda_status(cudaGetLastError());
   }
   const uint64_t nt = jagged_tile_records(jp);  // AoSoA: whole blocks
-  jp.ntiles = (nt + MRN_JAG_TILE - 1) / MRN_JAG_TILE;
+  const uint32_t tile = small ? MRN_JAG_SMALL_TILE : MRN_JAG_TILE;
+  jp.ntiles = (nt + tile - 1) / tile;
   if (jp.ntiles > 0x7fffffffull) return MRN_EUNSUPPORTED;
   char* sc = static_cast<char*>(scratch);
   jp.tile_counter = reinterpret_cast<unsigned int*>(sc);
   jp.tile_state = reinterpret_cast<unsigned long long*>(sc + 256);
-  cudaError_t e = cudaMemsetAsync(sc, 0, jagged_scratch_bytes(nt), s);
+  cudaError_t e = cudaMemsetAsync(sc, 0, jagged_scratch_bytes(nt, tile), s);
   if (e != cudaSuccess) return cuda_status(e);
-  void* fn = jag_a2s(jp.parent.vec, jp.child.vec);
+  void* fn = small ? reinterpret_cast<void*>(&k_jagged_a2s_small) : jag_a2s(jp.parent.vec, jp.child.vec);
   void* args[] = {&jp};
-  e = cudaLaunchKernel(fn, dim3((unsigned)jp.ntiles), dim3(MRN_JAG_THREADS), args, 0, s);
+  e = cudaLaunchKernel(fn, dim3((unsigned)jp.ntiles), dim3(small ? MRN_JAG_SMALL_THREADS : MRN_JAG_THREADS), args, 0,
+                       s);
   return cuda_status(e);
 }
 
@@ -2238,7 +2325,7 @@ int launch_moves(const MoveRange* r, size_t nr, void* stream) {
   if (rc == MRN_OK && P->nseg) {
     void* scratch = nullptr;
     const size_t sb = 256 + chunks * sizeof(unsigned int);
-    rc = cuda_status(cudaMallocAsync(&scratch, sb, st));
+    rc = scratch_alloc(&scratch, sb, st);
     if (rc == MRN_OK) {
       rc = cuda_status(cudaMemsetAsync(scratch, 0, sb, st));
       P->counter = static_cast<unsigned int*>(scratch);
@@ -2253,9 +2340,7 @@ int launch_moves(const MoveRange* r, size_t nr, void* stream) {
         rc = cuda_status(cudaLaunchKernel(reinterpret_cast<const void*>(&k_move), dim3(grid), dim3(kMoveThreads),
                                           args, 0, st));
       }
-      cudaFreeAsync(scratch, st);
-    } else {
-      cudaGetLastError();
+      scratch_free(scratch, st);
     }
   }
   delete P;

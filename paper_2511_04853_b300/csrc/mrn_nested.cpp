@@ -101,12 +101,9 @@ int convert_nested(const mrn_view& src, const mrn_view& dst, void* stream) {
   const uint64_t len_at = lb_bytes, beg_at = align_up(len_at + 4 * mcap, 256),
                  rec_at = align_up(beg_at + 8 * mcap, 256), tot_at = align_up(rec_at + 16 * mcap, 256);
   char* scratch = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&scratch), tot_at + 256, st) != cudaSuccess) {
-    cudaGetLastError();
-    return MRN_ENOMEM;
-  }
+  if (scratch_alloc(reinterpret_cast<void**>(&scratch), tot_at + 256, st) != MRN_OK) return MRN_ENOMEM;
   auto done = [&](int r) {
-    cudaFreeAsync(scratch, st);
+    scratch_free(scratch, st);
     return r;
   };
   C.aos_cols[C.naos++] = ColPlan{4, (int16_t)nc, ch->len_off};

@@ -210,6 +210,8 @@ inline uint64_t staged_tile_count(uint64_t n, uint64_t nrec, uint32_t T, uint32_
 #define MRN_JAG_CTAS 3       // resident jagged CTAs per SM the kernels are compiled for
 #endif
 #define MRN_JAG_WARPS (MRN_JAG_THREADS / 32)
+#define MRN_JAG_SMALL_TILE 256     // parents per tile of small single conversions
+#define MRN_JAG_SMALL_THREADS 256
 #define MRN_JAG_CHILD_GROUP 128  // child records per warp group of a jagged SoA -> AoS conversion
 
 // One job of a batched launch: a plain conversion (plan in jp.parent), a

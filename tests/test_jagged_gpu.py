@@ -14,16 +14,21 @@ from gpu_util import dev, dev_dest, dev_view, garbage, host, torch
 pytestmark = pytest.mark.gpu
 
 SPLIT_DEFAULT = 2**63 - 1  # parents from which single conversions run split (debug key 4): never
+SMALL_DEFAULT = 250000  # parents up to which fused conversions take 256-parent tiles (debug key 5)
 
 
-@pytest.fixture(autouse=True, params=["fused", "split"])
+@pytest.fixture(autouse=True, params=["fused", "fused_big", "split"])
 def jagged_path(request):
-    """Every test of this module runs twice: with jagged AoS -> field-major
-    conversions fused (the tiles gather their own children) and split (scan
-    pass, pool conversion when the pool is canonical, fall-back pass)."""
-    mrn.debug_set(4, -1 if request.param == "fused" else 0)
+    """Every test of this module runs three times: with jagged AoS ->
+    field-major conversions fused (the tiles gather their own children) in
+    tiles of 256 parents (the default up to 250,000 parents) and of 1,024,
+    and split (scan, parents, pool conversion when the pool is canonical,
+    fall-back pass)."""
+    mrn.debug_set(4, 0 if request.param == "split" else -1)
+    mrn.debug_set(5, -1 if request.param == "fused_big" else SMALL_DEFAULT)
     yield request.param
     mrn.debug_set(4, SPLIT_DEFAULT)
+    mrn.debug_set(5, SMALL_DEFAULT)
 
 
 def tracks(n, seed=2, **kw):
