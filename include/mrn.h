@@ -393,8 +393,9 @@ int mrn_batch_launch(mrn_batch* b, void* stream);
  * gather.
  * With use_graph = 1 the events are record nodes of a second graph of the
  * same work, captured at the first call and pointed at the given events at
- * each call; a batch without jobs of one kind records two events back to
- * back.  For measuring each kernel of a replay; no counterpart in the
+ * each call (three distinct events, else MRN_EINVAL; the events of earlier
+ * calls may have been destroyed since); a batch without jobs of one kind
+ * records two events back to back.  For measuring each kernel of a replay; no counterpart in the
  * paper (the batched form is not the paper's). */
 int mrn_batch_launch_timed(mrn_batch* b, void* stream, void* ev_begin, void* ev_mid, void* ev_end);
 /* Baseline: runs the same jobs with one mrn_convert launch per job. */

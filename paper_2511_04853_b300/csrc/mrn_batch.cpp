@@ -464,7 +464,8 @@ int mrn_batch_launch(mrn_batch* b, void* stream) {
 }
 
 int mrn_batch_launch_timed(mrn_batch* b, void* stream, void* ev_begin, void* ev_mid, void* ev_end) {
-  if (!b || !ev_begin || !ev_mid || !ev_end) return MRN_EINVAL;
+  if (!b || !ev_begin || !ev_mid || !ev_end || ev_begin == ev_mid || ev_mid == ev_end || ev_begin == ev_end)
+    return MRN_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaEvent_t ev[3] = {static_cast<cudaEvent_t>(ev_begin), static_cast<cudaEvent_t>(ev_mid),
                        static_cast<cudaEvent_t>(ev_end)};
@@ -481,11 +482,16 @@ int mrn_batch_launch_timed(mrn_batch* b, void* stream, void* ev_begin, void* ev_
       return rc;
     }
   }
-  for (int i = 0; i < 3; ++i)
-    if (cudaGraphExecEventRecordNodeSetEvent(b->texec, b->tnode[i], ev[i]) != cudaSuccess) {
-      cudaGetLastError();
-      return MRN_ECUDA;
-    }
+  // The nodes still name the previous call's events, which the caller may
+  // have destroyed since; a new event can then have the address of one
+  // that another node names, and two record nodes may not share an event.
+  // So every node goes back to the batch's own placeholder first.
+  for (int pass = 0; pass < 2; ++pass)
+    for (int i = 0; i < 3; ++i)
+      if (cudaGraphExecEventRecordNodeSetEvent(b->texec, b->tnode[i], pass ? ev[i] : b->tev[i]) != cudaSuccess) {
+        cudaGetLastError();
+        return MRN_ECUDA;
+      }
   return cudaGraphLaunch(b->texec, s) == cudaSuccess ? MRN_OK : MRN_ECUDA;
 }
 

@@ -340,3 +340,31 @@ def test_mixed_size_law_batch_matches_oracle_with_timed_launch():
 def torch_mod():
     import torch
     return torch
+
+
+def test_timed_launch_with_fresh_events_each_time():
+    """mrn_batch_launch_timed points the graph's three event-record nodes at
+    the caller's events on every call.  Events destroyed after one call and
+    created anew for the next may reuse the addresses the nodes still name;
+    the call must still succeed, measure, and give the oracle's bytes.
+    Repeated events are refused."""
+    import gc
+    t = torch_mod()
+    jobs = make_jobs(41, 12)
+    b = mrn.Batch([(s, d) for s, d, _, _ in jobs], use_graph=True)
+    for rnd in range(8):
+        ev = [t.cuda.Event(enable_timing=True) for _ in range(3)]
+        for _, d, _, _ in jobs:
+            d.tensors[0].fill_(0xA5)
+        b.launch_timed(*ev)
+        assert mrn.sync() == mrn.OK
+        t.cuda.synchronize()
+        assert ev[0].elapsed_time(ev[2]) > 0, "round %d" % rnd
+        for i, (s, d, want, name) in enumerate(jobs):
+            assert np.array_equal(result(d, want, name), want), "round %d job %d" % (rnd, i)
+        del ev
+        gc.collect()
+    e = t.cuda.Event(enable_timing=True)
+    e.record()
+    with pytest.raises(mrn.MrnError):
+        b.launch_timed(e, e, t.cuda.Event(enable_timing=True))
