@@ -602,7 +602,10 @@ def run_mine(args, rank, world):
     for name in () if profiling else ("points", "cells"):
         s = mrn.Schema(datagen.WORKLOAD_SCHEMAS[name])
         for dk, db in MIXED_TARGETS:
-            r = mrn.autotune(s, "aos", dk, 1 << 22, 0, db)
+            # tuned on 2^25 records (1.0-1.3 GB per pair, eight times the L2 or
+            # more): the batch streams every job from HBM, and at a few times
+            # the L2 the direct path wins on cache hits it will not get here
+            r = mrn.autotune(s, "aos", dk, 1 << 25, 0, db)
             tuned["%s_aos_to_%s%s" % (name, dk, db or "")] = {k: r[k] for k in ("staged", "threads",
                                                                                "tile_records", "ctas_per_sm")}
     batch = mrn.Batch(M["pairs"], use_graph=True)
