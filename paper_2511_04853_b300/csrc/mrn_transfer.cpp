@@ -227,6 +227,13 @@ void chunk_geometry(const mrn_view& src, const mrn_view& dst, uint64_t chunk_byt
 }
 }  // namespace
 
+uint64_t slot_stride(uint64_t chunk_bytes, uint64_t slot_bytes) {
+  // a chunk's staged view exceeds chunk_bytes by at most one staging
+  // granule of records and its regions' 128-byte alignment
+  const uint64_t base = align_up(chunk_bytes, 4096) + (64ull << 10);
+  return slot_bytes <= base ? base : align_up(slot_bytes, 4096);
+}
+
 uint64_t TransferEngine::staging_bytes(const mrn_view& src, const mrn_view& dst, uint64_t chunk_bytes,
                                        int n_slots) {
   const bool whole = src.schema->has_jagged;
@@ -239,8 +246,9 @@ uint64_t TransferEngine::staging_bytes(const mrn_view& src, const mrn_view& dst,
     return staged_view(like, nullptr, &tmp, a, b);
   }
   uint64_t R, slot;
-  chunk_geometry(src, dst, chunk_bytes ? chunk_bytes : (4ull << 20), &R, &slot);
-  return slot * (uint64_t)std::max(1, std::min(16, n_slots ? n_slots : 4));
+  const uint64_t cb = chunk_bytes ? chunk_bytes : (4ull << 20);
+  chunk_geometry(src, dst, cb, &R, &slot);
+  return slot_stride(cb, slot) * (uint64_t)std::max(1, std::min(16, n_slots ? n_slots : 4));
 }
 
 namespace {
@@ -267,14 +275,39 @@ int TransferEngine::run(const mrn_view& src, const mrn_view& dst, uint64_t chunk
   if (rc) return rc;
   if (!chunk_bytes) chunk_bytes = 4ull << 20;
   n_slots = std::max(1, std::min(16, n_slots ? n_slots : 4));
+  const bool chunked = !same_layout(src, dst) && !src.schema->has_jagged;
+  const uint64_t need = same_layout(src, dst) ? 0 : staging_bytes(src, dst, chunk_bytes, n_slots);
+  char* stage = arena;
+  if (!same_layout(src, dst)) {
+    if (!stage) {
+      if ((rc = ensure_staging(need))) return rc;
+      stage = staging_;
+    } else if (arena_bytes < need) {
+      return MRN_ENOMEM;
+    }
+  }
+  uint64_t R = 0, slot_bytes = 0, stride = 0;
+  if (chunked) {
+    chunk_geometry(src, dst, chunk_bytes, &R, &slot_bytes);
+    stride = slot_stride(chunk_bytes, slot_bytes);
+  }
   // The staging memory and both internal streams are shared by every call
-  // of this engine, whatever stream it came from: this call's copies and
-  // conversions start only after the previous call's have all finished
-  // (ev_done_ is recorded once both streams have joined), and after the
-  // caller's earlier work.  A call's own chunks still overlap each other.
-  if (cudaStreamWaitEvent(s_copy_, ev_done_, 0) != cudaSuccess ||
-      cudaStreamWaitEvent(s_conv_, ev_done_, 0) != cudaSuccess)
-    return MRN_ECUDA;
+  // of this engine, whatever stream it came from.  A chunked call that
+  // takes the same slots as the previous one waits for each slot it
+  // reuses (the slot events); any other call starts only after the
+  // previous call's copies and conversions have all finished (ev_done_ is
+  // recorded once both streams have joined).  Either way it starts after
+  // the caller's earlier work, and a call's own chunks overlap each other.
+  const bool reuse = chunked && stage == pipe_stage_ && stride == pipe_stride_ && n_slots == pipe_slots_;
+  if (!reuse) {
+    if (cudaStreamWaitEvent(s_copy_, ev_done_, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(s_conv_, ev_done_, 0) != cudaSuccess)
+      return MRN_ECUDA;
+    next_slot_ = 0;
+  }
+  pipe_stage_ = chunked ? stage : nullptr;
+  pipe_stride_ = stride;
+  pipe_slots_ = chunked ? n_slots : 0;
   if (cudaEventRecord(ev_start_, user) != cudaSuccess) return MRN_ECUDA;
   cudaStreamWaitEvent(s_copy_, ev_start_, 0);
   cudaStreamWaitEvent(s_conv_, ev_start_, 0);
@@ -289,17 +322,8 @@ int TransferEngine::run(const mrn_view& src, const mrn_view& dst, uint64_t chunk
     rc = copy_parts(view_parts(src), view_parts(dst), kind, s_copy_);
     if (!rc && h2d) rc = zero_dst_gaps(dst, s_copy_);
   } else {
-    const uint64_t need = staging_bytes(src, dst, chunk_bytes, n_slots);
-    char* stage = arena;
-    if (!stage) {
-      rc = ensure_staging(need);
-      stage = staging_;
-    } else if (arena_bytes < need) {
-      rc = MRN_ENOMEM;
-    }
-    if (!rc)
-      rc = src.schema->has_jagged ? run_whole(src, dst, user, stage, need)
-                                  : run_chunked(src, dst, chunk_bytes, n_slots, user, stage, need);
+    rc = src.schema->has_jagged ? run_whole(src, dst, user, stage, need)
+                                : run_chunked(src, dst, R, stride, n_slots, stage);
   }
   // Every return path after ev_start_ joins the two streams and orders the
   // caller's stream after them, so that work already queued by a call that
@@ -336,19 +360,18 @@ int TransferEngine::run_whole(const mrn_view& src, const mrn_view& dst, cudaStre
   return copy_parts(from, to, cudaMemcpyDeviceToHost, s_copy_);
 }
 
-int TransferEngine::run_chunked(const mrn_view& src, const mrn_view& dst, uint64_t chunk_bytes,
-                                int n_slots, cudaStream_t, char* stage, uint64_t) {
+int TransferEngine::run_chunked(const mrn_view& src, const mrn_view& dst, uint64_t R, uint64_t slot_bytes,
+                                int n_slots, char* stage) {
   const bool h2d = is_host(src);
   const mrn_view& hv = h2d ? src : dst;
   const mrn_view& dv = h2d ? dst : src;
-  uint64_t R, slot_bytes;
-  chunk_geometry(src, dst, chunk_bytes, &R, &slot_bytes);
   const uint64_t n = src.n_records;
   int rc;
   std::vector<void*> hc, dc, sc, sc2;
-  for (uint64_t k = 0, r0 = 0; r0 < n; ++k, r0 += R) {
+  for (uint64_t r0 = 0; r0 < n; r0 += R) {
     const uint64_t cnt = std::min(R, n - r0);
-    const int slot = (int)(k % (uint64_t)n_slots);
+    const int slot = next_slot_;
+    next_slot_ = (next_slot_ + 1) % n_slots;
     mrn_view hsub = sub_view(hv, r0, cnt, hc);
     mrn_view dsub = sub_view(dv, r0, cnt, dc);
     mrn_view like = hv;

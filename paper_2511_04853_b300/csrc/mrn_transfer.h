@@ -56,8 +56,7 @@ class TransferEngine {
   int ensure_staging(uint64_t bytes);
   int run_whole(const mrn_view& src, const mrn_view& dst, cudaStream_t user, char* stage,
                 uint64_t stage_bytes);
-  int run_chunked(const mrn_view& src, const mrn_view& dst, uint64_t chunk_bytes, int n_slots,
-                  cudaStream_t user, char* stage, uint64_t stage_bytes);
+  int run_chunked(const mrn_view& src, const mrn_view& dst, uint64_t R, uint64_t stride, int n_slots, char* stage);
 
   bool ready_ = false;
   cudaStream_t s_copy_ = nullptr, s_conv_ = nullptr;
@@ -65,6 +64,20 @@ class TransferEngine {
   cudaEvent_t ev_start_ = nullptr, ev_copy_done_ = nullptr, ev_done_ = nullptr;
   char* staging_ = nullptr;
   uint64_t staging_bytes_ = 0;
+  // The slots the last chunked call used (staging base, slot stride, slot
+  // count) and the slot its successor takes first.  A chunked call with the
+  // same slots waits only for each slot it reuses, so its first copies
+  // overlap the previous call's last conversions; any other call waits for
+  // the previous call to finish.
+  const char* pipe_stage_ = nullptr;
+  uint64_t pipe_stride_ = 0;
+  int pipe_slots_ = 0;
+  int next_slot_ = 0;
 };
+
+// Staging slot stride of chunked calls with `chunk_bytes` chunks: the same
+// for every schema and layout pair whose chunk fits it (so that their calls
+// can share slots), else the chunk's own size.
+uint64_t slot_stride(uint64_t chunk_bytes, uint64_t slot_bytes);
 
 }  // namespace mrn
