@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(256) k_convert(const __grid_constant__ ConvPla
 // ------------------------------------------------- staged tile transform
 
 // All threads: source tile -> destination tile in shared memory.  Wide:
-// the tables may hold widened fields (k_convert_ws<true>, for single
+// the tables may hold widened fields (k_convert_ws<true, false>, for single
 // conversions that have them; no other instance carries the branch).
 template <bool Wide>
 __device__ __forceinline__ void tma_transform(const TileHdr& h, uint32_t desc, const char* st, char* dt, uint32_t R,
@@ -1518,7 +1518,11 @@ __device__ __forceinline__ void batch_storer(const BatchJob* __restrict__ jobs, 
   bulk_wait_all();
 }
 
-template <bool kStatic, bool kWide>
+// kJag: the instance meets parents jobs of split jagged conversions (their
+// offsets epilogue is compiled in; where it cannot occur, leaving it out
+// keeps the transform's register allocation: single points AoS -> SoA at
+// 2^26 records 0.718 ms with it, 0.672 without).
+template <bool kStatic, bool kWide, bool kJag>
 __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
                                            const unsigned long long* __restrict__ first_tile, unsigned int njobs,
                                            unsigned long long total_tiles, unsigned int* counter,
@@ -1596,7 +1600,7 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
       tma_transform<kWide>(sd->h, smem_u32(sd->d), m.src(s), m.dst(d), ts.staged, lane, warp);
       // parents of a split jagged job: the offsets, from the staged lengths
       // (before the source stage is released)
-      if (ts.jag) jag_offsets_staged(jobs[ts.job].jp, ts.local, ts.staged, m.src(s), sd->h, lane, warp);
+      if (kJag && ts.jag) jag_offsets_staged(jobs[ts.job].jp, ts.local, ts.staged, m.src(s), sd->h, lane, warp);
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
@@ -1620,7 +1624,7 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
           r1 = r0 + J.tile_records;
         }
         conv_range<0, kBWin>(P, r0, r1, tw, lane, warp, 8);
-        if (J.kind == JOB_JAG_PARENTS) jag_offsets_direct(J.jp, r0, r1, lane, warp, 8);
+        if (kJag && J.kind == JOB_JAG_PARENTS) jag_offsets_direct(J.jp, r0, r1, lane, warp, 8);
       } else if (J.kind == JOB_JAG_S2A) {
         jagged_s2a_group<0, 0, kBWin>(J.jp, local * 8 + warp, J.parent_groups, tw, lane);
       } else {
@@ -1643,7 +1647,7 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
                                                         unsigned int* counter, uint32_t chunk,
                                                         const unsigned int* conds) {
   extern __shared__ __align__(128) char batch_smem[];
-  batch_main<false, false>(jobs, first_tile, njobs, total_tiles, counter, chunk, batch_smem, conds);
+  batch_main<false, false, true>(jobs, first_tile, njobs, total_tiles, counter, chunk, batch_smem, conds);
 }
 
 // One staged conversion through the same warp-specialized pipeline: the
@@ -1653,14 +1657,15 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
 // faster take more of them.  kWide: the instance for conversions whose
 // plan stores fields wider over an AoS destination's padding.
 // With `cond`, the launch does nothing when *cond != 0 (the child pool of a
-// split jagged conversion that the scan found not canonical).
-template <bool kWide>
+// split jagged conversion that the scan found not canonical).  kJag: the
+// instance for the parents job of a split jagged conversion.
+template <bool kWide, bool kJag>
 __global__ void __launch_bounds__(kBThreads, 3) k_convert_ws(const __grid_constant__ BatchJob job,
                                                              uint32_t chunk, unsigned int* counter,
                                                              const unsigned int* cond) {
   if (cond && ld_relaxed_u32(cond) != 0) return;
   extern __shared__ __align__(128) char batch_smem[];
-  batch_main<true, kWide>(&job, nullptr, 1u, job.ntiles, counter, chunk, batch_smem, nullptr);
+  batch_main<true, kWide, kJag>(&job, nullptr, 1u, job.ntiles, counter, chunk, batch_smem, nullptr);
 }
 
 // ================================================================== host
@@ -1826,8 +1831,9 @@ int launch_staged_job(BatchJob& job, void* stream, const LaunchShape& sh, const 
     job.ntiles = staged_tile_count(p.n, nrec, p.tg.T, p.tg.G);
     // the instance with the widened-field transform only for plans that
     // have widened fields: the branch costs the others a few percent
-    const void* fn = p.dst.kind == K_AOS && p.tg.nwide ? reinterpret_cast<const void*>(&k_convert_ws<true>)
-                                                       : reinterpret_cast<const void*>(&k_convert_ws<false>);
+    const void* fn = job.kind == JOB_JAG_PARENTS ? reinterpret_cast<const void*>(&k_convert_ws<false, true>)
+                     : p.dst.kind == K_AOS && p.tg.nwide ? reinterpret_cast<const void*>(&k_convert_ws<true, false>)
+                                                         : reinterpret_cast<const void*>(&k_convert_ws<false, false>);
     allow_batch_smem(fn);
     const int occ = occupancy(fn, kBThreads, kBatchSmem);
     const int per_sm = sh.ctas_per_sm ? std::min((int)sh.ctas_per_sm, occ) : occ;
