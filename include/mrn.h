@@ -351,8 +351,10 @@ typedef struct mrn_transfer_opts {
  * Jagged schemas: the whole source is staged, then converted.
  * Ordered after prior work on `stream`; later work on `stream` waits for
  * it.  Each device has one pipeline per direction: calls in the same
- * direction run one after another, a host->device and a device->host call
- * issued on different streams overlap (both directions of the host link).
+ * direction write their destinations in call order (a call's first copies
+ * may overlap the previous call's last conversions, through staging slots
+ * the two do not share), and a host->device and a device->host call issued
+ * on different streams overlap (both directions of the host link).
  * Pageable host memory works but serialises the copies.  With
  * MRN_TRANSFER_ZERO_COPY in opts->flags the kernel moves the data over the
  * host link itself (see above), on `stream`. */

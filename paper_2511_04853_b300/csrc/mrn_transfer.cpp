@@ -164,6 +164,10 @@ TransferEngine::~TransferEngine() {
   cudaEventDestroy(ev_start_);
   cudaEventDestroy(ev_copy_done_);
   cudaEventDestroy(ev_done_);
+  for (int h = 0; h < 2; ++h) {
+    cudaEventDestroy(ev_whole_free_[h]);
+    if (whole_[h]) cudaFree(whole_[h]);
+  }
   cudaStreamDestroy(s_copy_);
   cudaStreamDestroy(s_conv_);
   if (staging_) cudaFree(staging_);
@@ -183,7 +187,9 @@ int TransferEngine::init() {
       return MRN_ECUDA;
   if (cudaEventCreateWithFlags(&ev_start_, fl) != cudaSuccess ||
       cudaEventCreateWithFlags(&ev_copy_done_, fl) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ev_done_, fl) != cudaSuccess)
+      cudaEventCreateWithFlags(&ev_done_, fl) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ev_whole_free_[0], fl) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ev_whole_free_[1], fl) != cudaSuccess)
     return MRN_ECUDA;
   ready_ = true;
   return MRN_OK;
@@ -202,6 +208,22 @@ int TransferEngine::ensure_staging(uint64_t bytes) {
     return MRN_ENOMEM;
   }
   staging_bytes_ = bytes;
+  return MRN_OK;
+}
+
+int TransferEngine::ensure_whole(int h, uint64_t bytes) {
+  if (bytes <= whole_bytes_[h]) return MRN_OK;
+  cudaStreamSynchronize(s_copy_);
+  cudaStreamSynchronize(s_conv_);
+  if (whole_[h]) cudaFree(whole_[h]);
+  whole_[h] = nullptr;
+  whole_bytes_[h] = 0;
+  if (cudaMalloc(&whole_[h], bytes) != cudaSuccess) {
+    whole_[h] = nullptr;
+    cudaGetLastError();
+    return MRN_ENOMEM;
+  }
+  whole_bytes_[h] = bytes;
   return MRN_OK;
 }
 
@@ -275,10 +297,19 @@ int TransferEngine::run(const mrn_view& src, const mrn_view& dst, uint64_t chunk
   if (rc) return rc;
   if (!chunk_bytes) chunk_bytes = 4ull << 20;
   n_slots = std::max(1, std::min(16, n_slots ? n_slots : 4));
-  const bool chunked = !same_layout(src, dst) && !src.schema->has_jagged;
-  const uint64_t need = same_layout(src, dst) ? 0 : staging_bytes(src, dst, chunk_bytes, n_slots);
+  const bool equal = same_layout(src, dst);
+  const bool chunked = !equal && !src.schema->has_jagged;
+  // a whole source staged in one of the engine's two whole buffers
+  const bool whole_own = !equal && !chunked && !arena;
+  const uint64_t need = equal ? 0 : staging_bytes(src, dst, chunk_bytes, n_slots);
   char* stage = arena;
-  if (!same_layout(src, dst)) {
+  int whole_h = -1;
+  if (whole_own) {
+    whole_h = next_whole_;
+    if ((rc = ensure_whole(whole_h, need))) return rc;
+    next_whole_ ^= 1;
+    stage = whole_[whole_h];
+  } else if (!equal) {
     if (!stage) {
       if ((rc = ensure_staging(need))) return rc;
       stage = staging_;
@@ -293,21 +324,35 @@ int TransferEngine::run(const mrn_view& src, const mrn_view& dst, uint64_t chunk
   }
   // The staging memory and both internal streams are shared by every call
   // of this engine, whatever stream it came from.  A chunked call that
-  // takes the same slots as the previous one waits for each slot it
-  // reuses (the slot events); any other call starts only after the
-  // previous call's copies and conversions have all finished (ev_done_ is
-  // recorded once both streams have joined).  Either way it starts after
-  // the caller's earlier work, and a call's own chunks overlap each other.
+  // takes the same slots as the previous chunked call waits for each slot
+  // it reuses (the slot events); a call that stages a whole source in one
+  // of the engine's two whole buffers waits until that buffer is free.
+  // Any other call (equal layouts, whose copies write the destination
+  // directly, included) starts only after the previous call's copies and
+  // conversions have all finished (ev_done_ is recorded once both streams
+  // have joined).  Destinations are therefore written in call order:
+  // conversions run in order on s_conv_ and copies to the host in order on
+  // s_copy_.  Either way a call starts after the caller's earlier work, and
+  // its own chunks overlap each other.
   const bool reuse = chunked && stage == pipe_stage_ && stride == pipe_stride_ && n_slots == pipe_slots_;
-  if (!reuse) {
+  if (whole_own) {
+    if (cudaStreamWaitEvent(s_copy_, ev_whole_free_[whole_h], 0) != cudaSuccess ||
+        cudaStreamWaitEvent(s_conv_, ev_whole_free_[whole_h], 0) != cudaSuccess)
+      return MRN_ECUDA;
+  } else if (!reuse) {
     if (cudaStreamWaitEvent(s_copy_, ev_done_, 0) != cudaSuccess ||
         cudaStreamWaitEvent(s_conv_, ev_done_, 0) != cudaSuccess)
       return MRN_ECUDA;
     next_slot_ = 0;
   }
-  pipe_stage_ = chunked ? stage : nullptr;
-  pipe_stride_ = stride;
-  pipe_slots_ = chunked ? n_slots : 0;
+  if (chunked) {
+    pipe_stage_ = stage;
+    pipe_stride_ = stride;
+    pipe_slots_ = n_slots;
+  } else if (!whole_own) {  // an arena's whole source or equal layouts: the slots start over
+    pipe_stage_ = nullptr;
+    pipe_slots_ = 0;
+  }
   if (cudaEventRecord(ev_start_, user) != cudaSuccess) return MRN_ECUDA;
   cudaStreamWaitEvent(s_copy_, ev_start_, 0);
   cudaStreamWaitEvent(s_conv_, ev_start_, 0);
@@ -324,6 +369,11 @@ int TransferEngine::run(const mrn_view& src, const mrn_view& dst, uint64_t chunk
   } else {
     rc = src.schema->has_jagged ? run_whole(src, dst, user, stage, need)
                                 : run_chunked(src, dst, R, stride, n_slots, stage);
+    // the whole buffer is free once the stream that reads it last is past
+    // this call (host -> device: the conversion; device -> host: the copy)
+    if (whole_own && cudaEventRecord(ev_whole_free_[whole_h], is_host(src) ? s_conv_ : s_copy_) != cudaSuccess &&
+        !rc)
+      rc = MRN_ECUDA;
   }
   // Every return path after ev_start_ joins the two streams and orders the
   // caller's stream after them, so that work already queued by a call that

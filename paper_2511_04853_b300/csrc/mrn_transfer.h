@@ -54,6 +54,7 @@ class TransferEngine {
  private:
   int init();
   int ensure_staging(uint64_t bytes);
+  int ensure_whole(int h, uint64_t bytes);
   int run_whole(const mrn_view& src, const mrn_view& dst, cudaStream_t user, char* stage,
                 uint64_t stage_bytes);
   int run_chunked(const mrn_view& src, const mrn_view& dst, uint64_t R, uint64_t stride, int n_slots, char* stage);
@@ -73,6 +74,14 @@ class TransferEngine {
   uint64_t pipe_stride_ = 0;
   int pipe_slots_ = 0;
   int next_slot_ = 0;
+  // Calls that stage a whole source (jagged schemas) take two buffers of
+  // their own in turn: a call waits only until the call before last has
+  // finished with its buffer, so its copy overlaps the previous call's
+  // conversion.
+  char* whole_[2] = {};
+  uint64_t whole_bytes_[2] = {};
+  cudaEvent_t ev_whole_free_[2] = {};
+  int next_whole_ = 0;
 };
 
 // Staging slot stride of chunked calls with `chunk_bytes` chunks: the same

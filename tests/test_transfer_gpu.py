@@ -272,3 +272,58 @@ def test_back_to_back_calls_on_different_streams_share_staging_safely():
     assert np.array_equal(host(d1, o_soa.base.size), o_soa.base)
     assert np.array_equal(host(d2, ot_soa.base.size), ot_soa.base)
     assert np.array_equal(host(d3, o_soa.base.size), o_soa.base)
+
+
+def test_pipelined_calls_mixed_schemas_whole_sources_and_write_order():
+    """Host -> device calls on two streams with no synchronisation between
+    them: chunked calls of two schemas with the same chunk size (they share
+    the staging slots, each waiting only for the slots it reuses), three
+    jagged calls in a row (whole-source buffers taken in turn) and, last,
+    an equal-layout copy into a destination an earlier call converted into
+    (destinations are written in call order).  Every result equals the
+    oracle's."""
+    t = torch()
+    streams = [t.cuda.Stream(), t.cuda.Stream()]
+    n_c, n_p = 150000, 90001
+    sc, oc, dc = cells(n_c, seed=21)
+    c_soa = oracle.convert(oc, oracle.pack(oc, dc, "aos"), "soa")
+    h_c = host_side(oracle.pack(oc, dc, "aos").base)
+    c2_soa = oracle.convert(oc, oracle.pack(oc, datagen.workload("cells", n_c, 23), "aos"), "soa")
+    h_c2 = host_side(c2_soa.base)
+    sp, op = mrn.Schema(datagen.POINTS), oracle.Schema(datagen.POINTS)
+    p_aos = oracle.pack(op, datagen.workload("points", n_p, 22), "aos")
+    p_soa = oracle.convert(op, p_aos, "soa")
+    h_p = host_side(p_aos.base)
+    st, ot = mrn.Schema(datagen.TRACKS), oracle.Schema(datagen.TRACKS)
+    tracks = []
+    for k, nt in enumerate((20000, 35001, 12345)):
+        dt = datagen.workload("tracks", nt, 30 + k)
+        a = oracle.pack(ot, dt, "aos")
+        tracks.append((nt, dt["m"], host_side(a.base), host_side(a.pool), oracle.convert(ot, a, "soa")))
+    d_c1, d_c2 = garbage(sc.required_bytes("soa", n_c)), garbage(sc.required_bytes("soa", n_c))
+    d_p1, d_p2 = garbage(sp.required_bytes("soa", n_p)), garbage(sp.required_bytes("soa", n_p))
+    d_t = [garbage(st.required_bytes("soa", nt, m)) for nt, m, _, _, _ in tracks]
+    calls = [
+        (mrn.View(sc, "aos", n_c, base=h_c, mem="pinned"), mrn.View(sc, "soa", n_c, base=d_c1)),
+        (mrn.View(sp, "aos", n_p, base=h_p, mem="pinned"), mrn.View(sp, "soa", n_p, base=d_p1)),
+        (mrn.View(st, "aos", tracks[0][0], base=tracks[0][2], child_pool=tracks[0][3], m=tracks[0][1], mem="pinned"),
+         mrn.View(st, "soa", tracks[0][0], base=d_t[0], m=tracks[0][1])),
+        (mrn.View(sc, "aos", n_c, base=h_c, mem="pinned"), mrn.View(sc, "soa", n_c, base=d_c2)),
+        (mrn.View(st, "aos", tracks[1][0], base=tracks[1][2], child_pool=tracks[1][3], m=tracks[1][1], mem="pinned"),
+         mrn.View(st, "soa", tracks[1][0], base=d_t[1], m=tracks[1][1])),
+        (mrn.View(st, "aos", tracks[2][0], base=tracks[2][2], child_pool=tracks[2][3], m=tracks[2][1], mem="pinned"),
+         mrn.View(st, "soa", tracks[2][0], base=d_t[2], m=tracks[2][1])),
+        (mrn.View(sp, "aos", n_p, base=h_p, mem="pinned"), mrn.View(sp, "soa", n_p, base=d_p2)),
+        (mrn.View(sc, "soa", n_c, base=h_c2, mem="pinned"), mrn.View(sc, "soa", n_c, base=d_c1)),
+    ]
+    t.cuda.synchronize()
+    for i, (src, dst) in enumerate(calls):
+        mrn.transfer_convert(src, dst, chunk_bytes=256 << 10, n_slots=3, stream=streams[i % 2])
+    t.cuda.synchronize()
+    assert mrn.sync() == mrn.OK
+    assert np.array_equal(host(d_c1, c2_soa.base.size), c2_soa.base), "equal-layout copy not last"
+    assert np.array_equal(host(d_c2, c_soa.base.size), c_soa.base)
+    assert np.array_equal(host(d_p1, p_soa.base.size), p_soa.base)
+    assert np.array_equal(host(d_p2, p_soa.base.size), p_soa.base)
+    for k, (nt, m, _, _, want) in enumerate(tracks):
+        assert np.array_equal(host(d_t[k], want.base.size), want.base), "tracks call %d" % k
