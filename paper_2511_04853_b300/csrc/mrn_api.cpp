@@ -635,8 +635,19 @@ int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
         char* scratch = nullptr;
         const uint64_t beg_at = align_up(4 * n, 256);
         if (scratch_alloc(reinterpret_cast<void**>(&scratch), beg_at + 8 * n, st) != MRN_OK) return MRN_ENOMEM;
+        // The parents (a small conversion) go first, on a side stream, and
+        // the children's conversion right after on the caller's: its CTAs
+        // take the SMs as the parents' finish, so the two launches overlap
+        // instead of draining one before the other fills.
+        cudaStream_t side = side_stream();
+        cudaEvent_t fork = nullptr, join = nullptr;
+        const bool par = side && cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
+                         cudaEventCreateWithFlags(&join, cudaEventDisableTiming) == cudaSuccess &&
+                         cudaEventRecord(fork, st) == cudaSuccess && cudaStreamWaitEvent(side, fork, 0) == cudaSuccess;
+        if (!par) cudaGetLastError();
+        cudaStream_t ps_stream = par ? side : st;
         rc = launch_len_begin(jp.offsets, jp.off_size, n, reinterpret_cast<unsigned int*>(scratch),
-                              reinterpret_cast<unsigned long long*>(scratch + beg_at), stream);
+                              reinterpret_cast<unsigned long long*>(scratch + beg_at), ps_stream);
         std::vector<void*> cols(fp->src.size());
         for (size_t k = 0; k < cols.size(); ++k)
           cols[k] = fp->src[k] >= 0 ? jp.parent.src.col[fp->src[k]] : fp->src[k] == -1 ? scratch : scratch + beg_at;
@@ -647,8 +658,13 @@ int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
         ps.child_columns = nullptr;
         ps.n_children = pd.n_children = ps.n_grandchildren = pd.n_grandchildren = 0;
         pd.child_pool = pd.grandchild_pool = nullptr;
-        if (!rc) rc = mrn_convert(&ps, &pd, stream);
+        if (!rc) rc = mrn_convert(&ps, &pd, ps_stream);
         if (!rc) rc = launch_convert(kids, stream, nullptr);
+        if (par && (cudaEventRecord(join, side) != cudaSuccess || cudaStreamWaitEvent(st, join, 0) != cudaSuccess) &&
+            !rc)
+          rc = MRN_ECUDA;
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
         scratch_free(scratch, st);
         if (rc) return rc;
         return zero_dst_gaps(*dst, stream);
