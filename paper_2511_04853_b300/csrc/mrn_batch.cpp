@@ -470,29 +470,35 @@ int mrn_batch_launch_timed(mrn_batch* b, void* stream, void* ev_begin, void* ev_
   cudaEvent_t ev[3] = {static_cast<cudaEvent_t>(ev_begin), static_cast<cudaEvent_t>(ev_mid),
                        static_cast<cudaEvent_t>(ev_end)};
   if (!b->use_graph) return enqueue(b, s, ev, cudaEventRecordDefault);
-  if (!b->texec) {
-    for (cudaEvent_t& e : b->tev)
-      if (!e && cudaEventCreate(&e) != cudaSuccess) {
-        cudaGetLastError();
-        return MRN_ECUDA;
-      }
-    const int rc = capture_into(b, true, &b->tgraph, &b->texec);
-    if (rc) {
-      b->drop_timed();
-      return rc;
-    }
-  }
   // The nodes still name the previous call's events, which the caller may
   // have destroyed since; a new event can then have the address of one
   // that another node names, and two record nodes may not share an event.
-  // So every node goes back to the batch's own placeholder first.
-  for (int pass = 0; pass < 2; ++pass)
-    for (int i = 0; i < 3; ++i)
-      if (cudaGraphExecEventRecordNodeSetEvent(b->texec, b->tnode[i], pass ? ev[i] : b->tev[i]) != cudaSuccess) {
-        cudaGetLastError();
-        return MRN_ECUDA;
+  // So every node goes back to the batch's own placeholder first.  Should
+  // the driver refuse an update all the same (seen once in a long test
+  // run, not reproduced), the timed graph is captured afresh and the
+  // update tried once more.
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if (!b->texec) {
+      for (cudaEvent_t& e : b->tev)
+        if (!e && cudaEventCreate(&e) != cudaSuccess) {
+          cudaGetLastError();
+          return MRN_ECUDA;
+        }
+      const int rc = capture_into(b, true, &b->tgraph, &b->texec);
+      if (rc) {
+        b->drop_timed();
+        return rc;
       }
-  return cudaGraphLaunch(b->texec, s) == cudaSuccess ? MRN_OK : MRN_ECUDA;
+    }
+    bool ok = true;
+    for (int pass = 0; pass < 2 && ok; ++pass)
+      for (int i = 0; i < 3 && ok; ++i)
+        ok = cudaGraphExecEventRecordNodeSetEvent(b->texec, b->tnode[i], pass ? ev[i] : b->tev[i]) == cudaSuccess;
+    if (ok) return cudaGraphLaunch(b->texec, s) == cudaSuccess ? MRN_OK : MRN_ECUDA;
+    cudaGetLastError();
+    b->drop_timed();
+  }
+  return MRN_ECUDA;
 }
 
 int mrn_batch_launch_per_job(mrn_batch* b, void* stream) {

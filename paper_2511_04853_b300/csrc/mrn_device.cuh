@@ -623,10 +623,10 @@ __device__ __forceinline__ void tile_wide(uint32_t desc, uint32_t c0, uint32_t c
 // own, so no element access branches on its size.  With Wide, the last
 // h.nwide descriptors are fields of an AoS destination stored wider than
 // they are, over the padding after them; such records are not zeroed first.
-// An AoS <-> SoA tile whose AoS record is W (2 or 4) 4-byte words, the
-// columns in order (h.packed): the record moves as one 8- or 16-byte vector
-// on the AoS side, and word k to or from its SoA column.  Narrow records
-// are bound by the per-column work of the general body.
+// An AoS <-> SoA tile whose AoS record is W (1, 2 or 4) 4-byte words, the
+// columns in order (h.packed): the record moves as one 4-, 8- or 16-byte
+// vector on the AoS side, and word k to or from its SoA column.  Narrow
+// records are bound by the per-column work of the general body.
 template <int W>
 __device__ __forceinline__ void tile_convert_packed(const TileHdr& h, uint32_t desc, uint32_t st, uint32_t dt,
                                                     uint32_t r0, bool two) {
@@ -641,7 +641,9 @@ __device__ __forceinline__ void tile_convert_packed(const TileHdr& h, uint32_t d
   for (int q = 0; q < 2; ++q) {
     if (q == 1 && !two) break;
     const uint32_t r = r0 + 256 * q;
-    if (a2s) {
+    if constexpr (W == 1) {  // one 4-byte column: the tile is copied word by word
+      sts32(dt + (a2s ? off[0] : 0u) + r * 4, lds32(st + (a2s ? 0u : off[0]) + r * 4));
+    } else if (a2s) {
       if constexpr (W == 2) {
         const uint2 v = lds64(st + r * 8);
         sts32(dt + off[0] + r * 4, v.x);
@@ -667,8 +669,11 @@ __device__ __forceinline__ void tile_convert_packed(const TileHdr& h, uint32_t d
 template <bool Wide>
 __device__ __forceinline__ void tile_convert(const TileHdr& h, uint32_t desc, uint32_t st, uint32_t dt,
                                              uint32_t r0, bool two) {
-  if (h.packed == 2) return tile_convert_packed<2>(h, desc, st, dt, r0, two);
-  if (h.packed == 4) return tile_convert_packed<4>(h, desc, st, dt, r0, two);
+  if (h.packed) {
+    if (h.packed == 4) return tile_convert_packed<4>(h, desc, st, dt, r0, two);
+    if (h.packed == 2) return tile_convert_packed<2>(h, desc, st, dt, r0, two);
+    return tile_convert_packed<1>(h, desc, st, dt, r0, two);
+  }
   const uint32_t r1 = two ? r0 + 256 : r0;
   uint32_t sb0, si0, db0, di0, sb1, si1, db1, di1;
   tile_row(h.sblock, h.sshift, h.sbb, st, r0, &sb0, &si0);

@@ -91,7 +91,7 @@ __host__ __device__ __forceinline__ TileHdr tile_hdr(const ConvPlan& p, bool wid
   h.packed = 0;
   const uint32_t n4 = (p.tg.nsize >> 8) & 0xff;
   if (((p.src.kind == K_AOS && p.dst.kind == K_SOA) || (p.src.kind == K_SOA && p.dst.kind == K_AOS)) &&
-      p.tg.nsize == (n4 << 8) && (n4 == 2 || n4 == 4) && p.ncols == n4 && p.stride == 4 * n4) {
+      p.tg.nsize == (n4 << 8) && (n4 == 1 || n4 == 2 || n4 == 4) && p.ncols == n4 && p.stride == 4 * n4) {
     bool in_order = true;
     for (uint32_t k = 0; k < n4; ++k) in_order = in_order && (p.tg.col[p.tg.order[k]] & 0xffffffu) == 4 * k;
     if (in_order) h.packed = n4;
@@ -939,6 +939,110 @@ __device__ __forceinline__ void jag_scan_chunk(const JagPlan& jp, uint64_t c, un
     atomicExch(jp.noncanon, 1u);
     if (jp.any_noncanon) atomicExch(jp.any_noncanon, 1u);
   }
+}
+
+// Chunk c of a column scan (ColScan): the same sums, pool check and
+// look-back as jag_scan_chunk, the lengths and begins read from their
+// columns; once the chunk's base is known each warp reads its lengths again
+// (now from L2) and writes its parents' offsets itself.
+__device__ __forceinline__ void col_scan_chunk(const ColScan& cs, uint64_t c, ScanShared& sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t n = cs.n, pool_n = cs.pool_n;
+  const uint64_t g0 = c * kScanGroups + (uint64_t)warp * kScanWarpGroups;
+  unsigned long long gsum = 0, gd = 0;
+  bool guni = true;
+  constexpr int U = 4;
+#pragma unroll 1
+  for (uint32_t i0 = 0; i0 < kScanWarpGroups; i0 += U) {
+    uint32_t len[U];
+    uint64_t beg[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t r = (g0 + i0 + u) * 32 + lane;
+      len[u] = r < n ? __ldg(cs.len + r) : 0u;
+      beg[u] = r < n ? __ldg(cs.beg + r) : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t r = (g0 + i0 + u) * 32 + lane;
+      const bool bad = r < n && (beg[u] > pool_n || (uint64_t)len[u] > pool_n - beg[u]);
+      if (bad) flag_error(MRN_EINVAL);
+      unsigned long long excl, tot;
+      if (__any_sync(0xffffffffu, len[u] >= (1u << 26))) {
+        const unsigned long long x = warp_incl_scan_u64(len[u], lane);
+        excl = x - len[u];
+        tot = __shfl_sync(0xffffffffu, x, 31);
+      } else {
+        uint32_t x = len[u];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        excl = x - len[u];
+        tot = __reduce_add_sync(0xffffffffu, len[u]);
+      }
+      const unsigned long long d = beg[u] - excl;
+      const unsigned int has = __ballot_sync(0xffffffffu, len[u] > 0);
+      const unsigned long long d0 = __shfl_sync(0xffffffffu, d, has ? __ffs(has) - 1 : 0);
+      const bool uni = __all_sync(0xffffffffu, !bad && (len[u] == 0 || d == d0));
+      if ((uint32_t)lane == i0 + u) {
+        gsum = tot;
+        gd = d0;
+        guni = uni;
+      }
+    }
+  }
+  const unsigned long long x = warp_incl_scan_u64(gsum, lane);
+  if (lane == 31) sh.wsum[warp] = x;
+  __syncthreads();
+  unsigned long long agg = 0, wbase = 0;
+#pragma unroll
+  for (int w = 0; w < (int)(kScanThreads / 32); ++w) {
+    const unsigned long long v = sh.wsum[w];
+    if (w < warp) wbase += v;
+    agg += v;
+  }
+  const bool publish = (long long)c != cs.skip_publish_tile;
+  if (tid == 0 && publish) st_release_u64(&cs.state[c], (c == 0 ? MRN_TS_PREFIX : MRN_TS_AGG) | (agg & MRN_TS_VALUE));
+  if (warp == 0) {
+    unsigned long long prefix = 0;
+    if (c > 0) {
+      prefix = jagged_lookback(cs.timeout_ns, c, cs.state, lane);
+      if (publish && lane == 0) st_release_u64(&cs.state[c], MRN_TS_PREFIX | ((prefix + agg) & MRN_TS_VALUE));
+    }
+    if (lane == 0) sh.base = prefix;
+  }
+  __syncthreads();
+  const uint64_t g = g0 + lane;
+  const bool have = g * 32 < n;
+  const unsigned long long gb = sh.base + wbase + (x - gsum);  // lane i: group g0 + i's base
+  bool bad = have && (!guni || (gsum > 0 && gd != gb));
+  if (have && (n - 1) / 32 == g) {
+    const unsigned long long total = gb + gsum;
+    write_offset(cs.offsets, cs.off_size, n, total);
+    if (cs.off_size == 4 && total > 0xffffffffull) flag_error(MRN_EOVERFLOW);
+    if (total != pool_n) bad = true;
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(cs.noncanon, 1u);
+  // the offsets, group by group
+#pragma unroll 1
+  for (uint32_t i = 0; i < kScanWarpGroups; ++i) {
+    const uint64_t r = (g0 + i) * 32 + lane;
+    if ((g0 + i) * 32 >= n) break;
+    const uint32_t len = r < n ? __ldg(cs.len + r) : 0u;
+    const unsigned long long xi = warp_incl_scan_u64(len, lane);
+    const unsigned long long base = __shfl_sync(0xffffffffu, gb, (int)i);
+    if (r < n) write_offset(cs.offsets, cs.off_size, r, base + xi - len);
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads, 6) k_col_scan(const __grid_constant__ ColScan cs) {
+  __shared__ ScanShared sh;
+  __shared__ unsigned int s_chunk;
+  if (threadIdx.x == 0) s_chunk = atomicAdd(cs.counter, 1u);
+  __syncthreads();
+  col_scan_chunk(cs, s_chunk, sh);
 }
 
 // The split scan of one conversion: chunks handed out in increasing order,
@@ -2029,6 +2133,25 @@ int launch_jagged_a2s_split(JagPlan& jp, const ConvPlan& pool, void* scratch, vo
   const uint64_t grid = std::min<uint64_t>(jp.ntiles, (uint64_t)device_sm_count() * (uint64_t)per_sm);
   k_jagged_a2s_rest<<<(unsigned)grid, MRN_JAG_THREADS, 0, s>>>(jp);
   return cuda_status(cudaGetLastError());
+}
+
+int launch_col_scan(ColScan& cs, void* scratch, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cs.n == 0) return MRN_EINVAL;
+  const uint64_t nchunks = (cs.n + MRN_SCAN_CHUNK - 1) / MRN_SCAN_CHUNK;
+  if (nchunks > 0x7fffffffull) return MRN_EUNSUPPORTED;
+  char* sc = static_cast<char*>(scratch);
+  cs.counter = reinterpret_cast<unsigned int*>(sc);
+  cs.noncanon = reinterpret_cast<unsigned int*>(sc + 128);
+  cs.state = reinterpret_cast<unsigned long long*>(sc + 256);
+  cudaError_t e = cudaMemsetAsync(sc, 0, col_scan_scratch_bytes(cs.n), s);
+  if (e != cudaSuccess) return cuda_status(e);
+  k_col_scan<<<(unsigned)nchunks, kScanThreads, 0, s>>>(cs);
+  return cuda_status(cudaGetLastError());
+}
+
+uint64_t col_scan_scratch_bytes(uint64_t n) {
+  return 256 + (n + MRN_SCAN_CHUNK - 1) / MRN_SCAN_CHUNK * sizeof(unsigned long long);
 }
 
 int launch_jagged_s2a(const JagPlan& jp, void* stream) {

@@ -72,7 +72,7 @@ struct TileHdr {
   uint32_t ncols, stride, vec, pad, T, nsize;
   uint32_t sblock, sshift, sbb;  // source row geometry
   uint32_t dblock, dshift, dbb;  // destination row geometry
-  // 2 or 4: an AoS <-> SoA pair of that many 4-byte columns, the AoS
+  // 1, 2 or 4: an AoS <-> SoA pair of that many 4-byte columns, the AoS
   // record being exactly those words in column order (records move as one
   // vector); 0 otherwise
   uint32_t packed;
@@ -155,6 +155,25 @@ struct JagPlan {
   uint64_t chunk_begin;             // batches: the job's first chunk in the scan's numbering
   uint64_t nchunks;
 };
+// The scan of a jagged level whose lengths and begins are two columns (the
+// child level of a nested member, its descriptors gathered by level 0):
+// writes the level's offsets (n + 1, starting at 0) and clears nothing but
+// sets *noncanon unless the grandchild pool is canonical for them.
+struct ColScan {
+  const unsigned int* len;        // n lengths
+  const unsigned long long* beg;  // n begins into the pool
+  uint64_t n;
+  uint64_t pool_n;                // records in the pool
+  char* offsets;
+  uint32_t off_size;              // 4 or 8
+  uint32_t reserved;
+  unsigned long long* state;      // one look-back word per chunk of MRN_SCAN_CHUNK
+  unsigned int* counter;          // dynamic chunk id
+  unsigned int* noncanon;
+  unsigned long long timeout_ns;
+  long long skip_publish_tile;
+};
+
 #define JAG_FUSED 0u
 #define JAG_SPLIT 1u
 #define JAG_CHILDREN 2u
