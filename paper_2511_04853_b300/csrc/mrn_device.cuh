@@ -666,12 +666,36 @@ __device__ __forceinline__ void tile_convert_packed(const TileHdr& h, uint32_t d
   }
 }
 
+// An AoS <-> SoA tile whose AoS record is two 2-byte columns in order
+// (h.packed == kPacked2x16): one 4-byte word per record on the AoS side,
+// its halves to or from the two columns.
+constexpr uint32_t kPacked2x16 = 0x102u;
+__device__ __forceinline__ void tile_convert_2x16(const TileHdr& h, uint32_t desc, uint32_t st, uint32_t dt,
+                                                  uint32_t r0, bool two) {
+  const bool a2s = h.sshift == 0;
+  const uint4 d0 = lds128(desc), d1 = lds128(desc + 16);
+  const uint32_t o0 = a2s ? d0.z : d0.y, o1 = a2s ? d1.z : d1.y;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    if (q == 1 && !two) break;
+    const uint32_t r = r0 + 256 * q;
+    if (a2s) {
+      const uint32_t v = lds32(st + r * 4);
+      sts16(dt + o0 + r * 2, v & 0xffffu);
+      sts16(dt + o1 + r * 2, v >> 16);
+    } else {
+      sts32(dt + r * 4, lds16(st + o0 + r * 2) | (lds16(st + o1 + r * 2) << 16));
+    }
+  }
+}
+
 template <bool Wide>
 __device__ __forceinline__ void tile_convert(const TileHdr& h, uint32_t desc, uint32_t st, uint32_t dt,
                                              uint32_t r0, bool two) {
   if (h.packed) {
     if (h.packed == 4) return tile_convert_packed<4>(h, desc, st, dt, r0, two);
     if (h.packed == 2) return tile_convert_packed<2>(h, desc, st, dt, r0, two);
+    if (h.packed == kPacked2x16) return tile_convert_2x16(h, desc, st, dt, r0, two);
     return tile_convert_packed<1>(h, desc, st, dt, r0, two);
   }
   const uint32_t r1 = two ? r0 + 256 : r0;

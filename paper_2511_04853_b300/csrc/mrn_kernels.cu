@@ -63,6 +63,16 @@ __device__ __forceinline__ void tma_transform(const TileHdr& h, uint32_t desc, c
                                               int lane, int warp) {
   const uint32_t s = smem_u32(st), d = smem_u32(dt);
   const TileHdr hh = h;
+  if (hh.packed == 1) {
+    // one 4-byte column: both tiles hold the same words (R, a multiple of
+    // 32, records), copied 16 bytes per thread and step
+    const uint4 dd = lds128(desc);
+    const uint32_t so = hh.sshift == 0 ? 0u : dd.y, dof = hh.sshift == 0 ? dd.z : 0u;
+    if (((so | dof) & 15u) == 0) {
+      for (uint32_t i = (uint32_t)warp * 32 + lane; i < R / 4; i += 8 * 32) sts128(d + dof + 16 * i, lds128(s + so + 16 * i));
+      return;
+    }
+  }
   for (uint32_t g = (uint32_t)warp * 32; g < R; g += 2 * 8 * 32)
     tile_convert<Wide>(hh, desc, s, d, g + lane, g + 8 * 32 < R);
 }
@@ -96,6 +106,11 @@ __host__ __device__ __forceinline__ TileHdr tile_hdr(const ConvPlan& p, bool wid
     for (uint32_t k = 0; k < n4; ++k) in_order = in_order && (p.tg.col[p.tg.order[k]] & 0xffffffu) == 4 * k;
     if (in_order) h.packed = n4;
   }
+  // a 4-byte record of two 2-byte columns, in order
+  if (((p.src.kind == K_AOS && p.dst.kind == K_SOA) || (p.src.kind == K_SOA && p.dst.kind == K_AOS)) &&
+      p.tg.nsize == (2u << 16) && p.ncols == 2 && p.stride == 4 && (p.tg.col[p.tg.order[0]] & 0xffffffu) == 0 &&
+      (p.tg.col[p.tg.order[1]] & 0xffffffu) == 2)
+    h.packed = kPacked2x16;
   tile_side_geometry(p.src.kind, p.src.block, p.src.block_shift, p.src.block_bytes, p.stride, &h.sblock, &h.sshift,
                      &h.sbb);
   tile_side_geometry(p.dst.kind, p.dst.block, p.dst.block_shift, p.dst.block_bytes, p.stride, &h.dblock, &h.dshift,
@@ -943,14 +958,21 @@ __device__ __forceinline__ void jag_scan_chunk(const JagPlan& jp, uint64_t c, un
 
 // Chunk c of a column scan (ColScan): the same sums, pool check and
 // look-back as jag_scan_chunk, the lengths and begins read from their
-// columns; once the chunk's base is known each warp reads its lengths again
-// (now from L2) and writes its parents' offsets itself.
-__device__ __forceinline__ void col_scan_chunk(const ColScan& cs, uint64_t c, ScanShared& sh) {
+// columns.  Each parent's offset inside its group is kept in shared memory
+// (`ex`: [warp][group][lane]), so that once the chunk's base is known each
+// warp writes its parents' offsets without a second scan; a group whose
+// lengths could carry past 32 bits is scanned again from its lengths.
+struct ColScanShared {
+  uint32_t ex[kScanThreads / 32][kScanWarpGroups][32];
+  unsigned long long gb[kScanThreads / 32][32];
+};
+__device__ __forceinline__ void col_scan_chunk(const ColScan& cs, uint64_t c, ScanShared& sh, ColScanShared& cx) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t n = cs.n, pool_n = cs.pool_n;
   const uint64_t g0 = c * kScanGroups + (uint64_t)warp * kScanWarpGroups;
   unsigned long long gsum = 0, gd = 0;
   bool guni = true;
+  uint32_t big = 0;  // groups scanned in 64 bits (bit i: group g0 + i)
   constexpr int U = 4;
 #pragma unroll 1
   for (uint32_t i0 = 0; i0 < kScanWarpGroups; i0 += U) {
@@ -972,6 +994,7 @@ __device__ __forceinline__ void col_scan_chunk(const ColScan& cs, uint64_t c, Sc
         const unsigned long long x = warp_incl_scan_u64(len[u], lane);
         excl = x - len[u];
         tot = __shfl_sync(0xffffffffu, x, 31);
+        big |= 1u << (i0 + u);
       } else {
         uint32_t x = len[u];
 #pragma unroll
@@ -982,6 +1005,7 @@ __device__ __forceinline__ void col_scan_chunk(const ColScan& cs, uint64_t c, Sc
         excl = x - len[u];
         tot = __reduce_add_sync(0xffffffffu, len[u]);
       }
+      cx.ex[warp][i0 + u][lane] = (uint32_t)excl;
       const unsigned long long d = beg[u] - excl;
       const unsigned int has = __ballot_sync(0xffffffffu, len[u] > 0);
       const unsigned long long d0 = __shfl_sync(0xffffffffu, d, has ? __ffs(has) - 1 : 0);
@@ -1025,24 +1049,29 @@ __device__ __forceinline__ void col_scan_chunk(const ColScan& cs, uint64_t c, Sc
     if (total != pool_n) bad = true;
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(cs.noncanon, 1u);
-  // the offsets, group by group
-#pragma unroll 1
+  // the offsets, group by group (the warp's own shared rows: no barrier)
+  cx.gb[warp][lane] = gb;
+  __syncwarp();
+#pragma unroll 4
   for (uint32_t i = 0; i < kScanWarpGroups; ++i) {
     const uint64_t r = (g0 + i) * 32 + lane;
     if ((g0 + i) * 32 >= n) break;
-    const uint32_t len = r < n ? __ldg(cs.len + r) : 0u;
-    const unsigned long long xi = warp_incl_scan_u64(len, lane);
-    const unsigned long long base = __shfl_sync(0xffffffffu, gb, (int)i);
-    if (r < n) write_offset(cs.offsets, cs.off_size, r, base + xi - len);
+    unsigned long long e = cx.ex[warp][i][lane];
+    if ((big >> i) & 1u) {  // 64-bit group: scanned again
+      const uint32_t len = r < n ? __ldg(cs.len + r) : 0u;
+      e = warp_incl_scan_u64(len, lane) - len;
+    }
+    if (r < n) write_offset(cs.offsets, cs.off_size, r, cx.gb[warp][i] + e);
   }
 }
 
 __global__ void __launch_bounds__(kScanThreads, 6) k_col_scan(const __grid_constant__ ColScan cs) {
   __shared__ ScanShared sh;
+  __shared__ ColScanShared cx;
   __shared__ unsigned int s_chunk;
   if (threadIdx.x == 0) s_chunk = atomicAdd(cs.counter, 1u);
   __syncthreads();
-  col_scan_chunk(cs, s_chunk, sh);
+  col_scan_chunk(cs, s_chunk, sh, cx);
 }
 
 // The split scan of one conversion: chunks handed out in increasing order,

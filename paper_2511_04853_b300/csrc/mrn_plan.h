@@ -74,7 +74,8 @@ struct TileHdr {
   uint32_t dblock, dshift, dbb;  // destination row geometry
   // 1, 2 or 4: an AoS <-> SoA pair of that many 4-byte columns, the AoS
   // record being exactly those words in column order (records move as one
-  // vector); 0 otherwise
+  // vector); 0x102: the AoS record is two 2-byte columns in order (one
+  // 4-byte word); 0 otherwise
   uint32_t packed;
   // AoS destination: the last nwide descriptors are fields stored wider
   // than they are, over the padding that follows them (see TileGeom)

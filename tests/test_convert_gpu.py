@@ -24,6 +24,8 @@ TINY = [("a", "u8", 3)]                                 # 3-byte record: byte ac
 WIDE = [("v%d" % i, "f64" if i % 3 == 0 else "u16", 1) for i in range(40)]  # > 64-byte record
 PACK2 = [("index", "u32", 1), ("weight", "f32", 1)]       # records of two 4-byte words
 PACK4 = [("a", "i32", 1), ("v", "f32", 3)]                 # four 4-byte words (an array of 3)
+PACK1 = [("x", "f32", 1)]                                  # one 4-byte word: tiles copied whole
+PACK16 = [("t", "u16", 1), ("adc", "u16", 1)]              # one 4-byte word of two 2-byte columns
 # Padding that no field can be stored wide enough to cover (byte b at 1 is
 # not 2-aligned): AoS destination records keep their zeroing pass.  Points,
 # sensor, nested and odd records instead absorb their padding in widened
@@ -34,7 +36,7 @@ UNCOV = [("a", "u8", 1), ("b", "u8", 1), ("c", "u32", 1)]
 def schemas():
     return {"points": datagen.POINTS, "cells": datagen.CELLS, "sensor": datagen.SENSOR,
             "nested": NESTED, "odd": ODD, "tiny": TINY, "wide": WIDE, "pack2": PACK2, "pack4": PACK4,
-            "uncov": UNCOV}
+            "pack1": PACK1, "pack16": PACK16, "uncov": UNCOV}
 
 
 def data_for(name, n, seed=0, raw=False):
@@ -188,12 +190,14 @@ def test_large_staged_conversions(name, n):
         check_pair(name, n, sk, sb, dk, db, seed=11)
 
 
-@pytest.mark.parametrize("name", ["pack2", "pack4"])
-@pytest.mark.parametrize("n", [31, 32, 1000, 1536 * 3 + 64, 100003, 9_000_001])
+@pytest.mark.parametrize("name", ["pack1", "pack16", "pack2", "pack4"])
+@pytest.mark.parametrize("n", [31, 32, 1000, 1536 * 3 + 64, 3072 * 2 + 96, 100003, 9_000_001])
 def test_packed_records_aos_soa(name, n):
-    """Records that are exactly two or four 4-byte words, in column order,
-    move between AoS and SoA as one vector per record in the staged
-    transform; full tiles, partial tiles and the large-conversion path."""
+    """Records that are exactly one, two or four 4-byte words, or two
+    2-byte columns, in column order, move between AoS and SoA as one word
+    or vector per record in the staged transform (one 4-byte column: the
+    tile copied whole); full tiles, partial tiles and the large-conversion
+    path."""
     check_pair(name, n, "aos", 0, "soa", 0, seed=3)
     check_pair(name, n, "soa", 0, "aos", 0, seed=4)
     check_pair(name, n, "aos", 0, "aosoa", 32, seed=5)
