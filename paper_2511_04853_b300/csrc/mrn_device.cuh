@@ -689,14 +689,19 @@ __device__ __forceinline__ void tile_convert_2x16(const TileHdr& h, uint32_t des
   }
 }
 
-template <bool Wide>
+template <bool Wide, bool Narrow>
 __device__ __forceinline__ void tile_convert(const TileHdr& h, uint32_t desc, uint32_t st, uint32_t dt,
                                              uint32_t r0, bool two) {
-  if (h.packed) {
-    if (h.packed == 4) return tile_convert_packed<4>(h, desc, st, dt, r0, two);
+  if constexpr (Narrow) {
+    if (h.packed) {
+      if (h.packed == 4) return tile_convert_packed<4>(h, desc, st, dt, r0, two);
+      if (h.packed == 2) return tile_convert_packed<2>(h, desc, st, dt, r0, two);
+      if (h.packed == kPacked2x16) return tile_convert_2x16(h, desc, st, dt, r0, two);
+      return tile_convert_packed<1>(h, desc, st, dt, r0, two);
+    }
+  } else {  // the batch instance: packed records of two or four words only
     if (h.packed == 2) return tile_convert_packed<2>(h, desc, st, dt, r0, two);
-    if (h.packed == kPacked2x16) return tile_convert_2x16(h, desc, st, dt, r0, two);
-    return tile_convert_packed<1>(h, desc, st, dt, r0, two);
+    if (h.packed == 4) return tile_convert_packed<4>(h, desc, st, dt, r0, two);
   }
   const uint32_t r1 = two ? r0 + 256 : r0;
   uint32_t sb0, si0, db0, di0, sb1, si1, db1, di1;

@@ -58,12 +58,16 @@ __global__ void __launch_bounds__(256) k_convert(const __grid_constant__ ConvPla
 // All threads: source tile -> destination tile in shared memory.  Wide:
 // the tables may hold widened fields (k_convert_ws<true, false>, for single
 // conversions that have them; no other instance carries the branch).
-template <bool Wide>
+// Narrow: the instance takes the one-column and two-2-byte-column record
+// paths (single conversions); the persistent batch kernel leaves them out
+// (those records take the general body there) because their branches cost
+// its other jobs about 1%.
+template <bool Wide, bool Narrow>
 __device__ __forceinline__ void tma_transform(const TileHdr& h, uint32_t desc, const char* st, char* dt, uint32_t R,
                                               int lane, int warp) {
   const uint32_t s = smem_u32(st), d = smem_u32(dt);
   const TileHdr hh = h;
-  if (hh.packed == 1) {
+  if (Narrow && hh.packed == 1) {
     // one 4-byte column: both tiles hold the same words (R, a multiple of
     // 32, records), copied 16 bytes per thread and step
     const uint4 dd = lds128(desc);
@@ -74,7 +78,7 @@ __device__ __forceinline__ void tma_transform(const TileHdr& h, uint32_t desc, c
     }
   }
   for (uint32_t g = (uint32_t)warp * 32; g < R; g += 2 * 8 * 32)
-    tile_convert<Wide>(hh, desc, s, d, g + lane, g + 8 * 32 < R);
+    tile_convert<Wide, Narrow>(hh, desc, s, d, g + lane, g + 8 * 32 < R);
 }
 
 // Entry k of the staged-transform descriptor table: the k-th column in
@@ -1730,7 +1734,7 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
         break;
       }
       const StageDesc* sd = m.desc(s);
-      tma_transform<kWide>(sd->h, smem_u32(sd->d), m.src(s), m.dst(d), ts.staged, lane, warp);
+      tma_transform<kWide, kStatic>(sd->h, smem_u32(sd->d), m.src(s), m.dst(d), ts.staged, lane, warp);
       // parents of a split jagged job: the offsets, from the staged lengths
       // (before the source stage is released)
       if (kJag && ts.jag) jag_offsets_staged(jobs[ts.job].jp, ts.local, ts.staged, m.src(s), sd->h, lane, warp);

@@ -368,3 +368,26 @@ def test_timed_launch_with_fresh_events_each_time():
     e.record()
     with pytest.raises(mrn.MrnError):
         b.launch_timed(e, e, t.cuda.Event(enable_timing=True))
+
+
+def test_narrow_records_in_a_batch():
+    """Records of one 4-byte column and of two 2-byte columns, which single
+    conversions move by their own tile paths, take the general staged body in
+    the persistent batch kernel: both directions, tile edges, one launch,
+    each equal to the oracle."""
+    pairs, checks = [], []
+    for desc in ([("x", "f32", 1)], [("t", "u16", 1), ("adc", "u16", 1)]):
+        s, o = mrn.Schema(desc), oracle.Schema(desc)
+        for j, n in enumerate([1, 33, 3072 * 2 + 96, 100003]):
+            d = datagen.random_columns(desc, n, 90 + j)
+            for sk, dk in (("aos", "soa"), ("soa", "aos")):
+                o_src = oracle.pack(o, d, sk)
+                want = oracle.convert(o, o_src, dk).base
+                dst = dev_dest(s, dk, n)
+                pairs.append((mrn.View(s, sk, n, base=dev(o_src.base)), dst))
+                checks.append((dst, want))
+    b = mrn.Batch(pairs, use_graph=True)
+    b.launch()
+    assert mrn.sync() == mrn.OK
+    for k, (dst, want) in enumerate(checks):
+        assert np.array_equal(host(dst.tensors[0], want.size), want), "job %d" % k
