@@ -116,9 +116,9 @@ int mrn_schema_end_group(mrn_schema* s);
  *     single-block SoA for (n_children, n_grandchildren): child columns,
  *     the children's offsets (n_children + 1), the grandchild columns.
  *   Nested members convert between AoS and SoA / AoSoA(B) with
- *   mrn_convert; the AoS -> field-major direction reads the children's
- *   count back to the host between its two levels (it waits for `stream`
- *   once).  Other calls return MRN_EUNSUPPORTED for them.
+ *   mrn_convert, asynchronously like any conversion (too few child or
+ *   grandchild slots record MRN_ESIZE, reported by mrn_sync).  Other calls
+ *   return MRN_EUNSUPPORTED for them.
  * Returns MRN_EINVAL for deeper nesting or two jagged properties;
  * MRN_EUNSUPPORTED for a child with an interleaved array property. */
 int mrn_schema_add_jagged(mrn_schema* s, const char* name, int offset_dtype,

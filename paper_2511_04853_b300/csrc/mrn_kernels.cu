@@ -970,9 +970,10 @@ struct ColScanShared {
   uint32_t ex[kScanThreads / 32][kScanWarpGroups][32];
   unsigned long long gb[kScanThreads / 32][32];
 };
-__device__ __forceinline__ void col_scan_chunk(const ColScan& cs, uint64_t c, ScanShared& sh, ColScanShared& cx) {
+__device__ __forceinline__ void col_scan_chunk(const ColScan& cs, uint64_t n, uint64_t c, ScanShared& sh,
+                                               ColScanShared& cx) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint64_t n = cs.n, pool_n = cs.pool_n;
+  const uint64_t pool_n = cs.pool_n;
   const uint64_t g0 = c * kScanGroups + (uint64_t)warp * kScanWarpGroups;
   unsigned long long gsum = 0, gd = 0;
   bool guni = true;
@@ -1069,13 +1070,58 @@ __device__ __forceinline__ void col_scan_chunk(const ColScan& cs, uint64_t c, Sc
   }
 }
 
+// The grid covers cs.n entries; the count (read from device memory, where
+// the level above wrote it) may be smaller, and the chunks past it return.
 __global__ void __launch_bounds__(kScanThreads, 6) k_col_scan(const __grid_constant__ ColScan cs) {
   __shared__ ScanShared sh;
   __shared__ ColScanShared cx;
   __shared__ unsigned int s_chunk;
   if (threadIdx.x == 0) s_chunk = atomicAdd(cs.counter, 1u);
   __syncthreads();
-  col_scan_chunk(cs, s_chunk, sh, cx);
+  const uint64_t c = s_chunk;
+  const uint64_t n = cs.count ? min((uint64_t)ld_acquire_u64(cs.count), cs.n) : cs.n;
+  if (n == 0) {  // no entries: the single offset, and a pool with records is not theirs
+    if (c == 0 && threadIdx.x == 0) {
+      write_offset(cs.offsets, cs.off_size, 0, 0);
+      if (cs.pool_n != 0) atomicExch(cs.noncanon, 1u);
+    }
+    return;
+  }
+  if (c * MRN_SCAN_CHUNK >= n) return;
+  col_scan_chunk(cs, n, c, sh, cx);
+}
+
+// The gathering form of a column-scanned level, for a pool that is not
+// canonical (or whose conversion cannot be staged: `force`): every entry's
+// children are copied one by one from the pool (`P`: the pool's records ->
+// the level's columns) to the rows its offset gives.  Returns at once for
+// a canonical pool.  Entries whose children lie outside the pool were
+// recorded by the scan and are passed over; rows at or past `capacity`
+// record MRN_ESIZE.
+__global__ void __launch_bounds__(256) k_col_gather(const __grid_constant__ ColScan cs,
+                                                    const __grid_constant__ ConvPlan P, unsigned long long capacity,
+                                                    unsigned int force) {
+  if (!force && ld_relaxed_u32(cs.noncanon) == 0) return;
+  const uint64_t n = cs.count ? min((uint64_t)ld_acquire_u64(cs.count), cs.n) : cs.n;
+  for (uint64_t h = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; h < n; h += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t len = __ldg(cs.len + h);
+    const uint64_t beg = __ldg(cs.beg + h);
+    if (beg > cs.pool_n || (uint64_t)len > cs.pool_n - beg) continue;
+    const uint64_t row0 = read_offset(cs.offsets, cs.off_size, h);
+    for (uint32_t k = 0; k < len; ++k) {
+      const uint64_t row = row0 + k;
+      if (row >= capacity) {
+        flag_error(MRN_ESIZE);
+        break;
+      }
+      const char* rec = P.src.base + (beg + k) * P.stride;
+      for (uint32_t c = 0; c < P.naos; ++c) {
+        const ColPlan cp = P.aos_cols[c];
+        if (cp.fm < 0) continue;
+        st_elem(P.dst.col[cp.fm] + row * cp.size, cp.size, ld_elem(rec + cp.aos_off, cp.size));
+      }
+    }
+  }
 }
 
 // The split scan of one conversion: chunks handed out in increasing order,
@@ -2170,8 +2216,7 @@ int launch_jagged_a2s_split(JagPlan& jp, const ConvPlan& pool, void* scratch, vo
 
 int launch_col_scan(ColScan& cs, void* scratch, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cs.n == 0) return MRN_EINVAL;
-  const uint64_t nchunks = (cs.n + MRN_SCAN_CHUNK - 1) / MRN_SCAN_CHUNK;
+  const uint64_t nchunks = std::max<uint64_t>(1, (cs.n + MRN_SCAN_CHUNK - 1) / MRN_SCAN_CHUNK);
   if (nchunks > 0x7fffffffull) return MRN_EUNSUPPORTED;
   char* sc = static_cast<char*>(scratch);
   cs.counter = reinterpret_cast<unsigned int*>(sc);
@@ -2184,7 +2229,14 @@ int launch_col_scan(ColScan& cs, void* scratch, void* stream) {
 }
 
 uint64_t col_scan_scratch_bytes(uint64_t n) {
-  return 256 + (n + MRN_SCAN_CHUNK - 1) / MRN_SCAN_CHUNK * sizeof(unsigned long long);
+  return 256 + std::max<uint64_t>(1, (n + MRN_SCAN_CHUNK - 1) / MRN_SCAN_CHUNK) * sizeof(unsigned long long);
+}
+
+int launch_col_gather(const ColScan& cs, const ConvPlan& P, uint64_t capacity, bool force, void* stream) {
+  const unsigned grid = (unsigned)std::max<uint64_t>(
+      1, std::min<uint64_t>((cs.n + 255) / 256, (uint64_t)device_sm_count() * 8));
+  k_col_gather<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(cs, P, capacity, force ? 1u : 0u);
+  return cuda_status(cudaGetLastError());
 }
 
 int launch_jagged_s2a(const JagPlan& jp, void* stream) {

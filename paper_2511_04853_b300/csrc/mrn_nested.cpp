@@ -10,10 +10,10 @@
 //     from their offsets;
 //   AoS -> field-major: the parents' tile scan gathers each child's data
 //     columns into the child level and its {length, begin} into two scratch
-//     columns; the children's count is read back; the descriptors are packed
-//     into 16-byte records {u32 length, u64 begin}, which an ordinary jagged
-//     AoS -> SoA conversion of a descriptor-only schema turns into the
-//     children's offsets and the gathered grandchild columns.
+//     columns; a scan of those columns writes the children's offsets and
+//     checks the grandchild pool, which is then converted as one staged
+//     conversion when canonical and gathered child by child otherwise, all
+//     on the device (the children's count never returns to the host).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -101,12 +101,10 @@ int convert_nested(const mrn_view& src, const mrn_view& dst, void* stream) {
   const uint64_t len_at = lb_bytes, beg_at = align_up(len_at + 4 * mcap, 256),
                  tot_at = align_up(beg_at + 8 * mcap, 256);
   char* scratch = nullptr;
-  char* recs = nullptr;  // the packed descriptors (the gathering form of level 1 only)
   char* cscratch = nullptr;
   if (scratch_alloc(reinterpret_cast<void**>(&scratch), tot_at + 256, st) != MRN_OK) return MRN_ENOMEM;
   auto done = [&](int r) {
     scratch_free(cscratch, st);
-    scratch_free(recs, st);
     scratch_free(scratch, st);
     return r;
   };
@@ -124,79 +122,47 @@ int convert_nested(const mrn_view& src, const mrn_view& dst, void* stream) {
   jp.total_out = d_total;
   if (cudaMemsetAsync(d_total, 0, sizeof(unsigned long long), st) != cudaSuccess) return done(MRN_ECUDA);
   if ((rc = launch_jagged_a2s(jp, scratch, stream))) return done(rc);
-  unsigned long long m1 = 0;
-  if (cudaMemcpyAsync(&m1, d_total, sizeof(m1), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return done(MRN_ECUDA);
-  if (m1 > mcap) return done(MRN_ESIZE);  // recorded by the kernel as well
 
-  // The descriptors as 16-byte records {u32 length, u64 begin}.
-  OwnedSchema plain, desc;
-  if (mrn_schema_create(&plain.s) || mrn_schema_add_field(plain.s, "length", MRN_U32, 1) ||
-      mrn_schema_add_field(plain.s, "begin", MRN_U64, 1) || mrn_schema_finalize(plain.s) ||
-      mrn_schema_create(&desc.s) ||
+  // Level 1, without a return to the host: the children's count M stays in
+  // device memory (a count above the capacity is recorded by level 0 as
+  // MRN_ESIZE, and level 1 then covers the capacity).  A scan of the two
+  // gathered columns writes the children's offsets and checks the
+  // grandchild pool; a canonical pool (the grandchildren exactly its
+  // records, in child order) is one staged conversion of the grandchild
+  // schema, and otherwise a gathering pass copies each child's
+  // grandchildren to its rows (both decide on the device).
+  OwnedSchema desc;
+  if (mrn_schema_create(&desc.s) ||
       mrn_schema_add_jagged(desc.s, "v", ch->off_size == 4 ? MRN_U32 : MRN_U64, ch->child.get()) ||
       mrn_schema_finalize(desc.s))
     return done(MRN_ENOMEM);
-  if (plain.s->stride != 16 || desc.s->stride != 16 || desc.s->len_off != 0 || desc.s->begin_off != 8)
-    return done(MRN_EINVAL);
-
-  // Level 1: the children's offsets and the grandchild columns.
-  mrn_view ds = device_view(desc.s, MRN_AOS, src.device, m1, src.n_grandchildren);
+  mrn_view ds = device_view(desc.s, MRN_AOS, src.device, mcap, src.n_grandchildren);
+  ds.base = scratch + len_at;  // not read: the plans need a non-null base
   ds.child_pool = src.grandchild_pool;
-  mrn_view dd = device_view(desc.s, MRN_SOA, dst.device, m1, dst.n_grandchildren);
+  mrn_view dd = device_view(desc.s, MRN_SOA, dst.device, mcap, dst.n_grandchildren);
   dd.base = off1;
   dd.offsets = off1;
   dd.child_columns = gcols.data();
-  // First without packing the descriptors: a scan of the two columns writes
-  // the children's offsets and checks the grandchild pool, and a canonical
-  // pool (the grandchildren exactly its records, in child order) is one
-  // staged conversion of the grandchild schema.  The pool's check is read
-  // back; a pool that is not canonical (or that cannot be converted that
-  // way) takes the gathering form below, which writes the offsets again.
-  bool level1 = false;
-  if (m1 > 0 && src.n_grandchildren > 0 && src.n_grandchildren <= dst.n_grandchildren) {
-    JagPlan jp1;
-    ds.base = scratch + len_at;  // not read: the plan only needs a non-null base
-    ConvPlan pool;
-    if (build_jagged_plan(ds, dd, &jp1) == MRN_OK && jagged_pool_plan(desc.s, jp1, &pool) == MRN_OK &&
-        pool.tg.tma) {
-      if (scratch_alloc(reinterpret_cast<void**>(&cscratch), col_scan_scratch_bytes(m1), st) != MRN_OK)
-        return done(MRN_ENOMEM);
-      ColScan cs;
-      std::memset(&cs, 0, sizeof(cs));
-      cs.len = reinterpret_cast<const unsigned int*>(scratch + len_at);
-      cs.beg = reinterpret_cast<const unsigned long long*>(scratch + beg_at);
-      cs.n = m1;
-      cs.pool_n = src.n_grandchildren;
-      cs.offsets = off1;
-      cs.off_size = ch->off_size;
-      cs.timeout_ns = jp1.timeout_ns;
-      cs.skip_publish_tile = jp1.skip_publish_tile;
-      if ((rc = launch_col_scan(cs, cscratch, stream))) return done(rc);
-      if ((rc = launch_convert(pool, stream, nullptr, cs.noncanon))) return done(rc);
-      unsigned int nc = 1;
-      if (cudaMemcpyAsync(&nc, cs.noncanon, sizeof(nc), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-          cudaStreamSynchronize(st) != cudaSuccess)
-        return done(MRN_ECUDA);
-      level1 = nc == 0;
-    }
-  }
-  if (!level1) {
-    // The descriptors as 16-byte records {u32 length, u64 begin}, then an
-    // ordinary jagged AoS -> SoA conversion of the descriptor-only schema.
-    if (scratch_alloc(reinterpret_cast<void**>(&recs), 16 * std::max<uint64_t>(1, m1) + 256, st) != MRN_OK)
-      return done(MRN_ENOMEM);
-    void* pcols[2] = {scratch + len_at, scratch + beg_at};
-    mrn_view ps = device_view(plain.s, MRN_SOA, dst.device, m1, 0);
-    ps.base = scratch + len_at;
-    ps.columns = pcols;
-    mrn_view pd = device_view(plain.s, MRN_AOS, dst.device, m1, 0);
-    pd.base = recs;
-    if (m1 && (rc = mrn_convert(&ps, &pd, stream))) return done(rc);
-    ds.base = recs;
-    if ((rc = mrn_convert(&ds, &dd, stream))) return done(rc);
-  }
+  JagPlan jp1;
+  ConvPlan pool;
+  if ((rc = build_jagged_plan(ds, dd, &jp1)) || (rc = jagged_pool_plan(desc.s, jp1, &pool))) return done(rc);
+  const bool staged_pool = pool.tg.tma && src.n_grandchildren <= dst.n_grandchildren;
+  if (scratch_alloc(reinterpret_cast<void**>(&cscratch), col_scan_scratch_bytes(mcap), st) != MRN_OK)
+    return done(MRN_ENOMEM);
+  ColScan cs;
+  std::memset(&cs, 0, sizeof(cs));
+  cs.len = reinterpret_cast<const unsigned int*>(scratch + len_at);
+  cs.beg = reinterpret_cast<const unsigned long long*>(scratch + beg_at);
+  cs.n = mcap;
+  cs.count = d_total;
+  cs.pool_n = src.n_grandchildren;
+  cs.offsets = off1;
+  cs.off_size = ch->off_size;
+  cs.timeout_ns = jp1.timeout_ns;
+  cs.skip_publish_tile = jp1.skip_publish_tile;
+  if ((rc = launch_col_scan(cs, cscratch, stream))) return done(rc);
+  if (staged_pool && (rc = launch_convert(pool, stream, nullptr, cs.noncanon))) return done(rc);
+  if ((rc = launch_col_gather(cs, jp1.child, dst.n_grandchildren, !staged_pool, stream))) return done(rc);
   if ((rc = zero_dst_gaps(dst, stream))) return done(rc);
   return done(MRN_OK);
 }

@@ -158,12 +158,13 @@ struct JagPlan {
 };
 // The scan of a jagged level whose lengths and begins are two columns (the
 // child level of a nested member, its descriptors gathered by level 0):
-// writes the level's offsets (n + 1, starting at 0) and clears nothing but
-// sets *noncanon unless the grandchild pool is canonical for them.
+// writes the level's offsets (count + 1 entries, starting at 0) and sets
+// *noncanon unless the pool is canonical for them.
 struct ColScan {
-  const unsigned int* len;        // n lengths
-  const unsigned long long* beg;  // n begins into the pool
-  uint64_t n;
+  const unsigned int* len;        // lengths
+  const unsigned long long* beg;  // begins into the pool
+  uint64_t n;                     // entries of len / beg; the count is at most n
+  const unsigned long long* count;  // the count, in device memory (nullptr: n)
   uint64_t pool_n;                // records in the pool
   char* offsets;
   uint32_t off_size;              // 4 or 8

@@ -84,11 +84,11 @@ def test_capacity_and_bad_indices_are_reported():
     m, m2 = d["m"], d["m2"]
     src = mrn.View(s, "aos", n, base=dev(aos.base), child_pool=dev(aos.pool), m=m, m2=m2,
                    grandchild_pool=dev(aos.gpool))
-    # too few children slots: refused once the children's count is known
+    # too few children slots: recorded by the first level (the children's
+    # count never returns to the host), reported at the next sync
     small = fm_dest(s, "soa", n, m - 1, m2)
-    st = mrn.convert_status(src, mrn.View(s, "soa", n, base=small, m=m - 1, m2=m2))
-    assert st == mrn.ESIZE
-    mrn.sync()  # the kernel recorded it too
+    assert mrn.convert_status(src, mrn.View(s, "soa", n, base=small, m=m - 1, m2=m2)) == mrn.OK
+    assert mrn.sync() == mrn.ESIZE
     # too few grandchild slots: recorded by the second level
     dst = fm_dest(s, "soa", n, m, m2 - 1)
     assert mrn.convert_status(src, mrn.View(s, "soa", n, base=dst, m=m, m2=m2 - 1)) == mrn.OK
