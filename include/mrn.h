@@ -276,6 +276,20 @@ int mrn_sync(void* stream);
 /* As mrn_sync, but returns every recorded code: bit k of *bits = code k. */
 int mrn_sync_bits(void* stream, uint32_t* bits);
 
+/* Device scratch.  The calls that need scratch (jagged and nested
+ * conversions, large staged conversions, batches' look-back words) take it
+ * in stream order from a memory pool the library owns on each device.
+ * Between calls the pool keeps reserved the most its calls have held at
+ * once, so that a repeated call does not map its scratch again: at least
+ * 256 MiB, at most 1/64 of the device's memory or 4 GiB, whichever is less
+ * (a 2,097,152-parent nested conversion holds about 0.5 GB).  This call
+ * returns the pool's memory that no call holds to the device and resets
+ * the amount kept to 256 MiB.  MRN_OK (also when the library has no pool
+ * on `device` yet), MRN_EINVAL for a device index outside 0..63,
+ * MRN_ECUDA when CUDA refuses.  Scratch still in use by queued work stays
+ * reserved until it is freed. */
+int mrn_scratch_release(int device);
+
 /* The jagged AoS -> SoA conversion of mrn_convert, without any device
  * allocation by the library.  The paper has no counterpart: this exists for
  * callers that cannot let a library allocate device memory (an application

@@ -10,6 +10,6 @@ is its ctypes binding plus host-side helpers.
 from .mrn import (  # noqa: F401
     lib, Schema, View, convert, convert_status, sync, sync_bits, jagged_count,
     transfer_convert, Batch, autotune, autotune_clear, Server, MrnError,
-    memmove, Collection,
+    memmove, Collection, scratch_release,
     status_str, debug_set, AOS, SOA, AOSOA, OK, EINVAL, ESIZE, EALIGN,
     EOVERFLOW, ENOMEM, ETIMEOUT, ECUDA, EBUSY, ENOTFOUND, EUNSUPPORTED)

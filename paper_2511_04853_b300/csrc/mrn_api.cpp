@@ -296,10 +296,16 @@ uint64_t tile_bytes(const mrn_schema* s, const SidePlan& sp, uint32_t T, uint32_
       for (uint32_t c = 0; c < s->cols.size(); ++c) off[c] = (uint32_t)aosoa_col_start(s, sp.block, c);
     return (uint64_t)(T / sp.block) * sp.block_bytes;
   }
-  uint64_t pos = 0;
+  // SoA: one range of T elements per storage column, in column order (an
+  // interleaved array's T rows once, its columns at their sub-offsets)
+  uint64_t pos = 0, row_at = 0;
   for (uint32_t c = 0; c < s->cols.size(); ++c) {
-    if (off) off[c] = (uint32_t)pos;
-    pos += (uint64_t)T * s->cols[c].size;
+    const MrnColumn& q = s->cols[c];
+    if (q.sub == 0) {
+      row_at = pos;
+      pos += (uint64_t)T * q.es;
+    }
+    if (off) off[c] = (uint32_t)(row_at + q.sub);
   }
   return pos;
 }
@@ -309,8 +315,9 @@ uint64_t tile_bytes(const mrn_schema* s, const SidePlan& sp, uint32_t T, uint32_
 bool aosoa_hole_free(const mrn_schema* s, uint32_t B) {
   uint64_t pos = 0;
   for (uint32_t c = 0; c < s->cols.size(); ++c) {
+    if (s->cols[c].sub) continue;  // inside its interleaved array's rows
     if (aosoa_col_start(s, B, c) != pos) return false;
-    pos += (uint64_t)B * s->cols[c].size;
+    pos += (uint64_t)B * s->cols[c].es;
   }
   return pos == aosoa_block_bytes(s, B);
 }
@@ -320,7 +327,7 @@ bool side_stageable(const mrn_schema* s, const SidePlan& sp, bool is_dst) {
   if (sp.kind == K_AOSOA)
     return aligned16(sp.base) && sp.block_bytes % 16 == 0 && (!is_dst || aosoa_hole_free(s, sp.block));
   for (uint32_t c = 0; c < s->cols.size(); ++c)
-    if (!aligned16(sp.col[c])) return false;
+    if (s->cols[c].sub == 0 && !aligned16(sp.col[c])) return false;
   return true;
 }
 
@@ -380,9 +387,6 @@ void widen_into_padding(const mrn_schema* s, TileGeom* g) {
 void tile_geometry(const mrn_schema* s, ConvPlan* p, uint32_t stage_bytes) {
   TileGeom& g = p->tg;
   std::memset(&g, 0, sizeof(g));
-  // The staged tile keeps each field-major column contiguous; interleaved
-  // arrays go through the direct kernel.
-  if (s->interleaved) return;
   if (!side_stageable(s, p->src, false) || !side_stageable(s, p->dst, true)) return;
   if (s->stride >= (1u << 24)) return;
   uint64_t q = 32;
@@ -404,21 +408,23 @@ void tile_geometry(const mrn_schema* s, ConvPlan* p, uint32_t stage_bytes) {
   for (uint32_t c = 0; c < s->cols.size(); ++c) {
     const uint32_t sz = s->cols[c].size;
     const uint32_t lsz = sz == 1 ? 0 : sz == 2 ? 1 : sz == 4 ? 2 : 3;
-    g.col[c] = s->cols[c].aos_off | (lsz << 24);
+    g.col[c] = s->cols[c].aos_off | (lsz << 24) | (s->cols[c].sub ? MRN_COL_SUB : 0u);
     used += sz;
   }
+  g.inter = s->interleaved ? 1u : 0u;
   // the transform walks the columns one size class at a time
   for (uint32_t lsz = 4; lsz-- > 0;) {
     uint32_t cnt = 0;
     for (uint32_t c = 0; c < s->cols.size(); ++c)
-      if ((g.col[c] >> 24) == lsz) {
+      if (((g.col[c] >> 24) & 3u) == lsz) {
         g.order[k++] = (uint8_t)c;
         ++cnt;
       }
     g.nsize |= cnt << (8 * (3 - lsz));
   }
   g.pad = used != s->stride;
-  if (g.pad && p->dst.kind == K_AOS && !s->has_jagged) widen_into_padding(s, &g);
+  // (descriptor word 3 of an interleaved plan is the element stride)
+  if (g.pad && p->dst.kind == K_AOS && !s->has_jagged && !g.inter) widen_into_padding(s, &g);
   g.tma = 1;
 }
 
@@ -454,8 +460,10 @@ bool jagged_split_ok(const mrn_schema* s, JagPlan* jp, ConvPlan* pool) {
   if (g_split_parents.load() < 0 || jp->parent.n == 0 || jp->pool_n == 0 || jp->pool_n > jp->capacity) return false;
   if (jagged_pool_plan(s, *jp, pool) != MRN_OK || !pool->tg.tma) return false;
   tile_geometry(s, &jp->parent, MRN_BATCH_STAGE_BYTES);
-  // a staged tile's groups: at most three per consumer warp
-  if (jp->parent.tg.tma && jp->parent.tg.T > 768) jp->parent.tg.tma = 0;
+  // a staged tile's groups: at most three per consumer warp; parents with
+  // an interleaved array stay on the direct path (the parents instance has
+  // no interleaved transform)
+  if (jp->parent.tg.tma && (jp->parent.tg.T > 768 || jp->parent.tg.inter)) jp->parent.tg.tma = 0;
   return true;
 }
 
@@ -708,6 +716,8 @@ int mrn_sync(void* stream) {
   if (rc) return rc;
   return status_from_bits(bits);
 }
+
+int mrn_scratch_release(int device) { return mrn::scratch_release(device); }
 
 int mrn_sync_bits(void* stream, uint32_t* bits) {
   if (!bits) return MRN_EINVAL;

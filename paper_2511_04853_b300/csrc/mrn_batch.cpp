@@ -99,13 +99,14 @@ void own_view(const mrn_view& v, std::vector<void*>* c0, std::vector<void*>* c1,
 }
 
 // Tiles of a conversion job: the staged tiles of its plan, or (plans that
-// cannot be staged, or for which the autotuner chose the direct path)
-// direct tiles of the tuned size.
+// cannot be staged, plans with an interleaved array, whose transform the
+// batch kernel does not carry, or plans for which the autotuner chose the
+// direct path) direct tiles of the tuned size.
 void convert_tiles(BatchJob* j) {
   j->kind = JOB_CONVERT;
   const LaunchShape sh = tuned_shape(j->jp.parent);
   uint32_t tr;
-  if (j->jp.parent.tg.tma && !sh.generic) {
+  if (j->jp.parent.tg.tma && !j->jp.parent.tg.inter && !sh.generic) {
     tr = j->jp.parent.tg.T;  // batch tiles coincide with staged tiles
   } else {
     j->jp.parent.tg.tma = 0;

@@ -583,6 +583,41 @@ __device__ __forceinline__ void tile_class(uint32_t desc, uint32_t c0, uint32_t 
   }
 }
 
+// The columns [c0, c1) of 2^L bytes of a plan with an interleaved array:
+// on a field-major side column c of slot i lies at its offset + i * es_c
+// (descriptor word 3; an interleaved array's row is es_c = E * 2^L bytes,
+// any other column's es_c = 2^L), on an AoS side at its offset (slot 0).
+// Two columns' loads of both records before their stores, as tile_class.
+template <int L>
+__device__ __forceinline__ void tile_class_es(uint32_t desc, uint32_t c0, uint32_t c1, uint32_t sb0, uint32_t si0,
+                                              uint32_t sb1, uint32_t si1, uint32_t db0, uint32_t di0, uint32_t db1,
+                                              uint32_t di1, bool two) {
+  uint32_t c = c0;
+  for (; c + 1 < c1; c += 2) {
+    const uint4 d0 = lds128(desc + c * 16), d1 = lds128(desc + c * 16 + 16);
+    const uint2 v00 = lds_l<L>(sb0 + d0.y + si0 * d0.w), v10 = lds_l<L>(sb0 + d1.y + si0 * d1.w);
+    uint2 v01 = v00, v11 = v10;
+    if (two) {
+      v01 = lds_l<L>(sb1 + d0.y + si1 * d0.w);
+      v11 = lds_l<L>(sb1 + d1.y + si1 * d1.w);
+    }
+    sts_l<L>(db0 + d0.z + di0 * d0.w, v00);
+    sts_l<L>(db0 + d1.z + di0 * d1.w, v10);
+    if (two) {
+      sts_l<L>(db1 + d0.z + di1 * d0.w, v01);
+      sts_l<L>(db1 + d1.z + di1 * d1.w, v11);
+    }
+  }
+  if (c < c1) {
+    const uint4 d0 = lds128(desc + c * 16);
+    const uint2 v00 = lds_l<L>(sb0 + d0.y + si0 * d0.w);
+    uint2 v01 = v00;
+    if (two) v01 = lds_l<L>(sb1 + d0.y + si1 * d0.w);
+    sts_l<L>(db0 + d0.z + di0 * d0.w, v00);
+    if (two) sts_l<L>(db1 + d0.z + di1 * d0.w, v01);
+  }
+}
+
 // The widened columns [c0, c1) of an AoS destination (see tile_convert):
 // a field of 2^x bytes (x < 3, descriptor word x) is loaded as usual and
 // stored, zero-extended, with 2^w bytes (word w), which also writes the
@@ -623,6 +658,8 @@ __device__ __forceinline__ void tile_wide(uint32_t desc, uint32_t c0, uint32_t c
 // own, so no element access branches on its size.  With Wide, the last
 // h.nwide descriptors are fields of an AoS destination stored wider than
 // they are, over the padding after them; such records are not zeroed first.
+// With Inter (a plan with an interleaved array), the slot's offset is slot
+// times descriptor word 3 instead (tile_class_es).
 // An AoS <-> SoA tile whose AoS record is W (1, 2 or 4) 4-byte words, the
 // columns in order (h.packed): the record moves as one 4-, 8- or 16-byte
 // vector on the AoS side, and word k to or from its SoA column.  Narrow
@@ -689,10 +726,11 @@ __device__ __forceinline__ void tile_convert_2x16(const TileHdr& h, uint32_t des
   }
 }
 
-template <bool Wide, bool Narrow>
+template <bool Wide, bool Narrow, bool Inter>
 __device__ __forceinline__ void tile_convert(const TileHdr& h, uint32_t desc, uint32_t st, uint32_t dt,
                                              uint32_t r0, bool two) {
-  if constexpr (Narrow) {
+  if constexpr (Inter) {  // plans with an interleaved array: no packed records
+  } else if constexpr (Narrow) {
     if (h.packed) {
       if (h.packed == 4) return tile_convert_packed<4>(h, desc, st, dt, r0, two);
       if (h.packed == 2) return tile_convert_packed<2>(h, desc, st, dt, r0, two);
@@ -712,6 +750,13 @@ __device__ __forceinline__ void tile_convert(const TileHdr& h, uint32_t desc, ui
   zero_record(h, db0);
   if (two) zero_record(h, db1);
   const uint32_t e8 = h.nsize & 0xff, e4 = e8 + ((h.nsize >> 8) & 0xff), e2 = e4 + ((h.nsize >> 16) & 0xff);
+  if constexpr (Inter) {
+    tile_class_es<3>(desc, 0, e8, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
+    tile_class_es<2>(desc, e8, e4, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
+    tile_class_es<1>(desc, e4, e2, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
+    tile_class_es<0>(desc, e2, h.ncols, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
+    return;
+  }
   const uint32_t ew = Wide ? h.ncols - h.nwide : h.ncols;
   tile_class<3>(desc, 0, e8, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
   tile_class<2>(desc, e8, e4, sb0, si0, sb1, si1, db0, di0, db1, di1, two);

@@ -89,10 +89,13 @@ uint64_t fm_gchild_col_start(const mrn_schema* s, int kind, uint32_t B, uint64_t
 
 // ---- device status word and scratch helpers (mrn_kernels.cu)
 // Stream-ordered scratch for one call, from the library's own pool on the
-// stream's device (it keeps up to 256 MiB reserved between calls); freed
-// in stream order with scratch_free.  MRN_ENOMEM on failure.
+// stream's device (it keeps reserved between calls the most its calls have
+// held at once: at least 256 MiB, at most 1/64 of the device's memory or
+// 4 GiB); freed in stream order with scratch_free.  MRN_ENOMEM on failure.
 int scratch_alloc(void** p, size_t bytes, void* stream);
 void scratch_free(void* p, void* stream);
+// Returns device dev's pool memory that no call holds (mrn_scratch_release).
+int scratch_release(int dev);
 int device_sm_count();
 int read_and_clear_status(void* stream, uint32_t* bits);
 int status_from_bits(uint32_t bits);

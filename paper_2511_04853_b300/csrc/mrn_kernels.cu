@@ -61,13 +61,14 @@ __global__ void __launch_bounds__(256) k_convert(const __grid_constant__ ConvPla
 // Narrow: the instance takes the one-column and two-2-byte-column record
 // paths (single conversions); the persistent batch kernel leaves them out
 // (those records take the general body there) because their branches cost
-// its other jobs about 1%.
-template <bool Wide, bool Narrow>
+// its other jobs about 1%.  Inter: plans with an interleaved array (single
+// conversions; tile_class_es).
+template <bool Wide, bool Narrow, bool Inter>
 __device__ __forceinline__ void tma_transform(const TileHdr& h, uint32_t desc, const char* st, char* dt, uint32_t R,
                                               int lane, int warp) {
   const uint32_t s = smem_u32(st), d = smem_u32(dt);
   const TileHdr hh = h;
-  if (Narrow && hh.packed == 1) {
+  if (Narrow && !Inter && hh.packed == 1) {
     // one 4-byte column: both tiles hold the same words (R, a multiple of
     // 32, records), copied 16 bytes per thread and step
     const uint4 dd = lds128(desc);
@@ -78,18 +79,21 @@ __device__ __forceinline__ void tma_transform(const TileHdr& h, uint32_t desc, c
     }
   }
   for (uint32_t g = (uint32_t)warp * 32; g < R; g += 2 * 8 * 32)
-    tile_convert<Wide, Narrow>(hh, desc, s, d, g + lane, g + 8 * 32 < R);
+    tile_convert<Wide, Narrow, Inter>(hh, desc, s, d, g + lane, g + 8 * 32 < R);
 }
 
 // Entry k of the staged-transform descriptor table: the k-th column in
 // size-class order (see tile_convert); with `wide`, the order with the
-// fields widened over an AoS destination's padding last.
+// fields widened over an AoS destination's padding last.  Word 3 is the
+// widened store's log2 size, or (a plan with an interleaved array) the
+// column's field-major element stride.
 __host__ __device__ __forceinline__ uint4 tile_desc(const ConvPlan& p, uint32_t k, bool wide = false) {
   const bool w = wide && p.dst.kind == K_AOS && p.tg.nwide;
   const uint32_t c = w ? p.tg.worder[k] : p.tg.order[k];
   const uint32_t col = p.tg.col[c], aos_off = col & 0xffffffu;
   return make_uint4((col >> 24) & 3u, p.src.kind == K_AOS ? aos_off : p.tg.src_off[c],
-                    p.dst.kind == K_AOS ? aos_off : p.tg.dst_off[c], (col >> 28) & 3u);
+                    p.dst.kind == K_AOS ? aos_off : p.tg.dst_off[c],
+                    p.tg.inter ? (uint32_t)p.fm_es[c] : (col >> 28) & 3u);
 }
 
 __host__ __device__ __forceinline__ TileHdr tile_hdr(const ConvPlan& p, bool wide = false) {
@@ -104,15 +108,16 @@ __host__ __device__ __forceinline__ TileHdr tile_hdr(const ConvPlan& p, bool wid
   h.nwide = w ? p.tg.nwide : 0u;
   h.packed = 0;
   const uint32_t n4 = (p.tg.nsize >> 8) & 0xff;
-  if (((p.src.kind == K_AOS && p.dst.kind == K_SOA) || (p.src.kind == K_SOA && p.dst.kind == K_AOS)) &&
-      p.tg.nsize == (n4 << 8) && (n4 == 1 || n4 == 2 || n4 == 4) && p.ncols == n4 && p.stride == 4 * n4) {
+  // (not for interleaved plans: their SoA tiles hold rows, not columns)
+  const bool pair =
+      !p.tg.inter && ((p.src.kind == K_AOS && p.dst.kind == K_SOA) || (p.src.kind == K_SOA && p.dst.kind == K_AOS));
+  if (pair && p.tg.nsize == (n4 << 8) && (n4 == 1 || n4 == 2 || n4 == 4) && p.ncols == n4 && p.stride == 4 * n4) {
     bool in_order = true;
     for (uint32_t k = 0; k < n4; ++k) in_order = in_order && (p.tg.col[p.tg.order[k]] & 0xffffffu) == 4 * k;
     if (in_order) h.packed = n4;
   }
   // a 4-byte record of two 2-byte columns, in order
-  if (((p.src.kind == K_AOS && p.dst.kind == K_SOA) || (p.src.kind == K_SOA && p.dst.kind == K_AOS)) &&
-      p.tg.nsize == (2u << 16) && p.ncols == 2 && p.stride == 4 && (p.tg.col[p.tg.order[0]] & 0xffffffu) == 0 &&
+  if (pair && p.tg.nsize == (2u << 16) && p.ncols == 2 && p.stride == 4 && (p.tg.col[p.tg.order[0]] & 0xffffffu) == 0 &&
       (p.tg.col[p.tg.order[1]] & 0xffffffu) == 2)
     h.packed = kPacked2x16;
   tile_side_geometry(p.src.kind, p.src.block, p.src.block_shift, p.src.block_bytes, p.stride, &h.sblock, &h.sshift,
@@ -1378,11 +1383,12 @@ __device__ __forceinline__ uint32_t side_tile_bytes(const ConvPlan& p, const Sid
   if (R == p.tg.T) return full;
   if (sp.kind == K_AOS) return R * p.stride;
   if (sp.kind == K_AOSOA) return R / sp.block * (uint32_t)sp.block_bytes;
-  return full / p.tg.T * R;  // SoA: T * (sum of column sizes), columns packed
+  return full / p.tg.T * R;  // SoA: T * (sum of storage columns' element bytes), packed
 }
 
 // Warp-wide bulk stores of the first R records of destination tile lt;
 // every lane commits its own bulk group.
+template <bool kInter>
 __device__ __forceinline__ void tma_store_tile_warp(const ConvPlan& p, uint64_t lt, uint32_t R, const char* tile,
                                                     int lane) {
   const TileGeom& g = p.tg;
@@ -1393,6 +1399,9 @@ __device__ __forceinline__ void tma_store_tile_warp(const ConvPlan& p, uint64_t 
     if (lane == 0) bulk_s2g(sp.base + t0 * p.stride, tile, bytes);
   } else if (sp.kind == K_AOSOA) {
     if (lane == 0) bulk_s2g(sp.base + (t0 / sp.block) * sp.block_bytes, tile, bytes);
+  } else if (kInter) {  // a range per storage column (an interleaved array's rows once)
+    for (uint32_t c = lane; c < p.ncols; c += 32)
+      if (!(g.col[c] & MRN_COL_SUB)) bulk_s2g(sp.col[c] + t0 * p.fm_es[c], tile + g.dst_off[c], R * p.fm_es[c]);
   } else {
     for (uint32_t c = lane; c < p.ncols; c += 32)
       bulk_s2g(sp.col[c] + t0 * p.fm_size[c], tile + g.dst_off[c], R * p.fm_size[c]);
@@ -1473,9 +1482,11 @@ __device__ __forceinline__ void load_cache(const BatchJob& J, unsigned int job, 
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const uint32_t col = (uint32_t)lane + 32u * k;
-    const bool have = col < P.ncols && P.src.kind == K_SOA;
+    // a range per storage column: an interleaved array's rows are loaded
+    // with its first column
+    const bool have = col < P.ncols && P.src.kind == K_SOA && !(P.tg.col[col] & MRN_COL_SUB);
     c->col[k] = have ? P.src.col[col] : nullptr;
-    c->size[k] = have ? P.fm_size[col] : 0u;
+    c->size[k] = have ? P.fm_es[col] : 0u;
     c->off[k] = have ? P.tg.src_off[col] : 0u;
   }
 }
@@ -1656,6 +1667,7 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
 // Storer warp: stores staged tiles in order as the consumers finish them
 // (lane c stores SoA column c); each destination buffer is freed once its
 // stores have read it.
+template <bool kInter>
 __device__ __forceinline__ void batch_storer(const BatchJob* __restrict__ jobs, const BatchSmem& m, int lane) {
   uint32_t c = 0;
   int seen = 0;
@@ -1669,7 +1681,7 @@ __device__ __forceinline__ void batch_storer(const BatchJob* __restrict__ jobs, 
     if (ready) {
       __syncwarp();  // orders lane 0's acquire before the other lanes' stores
       const StoreItem it = *m.sq(c % kSQ);
-      tma_store_tile_warp(jobs[it.job].jp.parent, it.local, it.records, m.dst(d), lane);
+      tma_store_tile_warp<kInter>(jobs[it.job].jp.parent, it.local, it.records, m.dst(d), lane);
       bulk_wait_read<0>();
       __syncwarp();
       if (lane == 0) mbar_arrive(m.dfree(d));
@@ -1705,7 +1717,7 @@ __device__ __forceinline__ void batch_storer(const BatchJob* __restrict__ jobs, 
 // offsets epilogue is compiled in; where it cannot occur, leaving it out
 // keeps the transform's register allocation: single points AoS -> SoA at
 // 2^26 records 0.718 ms with it, 0.672 without).
-template <bool kStatic, bool kWide, bool kJag>
+template <bool kStatic, bool kWide, bool kJag, bool kInter>
 __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
                                            const unsigned long long* __restrict__ first_tile, unsigned int njobs,
                                            unsigned long long total_tiles, unsigned int* counter,
@@ -1757,7 +1769,7 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
     return;
   }
   if (warp == 9) {
-    batch_storer(jobs, m, lane);
+    batch_storer<kInter>(jobs, m, lane);
     return;
   }
   // consumers
@@ -1780,7 +1792,7 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
         break;
       }
       const StageDesc* sd = m.desc(s);
-      tma_transform<kWide, kStatic>(sd->h, smem_u32(sd->d), m.src(s), m.dst(d), ts.staged, lane, warp);
+      tma_transform<kWide, kStatic, kInter>(sd->h, smem_u32(sd->d), m.src(s), m.dst(d), ts.staged, lane, warp);
       // parents of a split jagged job: the offsets, from the staged lengths
       // (before the source stage is released)
       if (kJag && ts.jag) jag_offsets_staged(jobs[ts.job].jp, ts.local, ts.staged, m.src(s), sd->h, lane, warp);
@@ -1830,7 +1842,7 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
                                                         unsigned int* counter, uint32_t chunk,
                                                         const unsigned int* conds) {
   extern __shared__ __align__(128) char batch_smem[];
-  batch_main<false, false, true>(jobs, first_tile, njobs, total_tiles, counter, chunk, batch_smem, conds);
+  batch_main<false, false, true, false>(jobs, first_tile, njobs, total_tiles, counter, chunk, batch_smem, conds);
 }
 
 // One staged conversion through the same warp-specialized pipeline: the
@@ -1841,14 +1853,15 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
 // plan stores fields wider over an AoS destination's padding.
 // With `cond`, the launch does nothing when *cond != 0 (the child pool of a
 // split jagged conversion that the scan found not canonical).  kJag: the
-// instance for the parents job of a split jagged conversion.
-template <bool kWide, bool kJag>
+// instance for the parents job of a split jagged conversion.  kInter: the
+// instance for plans with an interleaved array.
+template <bool kWide, bool kJag, bool kInter>
 __global__ void __launch_bounds__(kBThreads, 3) k_convert_ws(const __grid_constant__ BatchJob job,
                                                              uint32_t chunk, unsigned int* counter,
                                                              const unsigned int* cond) {
   if (cond && ld_relaxed_u32(cond) != 0) return;
   extern __shared__ __align__(128) char batch_smem[];
-  batch_main<true, kWide, kJag>(&job, nullptr, 1u, job.ntiles, counter, chunk, batch_smem, nullptr);
+  batch_main<true, kWide, kJag, kInter>(&job, nullptr, 1u, job.ntiles, counter, chunk, batch_smem, nullptr);
 }
 
 // ================================================================== host
@@ -1894,15 +1907,23 @@ int occupancy(const void* fn, int threads, size_t smem) {
 }  // namespace
 
 // Scratch of the library's calls: stream-ordered allocations from a memory
-// pool the library owns, one per device, that keeps up to
-// kScratchKeepBytes reserved between calls.  (The device's default pool
-// returns its free memory at every synchronisation; a call whose scratch
-// must be mapped again then costs more than its kernel at small sizes.)
-// Under stream capture the allocation is an ordinary cudaMallocAsync.
+// pool the library owns, one per device.  The device's default pool
+// returns its free memory at every synchronisation, and a call whose
+// scratch must be mapped again then spends longer on the host than its
+// kernels take at small sizes (and, for the half-gigabyte scratch of a
+// 2,097,152-parent nested conversion, about 0.4 ms of a 0.8 ms call).  So
+// the pool keeps reserved between calls the most its calls have held at
+// once: its release threshold starts at kScratchKeepBytes and follows
+// that high-water mark up to 1/64 of the device's memory (at most
+// kScratchKeepMax); mrn_scratch_release returns it.  Under stream capture
+// the allocation is an ordinary cudaMallocAsync.
 namespace {
 constexpr uint64_t kScratchKeepBytes = 256ull << 20;
+constexpr uint64_t kScratchKeepMax = 4ull << 30;
 std::mutex g_pool_mu;
 cudaMemPool_t g_pools[64] = {};
+uint64_t g_pool_keep[64] = {};  // current release threshold
+uint64_t g_pool_cap[64] = {};   // its bound on this device
 
 cudaMemPool_t scratch_pool(int dev) {
   if (dev < 0 || dev >= 64) return nullptr;
@@ -1920,9 +1941,30 @@ cudaMemPool_t scratch_pool(int dev) {
     }
     uint64_t keep = kScratchKeepBytes;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    cudaDeviceProp prop;
+    const uint64_t total = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? (uint64_t)prop.totalGlobalMem : 0ull;
+    cudaGetLastError();
+    g_pool_cap[dev] = std::max<uint64_t>(kScratchKeepBytes, std::min<uint64_t>(kScratchKeepMax, total / 64));
+    g_pool_keep[dev] = keep;
     g_pools[dev] = pool;
   }
   return g_pools[dev];
+}
+
+// Raises device dev's release threshold to the memory its pool has in use
+// now (in 2 MiB steps, within the bound).
+void keep_in_use(cudaMemPool_t pool, int dev) {
+  uint64_t used = 0;
+  if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (used <= g_pool_keep[dev] || g_pool_keep[dev] >= g_pool_cap[dev]) return;
+  const uint64_t step = 2ull << 20;
+  uint64_t keep = std::min<uint64_t>(g_pool_cap[dev], (used + step - 1) / step * step);
+  if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess) g_pool_keep[dev] = keep;
+  cudaGetLastError();
 }
 }  // namespace
 
@@ -1942,6 +1984,22 @@ int scratch_alloc(void** p, size_t bytes, void* stream) {
     *p = nullptr;
     return MRN_ENOMEM;
   }
+  if (pool && bytes > kScratchKeepBytes / 4) keep_in_use(pool, dev);
+  return MRN_OK;
+}
+
+int scratch_release(int dev) {
+  if (dev < 0 || dev >= 64) return MRN_EINVAL;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  cudaMemPool_t pool = g_pools[dev];
+  if (!pool) return MRN_OK;
+  uint64_t keep = kScratchKeepBytes;
+  if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess ||
+      cudaMemPoolTrimTo(pool, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return MRN_ECUDA;
+  }
+  g_pool_keep[dev] = keep;
   return MRN_OK;
 }
 
@@ -2014,9 +2072,11 @@ int launch_staged_job(BatchJob& job, void* stream, const LaunchShape& sh, const 
     job.ntiles = staged_tile_count(p.n, nrec, p.tg.T, p.tg.G);
     // the instance with the widened-field transform only for plans that
     // have widened fields: the branch costs the others a few percent
-    const void* fn = job.kind == JOB_JAG_PARENTS ? reinterpret_cast<const void*>(&k_convert_ws<false, true>)
-                     : p.dst.kind == K_AOS && p.tg.nwide ? reinterpret_cast<const void*>(&k_convert_ws<true, false>)
-                                                         : reinterpret_cast<const void*>(&k_convert_ws<false, false>);
+    const void* fn = job.kind == JOB_JAG_PARENTS ? reinterpret_cast<const void*>(&k_convert_ws<false, true, false>)
+                     : p.tg.inter ? reinterpret_cast<const void*>(&k_convert_ws<false, false, true>)
+                     : p.dst.kind == K_AOS && p.tg.nwide
+                         ? reinterpret_cast<const void*>(&k_convert_ws<true, false, false>)
+                         : reinterpret_cast<const void*>(&k_convert_ws<false, false, false>);
     allow_batch_smem(fn);
     const int occ = occupancy(fn, kBThreads, kBatchSmem);
     const int per_sm = sh.ctas_per_sm ? std::min((int)sh.ctas_per_sm, occ) : occ;

@@ -39,6 +39,7 @@ struct ColPlan {
 // T*stride bytes; AoSoA: T/B whole blocks) or, for SoA, one range per column
 // packed in column order (column c at off[c] inside the tile).
 #define MRN_BATCH_STAGE_BYTES 12288u  // stage of the warp-specialized pipeline
+#define MRN_COL_SUB (1u << 30)
 struct TileGeom {
   uint32_t tma;        // 1: full tiles go through the TMA pipeline
   uint32_t T;          // records per tile (multiple of G)
@@ -54,9 +55,18 @@ struct TileGeom {
   // record needs no zeroing pass.  Single conversions use it; a batch's
   // stage tables keep `order`.
   uint32_t nwide, wnsize;
+  // 1: the schema stores an array property interleaved (an N x E array):
+  // a field-major tile holds that property's rows, column c of it at
+  // off[c] + slot * es_c, and descriptor word 3 carries es_c (the
+  // instance k_convert_ws<false, false, true>; batches take such jobs on
+  // the direct path)
+  uint32_t inter;
   uint32_t src_off[MRN_MAX_COLS];  // SoA: column offset in the tile; AoSoA: column start in a block
   uint32_t dst_off[MRN_MAX_COLS];
-  uint32_t col[MRN_MAX_COLS];      // per data column: AoS offset | log2(size) << 24 | w << 28
+  // per data column: AoS offset | log2(size) << 24 | w << 28, and
+  // MRN_COL_SUB for the elements after the first of an interleaved row
+  // (copied with that row's bulk copy)
+  uint32_t col[MRN_MAX_COLS];
   uint8_t order[MRN_MAX_COLS];     // data columns by decreasing size (stable)
   uint8_t worder[MRN_MAX_COLS];
 };

@@ -109,6 +109,7 @@ SIGNATURES = [
     ("mrn_convert_jagged_noalloc", ctypes.c_int, [ctypes.POINTER(ViewStruct), ctypes.POINTER(ViewStruct), vp]),
     ("mrn_sync", ctypes.c_int, [vp]),
     ("mrn_sync_bits", ctypes.c_int, [vp, ctypes.POINTER(u32)]),
+    ("mrn_scratch_release", ctypes.c_int, [ctypes.c_int]),
     ("mrn_jagged_count", ctypes.c_int, [ctypes.POINTER(ViewStruct), ctypes.POINTER(u64), vp]),
     ("mrn_debug_set", ctypes.c_int, [ctypes.c_int, ctypes.c_longlong]),
     ("mrn_transfer_convert", ctypes.c_int, [ctypes.POINTER(ViewStruct), ctypes.POINTER(ViewStruct),
@@ -375,6 +376,11 @@ def convert_status(src, dst, stream=None):
 def sync(stream=None):
     """Waits for the stream; returns the first device-recorded status."""
     return lib().mrn_sync(_stream(stream))
+
+
+def scratch_release(device=0):
+    """Returns the library's unused scratch memory on `device`."""
+    check(lib().mrn_scratch_release(device))
 
 
 def sync_bits(stream=None):

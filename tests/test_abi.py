@@ -154,6 +154,15 @@ def test_convert_rejects_bad_views_without_a_device():
     assert mrn.convert_status(src, dst2, stream=0) == mrn.EINVAL
 
 
+def test_scratch_release_without_a_device():
+    """No pool exists before a conversion: the release is a no-op; a device
+    index outside 0..63 is refused."""
+    mrn.scratch_release(0)
+    with pytest.raises(mrn.MrnError) as e:
+        mrn.scratch_release(64)
+    assert e.value.code == mrn.EINVAL
+
+
 @pytest.mark.parametrize("desc", [datagen.TRACKS_NESTED,
                                   [("g", "group", [("p", "f64", 1),
                                                    ("v", "jagged", "u32", [("x", "u8", 2),

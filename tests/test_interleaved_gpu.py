@@ -13,6 +13,17 @@ from gpu_util import dev, dev_dest, garbage, host
 
 pytestmark = pytest.mark.gpu
 
+
+@pytest.fixture(autouse=True, params=["staged", "direct"])
+def conversion_path(request):
+    """Every test of this module runs twice: single conversions on the
+    TMA-staged kernel wherever it applies (an interleaved array's rows are
+    one bulk copy per tile, its elements at slot * row bytes in the tile),
+    and on the direct kernel only."""
+    mrn.debug_set(3, 1 if request.param == "direct" else 0)
+    yield request.param
+    mrn.debug_set(3, 0)
+
 DTYPES = {1: "u8", 2: "u16", 4: "f32", 8: "u64"}
 PAIRS = [("aos", 0, "soa", 0), ("soa", 0, "aos", 0), ("aos", 0, "aosoa", 32), ("aosoa", 32, "aos", 0),
          ("soa", 0, "aosoa", 5), ("aosoa", 5, "soa", 0), ("aosoa", 32, "aosoa", 128)]
@@ -43,6 +54,15 @@ def check_pair(desc, n, sk, sb, dk, db, seed=1):
 def test_every_pair_extent_and_size(size, E, pair):
     for n in (1, 1000, 70001):
         check_pair(one_array(size, E), n, *pair, seed=size * 10 + E)
+
+
+@pytest.mark.parametrize("pair", PAIRS)
+def test_wide_rows(pair):
+    """Rows of 240 bytes (f32[60]: a staged tile of 32 records) and of
+    480 bytes (u64[60]: 32 records exceed a stage, the direct kernel
+    only)."""
+    for E, size, n in ((60, 4, 1000), (60, 8, 300)):
+        check_pair(one_array(size, E), n, *pair, seed=E)
 
 
 @pytest.mark.parametrize("pair", PAIRS)
