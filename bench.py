@@ -4,21 +4,21 @@ Step: one replay of the CUDA graph of the mixed batch -- 4,096 collections
 (records round(10^U(3, 6)), seed 3; schema uniform over points / cells /
 tracks, the tracks jagged with Poisson(20) children clipped at 256; AoS
 source; target uniform over SoA / AoSoA(32) / AoSoA(128)) converted in
-three launches: k_jag_scan (the tracks' lengths in chunks of 8,192
-parents: the offsets' bases and the check that each child pool is
-canonical), the persistent k_batch (points, cells, the tracks' parents with
-their offsets, and every canonical tracks pool as a plain conversion of the
-child schema), and k_batch_jag_rest (gathers the children of any pool that
-is not canonical; none here, so it returns at once).  About 92 GB of
-algorithmic bytes per step, inputs resident in HBM (far larger than the
-126 MB L2).
+three launches: the persistent k_batch twice (first the tracks' parents,
+their begins written as offsets and each child pool checked, record by
+record, to be canonical, with a share of the points / cells jobs; then
+every canonical tracks pool as a plain conversion of the child schema,
+with the other points / cells jobs), and k_batch_jag_rest (converts whole
+again any tracks job whose pool is not canonical; none here, so it returns
+at once).  About 92 GB of algorithmic bytes per step, inputs resident in
+HBM (far larger than the 126 MB L2).
 
 value         algorithmic bytes (read + write of every conversion) / step
               time (CUDA events around all timed steps)
 roofline      the dominant kernel (k_batch, which moves every algorithmic
               byte) against the measured HBM copy bandwidth, from events
-              recorded inside every timed replay after the scan;
-              per_kernel gives both parts
+              recorded inside every timed replay after the scratch
+              reset; per_kernel gives both parts
 e2e           the same collections through the C ABI from pinned HOST
               buffers: mrn_transfer_convert host AoS -> device target for
               every collection, then the status word read back
@@ -114,7 +114,7 @@ def cells_workload(batch):
 
 def workload_config(jobs, alg_bytes=None, records=None):
     """The step's workload: the mixed batch (the short name first)."""
-    c = {"workload": "mixed batch: %d collections, one CUDA graph (k_jag_scan + k_batch + k_batch_jag_rest)" % jobs,
+    c = {"workload": "mixed batch: %d collections, one CUDA graph (k_batch x 2 + k_batch_jag_rest)" % jobs,
          "collections": jobs,
          "sizes": "records round(10^U(3,6)), seed %d" % MIXED_SEED,
          "schemas": "uniform over points (32 B AoS), cells (24 B), tracks (24 B + jagged 8 B children, "
@@ -417,10 +417,9 @@ def build_mixed(mrn, torch, jobs):
             alg_jag += a
             parents += n
     torch.cuda.synchronize()
-    # k_batch moves every algorithmic byte; k_jag_scan re-reads the tracks'
-    # parent records (24 B each) for their lengths and begins
+    # k_batch (two launches) moves every algorithmic byte
     return {"items": items, "alg": alg, "alg_jag": alg_jag, "alg_plain": alg - alg_jag,
-            "scan_read_bytes": 24 * parents, "alg_kbatch": alg,
+            "parents": parents, "alg_kbatch": alg,
             "records": sum(n for _, n, _ in plan), "setup_s": round(time.perf_counter() - t0, 1),
             "pairs": [(it["src"], it["dst"]) for it in items]}
 
@@ -579,8 +578,9 @@ def timed_steps(mrn, torch, stream, batch, steps, warmup, world, local):
     clocks = clk.stop(window=(h0, h1))
     clocks["window_s"] = round(h1 - h0, 3)
     total = t_start.elapsed_time(t_end)
-    # ev: before the scratch reset, after k_jag_scan, after k_batch_jag_rest
-    return {"ms_per_step": total / steps, "k_jag_scan": [a.elapsed_time(b) for a, b, _ in ev],
+    # ev: before the scratch reset, before the first k_batch launch, after
+    # k_batch_jag_rest
+    return {"ms_per_step": total / steps, "setup": [a.elapsed_time(b) for a, b, _ in ev],
             "k_batch": [b.elapsed_time(c) for _, b, c in ev], "launch": [a.elapsed_time(c) for a, _, c in ev],
             "clocks": clocks}
 
@@ -628,7 +628,7 @@ def run_mine(args, rank, world):
     assert mrn.sync() == mrn.OK
     bad = outputs_equal(torch, M, want)
     assert bad < 0, "timed output of job %d differs from the checked output" % bad
-    lm, lj, lb = (statistics.mean(T[k]) for k in ("launch", "k_jag_scan", "k_batch"))
+    lm, lj, lb = (statistics.mean(T[k]) for k in ("launch", "setup", "k_batch"))
     ntr = sum(1 for it in M["items"] if it["name"] == "tracks")
     roofline = roof(M["alg_kbatch"], lb, peak, peak_src, "k_batch (the %d points / cells jobs, and the %d tracks "
                     "jobs' parents with their offsets and child pools; persistent)" % (len(M["items"]) - ntr, ntr),
@@ -637,21 +637,20 @@ def run_mine(args, rank, world):
                     step={"launch_ms_mean": round(lm, 5), "ms_per_step": round(ms_step, 5),
                           "gbps": round(M["alg"] / (lm * 1e-3) / 1e9, 1),
                           "frac": round(M["alg"] / (lm * 1e-3) / 1e9 / peak, 4)},
-                    per_kernel={"k_jag_scan": {"ms_mean": round(lj, 4), "algorithmic_bytes": 0,
-                                               "read_bytes": M["scan_read_bytes"],
-                                               "read_gbps": round(M["scan_read_bytes"] / (lj * 1e-3) / 1e9, 1),
-                                               "what": "the tracks' lengths and begins: a re-read of the parent "
-                                                       "records (24 B each), group bases and pool checks written",
-                                               "note": "includes the scratch-reset memset node before it"},
+                    per_kernel={"setup": {"ms_mean": round(lj, 4), "algorithmic_bytes": 0,
+                                          "what": "the scratch-reset memset node (and the fused jagged launch, "
+                                                  "which has no jobs here: every tracks pool fits its "
+                                                  "destination)"},
                                 "k_batch": {"ms_mean": round(lb, 4), "algorithmic_bytes": M["alg_kbatch"],
                                             "gbps": round(M["alg_kbatch"] / (lb * 1e-3) / 1e9, 1),
                                             "frac": round(M["alg_kbatch"] / (lb * 1e-3) / 1e9 / peak, 4),
                                             "what": "points and cells jobs, tracks parents and offsets, tracks "
                                                     "child pools (16 B per child)",
-                                            "note": "includes k_batch_jag_rest after it (returns at once: "
-                                                    "every pool is canonical)"}})
+                                            "note": "both persistent launches (%d parents checked record by "
+                                                    "record), and k_batch_jag_rest after them (returns at "
+                                                    "once: every pool is canonical)" % M["parents"]}})
     if rank == 0:
-        print("step: %.3f ms, %.1f GB/s; k_batch %.3f ms, k_jag_scan %.3f ms; parity %s" % (
+        print("step: %.3f ms, %.1f GB/s; k_batch %.3f ms, setup %.3f ms; parity %s" % (
             ms_step, value, lb, lj, parity), file=sys.stderr, flush=True)
     if profiling:
         if rank == 0:
@@ -710,8 +709,8 @@ def finish_mine(mrn, torch, stream, args, rank, world, M, batch, want, T, ms_ste
                                   "worst_ms": round(launch_shape.get("worst_ms", 0.0), 3),
                                   "worst_over_best": round(launch_shape.get("worst_ms", 0.0)
                                                            / max(1e-9, launch_shape.get("ms", 1.0)), 4),
-                                  "space": "chunk {1,2,4,8,16} x CTAs per SM {occupancy, 2} for k_batch; "
-                                           "k_jag_scan has one CTA per 8,192-parent chunk (no launch shape)"},
+                                  "space": "chunk {1,2,4,8,16} x CTAs per SM {occupancy, 2} for both "
+                                           "k_batch launches"},
                               "pair_shapes": tuned}
     link = host_link(torch, stream) if rank == 0 else None
     e2e = run_e2e_mixed(mrn, torch, M, world, link, want)

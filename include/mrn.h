@@ -315,9 +315,10 @@ int mrn_jagged_count(const mrn_view* src, uint64_t* m, void* stream);
 
 /* Test and fault-injection settings (host side; they take effect for
  * conversions planned afterwards):
- *   key 1: index of a jagged tile (in a split run: a scan chunk of 8,192
- *          parents) that never publishes its sum (-1: none), so that
- *          its successors' bounded waits expire and record MRN_ETIMEOUT;
+ *   key 1: index of a jagged tile (in a split single conversion: a scan
+ *          chunk of 8,192 parents) that never publishes its sum (-1: none),
+ *          so that its successors' bounded waits expire and record
+ *          MRN_ETIMEOUT;
  *   key 2: bound of each look-back wait in nanoseconds (default 2e9);
  *   key 3: 1 = single conversions use the direct kernel (vector loads and
  *          stores per lane) even where the TMA-staged kernel applies;
@@ -330,8 +331,9 @@ int mrn_jagged_count(const mrn_view* src, uint64_t* m, void* stream);
  *          as one staged conversion of the child schema when it is
  *          canonical, and a pass that gathers the children when it is not.
  *          Batches split every jagged AoS job whose pool fits the
- *          destination's child capacity.  A negative value turns split runs
- *          off (single conversions and batches);
+ *          destination's child capacity and whose offsets fit their type,
+ *          in their own form (see mrn_batch_create).  A negative value
+ *          turns split runs off (single conversions and batches);
  *   key 5: parents up to which a single fused jagged AoS -> SoA / AoSoA
  *          conversion uses tiles of 256 parents instead of 1,024 (default
  *          250,000; -1: never). */
@@ -387,15 +389,19 @@ typedef struct mrn_batch mrn_batch; /* opaque */
  * pairs, jagged AoS<->SoA included) to run in one persistent kernel launch:
  * a device job table, a prefix over the jobs' tiles, per-job tile sizes
  * from the autotuner cache.  A jagged AoS -> field-major job runs split
- * where it can (see mrn_debug_set, key 4): one launch before the persistent
- * one scans the lengths of all such jobs (chunks of 8,192 parents), and the
- * persistent launch converts their parents (writing the offsets) and their
- * child pools (each a plain conversion, run when the scan found the pool
- * canonical); a last launch gathers the children of any pool that was not
- * (it returns at once when every pool was).  Jagged jobs that cannot run
- * split (a pool larger than the destination's child capacity) run in one
- * more launch before the persistent one, one CTA per tile of 1,024 parents
- * that scans, converts and gathers.  With use_graph = 1 the launch sequence (scratch reset +
+ * where it can (see mrn_debug_set, key 4) and needs no scan: a pool is
+ * canonical (its records exactly the children, in parent order) when every
+ * parent's begin is the previous parent's begin plus its length (the first
+ * 0, the last parent's end the pool's size), and its offsets are then the
+ * begins.  The persistent launch converts the parents, writing the begins
+ * as offsets and checking those equalities; a second persistent launch
+ * converts the child pools (each a plain conversion, skipped unless its
+ * check passed); a last launch converts the jobs whose pools were not
+ * canonical whole again with the fused kernel (it returns at once when
+ * every pool was).  Jagged jobs that cannot run split (a pool larger than
+ * the destination's child capacity, or offsets beyond their type) run in
+ * one more launch before the persistent one, one CTA per tile of 1,024
+ * parents that scans, converts and gathers.  With use_graph = 1 the launch sequence (scratch reset +
  * the launches) is captured once into a CUDA graph and each mrn_batch_launch
  * replays it.  The views' buffers must stay valid while the batch is used.
  * Copies the job descriptions; `jobs` may be freed. */
@@ -404,9 +410,8 @@ int mrn_batch_create(const mrn_job* jobs, size_t n_jobs, int use_graph, mrn_batc
 int mrn_batch_launch(mrn_batch* b, void* stream);
 /* As mrn_batch_launch, and records three caller-created CUDA events
  * (cudaEvent_t, passed as void*) on `stream`: ev_begin before the batch's
- * work, ev_mid after the scratch reset, the split jobs' scan and the fused
- * jagged launch, ev_end after the persistent launch and the fall-back
- * gather.
+ * work, ev_mid after the scratch reset and the fused jagged launch, ev_end
+ * after the two persistent launches and the fall-back pass.
  * With use_graph = 1 the events are record nodes of a second graph of the
  * same work, captured at the first call and pointed at the given events at
  * each call (three distinct events, else MRN_EINVAL; the events of earlier

@@ -467,6 +467,11 @@ bool jagged_split_ok(const mrn_schema* s, JagPlan* jp, ConvPlan* pool) {
   return true;
 }
 
+bool jagged_local_ok(const JagPlan& jp) {
+  // the largest offset written, offset_base + pool_n, fits the offset type
+  return jp.off_size == 8 || (jp.offset_base <= 0xffffffffull && jp.pool_n <= 0xffffffffull - jp.offset_base);
+}
+
 int build_jagged_plan(const mrn_view& src, const mrn_view& dst, JagPlan* jp) {
   const mrn_schema* s = src.schema;
   std::memset(jp, 0, sizeof(*jp));

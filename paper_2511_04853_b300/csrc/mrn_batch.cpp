@@ -18,32 +18,36 @@ struct mrn_batch {
   std::vector<std::vector<void*>> cols;  // 4 per job
   std::vector<size_t> first_entry;       // job -> index of its first table entry
   std::vector<BatchJob> jobs;  // every planned job, in order
-  // The jobs split over the two launches: jagged AoS -> field-major jobs
-  // (k_batch_jag, one CTA per tile) and all others (k_batch, persistent);
-  // each launch numbers its own tiles.
+  // The jobs split over the kernels: fused jagged AoS -> field-major jobs
+  // (k_batch_jag, one CTA per tile) and the split ones' fall-back pass
+  // (k_batch_jag_rest) take `jag`; all others go to k_batch, in two
+  // persistent launches: the split jobs' parents with a share of the plain
+  // conversions first (plain[0, n_first)), the split jobs' pools (which the
+  // parents' checks decide) with the rest second.  Each launch numbers its
+  // own tiles.
   std::vector<BatchJob> plain, jag;
   std::vector<std::pair<int, size_t>> where;  // jobs[i] -> (0: plain / 1: jag, index)
-  std::vector<unsigned long long> first_tile;  // plain jobs
+  std::vector<unsigned long long> first_tile;  // plain jobs, in their launch's numbering
   std::vector<unsigned int> tile_job;          // jagged tile -> index in jag
   unsigned long long total_tiles = 0, jag_tiles = 0;
+  size_t n_first = 0;                    // plain jobs of the first k_batch launch
+  unsigned long long first_tiles = 0;    // its tiles (the second has total_tiles - first_tiles)
   BatchJob* d_jobs = nullptr;
   unsigned long long* d_first = nullptr;
+  unsigned long long* d_first2 = nullptr;  // the second launch's part of d_first (16-byte aligned)
   BatchJob* d_jag = nullptr;
   unsigned int* d_tile_job = nullptr;
-  // counters (k_batch at 0, k_batch_jag at 64, k_jag_scan at 192), the
-  // word "some split jagged job's pool is not canonical" at 128, one
-  // look-back word per fused jagged tile from 256, one per scan chunk of
-  // the split jagged jobs, one "pool not canonical" word per jagged job
-  // (d_flags); these are cleared before each launch (clear_bytes).  Then
-  // the split jobs' group bases, which the scan overwrites.
+  // counters (k_batch's two launches at 0 and 192, k_batch_jag at 64),
+  // the word "some split jagged job's pool is not canonical" at 128, one
+  // look-back word per fused jagged tile from 256, then one per fall-back
+  // tile of the split jobs, one "pool not canonical" word per jagged job
+  // (d_flags) and one fall-back ticket counter per jagged job; all cleared
+  // before each launch (clear_bytes).
   char* d_scratch = nullptr;
   size_t scratch_bytes = 0, clear_bytes = 0;
   unsigned int* d_flags = nullptr;
-  // split jagged jobs: the scan's chunks (chunk -> index in jag), and the
-  // most fall-back tiles of one of them
-  std::vector<unsigned int> chunk_job;
-  unsigned int* d_chunk_job = nullptr;
-  unsigned long long total_chunks = 0, max_rest_tiles = 0;
+  // split jagged jobs: how many, and the most fall-back tiles of one
+  unsigned long long max_rest_tiles = 0;
   size_t n_split = 0;
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
@@ -70,7 +74,6 @@ struct mrn_batch {
     cudaFree(d_first);
     cudaFree(d_jag);
     cudaFree(d_tile_job);
-    cudaFree(d_chunk_job);
     cudaFree(d_scratch);
   }
   void drop_timed() {
@@ -167,14 +170,13 @@ int plan_job(const mrn_view& src, const mrn_view& dst, std::vector<BatchJob>* ou
       j.kind = JOB_JAG_A2S;
       // an empty collection still has one tile: it writes offsets[0]
       j.ntiles = std::max<uint64_t>(1, (jagged_tile_records(j.jp) + MRN_JAG_TILE - 1) / MRN_JAG_TILE);
-      // Split: the scan (this job's chunks in k_jag_scan), the parents'
-      // data columns and offsets, and the pool (skipped unless canonical)
-      // as jobs of k_batch, and this job's tiles as the fall-back pass.
+      // Split (JAG_LOCAL): the parents' data columns and offsets (with the
+      // pool's check) and the pool (skipped unless canonical) as jobs of
+      // k_batch, and this job's tiles, fused, as the fall-back pass.
       BatchJob kids;
       std::memset(&kids, 0, sizeof(kids));
-      if (jagged_split_ok(src.schema, &j.jp, &kids.jp.parent)) {
-        j.jp.mode = JAG_SPLIT;
-        j.jp.nchunks = (src.n_records + MRN_SCAN_CHUNK - 1) / MRN_SCAN_CHUNK;
+      if (jagged_split_ok(src.schema, &j.jp, &kids.jp.parent) && jagged_local_ok(j.jp)) {
+        j.jp.mode = JAG_LOCAL;
         j.jp.ntiles = j.ntiles;  // the fall-back pass's tiles
         out->push_back(j);
         BatchJob par;
@@ -212,6 +214,13 @@ int plan_job(const mrn_view& src, const mrn_view& dst, std::vector<BatchJob>* ou
 }
 
 // Approximate bytes read and written by one tile of a job of k_batch.
+// The first persistent launch's share of the jobs other than split jobs'
+// parents and pools, relative to the parents' share of parents and pools
+// (1: as in the whole batch).  Measured on the 4,096-collection mixed
+// batch: 0 (the parents alone) 14.215 ms for both launches, 1 14.183, 2
+// 14.186.
+constexpr double kFirstPlainShare = 1.0;
+
 double tile_traffic(const BatchJob& j) {
   switch (j.kind) {
     case JOB_CONVERT:
@@ -239,18 +248,25 @@ int rebuild_tables(mrn_batch* b) {
   b->tile_job.clear();
   unsigned long long t = 0, tj = 0;
   b->n_split = 0;
-  b->chunk_job.clear();
-  b->total_chunks = b->max_rest_tiles = 0;
+  b->max_rest_tiles = 0;
+  // The first persistent launch: the split jobs' parents and, so that its
+  // tiles are not all of one kind, a share of the other plain jobs (in
+  // proportion to the parents' part of the work outside the pools).
+  double parents_bytes = 0, pool_bytes = 0, other_bytes = 0;
+  for (const BatchJob& j : b->jobs) {
+    if (j.kind == JOB_JAG_A2S) continue;
+    const double by = (double)j.ntiles * tile_traffic(j);
+    (j.kind == JOB_JAG_PARENTS ? parents_bytes : j.cond == ~0u ? pool_bytes : other_bytes) += by;
+  }
+  const double first_share =
+      parents_bytes > 0 ? kFirstPlainShare * parents_bytes / (parents_bytes + pool_bytes) : 0.0;
+  double acc_first = 0, acc_all = 0;
   for (BatchJob& j : b->jobs) {
     // 1 + the last jagged job (a split job's parents and pool follow it)
     if (j.cond == ~0u) j.cond = (uint32_t)b->jag.size();
     if (j.jag_link == ~0u) j.jag_link = (uint32_t)b->jag.size();
-    if (j.kind == JOB_JAG_A2S && j.jp.mode == JAG_SPLIT) {
+    if (j.kind == JOB_JAG_A2S && j.jp.mode == JAG_LOCAL) {
       ++b->n_split;
-      j.jp.chunk_begin = b->total_chunks;
-      if (b->total_chunks + j.jp.nchunks > 0x7fffffffull) return MRN_EUNSUPPORTED;
-      b->chunk_job.insert(b->chunk_job.end(), j.jp.nchunks, (unsigned int)b->jag.size());
-      b->total_chunks += j.jp.nchunks;
       b->max_rest_tiles = std::max<unsigned long long>(b->max_rest_tiles, j.ntiles);
       b->where.push_back({1, b->jag.size()});
       b->jag.push_back(j);
@@ -261,6 +277,14 @@ int rebuild_tables(mrn_batch* b) {
       b->tile_job.insert(b->tile_job.end(), j.ntiles, (unsigned int)b->jag.size());
       b->jag.push_back(j);
       tj += j.ntiles;
+    } else if (j.kind != JOB_JAG_PARENTS && (j.cond || [&] {
+                 const double by = (double)j.ntiles * tile_traffic(j);
+                 acc_all += by;
+                 if (acc_first + by > first_share * acc_all) return true;
+                 acc_first += by;
+                 return false;
+               }())) {
+      b->where.push_back({0, ~size_t(0)});  // the second launch
     } else {
       j.tile_begin = t;
       b->where.push_back({0, b->plain.size()});
@@ -268,6 +292,24 @@ int rebuild_tables(mrn_batch* b) {
       b->plain.push_back(j);
       t += j.ntiles;
     }
+  }
+  // The split jobs' pools and most other jobs form the second launch, in
+  // their own numbering: each pool is decided by its parents job's checks,
+  // all made in the first.  (Inside one launch a pool would have to wait
+  // for its parents' last tiles, and the wait, even where it never blocks,
+  // costs the loader warp of every tile about 2%; a second launch of the
+  // pools alone, narrow records only, ran 0.11 ms slower than pools mixed
+  // with the other jobs.)
+  b->n_first = b->plain.size();
+  b->first_tiles = t;
+  for (size_t k = 0; k < b->jobs.size(); ++k) {
+    if (b->where[k].first || b->where[k].second != ~size_t(0)) continue;
+    BatchJob& j = b->jobs[k];
+    j.tile_begin = t - b->first_tiles;
+    b->where[k].second = b->plain.size();
+    b->first_tile.push_back(t - b->first_tiles);
+    b->plain.push_back(j);
+    t += j.ntiles;
   }
   b->total_tiles = t;
   b->jag_tiles = tj;
@@ -283,84 +325,91 @@ int upload(mrn_batch* b) {
   const size_t jb = std::max<size_t>(1, b->plain.size()) * sizeof(BatchJob);
   const size_t gb = std::max<size_t>(1, b->jag.size()) * sizeof(BatchJob);
   // the tile index is read by whole 16-byte pieces (L2 prefetch)
-  const size_t fb = align_up(std::max<size_t>(1, b->first_tile.size()) * sizeof(unsigned long long), 16);
+  // each launch's part of the index starts on 16 bytes and is padded to
+  // them: k_batch prefetches it into L2 with bulk copies
+  const size_t fb1 = align_up(std::max<size_t>(1, b->n_first) * sizeof(unsigned long long), 16);
+  const size_t fb = fb1 + align_up(std::max<size_t>(1, b->first_tile.size() - b->n_first) * sizeof(unsigned long long), 16);
   const size_t tb = std::max<size_t>(1, b->tile_job.size()) * sizeof(unsigned int);
-  const size_t cb = std::max<size_t>(1, b->chunk_job.size()) * sizeof(unsigned int);
-  const size_t chunks_at = 256 + (size_t)b->jag_tiles * sizeof(unsigned long long);
-  const size_t flags_at = chunks_at + (size_t)b->total_chunks * sizeof(unsigned long long);
-  b->clear_bytes = flags_at + std::max<size_t>(1, b->jag.size()) * sizeof(unsigned int);
-  const size_t groups_at = align_up(b->clear_bytes, 256);
-  size_t ngroups = 0;
+  size_t local_tiles = 0;  // the fall-back pass's look-back words of split jobs
   for (const BatchJob& j : b->jag)
-    if (j.jp.mode == JAG_SPLIT) ngroups += (size_t)(j.jp.parent.n + 31) / 32;
-  b->scratch_bytes = groups_at + ngroups * sizeof(unsigned long long);
+    if (j.jp.mode == JAG_LOCAL) local_tiles += (size_t)j.ntiles;
+  const size_t local_at = 256 + (size_t)b->jag_tiles * sizeof(unsigned long long);
+  const size_t flags_at = local_at + local_tiles * sizeof(unsigned long long);
+  // per jagged job: its pool word, then its fall-back tickets
+  const size_t njag = std::max<size_t>(1, b->jag.size());
+  b->clear_bytes = flags_at + 2 * njag * sizeof(unsigned int);
+  b->scratch_bytes = b->clear_bytes;
   if (cudaMalloc(&b->d_jobs, jb) != cudaSuccess || cudaMalloc(&b->d_first, fb) != cudaSuccess ||
       cudaMalloc(&b->d_jag, gb) != cudaSuccess || cudaMalloc(&b->d_tile_job, tb) != cudaSuccess ||
-      cudaMalloc(&b->d_chunk_job, cb) != cudaSuccess || cudaMalloc(&b->d_scratch, b->scratch_bytes) != cudaSuccess) {
+      cudaMalloc(&b->d_scratch, b->scratch_bytes) != cudaSuccess) {
     cudaGetLastError();
     return MRN_ENOMEM;
   }
+  b->d_first2 = b->d_first + fb1 / sizeof(unsigned long long);
   b->d_flags = reinterpret_cast<unsigned int*>(b->d_scratch + flags_at);
-  // split jagged jobs: their pool word, chunk words and group bases in the
-  // scratch; their parents jobs write the offsets from the same bases
-  unsigned long long* chunks = reinterpret_cast<unsigned long long*>(b->d_scratch + chunks_at);
-  unsigned long long* groups = reinterpret_cast<unsigned long long*>(b->d_scratch + groups_at);
-  size_t g = 0;
+  unsigned int* tickets = b->d_flags + njag;
+  // split jagged jobs: their pool word, fall-back look-back words and
+  // tickets in the scratch; their parents jobs set the same pool word
+  unsigned long long* lstates = reinterpret_cast<unsigned long long*>(b->d_scratch + local_at);
+  size_t ls = 0;
   for (size_t k = 0; k < b->jobs.size(); ++k) {
     BatchJob& j = b->jobs[k];
-    if (j.kind != JOB_JAG_A2S || j.jp.mode != JAG_SPLIT) continue;
-    j.jp.noncanon = b->d_flags + b->where[k].second;
+    if (j.kind != JOB_JAG_A2S || j.jp.mode != JAG_LOCAL) continue;
+    const size_t q = b->where[k].second;
+    j.jp.noncanon = b->d_flags + q;
     j.jp.any_noncanon = reinterpret_cast<unsigned int*>(b->d_scratch + 128);
-    j.jp.chunk_state = chunks + j.jp.chunk_begin;
-    j.jp.group_base = groups + g;
-    g += (size_t)(j.jp.parent.n + 31) / 32;
-    b->jag[b->where[k].second] = j;
+    j.jp.tile_state = lstates + ls;
+    j.jp.tile_counter = tickets + q;
+    ls += (size_t)j.ntiles;
+    b->jag[q] = j;
   }
   for (size_t k = 0; k < b->jobs.size(); ++k) {
     BatchJob& j = b->jobs[k];
     if (j.kind != JOB_JAG_PARENTS) continue;
-    j.jp.group_base = b->jag[j.jag_link - 1].jp.group_base;
+    const JagPlan& owner = b->jag[j.jag_link - 1].jp;
+    j.jp.noncanon = owner.noncanon;
+    j.jp.any_noncanon = owner.any_noncanon;
     b->plain[b->where[k].second] = j;
   }
   auto put = [](void* d, const void* h, size_t n) {
     return n == 0 || cudaMemcpy(d, h, n, cudaMemcpyHostToDevice) == cudaSuccess;
   };
   if (!put(b->d_jobs, b->plain.data(), b->plain.size() * sizeof(BatchJob)) ||
-      !put(b->d_first, b->first_tile.data(), b->first_tile.size() * sizeof(unsigned long long)) ||
+      !put(b->d_first, b->first_tile.data(), b->n_first * sizeof(unsigned long long)) ||
+      !put(b->d_first2, b->first_tile.data() + b->n_first,
+           (b->first_tile.size() - b->n_first) * sizeof(unsigned long long)) ||
       !put(b->d_jag, b->jag.data(), b->jag.size() * sizeof(BatchJob)) ||
-      !put(b->d_tile_job, b->tile_job.data(), b->tile_job.size() * sizeof(unsigned int)) ||
-      !put(b->d_chunk_job, b->chunk_job.data(), b->chunk_job.size() * sizeof(unsigned int)))
+      !put(b->d_tile_job, b->tile_job.data(), b->tile_job.size() * sizeof(unsigned int)))
     return MRN_ECUDA;
   return MRN_OK;
 }
 
-// The batch's work on `s`: scratch reset, the scan of the split jagged AoS
-// jobs (k_jag_scan) and the launch of the fused ones (k_batch_jag), the
-// persistent launch of all other jobs (k_batch: plain conversions, the
-// split jobs' parents and pools), and the split jobs' fall-back pass
-// (k_batch_jag_rest).  With `ev`, ev[0] is recorded first, ev[1] before
-// k_batch and ev[2] last (`evflags` as for cudaEventRecordWithFlags;
-// cudaEventRecordExternal makes them graph nodes during capture).
+// The batch's work on `s`: scratch reset, the fused jagged AoS jobs
+// (k_batch_jag), the first persistent launch (k_batch: plain conversions
+// and the split jobs' parents, which check their pools), the second (the
+// split jobs' pools, each skipped unless its check passed), and the split
+// jobs' fall-back pass (k_batch_jag_rest).  With `ev`, ev[0] is recorded
+// first, ev[1] before the first k_batch launch and ev[2] last (`evflags`
+// as for cudaEventRecordWithFlags; cudaEventRecordExternal makes them
+// graph nodes during capture).
 int enqueue(mrn_batch* b, cudaStream_t s, const cudaEvent_t* ev = nullptr, unsigned evflags = 0) {
   auto mark = [&](int i) { return !ev || cudaEventRecordWithFlags(ev[i], s, evflags) == cudaSuccess; };
   if (!mark(0)) return MRN_ECUDA;
   int rc = MRN_OK;
-  if (b->total_tiles || b->jag_tiles || b->total_chunks) {
+  if (b->total_tiles || b->jag_tiles) {
     if (cudaMemsetAsync(b->d_scratch, 0, b->clear_bytes, s) != cudaSuccess) return MRN_ECUDA;
   }
-  // the scan of the split jagged jobs and the fused jagged tiles first: the
-  // split jobs' parents and pools (jobs of k_batch) need the scan's bases
-  // and pool checks
-  if (b->total_chunks)
-    rc = launch_jag_scan(b->d_jag, b->d_chunk_job, b->total_chunks,
-                         reinterpret_cast<unsigned int*>(b->d_scratch + 192), s);
-  if (!rc && b->jag_tiles)
+  if (b->jag_tiles)
     rc = launch_batch_jag(b->d_jag, b->d_tile_job, b->jag_tiles, reinterpret_cast<unsigned int*>(b->d_scratch + 64),
                           reinterpret_cast<unsigned long long*>(b->d_scratch + 256), s);
   if (!rc && !mark(1)) rc = MRN_ECUDA;
-  if (!rc && b->total_tiles)
-    rc = launch_batch(b->d_jobs, b->d_first, (unsigned)b->plain.size(), b->total_tiles,
-                      reinterpret_cast<unsigned int*>(b->d_scratch), b->ctas_per_sm, b->max_chunk, s, b->d_flags);
+  if (!rc && b->first_tiles)
+    rc = launch_batch(b->d_jobs, b->d_first, (unsigned)b->n_first, b->first_tiles,
+                      reinterpret_cast<unsigned int*>(b->d_scratch), b->ctas_per_sm, b->max_chunk, s, nullptr);
+  if (!rc && b->total_tiles > b->first_tiles)
+    rc = launch_batch(b->d_jobs + b->n_first, b->d_first2, (unsigned)(b->plain.size() - b->n_first),
+                      b->total_tiles - b->first_tiles, reinterpret_cast<unsigned int*>(b->d_scratch + 192),
+                      b->ctas_per_sm, b->max_chunk, s, b->d_flags);
   if (!rc && b->n_split)
     rc = launch_batch_jag_rest(b->d_jag, (unsigned)b->jag.size(), b->max_rest_tiles, b->d_flags,
                                reinterpret_cast<unsigned int*>(b->d_scratch + 128), s);
@@ -542,9 +591,8 @@ int mrn_batch_update(mrn_batch* b, size_t j, const mrn_view* src, const mrn_view
     if (fresh[i].kind == JOB_JAG_A2S || fresh[i].kind == JOB_JAG_PARENTS) {
       fresh[i].jp.noncanon = old.jp.noncanon;
       fresh[i].jp.any_noncanon = old.jp.any_noncanon;
-      fresh[i].jp.chunk_state = old.jp.chunk_state;
-      fresh[i].jp.group_base = old.jp.group_base;
-      fresh[i].jp.chunk_begin = old.jp.chunk_begin;
+      fresh[i].jp.tile_state = old.jp.tile_state;
+      fresh[i].jp.tile_counter = old.jp.tile_counter;
     }
   }
   for (int q = 0; q < 4; ++q) b->cols[4 * j + q] = std::move(c[q]);

@@ -350,6 +350,12 @@ __device__ __forceinline__ unsigned int ld_relaxed_u32(const unsigned int* p) {
   return v;
 }
 
+__device__ __forceinline__ uint32_t ld_acquire_u32(const unsigned int* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -407,8 +413,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint3
 }
 
 // Prefetch of a global range into L2 (bulk copy engine; address 16-byte
-// aligned, size a multiple of 16).
+// aligned, size a multiple of 16: a range that is not is left out, a
+// prefetch being only a hint).
 __device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  if (((reinterpret_cast<uintptr_t>(src) | bytes) & 15u) != 0 || bytes == 0) return;
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 

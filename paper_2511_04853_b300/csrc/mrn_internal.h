@@ -180,6 +180,10 @@ int jagged_pool_plan(const mrn_schema* s, const JagPlan& jp, ConvPlan* out);
 // conversion can be staged); fills *pool and gives jp->parent its staged
 // tiles where it can have them.
 bool jagged_split_ok(const mrn_schema* s, JagPlan* jp, ConvPlan* pool);
+// A batch job may run split (JAG_LOCAL: offsets from the begins, the pool
+// checked locally): its largest offset, offset_base + pool_n, fits the
+// offset type.
+bool jagged_local_ok(const JagPlan& jp);
 int launch_jagged_count(const ConvPlan& parent, uint64_t* dev_total, void* stream);
 // Parents' {length, begin} columns from a field-major side's offsets.
 int launch_len_begin(const char* offsets, uint32_t off_size, uint64_t n, unsigned int* len,
@@ -221,14 +225,10 @@ int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, uns
 int launch_batch_jag(const BatchJob* jobs, const unsigned int* tile_job, unsigned long long total,
                      unsigned int* counter, unsigned long long* states, void* stream);
 // The fall-back pass of the batch's split jagged jobs (flags[j] != 0: job j
-// of `jobs` gathers its own children; nothing runs unless *any != 0);
-// max_tiles: the most fall-back tiles of one job.
+// of `jobs` is converted whole again, fused; nothing runs unless *any !=
+// 0); max_tiles: the most fused tiles of one job.
 int launch_batch_jag_rest(const BatchJob* jobs, unsigned int njobs, unsigned long long max_tiles,
                           const unsigned int* flags, const unsigned int* any, void* stream);
-// The split scan of the batch's split jagged jobs (chunk_job[c] = the job
-// of chunk c, dynamic chunk ids from *counter).
-int launch_jag_scan(const BatchJob* jobs, const unsigned int* chunk_job, unsigned long long total,
-                    unsigned int* counter, void* stream);
 int batch_occupancy();
 
 // Cached launch shape for a plan (autotuner), or the default.

@@ -85,17 +85,21 @@ __device__ __forceinline__ void tma_transform(const TileHdr& h, uint32_t desc, c
 // Entry k of the staged-transform descriptor table: the k-th column in
 // size-class order (see tile_convert); with `wide`, the order with the
 // fields widened over an AoS destination's padding last.  Word 3 is the
-// widened store's log2 size, or (a plan with an interleaved array) the
-// column's field-major element stride.
+// widened store's log2 size, or (Inter: a plan with an interleaved array)
+// the column's field-major element stride.  Inter is a template argument:
+// as a run-time choice in the loader's stage-table fill it cost single
+// points SoA -> AoS 3% and AoSoA(32) -> AoS 5%.
+template <bool Inter>
 __host__ __device__ __forceinline__ uint4 tile_desc(const ConvPlan& p, uint32_t k, bool wide = false) {
   const bool w = wide && p.dst.kind == K_AOS && p.tg.nwide;
   const uint32_t c = w ? p.tg.worder[k] : p.tg.order[k];
   const uint32_t col = p.tg.col[c], aos_off = col & 0xffffffu;
   return make_uint4((col >> 24) & 3u, p.src.kind == K_AOS ? aos_off : p.tg.src_off[c],
                     p.dst.kind == K_AOS ? aos_off : p.tg.dst_off[c],
-                    p.tg.inter ? (uint32_t)p.fm_es[c] : (col >> 28) & 3u);
+                    Inter ? (uint32_t)p.fm_es[c] : (col >> 28) & 3u);
 }
 
+template <bool Inter>
 __host__ __device__ __forceinline__ TileHdr tile_hdr(const ConvPlan& p, bool wide = false) {
   const bool w = wide && p.dst.kind == K_AOS && p.tg.nwide;
   TileHdr h;
@@ -108,9 +112,11 @@ __host__ __device__ __forceinline__ TileHdr tile_hdr(const ConvPlan& p, bool wid
   h.nwide = w ? p.tg.nwide : 0u;
   h.packed = 0;
   const uint32_t n4 = (p.tg.nsize >> 8) & 0xff;
-  // (not for interleaved plans: their SoA tiles hold rows, not columns)
+  // (not for interleaved plans, whose SoA tiles hold rows, not columns:
+  // only the Inter instances meet them)
+  const bool rows = Inter && p.tg.inter;
   const bool pair =
-      !p.tg.inter && ((p.src.kind == K_AOS && p.dst.kind == K_SOA) || (p.src.kind == K_SOA && p.dst.kind == K_AOS));
+      !rows && ((p.src.kind == K_AOS && p.dst.kind == K_SOA) || (p.src.kind == K_SOA && p.dst.kind == K_AOS));
   if (pair && p.tg.nsize == (n4 << 8) && (n4 == 1 || n4 == 2 || n4 == 4) && p.ncols == n4 && p.stride == 4 * n4) {
     bool in_order = true;
     for (uint32_t k = 0; k < n4; ++k) in_order = in_order && (p.tg.col[p.tg.order[k]] & 0xffffffu) == 4 * k;
@@ -769,10 +775,13 @@ __global__ void __launch_bounds__(MRN_JAG_THREADS, MRN_JAG_CTAS) k_batch_jag(con
   jagged_a2s_tile<0, 0>(*reinterpret_cast<const JagPlan*>(jps), t - tb, states + tb, tw_all, sh, sw);
 }
 
-// Fall-back pass of a batch's split jagged jobs: nothing to do unless the
-// scan pass (k_batch_jag) found some job's pool not canonical (*any);
-// then every CTA walks the jobs, 32 flags at a time, and takes its share of
-// each flagged job's tiles (plan mode JAG_CHILDREN in the shared copy).
+// Fall-back pass of a batch's split jagged jobs (JAG_LOCAL): nothing to do
+// unless a parents job's local check found its pool not canonical (*any);
+// then every CTA walks the jobs, 32 flags at a time, and converts each
+// flagged job whole again (plan mode JAG_FUSED in the shared copy: the
+// parents job wrote the begins as offsets, which the fused tiles write
+// again, with the children gathered), tiles taken by ticket in increasing
+// order for the look-back.
 __global__ void __launch_bounds__(MRN_JAG_THREADS, MRN_JAG_CTAS) k_batch_jag_rest(const BatchJob* __restrict__ jobs,
                                                                       unsigned int njobs,
                                                                       const unsigned int* flags,
@@ -783,7 +792,7 @@ __global__ void __launch_bounds__(MRN_JAG_THREADS, MRN_JAG_CTAS) k_batch_jag_res
   uint32_t* tw_all = reinterpret_cast<uint32_t*>(jag_raw);
   JagShared& sh = *reinterpret_cast<JagShared*>(jag_raw);
   __shared__ JagWarp sw;
-  __shared__ unsigned int s_mask;
+  __shared__ unsigned int s_mask, s_tile;
   __shared__ __align__(16) unsigned long long jps[(sizeof(JagPlan) + 7) / 8];
   JagPlan& jp = *reinterpret_cast<JagPlan*>(jps);
   for (unsigned int j0 = 0; j0 < njobs; j0 += 32) {
@@ -800,16 +809,20 @@ __global__ void __launch_bounds__(MRN_JAG_THREADS, MRN_JAG_CTAS) k_batch_jag_res
       mask &= mask - 1u;
       const BatchJob& J = jobs[j];
       const uint64_t nt = J.ntiles;
-      if (blockIdx.x >= nt) continue;
       const unsigned long long* g = reinterpret_cast<const unsigned long long*>(&J.jp);
       for (uint32_t i = threadIdx.x; i < sizeof(JagPlan) / 8; i += blockDim.x) jps[i] = __ldg(g + i);
       __syncthreads();
-      if (threadIdx.x == 0) jp.mode = JAG_CHILDREN;
+      if (threadIdx.x == 0) jp.mode = JAG_FUSED;
       __syncthreads();
-      for (uint64_t t = blockIdx.x; t < nt; t += gridDim.x) {
-        jagged_a2s_tile<0, 0>(jp, t, nullptr, tw_all, sh, sw);
-        __syncthreads();  // the next tile's windows (or plan) overlay this tile's state
+      for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(jp.tile_counter, 1u);
+        __syncthreads();
+        const uint64_t t = s_tile;
+        if (t >= nt) break;
+        jagged_a2s_tile<0, 0>(jp, t, jp.tile_state, tw_all, sh, sw);
+        __syncthreads();  // the next ticket (and tile) overlay this tile's state
       }
+      __syncthreads();  // s_tile and the plan are written again for the next job
     }
   }
 }
@@ -1139,23 +1152,6 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_jag_scan_one(const __grid_c
   jag_scan_chunk(jp, s_chunk, jp.chunk_state, sh);
 }
 
-// The split scan of a batch's jagged jobs: the chunks of all of them in one
-// numbering (chunk_job[c] = the job of chunk c), handed out in increasing
-// order; a chunk's look-back visits only its own job's earlier chunks.
-__global__ void __launch_bounds__(kScanThreads, 6) k_jag_scan(const BatchJob* __restrict__ jobs,
-                                                           const unsigned int* __restrict__ chunk_job,
-                                                           unsigned long long total, unsigned int* counter) {
-  __shared__ ScanShared sh;
-  __shared__ unsigned int s_chunk;
-  if (threadIdx.x == 0) s_chunk = atomicAdd(counter, 1u);
-  __syncthreads();
-  const uint64_t c = s_chunk;
-  if (c >= total) return;
-  const JagPlan& jp = jobs[__ldg(chunk_job + c)].jp;
-  const uint64_t cb = jp.chunk_begin;
-  jag_scan_chunk(jp, c - cb, jp.chunk_state, sh);
-}
-
 // Offsets of the parents of a split jagged job, group by group (32
 // parents, starting at a multiple of 32): offset_base + the group's base +
 // the exclusive prefix of the lengths inside the group.  From staged tile
@@ -1193,6 +1189,70 @@ __device__ __forceinline__ void jag_offsets_direct(const JagPlan& jp, uint64_t r
     const unsigned long long gbase = __ldg(jp.group_base + q / 32);
     if (r < r1) write_offset(jp.offsets, jp.off_size, r, jp.offset_base + gbase + x - len);
   }
+}
+
+// Parents of a JAG_LOCAL job (see JagPlan): offsets = offset_base + the
+// begins, offsets[n] = offset_base + pool_n, and the local checks of the
+// pool (begin[0] = 0, begin[r] + length[r] = begin[r + 1], the last parent's
+// end = pool_n); a warp whose check failed sets the job's pool word (the
+// pool launch skips the pool, the fall-back pass redoes the job).
+__device__ __forceinline__ void jag_local_flag(const JagPlan& jp, bool bad, int lane) {
+  if (__any_sync(0xffffffffu, bad) && lane == 0) {
+    atomicExch(jp.noncanon, 1u);
+    atomicExch(jp.any_noncanon, 1u);
+  }
+}
+
+// From staged tile `local` of R records (`stage`: its AoS records; consumer
+// warp w takes groups w, w + 8, w + 16): a lane's successor is the next
+// lane's record, the group's last lane's the next group's first record (in
+// the tile, else in global memory, else the pool's end).
+__device__ __forceinline__ void jag_local_staged(const JagPlan& jp, uint64_t local, uint32_t R, const char* stage,
+                                                 const TileHdr& h, int lane, int warp) {
+  const ConvPlan& P = jp.parent;
+  const uint64_t r0 = local * h.T, n = P.n;
+  bool bad = false;
+#pragma unroll 1
+  for (int k = 0; k < kJagTileGroups; ++k) {
+    const uint32_t q = (uint32_t)(warp + 8 * k) * 32;
+    if (q >= R) break;
+    const char* rec = stage + (size_t)(q + lane) * h.stride;
+    const uint32_t len = *reinterpret_cast<const unsigned int*>(rec + jp.len_off);
+    const unsigned long long beg = *reinterpret_cast<const unsigned long long*>(rec + jp.begin_off);
+    unsigned long long next = __shfl_down_sync(0xffffffffu, beg, 1);
+    const uint64_t r = r0 + q + lane;
+    if (lane == 31) {
+      if (q + 32 < R)
+        next = *reinterpret_cast<const unsigned long long*>(stage + (size_t)(q + 32) * h.stride + jp.begin_off);
+      else if (r + 1 < n)
+        next = ld_u64_rec(P.src.base + (r + 1) * P.stride + jp.begin_off, P.vec);
+      else
+        next = jp.pool_n;
+    }
+    bad |= beg + len != next || (r == 0 && beg != 0);
+    write_offset(jp.offsets, jp.off_size, r, jp.offset_base + beg);
+    if (r + 1 == n) write_offset(jp.offsets, jp.off_size, n, jp.offset_base + jp.pool_n);
+  }
+  jag_local_flag(jp, bad, lane);
+}
+
+// The same for records [r0, r1) of a direct tile (from global memory).
+__device__ __forceinline__ void jag_local_direct(const JagPlan& jp, uint64_t r0, uint64_t r1, int lane, int warp,
+                                                 int nwarps) {
+  const ConvPlan& P = jp.parent;
+  const uint64_t n = P.n;
+  if (r1 > n) r1 = n;
+  bool bad = false;
+  for (uint64_t r = r0 + (uint64_t)warp * 32 + lane; r < r1; r += (uint64_t)nwarps * 32) {
+    const char* rec = P.src.base + r * P.stride;
+    const uint32_t len = ld_u32_rec(rec + jp.len_off, P.vec);
+    const unsigned long long beg = ld_u64_rec(rec + jp.begin_off, P.vec);
+    const unsigned long long next = r + 1 < n ? ld_u64_rec(rec + P.stride + jp.begin_off, P.vec) : jp.pool_n;
+    bad |= beg + len != next || (r == 0 && beg != 0);
+    write_offset(jp.offsets, jp.off_size, r, jp.offset_base + beg);
+    if (r + 1 == n) write_offset(jp.offsets, jp.off_size, n, jp.offset_base + jp.pool_n);
+  }
+  jag_local_flag(jp, bad, lane);
 }
 
 // One warp group of a jagged SoA -> AoS conversion: groups [0,
@@ -1412,11 +1472,12 @@ __device__ __forceinline__ void tma_store_tile_warp(const ConvPlan& p, uint64_t 
 // Loader warp, one conversion per launch: the plan's column descriptors and
 // header into stage s's table (lane c writes column c), padding absorbed in
 // widened field stores where the plan has them.
+template <bool Inter>
 __device__ __forceinline__ void fill_stage_desc(const ConvPlan& p, const BatchSmem& m, uint32_t s, int lane,
                                                 bool wide) {
   StageDesc* sd = m.desc(s);
-  for (uint32_t c = lane; c < p.ncols; c += 32) sd->d[c] = tile_desc(p, c, wide);
-  if (lane == 0) sd->h = tile_hdr(p, wide);
+  for (uint32_t c = lane; c < p.ncols; c += 32) sd->d[c] = tile_desc<Inter>(p, c, wide);
+  if (lane == 0) sd->h = tile_hdr<Inter>(p, wide);
 }
 
 static_assert(sizeof(BatchJob) % 16 == 0, "a job descriptor is one whole L2 prefetch");
@@ -1521,10 +1582,19 @@ __device__ __forceinline__ void tma_load_tile_cached(const LoadCache& c, uint64_
   }
 }
 
+// The loader's decision for a tile of the cached job: skipped (a pool that
+// is not canonical), or staged with its records, or direct.
+__device__ __forceinline__ void decide_tile(const LoadCache& lc, TileSlot* cand) {
+  if (lc.skip)
+    cand->local = kSkipTile;
+  else if (lc.staged_job)
+    cand->staged = cand->local < lc.nfull ? lc.T : (cand->local == lc.nfull ? lc.rs : 0u);
+}
+
 // Loader warp: decides tiles in order (lane 0 decides, the warp follows)
 // and issues the loads of staged ones; returns after publishing the
 // end-of-work slot, or on abort once its loads in flight have landed.
-template <bool kStatic, bool kWide>
+template <bool kStatic, bool kWide, bool kInter>
 __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
                                              const unsigned long long* __restrict__ first_tile,
                                              unsigned int njobs, unsigned long long total_tiles,
@@ -1590,10 +1660,7 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
         cand.job = cursor;
         cand.local = cand.t - lc.tile_begin;
         cand.jag = lc.jag_parents ? 1u : 0u;
-        if (lc.skip)
-          cand.local = kSkipTile;
-        else if (lc.staged_job)
-          cand.staged = cand.local < lc.nfull ? lc.T : (cand.local == lc.nfull ? lc.rs : 0u);
+        decide_tile(lc, &cand);
       }
       have = true;
     }
@@ -1621,7 +1688,7 @@ __device__ __forceinline__ void batch_loader(const BatchJob* __restrict__ jobs,
         const StageRec* rec = nullptr;
         if (m.sjob()[s] != cand.job) {
           if constexpr (kStatic)
-            fill_stage_desc(P, m, s, lane, kWide);
+            fill_stage_desc<kInter>(P, m, s, lane, kWide);
           else
             rec = &jobs[cand.job].stage;
           __syncwarp();
@@ -1713,11 +1780,14 @@ __device__ __forceinline__ void batch_storer(const BatchJob* __restrict__ jobs, 
   bulk_wait_all();
 }
 
-// kJag: the instance meets parents jobs of split jagged conversions (their
-// offsets epilogue is compiled in; where it cannot occur, leaving it out
-// keeps the transform's register allocation: single points AoS -> SoA at
-// 2^26 records 0.718 ms with it, 0.672 without).
-template <bool kStatic, bool kWide, bool kJag, bool kInter>
+// kJag: the parents jobs of split jagged conversions the instance meets,
+// whose offsets epilogue it compiles in: 1 those of JAG_SPLIT (single
+// conversions: offsets from the scan's group bases), 2 those of JAG_LOCAL
+// (batches: offsets from the begins, and the pool's check), 0 none.  Where
+// an epilogue cannot occur, leaving it out keeps the transform's register
+// allocation (single points AoS -> SoA at 2^26 records 0.718 ms with the
+// first, 0.672 without; the batch 0.6% slower with both than with its one).
+template <bool kStatic, bool kWide, int kJag, bool kInter>
 __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
                                            const unsigned long long* __restrict__ first_tile, unsigned int njobs,
                                            unsigned long long total_tiles, unsigned int* counter,
@@ -1764,7 +1834,7 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
   }
   __syncthreads();
   if (warp == 8) {
-    batch_loader<kStatic, kWide>(jobs, first_tile, njobs, total_tiles, counter, chunk, first_start, first_size, m,
+    batch_loader<kStatic, kWide, kInter>(jobs, first_tile, njobs, total_tiles, counter, chunk, first_start, first_size, m,
                                  lane, conds);
     return;
   }
@@ -1794,8 +1864,9 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
       const StageDesc* sd = m.desc(s);
       tma_transform<kWide, kStatic, kInter>(sd->h, smem_u32(sd->d), m.src(s), m.dst(d), ts.staged, lane, warp);
       // parents of a split jagged job: the offsets, from the staged lengths
-      // (before the source stage is released)
-      if (kJag && ts.jag) jag_offsets_staged(jobs[ts.job].jp, ts.local, ts.staged, m.src(s), sd->h, lane, warp);
+      // (or, with the local check, begins) before the source stage is released
+      if (kJag == 1 && ts.jag) jag_offsets_staged(jobs[ts.job].jp, ts.local, ts.staged, m.src(s), sd->h, lane, warp);
+      if (kJag == 2 && ts.jag) jag_local_staged(jobs[ts.job].jp, ts.local, ts.staged, m.src(s), sd->h, lane, warp);
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
@@ -1819,7 +1890,8 @@ __device__ __forceinline__ void batch_main(const BatchJob* __restrict__ jobs,
           r1 = r0 + J.tile_records;
         }
         conv_range<0, kBWin>(P, r0, r1, tw, lane, warp, 8);
-        if (kJag && J.kind == JOB_JAG_PARENTS) jag_offsets_direct(J.jp, r0, r1, lane, warp, 8);
+        if (kJag == 1 && J.kind == JOB_JAG_PARENTS) jag_offsets_direct(J.jp, r0, r1, lane, warp, 8);
+        if (kJag == 2 && J.kind == JOB_JAG_PARENTS) jag_local_direct(J.jp, r0, r1, lane, warp, 8);
       } else if (J.kind == JOB_JAG_S2A) {
         jagged_s2a_group<0, 0, kBWin>(J.jp, local * 8 + warp, J.parent_groups, tw, lane);
       } else {
@@ -1842,7 +1914,7 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
                                                         unsigned int* counter, uint32_t chunk,
                                                         const unsigned int* conds) {
   extern __shared__ __align__(128) char batch_smem[];
-  batch_main<false, false, true, false>(jobs, first_tile, njobs, total_tiles, counter, chunk, batch_smem, conds);
+  batch_main<false, false, 2, false>(jobs, first_tile, njobs, total_tiles, counter, chunk, batch_smem, conds);
 }
 
 // One staged conversion through the same warp-specialized pipeline: the
@@ -1861,7 +1933,7 @@ __global__ void __launch_bounds__(kBThreads, 3) k_convert_ws(const __grid_consta
                                                              const unsigned int* cond) {
   if (cond && ld_relaxed_u32(cond) != 0) return;
   extern __shared__ __align__(128) char batch_smem[];
-  batch_main<true, kWide, kJag, kInter>(&job, nullptr, 1u, job.ntiles, counter, chunk, batch_smem, nullptr);
+  batch_main<true, kWide, kJag ? 1 : 0, kInter>(&job, nullptr, 1u, job.ntiles, counter, chunk, batch_smem, nullptr);
 }
 
 // ================================================================== host
@@ -2146,9 +2218,9 @@ int launch_zero_gaps(const GapPlan& g, void* stream) {
 
 void fill_stage_rec(const ConvPlan& p, StageRec* out) {
   std::memset(out, 0, sizeof(*out));
-  out->h = tile_hdr(p);
+  out->h = tile_hdr<false>(p);  // batches stage no plan with an interleaved array
   for (uint32_t c = 0; c < p.ncols; ++c) {
-    const uint4 d = tile_desc(p, c);
+    const uint4 d = tile_desc<false>(p, c);
     out->d[c][0] = d.x;
     out->d[c][1] = d.y;
     out->d[c][2] = d.z;
@@ -2356,14 +2428,6 @@ int launch_batch_jag_rest(const BatchJob* jobs, unsigned int njobs, unsigned lon
   return cuda_status(cudaGetLastError());
 }
 
-int launch_jag_scan(const BatchJob* jobs, const unsigned int* chunk_job, unsigned long long total,
-                    unsigned int* counter, void* stream) {
-  if (total == 0) return MRN_OK;
-  k_jag_scan<<<(unsigned)total, kScanThreads, 0, static_cast<cudaStream_t>(stream)>>>(jobs, chunk_job, total,
-                                                                                    counter);
-  return cuda_status(cudaGetLastError());
-}
-
 int launch_batch(const BatchJob* jobs, const unsigned long long* first_tile, unsigned int njobs,
                  unsigned long long total_tiles, unsigned int* counter,
                  unsigned int ctas_per_sm, unsigned int max_chunk, void* stream, const unsigned int* conds) {
@@ -2420,12 +2484,6 @@ struct MovePlan {
   unsigned int* flags;    // per chunk: 1 once its source has been read
   unsigned long long timeout_ns;
 };
-
-__device__ __forceinline__ uint32_t ld_acquire_u32(const unsigned int* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
 
 __device__ __forceinline__ void st_release_u32(unsigned int* p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");

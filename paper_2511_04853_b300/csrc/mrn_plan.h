@@ -157,6 +157,18 @@ struct JagPlan {
   //    -> child row j);
   //  - otherwise the fall-back pass gathers the children (tiles in mode
   //    JAG_CHILDREN, their bases read from the finished offsets).
+  // or, in batches, split by a local check (JAG_LOCAL), with no scan: a
+  // pool is canonical exactly when begin[0] = 0, begin[i] + length[i] =
+  // begin[i+1] and begin[n-1] + length[n-1] = pool_n, each a comparison of
+  // neighbours, and its offsets are then offset_base + the begins:
+  //  - the parents job (JOB_JAG_PARENTS, in the batch's first persistent
+  //    launch) writes those offsets and makes the checks; a failed one
+  //    sets *noncanon and *any_noncanon;
+  //  - the pool job runs in the second persistent launch, skipped when
+  //    *noncanon;
+  //  - otherwise the fall-back pass runs the whole job fused (look-back
+  //    words tile_state, tiles ticketed from *tile_counter), rewriting the
+  //    parents, offsets and children.
   uint32_t mode;
   uint32_t begin_off;               // byte offset of the begin in a parent record
   unsigned int* noncanon;
@@ -189,6 +201,7 @@ struct ColScan {
 #define JAG_FUSED 0u
 #define JAG_SPLIT 1u
 #define JAG_CHILDREN 2u
+#define JAG_LOCAL 3u
 #define MRN_SCAN_CHUNK 8192u  // parents per chunk of the split scan (256 groups of 32)
 
 // Zero-fill of the alignment holes of a destination: for each of `nblocks`

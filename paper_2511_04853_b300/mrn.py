@@ -427,8 +427,9 @@ class Batch:
 
     def launch_timed(self, ev_begin, ev_mid, ev_end, stream=None):
         """``mrn_batch_launch_timed``: the events (torch.cuda.Event with
-        timing) are recorded before the batch, between its two kernels and
-        after them."""
+        timing) are recorded before the batch, after the scratch reset and
+        the fused jagged launch, and after the persistent launches and the
+        fall-back pass."""
         evs = []
         for e in (ev_begin, ev_mid, ev_end):
             if not e.cuda_event:  # torch creates an event at its first record

@@ -122,9 +122,11 @@ def test_autotune_then_convert_still_exact():
 
 @pytest.fixture(params=["split", "fused"])
 def jagged_path(request):
-    """Batches split their jagged AoS jobs by default (scan tiles, pool
-    conversions as jobs of the persistent kernel, a fall-back pass); debug
-    key 4 < 0 keeps them fused."""
+    """Batches split their jagged AoS jobs by default: the parents (whose
+    job also checks, record by record, that the pool is canonical) in the
+    first persistent launch, the pool in the second (skipped unless
+    canonical), and a fall-back pass that converts the jobs whose pools
+    are not canonical whole again; debug key 4 < 0 keeps them fused."""
     if request.param == "fused":
         mrn.debug_set(4, -1)
     yield request.param
@@ -165,14 +167,17 @@ def test_jagged_jobs_shuffled_pools_many_tiles(jagged_path):
 
 
 def test_batch_lookback_wait_is_bounded(jagged_path):
-    """Host-side fault injection: jagged tile 1 of a batched job (the split
-    scan's chunk 1) never publishes its sum, so the later look-backs must
-    expire (1 ms bound) and report MRN_ETIMEOUT; batches built afterwards
-    run normally."""
-    n = 4 * 8192  # at least four tiles / scan chunks, at up to 8,192 parents each
+    """Host-side fault injection: jagged tile 1 of a batched job never
+    publishes its sum, so the later look-backs must expire (1 ms bound) and
+    report MRN_ETIMEOUT; batches built afterwards run normally.  A split
+    job's look-back is its fall-back pass's, so its pool is shuffled (not
+    canonical) to make that pass run."""
+    n = 4 * 8192  # at least four tiles of up to 1,024 parents
     s, o = mrn.Schema(datagen.TRACKS), oracle.Schema(datagen.TRACKS)
     d = datagen.workload("tracks", n, 3)
     o_aos = oracle.pack(o, d, "aos")
+    if jagged_path == "split":
+        o_aos = oracle.shuffle_pool(o, o_aos, np.random.default_rng(2).permutation(n), gap=0)
     src = mrn.View(s, "aos", n, base=dev(o_aos.base), child_pool=dev(o_aos.pool), m=d["m"])
     try:
         mrn.debug_set(2, 1_000_000)
@@ -391,3 +396,55 @@ def test_narrow_records_in_a_batch():
     assert mrn.sync() == mrn.OK
     for k, (dst, want) in enumerate(checks):
         assert np.array_equal(host(dst.tensors[0], want.size), want), "job %d" % k
+
+
+@pytest.mark.parametrize("case", ["canonical", "swapped_runs", "extra_records", "shuffled", "late_break"])
+def test_batch_pool_checks(case, jagged_path):
+    """A batched jagged job's pool is converted as one plain conversion
+    only when canonical: swapped runs, records beyond the children, a
+    shuffled pool and a break in the last parents tile take the fall-back
+    pass.  Offsets and child rows equal the oracle's, child rows past the
+    written count (capacity above the pool) keep their bytes, and a plain
+    job beside it is exact."""
+    n = 9 * 1024 + 333
+    s, o = mrn.Schema(datagen.TRACKS), oracle.Schema(datagen.TRACKS)
+    d = datagen.workload("tracks", n, 71)
+    o_aos = oracle.pack(o, d, "aos")
+    m, lens = d["m"], d["lengths"]
+    if case in ("swapped_runs", "late_break"):
+        order = np.arange(n)
+        lo, hi = (2048, 3072) if case == "swapped_runs" else (n - 40, n)
+        nz = [i for i in range(lo, hi) if lens[i] > 0]
+        order[nz[1]], order[nz[2]] = nz[2], nz[1]
+        o_aos = oracle.shuffle_pool(o, o_aos, order, gap=0)
+    elif case == "extra_records":
+        pool = np.concatenate([o_aos.pool[: m * 8], np.full(50 * 8, 7, np.uint8)])
+        o_aos = oracle.Side("aos", n, m + 50, base=o_aos.base, pool=pool)
+    elif case == "shuffled":
+        o_aos = oracle.shuffle_pool(o, o_aos, np.random.default_rng(5).permutation(n), gap=0)
+    cap = o_aos.m + 100
+    o_soa = oracle.convert(o, o_aos, "soa", m=m)
+    cols = [garbage(n * 4) for _ in range(3)]
+    offs = garbage((n + 1) * 4)
+    kids = [garbage(cap * 4) for _ in range(2)]
+    dst = mrn.View(s, "soa", n, columns=cols, offsets=offs, child_columns=kids, m=cap)
+    src = mrn.View(s, "aos", n, base=dev(o_aos.base), child_pool=dev(o_aos.pool), m=o_aos.m)
+    c_s, c_o = mrn.Schema(datagen.CELLS), oracle.Schema(datagen.CELLS)
+    cd = datagen.workload("cells", 7000, 72)
+    c_src = oracle.pack(c_o, cd, "aos")
+    c_dst = dev_dest(c_s, "soa", 7000)
+    b = mrn.Batch([(src, dst), (mrn.View(c_s, "aos", 7000, base=dev(c_src.base)), c_dst)], use_graph=True)
+    for _ in range(2):
+        for t in cols + [offs] + kids:
+            t.fill_(0xA5)
+        b.launch()
+        assert mrn.sync() == mrn.OK
+        for c in range(3):
+            assert np.array_equal(host(cols[c]), oracle.region(o, o_soa, c))
+        assert np.array_equal(host(offs), oracle.region(o, o_soa, 3))
+        for c in range(2):
+            got = host(kids[c])
+            assert np.array_equal(got[: m * 4], oracle.region(o, o_soa, 4 + c)), "child column %d" % c
+            assert (got[m * 4:] == 0xA5).all(), "child rows past the count were written"
+        want = oracle.convert(c_o, c_src, "soa").base
+        assert np.array_equal(host(c_dst.tensors[0], want.size), want)
