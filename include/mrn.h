@@ -323,20 +323,26 @@ int mrn_jagged_count(const mrn_view* src, uint64_t* m, void* stream);
  *   key 3: 1 = single conversions use the direct kernel (vector loads and
  *          stores per lane) even where the TMA-staged kernel applies;
  *   key 4: parents from which a single jagged AoS -> SoA / AoSoA conversion
- *          runs split (default: never, the fused kernel is faster for one
- *          collection at every size measured): a scan of the lengths in chunks
- *          (offsets' bases, and a check that the pool is canonical: its
- *          records are exactly the children, in parent order), the parents
- *          as one staged conversion that also writes the offsets, the pool
- *          as one staged conversion of the child schema when it is
- *          canonical, and a pass that gathers the children when it is not.
+ *          runs split (default: never, the fused kernel is as fast or faster
+ *          for one collection at every size measured): the parents as one
+ *          staged conversion that writes their begins as offsets and checks
+ *          that the pool is canonical (its records exactly the children, in
+ *          parent order: each begin the previous begin plus its length), the
+ *          pool as one staged conversion of the child schema when it is, and
+ *          otherwise the whole conversion again with the fused kernel.
  *          Batches split every jagged AoS job whose pool fits the
  *          destination's child capacity and whose offsets fit their type,
  *          in their own form (see mrn_batch_create).  A negative value
  *          turns split runs off (single conversions and batches);
  *   key 5: parents up to which a single fused jagged AoS -> SoA / AoSoA
  *          conversion uses tiles of 256 parents instead of 1,024 (default
- *          250,000; -1: never). */
+ *          250,000; -1: never);
+ *   key 6: 1 = split single conversions take the scan form instead: a scan
+ *          of the lengths in chunks of 8,192 parents (offsets' bases and the
+ *          pool's check) before the parents and the pool, and a pass that
+ *          gathers the children when the pool is not canonical (the form
+ *          also taken where offset_base + the pool's size overflows the
+ *          offset type). */
 int mrn_debug_set(int key, long long value);
 
 /* ------------------------------------------------------- transfer+convert */

@@ -28,6 +28,9 @@ std::atomic<long long> g_split_parents{LLONG_MAX};
 // Parents up to which a single fused jagged AoS -> field-major conversion
 // takes tiles of MRN_JAG_SMALL_TILE parents (more CTAs for few parents).
 std::atomic<long long> g_small_tile_parents{250000};
+// 1: split single conversions take the scan form (JAG_SPLIT) even where the
+// local check (JAG_LOCAL) applies.
+std::atomic<int> g_split_scan{0};
 
 namespace {
 
@@ -623,7 +626,8 @@ int mrn_convert(const mrn_view* src, const mrn_view* dst, void* stream) {
                   : jagged_scratch_bytes(jagged_tile_records(jp), small ? MRN_JAG_SMALL_TILE : MRN_JAG_TILE);
         if (scratch_alloc(&scratch, sb, st) != MRN_OK) return MRN_ENOMEM;
       }
-      rc = split ? launch_jagged_a2s_split(jp, pool, scratch, stream) : launch_jagged_a2s(jp, scratch, stream, small);
+      rc = split ? launch_jagged_a2s_split(jp, pool, scratch, stream, !g_split_scan.load() && jagged_local_ok(jp))
+                 : launch_jagged_a2s(jp, scratch, stream, small);
       scratch_free(scratch, st);
       if (rc) return rc;
       if (fold) return MRN_OK;
@@ -766,6 +770,7 @@ int mrn_debug_set(int key, long long value) {
     case 3: g_force_direct.store(value ? 1 : 0); return MRN_OK;
     case 4: g_split_parents.store(value < 0 ? -1 : value); return MRN_OK;
     case 5: g_small_tile_parents.store(value); return MRN_OK;
+    case 6: g_split_scan.store(value ? 1 : 0); return MRN_OK;
     default: return MRN_EINVAL;
   }
 }

@@ -159,10 +159,13 @@ int launch_jagged_a2s(JagPlan& jp, void* scratch, void* stream, bool small = fal
 // offsets as one staged conversion, the pool's records as one staged
 // conversion `pool` of the child schema into the child rows when it is
 // canonical, and a pass in which the tiles gather their children when it is
-// not.  jp.parent and `pool` must be staged; n > 0; `scratch` holds
-// jagged_split_scratch_bytes(n) bytes.
+// not.  With `local` (jagged_local_ok holds), the local form instead
+// (JAG_LOCAL): no scan, the parents' begins written as offsets with the
+// pool's checks, the pool conversion when they passed, and otherwise the
+// whole conversion again, fused.  jp.parent and `pool` must be staged;
+// n > 0; `scratch` holds jagged_split_scratch_bytes(n) bytes.
 uint64_t jagged_split_scratch_bytes(uint64_t n, size_t* group_at = nullptr);
-int launch_jagged_a2s_split(JagPlan& jp, const ConvPlan& pool, void* scratch, void* stream);
+int launch_jagged_a2s_split(JagPlan& jp, const ConvPlan& pool, void* scratch, void* stream, bool local);
 int launch_jagged_s2a(const JagPlan& jp, void* stream);
 // The column scan (ColScan) of one jagged level: `scratch` holds
 // col_scan_scratch_bytes(cs.n) bytes (counter, pool word at +128, chunk

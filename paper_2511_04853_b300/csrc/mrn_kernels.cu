@@ -742,6 +742,33 @@ __global__ void __launch_bounds__(MRN_JAG_THREADS, MRN_JAG_CTAS) k_jagged_a2s_re
   }
 }
 
+// Fall-back pass of a split single conversion in the local form (plan mode
+// JAG_FUSED here, the parents' checks done): block 0 first zeroes the
+// destination's gap bytes, which the staged jobs leave; nothing else unless
+// the checks found the pool not canonical, and then the whole conversion
+// again, fused, tiles taken by ticket in increasing order (look-back over
+// tile_state).
+__global__ void __launch_bounds__(MRN_JAG_THREADS, MRN_JAG_CTAS) k_jagged_a2s_whole_if(const __grid_constant__ JagPlan jp) {
+  if (blockIdx.x == 0)
+    for (uint32_t k = 0; k < jp.ngaps; ++k)
+      for (uint32_t b = threadIdx.x; b < jp.gap_len[k]; b += blockDim.x) jp.gap_base[jp.gap_off[k] + b] = 0;
+  if (ld_relaxed_u32(jp.noncanon) == 0) return;
+  constexpr size_t kTw = MRN_JAG_WARPS * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t);
+  __shared__ __align__(16) unsigned char jag_raw[kTw > sizeof(JagShared) ? kTw : sizeof(JagShared)];
+  uint32_t* tw_all = reinterpret_cast<uint32_t*>(jag_raw);
+  JagShared& sh = *reinterpret_cast<JagShared*>(jag_raw);
+  __shared__ JagWarp sw;
+  __shared__ unsigned int s_tile;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(jp.tile_counter, 1u);
+    __syncthreads();
+    const uint64_t t = s_tile;
+    if (t >= jp.ntiles) break;
+    jagged_a2s_tile<0, 0>(jp, t, jp.tile_state, tw_all, sh, sw);
+    __syncthreads();  // the next ticket (and tile) overlay this tile's state
+  }
+}
+
 // The jagged AoS -> field-major jobs of a batch: one CTA per tile as in
 // k_jagged_a2s, 3 CTAs (48 warps) per SM, tiles taken in increasing order
 // over all the jobs,
@@ -1925,15 +1952,16 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batch(const BatchJob* __restri
 // plan stores fields wider over an AoS destination's padding.
 // With `cond`, the launch does nothing when *cond != 0 (the child pool of a
 // split jagged conversion that the scan found not canonical).  kJag: the
-// instance for the parents job of a split jagged conversion.  kInter: the
+// instance for the parents job of a split jagged conversion (1: the scan
+// form's, JAG_SPLIT; 2: the local check's, JAG_LOCAL).  kInter: the
 // instance for plans with an interleaved array.
-template <bool kWide, bool kJag, bool kInter>
+template <bool kWide, int kJag, bool kInter>
 __global__ void __launch_bounds__(kBThreads, 3) k_convert_ws(const __grid_constant__ BatchJob job,
                                                              uint32_t chunk, unsigned int* counter,
                                                              const unsigned int* cond) {
   if (cond && ld_relaxed_u32(cond) != 0) return;
   extern __shared__ __align__(128) char batch_smem[];
-  batch_main<true, kWide, kJag ? 1 : 0, kInter>(&job, nullptr, 1u, job.ntiles, counter, chunk, batch_smem, nullptr);
+  batch_main<true, kWide, kJag, kInter>(&job, nullptr, 1u, job.ntiles, counter, chunk, batch_smem, nullptr);
 }
 
 // ================================================================== host
@@ -2144,11 +2172,13 @@ int launch_staged_job(BatchJob& job, void* stream, const LaunchShape& sh, const 
     job.ntiles = staged_tile_count(p.n, nrec, p.tg.T, p.tg.G);
     // the instance with the widened-field transform only for plans that
     // have widened fields: the branch costs the others a few percent
-    const void* fn = job.kind == JOB_JAG_PARENTS ? reinterpret_cast<const void*>(&k_convert_ws<false, true, false>)
-                     : p.tg.inter ? reinterpret_cast<const void*>(&k_convert_ws<false, false, true>)
-                     : p.dst.kind == K_AOS && p.tg.nwide
-                         ? reinterpret_cast<const void*>(&k_convert_ws<true, false, false>)
-                         : reinterpret_cast<const void*>(&k_convert_ws<false, false, false>);
+    const void* fn =
+        job.kind == JOB_JAG_PARENTS
+            ? (job.jp.mode == JAG_LOCAL ? reinterpret_cast<const void*>(&k_convert_ws<false, 2, false>)
+                                        : reinterpret_cast<const void*>(&k_convert_ws<false, 1, false>))
+        : p.tg.inter ? reinterpret_cast<const void*>(&k_convert_ws<false, 0, true>)
+        : p.dst.kind == K_AOS && p.tg.nwide ? reinterpret_cast<const void*>(&k_convert_ws<true, 0, false>)
+                                            : reinterpret_cast<const void*>(&k_convert_ws<false, 0, false>);
     allow_batch_smem(fn);
     const int occ = occupancy(fn, kBThreads, kBatchSmem);
     const int per_sm = sh.ctas_per_sm ? std::min((int)sh.ctas_per_sm, occ) : occ;
@@ -2308,13 +2338,41 @@ uint64_t jagged_split_scratch_bytes(uint64_t n, size_t* group_at) {
   return at + (n + 31) / 32 * sizeof(unsigned long long);
 }
 
-int launch_jagged_a2s_split(JagPlan& jp, const ConvPlan& pool, void* scratch, void* stream) {
+int launch_jagged_a2s_split(JagPlan& jp, const ConvPlan& pool, void* scratch, void* stream, bool local) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const uint64_t n = jp.parent.n;
   if (n == 0 || !pool.tg.tma || !jp.parent.tg.tma) return MRN_EINVAL;
   jp.nchunks = (n + MRN_SCAN_CHUNK - 1) / MRN_SCAN_CHUNK;
   jp.ntiles = (jagged_tile_records(jp) + MRN_JAG_TILE - 1) / MRN_JAG_TILE;  // tiles of the fall-back pass
   if (jp.nchunks > 0x7fffffffull || jp.ntiles > 0x7fffffffull) return MRN_EUNSUPPORTED;
+  if (local) {
+    // The local form (see JagPlan, JAG_LOCAL): no scan.  Scratch: the
+    // fall-back's ticket at 0, the pool word at 128 (and its copy at 192),
+    // the fall-back's look-back words from 256.
+    char* sc = static_cast<char*>(scratch);
+    jp.mode = JAG_LOCAL;
+    jp.noncanon = reinterpret_cast<unsigned int*>(sc + 128);
+    jp.any_noncanon = reinterpret_cast<unsigned int*>(sc + 192);
+    cudaError_t e = cudaMemsetAsync(sc, 0, 256 + jp.ntiles * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_status(e);
+    // 1. the parents' data columns, their begins as offsets and the checks
+    BatchJob job;
+    std::memset(&job, 0, sizeof(job));
+    job.kind = JOB_JAG_PARENTS;
+    job.jp = jp;
+    int rc = launch_staged_job(job, stream, LaunchShape{}, nullptr);
+    if (rc) return rc;
+    // 2. a canonical pool: its records -> the child rows, one staged conversion
+    if ((rc = launch_convert(pool, stream, nullptr, jp.noncanon))) return rc;
+    // 3. the gaps, and otherwise the whole conversion again, fused
+    jp.mode = JAG_FUSED;
+    jp.tile_counter = reinterpret_cast<unsigned int*>(sc);
+    jp.tile_state = reinterpret_cast<unsigned long long*>(sc + 256);
+    const int per_sm = occupancy(reinterpret_cast<const void*>(&k_jagged_a2s_whole_if), MRN_JAG_THREADS, 0);
+    const uint64_t grid = std::min<uint64_t>(jp.ntiles, (uint64_t)device_sm_count() * (uint64_t)per_sm);
+    k_jagged_a2s_whole_if<<<(unsigned)std::max<uint64_t>(1, grid), MRN_JAG_THREADS, 0, s>>>(jp);
+    return cuda_status(cudaGetLastError());
+  }
   size_t group_at = 0;
   jagged_split_scratch_bytes(n, &group_at);
   char* sc = static_cast<char*>(scratch);

@@ -17,18 +17,22 @@ SPLIT_DEFAULT = 2**63 - 1  # parents from which single conversions run split (de
 SMALL_DEFAULT = 250000  # parents up to which fused conversions take 256-parent tiles (debug key 5)
 
 
-@pytest.fixture(autouse=True, params=["fused", "fused_big", "split"])
+@pytest.fixture(autouse=True, params=["fused", "fused_big", "split", "split_scan"])
 def jagged_path(request):
-    """Every test of this module runs three times: with jagged AoS ->
+    """Every test of this module runs four times: with jagged AoS ->
     field-major conversions fused (the tiles gather their own children) in
     tiles of 256 parents (the default up to 250,000 parents) and of 1,024,
-    and split (scan, parents, pool conversion when the pool is canonical,
-    fall-back pass)."""
-    mrn.debug_set(4, 0 if request.param == "split" else -1)
+    and split in the local form (parents with their begins as offsets and
+    the pool's checks, pool conversion when canonical, otherwise the whole
+    conversion again fused) and in the scan form (debug key 6: scan,
+    parents, pool conversion when canonical, gathering pass)."""
+    mrn.debug_set(4, 0 if request.param.startswith("split") else -1)
     mrn.debug_set(5, -1 if request.param == "fused_big" else SMALL_DEFAULT)
+    mrn.debug_set(6, 1 if request.param == "split_scan" else 0)
     yield request.param
     mrn.debug_set(4, SPLIT_DEFAULT)
     mrn.debug_set(5, SMALL_DEFAULT)
+    mrn.debug_set(6, 0)
 
 
 def tracks(n, seed=2, **kw):
@@ -241,14 +245,18 @@ def test_decreasing_offsets_reported():
     assert mrn.sync() == mrn.EINVAL
 
 
-def test_lookback_wait_is_bounded():
+def test_lookback_wait_is_bounded(jagged_path):
     """Fault injection on the host side: tile 1 (the split scan's chunk 1)
     never publishes its sum, so the look-back waits of the later ones must
     expire (1 ms bound) and report MRN_ETIMEOUT; the context stays usable
-    afterwards."""
+    afterwards.  The local split form looks back only in its fused
+    fall-back pass, so there the pool is shuffled (not canonical) to make
+    that pass run."""
     n = 4 * 8192  # at least four tiles / scan chunks, at up to 8,192 parents each
     s, o, d = tracks(n, seed=3)
     o_aos = oracle.pack(o, d, "aos")
+    if jagged_path == "split":
+        o_aos = oracle.shuffle_pool(o, o_aos, np.random.default_rng(4).permutation(n), gap=0)
     try:
         mrn.debug_set(2, 1_000_000)
         mrn.debug_set(1, 1)
@@ -377,12 +385,13 @@ def test_large_soa_to_aos_parents_as_a_plain_conversion(n, osz, raw):
 
 @pytest.mark.parametrize("case", ["canonical", "swapped_runs", "extra_records", "shuffled"])
 def test_split_pool_checks(case, jagged_path):
-    """The scan pass decides whether the pool can be converted as one plain
-    conversion (pool record j -> child row j): only for a canonical pool that
-    holds no other records.  Swapped runs, records beyond the children and a
-    shuffled pool must take the gathering pass; either way the offsets and
-    child rows equal the oracle's, and child rows past the written count
-    (capacity above the pool) keep their bytes."""
+    """A split run's check (the scan's, or the parents' local one) decides
+    whether the pool can be converted as one plain conversion (pool record
+    j -> child row j): only for a canonical pool that holds no other
+    records.  Swapped runs, records beyond the children and a shuffled pool
+    must take the fall-back pass; either way the offsets and child rows
+    equal the oracle's, and child rows past the written count (capacity
+    above the pool) keep their bytes."""
     n = 5 * 1024 + 333
     s, o, d = tracks(n, seed=61)
     o_aos = oracle.pack(o, d, "aos")
