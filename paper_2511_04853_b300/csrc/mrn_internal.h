@@ -168,12 +168,16 @@ uint64_t jagged_split_scratch_bytes(uint64_t n, size_t* group_at = nullptr);
 int launch_jagged_a2s_split(JagPlan& jp, const ConvPlan& pool, void* scratch, void* stream, bool local);
 int launch_jagged_s2a(const JagPlan& jp, void* stream);
 // The column scan (ColScan) of one jagged level: `scratch` holds
-// col_scan_scratch_bytes(cs.n) bytes (counter, pool word at +128, chunk
-// words), cleared on `stream` first.  Sets cs.noncanon.  Then its gathering
-// form (returns at once for a canonical pool unless `force`): `P` converts
-// the pool's records into the level's columns, `capacity` rows there.
+// col_scan_scratch_bytes(cs.n) bytes (counter, pool word at +128, the local
+// form's word at +192, chunk words), cleared on `stream` first.  Sets
+// cs.noncanon.  With `local` (the largest offset, pool_n, fits the offset
+// type), the local form first (k_col_local: the begins as offsets and the
+// neighbours' checks), the scan then running only where a check failed.
+// Then its gathering form (returns at once for a canonical pool unless
+// `force`): `P` converts the pool's records into the level's columns,
+// `capacity` rows there.
 uint64_t col_scan_scratch_bytes(uint64_t n);
-int launch_col_scan(ColScan& cs, void* scratch, void* stream);
+int launch_col_scan(ColScan& cs, void* scratch, void* stream, bool local);
 int launch_col_gather(const ColScan& cs, const ConvPlan& P, uint64_t capacity, bool force, void* stream);
 // The child pool of a jagged AoS -> field-major plan as a plain conversion of
 // the child schema (pool record j -> child row j, j < pool_n), with tiles.

@@ -1118,6 +1118,7 @@ __device__ __forceinline__ void col_scan_chunk(const ColScan& cs, uint64_t n, ui
 // The grid covers cs.n entries; the count (read from device memory, where
 // the level above wrote it) may be smaller, and the chunks past it return.
 __global__ void __launch_bounds__(kScanThreads, 6) k_col_scan(const __grid_constant__ ColScan cs) {
+  if (cs.only_if && ld_relaxed_u32(cs.only_if) == 0) return;
   __shared__ ScanShared sh;
   __shared__ ColScanShared cx;
   __shared__ unsigned int s_chunk;
@@ -1134,6 +1135,28 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_col_scan(const __grid_const
   }
   if (c * MRN_SCAN_CHUNK >= n) return;
   col_scan_chunk(cs, n, c, sh, cx);
+}
+
+// The local form of a column-scanned level: a pool is canonical for the
+// entries exactly when beg[0] = 0, beg[h] + len[h] = beg[h + 1] and the last
+// entry's end is pool_n, and its offsets are then the begins.  Every entry
+// writes its begin as its offset (the last also offsets[count] = pool_n),
+// and a failed check sets *local_bad, on which the scan then runs and
+// writes the offsets and the pool word as usual.  The grid covers cs.n
+// entries, the count being read from device memory.
+__global__ void __launch_bounds__(256) k_col_local(const __grid_constant__ ColScan cs) {
+  const uint64_t n = cs.count ? min((uint64_t)ld_acquire_u64(cs.count), cs.n) : cs.n;
+  bool bad = false;
+  for (uint64_t h = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; h < n; h += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t len = __ldg(cs.len + h);
+    const unsigned long long beg = __ldg(cs.beg + h);
+    const unsigned long long next = h + 1 < n ? __ldg(cs.beg + h + 1) : cs.pool_n;
+    bad |= beg + len != next || (h == 0 && beg != 0);
+    write_offset(cs.offsets, cs.off_size, h, beg);
+    if (h + 1 == n) write_offset(cs.offsets, cs.off_size, n, cs.pool_n);
+  }
+  if (n == 0 && blockIdx.x == 0 && threadIdx.x == 0) bad = true;  // the scan's own empty case
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(cs.local_bad, 1u);
 }
 
 // The gathering form of a column-scanned level, for a pool that is not
@@ -2404,16 +2427,25 @@ int launch_jagged_a2s_split(JagPlan& jp, const ConvPlan& pool, void* scratch, vo
   return cuda_status(cudaGetLastError());
 }
 
-int launch_col_scan(ColScan& cs, void* scratch, void* stream) {
+int launch_col_scan(ColScan& cs, void* scratch, void* stream, bool local) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const uint64_t nchunks = std::max<uint64_t>(1, (cs.n + MRN_SCAN_CHUNK - 1) / MRN_SCAN_CHUNK);
   if (nchunks > 0x7fffffffull) return MRN_EUNSUPPORTED;
   char* sc = static_cast<char*>(scratch);
   cs.counter = reinterpret_cast<unsigned int*>(sc);
   cs.noncanon = reinterpret_cast<unsigned int*>(sc + 128);
+  cs.local_bad = reinterpret_cast<unsigned int*>(sc + 192);
+  cs.only_if = nullptr;
   cs.state = reinterpret_cast<unsigned long long*>(sc + 256);
   cudaError_t e = cudaMemsetAsync(sc, 0, col_scan_scratch_bytes(cs.n), s);
   if (e != cudaSuccess) return cuda_status(e);
+  if (local) {
+    const unsigned grid = (unsigned)std::max<uint64_t>(
+        1, std::min<uint64_t>((cs.n + 255) / 256, (uint64_t)device_sm_count() * 8));
+    k_col_local<<<grid, 256, 0, s>>>(cs);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    cs.only_if = cs.local_bad;
+  }
   k_col_scan<<<(unsigned)nchunks, kScanThreads, 0, s>>>(cs);
   return cuda_status(cudaGetLastError());
 }

@@ -10,8 +10,9 @@
 //     from their offsets;
 //   AoS -> field-major: the parents' tile scan gathers each child's data
 //     columns into the child level and its {length, begin} into two scratch
-//     columns; a scan of those columns writes the children's offsets and
-//     checks the grandchild pool, which is then converted as one staged
+//     columns; the children's offsets are their begins when the grandchild
+//     pool is canonical (checked child against child), else a scan of those
+//     columns writes them; the pool is then converted as one staged
 //     conversion when canonical and gathered child by child otherwise, all
 //     on the device (the children's count never returns to the host).
 #include <cuda_runtime.h>
@@ -125,12 +126,14 @@ int convert_nested(const mrn_view& src, const mrn_view& dst, void* stream) {
 
   // Level 1, without a return to the host: the children's count M stays in
   // device memory (a count above the capacity is recorded by level 0 as
-  // MRN_ESIZE, and level 1 then covers the capacity).  A scan of the two
-  // gathered columns writes the children's offsets and checks the
-  // grandchild pool; a canonical pool (the grandchildren exactly its
-  // records, in child order) is one staged conversion of the grandchild
-  // schema, and otherwise a gathering pass copies each child's
-  // grandchildren to its rows (both decide on the device).
+  // MRN_ESIZE, and level 1 then covers the capacity).  The children's
+  // offsets are their begins where the grandchild pool is canonical (the
+  // grandchildren exactly its records, in child order: each begin the
+  // previous begin plus its length), which a pass over the two gathered
+  // columns checks; where a check fails, a scan of the columns writes the
+  // offsets instead.  A canonical pool is then one staged conversion of
+  // the grandchild schema, and otherwise a gathering pass copies each
+  // child's grandchildren to its rows (all decided on the device).
   OwnedSchema desc;
   if (mrn_schema_create(&desc.s) ||
       mrn_schema_add_jagged(desc.s, "v", ch->off_size == 4 ? MRN_U32 : MRN_U64, ch->child.get()) ||
@@ -160,7 +163,8 @@ int convert_nested(const mrn_view& src, const mrn_view& dst, void* stream) {
   cs.off_size = ch->off_size;
   cs.timeout_ns = jp1.timeout_ns;
   cs.skip_publish_tile = jp1.skip_publish_tile;
-  if ((rc = launch_col_scan(cs, cscratch, stream))) return done(rc);
+  const bool local = cs.off_size == 8 || cs.pool_n <= 0xffffffffull;
+  if ((rc = launch_col_scan(cs, cscratch, stream, local))) return done(rc);
   if (staged_pool && (rc = launch_convert(pool, stream, nullptr, cs.noncanon))) return done(rc);
   if ((rc = launch_col_gather(cs, jp1.child, dst.n_grandchildren, !staged_pool, stream))) return done(rc);
   if ((rc = zero_dst_gaps(dst, stream))) return done(rc);

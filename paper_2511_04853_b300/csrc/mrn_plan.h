@@ -196,6 +196,11 @@ struct ColScan {
   unsigned int* noncanon;
   unsigned long long timeout_ns;
   long long skip_publish_tile;
+  // The local form (k_col_local before the scan): its word "some check
+  // failed", and the scan's condition (nullptr: the scan always runs; else
+  // only when *only_if != 0)
+  unsigned int* local_bad;
+  const unsigned int* only_if;
 };
 
 #define JAG_FUSED 0u
