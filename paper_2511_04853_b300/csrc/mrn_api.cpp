@@ -426,8 +426,7 @@ void tile_geometry(const mrn_schema* s, ConvPlan* p, uint32_t stage_bytes) {
     g.nsize |= cnt << (8 * (3 - lsz));
   }
   g.pad = used != s->stride;
-  // (descriptor word 3 of an interleaved plan is the element stride)
-  if (g.pad && p->dst.kind == K_AOS && !s->has_jagged && !g.inter) widen_into_padding(s, &g);
+  if (g.pad && p->dst.kind == K_AOS && !s->has_jagged) widen_into_padding(s, &g);
   g.tma = 1;
 }
 

@@ -593,9 +593,10 @@ __device__ __forceinline__ void tile_class(uint32_t desc, uint32_t c0, uint32_t 
 
 // The columns [c0, c1) of 2^L bytes of a plan with an interleaved array:
 // on a field-major side column c of slot i lies at its offset + i * es_c
-// (descriptor word 3; an interleaved array's row is es_c = E * 2^L bytes,
-// any other column's es_c = 2^L), on an AoS side at its offset (slot 0).
-// Two columns' loads of both records before their stores, as tile_class.
+// (the low 16 bits of descriptor word 3; an interleaved array's row is
+// es_c = E * 2^L bytes, any other column's es_c = 2^L), on an AoS side at
+// its offset (slot 0).  Two columns' loads of both records before their
+// stores, as tile_class.
 template <int L>
 __device__ __forceinline__ void tile_class_es(uint32_t desc, uint32_t c0, uint32_t c1, uint32_t sb0, uint32_t si0,
                                               uint32_t sb1, uint32_t si1, uint32_t db0, uint32_t di0, uint32_t db1,
@@ -603,26 +604,26 @@ __device__ __forceinline__ void tile_class_es(uint32_t desc, uint32_t c0, uint32
   uint32_t c = c0;
   for (; c + 1 < c1; c += 2) {
     const uint4 d0 = lds128(desc + c * 16), d1 = lds128(desc + c * 16 + 16);
-    const uint2 v00 = lds_l<L>(sb0 + d0.y + si0 * d0.w), v10 = lds_l<L>(sb0 + d1.y + si0 * d1.w);
+    const uint2 v00 = lds_l<L>(sb0 + d0.y + si0 * (d0.w & 0xffffu)), v10 = lds_l<L>(sb0 + d1.y + si0 * (d1.w & 0xffffu));
     uint2 v01 = v00, v11 = v10;
     if (two) {
-      v01 = lds_l<L>(sb1 + d0.y + si1 * d0.w);
-      v11 = lds_l<L>(sb1 + d1.y + si1 * d1.w);
+      v01 = lds_l<L>(sb1 + d0.y + si1 * (d0.w & 0xffffu));
+      v11 = lds_l<L>(sb1 + d1.y + si1 * (d1.w & 0xffffu));
     }
-    sts_l<L>(db0 + d0.z + di0 * d0.w, v00);
-    sts_l<L>(db0 + d1.z + di0 * d1.w, v10);
+    sts_l<L>(db0 + d0.z + di0 * (d0.w & 0xffffu), v00);
+    sts_l<L>(db0 + d1.z + di0 * (d1.w & 0xffffu), v10);
     if (two) {
-      sts_l<L>(db1 + d0.z + di1 * d0.w, v01);
-      sts_l<L>(db1 + d1.z + di1 * d1.w, v11);
+      sts_l<L>(db1 + d0.z + di1 * (d0.w & 0xffffu), v01);
+      sts_l<L>(db1 + d1.z + di1 * (d1.w & 0xffffu), v11);
     }
   }
   if (c < c1) {
     const uint4 d0 = lds128(desc + c * 16);
-    const uint2 v00 = lds_l<L>(sb0 + d0.y + si0 * d0.w);
+    const uint2 v00 = lds_l<L>(sb0 + d0.y + si0 * (d0.w & 0xffffu));
     uint2 v01 = v00;
-    if (two) v01 = lds_l<L>(sb1 + d0.y + si1 * d0.w);
-    sts_l<L>(db0 + d0.z + di0 * d0.w, v00);
-    if (two) sts_l<L>(db1 + d0.z + di1 * d0.w, v01);
+    if (two) v01 = lds_l<L>(sb1 + d0.y + si1 * (d0.w & 0xffffu));
+    sts_l<L>(db0 + d0.z + di0 * (d0.w & 0xffffu), v00);
+    if (two) sts_l<L>(db1 + d0.z + di1 * (d0.w & 0xffffu), v01);
   }
 }
 
@@ -654,6 +655,22 @@ __device__ __forceinline__ void tile_wide(uint32_t desc, uint32_t c0, uint32_t c
   }
 }
 
+// tile_wide for a plan with an interleaved array: the field-major source's
+// slot offset is slot * es_c (word 3's low 16 bits), the store width 2^w
+// (word 3's bits 16-17).
+__device__ __forceinline__ void tile_wide_es(uint32_t desc, uint32_t c0, uint32_t c1, uint32_t sb0, uint32_t si0,
+                                             uint32_t sb1, uint32_t si1, uint32_t db0, uint32_t db1, bool two) {
+  for (uint32_t c = c0; c < c1; ++c) {
+    const uint4 d = lds128(desc + c * 16);
+    const uint32_t es = d.w & 0xffffu, w = d.w >> 16;
+    const uint2 v0 = lds_any(sb0 + d.y + si0 * es, d.x);
+    uint2 v1 = v0;
+    if (two) v1 = lds_any(sb1 + d.y + si1 * es, d.x);
+    sts_wide(db0 + d.z, v0, w);
+    if (two) sts_wide(db1 + d.z, v1, w);
+  }
+}
+
 // Staged tile transform: each lane converts records r0 and r1 (= r0 + 256,
 // when `two`) of the tile.  Per column one shared load and one shared store
 // per record, addressed from the column descriptor table `desc` (uint4
@@ -667,7 +684,8 @@ __device__ __forceinline__ void tile_wide(uint32_t desc, uint32_t c0, uint32_t c
 // h.nwide descriptors are fields of an AoS destination stored wider than
 // they are, over the padding after them; such records are not zeroed first.
 // With Inter (a plan with an interleaved array), the slot's offset is slot
-// times descriptor word 3 instead (tile_class_es).
+// times descriptor word 3's low 16 bits instead (tile_class_es; widened
+// fields: tile_wide_es, the store width in bits 16-17).
 // An AoS <-> SoA tile whose AoS record is W (1, 2 or 4) 4-byte words, the
 // columns in order (h.packed): the record moves as one 4-, 8- or 16-byte
 // vector on the AoS side, and word k to or from its SoA column.  Narrow
@@ -758,14 +776,15 @@ __device__ __forceinline__ void tile_convert(const TileHdr& h, uint32_t desc, ui
   zero_record(h, db0);
   if (two) zero_record(h, db1);
   const uint32_t e8 = h.nsize & 0xff, e4 = e8 + ((h.nsize >> 8) & 0xff), e2 = e4 + ((h.nsize >> 16) & 0xff);
+  const uint32_t ew = Wide ? h.ncols - h.nwide : h.ncols;
   if constexpr (Inter) {
     tile_class_es<3>(desc, 0, e8, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
     tile_class_es<2>(desc, e8, e4, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
     tile_class_es<1>(desc, e4, e2, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
-    tile_class_es<0>(desc, e2, h.ncols, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
+    tile_class_es<0>(desc, e2, ew, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
+    if (Wide && ew < h.ncols) tile_wide_es(desc, ew, h.ncols, sb0, si0, sb1, si1, db0, db1, two);
     return;
   }
-  const uint32_t ew = Wide ? h.ncols - h.nwide : h.ncols;
   tile_class<3>(desc, 0, e8, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
   tile_class<2>(desc, e8, e4, sb0, si0, sb1, si1, db0, di0, db1, di1, two);
   tile_class<1>(desc, e4, e2, sb0, si0, sb1, si1, db0, di0, db1, di1, two);

@@ -86,7 +86,8 @@ __device__ __forceinline__ void tma_transform(const TileHdr& h, uint32_t desc, c
 // size-class order (see tile_convert); with `wide`, the order with the
 // fields widened over an AoS destination's padding last.  Word 3 is the
 // widened store's log2 size, or (Inter: a plan with an interleaved array)
-// the column's field-major element stride.  Inter is a template argument:
+// the column's field-major element stride with that log2 size in bits
+// 16-17.  Inter is a template argument:
 // as a run-time choice in the loader's stage-table fill it cost single
 // points SoA -> AoS 3% and AoSoA(32) -> AoS 5%.
 template <bool Inter>
@@ -96,7 +97,7 @@ __host__ __device__ __forceinline__ uint4 tile_desc(const ConvPlan& p, uint32_t 
   const uint32_t col = p.tg.col[c], aos_off = col & 0xffffffu;
   return make_uint4((col >> 24) & 3u, p.src.kind == K_AOS ? aos_off : p.tg.src_off[c],
                     p.dst.kind == K_AOS ? aos_off : p.tg.dst_off[c],
-                    Inter ? (uint32_t)p.fm_es[c] : (col >> 28) & 3u);
+                    Inter ? (uint32_t)p.fm_es[c] | (((col >> 28) & 3u) << 16) : (col >> 28) & 3u);
 }
 
 template <bool Inter>
@@ -2199,7 +2200,8 @@ int launch_staged_job(BatchJob& job, void* stream, const LaunchShape& sh, const 
         job.kind == JOB_JAG_PARENTS
             ? (job.jp.mode == JAG_LOCAL ? reinterpret_cast<const void*>(&k_convert_ws<false, 2, false>)
                                         : reinterpret_cast<const void*>(&k_convert_ws<false, 1, false>))
-        : p.tg.inter ? reinterpret_cast<const void*>(&k_convert_ws<false, 0, true>)
+        : p.tg.inter ? (p.dst.kind == K_AOS && p.tg.nwide ? reinterpret_cast<const void*>(&k_convert_ws<true, 0, true>)
+                                                          : reinterpret_cast<const void*>(&k_convert_ws<false, 0, true>))
         : p.dst.kind == K_AOS && p.tg.nwide ? reinterpret_cast<const void*>(&k_convert_ws<true, 0, false>)
                                             : reinterpret_cast<const void*>(&k_convert_ws<false, 0, false>);
     allow_batch_smem(fn);
