@@ -342,7 +342,13 @@ int mrn_jagged_count(const mrn_view* src, uint64_t* m, void* stream);
  *          pool's check) before the parents and the pool, and a pass that
  *          gathers the children when the pool is not canonical (the form
  *          also taken where offset_base + the pool's size overflows the
- *          offset type). */
+ *          offset type);
+ *   key 7: children from which a nested AoS -> field-major conversion runs
+ *          its parent level split in the local form (default 262,144; -1:
+ *          never): the parents with their begins as offsets and the child
+ *          pool's check, then the child pool as one staged conversion of the
+ *          child record (its {length, begin} included), and the fused
+ *          kernel again only for a pool that is not canonical. */
 int mrn_debug_set(int key, long long value);
 
 /* ------------------------------------------------------- transfer+convert */

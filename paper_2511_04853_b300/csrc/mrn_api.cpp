@@ -31,6 +31,10 @@ std::atomic<long long> g_small_tile_parents{250000};
 // 1: split single conversions take the scan form (JAG_SPLIT) even where the
 // local check (JAG_LOCAL) applies.
 std::atomic<int> g_split_scan{0};
+// Children from which a nested AoS -> field-major conversion runs its
+// parent level split in the local form (the child pool one staged
+// conversion of the child record's flat schema); negative: never.
+std::atomic<long long> g_nested_split_children{1 << 18};
 
 namespace {
 
@@ -469,6 +473,8 @@ bool jagged_split_ok(const mrn_schema* s, JagPlan* jp, ConvPlan* pool) {
   return true;
 }
 
+long long nested_split_children() { return g_nested_split_children.load(); }
+
 bool jagged_local_ok(const JagPlan& jp) {
   // the largest offset written, offset_base + pool_n, fits the offset type
   return jp.off_size == 8 || (jp.offset_base <= 0xffffffffull && jp.pool_n <= 0xffffffffull - jp.offset_base);
@@ -770,6 +776,7 @@ int mrn_debug_set(int key, long long value) {
     case 4: g_split_parents.store(value < 0 ? -1 : value); return MRN_OK;
     case 5: g_small_tile_parents.store(value); return MRN_OK;
     case 6: g_split_scan.store(value ? 1 : 0); return MRN_OK;
+    case 7: g_nested_split_children.store(value < 0 ? -1 : value); return MRN_OK;
     default: return MRN_EINVAL;
   }
 }

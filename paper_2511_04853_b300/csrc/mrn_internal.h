@@ -191,6 +191,9 @@ bool jagged_split_ok(const mrn_schema* s, JagPlan* jp, ConvPlan* pool);
 // checked locally): its largest offset, offset_base + pool_n, fits the
 // offset type.
 bool jagged_local_ok(const JagPlan& jp);
+// mrn_debug_set key 7: children from which a nested AoS -> field-major
+// conversion splits its parent level (negative: never).
+long long nested_split_children();
 int launch_jagged_count(const ConvPlan& parent, uint64_t* dev_total, void* stream);
 // Parents' {length, begin} columns from a field-major side's offsets.
 int launch_len_begin(const char* offsets, uint32_t off_size, uint64_t n, unsigned int* len,

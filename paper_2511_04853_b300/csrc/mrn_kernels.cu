@@ -745,15 +745,19 @@ __global__ void __launch_bounds__(MRN_JAG_THREADS, MRN_JAG_CTAS) k_jagged_a2s_re
 
 // Fall-back pass of a split single conversion in the local form (plan mode
 // JAG_FUSED here, the parents' checks done): block 0 first zeroes the
-// destination's gap bytes, which the staged jobs leave; nothing else unless
-// the checks found the pool not canonical, and then the whole conversion
-// again, fused, tiles taken by ticket in increasing order (look-back over
-// tile_state).
+// destination's gap bytes, which the staged jobs leave, and (a canonical
+// pool) writes the children's count, the pool's size, to total_out;
+// nothing else unless the checks found the pool not canonical, and then
+// the whole conversion again, fused, tiles taken by ticket in increasing
+// order (look-back over tile_state; its tiles write total_out).
 __global__ void __launch_bounds__(MRN_JAG_THREADS, MRN_JAG_CTAS) k_jagged_a2s_whole_if(const __grid_constant__ JagPlan jp) {
   if (blockIdx.x == 0)
     for (uint32_t k = 0; k < jp.ngaps; ++k)
       for (uint32_t b = threadIdx.x; b < jp.gap_len[k]; b += blockDim.x) jp.gap_base[jp.gap_off[k] + b] = 0;
-  if (ld_relaxed_u32(jp.noncanon) == 0) return;
+  if (ld_relaxed_u32(jp.noncanon) == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && jp.total_out) *jp.total_out = jp.pool_n;
+    return;
+  }
   constexpr size_t kTw = MRN_JAG_WARPS * MRN_TW_WORDS_PER_WARP * sizeof(uint32_t);
   __shared__ __align__(16) unsigned char jag_raw[kTw > sizeof(JagShared) ? kTw : sizeof(JagShared)];
   uint32_t* tw_all = reinterpret_cast<uint32_t*>(jag_raw);

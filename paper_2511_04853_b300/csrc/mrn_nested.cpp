@@ -98,6 +98,7 @@ int convert_nested(const mrn_view& src, const mrn_view& dst, void* stream) {
   const uint32_t nc = (uint32_t)ch->cols.size();
   if (nc + 2 > MRN_MAX_COLS) return MRN_EUNSUPPORTED;
   const uint64_t mcap = dst.n_children;
+  // (the look-back words of level 0, fused or the split's fall-back)
   const uint64_t lb_bytes = align_up(jagged_scratch_bytes(std::max<uint64_t>(1, jagged_tile_records(jp))), 256);
   const uint64_t len_at = lb_bytes, beg_at = align_up(len_at + 4 * mcap, 256),
                  tot_at = align_up(beg_at + 8 * mcap, 256);
@@ -122,7 +123,36 @@ int convert_nested(const mrn_view& src, const mrn_view& dst, void* stream) {
   unsigned long long* d_total = reinterpret_cast<unsigned long long*>(scratch + tot_at);
   jp.total_out = d_total;
   if (cudaMemsetAsync(d_total, 0, sizeof(unsigned long long), st) != cudaSuccess) return done(MRN_ECUDA);
-  if ((rc = launch_jagged_a2s(jp, scratch, stream))) return done(rc);
+  // Many children: level 0 split in the local form (the parents with their
+  // begins as offsets and the pool's check, then the child pool as one
+  // staged conversion of the child record's flat schema, its {length,
+  // begin} into the scratch columns, and the fused tiles again only for a
+  // pool that is not canonical).  The parents need staged tiles of at most
+  // 768 records and the pool's records a flat schema.
+  const long long split_from = nested_split_children();
+  bool split0 = false;
+  ConvPlan pool0;
+  const FlatParent* fc = split_from >= 0 && src.n_children >= (uint64_t)split_from && src.n_records > 0 &&
+                                 src.n_children > 0 && src.n_children <= mcap && jagged_local_ok(jp)
+                             ? flat_parent_schema(ch)
+                             : nullptr;
+  std::vector<void*> pcols;
+  if (fc) {
+    pcols.resize(fc->src.size());
+    for (size_t k = 0; k < pcols.size(); ++k)
+      pcols[k] = fc->src[k] >= 0 ? kcols[fc->src[k]] : fc->src[k] == -1 ? scratch + len_at : scratch + beg_at;
+    mrn_view ps = device_view(fc->schema.get(), MRN_AOS, src.device, src.n_children, 0);
+    ps.base = src.child_pool;
+    mrn_view pd = device_view(fc->schema.get(), MRN_SOA, dst.device, src.n_children, 0);
+    pd.base = scratch + len_at;  // not read: the columns are given
+    pd.columns = pcols.data();
+    if (build_plan(ps, pd, &pool0) == MRN_OK && pool0.tg.tma) {
+      plan_tiles(s, &jp.parent, MRN_BATCH_STAGE_BYTES);
+      split0 = jp.parent.tg.tma && jp.parent.tg.T <= 768 && !jp.parent.tg.inter;
+    }
+  }
+  if ((rc = split0 ? launch_jagged_a2s_split(jp, pool0, scratch, stream, true) : launch_jagged_a2s(jp, scratch, stream)))
+    return done(rc);
 
   // Level 1, without a return to the host: the children's count M stays in
   // device memory (a count above the capacity is recorded by level 0 as

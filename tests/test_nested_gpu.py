@@ -12,6 +12,19 @@ from gpu_util import dev, garbage, host
 from nested_util import shuffled_nested
 
 pytestmark = pytest.mark.gpu
+NESTED_SPLIT_DEFAULT = 1 << 18  # children from which level 0 of AoS -> field-major runs split (debug key 7)
+
+
+@pytest.fixture(autouse=True, params=["level0_fused", "level0_split"])
+def level0_path(request):
+    """Every test of this module runs twice: level 0 of AoS -> field-major
+    fused (its tiles gather the children and their descriptors), and split
+    (the parents with the child pool's check, the pool as one staged
+    conversion of the child record, the fused tiles again when the pool is
+    not canonical)."""
+    mrn.debug_set(7, -1 if request.param == "level0_fused" else 0)
+    yield request.param
+    mrn.debug_set(7, NESTED_SPLIT_DEFAULT)
 
 SMALL = [
     [("a", "u8", 1), ("v", "jagged", "u32", [("x", "u16", 1), ("w", "jagged", "u32", [("y", "u8", 1)])])],
