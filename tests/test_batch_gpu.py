@@ -448,3 +448,61 @@ def test_batch_pool_checks(case, jagged_path):
             assert (got[m * 4:] == 0xA5).all(), "child rows past the count were written"
         want = oracle.convert(c_o, c_src, "soa").base
         assert np.array_equal(host(c_dst.tensors[0], want.size), want)
+
+
+def test_batch_offset_base_forms(jagged_path):
+    """offset_base in a batch: a canonical pool with a base (the local form
+    writes base + the begins), a shard whose begins start inside a larger
+    pool (the local check fails: the fused fall-back writes the offsets),
+    and a base whose u32 offsets overflow (no local form: the fused job
+    records MRN_EOVERFLOW); the first two equal the oracle's offsets plus
+    their base, with the oracle's children."""
+    s, o = mrn.Schema(datagen.TRACKS), oracle.Schema(datagen.TRACKS)
+    d = datagen.workload("tracks", 6000, 81)
+    o_aos = oracle.pack(o, d, "aos")
+    o_soa = oracle.convert(o, o_aos, "soa", m=d["m"])
+    whole_off = oracle.region(o, o_soa, 3).view(np.uint32).astype(np.uint64)
+    lens = d["lengths"]
+    half = 2500
+    m0, m1 = int(lens[:half].sum()), int(lens[half:].sum())
+    pairs, checks = [], []
+    # 1. the first shard, its own canonical pool, base 123,456
+    sub = oracle.Side("aos", half, m0, base=o_aos.base[: half * 24].copy(), pool=o_aos.pool[: m0 * 8].copy())
+    want1 = oracle.convert(o, sub, "soa", m=m0)
+    offs1, kids1 = garbage((half + 1) * 4), [garbage(m0 * 4) for _ in range(2)]
+    cols1 = [garbage(half * 4) for _ in range(3)]
+    pairs.append((mrn.View(s, "aos", half, base=dev(sub.base), child_pool=dev(sub.pool), m=m0),
+                  mrn.View(s, "soa", half, columns=cols1, offsets=offs1, child_columns=kids1, m=m0,
+                           offset_base=123456)))
+    # 2. the second shard, begins from m0 in the whole pool, base m0 (a child
+    #    capacity of the whole pool, so that a batch may run it split)
+    n2 = 6000 - half
+    pairs.append((mrn.View(s, "aos", n2, base=dev(o_aos.base[half * 24: 6000 * 24].copy()),
+                           child_pool=dev(o_aos.pool), m=o_aos.m),
+                  None))
+    offs2, kids2 = garbage((n2 + 1) * 4), [garbage(o_aos.m * 4) for _ in range(2)]
+    cols2 = [garbage(n2 * 4) for _ in range(3)]
+    pairs[-1] = (pairs[-1][0], mrn.View(s, "soa", n2, columns=cols2, offsets=offs2, child_columns=kids2,
+                                        m=o_aos.m, offset_base=m0))
+    # 3. a base that overflows u32 offsets
+    d3 = datagen.workload("tracks", 600, 82)
+    o3 = oracle.pack(o, d3, "aos")
+    dst3 = dev_dest(s, "soa", 600, d3["m"])
+    dst3.s.offset_base = 2**32 - 100
+    pairs.append((mrn.View(s, "aos", 600, base=dev(o3.base), child_pool=dev(o3.pool), m=d3["m"]), dst3))
+    b = mrn.Batch(pairs, use_graph=True)
+    for _ in range(2):
+        b.launch()
+        bits = mrn.sync_bits()
+        assert bits & (1 << mrn.EOVERFLOW) and not bits & ~(1 << mrn.EOVERFLOW)
+        got1 = host(offs1).view(np.uint32).astype(np.uint64)
+        assert np.array_equal(got1, oracle.region(o, want1, 3).view(np.uint32).astype(np.uint64) + 123456)
+        for c in range(2):
+            assert np.array_equal(host(kids1[c]), oracle.region(o, want1, 4 + c))
+        for c in range(3):
+            assert np.array_equal(host(cols1[c]), oracle.region(o, want1, c))
+            assert np.array_equal(host(cols2[c]), oracle.region(o, o_soa, c)[half * 4:])
+        got2 = host(offs2).view(np.uint32).astype(np.uint64)
+        assert np.array_equal(got2, whole_off[half:])
+        for c in range(2):
+            assert np.array_equal(host(kids2[c], m1 * 4), oracle.region(o, o_soa, 4 + c)[m0 * 4:])
