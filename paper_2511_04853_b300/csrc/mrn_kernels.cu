@@ -1151,8 +1151,30 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_col_scan(const __grid_const
 // entries, the count being read from device memory.
 __global__ void __launch_bounds__(256) k_col_local(const __grid_constant__ ColScan cs) {
   const uint64_t n = cs.count ? min((uint64_t)ld_acquire_u64(cs.count), cs.n) : cs.n;
+  const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
   bool bad = false;
-  for (uint64_t h = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; h < n; h += (uint64_t)gridDim.x * blockDim.x) {
+  uint64_t h = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // four entries per thread and pass, their loads issued together
+  constexpr int U = 4;
+  for (; h + (U - 1) * step < n; h += U * step) {
+    uint32_t len[U];
+    unsigned long long beg[U], next[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t e = h + u * step;
+      len[u] = __ldg(cs.len + e);
+      beg[u] = __ldg(cs.beg + e);
+      next[u] = e + 1 < n ? __ldg(cs.beg + e + 1) : cs.pool_n;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t e = h + u * step;
+      bad |= beg[u] + len[u] != next[u] || (e == 0 && beg[u] != 0);
+      write_offset(cs.offsets, cs.off_size, e, beg[u]);
+      if (e + 1 == n) write_offset(cs.offsets, cs.off_size, n, cs.pool_n);
+    }
+  }
+  for (; h < n; h += step) {
     const uint32_t len = __ldg(cs.len + h);
     const unsigned long long beg = __ldg(cs.beg + h);
     const unsigned long long next = h + 1 < n ? __ldg(cs.beg + h + 1) : cs.pool_n;
